@@ -1,0 +1,329 @@
+"""FP64 CPU oracle of one vegas+ iteration -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference legs may import this package.  The product library never does, and
+this package never imports the product.
+
+The arithmetic lives in ``vegasp_oracle.c`` (plain C, FP64, sequential); this
+module loads it with ctypes and strings the steps of the method together in the
+paper's order (Lepage, arXiv:2009.05112):
+
+* one iteration = sampling + moments + histograms (§2.3, §2.4, §3 step 2),
+  then the estimate I_j, sigma_j^2 (§3 Eq. sumI);
+* adaptation = reallocation (§3 steps 2-4, Eqs. dh, nh) and grid refinement
+  of every axis (§2.3) from the same iteration's data (§3, last paragraph);
+* combination of iterations = weighted mean, its error and chi^2 (§2.5).
+
+Each function names the passage it follows.  Parity status of every function
+is recorded in its docstring ("pinned by ..." / "parity unpinned").
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+
+KIND_GAUSS, KIND_BALL, KIND_EXPNORM, KIND_POSTERIOR = 0, 1, 2, 3
+
+
+def lib():
+    """Load (building first if needed) the oracle's shared object."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.or_philox4x32_10.restype = None
+        L.or_nstrat.argtypes = [ctypes.c_int, ctypes.c_int64]
+        L.or_nstrat.restype = ctypes.c_int64
+        L.or_integrand.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p]
+        L.or_integrand.restype = ctypes.c_double
+        L.or_integrand_many.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, ctypes.c_int64, _f64p,
+                                        _f64p]
+        L.or_integrand_many.restype = None
+        L.or_eval_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                     ctypes.c_uint32, _f64p, ctypes.c_int, _f64p, ctypes.c_uint32,
+                                     ctypes.c_uint64, ctypes.c_uint32, _f64p, _i32p,
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+        L.or_eval_sample.restype = None
+        L.or_sample_iteration.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                          ctypes.c_uint64, ctypes.c_uint32, _f64p, ctypes.c_int,
+                                          _f64p, ctypes.c_uint32, _u32p, _f64p, _f64p, _f64p,
+                                          _f64p]
+        L.or_sample_iteration.restype = ctypes.c_int
+        L.or_tree_sum.argtypes = [_f64p, ctypes.c_int64]
+        L.or_tree_sum.restype = ctypes.c_double
+        L.or_estimate.argtypes = [ctypes.c_int64, ctypes.c_double, _f64p, _f64p, _u32p, _f64p,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.or_estimate.restype = None
+        L.or_sigma.argtypes = [ctypes.c_int64, ctypes.c_double, _f64p, _f64p, _u32p, _f64p]
+        L.or_sigma.restype = None
+        L.or_damp.argtypes = [ctypes.c_int64, ctypes.c_double, _f64p, _f64p]
+        L.or_damp.restype = None
+        L.or_allocate.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _f64p, _u32p,
+                                  _u64p]
+        L.or_allocate.restype = ctypes.c_int
+        L.or_refine_axis.argtypes = [ctypes.c_int, _f64p, _f64p, _f64p, ctypes.c_double, _f64p,
+                                     _f64p]
+        L.or_refine_axis.restype = None
+        L.or_smooth_compress.argtypes = [ctypes.c_int, _f64p, _f64p, ctypes.c_double, _f64p,
+                                         _f64p]
+        L.or_smooth_compress.restype = ctypes.c_int
+        L.or_regrid.argtypes = [ctypes.c_int, _f64p, _f64p, _f64p]
+        L.or_regrid.restype = None
+        _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------
+# Thin wrappers over the C steps
+# --------------------------------------------------------------------------
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block (Salmon et al. SC'11).  Pinned by the published
+    known-answer vectors (tests/golden/philox4x32_10_kat.txt)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(c, k, out)
+    return out
+
+
+def nstrat(dim, n_ev):
+    """§3 Eq. (Nst_vegasp) as an exact integer.  Pinned by brute force."""
+    return int(lib().or_nstrat(int(dim), int(n_ev)))
+
+
+def integrand(kind, dim, prm, x):
+    """The integrand families of §2.4, §3.1 and App. B at one point.  Pinned by
+    closed forms (erf products, ball volumes) through the quadrature tests."""
+    return float(lib().or_integrand(int(kind), int(dim),
+                                    np.ascontiguousarray(prm, np.float64),
+                                    np.ascontiguousarray(x, np.float64)))
+
+
+def integrand_many(kind, dim, prm, X):
+    """The integrand at the rows of X (n x dim)."""
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, int(dim))
+    out = np.zeros(X.shape[0])
+    lib().or_integrand_many(int(kind), int(dim), np.ascontiguousarray(prm, np.float64),
+                            X.shape[0], X, out)
+    return out
+
+
+def tree_sum(v):
+    """Fixed-order sum over hypercubes (the library's stated summation order).
+    Pinned against math.fsum within its error bound and exactly on integers."""
+    v = np.ascontiguousarray(v, np.float64)
+    return float(lib().or_tree_sum(v, v.size))
+
+
+def estimate(omega, s1, s2, n_h):
+    """§3 Eq. (sumI) with per-hypercube simple-MC estimates (§2.1 Eqs. MCIy,
+    sigest).  Pinned by a hand-computed 3-hypercube example and f = 1."""
+    n = len(n_h)
+    work = np.zeros(max(n, 1), np.float64)
+    I = ctypes.c_double()
+    var = ctypes.c_double()
+    lib().or_estimate(n, float(omega), np.ascontiguousarray(s1, np.float64),
+                      np.ascontiguousarray(s2, np.float64),
+                      np.ascontiguousarray(n_h, np.uint32), work, ctypes.byref(I),
+                      ctypes.byref(var))
+    return I.value, var.value
+
+
+def sigma(omega, s1, s2, n_h):
+    """§3 step 2: sigma_h(Jf) from the iteration's samples."""
+    out = np.zeros(len(n_h), np.float64)
+    lib().or_sigma(len(n_h), float(omega), np.ascontiguousarray(s1, np.float64),
+                   np.ascontiguousarray(s2, np.float64), np.ascontiguousarray(n_h, np.uint32),
+                   out)
+    return out
+
+
+def damp(beta, sig):
+    """§3 Eq. (dh): d_h = sigma_h^beta."""
+    sig = np.ascontiguousarray(sig, np.float64)
+    out = np.zeros_like(sig)
+    lib().or_damp(sig.size, float(beta), sig, out)
+    return out
+
+
+def allocate(n_ev, d, plus2=False):
+    """§3 Eq. (nh) and the exclusive offsets.  Pinned by brute force on small
+    arrays and by the beta = 0 equal split.  Returns (n_h, offsets)."""
+    d = np.ascontiguousarray(d, np.float64)
+    n_h = np.zeros(d.size, np.uint32)
+    off = np.zeros(d.size + 1, np.uint64)
+    rc = lib().or_allocate(d.size, int(n_ev), int(bool(plus2)), d, n_h, off)
+    if rc != 0:
+        raise FloatingPointError("non-finite d_h")
+    return n_h, off
+
+
+def refine_axis(edges, hsum, hcnt, alpha):
+    """§2.3 smoothing, compression and four-step re-gridding of one axis.
+    Pinned by a hand-computed 4-increment example, constant-d invariance and
+    alpha = 0."""
+    edges = np.ascontiguousarray(edges, np.float64)
+    n_g = edges.size - 1
+    out = np.zeros_like(edges)
+    work = np.zeros(2 * n_g, np.float64)
+    lib().or_refine_axis(n_g, edges, np.ascontiguousarray(hsum, np.float64),
+                         np.ascontiguousarray(hcnt, np.float64), float(alpha), out, work)
+    return out
+
+
+def smooth_compress(hsum, hcnt, alpha):
+    """§2.3 d_i, smoothing + normalisation, compression.  Returns None when all
+    d_i vanish.  Pinned by constant and two-increment special cases and by the
+    compression's known value at d = 1/e."""
+    hsum = np.ascontiguousarray(hsum, np.float64)
+    n_g = hsum.size
+    out = np.zeros(n_g)
+    work = np.zeros(n_g)
+    rc = lib().or_smooth_compress(n_g, hsum, np.ascontiguousarray(hcnt, np.float64),
+                                  float(alpha), out, work)
+    return None if rc else out
+
+
+def regrid(edges, d):
+    """§2.3 four-step re-gridding.  Pinned against numpy's piecewise-linear
+    inverse of the cumulative d (np.interp)."""
+    edges = np.ascontiguousarray(edges, np.float64)
+    out = np.zeros_like(edges)
+    lib().or_regrid(edges.size - 1, edges, np.ascontiguousarray(d, np.float64), out)
+    return out
+
+
+def combine(I, var, discard=0):
+    """§2.5: weighted mean, its standard error and chi^2 over iterations j >=
+    discard (the paper's remedy of dropping early iterations).
+
+    reading: if some included sigma_j^2 is zero the weighted mean is undefined;
+    the mean of those zero-variance I_j is returned with error 0.  Pinned by
+    hand-computed values."""
+    I = np.asarray(I, np.float64)[discard:]
+    var = np.asarray(var, np.float64)[discard:]
+    n = I.size
+    if n == 0:
+        return dict(mean=math.nan, sdev=math.nan, chi2=math.nan, dof=0, n_it=0)
+    if np.any(var <= 0.0):
+        zero = var <= 0.0
+        m = float(np.mean(I[zero]))
+        return dict(mean=m, sdev=0.0, chi2=0.0, dof=n - 1, n_it=n)
+    w = 1.0 / var
+    mean = float(np.sum(I * w) / np.sum(w))
+    sdev = float(np.sum(w) ** -0.5)
+    chi2 = float(np.sum((I - mean) ** 2 * w))
+    return dict(mean=mean, sdev=sdev, chi2=chi2, dof=n - 1, n_it=n)
+
+
+def combine_unweighted(I, var, discard=0):
+    """§2.5, last paragraph: unweighted mean of the I_j and mean sigma_j over
+    sqrt(N_it) (used with a frozen map, alpha = 0)."""
+    I = np.asarray(I, np.float64)[discard:]
+    s = np.sqrt(np.asarray(var, np.float64)[discard:])
+    n = I.size
+    return dict(mean=float(np.mean(I)), sdev=float(np.mean(s) / math.sqrt(n)), n_it=n)
+
+
+# --------------------------------------------------------------------------
+# The whole method, iteration by iteration
+# --------------------------------------------------------------------------
+class VegasPlus:
+    """vegas+ (§2-§3) on one integral, FP64, in the paper's step order.
+
+    Parameters follow the library's: dim, lo/hi (the box [a, b] per axis), n_g
+    increments per axis, n_ev samples per iteration, alpha (§2.3), beta (§3 Eq.
+    dh), seed and integral_id (the Philox key and counter word 3), plus2 (the
+    alternative of §3 Eq. nh), kind and prm (integrand family and blob), n_st
+    (0: §3 Eq. Nst_vegasp; otherwise the stratification count to use).
+    """
+
+    def __init__(self, dim, lo, hi, n_g, n_ev, alpha, beta, seed, kind, prm,
+                 integral_id=0, plus2=False, n_st=0):
+        self.dim, self.n_g, self.n_ev = int(dim), int(n_g), int(n_ev)
+        self.alpha, self.beta = float(alpha), float(beta)
+        self.seed, self.integral_id, self.plus2 = int(seed), int(integral_id), bool(plus2)
+        self.kind, self.prm = int(kind), np.ascontiguousarray(prm, np.float64)
+        lo = np.broadcast_to(np.asarray(lo, np.float64), (self.dim,))
+        hi = np.broadcast_to(np.asarray(hi, np.float64), (self.dim,))
+        # §2.3: the first iteration uses a uniform grid.
+        self.edges = np.ascontiguousarray(
+            [lo[m] + (hi[m] - lo[m]) * np.arange(self.n_g + 1) / self.n_g
+             for m in range(self.dim)], np.float64)
+        self.edges[:, 0] = lo
+        self.edges[:, -1] = hi
+        # §3 Eq. (Nst_vegasp), unless a stratification count is forced (N_st = 1
+        # is the simple y-space Monte Carlo of §2.4).
+        self.n_st = int(n_st) if n_st else nstrat(self.dim, self.n_ev)
+        self.n_hc = self.n_st ** self.dim
+        self.omega = 1.0 / float(self.n_hc)
+        # reading: the first allocation is the equal split max(2, floor(N_ev/N_h)).
+        self.n_h, self.offsets = allocate(self.n_ev, np.ones(self.n_hc))
+        self.t = 0
+        self.I, self.var = [], []
+        self.s1 = self.s2 = self.hsum = self.hcnt = None
+
+    def sample(self):
+        """Steps a1-a5 of the current iteration (no state change but the buffers)."""
+        self.s1 = np.zeros(self.n_hc)
+        self.s2 = np.zeros(self.n_hc)
+        self.hsum = np.zeros((self.dim, self.n_g))
+        self.hcnt = np.zeros((self.dim, self.n_g))
+        rc = lib().or_sample_iteration(self.dim, self.n_g, self.n_st, self.seed,
+                                       self.integral_id, self.edges, self.kind, self.prm,
+                                       self.t, self.n_h, self.s1, self.s2, self.hsum,
+                                       self.hcnt)
+        assert rc == 0
+
+    def iterate(self):
+        """One iteration's sampling and estimate (steps a1-a6); returns (I_j, var_j)."""
+        self.sample()
+        I, var = estimate(self.omega, self.s1, self.s2, self.n_h)
+        self.I.append(I)
+        self.var.append(var)
+        self.t += 1
+        return I, var
+
+    def adapt(self):
+        """Step a7 (reallocation) then a8 (refinement), from the same iteration's
+        data (§3: both are updated after every iteration)."""
+        sig = sigma(self.omega, self.s1, self.s2, self.n_h)
+        d = damp(self.beta, sig)
+        self.n_h, self.offsets = allocate(self.n_ev, d, self.plus2)
+        new = np.empty_like(self.edges)
+        for m in range(self.dim):
+            new[m] = refine_axis(self.edges[m], self.hsum[m], self.hcnt[m], self.alpha)
+        self.edges = new
+
+    def eval_sample(self, t, h, j):
+        """x, increment indices, J and f of sample j in hypercube h at iteration t."""
+        x = np.zeros(self.dim)
+        idx = np.zeros(self.dim, np.int32)
+        jac = ctypes.c_double()
+        f = ctypes.c_double()
+        lib().or_eval_sample(self.dim, self.n_g, self.n_st, self.seed, self.integral_id,
+                             self.edges, self.kind, self.prm, int(t), int(h), int(j), x, idx,
+                             ctypes.byref(jac), ctypes.byref(f))
+        return x, idx, jac.value, f.value
+
+    def run(self, n_it, adapt=True):
+        for _ in range(n_it):
+            self.iterate()
+            if adapt:
+                self.adapt()
+        return self
+
+    def result(self, discard=0):
+        return combine(self.I, self.var, discard)
