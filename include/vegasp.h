@@ -1,0 +1,190 @@
+/*
+ * vegasp.h -- C-ABI of libvegasp: the data-parallel hot path of vegas+
+ * (G. P. Lepage, "Adaptive Multidimensional Integration: vegas Enhanced",
+ * arXiv:2009.05112) on one NVIDIA GB300 (sm_103a).
+ *
+ * One adaptive iteration of vegas+ is
+ *   vp_iterate: draw n_h samples in every stratification hypercube h (§3),
+ *               map them through the per-axis vegas map x(y) and its Jacobian
+ *               J(y) (§2.2 Eqs. y, jac; §2.4 Eq. y-Dspace), evaluate the
+ *               integrand, accumulate the per-hypercube sums of J f and (J f)^2
+ *               (§3 step 2), the per-axis increment histograms behind d_i
+ *               (§2.3, §2.4) and the iteration's estimate I_j, sigma_j^2
+ *               (§3 Eq. sumI);
+ *   vp_adapt:   reallocate samples n_h = max(2, N_ev d_h / sum d), d_h =
+ *               sigma_h^beta (§3 steps 2-4, Eqs. dh, nh) and refine every
+ *               axis's grid (§2.3: smoothing, compression with alpha, the
+ *               equal-share re-gridding), both from the same iteration's data
+ *               (§3, last paragraph of the algorithm).
+ *   vp_result:  combine iterations: weighted mean, its error, chi^2 (§2.5).
+ *
+ * The integral is I = int_a^b d^D x f(x) over a box (§2.1 Eq. Iy, §2.4).
+ *
+ * Conventions for every entry point:
+ *  - Host pointers are read during the call only; the library copies what it
+ *    keeps.  Device memory owned by a context is allocated when the context is
+ *    created (through the allocator installed with vp_set_allocator, else
+ *    cudaMallocAsync on the given stream) and released by the destroy call.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued asynchronously on it; calls that return data to the host
+ *    synchronise that stream first.
+ *  - Every call returns a vp_status.  On an error the context is unchanged
+ *    (except after VP_ECUDA, which leaves the CUDA context as the runtime left
+ *    it) and vp_last_error() describes it.  No exception crosses the ABI.
+ *  - Contexts are not thread-safe: one host thread at a time per context.
+ *  - The library runs on the current CUDA device; a context must be used on
+ *    the device it was created on.
+ */
+#ifndef VEGASP_H
+#define VEGASP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VP_OK = 0,
+    VP_EINVAL = 1,      /* bad argument or size beyond a stated limit */
+    VP_ENOMEM = 2,      /* device or host allocation failed */
+    VP_ECUDA = 3,       /* a CUDA runtime call failed */
+    VP_ETIMEOUT = 4,    /* a bounded host wait gave up */
+    VP_ENONFINITE = 5,  /* the integrand produced NaN/Inf (flag read by vp_result) */
+    VP_EBUSY = 6        /* no free slot / resource (server admission) */
+} vp_status;
+
+typedef enum { VP_FP64 = 0, VP_FP32 = 1 } vp_precision;
+
+/* Integrand families (the paper's example shapes).  Parameter blobs are
+ * arrays of doubles:
+ *  VP_GAUSS     [K, {a_k, w_k, c_k[D]} x K]  f = sum_k a_k exp(-|x-c_k|^2/w_k^2)
+ *               (§2.4 Eq. easy; w = 0.1 is the paper's coefficient 100)
+ *  VP_BALL      [K, {a_k, r_k, c_k[D]} x K]  f = sum_k a_k Theta(|x-c_k| < r_k)
+ *               (§2.4 Eq. balls; §1 footnote: the 20-D ball)
+ *  VP_EXPNORM   [K, {a_k, s_k, c_k[D]} x K]  f = sum_k a_k exp(-s_k |x-c_k|)
+ *               (§3.1 Eq. exponentials)
+ *  VP_POSTERIOR [n, P, sigma_y, pw, log_ref, y[n], A[n][P]], D = P + 1,
+ *               x = (c_0..c_{P-1}, w), r_i = y_i - sum_m A[i][m] c_m,
+ *               f = exp(sum_i log[(1-w) N(r_i; sigma_y) + w N(r_i; 10 sigma_y)]
+ *                       - sum_m c_m^2/(2 pw^2) - log_ref)
+ *               (App. B Eqs. posterior, prior with Gaussian priors).
+ * Limits: K <= 64; POSTERIOR n <= 256. */
+enum { VP_GAUSS = 0, VP_BALL = 1, VP_EXPNORM = 2, VP_POSTERIOR = 3 };
+
+typedef struct {
+    int kind;            /* VP_GAUSS ... VP_POSTERIOR */
+    int n_param;         /* number of doubles in param */
+    const double *param; /* blob as above; copied */
+} vp_integrand;
+
+typedef struct {
+    int dim;            /* D, 1..24 */
+    const double *lo;   /* [D] lower box edges a (§2.2: x_0 = a); copied */
+    const double *hi;   /* [D] upper box edges b (x_{N_g} = b), hi > lo; copied */
+    int n_g;            /* N_g increments per axis (§2.2), 1..4096 */
+    int64_t n_ev;       /* N_ev samples per iteration (§3), >= 2 */
+    double alpha;       /* grid compression exponent (§2.3), >= 0; 0 freezes the grid */
+    double beta;        /* allocation damping exponent (§3 Eq. dh), >= 0 */
+    uint64_t seed;      /* Philox key */
+    uint32_t integral_id; /* Philox counter word 3: distinguishes integrals sharing a seed */
+    int precision;      /* VP_FP64: map, integrand and moments in FP64.
+                           VP_FP32: map and integrand in FP32, per-hypercube moments
+                           Kahan-compensated FP32, flushed to FP64; estimate,
+                           reallocation and refinement always FP64. */
+    int plus2;          /* 0: n_h = max(2, N_ev d_h/sum d); 1: N_ev d_h/sum d + 2 (§3 Eq. nh) */
+    int n_st;           /* 0: N_st = floor((N_ev/4)^(1/D)) (§3 Eq. Nst_vegasp),
+                           computed exactly; > 0: use this many strata per axis */
+    int max_it;         /* capacity of the iteration history (0 = 1024) */
+} vp_params;
+
+typedef struct {
+    double mean;    /* weighted mean over iterations j >= discard (§2.5) */
+    double sdev;    /* its standard error (§2.5) */
+    double chi2;    /* sum_j (I_j - mean)^2 / sigma_j^2 (§2.5) */
+    int dof;        /* n_it - 1 */
+    int n_it;       /* iterations included */
+    int64_t n_eval; /* integrand evaluations in all iterations so far */
+    double last_i;  /* I_j of the latest iteration */
+    double last_sdev; /* sigma_j of the latest iteration */
+} vp_result_t;
+
+typedef struct vp_ctx vp_ctx;
+
+/* ---- allocator -------------------------------------------------------- */
+/* Device memory for contexts comes from alloc/free when installed (e.g. a
+ * framework's caching allocator), else from cudaMallocAsync/cudaFreeAsync.
+ * alloc returns NULL on failure.  Pass NULLs to restore the default.  Applies
+ * to contexts created afterwards; each context frees with the allocator it
+ * was created with. */
+typedef void *(*vp_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*vp_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+vp_status vp_set_allocator(vp_alloc_fn alloc, vp_free_fn free_fn, void *user);
+
+/* ---- the four calls of the method --------------------------------------- */
+
+/* Creates a context for one integral: validates the parameters (VP_EINVAL on
+ * D outside 1..24, N_g outside 1..4096, N_ev < 2, lo >= hi, alpha/beta < 0 or
+ * not finite, a malformed blob, N_st^D > 2^31, or (N_ev + 2 N_h) ceil(D/4) >=
+ * 2^32 (the Philox counter word 0)), computes N_st, allocates every device
+ * buffer, starts from a uniform grid (§2.3) and the equal split n_h =
+ * max(2, floor(N_ev / N_h)).  *out receives the context. */
+vp_status vp_map_create(const vp_params *params, const vp_integrand *f, void *stream,
+                        vp_ctx **out);
+
+/* One iteration's sampling, moments, histograms and estimate (steps a1-a6),
+ * enqueued on stream.  Iteration t uses Philox counters (j ceil(D/4) + q, h, t,
+ * integral_id) with key (seed_lo, seed_hi). */
+vp_status vp_iterate(vp_ctx *ctx, void *stream);
+
+/* Reallocation (a7) then grid refinement (a8, skipped when alpha == 0), from
+ * the data of the latest vp_iterate. */
+vp_status vp_adapt(vp_ctx *ctx, void *stream);
+
+/* vp_iterate + vp_adapt replayed from a CUDA graph captured on first use. */
+vp_status vp_step(vp_ctx *ctx, void *stream);
+
+/* Synchronises the context's stream, reads the iteration history and
+ * combines iterations j >= discard (§2.5).  VP_ENONFINITE if any iteration saw
+ * a non-finite integrand value (out still filled). */
+vp_status vp_result(vp_ctx *ctx, int discard, vp_result_t *out);
+
+vp_status vp_map_destroy(vp_ctx *ctx);
+
+/* Message of the latest failing call on this thread (never NULL). */
+const char *vp_last_error(void);
+
+/* ---- inspection and test hooks (host buffers; each synchronises) ------- */
+vp_status vp_get_info(vp_ctx *ctx, int64_t *n_st, int64_t *n_hc, int *n_it);
+/* edges[D][N_g + 1] (FP64 master grid) */
+vp_status vp_get_edges(vp_ctx *ctx, double *edges);
+/* replaces the grid (edges[D][N_g+1], strictly increasing, ends = box) */
+vp_status vp_set_edges(vp_ctx *ctx, const double *edges);
+/* n_h[N_h] and offsets[N_h + 1] of the current allocation */
+vp_status vp_get_alloc(vp_ctx *ctx, uint32_t *n_h, uint64_t *offsets);
+/* per-hypercube sums S1_h = sum J f, S2_h = sum (J f)^2 of the latest iteration */
+vp_status vp_get_moments(vp_ctx *ctx, double *s1, double *s2);
+/* histograms hsum[D][N_g] = sum (J f)^2 and hcnt[D][N_g] = sample counts */
+vp_status vp_get_hist(vp_ctx *ctx, double *hsum, double *hcnt);
+/* I_j and sigma_j^2 of the first n iterations */
+vp_status vp_get_history(vp_ctx *ctx, int n, double *i_j, double *var_j);
+/* Reallocation (a7) from given d_h[N_h] (skips sigma_h and the damping) or
+ * from given sigma_h[N_h] (applies d_h = sigma_h^beta); sets n_h and offsets. */
+vp_status vp_alloc_from_dh(vp_ctx *ctx, const double *d_h, void *stream);
+vp_status vp_alloc_from_sigma(vp_ctx *ctx, const double *sigma_h, void *stream);
+/* Grid refinement (a8) from given histograms hsum/hcnt[D][N_g]. */
+vp_status vp_refine_from_hist(vp_ctx *ctx, const double *hsum, const double *hcnt,
+                              void *stream);
+/* Evaluates n samples (h[k], j[k]) of iteration t with the sampling kernel's
+ * own device code: x[n][D], idx[n][D] (increment indices), jac[n], f[n]. */
+vp_status vp_eval_samples(vp_ctx *ctx, int64_t n, const uint64_t *h, const uint32_t *j,
+                          uint32_t t, double *x, int32_t *idx, double *jac, double *f);
+/* Device-side timing of the latest sampling launch, in ms (CUDA events on the
+ * launching stream); -1 if none recorded. */
+vp_status vp_last_sample_ms(vp_ctx *ctx, float *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VEGASP_H */

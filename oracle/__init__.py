@@ -61,6 +61,12 @@ def lib():
                                           _f64p, ctypes.c_uint32, _u32p, _f64p, _f64p, _f64p,
                                           _f64p]
         L.or_sample_iteration.restype = ctypes.c_int
+        L.or_hcube_moments.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                       ctypes.c_uint32, _f64p, ctypes.c_int, _f64p,
+                                       ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+        L.or_hcube_moments.restype = None
         L.or_tree_sum.argtypes = [_f64p, ctypes.c_int64]
         L.or_tree_sum.restype = ctypes.c_double
         L.or_estimate.argtypes = [ctypes.c_int64, ctypes.c_double, _f64p, _f64p, _u32p, _f64p,
@@ -317,6 +323,15 @@ class VegasPlus:
                              self.edges, self.kind, self.prm, int(t), int(h), int(j), x, idx,
                              ctypes.byref(jac), ctypes.byref(f))
         return x, idx, jac.value, f.value
+
+    def hcube_moments(self, t, h, n):
+        """S1_h, S2_h of hypercube h with n samples at iteration t (same sample
+        sequence as sample())."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        lib().or_hcube_moments(self.dim, self.n_g, self.n_st, self.seed, self.integral_id,
+                               self.edges, self.kind, self.prm, int(t), int(h), int(n),
+                               ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
 
     def run(self, n_it, adapt=True):
         for _ in range(n_it):

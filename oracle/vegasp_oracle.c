@@ -244,6 +244,25 @@ int or_sample_iteration(int dim, int n_g, int64_t n_st, uint64_t seed, uint32_t 
     return 0;
 }
 
+/* S1_h, S2_h of one hypercube h with n samples (for spot checks at sizes  */
+/* where a whole iteration is too slow on the CPU).                          */
+void or_hcube_moments(int dim, int n_g, int64_t n_st, uint64_t seed, uint32_t integral_id,
+                      const double *edges, int kind, const double *prm, uint32_t t,
+                      uint64_t h, uint32_t n, double *s1, double *s2) {
+    or_problem P = {dim, n_g, n_st, seed, integral_id, edges, kind, prm};
+    double x[64];
+    int idx[64];
+    double a1 = 0.0, a2 = 0.0;
+    for (uint32_t j = 0; j < n; ++j) {
+        double f;
+        double jf = or_sample(&P, t, h, j, x, idx, &f) * f;
+        a1 += jf;
+        a2 += jf * jf;
+    }
+    *s1 = a1;
+    *s2 = a2;
+}
+
 /* ------------------------------------------------------------------------ */
 /* reading (summation order): every sum over hypercubes is taken in one fixed */
 /* order -- blocks of 1024 consecutive terms, each summed by pairwise halving */

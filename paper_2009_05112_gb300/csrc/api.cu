@@ -1,0 +1,865 @@
+// api.cu -- host side of libvegasp: the C-ABI of include/vegasp.h.
+//
+// A context owns one "problem set" (one integral here; the batched entry
+// points reuse the same machinery with many).  All state lives in one device
+// arena per set, laid out member by member; kernels find it through a device
+// array of descriptors.  Nothing per iteration crosses to the host: the
+// iteration counter, the scale exponent, sum_h d_h and the allocation totals
+// are device scalars, so an iterate+adapt pair can be captured once as a CUDA
+// graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sample_impl.cuh"
+#include "vp_internal.cuh"
+
+namespace vp {
+cudaError_t launch_zero(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t);
+cudaError_t launch_chunks(const Desc *, const uint32_t *, int, uint64_t *, uint32_t *, uint32_t,
+                          cudaStream_t);
+cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
+cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t);
+cudaError_t launch_refine(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
+}  // namespace vp
+
+using namespace vp;
+
+// ---------------------------------------------------------------------------
+// errors and allocator
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err = "no error";
+
+static vp_status fail(vp_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(VP_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+static vp_alloc_fn g_alloc = nullptr;
+static vp_free_fn g_free = nullptr;
+static void *g_user = nullptr;
+
+extern "C" vp_status vp_set_allocator(vp_alloc_fn alloc, vp_free_fn free_fn, void *user) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(VP_EINVAL, "vp_set_allocator: give both alloc and free, or neither");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_user = user;
+    return VP_OK;
+}
+
+extern "C" const char *vp_last_error(void) { return g_err.c_str(); }
+
+struct DevMem {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    vp_alloc_fn alloc = nullptr;
+    vp_free_fn free_fn = nullptr;
+    void *user = nullptr;
+};
+
+static vp_status dev_alloc(DevMem &m, size_t bytes, cudaStream_t s) {
+    m.bytes = bytes;
+    m.alloc = g_alloc;
+    m.free_fn = g_free;
+    m.user = g_user;
+    if (bytes == 0) return VP_OK;
+    if (m.alloc) {
+        m.ptr = m.alloc(bytes, (void *)s, m.user);
+        if (!m.ptr) return fail(VP_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(&m.ptr, bytes, s);
+        if (e != cudaSuccess) {
+            m.ptr = nullptr;
+            cudaGetLastError();
+            return fail(VP_ENOMEM, "cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    return VP_OK;
+}
+
+static void dev_free(DevMem &m, cudaStream_t s) {
+    if (!m.ptr) return;
+    if (m.free_fn) m.free_fn(m.ptr, m.bytes, (void *)s, m.user);
+    else cudaFreeAsync(m.ptr, s);
+    m.ptr = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// the problem set
+// ---------------------------------------------------------------------------
+struct Member {
+    vp_params p;
+    int kind;
+    std::vector<double> lo, hi, prm;
+    std::vector<float> prm32;
+    int64_t n_st;
+    uint64_t n_hc;
+    uint32_t n_tree;
+    int hist_cap;
+    int bucket;
+    size_t off_bytes[20];  // offsets of the buffers within the arena
+};
+
+struct Group {
+    int bucket, kind, prec;
+    std::vector<uint32_t> members;
+    uint32_t *d_members = nullptr;
+    uint64_t *d_chunk_base = nullptr;
+    uint32_t *d_head = nullptr;
+    int threads = 256, R = 1, blocks = 1, hist_shared = 0, hist_words = 0;
+    size_t smem = 0;
+};
+
+struct Set {
+    int device = 0;
+    int n_sm = 0;
+    std::vector<Member> m;
+    std::vector<Desc> h_desc;
+    std::vector<Group> groups;
+    DevMem arena;
+    Desc *d_desc = nullptr;
+    uint32_t *d_tree_base = nullptr, *d_axis_base = nullptr;
+    uint32_t n_tree_total = 0, n_axis_total = 0;
+    int max_ng = 1;
+    bool any_refine = false;
+    cudaStream_t last = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+struct vp_ctx {
+    Set set;
+};
+
+static int bucket_of(int dim) {
+    if (dim <= 4) return 0;
+    if (dim <= 8) return 1;
+    if (dim <= 12) return 2;
+    if (dim <= 16) return 3;
+    return 4;
+}
+
+// floor((N_ev/4)^(1/D)) as the largest n >= 1 with 4 n^D <= N_ev.
+static int64_t nstrat_exact(int dim, int64_t n_ev) {
+    auto fits = [&](int64_t n) {
+        int64_t lim = n_ev / 4, p = 1;
+        for (int i = 0; i < dim; ++i) {
+            if (p > lim / n) return false;
+            p *= n;
+        }
+        return p <= lim;
+    };
+    if (n_ev < 4) return 1;
+    int64_t n = (int64_t)std::floor(std::pow((double)n_ev / 4.0, 1.0 / (double)dim));
+    if (n < 1) n = 1;
+    while (n > 1 && !fits(n)) --n;
+    while (fits(n + 1)) ++n;
+    return n;
+}
+
+static vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb) {
+    if (!p || !f) return fail(VP_EINVAL, "NULL params or integrand");
+    if (p->dim < 1 || p->dim > kMaxDim) return fail(VP_EINVAL, "dim %d outside 1..%d", p->dim, kMaxDim);
+    if (p->n_g < 1 || p->n_g > kMaxNg) return fail(VP_EINVAL, "n_g %d outside 1..%d", p->n_g, kMaxNg);
+    if (p->n_ev < 2) return fail(VP_EINVAL, "n_ev must be >= 2");
+    if (!p->lo || !p->hi) return fail(VP_EINVAL, "NULL box");
+    for (int i = 0; i < p->dim; ++i)
+        if (!(std::isfinite(p->lo[i]) && std::isfinite(p->hi[i]) && p->lo[i] < p->hi[i]))
+            return fail(VP_EINVAL, "box axis %d: need finite lo < hi", i);
+    if (!(p->alpha >= 0.0 && std::isfinite(p->alpha))) return fail(VP_EINVAL, "alpha must be finite and >= 0");
+    if (!(p->beta >= 0.0 && std::isfinite(p->beta))) return fail(VP_EINVAL, "beta must be finite and >= 0");
+    if (p->precision != VP_FP64 && p->precision != VP_FP32) return fail(VP_EINVAL, "bad precision");
+    if (p->n_st < 0) return fail(VP_EINVAL, "n_st must be >= 0");
+    if (p->max_it < 0 || p->max_it > (1 << 24)) return fail(VP_EINVAL, "max_it outside 0..2^24");
+    if (f->n_param < 1 || !f->param) return fail(VP_EINVAL, "empty integrand blob");
+    const int D = p->dim;
+    const double *q = f->param;
+    const int n = f->n_param;
+    switch (f->kind) {
+        case VP_GAUSS:
+        case VP_BALL:
+        case VP_EXPNORM: {
+            const double Kd = q[0];
+            if (!(Kd >= 1 && Kd <= kMaxPeaks && Kd == std::floor(Kd)))
+                return fail(VP_EINVAL, "peak count must be 1..%d", kMaxPeaks);
+            const int K = (int)Kd;
+            if (n != 1 + K * (2 + D)) return fail(VP_EINVAL, "blob needs %d doubles, got %d", 1 + K * (2 + D), n);
+            break;
+        }
+        case VP_POSTERIOR: {
+            if (n < 5) return fail(VP_EINVAL, "posterior blob too short");
+            const double nd = q[0], Pd = q[1];
+            if (!(nd >= 1 && nd <= kMaxPoints && nd == std::floor(nd)))
+                return fail(VP_EINVAL, "posterior point count must be 1..%d", kMaxPoints);
+            if (!(Pd == D - 1 && Pd >= 1)) return fail(VP_EINVAL, "posterior needs P = dim - 1 >= 1");
+            const int np = (int)nd, P = (int)Pd;
+            if (n != 5 + np + np * P) return fail(VP_EINVAL, "posterior blob needs %d doubles", 5 + np + np * P);
+            if (!(q[2] > 0 && q[3] > 0)) return fail(VP_EINVAL, "posterior widths must be > 0");
+            break;
+        }
+        default:
+            return fail(VP_EINVAL, "unknown integrand kind %d", f->kind);
+    }
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(q[i])) return fail(VP_EINVAL, "non-finite integrand parameter %d", i);
+    mb.p = *p;
+    mb.kind = f->kind;
+    mb.lo.assign(p->lo, p->lo + D);
+    mb.hi.assign(p->hi, p->hi + D);
+    mb.prm.assign(q, q + n);
+    mb.n_st = p->n_st > 0 ? p->n_st : nstrat_exact(D, p->n_ev);
+    // N_h = N_st^D <= 2^31
+    uint64_t nh = 1;
+    for (int i = 0; i < D; ++i) {
+        nh *= (uint64_t)mb.n_st;
+        if (nh > (1ull << 31)) return fail(VP_EINVAL, "N_st^D exceeds 2^31 hypercubes");
+    }
+    mb.n_hc = nh;
+    const uint64_t calls = (uint64_t)((D + 3) / 4);
+    const uint64_t max_nh = (uint64_t)p->n_ev + 2 * nh + 2;
+    if (max_nh * calls >= (1ull << 32))
+        return fail(VP_EINVAL, "(N_ev + 2 N_h) ceil(D/4) must stay below 2^32 (Philox counter word 0)");
+    mb.n_tree = (uint32_t)((nh + kTreeBlock - 1) / kTreeBlock);
+    mb.hist_cap = p->max_it > 0 ? p->max_it : 1024;
+    mb.bucket = bucket_of(D);
+    // FP32 integrand constants
+    const double L2E = 1.4426950408889634074;
+    mb.prm32.clear();
+    if (f->kind == VP_POSTERIOR) {
+        const int np = (int)q[0], P = (int)q[1];
+        const double sy = q[2], pw = q[3], lref = q[4];
+        const double s2pi = std::sqrt(2.0 * M_PI);
+        mb.prm32.push_back((float)np);
+        mb.prm32.push_back((float)P);
+        mb.prm32.push_back((float)(L2E / (2.0 * sy * sy)));
+        mb.prm32.push_back((float)(L2E / (200.0 * sy * sy)));
+        mb.prm32.push_back((float)std::log2(1.0 / (s2pi * sy)));
+        mb.prm32.push_back((float)std::log2(1.0 / (s2pi * 10.0 * sy)));
+        mb.prm32.push_back((float)(L2E / (2.0 * pw * pw)));
+        mb.prm32.push_back((float)(lref * L2E));
+        for (int i = 0; i < np; ++i) mb.prm32.push_back((float)q[5 + i]);
+        for (int i = 0; i < np * P; ++i) mb.prm32.push_back((float)q[5 + np + i]);
+    } else {
+        const int K = (int)q[0];
+        for (int k = 0; k < K; ++k) {
+            const double *pk = q + 1 + k * (2 + D);
+            mb.prm32.push_back((float)pk[0]);
+            if (f->kind == VP_GAUSS) mb.prm32.push_back((float)(L2E / (pk[1] * pk[1])));
+            else if (f->kind == VP_BALL) mb.prm32.push_back((float)(pk[1] * pk[1]));
+            else mb.prm32.push_back((float)(pk[1] * L2E));
+            for (int i = 0; i < D; ++i) mb.prm32.push_back((float)pk[2 + i]);
+        }
+    }
+    return VP_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+enum {
+    B_EDGES, B_TAB, B_PRM, B_PRM32, B_NH, B_OFF, B_S1, B_S2, B_DH, B_HSUM, B_HCNT, B_PART,
+    B_BSUM, B_HI, B_HV, B_ST, B_COUNT
+};
+
+static size_t member_layout(Member &mb, size_t base) {
+    const size_t D = mb.p.dim, G = mb.p.n_g, H = mb.n_hc, T = mb.n_tree, C = mb.hist_cap;
+    const size_t sz[B_COUNT] = {D * (G + 1) * 8, D * G * 8, mb.prm.size() * 8,
+                                mb.prm32.size() * 4, H * 4, (H + 1) * 8, H * 8, H * 8, H * 8,
+                                D * G * 8, D * G * 4, T * 3 * 8, T * 8, C * 8, C * 8,
+                                sizeof(State)};
+    for (int i = 0; i < B_COUNT; ++i) {
+        mb.off_bytes[i] = base;
+        base = align256(base + sz[i]);
+    }
+    return base;
+}
+
+template <typename T>
+static T *at(const Set &s, const Member &mb, int which) {
+    return (T *)((char *)s.arena.ptr + mb.off_bytes[which]);
+}
+
+// FP32 mirror {x_i, N_g dx_i} of one axis.
+static void make_tab(const double *e, int n_g, float2 *tab) {
+    for (int i = 0; i < n_g; ++i)
+        tab[i] = make_float2((float)e[i], (float)((double)n_g * (e[i + 1] - e[i])));
+}
+
+static vp_status plan_groups(Set &s) {
+    // one launch group per (bucket, kind, precision)
+    for (uint32_t i = 0; i < s.m.size(); ++i) {
+        const Member &mb = s.m[i];
+        Group *g = nullptr;
+        for (auto &q : s.groups)
+            if (q.bucket == mb.bucket && q.kind == mb.kind && q.prec == mb.p.precision) g = &q;
+        if (!g) {
+            s.groups.push_back(Group());
+            g = &s.groups.back();
+            g->bucket = mb.bucket;
+            g->kind = mb.kind;
+            g->prec = mb.p.precision;
+        }
+        g->members.push_back(i);
+    }
+    for (auto &g : s.groups) {
+        double expect = 0.0;
+        int max_bins = 0, max_words = 0;
+        for (uint32_t i : g.members) {
+            expect += (double)s.m[i].p.n_ev + 2.0 * (double)s.m[i].n_hc;
+            max_bins = std::max(max_bins, s.m[i].p.dim * s.m[i].p.n_g);
+            max_words = std::max(max_words, (int)s.m[i].prm32.size());
+        }
+        const size_t tbytes = g.prec == VP_FP64 ? 8 : 4;
+        const size_t hist_bytes = (size_t)max_bins * (tbytes + 4);
+        g.threads = 256;
+        g.hist_words = max_bins;
+        const int occ_probe = g.prec == VP_FP64
+                                  ? sample_occupancy_f64(g.bucket, g.kind, g.threads, 0)
+                                  : sample_occupancy_f32(g.bucket, g.kind, g.threads, 0);
+        const double per_cta = expect / std::max(1, s.n_sm * std::max(1, occ_probe));
+        g.hist_shared = (hist_bytes <= 64 * 1024 && per_cta >= 0.5 * max_bins) ? 1 : 0;
+        g.smem = g.hist_shared ? hist_bytes : 0;
+        if (g.smem > 48 * 1024) {
+            cudaError_t e = g.prec == VP_FP64
+                                ? sample_smem_config_f64(g.bucket, g.kind, (int)g.smem)
+                                : sample_smem_config_f32(g.bucket, g.kind, (int)g.smem);
+            if (e != cudaSuccess) return fail(VP_ECUDA, "smem config: %s", cudaGetErrorString(e));
+        }
+        int occ = g.prec == VP_FP64 ? sample_occupancy_f64(g.bucket, g.kind, g.threads, g.smem)
+                                    : sample_occupancy_f32(g.bucket, g.kind, g.threads, g.smem);
+        if (occ < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem);
+        g.blocks = s.n_sm * occ;
+        const double per_thread = expect / ((double)g.blocks * g.threads * 4.0);
+        g.R = (int)std::min(64.0, std::max(1.0, std::ceil(per_thread)));
+        (void)max_words;
+    }
+    return VP_OK;
+}
+
+static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integrand *fs,
+                            cudaStream_t stream) {
+    if (n < 1 || !ps || !fs) return fail(VP_EINVAL, "need at least one integral");
+    // host-side validation first: no CUDA call before the arguments are known good
+    s.m.resize(n);
+    for (int i = 0; i < n; ++i) {
+        vp_status st = validate(&ps[i], &fs[i], s.m[i]);
+        if (st != VP_OK) return st;
+    }
+    CU(cudaGetDevice(&s.device));
+    CU(cudaDeviceGetAttribute(&s.n_sm, cudaDevAttrMultiProcessorCount, s.device));
+    // arena layout: members, then descriptors and the set-level tables
+    size_t base = 0;
+    for (auto &mb : s.m) base = member_layout(mb, base);
+    const size_t desc_off = base;
+    base = align256(base + n * sizeof(Desc));
+    const size_t tree_off = base;
+    base = align256(base + (n + 1) * 4);
+    const size_t axis_off = base;
+    base = align256(base + (n + 1) * 4);
+    {
+        vp_status pst = plan_groups(s);
+        if (pst != VP_OK) return pst;
+    }
+    std::vector<size_t> gmem_off(s.groups.size() * 3);
+    for (size_t g = 0; g < s.groups.size(); ++g) {
+        gmem_off[3 * g] = base;
+        base = align256(base + s.groups[g].members.size() * 4);
+        gmem_off[3 * g + 1] = base;
+        base = align256(base + (s.groups[g].members.size() + 1) * 8);
+        gmem_off[3 * g + 2] = base;
+        base = align256(base + 16);
+    }
+    vp_status st = dev_alloc(s.arena, base, stream);
+    if (st != VP_OK) return st;
+    char *A = (char *)s.arena.ptr;
+    CU(cudaMemsetAsync(A, 0, base, stream));
+    s.d_desc = (Desc *)(A + desc_off);
+    s.d_tree_base = (uint32_t *)(A + tree_off);
+    s.d_axis_base = (uint32_t *)(A + axis_off);
+    for (size_t g = 0; g < s.groups.size(); ++g) {
+        s.groups[g].d_members = (uint32_t *)(A + gmem_off[3 * g]);
+        s.groups[g].d_chunk_base = (uint64_t *)(A + gmem_off[3 * g + 1]);
+        s.groups[g].d_head = (uint32_t *)(A + gmem_off[3 * g + 2]);
+    }
+    // host images of the initial state
+    std::vector<uint32_t> tree_base(n + 1, 0), axis_base(n + 1, 0);
+    s.h_desc.resize(n);
+    std::vector<char> stage;
+    for (int i = 0; i < n; ++i) {
+        Member &mb = s.m[i];
+        const int D = mb.p.dim, G = mb.p.n_g;
+        Desc &d = s.h_desc[i];
+        memset(&d, 0, sizeof d);
+        d.dim = D;
+        d.n_g = G;
+        d.kind = mb.kind;
+        d.prec = mb.p.precision;
+        d.plus2 = mb.p.plus2 ? 1 : 0;
+        d.n_peaks = (int)mb.prm[0];
+        d.n_par = mb.kind == VP_POSTERIOR ? (int)mb.prm[1] : 0;
+        d.hist_cap = mb.hist_cap;
+        d.n_st = (uint32_t)mb.n_st;
+        d.integral_id = mb.p.integral_id;
+        d.key0 = (uint32_t)mb.p.seed;
+        d.key1 = (uint32_t)(mb.p.seed >> 32);
+        d.n_tree = mb.n_tree;
+        d.n_ev = mb.p.n_ev;
+        d.n_hc = mb.n_hc;
+        d.omega = 1.0 / (double)mb.n_hc;
+        d.alpha = mb.p.alpha;
+        d.beta = mb.p.beta;
+        d.ng_over_nst = (float)((double)G / (double)mb.n_st);
+        d.inv_ng = (float)(1.0 / (double)G);
+        d.edges = at<double>(s, mb, B_EDGES);
+        d.tab = at<float2>(s, mb, B_TAB);
+        d.prm = at<double>(s, mb, B_PRM);
+        d.prm32 = at<float>(s, mb, B_PRM32);
+        d.n_h = at<uint32_t>(s, mb, B_NH);
+        d.off = at<uint64_t>(s, mb, B_OFF);
+        d.s1 = at<double>(s, mb, B_S1);
+        d.s2 = at<double>(s, mb, B_S2);
+        d.dh = at<double>(s, mb, B_DH);
+        d.hsum = at<double>(s, mb, B_HSUM);
+        d.hcnt = at<uint32_t>(s, mb, B_HCNT);
+        d.part = at<double>(s, mb, B_PART);
+        d.bsum = at<uint64_t>(s, mb, B_BSUM);
+        d.hist_i = at<double>(s, mb, B_HI);
+        d.hist_var = at<double>(s, mb, B_HV);
+        d.st = at<State>(s, mb, B_ST);
+        tree_base[i + 1] = tree_base[i] + mb.n_tree;
+        axis_base[i + 1] = axis_base[i] + D;
+        s.max_ng = std::max(s.max_ng, G);
+        if (mb.p.alpha > 0.0 && G > 1) s.any_refine = true;
+        // uniform grid (§2.3: the first iteration uses a uniform grid)
+        std::vector<double> edges((size_t)D * (G + 1));
+        std::vector<float2> tab((size_t)D * G);
+        double vol = 1.0;
+        for (int mu = 0; mu < D; ++mu) {
+            const double a = mb.lo[mu], b = mb.hi[mu];
+            double *e = &edges[(size_t)mu * (G + 1)];
+            for (int k = 0; k <= G; ++k) e[k] = a + (b - a) * (double)k / (double)G;
+            e[0] = a;
+            e[G] = b;
+            make_tab(e, G, &tab[(size_t)mu * G]);
+            vol *= (b - a);
+        }
+        State sti;
+        memset(&sti, 0, sizeof sti);
+        int e = std::ilogb(vol);
+        sti.scale_exp = -(e > 120 ? 120 : (e < -120 ? -120 : e));
+        std::vector<double> ones(mb.n_hc, 1.0);
+        CU(cudaMemcpyAsync(d.edges, edges.data(), edges.size() * 8, cudaMemcpyHostToDevice, stream));
+        CU(cudaMemcpyAsync(d.tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, stream));
+        CU(cudaMemcpyAsync((void *)d.prm, mb.prm.data(), mb.prm.size() * 8, cudaMemcpyHostToDevice, stream));
+        CU(cudaMemcpyAsync((void *)d.prm32, mb.prm32.data(), mb.prm32.size() * 4, cudaMemcpyHostToDevice, stream));
+        CU(cudaMemcpyAsync(d.dh, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, stream));
+        CU(cudaMemcpyAsync(d.st, &sti, sizeof sti, cudaMemcpyHostToDevice, stream));
+        CU(cudaStreamSynchronize(stream));  // host vectors go out of scope
+    }
+    s.n_tree_total = tree_base[n];
+    s.n_axis_total = axis_base[n];
+    CU(cudaMemcpyAsync(s.d_desc, s.h_desc.data(), n * sizeof(Desc), cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(s.d_tree_base, tree_base.data(), (n + 1) * 4, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(s.d_axis_base, axis_base.data(), (n + 1) * 4, cudaMemcpyHostToDevice, stream));
+    for (auto &g : s.groups)
+        CU(cudaMemcpyAsync(g.d_members, g.members.data(), g.members.size() * 4,
+                           cudaMemcpyHostToDevice, stream));
+    // first allocation: d_h = 1 -> max(2, floor(N_ev / N_h)) (the classic equal split)
+    CU(launch_estimate(s.d_desc, s.d_tree_base, n, s.n_tree_total, 2, stream));
+    CU(launch_alloc(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream));
+    CU(cudaEventCreate(&s.ev0));
+    CU(cudaEventCreate(&s.ev1));
+    CU(cudaStreamSynchronize(stream));
+    s.last = stream;
+    return VP_OK;
+}
+
+static void set_destroy(Set &s) {
+    if (!s.arena.ptr && !s.ev0) return;  // nothing was created on the device
+    if (s.gexec) cudaGraphExecDestroy(s.gexec);
+    if (s.graph) cudaGraphDestroy(s.graph);
+    if (s.ev0) cudaEventDestroy(s.ev0);
+    if (s.ev1) cudaEventDestroy(s.ev1);
+    cudaStreamSynchronize(s.last);
+    dev_free(s.arena, s.last);
+    cudaStreamSynchronize(s.last);
+}
+
+static vp_status set_iterate(Set &s, cudaStream_t stream) {
+    const int n = (int)s.m.size();
+    CU(launch_zero(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream));
+    for (size_t gi = 0; gi < s.groups.size(); ++gi) {
+        Group &g = s.groups[gi];
+        CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base, g.d_head,
+                         (uint32_t)(g.threads * g.R), stream));
+    }
+    CU(cudaEventRecord(s.ev0, stream));
+    for (size_t gi = 0; gi < s.groups.size(); ++gi) {
+        Group &g = s.groups[gi];
+        SampleArgs a;
+        a.desc = s.d_desc;
+        a.members = g.d_members;
+        a.chunk_base = g.d_chunk_base;
+        a.head = g.d_head;
+        a.n_group = (int)g.members.size();
+        a.R = g.R;
+        a.hist_shared = g.hist_shared;
+        a.hist_words = g.hist_words;
+        a.prm_words = 0;
+        cudaError_t e = g.prec == VP_FP64
+                            ? launch_sample_f64(g.bucket, g.kind, g.blocks, g.threads, g.smem, stream, a)
+                            : launch_sample_f32(g.bucket, g.kind, g.blocks, g.threads, g.smem, stream, a);
+        if (e != cudaSuccess) return fail(VP_ECUDA, "sampling launch: %s", cudaGetErrorString(e));
+    }
+    CU(cudaEventRecord(s.ev1, stream));
+    s.timed = true;
+    CU(launch_estimate(s.d_desc, s.d_tree_base, n, s.n_tree_total, 0, stream));
+    s.last = stream;
+    return VP_OK;
+}
+
+static vp_status set_adapt(Set &s, cudaStream_t stream) {
+    const int n = (int)s.m.size();
+    CU(launch_alloc(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream));
+    if (s.any_refine)
+        CU(launch_refine(s.d_desc, s.d_axis_base, n, s.n_axis_total, s.max_ng, stream));
+    s.last = stream;
+    return VP_OK;
+}
+
+static vp_status set_step(Set &s, cudaStream_t stream) {
+    if (!s.gexec) {
+        // capture on a private stream so that the caller's stream may be the
+        // legacy default stream (which cannot be captured)
+        cudaStream_t cap;
+        CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        CU(cudaStreamSynchronize(stream));
+        CU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        vp_status st = set_iterate(s, cap);
+        if (st == VP_OK) st = set_adapt(s, cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (st != VP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(VP_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        s.graph = g;
+        CU(cudaGraphInstantiate(&s.gexec, s.graph, 0));
+    }
+    CU(cudaGraphLaunch(s.gexec, stream));
+    s.last = stream;
+    return VP_OK;
+}
+
+// §2.5 combination of iterations j >= discard.
+static void combine(const double *I, const double *V, int n, int discard, vp_result_t *r) {
+    int first = discard < 0 ? 0 : discard;
+    r->n_it = n > first ? n - first : 0;
+    r->dof = r->n_it > 0 ? r->n_it - 1 : 0;
+    r->mean = NAN;
+    r->sdev = NAN;
+    r->chi2 = NAN;
+    if (r->n_it == 0) return;
+    int zero = 0;
+    double zsum = 0.0;
+    for (int j = first; j < n; ++j)
+        if (!(V[j] > 0.0)) {
+            ++zero;
+            zsum += I[j];
+        }
+    if (zero) {  // reading: zero-variance iterations are exact
+        r->mean = zsum / zero;
+        r->sdev = 0.0;
+        r->chi2 = 0.0;
+        return;
+    }
+    double sw = 0.0, swi = 0.0;
+    for (int j = first; j < n; ++j) {
+        sw += 1.0 / V[j];
+        swi += I[j] / V[j];
+    }
+    r->mean = swi / sw;
+    r->sdev = 1.0 / std::sqrt(sw);
+    double c = 0.0;
+    for (int j = first; j < n; ++j) c += (I[j] - r->mean) * (I[j] - r->mean) / V[j];
+    r->chi2 = c;
+}
+
+static vp_status member_result(Set &s, int i, int discard, vp_result_t *out) {
+    CU(cudaStreamSynchronize(s.last));
+    const Desc &d = s.h_desc[i];
+    State st;
+    CU(cudaMemcpy(&st, d.st, sizeof st, cudaMemcpyDeviceToHost));
+    const int n = (int)std::min<uint32_t>(st.t, (uint32_t)d.hist_cap);
+    std::vector<double> I(n), V(n);
+    if (n) {
+        CU(cudaMemcpy(I.data(), d.hist_i, n * 8, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(V.data(), d.hist_var, n * 8, cudaMemcpyDeviceToHost));
+    }
+    memset(out, 0, sizeof *out);
+    combine(I.data(), V.data(), n, discard, out);
+    out->n_eval = (int64_t)st.n_eval_total;
+    out->last_i = st.last_i;
+    out->last_sdev = std::sqrt(st.last_var);
+    if (st.status & kStatusNonFinite) return fail(VP_ENONFINITE, "integrand produced a non-finite value");
+    return VP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+#define CHECK_CTX(c) \
+    if (!(c)) return fail(VP_EINVAL, "NULL context")
+
+extern "C" vp_status vp_map_create(const vp_params *params, const vp_integrand *f, void *stream,
+                                   vp_ctx **out) {
+    if (!out) return fail(VP_EINVAL, "NULL out");
+    *out = nullptr;
+    vp_ctx *c = new (std::nothrow) vp_ctx();
+    if (!c) return fail(VP_ENOMEM, "host allocation failed");
+    vp_status st = set_create(c->set, 1, params, f, (cudaStream_t)stream);
+    if (st != VP_OK) {
+        std::string keep = g_err;
+        set_destroy(c->set);
+        delete c;
+        g_err = keep;
+        return st;
+    }
+    *out = c;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_iterate(vp_ctx *c, void *stream) {
+    CHECK_CTX(c);
+    return set_iterate(c->set, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_adapt(vp_ctx *c, void *stream) {
+    CHECK_CTX(c);
+    return set_adapt(c->set, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_step(vp_ctx *c, void *stream) {
+    CHECK_CTX(c);
+    return set_step(c->set, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_result(vp_ctx *c, int discard, vp_result_t *out) {
+    CHECK_CTX(c);
+    if (!out) return fail(VP_EINVAL, "NULL out");
+    return member_result(c->set, 0, discard, out);
+}
+
+extern "C" vp_status vp_map_destroy(vp_ctx *c) {
+    if (!c) return VP_OK;
+    set_destroy(c->set);
+    delete c;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_info(vp_ctx *c, int64_t *n_st, int64_t *n_hc, int *n_it) {
+    CHECK_CTX(c);
+    CU(cudaStreamSynchronize(c->set.last));
+    State st;
+    CU(cudaMemcpy(&st, c->set.h_desc[0].st, sizeof st, cudaMemcpyDeviceToHost));
+    if (n_st) *n_st = c->set.m[0].n_st;
+    if (n_hc) *n_hc = (int64_t)c->set.m[0].n_hc;
+    if (n_it) *n_it = (int)st.t;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_edges(vp_ctx *c, double *edges) {
+    CHECK_CTX(c);
+    if (!edges) return fail(VP_EINVAL, "NULL edges");
+    const Desc &d = c->set.h_desc[0];
+    CU(cudaStreamSynchronize(c->set.last));
+    CU(cudaMemcpy(edges, d.edges, (size_t)d.dim * (d.n_g + 1) * 8, cudaMemcpyDeviceToHost));
+    return VP_OK;
+}
+
+extern "C" vp_status vp_set_edges(vp_ctx *c, const double *edges) {
+    CHECK_CTX(c);
+    if (!edges) return fail(VP_EINVAL, "NULL edges");
+    const Desc &d = c->set.h_desc[0];
+    const Member &mb = c->set.m[0];
+    const int D = d.dim, G = d.n_g;
+    for (int mu = 0; mu < D; ++mu) {
+        const double *e = edges + (size_t)mu * (G + 1);
+        if (e[0] != mb.lo[mu] || e[G] != mb.hi[mu]) return fail(VP_EINVAL, "grid ends must equal the box");
+        for (int k = 0; k < G; ++k)
+            if (!(e[k + 1] > e[k])) return fail(VP_EINVAL, "grid must be strictly increasing");
+    }
+    std::vector<float2> tab((size_t)D * G);
+    for (int mu = 0; mu < D; ++mu) make_tab(edges + (size_t)mu * (G + 1), G, &tab[(size_t)mu * G]);
+    CU(cudaStreamSynchronize(c->set.last));
+    CU(cudaMemcpy(d.edges, edges, (size_t)D * (G + 1) * 8, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(d.tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice));
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_alloc(vp_ctx *c, uint32_t *n_h, uint64_t *offsets) {
+    CHECK_CTX(c);
+    const Desc &d = c->set.h_desc[0];
+    CU(cudaStreamSynchronize(c->set.last));
+    if (n_h) CU(cudaMemcpy(n_h, d.n_h, d.n_hc * 4, cudaMemcpyDeviceToHost));
+    if (offsets) CU(cudaMemcpy(offsets, d.off, (d.n_hc + 1) * 8, cudaMemcpyDeviceToHost));
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_moments(vp_ctx *c, double *s1, double *s2) {
+    CHECK_CTX(c);
+    const Desc &d = c->set.h_desc[0];
+    CU(cudaStreamSynchronize(c->set.last));
+    if (s1) CU(cudaMemcpy(s1, d.s1, d.n_hc * 8, cudaMemcpyDeviceToHost));
+    if (s2) CU(cudaMemcpy(s2, d.s2, d.n_hc * 8, cudaMemcpyDeviceToHost));
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_hist(vp_ctx *c, double *hsum, double *hcnt) {
+    CHECK_CTX(c);
+    const Desc &d = c->set.h_desc[0];
+    const size_t bins = (size_t)d.dim * d.n_g;
+    CU(cudaStreamSynchronize(c->set.last));
+    if (hsum) CU(cudaMemcpy(hsum, d.hsum, bins * 8, cudaMemcpyDeviceToHost));
+    if (hcnt) {
+        std::vector<uint32_t> tmp(bins);
+        CU(cudaMemcpy(tmp.data(), d.hcnt, bins * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < bins; ++i) hcnt[i] = (double)tmp[i];
+    }
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_history(vp_ctx *c, int n, double *i_j, double *var_j) {
+    CHECK_CTX(c);
+    const Desc &d = c->set.h_desc[0];
+    if (n < 0 || n > d.hist_cap) return fail(VP_EINVAL, "n outside the history capacity");
+    CU(cudaStreamSynchronize(c->set.last));
+    if (n && i_j) CU(cudaMemcpy(i_j, d.hist_i, n * 8, cudaMemcpyDeviceToHost));
+    if (n && var_j) CU(cudaMemcpy(var_j, d.hist_var, n * 8, cudaMemcpyDeviceToHost));
+    return VP_OK;
+}
+
+static vp_status alloc_from(vp_ctx *c, const double *v, int mode, cudaStream_t stream) {
+    CHECK_CTX(c);
+    if (!v) return fail(VP_EINVAL, "NULL input");
+    Set &s = c->set;
+    const Desc &d = s.h_desc[0];
+    for (uint64_t h = 0; h < d.n_hc; ++h)
+        if (!(v[h] >= 0.0) || !std::isfinite(v[h])) return fail(VP_EINVAL, "entries must be finite and >= 0");
+    CU(cudaStreamSynchronize(s.last));
+    CU(cudaMemcpyAsync(d.dh, v, d.n_hc * 8, cudaMemcpyHostToDevice, stream));
+    CU(launch_estimate(s.d_desc, s.d_tree_base, 1, s.n_tree_total, mode, stream));
+    CU(launch_alloc(s.d_desc, s.d_tree_base, 1, s.n_tree_total, stream));
+    CU(cudaStreamSynchronize(stream));
+    s.last = stream;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_alloc_from_dh(vp_ctx *c, const double *d_h, void *stream) {
+    return alloc_from(c, d_h, 2, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_alloc_from_sigma(vp_ctx *c, const double *sigma_h, void *stream) {
+    return alloc_from(c, sigma_h, 1, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_refine_from_hist(vp_ctx *c, const double *hsum, const double *hcnt,
+                                         void *stream) {
+    CHECK_CTX(c);
+    if (!hsum || !hcnt) return fail(VP_EINVAL, "NULL histogram");
+    Set &s = c->set;
+    const Desc &d = s.h_desc[0];
+    const size_t bins = (size_t)d.dim * d.n_g;
+    std::vector<uint32_t> cnt(bins);
+    for (size_t i = 0; i < bins; ++i) {
+        if (!(hcnt[i] >= 0.0 && hcnt[i] < 4294967296.0) || hcnt[i] != std::floor(hcnt[i]))
+            return fail(VP_EINVAL, "counts must be integers in [0, 2^32)");
+        if (!std::isfinite(hsum[i]) || hsum[i] < 0.0) return fail(VP_EINVAL, "sums must be finite and >= 0");
+        cnt[i] = (uint32_t)hcnt[i];
+    }
+    CU(cudaStreamSynchronize(s.last));
+    CU(cudaMemcpyAsync(d.hsum, hsum, bins * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CU(cudaMemcpyAsync(d.hcnt, cnt.data(), bins * 4, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CU(launch_refine(s.d_desc, s.d_axis_base, 1, s.n_axis_total, s.max_ng, (cudaStream_t)stream));
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    s.last = (cudaStream_t)stream;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_eval_samples(vp_ctx *c, int64_t n, const uint64_t *h, const uint32_t *j,
+                                     uint32_t t, double *x, int32_t *idx, double *jac, double *f) {
+    CHECK_CTX(c);
+    if (n < 0) return fail(VP_EINVAL, "n < 0");
+    if (n == 0) return VP_OK;
+    if (!h || !j || !x || !idx || !jac || !f) return fail(VP_EINVAL, "NULL buffer");
+    Set &s = c->set;
+    const Desc &d = s.h_desc[0];
+    for (int64_t k = 0; k < n; ++k)
+        if (h[k] >= d.n_hc) return fail(VP_EINVAL, "hypercube index %llu out of range", (unsigned long long)h[k]);
+    const size_t D = d.dim;
+    const size_t bytes = n * (8 + 4 + D * 8 + D * 4 + 8 + 8) + 6 * 256;
+    DevMem tmp;
+    cudaStream_t stream = s.last;
+    CU(cudaStreamSynchronize(stream));
+    vp_status st = dev_alloc(tmp, bytes, stream);
+    if (st != VP_OK) return st;
+    char *p = (char *)tmp.ptr;
+    uint64_t *dh_ = (uint64_t *)p;
+    p += align256(n * 8);
+    uint32_t *dj = (uint32_t *)p;
+    p += align256(n * 4);
+    double *dx = (double *)p;
+    p += align256(n * D * 8);
+    int32_t *di = (int32_t *)p;
+    p += align256(n * D * 4);
+    double *djac = (double *)p;
+    p += align256(n * 8);
+    double *df = (double *)p;
+    cudaError_t e = cudaMemcpyAsync(dh_, h, n * 8, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dj, j, n * 4, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = d.prec == VP_FP64
+                ? launch_eval_f64(s.m[0].bucket, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di, djac, df)
+                : launch_eval_f32(s.m[0].bucket, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di, djac, df);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, dx, n * D * 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, n * D * 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(jac, djac, n * 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, df, n * 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    dev_free(tmp, stream);
+    cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail(VP_ECUDA, "vp_eval_samples: %s", cudaGetErrorString(e));
+    return VP_OK;
+}
+
+extern "C" vp_status vp_last_sample_ms(vp_ctx *c, float *ms) {
+    CHECK_CTX(c);
+    if (!ms) return fail(VP_EINVAL, "NULL out");
+    *ms = -1.0f;
+    if (!c->set.timed) return VP_OK;
+    CU(cudaEventSynchronize(c->set.ev1));
+    CU(cudaEventElapsedTime(ms, c->set.ev0, c->set.ev1));
+    return VP_OK;
+}

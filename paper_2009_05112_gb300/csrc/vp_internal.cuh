@@ -1,0 +1,132 @@
+// vp_internal.cuh -- device-side data layout and shared device helpers of
+// libvegasp (vegas+ hot path, arXiv:2009.05112).
+//
+// A "problem set" is a list of independent integrals iterated together.  The
+// single-integral context is a set of one.  Every integral's state lives in
+// device memory (HBM) for its whole life; the kernels read it through a
+// descriptor array, so one launch can serve many integrals.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vegasp.h"
+
+namespace vp {
+
+constexpr int kMaxDim = 24;        // D limit (largest bucket of the sampling kernel)
+constexpr int kMaxNg = 4096;       // N_g limit (refinement keeps a whole axis in shared memory)
+constexpr int kTreeBlock = 1024;   // hypercubes per block of the fixed-order sum
+constexpr int kMaxPeaks = 64;
+constexpr int kMaxPoints = 256;
+
+// Status bits (State::status).
+constexpr uint32_t kStatusNonFinite = 1u;
+
+// Mutable per-integral scalars, device resident.
+struct State {
+    uint32_t t;           // iterations done = Philox counter word 2 of the next one
+    int32_t scale_exp;    // the sampling kernel accumulates v = J f 2^scale_exp
+    uint32_t done_est;    // last-block counter of the estimate kernel
+    uint32_t done_alloc;  // last-block counter of the allocation kernel
+    uint32_t status;      // kStatus* bits
+    uint32_t pad;
+    double sum_d;         // sum_h d_h in the fixed order (set by the estimate kernel)
+    uint64_t n_samples;   // sum_h n_h of the current allocation
+    uint64_t n_eval_total;// integrand evaluations over all iterations
+    double last_i, last_var;
+};
+
+// Read-only (per iteration) description of one integral.
+struct Desc {
+    int32_t dim, n_g, kind, prec;
+    int32_t plus2, n_peaks;    // n_peaks: K for peak families, n points for POSTERIOR
+    int32_t n_par;             // POSTERIOR: P (= dim - 1)
+    int32_t hist_cap;          // capacity of the iteration history
+    uint32_t n_st, integral_id;
+    uint32_t key0, key1;       // Philox key (seed lo, hi)
+    uint32_t n_tree;           // ceil(n_hc / kTreeBlock)
+    uint32_t pad0;
+    int64_t n_ev;
+    uint64_t n_hc;             // N_h = N_st^D
+    double omega;              // y-volume of a hypercube, N_st^-D
+    double alpha, beta;
+    float ng_over_nst;         // N_g / N_st (FP32 path)
+    float inv_ng;              // 1 / N_g (FP32 path)
+    // device buffers (all owned by the set)
+    double *edges;     // [dim][n_g + 1] FP64 grid
+    float2 *tab;       // [dim][n_g] {x_i, J_i = N_g dx_i}, FP32 mirror of the grid
+    const double *prm;  // integrand blob as given (FP64 path)
+    const float *prm32; // FP32 constants derived from the blob (FP32 path)
+    uint32_t *n_h;     // [n_hc]
+    uint64_t *off;     // [n_hc + 1] exclusive offsets; off[n_hc] = samples this iteration
+    double *s1, *s2;   // [n_hc] per-hypercube sums of v, v^2 (unscaled)
+    double *dh;        // [n_hc] d_h of the latest estimate
+    double *hsum;      // [dim][n_g] sum v^2 per increment (unscaled)
+    uint32_t *hcnt;    // [dim][n_g] samples per increment
+    double *part;      // [n_tree][3] block partial sums (I, var, d)
+    uint64_t *bsum;    // [n_tree] block sums of n_h, then block offsets
+    double *hist_i, *hist_var;  // [hist_cap] iteration history
+    State *st;
+};
+
+// Set-level work queue of the sampling kernel.
+struct Queue {
+    uint64_t *chunk_base;  // [n_int + 1] prefix of chunks per integral
+    uint32_t *head;        // next chunk to hand out
+    uint32_t *done;        // last-block counter of the prefix kernel
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
+// S-P network, key bumped by the Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t a, b, c, d; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c.a), lo0 = m0 * c.a;
+        uint32_t hi1 = __umulhi(m1, c.c), lo1 = m1 * c.c;
+        U4 n;
+        n.a = hi1 ^ c.b ^ k0;
+        n.b = lo1;
+        n.c = hi0 ^ c.d ^ k1;
+        n.d = lo0;
+        c = n;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t lane_of(const U4 &r, int l) {
+    return l == 0 ? r.a : (l == 1 ? r.b : (l == 2 ? r.c : r.d));
+}
+
+// Uniforms strictly inside (0,1): FP64 (r + 1/2) 2^-32 (exact); FP32
+// ((r >> 9) + 1/2) 2^-23 (exact, 24 significant bits).
+__device__ __forceinline__ double u01_f64(uint32_t r) {
+    return __dmul_rn(__dadd_rn((double)r, 0.5), 2.3283064365386962890625e-10);
+}
+__device__ __forceinline__ float u01_f32(uint32_t r) {
+    return ((float)(r >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+// PTX MUFU forms (documented instructions; ~2^-22 relative error).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Host-visible launch helpers (defined in the .cu files).
+struct SetDev;  // fwd
+
+}  // namespace vp

@@ -1,0 +1,292 @@
+"""Python binding of libvegasp (include/vegasp.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module only
+converts numpy arrays and torch streams to the C-ABI's plain pointers.  It
+fails loudly (ImportError) when ``libvegasp.so`` has not been built: there is
+no CPU fallback.
+
+The C entry points are exposed under their own names (``vp_map_create``,
+``vp_iterate``, ``vp_adapt``, ``vp_step``, ``vp_result`` ...) through
+``lib()``; :class:`Integrator` wraps one context for convenience.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvegasp.so")
+
+VP_OK, VP_EINVAL, VP_ENOMEM, VP_ECUDA, VP_ETIMEOUT, VP_ENONFINITE, VP_EBUSY = range(7)
+VP_FP64, VP_FP32 = 0, 1
+VP_GAUSS, VP_BALL, VP_EXPNORM, VP_POSTERIOR = 0, 1, 2, 3
+STATUS_NAMES = {0: "VP_OK", 1: "VP_EINVAL", 2: "VP_ENOMEM", 3: "VP_ECUDA", 4: "VP_ETIMEOUT",
+                5: "VP_ENONFINITE", 6: "VP_EBUSY"}
+
+
+class VegasError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class vp_params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("lo", ctypes.POINTER(ctypes.c_double)),
+                ("hi", ctypes.POINTER(ctypes.c_double)), ("n_g", ctypes.c_int),
+                ("n_ev", ctypes.c_int64), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("integral_id", ctypes.c_uint32),
+                ("precision", ctypes.c_int), ("plus2", ctypes.c_int), ("n_st", ctypes.c_int),
+                ("max_it", ctypes.c_int)]
+
+
+class vp_integrand(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_param", ctypes.c_int),
+                ("param", ctypes.POINTER(ctypes.c_double))]
+
+
+class vp_result_t(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("sdev", ctypes.c_double), ("chi2", ctypes.c_double),
+                ("dof", ctypes.c_int), ("n_it", ctypes.c_int), ("n_eval", ctypes.c_int64),
+                ("last_i", ctypes.c_double), ("last_sdev", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_P = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "vp_set_allocator": [ALLOC_FN, FREE_FN, _P],
+    "vp_map_create": [ctypes.POINTER(vp_params), ctypes.POINTER(vp_integrand), _P,
+                      ctypes.POINTER(_P)],
+    "vp_iterate": [_P, _P],
+    "vp_adapt": [_P, _P],
+    "vp_step": [_P, _P],
+    "vp_result": [_P, ctypes.c_int, ctypes.POINTER(vp_result_t)],
+    "vp_map_destroy": [_P],
+    "vp_get_info": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                    ctypes.POINTER(ctypes.c_int)],
+    "vp_get_edges": [_P, _P],
+    "vp_set_edges": [_P, _P],
+    "vp_get_alloc": [_P, _P, _P],
+    "vp_get_moments": [_P, _P, _P],
+    "vp_get_hist": [_P, _P, _P],
+    "vp_get_history": [_P, ctypes.c_int, _P, _P],
+    "vp_alloc_from_dh": [_P, _P, _P],
+    "vp_alloc_from_sigma": [_P, _P, _P],
+    "vp_refine_from_hist": [_P, _P, _P, _P],
+    "vp_eval_samples": [_P, ctypes.c_int64, _P, _P, ctypes.c_uint32, _P, _P, _P, _P],
+    "vp_last_sample_ms": [_P, ctypes.POINTER(ctypes.c_float)],
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises ImportError if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libvegasp.so is not built (run __graft_entry__.build()); "
+                              "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.vp_last_error.argtypes = []
+        L.vp_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != VP_OK:
+        raise VegasError(status, lib().vp_last_error().decode(errors="replace"))
+    return status
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+
+def current_stream():
+    """cudaStream_t of torch's current stream (0 when torch/CUDA is absent)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+# torch's caching allocator as the library's device allocator --------------
+_keep = []
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:  # the library reports VP_ENOMEM
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _keep[:] = [a, f]
+    check(lib().vp_set_allocator(a, f, None))
+
+
+class Integrator:
+    """One vegas+ integral on the GPU (a vp_ctx)."""
+
+    def __init__(self, dim, lo, hi, kind, prm, n_g=1000, n_ev=10_000, alpha=0.5, beta=0.75,
+                 seed=0, integral_id=0, precision=VP_FP64, plus2=False, n_st=0, max_it=0,
+                 stream=None):
+        self.dim, self.n_g = int(dim), int(n_g)
+        self._lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.dim,)))
+        self._hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (self.dim,)))
+        self._prm = np.ascontiguousarray(prm, np.float64)
+        if isinstance(precision, str):
+            precision = {"fp64": VP_FP64, "fp32": VP_FP32}[precision]
+        p = vp_params(self.dim, self._lo.ctypes.data_as(_dp), self._hi.ctypes.data_as(_dp),
+                      self.n_g, int(n_ev), float(alpha), float(beta), int(seed) & (2 ** 64 - 1),
+                      int(integral_id), int(precision), int(bool(plus2)), int(n_st), int(max_it))
+        f = vp_integrand(int(kind), self._prm.size, self._prm.ctypes.data_as(_dp))
+        self.stream = current_stream() if stream is None else ctypes.c_void_p(stream)
+        h = ctypes.c_void_p()
+        check(lib().vp_map_create(ctypes.byref(p), ctypes.byref(f), self.stream, ctypes.byref(h)))
+        self.ctx = h
+        n_st_, n_hc_, _ = self.info()
+        self.n_st, self.n_hc = n_st_, n_hc_
+
+    @classmethod
+    def from_problem(cls, prob: "_inputs.Problem", precision=VP_FP64, **kw):
+        args = dict(dim=prob.dim, lo=prob.lo, hi=prob.hi, kind=prob.kind, prm=prob.prm,
+                    n_g=prob.n_g, n_ev=prob.n_ev, alpha=prob.alpha, beta=prob.beta,
+                    seed=prob.seed, integral_id=prob.integral_id, precision=precision,
+                    plus2=prob.plus2, n_st=prob.n_st)
+        args.update(kw)
+        return cls(**args)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().vp_map_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # the method
+    def iterate(self):
+        check(lib().vp_iterate(self.ctx, self.stream))
+
+    def adapt(self):
+        check(lib().vp_adapt(self.ctx, self.stream))
+
+    def step(self):
+        check(lib().vp_step(self.ctx, self.stream))
+
+    def run(self, n_it, graph=True):
+        for _ in range(n_it):
+            if graph:
+                self.step()
+            else:
+                self.iterate()
+                self.adapt()
+        return self
+
+    def result(self, discard=0, allow_nonfinite=False):
+        r = vp_result_t()
+        st = lib().vp_result(self.ctx, int(discard), ctypes.byref(r))
+        if not (allow_nonfinite and st == VP_ENONFINITE):
+            check(st)
+        return dict(mean=r.mean, sdev=r.sdev, chi2=r.chi2, dof=r.dof, n_it=r.n_it,
+                    n_eval=r.n_eval, last_i=r.last_i, last_sdev=r.last_sdev, status=st)
+
+    # inspection
+    def info(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        check(lib().vp_get_info(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def edges(self):
+        out = np.zeros((self.dim, self.n_g + 1))
+        check(lib().vp_get_edges(self.ctx, _ptr(out)))
+        return out
+
+    def set_edges(self, e):
+        e = np.ascontiguousarray(e, np.float64)
+        assert e.shape == (self.dim, self.n_g + 1)
+        check(lib().vp_set_edges(self.ctx, _ptr(e)))
+
+    def alloc(self):
+        n = np.zeros(self.n_hc, np.uint32)
+        off = np.zeros(self.n_hc + 1, np.uint64)
+        check(lib().vp_get_alloc(self.ctx, _ptr(n), _ptr(off)))
+        return n, off
+
+    def moments(self):
+        s1, s2 = np.zeros(self.n_hc), np.zeros(self.n_hc)
+        check(lib().vp_get_moments(self.ctx, _ptr(s1), _ptr(s2)))
+        return s1, s2
+
+    def hist(self):
+        hs = np.zeros((self.dim, self.n_g))
+        hc = np.zeros((self.dim, self.n_g))
+        check(lib().vp_get_hist(self.ctx, _ptr(hs), _ptr(hc)))
+        return hs, hc
+
+    def history(self):
+        n = self.info()[2]
+        I, V = np.zeros(n), np.zeros(n)
+        check(lib().vp_get_history(self.ctx, n, _ptr(I), _ptr(V)))
+        return I, V
+
+    def alloc_from_dh(self, d_h):
+        d = np.ascontiguousarray(d_h, np.float64)
+        assert d.size == self.n_hc
+        check(lib().vp_alloc_from_dh(self.ctx, _ptr(d), self.stream))
+
+    def alloc_from_sigma(self, sigma):
+        d = np.ascontiguousarray(sigma, np.float64)
+        assert d.size == self.n_hc
+        check(lib().vp_alloc_from_sigma(self.ctx, _ptr(d), self.stream))
+
+    def refine_from_hist(self, hsum, hcnt):
+        hs = np.ascontiguousarray(hsum, np.float64).reshape(self.dim, self.n_g)
+        hc = np.ascontiguousarray(hcnt, np.float64).reshape(self.dim, self.n_g)
+        check(lib().vp_refine_from_hist(self.ctx, _ptr(hs), _ptr(hc), self.stream))
+
+    def eval_samples(self, h, j, t):
+        h = np.ascontiguousarray(h, np.uint64)
+        j = np.ascontiguousarray(j, np.uint32)
+        n = h.size
+        x = np.zeros((n, self.dim))
+        idx = np.zeros((n, self.dim), np.int32)
+        jac, f = np.zeros(n), np.zeros(n)
+        check(lib().vp_eval_samples(self.ctx, n, _ptr(h), _ptr(j), int(t), _ptr(x), _ptr(idx),
+                                    _ptr(jac), _ptr(f)))
+        return x, idx, jac, f
+
+    def last_sample_ms(self):
+        ms = ctypes.c_float()
+        check(lib().vp_last_sample_ms(self.ctx, ctypes.byref(ms)))
+        return ms.value

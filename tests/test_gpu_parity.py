@@ -1,0 +1,391 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Bars (stated in the design doc and here):
+* integer work -- n_h, offsets, increment indices -- bit-exact;
+* FP64 path: the map x(y), J(y) bit-exact (same IEEE sequence), f within 1e-14
+  (CUDA's exp vs the host's), per-hypercube moments and histograms within
+  1e-12 (summation order), I_j, sigma_j^2 and grid edges within 1e-10 relative;
+* FP32 path: x within 1e-5 of the axis width, J within 1e-5 relative where
+  the increment index agrees, f through its exponent |dA| <= 1e-5 max(1, A),
+  and the integral within 3 sigma of the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_05112_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_05112_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def V():
+    from paper_2009_05112_gb300 import vegasp
+    return vegasp
+
+
+def oracle_of(prob, **kw):
+    args = dict(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
+                alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind, prm=prob.prm,
+                integral_id=prob.integral_id, plus2=prob.plus2, n_st=prob.n_st)
+    args.update(kw)
+    return oracle.VegasPlus(**args)
+
+
+def gpu_of(prob, precision=0, **kw):
+    return V().Integrator.from_problem(prob, precision=precision, **kw)
+
+
+def random_grid(rng, lo, hi, n_g):
+    lo, hi = np.asarray(lo, float), np.asarray(hi, float)
+    e = np.empty((lo.size, n_g + 1))
+    for m in range(lo.size):
+        w = rng.exponential(size=n_g) + 0.05
+        c = np.concatenate([[0.0], np.cumsum(w)])
+        e[m] = lo[m] + (hi[m] - lo[m]) * c / c[-1]
+        e[m, 0], e[m, -1] = lo[m], hi[m]
+    return e
+
+
+def problem_of_kind(kind, dim, rng, n_g=50, n_ev=2000):
+    if kind == inputs.GAUSS:
+        K = 3
+        blob = inputs.gauss_blob(rng.uniform(0.5, 2, K), rng.uniform(0.05, 0.3, K),
+                                 [rng.uniform(0.1, 0.9, dim) for _ in range(K)])
+        lo, hi = np.zeros(dim), np.ones(dim)
+    elif kind == inputs.BALL:
+        blob = inputs.ball_blob([0.45, 0.2], [np.full(dim, 0.5), rng.uniform(0.2, 0.8, dim)],
+                                amps=[1.0, 2.0])
+        lo, hi = np.zeros(dim), np.ones(dim)
+    elif kind == inputs.EXPNORM:
+        blob = inputs.expnorm_blob([1.0, 0.5], [20.0, 5.0],
+                                   [rng.uniform(0.2, 0.8, dim), rng.uniform(0.2, 0.8, dim)])
+        lo, hi = np.zeros(dim), np.ones(dim)
+    else:
+        p = inputs.posterior(dim=dim, n_pts=20, seed=int(rng.integers(1000)))
+        return inputs.Problem("post", dim, kind, p.prm, p.lo, p.hi, n_g=n_g, n_ev=n_ev,
+                              seed=int(rng.integers(1 << 40)))
+    return inputs.Problem("k%d" % kind, dim, kind, blob, lo, hi, n_g=n_g, n_ev=n_ev,
+                          seed=int(rng.integers(1 << 40)), integral_id=int(rng.integers(1 << 31)))
+
+
+# ---------------------------------------------------------------------------
+# a1-a3 per sample
+# ---------------------------------------------------------------------------
+CASES = [(k, d) for k in (0, 1, 2) for d in (1, 4, 5, 12, 13, 20, 24)] + \
+        [(3, 3), (3, 8), (3, 21)]
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_samples_fp64_match_oracle(kind, dim):
+    rng = np.random.default_rng(100 * kind + dim)
+    prob = problem_of_kind(kind, dim, rng)
+    g = gpu_of(prob, 0)
+    o = oracle_of(prob, n_st=g.n_st)
+    e = random_grid(rng, prob.lo, prob.hi, prob.n_g)
+    g.set_edges(e)
+    o.edges = np.ascontiguousarray(e)
+    n = 300
+    hs = rng.integers(0, g.n_hc, n).astype(np.uint64)
+    js = rng.integers(0, 50, n).astype(np.uint32)
+    t = 7
+    x, idx, jac, f = g.eval_samples(hs, js, t)
+    for k in range(n):
+        xo, io, jo, fo = o.eval_sample(t, int(hs[k]), int(js[k]))
+        assert np.array_equal(idx[k], io)
+        assert np.array_equal(x[k], xo), (k, x[k] - xo)
+        assert jac[k] == jo
+        assert f[k] == pytest.approx(fo, rel=1e-13, abs=1e-300)
+
+
+@pytest.mark.parametrize("kind,dim", CASES)
+def test_samples_fp32_within_tolerance(kind, dim):
+    rng = np.random.default_rng(7 + 100 * kind + dim)
+    prob = problem_of_kind(kind, dim, rng)
+    g = gpu_of(prob, 1)
+    o = oracle_of(prob, n_st=g.n_st)
+    e = random_grid(rng, prob.lo, prob.hi, prob.n_g)
+    g.set_edges(e)
+    o.edges = np.ascontiguousarray(e)
+    n = 300
+    hs = rng.integers(0, g.n_hc, n).astype(np.uint64)
+    js = rng.integers(0, 50, n).astype(np.uint32)
+    x, idx, jac, f = g.eval_samples(hs, js, 3)
+    width = np.asarray(prob.hi) - np.asarray(prob.lo)
+    flips = 0
+    for k in range(n):
+        xo, io, jo, fo = o.eval_sample(3, int(hs[k]), int(js[k]))
+        assert np.all(np.abs(x[k] - xo) <= 1e-5 * width)
+        if not np.array_equal(idx[k], io):
+            assert np.all(np.abs(idx[k] - io) <= 1)
+            flips += 1
+            continue
+        assert jac[k] == pytest.approx(jo, rel=1e-5)
+        if kind == inputs.BALL:
+            if f[k] != fo:
+                flips += 1  # a point within rounding of a sphere
+            continue
+        if fo > 1e-30 and f[k] > 0:
+            A = abs(math.log(fo))
+            assert abs(math.log(f[k]) - math.log(fo)) <= 1e-5 * max(1.0, A), (k, f[k], fo)
+        else:
+            assert f[k] <= 1e-25
+    assert flips <= 0.02 * n
+
+
+# ---------------------------------------------------------------------------
+# a7: integer allocation, bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n_st", [(1, 1), (2, 4), (4, 7), (1, 1025), (8, 4), (20, 2)])
+@pytest.mark.parametrize("plus2", [False, True])
+def test_alloc_from_dh_bit_exact(dim, n_st, plus2):
+    rng = np.random.default_rng(dim * 1000 + n_st + plus2)
+    prob = inputs.Problem("alloc", dim, inputs.GAUSS,
+                          inputs.gauss_blob([1.0], [0.2], [np.full(dim, 0.5)]), np.zeros(dim),
+                          np.ones(dim), n_g=8, n_ev=max(4 * n_st ** dim, 10_000_000 // (1 + dim)),
+                          n_st=n_st, plus2=plus2)
+    g = gpu_of(prob)
+    n_hc = n_st ** dim
+    for trial in range(3):
+        d = rng.exponential(size=n_hc) * 10.0 ** rng.uniform(-20, 20, size=n_hc)
+        d[rng.uniform(size=n_hc) < 0.25] = 0.0
+        if trial == 2:
+            d[:] = 0.0
+        g.alloc_from_dh(d)
+        n_h, off = g.alloc()
+        n_ref, off_ref = oracle.allocate(prob.n_ev, d, plus2=plus2)
+        assert np.array_equal(n_h, n_ref)
+        assert np.array_equal(off, off_ref)
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0, 0.75])
+def test_alloc_from_sigma(beta):
+    rng = np.random.default_rng(11)
+    dim, n_st = 8, 4
+    prob = inputs.Problem("alloc", dim, inputs.GAUSS,
+                          inputs.gauss_blob([1.0], [0.2], [np.full(dim, 0.5)]), np.zeros(dim),
+                          np.ones(dim), n_g=8, n_ev=10 ** 6, n_st=n_st, beta=beta)
+    g = gpu_of(prob)
+    sig = rng.exponential(size=n_st ** dim) * 1e-3
+    g.alloc_from_sigma(sig)
+    n_h, off = g.alloc()
+    n_ref, off_ref = oracle.allocate(prob.n_ev, oracle.damp(beta, sig))
+    if beta in (0.0, 1.0):
+        assert np.array_equal(n_h, n_ref) and np.array_equal(off, off_ref)
+    else:
+        # CUDA's pow and the host's may differ in the last bit of a few d_h
+        diff = n_h.astype(np.int64) - n_ref.astype(np.int64)
+        assert np.count_nonzero(diff) <= 1e-3 * n_h.size
+        assert np.all(np.abs(diff) <= 1)
+
+
+# ---------------------------------------------------------------------------
+# a8: grid refinement
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_g", [2, 3, 257, 1000, 4096])
+@pytest.mark.parametrize("alpha", [0.0, 0.5, 1.5])
+def test_refine_matches_oracle(n_g, alpha):
+    rng = np.random.default_rng(n_g * 10 + int(alpha * 10))
+    dim = 3
+    prob = inputs.Problem("refine", dim, inputs.GAUSS,
+                          inputs.gauss_blob([1.0], [0.2], [np.full(dim, 0.5)]),
+                          np.array([0.0, -2.0, 1.0]), np.array([1.0, 3.0, 1.5]), n_g=n_g,
+                          n_ev=1000, alpha=alpha)
+    g = gpu_of(prob)
+    e0 = random_grid(rng, prob.lo, prob.hi, n_g)
+    g.set_edges(e0)
+    hc = rng.integers(0, 50, size=(dim, n_g)).astype(float)
+    hs = rng.exponential(size=(dim, n_g)) * hc * 10.0 ** rng.uniform(-3, 3, size=(dim, n_g))
+    hs[2] = 0.0  # an axis with f = 0 stays put
+    g.refine_from_hist(hs, hc)
+    e = g.edges()
+    for m in range(dim):
+        ref = oracle.refine_axis(e0[m], hs[m], hc[m], alpha)
+        w = prob.hi[m] - prob.lo[m]
+        assert np.max(np.abs(e[m] - ref)) <= 1e-10 * w, m
+        assert e[m][0] == prob.lo[m] and e[m][-1] == prob.hi[m]
+        assert np.all(np.diff(e[m]) > 0)
+    assert np.array_equal(e[2], e0[2])
+
+
+# ---------------------------------------------------------------------------
+# whole iterations, FP64
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("graph", [False, True])
+def test_three_peaks_d4_fp64_iterations_match_oracle(graph):
+    """The 4-D three-peak workload (N_ev = 1e4, N_g = 1000, 10 iterations):
+    every I_j and sigma_j^2 within 1e-10, every n_h identical, edges within
+    1e-10, and the first iteration's moments and histograms within 1e-12."""
+    prob = inputs.three_peaks_d4()
+    g = gpu_of(prob)
+    o = oracle_of(prob)
+    assert g.n_st == o.n_st == 7 and g.n_hc == 2401
+    for it in range(prob.n_it):
+        if graph:
+            g.step()  # iterate + adapt replayed from the captured graph
+        else:
+            g.iterate()
+        o.iterate()
+        if not graph and it == 0:
+            s1, s2 = g.moments()
+            np.testing.assert_allclose(s1, o.s1, rtol=1e-12, atol=0)
+            np.testing.assert_allclose(s2, o.s2, rtol=1e-12, atol=0)
+            hs, hc = g.hist()
+            assert np.array_equal(hc, o.hcnt)
+            np.testing.assert_allclose(hs, o.hsum, rtol=1e-12, atol=0)
+        if not graph:
+            g.adapt()
+        o.adapt()
+        if not graph or it == prob.n_it - 1:
+            n_h, off = g.alloc()
+            assert np.array_equal(n_h, o.n_h), it
+            assert np.array_equal(off, o.offsets), it
+            assert np.max(np.abs(g.edges() - o.edges)) <= 1e-10, it
+    I, Vv = g.history()
+    np.testing.assert_allclose(I, o.I, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(Vv, o.var, rtol=1e-10, atol=0)
+    r, ro = g.result(), o.result()
+    assert r["mean"] == pytest.approx(ro["mean"], rel=1e-10)
+    assert r["sdev"] == pytest.approx(ro["sdev"], rel=1e-10)
+    assert r["chi2"] == pytest.approx(ro["chi2"], rel=1e-8, abs=1e-9)
+    assert abs(r["mean"] - prob.exact) < 3 * r["sdev"]
+
+
+@pytest.mark.parametrize("kind,dim", [(1, 4), (2, 8), (3, 3)])
+def test_other_integrands_fp64_iterations_match_oracle(kind, dim):
+    rng = np.random.default_rng(kind * 31 + dim)
+    prob = problem_of_kind(kind, dim, rng, n_g=200, n_ev=20_000)
+    g = gpu_of(prob)
+    o = oracle_of(prob)
+    for it in range(5):
+        g.iterate()
+        g.adapt()
+        o.iterate()
+        o.adapt()
+        n_h, _ = g.alloc()
+        assert np.array_equal(n_h, o.n_h), it
+    I, Vv = g.history()
+    np.testing.assert_allclose(I, o.I, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(Vv, o.var, rtol=1e-10, atol=0)
+    assert np.max(np.abs(g.edges() - o.edges)) <= 1e-10 * np.max(prob.hi - prob.lo)
+
+
+# ---------------------------------------------------------------------------
+# the FP32 path against the FP64 oracle
+# ---------------------------------------------------------------------------
+def test_four_peaks_d8_fp32_within_3_sigma_of_oracle():
+    prob = inputs.four_peaks_d8(n_ev=100_000, n_it=10)
+    g = gpu_of(prob, 1).run(prob.n_it)
+    o = oracle_of(prob).run(prob.n_it)
+    r, ro = g.result(discard=3), o.result(discard=3)
+    assert abs(r["mean"] - ro["mean"]) < 3 * ro["sdev"]
+    assert abs(r["mean"] - prob.exact) < 3 * r["sdev"]
+    # the same samples: iteration by iteration far closer than sigma
+    I, _ = g.history()
+    assert np.all(np.abs(I - np.array(o.I)) < 0.1 * np.sqrt(np.array(o.var)))
+
+
+# ---------------------------------------------------------------------------
+# full size (20-D ball, N_ev = 1e7): sampled outputs the oracle computes one by one
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ball_d20_full_size_sampled(precision):
+    prob = inputs.ball_d20()
+    rng = np.random.default_rng(20)
+    g = gpu_of(prob, precision)
+    o = oracle_of(prob)
+    assert g.n_hc == 2 ** 20 and o.n_st == 2
+    # a shared, seeded, non-uniform grid concentrated towards the centre
+    e = np.empty((20, prob.n_g + 1))
+    y = np.linspace(0, 1, prob.n_g + 1)
+    for m in range(20):
+        s = rng.uniform(0.6, 0.9)
+        e[m] = 0.5 + 0.5 * np.sign(2 * y - 1) * np.abs(2 * y - 1) ** (1 / s)
+        e[m, 0], e[m, -1] = 0.0, 1.0
+    g.set_edges(e)
+    o.edges = np.ascontiguousarray(e)
+    g.iterate()
+    n_h, off = g.alloc()
+    assert np.all(n_h == 9) and int(off[-1]) == 9 * 2 ** 20
+    s1, s2 = g.moments()
+    hs, hc = g.hist()
+    # properties at any size
+    assert np.all(hc.sum(axis=1) == off[-1])
+    tot2 = s2.sum()
+    np.testing.assert_allclose(hs.sum(axis=1), tot2, rtol=1e-6 if precision else 1e-12)
+    I, Vv = g.history()
+    np.testing.assert_allclose(I[0], (s1 / n_h).sum() / 2 ** 20, rtol=1e-9)
+    # sampled hypercubes against the oracle, one by one
+    bad = 0
+    for h in rng.integers(0, 2 ** 20, 300):
+        a, b = o.hcube_moments(0, int(h), int(n_h[h]))
+        if precision == 0:
+            assert s1[h] == pytest.approx(a, rel=1e-12, abs=1e-300)
+            assert s2[h] == pytest.approx(b, rel=1e-12, abs=1e-300)
+        elif not (abs(s1[h] - a) <= 1e-5 * abs(a) + 1e-30):
+            bad += 1  # a sample within FP32 rounding of the sphere
+    assert bad <= 3
+
+
+def test_ball_d20_result_matches_volume():
+    """§1 footnote: 10 iterations of 1e7 find the 20-D ball, 10 more give the
+    volume to about 0.05%; FP32 map with FP64 accumulation."""
+    prob = inputs.ball_d20()
+    g = gpu_of(prob, 1).run(prob.n_it)
+    r = g.result(discard=prob.discard)
+    assert abs(r["mean"] - prob.exact) < 3 * r["sdev"]
+    assert r["sdev"] / prob.exact < 1.5e-3
+    assert r["chi2"] / r["dof"] < 3.0
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_single_hypercube_and_single_increment():
+    rng = np.random.default_rng(3)
+    prob = inputs.Problem("edge", 1, inputs.GAUSS, inputs.gauss_blob([1.0], [0.2], [[0.4]]),
+                          np.zeros(1), np.ones(1), n_g=1, n_ev=3)
+    g = gpu_of(prob)
+    o = oracle_of(prob)
+    assert g.n_st == 1 and g.n_hc == 1
+    for _ in range(3):
+        g.iterate(); g.adapt(); o.iterate(); o.adapt()
+    I, Vv = g.history()
+    np.testing.assert_allclose(I, o.I, rtol=1e-12)
+    assert np.array_equal(g.edges(), o.edges)
+
+
+def test_alpha_zero_freezes_grid_and_plus2():
+    prob = inputs.three_peaks_d4(n_ev=5000, n_g=100)
+    prob.alpha, prob.plus2 = 0.0, True
+    g = gpu_of(prob)
+    o = oracle_of(prob)
+    e0 = g.edges()
+    for _ in range(3):
+        g.iterate(); g.adapt(); o.iterate(); o.adapt()
+    assert np.array_equal(g.edges(), e0)
+    n_h, _ = g.alloc()
+    assert np.array_equal(n_h, o.n_h) and n_h.min() >= 2
+
+
+def test_nonfinite_integrand_is_reported():
+    # (J f)^2 overflows FP64: f ~ 1e300 over the whole box
+    prob = inputs.Problem("inf", 2, inputs.GAUSS, inputs.gauss_blob([1e300], [10.0], [[0.5, 0.5]]),
+                          np.zeros(2), np.ones(2), n_g=4, n_ev=100)
+    g = gpu_of(prob)
+    g.iterate()
+    g.adapt()
+    r = g.result(allow_nonfinite=True)
+    assert r["status"] == V().VP_ENONFINITE
