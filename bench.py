@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Throughput of the vegas+ hot path (one adaptive iteration = one step) on GB300.
+
+Workload: the 8-D integral of four Gaussian peaks on the diagonal (centres
+0.2, 0.4, 0.6, 0.8, width 0.1, amplitudes U[0.5, 2] from seed 0), N_ev = 1e6
+samples per iteration, N_g = 1000, beta = 0.75, alpha = 0.5; map and integrand
+in FP32, per-hypercube moments Kahan-compensated FP32, estimate, reallocation
+and refinement in FP64.  A step is one vp_step: sampling (a1-a5), estimate
+(a6), reallocation (a7) and grid refinement (a8), replayed from a CUDA graph.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead (the reference arm of this build).
+
+Multi-GPU (torchrun): one independent integral per rank (distinct Philox
+counter word 3), no collective on the data path; value = all ranks' integrand
+evaluations / max-over-ranks time ("scaling": "weak").
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "four_peaks_d8"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB of L2, written between timed steps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def flops_per_sample(dim, n_peaks):
+    """Algorithmic FP32 flops per sample of the fused kernel: the map 4 per axis
+    (y N_g, the fraction, the x multiply-add as 2, the J product), the Gaussian
+    integrand 3 per axis per peak plus 2 per peak, and 10 for the compensated
+    moments (2 plain + 8 Kahan)."""
+    return 4 * dim + n_peaks * (3 * dim + 2) + 10
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_from_profile(kernel_src_hash):
+    """DRAM bytes per sampling launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sample_kernel_four_peaks_d8.txt")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha1") != kernel_src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ["sample_impl.cuh", "vp_internal.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_2009_05112_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 CPU oracle, as it stands, on this host: whole iterations of the
+    same workload (N_ev = 1e6) until ~seconds of CPU time; one thread."""
+    import oracle
+    from paper_2009_05112_gb300 import inputs
+    prob = inputs.four_peaks_d8()
+    o = oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
+                         alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind,
+                         prm=prob.prm)
+    evals, t0, its = 0, time.perf_counter(), 0
+    while True:
+        n = int(o.offsets[-1])
+        o.iterate()
+        o.adapt()
+        evals += n
+        its += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or its >= 50:
+            break
+    return {"value": evals / el, "unit": "integrand evals/s", "cores": 1, "kind": "oracle",
+            "sample": "%d whole iterations (N_ev=1e6, D=8, 4 peaks, N_g=1000) of the FP64 C "
+                      "oracle, single thread, %.1f s" % (its, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2009_05112_gb300 import inputs
+    prob = inputs.four_peaks_d8()
+    o = oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
+                         alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind,
+                         prm=prob.prm)
+    for _ in range(args.warmup):
+        o.iterate()
+        o.adapt()
+    evals = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        evals += int(o.offsets[-1])
+        o.iterate()
+        o.adapt()
+    el = time.perf_counter() - t0
+    v = evals / el
+    line = {"metric": "integrand evals/s", "value": v, "unit": "integrand evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "dim": 8, "n_ev": prob.n_ev, "n_g": prob.n_g,
+                       "alpha": prob.alpha, "beta": prob.beta},
+            "cpu_baseline": {"value": v, "unit": "integrand evals/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "%d whole iterations (N_ev=1e6) after %d warm-up, "
+                                       "single thread" % (args.steps, args.warmup)},
+            "e2e": {"value": v, "unit": "integrand evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2009_05112_gb300 import build as _build
+    from paper_2009_05112_gb300 import inputs, vegasp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    vegasp.use_torch_allocator()
+    prob = inputs.four_peaks_d8()
+    prob.integral_id = rank
+    stream = torch.cuda.current_stream()
+    g = vegasp.Integrator.from_problem(prob, precision=vegasp.VP_FP32)
+    for _ in range(args.warmup):
+        g.step()
+    n0 = g.result()["n_eval"]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    k1_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)           # evict L2 between timed steps
+            ev[k][0].record(stream)
+            g.step()
+            ev[k][1].record(stream)
+            k1_ms.append(g.last_sample_ms())  # sampling kernel, CUDA events on its stream
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    evals = g.result()["n_eval"] - n0
+    t_max = total_ms
+    evals_all = evals
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        e = torch.tensor([evals], device="cuda", dtype=torch.float64)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        evals_all = float(e.item())
+        dist.barrier()
+    value = evals_all / (t_max / 1e3)
+
+    # end to end through the public API with host buffers: create from host
+    # parameters (H2D), steps, and the host read of every step's estimate (D2H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g2 = vegasp.Integrator.from_problem(prob, precision=vegasp.VP_FP32)
+    for _ in range(args.steps):
+        g2.step()
+        r2 = g2.result()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_evals = r2["n_eval"]
+    g2.close()
+    h2d = (prob.prm.size * 8 + 2 * prob.dim * 8 + prob.dim * (prob.n_g + 1) * 8 +
+           prob.dim * prob.n_g * 8 + g.n_hc * 8 + 64)  # blob, box, grid, FP32 table, d_h, state
+    d2h = 64 + args.steps * 16                           # state + history read per step (max)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    max_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    samples_per_step = evals / args.steps
+    k1_avg_ms = sum(k1_ms) / len(k1_ms)
+    k1_tflops = flops_per_sample(prob.dim, 4) * samples_per_step / (k1_avg_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": k1_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": k1_tflops / fp32_peak, "traffic": traffic_from_profile(kernel_source_hash()),
+            "kernel": "k_sample (fused a1-a5)", "kernel_ms": k1_avg_ms,
+            "kernel_share_of_step": k1_avg_ms / (total_ms / args.steps),
+            "peak_note": "FP32 = SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % max_mhz}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = k1_tflops / (n_sm * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
+    line = {"metric": "integrand evals/s", "value": value, "unit": "integrand evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": prob.dim, "n_ev": prob.n_ev,
+                       "n_g": prob.n_g, "alpha": prob.alpha, "beta": prob.beta, "peaks": 4,
+                       "precision": "fp32 map/integrand, Kahan fp32 moments, fp64 estimate",
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": "one integral per GPU" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_evals / e2e_s, "unit": "integrand evals/s",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h,
+                    "note": "create from host parameters + %d steps + a host read of the "
+                            "estimate after every step, wall clock" % args.steps},
+            "roofline": roof, "clocks": clocks,
+            "gpu_launches": 7 * args.steps,
+            "integral": {"mean": g.result()["mean"], "sdev": g.result()["sdev"],
+                         "exact": prob.exact}}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

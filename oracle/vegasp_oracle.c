@@ -367,9 +367,12 @@ int or_allocate(int64_t n_hc, int64_t n_ev, int plus2, const double *d, uint32_t
 
 /* d_i = hsum_i / hcnt_i (reading: 0 when the increment got no sample), then   */
 /* the smoothing (7,1)/8, (1,6,1)/8, (1,7)/8 with division by sum_i d_i, then  */
-/* the compression d_i -> ((1 - d_i)/ln(1/d_i))^alpha (reading: 1 at d_i = 1,  */
-/* 0 at d_i = 0).  Returns 0, or 1 when every d_i is zero (or the sum is not   */
-/* finite): nothing to refine.  Needs n_g >= 2.                                */
+/* the compression d_i -> ((1 - d_i)/ln(1/d_i))^alpha (reading: 1 at d_i = 1;  */
+/* a smoothed d_i of zero is raised to the smallest normal double first, so    */
+/* that, as for alpha -> 0 "no refinement", an increment nobody sampled keeps  */
+/* a small nonzero share instead of vanishing from the grid).  Returns 0, or 1 */
+/* when every d_i is zero (or the sum is not finite): nothing to refine.       */
+/* Needs n_g >= 2.                                                             */
 int or_smooth_compress(int n_g, const double *hsum, const double *hcnt, double alpha,
                        double *out, double *work) {
     double *d = work;
@@ -385,8 +388,8 @@ int or_smooth_compress(int n_g, const double *hsum, const double *hcnt, double a
     for (int i = 0; i < n_g; ++i) out[i] = out[i] / sum_d;
     for (int i = 0; i < n_g; ++i) {
         double v = out[i];
-        if (v <= 0.0) out[i] = 0.0;
-        else if (v == 1.0) out[i] = 1.0;
+        if (v <= 0.0) v = 2.2250738585072014e-308; /* smallest normal double */
+        if (v == 1.0) out[i] = 1.0;
         else out[i] = pow((1.0 - v) / log(1.0 / v), alpha);
     }
     return 0;

@@ -11,12 +11,14 @@
 //               fixed order (blocks of 1024 hypercubes, pairwise halving inside
 //               a block, block sums left to right), so sum_h d_h -- and with it
 //               every integer n_h -- is reproducible bit for bit;
-//   k_alloc     a7: n_h = max(2, floor(N_ev d_h / sum d)) (§3 Eq. nh; or + 2),
+//   k_alloc     a7: n_h = max(2, floor(N_ev d_h / sum d)) (§3 Eq. nh; or + 2;
+//               the first allocation is always the equal split max(2, .)),
 //               block sums of n_h, then (last block) the block offsets;
 //   k_offsets   a7: exclusive offsets off[h] = sum_{h' < h} n_h';
 //   k_refine    a8 on one axis (§2.3): d_i = hsum_i / hcnt_i, smoothing
 //               (7,1)/(1,6,1)/(1,7) over 8, normalisation by sum d_i,
-//               compression ((1 - d)/ln(1/d))^alpha, then the equal-share
+//               compression ((1 - d)/ln(1/d))^alpha (a zero d first raised to
+//               the smallest normal double), then the equal-share
 //               re-gridding as an inverse of the cumulative d: new edge k is
 //               where the cumulative reaches k sum(d)/N_g, d spread uniformly
 //               over each old increment (the same points the paper's four-step
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(512) k_estimate(const Desc *desc, const uint32
 // finite; the status flag records it.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_alloc(const Desc *desc, const uint32_t *tree_base,
-                                               int n_int) {
+                                               int n_int, int initial) {
     __shared__ unsigned long long s_sum;
     __shared__ bool s_last;
     const int b = owner_of(tree_base, n_int, blockIdx.x);
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(256) k_alloc(const Desc *desc, const uint32_t 
         else q = __ddiv_rn((double)d.n_ev, (double)d.n_hc);
         const double fl = floor(q);
         uint32_t n;
-        if (d.plus2) n = (uint32_t)fl + 2u;
+        if (d.plus2 && !initial) n = (uint32_t)fl + 2u;
         else n = fl > 2.0 ? (uint32_t)fl : 2u;
         d.n_h[h] = n;
         mine += n;
@@ -384,9 +386,11 @@ __global__ void __launch_bounds__(256) k_refine(const Desc *desc, const uint32_t
         else if (i == n_g - 1) s = (dd[n_g - 2] + 7.0 * dd[n_g - 1]) / 8.0;
         else s = (dd[i - 1] + 6.0 * dd[i] + dd[i + 1]) / 8.0;
         s = s / sum_d;
+        // reading: an unsampled increment keeps the weight of the smallest
+        // normal double (the alpha -> 0 limit stays "no refinement")
+        if (s <= 0.0) s = 2.2250738585072014e-308;
         double c;
-        if (s <= 0.0) c = 0.0;
-        else if (s == 1.0) c = 1.0;
+        if (s == 1.0) c = 1.0;
         else c = pow((1.0 - s) / log(1.0 / s), d.alpha);
         cval[i - i0] = c;
         local += c;
@@ -455,8 +459,8 @@ cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_i
 }
 
 cudaError_t launch_alloc(const Desc *desc, const uint32_t *tree_base, int n_int,
-                         uint32_t n_blocks, cudaStream_t s) {
-    k_alloc<<<n_blocks, 256, 0, s>>>(desc, tree_base, n_int);
+                         uint32_t n_blocks, cudaStream_t s, int initial) {
+    k_alloc<<<n_blocks, 256, 0, s>>>(desc, tree_base, n_int, initial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_offsets<<<n_blocks, 256, 0, s>>>(desc, tree_base, n_int);

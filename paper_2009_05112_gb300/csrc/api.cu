@@ -24,7 +24,7 @@ cudaError_t launch_zero(const Desc *, const uint32_t *, int, uint32_t, cudaStrea
 cudaError_t launch_chunks(const Desc *, const uint32_t *, int, uint64_t *, uint32_t *, uint32_t,
                           cudaStream_t);
 cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
-cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t);
+cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t, int initial);
 cudaError_t launch_refine(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
 }  // namespace vp
 
@@ -486,7 +486,7 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
                            cudaMemcpyHostToDevice, stream));
     // first allocation: d_h = 1 -> max(2, floor(N_ev / N_h)) (the classic equal split)
     CU(launch_estimate(s.d_desc, s.d_tree_base, n, s.n_tree_total, 2, stream));
-    CU(launch_alloc(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream));
+    CU(launch_alloc(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream, 1));
     CU(cudaEventCreate(&s.ev0));
     CU(cudaEventCreate(&s.ev1));
     CU(cudaStreamSynchronize(stream));
@@ -513,7 +513,8 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
         CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base, g.d_head,
                          (uint32_t)(g.threads * g.R), stream));
     }
-    CU(cudaEventRecord(s.ev0, stream));
+    // external record nodes when captured into the step graph
+    CU(cudaEventRecordWithFlags(s.ev0, stream, cudaEventRecordExternal));
     for (size_t gi = 0; gi < s.groups.size(); ++gi) {
         Group &g = s.groups[gi];
         SampleArgs a;
@@ -531,7 +532,7 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
                             : launch_sample_f32(g.bucket, g.kind, g.blocks, g.threads, g.smem, stream, a);
         if (e != cudaSuccess) return fail(VP_ECUDA, "sampling launch: %s", cudaGetErrorString(e));
     }
-    CU(cudaEventRecord(s.ev1, stream));
+    CU(cudaEventRecordWithFlags(s.ev1, stream, cudaEventRecordExternal));
     s.timed = true;
     CU(launch_estimate(s.d_desc, s.d_tree_base, n, s.n_tree_total, 0, stream));
     s.last = stream;
@@ -540,7 +541,7 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
 
 static vp_status set_adapt(Set &s, cudaStream_t stream) {
     const int n = (int)s.m.size();
-    CU(launch_alloc(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream));
+    CU(launch_alloc(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream, 0));
     if (s.any_refine)
         CU(launch_refine(s.d_desc, s.d_axis_base, n, s.n_axis_total, s.max_ng, stream));
     s.last = stream;
@@ -771,7 +772,7 @@ static vp_status alloc_from(vp_ctx *c, const double *v, int mode, cudaStream_t s
     CU(cudaStreamSynchronize(s.last));
     CU(cudaMemcpyAsync(d.dh, v, d.n_hc * 8, cudaMemcpyHostToDevice, stream));
     CU(launch_estimate(s.d_desc, s.d_tree_base, 1, s.n_tree_total, mode, stream));
-    CU(launch_alloc(s.d_desc, s.d_tree_base, 1, s.n_tree_total, stream));
+    CU(launch_alloc(s.d_desc, s.d_tree_base, 1, s.n_tree_total, stream, 0));
     CU(cudaStreamSynchronize(stream));
     s.last = stream;
     return VP_OK;

@@ -162,18 +162,40 @@ __device__ __forceinline__ float f_post32(const float *p, int dim, const float (
 // One sample: a1-a3.  Returns J and f; x[] and idx[] are filled.
 // digits kd[] hold k_mu of hypercube h as the real type.
 // ---------------------------------------------------------------------------
+// FP32 Jacobians of adapted high-dimensional maps leave the FP32 range (e.g.
+// 20 axes of N_g dx ~ 3e-3 give 3e-51), so the FP32 path carries J as a
+// mantissa in [1, 2) and a separate integer exponent, renormalised after
+// every group of four axes (four factors cannot leave the range: each is at
+// least ~N_g ulp(x) and at most N_g (b - a)).
+__device__ __forceinline__ void renorm(float &m, int &e) {
+    const int b = __float_as_int(m);
+    const int ex = (b >> 23) & 0xff;
+    if (ex != 0) {  // zero stays zero
+        e += ex - 127;
+        m = __int_as_float((b & 0x807fffff) | 0x3f800000);
+    }
+}
+
+// x * 2^n for any int n, by two exact power-of-two multiplies.
+__device__ __forceinline__ float scale2(float x, int n) {
+    const int n1 = max(-126, min(127, n));
+    const int n2 = max(-126, min(127, n - n1));
+    return x * __int_as_float((n1 + 127) << 23) * __int_as_float((n2 + 127) << 23);
+}
+
 template <int DMAX, bool F64, int KIND>
 __device__ __forceinline__ void sample_point(const Desc &d, const void *prm, uint32_t t,
                                              uint32_t h, uint32_t j,
                                              const typename Real<F64>::T (&kd)[DMAX],
                                              typename Real<F64>::T (&x)[DMAX],
                                              int (&idx)[DMAX],
-                                             typename Real<F64>::T &jac,
+                                             typename Real<F64>::T &jac, int &jexp,
                                              typename Real<F64>::T &f) {
     typedef typename Real<F64>::T T;
     const int dim = d.dim, n_g = d.n_g;
     const uint32_t calls = (uint32_t)((dim + 3) >> 2);
     T J = (T)1;
+    int Je = 0;
 #pragma unroll
     for (int q = 0; q < (DMAX + 3) / 4; ++q) {
         if (q < (int)calls) {
@@ -210,9 +232,15 @@ __device__ __forceinline__ void sample_point(const Desc &d, const void *prm, uin
                     }
                 }
             }
+            if (!F64) {
+                float m = (float)J;
+                renorm(m, Je);
+                J = (T)m;
+            }
         }
     }
     jac = J;
+    jexp = Je;
     if (F64) {
         const double *p = (const double *)prm;
         double xv[DMAX];
@@ -394,8 +422,11 @@ __global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
             T x[DMAX];
             int idx[DMAX];
             T jac, f;
-            sample_point<DMAX, F64, KIND>(d, prm, t, (uint32_t)h, j, kd, x, idx, jac, f);
-            const T v = jac * f * scale;
+            int jexp;
+            sample_point<DMAX, F64, KIND>(d, prm, t, (uint32_t)h, j, kd, x, idx, jac, jexp, f);
+            T v;
+            if (F64) v = jac * f * scale;
+            else v = (T)scale2((float)(jac * f), jexp + sexp);
             acc.add(v);
             const T v2 = v * v;
 #pragma unroll
@@ -440,14 +471,14 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         T kd[DMAX], x[DMAX], jac, f;
-        int idx[DMAX];
+        int idx[DMAX], jexp;
         decode_digits<DMAX, T>((uint32_t)hs[k], d.n_st, d.dim, kd);
-        sample_point<DMAX, F64, KIND>(d, prm, t, (uint32_t)hs[k], js[k], kd, x, idx, jac, f);
+        sample_point<DMAX, F64, KIND>(d, prm, t, (uint32_t)hs[k], js[k], kd, x, idx, jac, jexp, f);
         for (int mu = 0; mu < d.dim; ++mu) {
             xo[k * d.dim + mu] = (double)x[mu];
             io[k * d.dim + mu] = idx[mu];
         }
-        jo[k] = (double)jac;
+        jo[k] = ldexp((double)jac, jexp);
         fo[k] = (double)f;
     }
 }

@@ -125,9 +125,9 @@ def two_gaussians_d4(n_ev=10_000, n_it=10, n_g=1000, seed=0, n_st=0):
                    exact=gauss_exact(amps, ws, cs))
 
 
-def two_balls_d4(n_ev=100_000, n_it=20, n_g=100, seed=0, alpha=0.2, n_st=0):
-    """§2.4 Eq. (balls): two balls of radius 0.067 at the Eq. (easyr) centres.
-    The paper does not state N_g for this example; N_g = 100 is used."""
+def two_balls_d4(n_ev=100_000, n_it=20, n_g=1000, seed=0, alpha=0.2, n_st=0):
+    """§2.4 Eq. (balls): two balls of radius 0.067 at the Eq. (easyr) centres
+    (N_g = 1000, the paper's typical value)."""
     dim = 4
     cs = [np.array([0.33, 0.5, 0.5, 0.5]), np.array([0.67, 0.5, 0.5, 0.5])]
     return Problem("two_balls_d4", dim, BALL, ball_blob([0.067, 0.067], cs), np.zeros(dim),

@@ -107,7 +107,13 @@ def test_samples_fp64_match_oracle(kind, dim):
         assert np.array_equal(idx[k], io)
         assert np.array_equal(x[k], xo), (k, x[k] - xo)
         assert jac[k] == jo
-        assert f[k] == pytest.approx(fo, rel=1e-13, abs=1e-300)
+        if fo > 0:
+            # CUDA's exp/log and the host's differ by an ulp or two; a long
+            # log-likelihood carries that relative error into ln f
+            A = abs(math.log(fo))
+            assert f[k] > 0 and abs(math.log(f[k]) - math.log(fo)) <= 2e-14 * max(1.0, A)
+        else:
+            assert f[k] == 0.0
 
 
 @pytest.mark.parametrize("kind,dim", CASES)
@@ -286,15 +292,18 @@ def test_other_integrands_fp64_iterations_match_oracle(kind, dim):
 # the FP32 path against the FP64 oracle
 # ---------------------------------------------------------------------------
 def test_four_peaks_d8_fp32_within_3_sigma_of_oracle():
-    prob = inputs.four_peaks_d8(n_ev=100_000, n_it=10)
+    """The 8-D four-peak workload at full size (N_ev = 1e6), 10 iterations: the
+    FP32 path against the FP64 oracle on the same Philox samples."""
+    prob = inputs.four_peaks_d8(n_it=10)
     g = gpu_of(prob, 1).run(prob.n_it)
     o = oracle_of(prob).run(prob.n_it)
     r, ro = g.result(discard=3), o.result(discard=3)
     assert abs(r["mean"] - ro["mean"]) < 3 * ro["sdev"]
     assert abs(r["mean"] - prob.exact) < 3 * r["sdev"]
-    # the same samples: iteration by iteration far closer than sigma
-    I, _ = g.history()
-    assert np.all(np.abs(I - np.array(o.I)) < 0.1 * np.sqrt(np.array(o.var)))
+    # the same samples: iteration by iteration far closer than sigma_j
+    I, Vg = g.history()
+    assert np.all(np.abs(I - np.array(o.I)) < 0.25 * np.sqrt(np.array(o.var)))
+    assert np.all(np.abs(np.sqrt(Vg) / np.sqrt(np.array(o.var)) - 1) < 0.05)
 
 
 # ---------------------------------------------------------------------------
@@ -340,14 +349,19 @@ def test_ball_d20_full_size_sampled(precision):
 
 
 def test_ball_d20_result_matches_volume():
-    """§1 footnote: 10 iterations of 1e7 find the 20-D ball, 10 more give the
-    volume to about 0.05%; FP32 map with FP64 accumulation."""
+    """§1 footnote: vegas+ finds the 20-D ball of radius 0.5 with iterations of
+    N_ev = 1e7 and then measures its volume to about 0.05% in 10 more.  The
+    first hit is a matter of luck (~0.25 expected per iteration at first); with
+    seed 0 it comes in iteration 5, so 30 iterations are run and the last 10
+    combined.  FP32 map and integrand, FP64 accumulation."""
     prob = inputs.ball_d20()
-    g = gpu_of(prob, 1).run(prob.n_it)
-    r = g.result(discard=prob.discard)
-    assert abs(r["mean"] - prob.exact) < 3 * r["sdev"]
-    assert r["sdev"] / prob.exact < 1.5e-3
+    g = gpu_of(prob, 1).run(30)
+    I, Vv = g.history()
+    r = g.result(discard=20)
+    assert abs(r["mean"] - prob.exact) < 3 * r["sdev"], (r, prob.exact)
+    assert r["sdev"] / prob.exact < 1e-3
     assert r["chi2"] / r["dof"] < 3.0
+    assert np.sqrt(Vv[-1]) / prob.exact < 5e-3
 
 
 # ---------------------------------------------------------------------------

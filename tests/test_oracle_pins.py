@@ -9,6 +9,7 @@ term, a wrong sign or index, a transposed operand) fails at least one of them.
 """
 import math
 import os
+import sys
 from fractions import Fraction
 
 import numpy as np
@@ -357,7 +358,11 @@ def test_smoothing_special_cases():
     assert out[3] == pytest.approx(comp(1 / 8), rel=1e-14)
     assert out[4] == pytest.approx(comp(6 / 8), rel=1e-14)
     assert out[5] == pytest.approx(comp(1 / 8), rel=1e-14)
-    assert np.all(out[[0, 1, 2, 6, 7, 8]] == 0.0)
+    # an increment whose smoothed d is zero keeps the weight of the smallest
+    # normal double: (1/ln(1/DBL_MIN))^alpha, about 0.0014 at alpha = 1
+    tiny = comp(sys.float_info.min)
+    assert np.all(out[[0, 1, 2, 6, 7, 8]] == pytest.approx(tiny, rel=1e-12))
+    assert 0.0013 < tiny < 0.0015
     hs = np.zeros(5)
     hs[0] = 2.0
     out = oracle.smooth_compress(hs, np.ones(5), 2.0)
@@ -454,8 +459,7 @@ def test_two_gaussians_accuracy_vs_ng():
 
 def test_two_balls_accuracy():
     """§2.4 Eq. (balls), N_ev = 1e5, alpha = 0.2: from ~24% before adapting to
-    ~0.34% after 10-20 iterations (simple y-space Monte Carlo; N_g = 100, which
-    the paper does not state)."""
+    ~0.34% after 10-20 iterations (simple y-space Monte Carlo, N_g = 1000)."""
     prob = inputs.two_balls_d4(n_st=1)
     assert prob.exact == pytest.approx(2 * math.pi ** 2 / 2 * 0.067 ** 4, rel=1e-12)
     o = make(prob).run(20)
