@@ -429,11 +429,11 @@ __global__ void __launch_bounds__(256) k_refine(const Desc *desc, const uint32_t
         edges[k] = xn;
     }
     __syncthreads();
-    // FP32 mirror {x_i, N_g dx_i}
+    // FP32 mirror {x_i, dx_i}
     float2 *tab = d.tab + (size_t)mu * n_g;
     for (int i = t; i < n_g; i += nt) {
         const double e0 = __ldcg(edges + i), e1 = __ldcg(edges + i + 1);
-        tab[i] = make_float2((float)e0, (float)((double)n_g * (e1 - e0)));
+        tab[i] = make_float2((float)e0, (float)(e1 - e0));
     }
 }
 

@@ -125,7 +125,7 @@ struct Group {
     uint32_t *d_members = nullptr;
     uint64_t *d_chunk_base = nullptr;
     uint32_t *d_head = nullptr;
-    int threads = 256, R = 1, blocks = 1, hist_shared = 0, hist_words = 0;
+    int threads = 256, R = 1, blocks = 1, hist_shared = 0, hist_words = 0, prm_words = 0;
     size_t smem = 0;
 };
 
@@ -261,14 +261,18 @@ static vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb)
         for (int i = 0; i < np; ++i) mb.prm32.push_back((float)q[5 + i]);
         for (int i = 0; i < np * P; ++i) mb.prm32.push_back((float)q[5 + np + i]);
     } else {
+        // per peak {a, k, 0, 0, c[D], pad}: a multiple of 4 floats
         const int K = (int)q[0];
+        const int D4 = (D + 3) & ~3;
         for (int k = 0; k < K; ++k) {
             const double *pk = q + 1 + k * (2 + D);
             mb.prm32.push_back((float)pk[0]);
             if (f->kind == VP_GAUSS) mb.prm32.push_back((float)(L2E / (pk[1] * pk[1])));
             else if (f->kind == VP_BALL) mb.prm32.push_back((float)(pk[1] * pk[1]));
             else mb.prm32.push_back((float)(pk[1] * L2E));
-            for (int i = 0; i < D; ++i) mb.prm32.push_back((float)pk[2 + i]);
+            mb.prm32.push_back(0.0f);
+            mb.prm32.push_back(0.0f);
+            for (int i = 0; i < D4; ++i) mb.prm32.push_back(i < D ? (float)pk[2 + i] : 0.0f);
         }
     }
     return VP_OK;
@@ -299,10 +303,9 @@ static T *at(const Set &s, const Member &mb, int which) {
     return (T *)((char *)s.arena.ptr + mb.off_bytes[which]);
 }
 
-// FP32 mirror {x_i, N_g dx_i} of one axis.
+// FP32 mirror {x_i, dx_i} of one axis.
 static void make_tab(const double *e, int n_g, float2 *tab) {
-    for (int i = 0; i < n_g; ++i)
-        tab[i] = make_float2((float)e[i], (float)((double)n_g * (e[i + 1] - e[i])));
+    for (int i = 0; i < n_g; ++i) tab[i] = make_float2((float)e[i], (float)(e[i + 1] - e[i]));
 }
 
 static vp_status plan_groups(Set &s) {
@@ -333,12 +336,15 @@ static vp_status plan_groups(Set &s) {
         const size_t hist_bytes = (size_t)max_bins * (tbytes + 4);
         g.threads = 256;
         g.hist_words = max_bins;
+        g.prm_words = g.prec == VP_FP64 ? 0 : ((max_words + 3) & ~3);
+        const size_t prm_bytes = (size_t)g.prm_words * 4;
         const int occ_probe = g.prec == VP_FP64
                                   ? sample_occupancy_f64(g.bucket, g.kind, g.threads, 0)
                                   : sample_occupancy_f32(g.bucket, g.kind, g.threads, 0);
         const double per_cta = expect / std::max(1, s.n_sm * std::max(1, occ_probe));
-        g.hist_shared = (hist_bytes <= 64 * 1024 && per_cta >= 0.5 * max_bins) ? 1 : 0;
-        g.smem = g.hist_shared ? hist_bytes : 0;
+        (void)per_cta;
+        g.hist_shared = (hist_bytes + prm_bytes <= 112 * 1024) ? 1 : 0;
+        g.smem = prm_bytes + (g.hist_shared ? hist_bytes : 0);
         if (g.smem > 48 * 1024) {
             cudaError_t e = g.prec == VP_FP64
                                 ? sample_smem_config_f64(g.bucket, g.kind, (int)g.smem)
@@ -351,7 +357,6 @@ static vp_status plan_groups(Set &s) {
         g.blocks = s.n_sm * occ;
         const double per_thread = expect / ((double)g.blocks * g.threads * 4.0);
         g.R = (int)std::min(64.0, std::max(1.0, std::ceil(per_thread)));
-        (void)max_words;
     }
     return VP_OK;
 }
@@ -430,6 +435,12 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         d.beta = mb.p.beta;
         d.ng_over_nst = (float)((double)G / (double)mb.n_st);
         d.inv_ng = (float)(1.0 / (double)G);
+        {
+            int e = 0;
+            const double m = std::frexp(std::pow((double)G, (double)D), &e);  // m in [0.5, 1)
+            d.ngD_m = (float)(2.0 * m);
+            d.ngD_e = e - 1;
+        }
         d.edges = at<double>(s, mb, B_EDGES);
         d.tab = at<float2>(s, mb, B_TAB);
         d.prm = at<double>(s, mb, B_PRM);
@@ -513,8 +524,11 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
         CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base, g.d_head,
                          (uint32_t)(g.threads * g.R), stream));
     }
-    // external record nodes when captured into the step graph
-    CU(cudaEventRecordWithFlags(s.ev0, stream, cudaEventRecordExternal));
+    // inside the step graph's capture the events must be external record nodes
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(stream, &cap));
+    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    CU(cudaEventRecordWithFlags(s.ev0, stream, ev_flags));
     for (size_t gi = 0; gi < s.groups.size(); ++gi) {
         Group &g = s.groups[gi];
         SampleArgs a;
@@ -526,13 +540,13 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
         a.R = g.R;
         a.hist_shared = g.hist_shared;
         a.hist_words = g.hist_words;
-        a.prm_words = 0;
+        a.prm_words = g.prm_words;
         cudaError_t e = g.prec == VP_FP64
                             ? launch_sample_f64(g.bucket, g.kind, g.blocks, g.threads, g.smem, stream, a)
                             : launch_sample_f32(g.bucket, g.kind, g.blocks, g.threads, g.smem, stream, a);
         if (e != cudaSuccess) return fail(VP_ECUDA, "sampling launch: %s", cudaGetErrorString(e));
     }
-    CU(cudaEventRecordWithFlags(s.ev1, stream, cudaEventRecordExternal));
+    CU(cudaEventRecordWithFlags(s.ev1, stream, ev_flags));
     s.timed = true;
     CU(launch_estimate(s.d_desc, s.d_tree_base, n, s.n_tree_total, 0, stream));
     s.last = stream;
@@ -842,8 +856,9 @@ extern "C" vp_status vp_eval_samples(vp_ctx *c, int64_t n, const uint64_t *h, co
     if (e == cudaSuccess) e = cudaMemcpyAsync(dj, j, n * 4, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
         e = d.prec == VP_FP64
-                ? launch_eval_f64(s.m[0].bucket, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di, djac, df)
-                : launch_eval_f32(s.m[0].bucket, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di, djac, df);
+                ? launch_eval_f64(s.m[0].bucket, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di, djac, df, 0)
+                : launch_eval_f32(s.m[0].bucket, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di, djac, df,
+                                  (int)((s.m[0].prm32.size() + 3) & ~(size_t)3));
     if (e == cudaSuccess) e = cudaMemcpyAsync(x, dx, n * D * 8, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, n * D * 4, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(jac, djac, n * 8, cudaMemcpyDeviceToHost, stream);

@@ -79,36 +79,36 @@ int sample_occupancy_f32(int bucket, int kind, int threads, size_t smem) {
 template <int DMAX, int KIND>
 static cudaError_t eval_one(cudaStream_t s, const Desc *desc, int member, int64_t n,
                             const uint64_t *h, const uint32_t *j, uint32_t t, double *x,
-                            int32_t *idx, double *jac, double *f) {
+                            int32_t *idx, double *jac, double *f, int pw) {
     int blocks = (int)((n + 127) / 128);
     if (blocks < 1) blocks = 1;
     if (blocks > 4096) blocks = 4096;
-    k_eval<DMAX, false, KIND><<<blocks, 128, 0, s>>>(desc, member, n, h, j, t, x, idx, jac, f);
+    k_eval<DMAX, false, KIND><<<blocks, 128, (size_t)pw * 4, s>>>(desc, member, n, h, j, t, x, idx, jac, f, pw);
     return cudaGetLastError();
 }
 
 template <int DMAX>
 static cudaError_t eval_kind(int kind, cudaStream_t s, const Desc *desc, int member, int64_t n,
                              const uint64_t *h, const uint32_t *j, uint32_t t, double *x,
-                             int32_t *idx, double *jac, double *f) {
+                             int32_t *idx, double *jac, double *f, int pw) {
     switch (kind) {
-        case VP_GAUSS: return eval_one<DMAX, VP_GAUSS>(s, desc, member, n, h, j, t, x, idx, jac, f);
-        case VP_BALL: return eval_one<DMAX, VP_BALL>(s, desc, member, n, h, j, t, x, idx, jac, f);
-        case VP_EXPNORM: return eval_one<DMAX, VP_EXPNORM>(s, desc, member, n, h, j, t, x, idx, jac, f);
-        case VP_POSTERIOR: return eval_one<DMAX, VP_POSTERIOR>(s, desc, member, n, h, j, t, x, idx, jac, f);
+        case VP_GAUSS: return eval_one<DMAX, VP_GAUSS>(s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+        case VP_BALL: return eval_one<DMAX, VP_BALL>(s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+        case VP_EXPNORM: return eval_one<DMAX, VP_EXPNORM>(s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+        case VP_POSTERIOR: return eval_one<DMAX, VP_POSTERIOR>(s, desc, member, n, h, j, t, x, idx, jac, f, pw);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_eval_f32(int bucket, int kind, cudaStream_t s, const Desc *desc, int member,
                             int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t,
-                            double *x, int32_t *idx, double *jac, double *f) {
+                            double *x, int32_t *idx, double *jac, double *f, int pw) {
     switch (bucket) {
-        case 0: return eval_kind<4>(kind, s, desc, member, n, h, j, t, x, idx, jac, f);
-        case 1: return eval_kind<8>(kind, s, desc, member, n, h, j, t, x, idx, jac, f);
-        case 2: return eval_kind<12>(kind, s, desc, member, n, h, j, t, x, idx, jac, f);
-        case 3: return eval_kind<16>(kind, s, desc, member, n, h, j, t, x, idx, jac, f);
-        case 4: return eval_kind<24>(kind, s, desc, member, n, h, j, t, x, idx, jac, f);
+        case 0: return eval_kind<4>(kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+        case 1: return eval_kind<8>(kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+        case 2: return eval_kind<12>(kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+        case 3: return eval_kind<16>(kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+        case 4: return eval_kind<24>(kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
     }
     return cudaErrorInvalidValue;
 }

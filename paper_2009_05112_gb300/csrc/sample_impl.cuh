@@ -45,9 +45,10 @@ template <> struct Real<false> { typedef float T; };
 // ---------------------------------------------------------------------------
 // Integrands.  FP64 versions follow the blob (see vegasp.h) in IEEE-rounded
 // steps; FP32 versions use constants prepared on the host (prm32):
-//  GAUSS    per peak {a, log2(e)/w^2, c[D]}     f = sum a 2^(-k |x-c|^2)
-//  BALL     per peak {a, r^2, c[D]}             f = sum a [|x-c|^2 < r^2]
-//  EXPNORM  per peak {a, s log2(e), c[D]}       f = sum a 2^(-k |x-c|)
+//  GAUSS    per peak {a, log2(e)/w^2, 0, 0, c[D], pad}  f = sum a 2^(-k |x-c|^2)
+//  BALL     per peak {a, r^2, 0, 0, c[D], pad}          f = sum a [|x-c|^2 < r^2]
+//  EXPNORM  per peak {a, s log2(e), 0, 0, c[D], pad}    f = sum a 2^(-k |x-c|)
+//           (peaks padded to a multiple of 4 floats for 16-byte shared loads)
 //  POSTERIOR {n, P, kN, kW, lcN, lcW, kprior, logref2, y[n], A[n][P]} in log2 units
 // ---------------------------------------------------------------------------
 template <int DMAX>
@@ -76,22 +77,29 @@ __device__ __forceinline__ double f_peaks64(int kind, const double *p, int K, in
 template <int DMAX>
 __device__ __forceinline__ float f_peaks32(int kind, const float *p, int K, int dim,
                                            const float (&x)[DMAX]) {
+    // per peak: {a, k, 0, 0, c_0 .. c_{D-1}, pad to 4} in shared memory
+    const int stride = 4 + ((dim + 3) & ~3);
     float f = 0.0f;
-    for (int k = 0; k < K; ++k) {
-        const float a = p[0], kk = p[1];
-        const float *c = p + 2;
+    for (int k = 0; k < K; ++k, p += stride) {
+        const float4 hd = *(const float4 *)p;
         float r2 = 0.0f;
 #pragma unroll
-        for (int mu = 0; mu < DMAX; ++mu) {
-            if (mu < dim) {
-                float dx = x[mu] - c[mu];
-                r2 = fmaf(dx, dx, r2);
+        for (int m4 = 0; m4 < DMAX; m4 += 4) {
+            if (m4 < dim) {
+                const float4 c = *(const float4 *)(p + 4 + m4);
+                const float cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    if (m4 + l < DMAX && m4 + l < dim) {
+                        const float dx = x[m4 + l] - cc[l];
+                        r2 = fmaf(dx, dx, r2);
+                    }
+                }
             }
         }
-        if (kind == VP_GAUSS) f += a * ex2_approx(-kk * r2);
-        else if (kind == VP_BALL) f += (r2 < kk) ? a : 0.0f;
-        else f += a * ex2_approx(-kk * sqrtf(r2));
-        p += 2 + dim;
+        if (kind == VP_GAUSS) f = fmaf(hd.x, ex2_approx(-hd.y * r2), f);
+        else if (kind == VP_BALL) f += (r2 < hd.y) ? hd.x : 0.0f;
+        else f = fmaf(hd.x, ex2_approx(-hd.y * sqrtf(r2)), f);
     }
     return f;
 }
@@ -165,8 +173,8 @@ __device__ __forceinline__ float f_post32(const float *p, int dim, const float (
 // FP32 Jacobians of adapted high-dimensional maps leave the FP32 range (e.g.
 // 20 axes of N_g dx ~ 3e-3 give 3e-51), so the FP32 path carries J as a
 // mantissa in [1, 2) and a separate integer exponent, renormalised after
-// every group of four axes (four factors cannot leave the range: each is at
-// least ~N_g ulp(x) and at most N_g (b - a)).
+// every group of four axes (four factors dx_i cannot leave the range: each is
+// at least ~ulp(x) and at most b - a).
 __device__ __forceinline__ void renorm(float &m, int &e) {
     const int b = __float_as_int(m);
     const int ex = (b >> 23) & 0xff;
@@ -183,106 +191,184 @@ __device__ __forceinline__ float scale2(float x, int n) {
     return x * __int_as_float((n1 + 127) << 23) * __int_as_float((n2 + 127) << 23);
 }
 
-template <int DMAX, bool F64, int KIND>
-__device__ __forceinline__ void sample_point(const Desc &d, const void *prm, uint32_t t,
-                                             uint32_t h, uint32_t j,
-                                             const typename Real<F64>::T (&kd)[DMAX],
-                                             typename Real<F64>::T (&x)[DMAX],
-                                             int (&idx)[DMAX],
-                                             typename Real<F64>::T &jac, int &jexp,
-                                             typename Real<F64>::T &f) {
-    typedef typename Real<F64>::T T;
-    const int dim = d.dim, n_g = d.n_g;
-    const uint32_t calls = (uint32_t)((dim + 3) >> 2);
-    T J = (T)1;
-    int Je = 0;
+// Per-integral constants of the sampling loop, read once into registers.
+struct Loop {
+    int dim, n_g, K;
+    uint32_t n_st, calls, iid, t;
+    uint32_t rk0[10], rk1[10];  // Philox round keys
+    float c32;                  // N_g / N_st
+    float c32x;                 // N_g / N_st * 2^-23
+    float ngm1;                 // N_g - 1
+    float ngD_m;                // N_g^D = ngD_m 2^ngD_e
+    int ngD_e;
+    double nst, ng;
+    const float2 *tab;
+    const double *edges;
+};
+
+__device__ __forceinline__ Loop make_loop(const Desc *dp, uint32_t t) {
+    Loop L;
+    L.dim = __ldg(&dp->dim);
+    L.n_g = __ldg(&dp->n_g);
+    L.K = __ldg(&dp->n_peaks);
+    L.n_st = __ldg(&dp->n_st);
+    L.calls = (uint32_t)((L.dim + 3) >> 2);
+    L.iid = __ldg(&dp->integral_id);
+    L.t = t;
+    uint32_t k0 = __ldg(&dp->key0), k1 = __ldg(&dp->key1);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        L.rk0[r] = k0;
+        L.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    L.c32 = __ldg(&dp->ng_over_nst);
+    L.c32x = L.c32 * 1.1920928955078125e-07f;
+    L.ngm1 = (float)(L.n_g - 1);
+    L.ngD_m = __ldg(&dp->ngD_m);
+    L.ngD_e = __ldg(&dp->ngD_e);
+    L.nst = (double)L.n_st;
+    L.ng = (double)L.n_g;
+    L.tab = (const float2 *)__ldg((const unsigned long long *)&dp->tab);
+    L.edges = (const double *)__ldg((const unsigned long long *)&dp->edges);
+    return L;
+}
+
+// Philox4x32-10 with precomputed round keys (same function as philox4x32_10).
+__device__ __forceinline__ U4 philox_rk(U4 c, const uint32_t (&k0)[10], const uint32_t (&k1)[10]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        const uint32_t hi0 = __umulhi(m0, c.a), lo0 = m0 * c.a;
+        const uint32_t hi1 = __umulhi(m1, c.c), lo1 = m1 * c.c;
+        U4 n;
+        n.a = hi1 ^ c.b ^ k0[r];
+        n.b = lo1;
+        n.c = hi0 ^ c.d ^ k1[r];
+        n.d = lo0;
+        c = n;
+    }
+    return c;
+}
+
+// FP32 per-hypercube offsets kc[mu] = (k_mu - 1 + 2^-24) N_g/N_st so that
+// y N_g = (1 + m 2^-23) N_g/N_st + kc with m = r >> 9, i.e. u = (m + 1/2) 2^-23.
+template <int DMAX>
+__device__ __forceinline__ void hcube_offsets(const Loop &L, const uint32_t (&kd)[DMAX],
+                                              float (&kc)[DMAX]) {
+#pragma unroll
+    for (int mu = 0; mu < DMAX; ++mu)
+        kc[mu] = ((float)kd[mu] - 0.99999994039535522461f) * L.c32;
+}
+
+// ---------------------------------------------------------------------------
+// One sample, FP32 path (a1-a3): x[], idx[], J = Jm 2^Je, f.
+// ---------------------------------------------------------------------------
+template <int DMAX, int KIND>
+__device__ __forceinline__ void point32(const Loop &L, const float *prm, uint32_t h, uint32_t j,
+                                        const float (&kc)[DMAX], float (&x)[DMAX],
+                                        int (&idx)[DMAX], float &Jm, int &Je, float &f) {
+    float J = L.ngD_m;
+    int e = L.ngD_e;
 #pragma unroll
     for (int q = 0; q < (DMAX + 3) / 4; ++q) {
-        if (q < (int)calls) {
-            U4 c = {j * calls + (uint32_t)q, h, t, d.integral_id};
-            U4 r = philox4x32_10(c, d.key0, d.key1);
+        if (q < (int)L.calls) {
+            U4 c = {j * L.calls + (uint32_t)q, h, L.t, L.iid};
+            const U4 r = philox_rk(c, L.rk0, L.rk1);
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
                 const int mu = 4 * q + l;
-                if (mu < DMAX && mu < dim) {
-                    const uint32_t word = lane_of(r, l);
-                    if (F64) {
-                        const double u = u01_f64(word);
-                        const double y = __ddiv_rn(__dadd_rn((double)kd[mu], u), (double)d.n_st);
-                        const double yng = __dmul_rn(y, (double)n_g);
-                        int i = (int)floor(yng);
-                        i = i > n_g - 1 ? n_g - 1 : i;
-                        const double delta = __dsub_rn(yng, (double)i);
-                        const double *e = d.edges + (size_t)mu * (size_t)(n_g + 1);
-                        const double e0 = __ldg(e + i), e1 = __ldg(e + i + 1);
-                        const double dx = __dsub_rn(e1, e0);
-                        x[mu] = (T)__dadd_rn(e0, __dmul_rn(dx, delta));
-                        J = (T)__dmul_rn((double)J, __dmul_rn((double)n_g, dx));
-                        idx[mu] = i;
-                    } else {
-                        const float u = u01_f32(word);
-                        const float tt = ((float)kd[mu] + u) * d.ng_over_nst;
-                        int i = (int)tt;
-                        i = i > n_g - 1 ? n_g - 1 : i;
-                        const float delta = tt - (float)i;
-                        const float2 e = __ldg(d.tab + (size_t)mu * (size_t)n_g + i);
-                        x[mu] = (T)fmaf(e.y, delta * d.inv_ng, e.x);
-                        J = (T)((float)J * e.y);
-                        idx[mu] = i;
-                    }
+                if (mu < DMAX && mu < L.dim) {
+                    const uint32_t w = lane_of(r, l);
+                    // (1 + m 2^-23) from the top 23 bits, no int->float conversion
+                    const float one_m = __int_as_float(0x3f800000 | (w >> 9));
+                    const float tt = fmaf(one_m, L.c32, kc[mu]);  // y N_g
+                    // floor(tt) for 0 <= tt < 2^22 by a round-down add of 1.5 2^23
+                    const float big = __fadd_rd(tt, 12582912.0f);
+                    int i = __float_as_int(big) - 0x4B400000;
+                    float fl = big - 12582912.0f;
+                    i = min(i, L.n_g - 1);
+                    fl = fminf(fl, L.ngm1);
+                    const float delta = tt - fl;
+                    const float2 ed = __ldg(L.tab + mu * L.n_g + i);  // {x_i, dx_i}
+                    x[mu] = fmaf(ed.y, delta, ed.x);
+                    J *= ed.y;
+                    idx[mu] = i;
                 }
             }
-            if (!F64) {
-                float m = (float)J;
-                renorm(m, Je);
-                J = (T)m;
+            renorm(J, e);
+        }
+    }
+    Jm = J;
+    Je = e;
+    if (KIND == VP_POSTERIOR) f = f_post32<DMAX>(prm, L.dim, x);
+    else f = f_peaks32<DMAX>(KIND, prm, L.K, L.dim, x);
+}
+
+// ---------------------------------------------------------------------------
+// One sample, FP64 path (a1-a3), the oracle's IEEE sequence step by step.
+// ---------------------------------------------------------------------------
+template <int DMAX, int KIND>
+__device__ __forceinline__ void point64(const Loop &L, const double *prm, uint32_t h, uint32_t j,
+                                        const uint32_t (&kd)[DMAX], double (&x)[DMAX],
+                                        int (&idx)[DMAX], double &J, double &f) {
+    J = 1.0;
+#pragma unroll
+    for (int q = 0; q < (DMAX + 3) / 4; ++q) {
+        if (q < (int)L.calls) {
+            U4 c = {j * L.calls + (uint32_t)q, h, L.t, L.iid};
+            const U4 r = philox_rk(c, L.rk0, L.rk1);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int mu = 4 * q + l;
+                if (mu < DMAX && mu < L.dim) {
+                    const double u = u01_f64(lane_of(r, l));
+                    const double y = __ddiv_rn(__dadd_rn((double)kd[mu], u), L.nst);
+                    const double yng = __dmul_rn(y, L.ng);
+                    int i = (int)floor(yng);
+                    i = i > L.n_g - 1 ? L.n_g - 1 : i;
+                    const double delta = __dsub_rn(yng, (double)i);
+                    const double *e = L.edges + (size_t)mu * (size_t)(L.n_g + 1);
+                    const double e0 = __ldg(e + i), e1 = __ldg(e + i + 1);
+                    const double dx = __dsub_rn(e1, e0);
+                    x[mu] = __dadd_rn(e0, __dmul_rn(dx, delta));
+                    J = __dmul_rn(J, __dmul_rn(L.ng, dx));
+                    idx[mu] = i;
+                }
             }
         }
     }
-    jac = J;
-    jexp = Je;
-    if (F64) {
-        const double *p = (const double *)prm;
-        double xv[DMAX];
-#pragma unroll
-        for (int mu = 0; mu < DMAX; ++mu) xv[mu] = (double)x[mu];
-        if (KIND == VP_POSTERIOR) f = (T)f_post64<DMAX>(p, dim, xv);
-        else f = (T)f_peaks64<DMAX>(KIND, p + 1, (int)p[0], dim, xv);
-    } else {
-        const float *p = (const float *)prm;
-        float xv[DMAX];
-#pragma unroll
-        for (int mu = 0; mu < DMAX; ++mu) xv[mu] = (float)x[mu];
-        if (KIND == VP_POSTERIOR) f = (T)f_post32<DMAX>(p, dim, xv);
-        else f = (T)f_peaks32<DMAX>(KIND, p, d.n_peaks, dim, xv);
-    }
+    if (KIND == VP_POSTERIOR) f = f_post64<DMAX>(prm, L.dim, x);
+    else f = f_peaks64<DMAX>(KIND, prm + 1, L.K, L.dim, x);
 }
 
 // Mixed-radix digits of h: k_mu = (h / N_st^mu) mod N_st.
-template <int DMAX, typename T>
-__device__ __forceinline__ void decode_digits(uint32_t h, uint32_t n_st, int dim, T (&kd)[DMAX]) {
+template <int DMAX>
+__device__ __forceinline__ void decode_digits(uint32_t h, uint32_t n_st, int dim,
+                                              uint32_t (&kd)[DMAX]) {
 #pragma unroll
     for (int mu = 0; mu < DMAX; ++mu) {
         if (mu < dim) {
-            uint32_t q = h / n_st;
-            kd[mu] = (T)(h - q * n_st);
+            const uint32_t q = h / n_st;
+            kd[mu] = h - q * n_st;
             h = q;
         } else {
-            kd[mu] = (T)0;
+            kd[mu] = 0u;
         }
     }
 }
 
 // h -> h + 1 on the digits (carry propagation).
-template <int DMAX, typename T>
-__device__ __forceinline__ void next_digits(uint32_t n_st, int dim, T (&kd)[DMAX]) {
+template <int DMAX>
+__device__ __forceinline__ void next_digits(uint32_t n_st, int dim, uint32_t (&kd)[DMAX]) {
     bool carry = true;
 #pragma unroll
     for (int mu = 0; mu < DMAX; ++mu) {
         if (carry && mu < dim) {
-            T v = kd[mu] + (T)1;
-            if (v >= (T)n_st) {
-                kd[mu] = (T)0;
+            const uint32_t v = kd[mu] + 1u;
+            if (v >= n_st) {
+                kd[mu] = 0u;
             } else {
                 kd[mu] = v;
                 carry = false;
@@ -317,7 +403,7 @@ template <bool F64> struct Acc;
 template <> struct Acc<true> {
     double s1, s2;
     __device__ __forceinline__ void reset() { s1 = 0.0; s2 = 0.0; }
-    __device__ __forceinline__ void add(double v) { s1 += v; s2 += v * v; }
+    __device__ __forceinline__ void add(double v, double v2) { s1 += v; s2 += v2; }
     __device__ __forceinline__ double m1() const { return s1; }
     __device__ __forceinline__ double m2() const { return s2; }
 };
@@ -325,36 +411,53 @@ template <> struct Acc<false> {
     float s1, c1, s2, c2;
     __device__ __forceinline__ void reset() { s1 = c1 = s2 = c2 = 0.0f; }
     __device__ __forceinline__ static void kahan(float &s, float &c, float v) {
-        float y = __fsub_rn(v, c);
-        float t = __fadd_rn(s, y);
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
-    __device__ __forceinline__ void add(float v) {
+    __device__ __forceinline__ void add(float v, float v2) {
         kahan(s1, c1, v);
-        kahan(s2, c2, __fmul_rn(v, v));
+        kahan(s2, c2, v2);
     }
     __device__ __forceinline__ double m1() const { return (double)s1 - (double)c1; }
     __device__ __forceinline__ double m2() const { return (double)s2 - (double)c2; }
 };
 
+// Integrand constants for this CTA: FP32 path copies them to shared memory
+// (read with broadcast loads in the sample loop); FP64 path reads the blob.
+__device__ __forceinline__ void load_prm32(const Desc *dp, float *sprm, int words) {
+    const float *src = (const float *)__ldg((const unsigned long long *)&dp->prm32);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) sprm[i] = __ldg(src + i);
+}
+
 // ---------------------------------------------------------------------------
 // The fused sampling kernel.
-// Shared memory: [prm_words x 4 B][hist sum: hist_words x (4|8) B][hist count: hist_words x 4 B]
+// Shared memory: [prm: prm_words x 4 B][hist sum: hist_words x (4|8) B]
+//                [hist count: hist_words x 4 B]
 // ---------------------------------------------------------------------------
 template <int DMAX, bool F64, int KIND>
 __global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
     typedef typename Real<F64>::T T;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_chunk;
-    uint32_t *sprm = (uint32_t *)smem;
+    float *sprm = (float *)smem;
     T *hs = (T *)(smem + (size_t)a.prm_words * 4);
     uint32_t *hc = (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.hist_words * sizeof(T));
 
-    const uint64_t total = a.chunk_base[a.n_group];
+    const uint64_t total = __ldg(a.chunk_base + a.n_group);
     const uint32_t C = blockDim.x * (uint32_t)a.R;
     int cur = -1;
     const Desc *dp = nullptr;
+    Loop L;
+    const void *prm = nullptr;
+    int bins = 0, sexp = 0;
+    T scale = (T)1;
+    double unscale = 1.0;
+    const uint64_t *off = nullptr;
+    uint64_t n_hc = 0, n_total = 0;
+    double *S1 = nullptr, *S2 = nullptr, *HS = nullptr;
+    uint32_t *HC = nullptr;
 
     for (;;) {
         __syncthreads();
@@ -364,22 +467,39 @@ __global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
         if (c >= total) break;
         const int g = upper_index(a.chunk_base, a.n_group, c);
         if (g != cur) {
-            // leaving integral cur: flush its privatised histograms
-            if (cur >= 0 && a.hist_shared) {
-                const int bins = dp->dim * dp->n_g;
-                const double unscale = ldexp(1.0, -2 * dp->st->scale_exp);
+            if (cur >= 0 && a.hist_shared) {  // leaving integral cur: flush its histograms
+                const double un2 = unscale * unscale;
                 for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-                    if (hc[b]) {
-                        atomicAdd(dp->hsum + b, (double)hs[b] * unscale);
-                        atomicAdd(dp->hcnt + b, hc[b]);
+                    const uint32_t n = hc[b];
+                    if (n) {
+                        atomicAdd(HS + b, (double)hs[b] * un2);
+                        atomicAdd(HC + b, n);
                     }
                 }
                 __syncthreads();
             }
             cur = g;
-            dp = a.desc + a.members[g];
+            dp = a.desc + __ldg(a.members + g);
+            const State *st = (const State *)__ldg((const unsigned long long *)&dp->st);
+            L = make_loop(dp, __ldcg(&st->t));
+            sexp = __ldcg(&st->scale_exp);
+            scale = (T)ldexp(1.0, sexp);
+            unscale = ldexp(1.0, -sexp);
+            bins = L.dim * L.n_g;
+            off = (const uint64_t *)__ldg((const unsigned long long *)&dp->off);
+            n_hc = __ldg(&dp->n_hc);
+            n_total = __ldcg(off + n_hc);
+            S1 = (double *)__ldg((const unsigned long long *)&dp->s1);
+            S2 = (double *)__ldg((const unsigned long long *)&dp->s2);
+            HS = (double *)__ldg((const unsigned long long *)&dp->hsum);
+            HC = (uint32_t *)__ldg((const unsigned long long *)&dp->hcnt);
+            if (F64) {
+                prm = (const void *)__ldg((const unsigned long long *)&dp->prm);
+            } else {
+                load_prm32(dp, sprm, a.prm_words);
+                prm = (const void *)sprm;
+            }
             if (a.hist_shared) {
-                const int bins = dp->dim * dp->n_g;
                 for (int b = threadIdx.x; b < bins; b += blockDim.x) {
                     hs[b] = (T)0;
                     hc[b] = 0u;
@@ -387,74 +507,72 @@ __global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
             }
             __syncthreads();
         }
-        const Desc &d = *dp;
-        const int dim = d.dim;
-        const uint64_t n_total = __ldcg(d.off + d.n_hc);
-        const uint64_t c0 = (c - a.chunk_base[g]) * (uint64_t)C;
+        const uint64_t c0 = (c - __ldg(a.chunk_base + g)) * (uint64_t)C;
         const uint64_t c_end = min(c0 + (uint64_t)C, n_total);
         const uint64_t s_begin = c0 + (uint64_t)threadIdx.x * (uint64_t)a.R;
         const uint64_t s_end = min(s_begin + (uint64_t)a.R, c_end);
         if (s_begin >= s_end) continue;
 
-        const uint32_t t = __ldcg(&d.st->t);
-        const int sexp = __ldcg(&d.st->scale_exp);
-        const T scale = (T)ldexp(1.0, sexp);
-        const double unscale = ldexp(1.0, -sexp);
-        const void *prm = F64 ? (const void *)d.prm : (const void *)d.prm32;
-
-        uint64_t h = find_hcube(d.off, d.n_hc, s_begin);
-        uint64_t next = __ldg(d.off + h + 1);
-        uint32_t j = (uint32_t)(s_begin - __ldg(d.off + h));
-        T kd[DMAX];
-        decode_digits<DMAX, T>((uint32_t)h, d.n_st, dim, kd);
+        uint64_t h = find_hcube(off, n_hc, s_begin);
+        uint64_t next = __ldg(off + h + 1);
+        uint32_t j = (uint32_t)(s_begin - __ldg(off + h));
+        uint32_t kd[DMAX];
+        decode_digits<DMAX>((uint32_t)h, L.n_st, L.dim, kd);
+        float kc[DMAX];
+        if (!F64) hcube_offsets<DMAX>(L, kd, kc);
         Acc<F64> acc;
         acc.reset();
         for (uint64_t s = s_begin; s < s_end; ++s) {
             if (s == next) {
-                atomicAdd(d.s1 + h, acc.m1() * unscale);
-                atomicAdd(d.s2 + h, acc.m2() * unscale * unscale);
+                atomicAdd(S1 + h, acc.m1() * unscale);
+                atomicAdd(S2 + h, acc.m2() * unscale * unscale);
                 acc.reset();
                 ++h;
-                next = __ldg(d.off + h + 1);
+                next = __ldg(off + h + 1);
                 j = 0;
-                next_digits<DMAX, T>(d.n_st, dim, kd);
+                next_digits<DMAX>(L.n_st, L.dim, kd);
+                if (!F64) hcube_offsets<DMAX>(L, kd, kc);
             }
-            T x[DMAX];
             int idx[DMAX];
-            T jac, f;
-            int jexp;
-            sample_point<DMAX, F64, KIND>(d, prm, t, (uint32_t)h, j, kd, x, idx, jac, jexp, f);
             T v;
-            if (F64) v = jac * f * scale;
-            else v = (T)scale2((float)(jac * f), jexp + sexp);
-            acc.add(v);
+            if (F64) {
+                double x[DMAX], J, f;
+                point64<DMAX, KIND>(L, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
+                v = (T)(J * f * (double)scale);
+            } else {
+                float x[DMAX], Jm, f;
+                int Je;
+                point32<DMAX, KIND>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je, f);
+                v = (T)scale2(Jm * f, Je + sexp);
+            }
             const T v2 = v * v;
+            acc.add(v, v2);
 #pragma unroll
             for (int mu = 0; mu < DMAX; ++mu) {
-                if (mu < dim) {
-                    const int b = mu * d.n_g + idx[mu];
+                if (mu < L.dim) {
+                    const int b = mu * L.n_g + idx[mu];
                     if (a.hist_shared) {
                         if (v2 != (T)0) atomicAdd(hs + b, v2);
                         atomicAdd(hc + b, 1u);
                     } else {
-                        if (v2 != (T)0) atomicAdd(d.hsum + b, (double)v2 * unscale * unscale);
-                        atomicAdd(d.hcnt + b, 1u);
+                        if (v2 != (T)0) atomicAdd(HS + b, (double)v2 * unscale * unscale);
+                        atomicAdd(HC + b, 1u);
                     }
                 }
             }
             ++j;
         }
-        atomicAdd(d.s1 + h, acc.m1() * unscale);
-        atomicAdd(d.s2 + h, acc.m2() * unscale * unscale);
+        atomicAdd(S1 + h, acc.m1() * unscale);
+        atomicAdd(S2 + h, acc.m2() * unscale * unscale);
     }
     if (cur >= 0 && a.hist_shared) {
         __syncthreads();
-        const int bins = dp->dim * dp->n_g;
-        const double unscale = ldexp(1.0, -2 * dp->st->scale_exp);
+        const double un2 = unscale * unscale;
         for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-            if (hc[b]) {
-                atomicAdd(dp->hsum + b, (double)hs[b] * unscale);
-                atomicAdd(dp->hcnt + b, hc[b]);
+            const uint32_t n = hc[b];
+            if (n) {
+                atomicAdd(HS + b, (double)hs[b] * un2);
+                atomicAdd(HC + b, n);
             }
         }
     }
@@ -464,22 +582,41 @@ __global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
 template <int DMAX, bool F64, int KIND>
 __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *hs,
                        const uint32_t *js, uint32_t t, double *xo, int32_t *io, double *jo,
-                       double *fo) {
-    typedef typename Real<F64>::T T;
-    const Desc &d = desc[member];
-    const void *prm = F64 ? (const void *)d.prm : (const void *)d.prm32;
+                       double *fo, int prm_words) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *sprm = (float *)smem;
+    const Desc *dp = desc + member;
+    const Loop L = make_loop(dp, t);
+    if (!F64) load_prm32(dp, sprm, prm_words);
+    __syncthreads();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        T kd[DMAX], x[DMAX], jac, f;
-        int idx[DMAX], jexp;
-        decode_digits<DMAX, T>((uint32_t)hs[k], d.n_st, d.dim, kd);
-        sample_point<DMAX, F64, KIND>(d, prm, t, (uint32_t)hs[k], js[k], kd, x, idx, jac, jexp, f);
-        for (int mu = 0; mu < d.dim; ++mu) {
-            xo[k * d.dim + mu] = (double)x[mu];
-            io[k * d.dim + mu] = idx[mu];
+        uint32_t kd[DMAX];
+        int idx[DMAX];
+        decode_digits<DMAX>((uint32_t)hs[k], L.n_st, L.dim, kd);
+        double xd[DMAX], jac, f;
+        if (F64) {
+            point64<DMAX, KIND>(L, (const double *)__ldg((const unsigned long long *)&dp->prm),
+                                (uint32_t)hs[k], js[k], kd, xd, idx, jac, f);
+        } else {
+            float kc[DMAX], x[DMAX], Jm, ff;
+            int Je;
+            hcube_offsets<DMAX>(L, kd, kc);
+            point32<DMAX, KIND>(L, sprm, (uint32_t)hs[k], js[k], kc, x, idx, Jm, Je, ff);
+#pragma unroll
+            for (int mu = 0; mu < DMAX; ++mu) xd[mu] = (double)x[mu];
+            jac = ldexp((double)Jm, Je);
+            f = (double)ff;
         }
-        jo[k] = ldexp((double)jac, jexp);
-        fo[k] = (double)f;
+#pragma unroll
+        for (int mu = 0; mu < DMAX; ++mu) {
+            if (mu < L.dim) {
+                xo[k * L.dim + mu] = xd[mu];
+                io[k * L.dim + mu] = idx[mu];
+            }
+        }
+        jo[k] = jac;
+        fo[k] = f;
     }
 }
 
@@ -490,10 +627,10 @@ cudaError_t launch_sample_f64(int bucket, int kind, dim3 grid, dim3 block, size_
                               cudaStream_t s, const SampleArgs &a);
 cudaError_t launch_eval_f32(int bucket, int kind, cudaStream_t s, const Desc *desc, int member,
                             int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t,
-                            double *x, int32_t *idx, double *jac, double *f);
+                            double *x, int32_t *idx, double *jac, double *f, int prm_words);
 cudaError_t launch_eval_f64(int bucket, int kind, cudaStream_t s, const Desc *desc, int member,
                             int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t,
-                            double *x, int32_t *idx, double *jac, double *f);
+                            double *x, int32_t *idx, double *jac, double *f, int prm_words);
 cudaError_t sample_smem_config_f32(int bucket, int kind, int max_smem);
 cudaError_t sample_smem_config_f64(int bucket, int kind, int max_smem);
 int sample_occupancy_f32(int bucket, int kind, int threads, size_t smem);

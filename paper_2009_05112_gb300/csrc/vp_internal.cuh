@@ -53,9 +53,11 @@ struct Desc {
     double alpha, beta;
     float ng_over_nst;         // N_g / N_st (FP32 path)
     float inv_ng;              // 1 / N_g (FP32 path)
+    float ngD_m;               // N_g^D = ngD_m 2^ngD_e (FP32 path: J = N_g^D prod dx_i)
+    int32_t ngD_e;
     // device buffers (all owned by the set)
     double *edges;     // [dim][n_g + 1] FP64 grid
-    float2 *tab;       // [dim][n_g] {x_i, J_i = N_g dx_i}, FP32 mirror of the grid
+    float2 *tab;       // [dim][n_g] {x_i, dx_i}, FP32 mirror of the grid
     const double *prm;  // integrand blob as given (FP64 path)
     const float *prm32; // FP32 constants derived from the blob (FP32 path)
     uint32_t *n_h;     // [n_hc]
