@@ -184,6 +184,33 @@ vp_status vp_eval_samples(vp_ctx *ctx, int64_t n, const uint64_t *h, const uint3
  * launching stream); -1 if none recorded. */
 vp_status vp_last_sample_ms(vp_ctx *ctx, float *ms);
 
+/* ---- reallocation without device allocation --------------------------- */
+/* vp_alloc_static: the reallocation step of vp_adapt (the fixed-order sum of
+ * d_h, n_h = max(2, floor(N_ev d_h / sum d)) -- or floor(.) + 2 when plus2 is
+ * set -- and the exclusive offsets) on buffers the caller provides, allocating
+ * nothing.  The paper has no counterpart: this entry point is for callers that
+ * cannot allocate device memory while they work, such as a serving process that
+ * reserved all device memory up front for a pool it manages itself, or code
+ * that must not call cudaMalloc mid-step because cudaMalloc can synchronise the
+ * device.
+ *   d_h      [n_hc] DEVICE doubles, finite and >= 0 (read)
+ *   n_h      [n_hc] DEVICE uint32 (written)
+ *   offsets  [n_hc + 1] DEVICE uint64 (written; offsets[n_hc] = sum of n_h)
+ *   n_hc     1 .. 4,194,304 (VP_EINVAL beyond: the scratch holds 4096 blocks of
+ *            1024 hypercubes); n_ev >= 2
+ * Work is enqueued on stream; nothing is allocated and nothing is freed.  Its
+ * scratch is one static device array of about 64 KB, which every GPU that loads
+ * the library holds until the process exits.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the array and leaves the last call's contents in it: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race, so
+ * the caller must order them.  If the sum of d_h is not finite, n_h and offsets
+ * are left unchanged.  VP_EINVAL: NULL buffer or size out of range; VP_ECUDA: a
+ * launch failed. */
+vp_status vp_alloc_static(const double *d_h, int64_t n_hc, int64_t n_ev, int plus2,
+                          uint32_t *n_h, uint64_t *offsets, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,14 @@ extern "C" vp_status vp_set_allocator(vp_alloc_fn alloc, vp_free_fn free_fn, voi
 
 extern "C" const char *vp_last_error(void) { return g_err.c_str(); }
 
+namespace vp {
+// Records a message for vp_last_error (used by entry points in other files).
+const char *set_error_message(vp_status, const char *msg) {
+    g_err = msg;
+    return g_err.c_str();
+}
+}  // namespace vp
+
 struct DevMem {
     void *ptr = nullptr;
     size_t bytes = 0;

@@ -79,6 +79,7 @@ _SIGS = {
     "vp_refine_from_hist": [_P, _P, _P, _P],
     "vp_eval_samples": [_P, ctypes.c_int64, _P, _P, ctypes.c_uint32, _P, _P, _P, _P],
     "vp_last_sample_ms": [_P, ctypes.POINTER(ctypes.c_float)],
+    "vp_alloc_static": [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P, _P, _P],
 }
 
 _lib = None
