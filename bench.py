@@ -305,7 +305,7 @@ def run_ours(args):
                     "note": "create from host parameters + %d steps + a host read of the "
                             "estimate after every step, wall clock" % args.steps},
             "roofline": roof, "clocks": clocks,
-            "gpu_launches": 7 * args.steps,
+            "gpu_launches": 5 * args.steps,  # sample, estimate, alloc, offsets, refine
             "integral": {"mean": g.result()["mean"], "sdev": g.result()["sdev"],
                          "exact": prob.exact}}
     if world == 1 and not args.no_cpu_baseline:

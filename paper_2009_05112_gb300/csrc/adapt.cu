@@ -1,6 +1,5 @@
 // adapt.cu -- the per-hypercube and per-axis kernels of one vegas+ iteration:
 //
-//   k_zero      clears the accumulators of the coming iteration;
 //   k_chunks    prefix of sample chunks over the integrals of a launch group
 //               (the sampling kernel's work queue);
 //   k_estimate  step a6 and the first half of a7: per hypercube
@@ -26,6 +25,7 @@
 //
 // The per-hypercube kernels are memory-bound streams over N_h elements; the
 // refinement is one CTA per (integral, axis) and latency-bound at N_g <= 4096.
+#include <cooperative_groups.h>
 #include <cstdio>
 
 #include "vp_internal.cuh"
@@ -42,30 +42,6 @@ __device__ __forceinline__ int owner_of(const uint32_t *base, int n, uint32_t bl
         else hi = mid;
     }
     return lo;
-}
-
-// ---------------------------------------------------------------------------
-// k_zero: S1, S2 (per hypercube) and the histograms of every integral.
-// grid: tree blocks of all integrals (tree_base); 256 threads.
-// ---------------------------------------------------------------------------
-__global__ void k_zero(const Desc *desc, const uint32_t *tree_base, int n_int) {
-    const int b = owner_of(tree_base, n_int, blockIdx.x);
-    const Desc &d = desc[b];
-    const uint32_t k = blockIdx.x - tree_base[b];
-    const uint64_t h0 = (uint64_t)k * kTreeBlock;
-    for (int i = threadIdx.x; i < kTreeBlock; i += blockDim.x) {
-        const uint64_t h = h0 + i;
-        if (h < d.n_hc) {
-            d.s1[h] = 0.0;
-            d.s2[h] = 0.0;
-        }
-    }
-    // histograms: spread over the integral's blocks
-    const int bins = d.dim * d.n_g;
-    for (int i = k * blockDim.x + threadIdx.x; i < bins; i += d.n_tree * blockDim.x) {
-        d.hsum[i] = 0.0;
-        d.hcnt[i] = 0u;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -105,128 +81,189 @@ __global__ void k_chunks(const Desc *desc, const uint32_t *members, int n_group,
     }
 }
 
-// ---------------------------------------------------------------------------
-// Fixed-order block reduction of three doubles over kTreeBlock = 1024 terms
-// with 512 threads: thread i first adds terms i and i + 512 (halving step
-// s = 512), then s = 256 ... 32 through shared memory, then s = 16 ... 1 with
-// shuffles (lane i receives lane i + s: the same pairing).  Result valid in
-// thread 0.
-// ---------------------------------------------------------------------------
 struct D3 { double a, b, c; };
 
-__device__ __forceinline__ D3 tree_reduce3(D3 v, double (*sh)[512]) {
-    const int t = threadIdx.x;
-    sh[0][t] = v.a;
-    sh[1][t] = v.b;
-    sh[2][t] = v.c;
-    __syncthreads();
-    for (int s = 256; s >= 32; s >>= 1) {
-        if (t < s) {
-            sh[0][t] = __dadd_rn(sh[0][t], sh[0][t + s]);
-            sh[1][t] = __dadd_rn(sh[1][t], sh[1][t + s]);
-            sh[2][t] = __dadd_rn(sh[2][t], sh[2][t + s]);
-        }
-        __syncthreads();
-    }
-    D3 r = {0.0, 0.0, 0.0};
-    if (t < 32) {
-        r.a = sh[0][t];
-        r.b = sh[1][t];
-        r.c = sh[2][t];
-        for (int s = 16; s >= 1; s >>= 1) {
-            const double oa = __shfl_down_sync(0xffffffffu, r.a, s);
-            const double ob = __shfl_down_sync(0xffffffffu, r.b, s);
-            const double oc = __shfl_down_sync(0xffffffffu, r.c, s);
-            r.a = __dadd_rn(r.a, oa);
-            r.b = __dadd_rn(r.b, ob);
-            r.c = __dadd_rn(r.c, oc);
-        }
-    }
-    return r;
+// floor(q) for 0 <= q < 2^52 without FP64 <-> integer conversions (slow on
+// this part): q + 2^52 rounded down holds floor(q) in its low mantissa bits.
+__device__ __forceinline__ double floor_pos(double q, uint64_t *iq) {
+    const double big = __dadd_rd(q, 4503599627370496.0);  // 2^52
+    *iq = (uint64_t)__double_as_longlong(big) & ((1ull << 52) - 1);
+    return big - 4503599627370496.0;
 }
 
-// d_h = sigma_h^beta; beta = 0 and 1 exactly.
+// d_h = sigma_h^beta; beta = 0 and 1 exactly; 1/2 and 3/4 (the paper's
+// default) through square roots, within an ulp or two of pow.
 __device__ __forceinline__ double damp(double sigma, double beta) {
     if (beta == 0.0) return 1.0;
     if (beta == 1.0) return sigma;
+    if (beta == 0.5) return sqrt(sigma);
+    if (beta == 0.75) return sqrt(sigma * sqrt(sigma));
     return pow(sigma, beta);
 }
 
 // ---------------------------------------------------------------------------
 // k_estimate.  mode 0: from the moments (a6 + sigma_h + d_h), records the
 // iteration; mode 1: dh[] holds sigma_h, turn it into d_h and sum; mode 2:
-// dh[] holds d_h, sum only.  grid: tree blocks of all integrals; 512 threads.
+// dh[] holds d_h, sum only.
+// A cluster of 4 CTAs (256 threads each) serves one block of 1024 hypercubes,
+// so the per-hypercube FP64 work (square roots, the damping power) spreads
+// over four SMs.  CTA q holds terms 256q .. 256q + 255; the fixed-order tree
+// runs its first two halving steps across the cluster through distributed
+// shared memory (s = 512: CTAs 2, 3 -> 0, 1; s = 256: CTA 1 -> 0) and the
+// rest in CTA 0.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_estimate(const Desc *desc, const uint32_t *tree_base,
-                                                  int n_int, int mode) {
-    __shared__ double sh[3][512];
-    __shared__ bool s_last;
-    const int b = owner_of(tree_base, n_int, blockIdx.x);
-    const Desc &d = desc[b];
-    const uint32_t k = blockIdx.x - tree_base[b];
-    const uint64_t h0 = (uint64_t)k * kTreeBlock;
-    const double om = d.omega, om2 = __dmul_rn(d.omega, d.omega);
+constexpr int kEstCtas = 4;
 
-    D3 acc = {0.0, 0.0, 0.0};
-    for (int half = 0; half < 2; ++half) {
-        const uint64_t h = h0 + threadIdx.x + half * 512;
-        D3 v = {0.0, 0.0, 0.0};
-        if (h < d.n_hc) {
-            if (mode == 0) {
-                const double n = (double)d.n_h[h];
-                const double s1 = d.s1[h], s2 = d.s2[h];
-                v.a = __dmul_rn(om, __ddiv_rn(s1, n));
-                const double m1 = __ddiv_rn(s1, n), m2 = __ddiv_rn(s2, n);
-                double var = __dsub_rn(m2, __dmul_rn(m1, m1));
-                var = var < 0.0 ? 0.0 : var;
-                v.b = __ddiv_rn(__dmul_rn(om2, var), __dsub_rn(n, 1.0));
-                const double sa = __dmul_rn(__ddiv_rn(om2, n), s2);
-                const double sb = __dmul_rn(__ddiv_rn(om, n), s1);
-                const double sv = __dsub_rn(sa, __dmul_rn(sb, sb));
-                const double sigma = sv > 0.0 ? sqrt(sv) : 0.0;
-                v.c = damp(sigma, d.beta);
-                d.dh[h] = v.c;
-            } else if (mode == 1) {
-                v.c = damp(d.dh[h], d.beta);
-                d.dh[h] = v.c;
-            } else {
-                v.c = d.dh[h];
-            }
-        }
-        if (half == 0) acc = v;
-        else {
-            acc.a = __dadd_rn(acc.a, v.a);  // the s = 512 halving step
-            acc.b = __dadd_rn(acc.b, v.b);
-            acc.c = __dadd_rn(acc.c, v.c);
+struct EstShared {
+    double own[3][256];
+    double recv[3][256];
+    double red[3][256];
+};
+
+__device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, uint32_t par) {
+    D3 v = {0.0, 0.0, 0.0};
+    if (h >= d.n_hc) return v;
+    if (mode == 0) {
+        // FP64 is scarce on this part: reciprocals of the (small, integer)
+        // n_h come from a table; one square root for sigma_h
+        const uint32_t nh = d.n_h[h];
+        const double inv_n = nh < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh) : 1.0 / (double)nh;
+        const double inv_n1 =
+            nh - 1 < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh - 1) : 1.0 / (double)(nh - 1);
+        const double om = d.omega;
+        const uint64_t ph = (uint64_t)par * d.n_hc + h;
+        const double m1 = d.s1[ph] * inv_n, m2 = d.s2[ph] * inv_n;
+        // the other buffer collects the next iteration's sums
+        const uint64_t qh = (uint64_t)(par ^ 1u) * d.n_hc + h;
+        d.s1[qh] = 0.0;
+        d.s2[qh] = 0.0;
+        double var = m2 - m1 * m1;
+        var = var < 0.0 ? 0.0 : var;
+        v.a = om * m1;
+        v.b = om * om * var * inv_n1;
+        v.c = damp(om * sqrt(var), d.beta);
+        d.dh[h] = v.c;
+    } else if (mode == 1) {
+        v.c = damp(d.dh[h], d.beta);
+        d.dh[h] = v.c;
+    } else {
+        v.c = d.dh[h];
+    }
+    return v;
+}
+
+__global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
+    k_estimate(const Desc *desc, const uint32_t *tree_base, int n_int, int mode) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ EstShared sm;
+    __shared__ bool s_last;
+    const int rank = (int)cl.block_rank();
+    const uint32_t tb = blockIdx.x / kEstCtas;
+    const int b = owner_of(tree_base, n_int, tb);
+    const Desc &d = desc[b];
+    const uint32_t k = tb - tree_base[b];
+    const int t = threadIdx.x;
+    const uint32_t par = d.st->t & 1u;  // buffer of the iteration being estimated
+    const D3 v = hcube_terms(d, (uint64_t)k * kTreeBlock + 256 * rank + t, mode, par);
+    if (mode == 0) {  // clear the other histogram buffer, spread over this integral's CTAs
+        const int bins = d.dim * d.n_g;
+        double *hs = d.hsum + (size_t)(par ^ 1u) * bins;
+        uint32_t *hc = d.hcnt + (size_t)(par ^ 1u) * bins;
+        const int stride = (int)d.n_tree * kEstCtas * 256;
+        for (int i = (int)(k * kEstCtas + rank) * 256 + t; i < bins; i += stride) {
+            hs[i] = 0.0;
+            hc[i] = 0u;
         }
     }
-    const D3 r = tree_reduce3(acc, sh);
-    if (threadIdx.x == 0) {
-        d.part[3 * k + 0] = r.a;
-        d.part[3 * k + 1] = r.b;
-        d.part[3 * k + 2] = r.c;
-        __threadfence();
-        const uint32_t ticket = atomicAdd(&d.st->done_est, 1u);
-        s_last = (ticket == d.n_tree - 1);
+    // s = 512: term t + 512 (CTA 2) joins term t (CTA 0); t + 768 (CTA 3) joins t + 256 (CTA 1)
+    if (rank >= 2) {
+        EstShared *dst = cl.map_shared_rank(&sm, rank - 2);
+        dst->recv[0][t] = v.a;
+        dst->recv[1][t] = v.b;
+        dst->recv[2][t] = v.c;
+    }
+    cl.sync();
+    D3 a = v;
+    if (rank < 2) {
+        a.a = __dadd_rn(v.a, sm.recv[0][t]);
+        a.b = __dadd_rn(v.b, sm.recv[1][t]);
+        a.c = __dadd_rn(v.c, sm.recv[2][t]);
+    }
+    cl.sync();  // CTA 0's recv buffer is free again
+    // s = 256: term t + 256 (CTA 1) joins term t (CTA 0)
+    if (rank == 1) {
+        EstShared *dst = cl.map_shared_rank(&sm, 0);
+        dst->recv[0][t] = a.a;
+        dst->recv[1][t] = a.b;
+        dst->recv[2][t] = a.c;
+    }
+    cl.sync();
+    if (rank != 0) return;
+    double *r0 = sm.red[0], *r1 = sm.red[1], *r2 = sm.red[2];
+    r0[t] = __dadd_rn(a.a, sm.recv[0][t]);
+    r1[t] = __dadd_rn(a.b, sm.recv[1][t]);
+    r2[t] = __dadd_rn(a.c, sm.recv[2][t]);
+    __syncthreads();
+    for (int s = 128; s >= 32; s >>= 1) {
+        if (t < s) {
+            r0[t] = __dadd_rn(r0[t], r0[t + s]);
+            r1[t] = __dadd_rn(r1[t], r1[t + s]);
+            r2[t] = __dadd_rn(r2[t], r2[t + s]);
+        }
+        __syncthreads();
+    }
+    if (t < 32) {
+        double x0 = r0[t], x1 = r1[t], x2 = r2[t];
+        for (int s = 16; s >= 1; s >>= 1) {
+            x0 = __dadd_rn(x0, __shfl_down_sync(0xffffffffu, x0, s));
+            x1 = __dadd_rn(x1, __shfl_down_sync(0xffffffffu, x1, s));
+            x2 = __dadd_rn(x2, __shfl_down_sync(0xffffffffu, x2, s));
+        }
+        if (t == 0) {
+            d.part[3 * k + 0] = x0;
+            d.part[3 * k + 1] = x1;
+            d.part[3 * k + 2] = x2;
+            __threadfence();
+            const uint32_t ticket = atomicAdd(&d.st->done_est, 1u);
+            s_last = (ticket == d.n_tree - 1);
+        }
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    // last block of this integral: block sums left to right
+    if (!s_last) return;
+    // last block of this integral: block sums left to right, staged through
+    // shared memory (loads in parallel; the three sums in three warps)
     __threadfence();
-    double I = 0.0, V = 0.0, Sd = 0.0;
-    for (uint32_t q = 0; q < d.n_tree; ++q) {
-        I = __dadd_rn(I, __ldcg(d.part + 3 * q + 0));
-        V = __dadd_rn(V, __ldcg(d.part + 3 * q + 1));
-        Sd = __dadd_rn(Sd, __ldcg(d.part + 3 * q + 2));
+    double acc = 0.0;
+    for (uint32_t q0 = 0; q0 < d.n_tree; q0 += 256) {
+        const uint32_t m = min(256u, d.n_tree - q0);
+        __syncthreads();
+        if ((uint32_t)t < m) {
+            r0[t] = __ldcg(d.part + 3 * (q0 + t) + 0);
+            r1[t] = __ldcg(d.part + 3 * (q0 + t) + 1);
+            r2[t] = __ldcg(d.part + 3 * (q0 + t) + 2);
+        }
+        __syncthreads();
+        if ((t & 31) == 0 && t < 96) {
+            const double *r = t == 0 ? r0 : (t == 32 ? r1 : r2);
+            for (uint32_t i = 0; i < m; ++i) acc = __dadd_rn(acc, r[i]);
+        }
     }
+    __syncthreads();
+    if (t == 32) r1[0] = acc;
+    if (t == 64) r2[0] = acc;
+    __syncthreads();
+    if (t != 0) return;
+    const double I = acc, V = r1[0], Sd = r2[0];
     State *st = d.st;
     st->done_est = 0u;
     st->sum_d = Sd;
+    st->inv_sum_d = Sd > 0.0 ? 1.0 / Sd : 0.0;
     if (mode == 0) {
-        const uint32_t t = st->t;
-        if (t < (uint32_t)d.hist_cap) {
-            d.hist_i[t] = I;
-            d.hist_var[t] = V;
+        const uint32_t tt = st->t;
+        if (tt < (uint32_t)d.hist_cap) {
+            d.hist_i[tt] = I;
+            d.hist_var[tt] = V;
         }
         st->last_i = I;
         st->last_var = V;
@@ -239,7 +276,7 @@ __global__ void __launch_bounds__(512) k_estimate(const Desc *desc, const uint32
             e = e > 120 ? 120 : (e < -120 ? -120 : e);
             st->scale_exp = -e;
         }
-        st->t = t + 1;
+        st->t = tt + 1;
     }
 }
 
@@ -258,23 +295,40 @@ __global__ void __launch_bounds__(256) k_alloc(const Desc *desc, const uint32_t 
     const uint32_t k = blockIdx.x - tree_base[b];
     const uint64_t h0 = (uint64_t)k * kTreeBlock;
     const double sum_d = d.st->sum_d;
+    const double inv_sum = d.st->inv_sum_d;
     if (!isfinite(sum_d)) {
         if (threadIdx.x == 0 && k == 0) d.st->status |= kStatusNonFinite;
         return;
     }
     if (threadIdx.x == 0) s_sum = 0ull;
     __syncthreads();
+    const double n_ev_d = (double)d.n_ev;
     unsigned long long mine = 0;
     for (int i = threadIdx.x; i < kTreeBlock; i += blockDim.x) {
         const uint64_t h = h0 + i;
         if (h >= d.n_hc) break;
         double q;
-        if (sum_d > 0.0) q = __ddiv_rn(__dmul_rn((double)d.n_ev, d.dh[h]), sum_d);
-        else q = __ddiv_rn((double)d.n_ev, (double)d.n_hc);
-        const double fl = floor(q);
+        uint64_t iq;
+        if (sum_d > 0.0) {
+            // the IEEE quotient (N_ev d_h)/sum_d decides n_h; a multiply by the
+            // reciprocal is within 4e-16 q of it, so only quotients that close
+            // to an integer need the division itself
+            const double num = __dmul_rn(n_ev_d, d.dh[h]);
+            q = num * inv_sum;
+            const double fl = floor_pos(q, &iq);
+            const double tol = 1e-14 * q;
+            // (a zero numerator is exact; below 2 - tol the max(2, .) decides)
+            if (num > 0.0 && (d.plus2 || q > 1.5) && (q - fl <= tol || fl + 1.0 - q <= tol)) {
+                q = __ddiv_rn(num, sum_d);
+                floor_pos(q, &iq);
+            }
+        } else {
+            q = __ddiv_rn(n_ev_d, (double)d.n_hc);
+            floor_pos(q, &iq);
+        }
         uint32_t n;
-        if (d.plus2 && !initial) n = (uint32_t)fl + 2u;
-        else n = fl > 2.0 ? (uint32_t)fl : 2u;
+        if (d.plus2 && !initial) n = (uint32_t)iq + 2u;
+        else n = iq > 2u ? (uint32_t)iq : 2u;
         d.n_h[h] = n;
         mine += n;
     }
@@ -288,17 +342,37 @@ __global__ void __launch_bounds__(256) k_alloc(const Desc *desc, const uint32_t 
         s_last = (ticket == d.n_tree - 1);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
+    // last block: exclusive scan of the block sums (integers: any order is exact)
     __threadfence();
-    uint64_t run = 0;
-    for (uint32_t q = 0; q < d.n_tree; ++q) {
-        const uint64_t v = __ldcg(d.bsum + q);
-        d.bsum[q] = run;
-        run += v;
+    __shared__ unsigned long long s_w[8];
+    __shared__ unsigned long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0ull;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t q0 = 0; q0 < d.n_tree; q0 += blockDim.x) {
+        const uint32_t q = q0 + threadIdx.x;
+        const unsigned long long v = q < d.n_tree ? __ldcg(d.bsum + q) : 0ull;
+        unsigned long long inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        __syncthreads();
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        unsigned long long base = s_carry;
+        for (int w = 0; w < warp; ++w) base += s_w[w];
+        if (q < d.n_tree) d.bsum[q] = base + inc - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = base + inc;
     }
-    d.off[d.n_hc] = run;
-    d.st->n_samples = run;
-    d.st->done_alloc = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long run = s_carry;
+        d.off[d.n_hc] = run;
+        d.st->n_samples = run;
+        d.st->done_alloc = 0u;
+    }
 }
 
 // k_offsets: off[h] = bsum[block] + exclusive scan of n_h within the block.
@@ -310,12 +384,13 @@ __global__ void __launch_bounds__(256) k_offsets(const Desc *desc, const uint32_
     if (!isfinite(d.st->sum_d)) return;
     const uint32_t k = blockIdx.x - tree_base[b];
     const uint64_t h0 = (uint64_t)k * kTreeBlock + (uint64_t)threadIdx.x * 4;
+    const uint64_t n_hc = d.n_hc;
     // 4 consecutive hypercubes per thread
     uint32_t n[4];
     unsigned long long tot = 0;
     for (int i = 0; i < 4; ++i) {
         const uint64_t h = h0 + i;
-        n[i] = h < d.n_hc ? d.n_h[h] : 0u;
+        n[i] = h < n_hc ? d.n_h[h] : 0u;
         tot += n[i];
     }
     // exclusive scan of tot over the block
@@ -332,120 +407,183 @@ __global__ void __launch_bounds__(256) k_offsets(const Desc *desc, const uint32_
     unsigned long long run = d.bsum[k] + wbase + inc - tot;
     for (int i = 0; i < 4; ++i) {
         const uint64_t h = h0 + i;
-        if (h < d.n_hc) d.off[h] = run;
+        if (h < n_hc) d.off[h] = run;
         run += n[i];
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_refine: a8 for one (integral, axis); 256 threads; N_g <= 4096.
-// Shared: x[N_g + 1], dd[N_g] (raw d, then compressed), C[N_g + 1].
+// k_refine: a8 for one (integral, axis) on a cluster of kRefineCtas CTAs.
+// CTA r of the cluster owns increments [r S, (r + 1) S), S = ceil(N_g / 8);
+// the FP64 work (d_i, smoothing, log and root of the compression) is spread
+// over the cluster, and the CTAs exchange the partial sums they need through
+// distributed shared memory:
+//   1. d_i for the owned range plus one halo increment each side; partial sum
+//   2. sum_i d_i = the 8 partials in rank order (identical in every CTA)
+//   3. smoothing, normalisation, compression; local inclusive scan
+//   4. cumulative base of every CTA = the totals of lower ranks
+//   5. new edge k (for k in the owned range) where the cumulative reaches
+//      k sum(c)/N_g: the owning rank is found from the totals, then a binary
+//      search in that rank's local scan, read remotely
+//   6. edges and the FP32 table {x_i, dx_i} written back.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_refine(const Desc *desc, const uint32_t *axis_base,
-                                                int n_int) {
-    extern __shared__ double rsm[];
-    __shared__ double s_red[256];
-    __shared__ double s_scan[256];
-    const int b = owner_of(axis_base, n_int, blockIdx.x);
-    const Desc &d = desc[b];
-    const int mu = blockIdx.x - axis_base[b];
-    const int n_g = d.n_g;
-    if (d.alpha == 0.0 || n_g < 2) return;
-    double *x = rsm;
-    double *dd = rsm + (n_g + 1);
-    double *C = dd + n_g;
-    double *edges = d.edges + (size_t)mu * (size_t)(n_g + 1);
-    const double *hs = d.hsum + (size_t)mu * n_g;
-    const uint32_t *hc = d.hcnt + (size_t)mu * n_g;
-    const int t = threadIdx.x, nt = blockDim.x;
+constexpr int kRefineCtas = 8;
+constexpr int kRefineThreads = 128;
+constexpr int kRefineSlice = kMaxNg / kRefineCtas;  // 512
 
+struct RefineShared {
+    double x[kRefineSlice + 1];   // old edges x_{i0} .. x_{i0 + S}
+    double d[kRefineSlice + 2];   // raw d_{i0 - 1} .. d_{i0 + S}
+    double c[kRefineSlice];       // compressed d of the owned increments
+    double C[kRefineSlice];       // local inclusive scan of c
+    double xn[kRefineSlice + 1];  // new edges of the owned range (and one more)
+    double red[kRefineThreads / 32];
+    double part;                  // sum of own raw d
+    double tot;                   // sum of own c
+    int n_own;
+};
+
+__global__ void __cluster_dims__(kRefineCtas, 1, 1) __launch_bounds__(kRefineThreads)
+    k_refine(const Desc *desc, const uint32_t *axis_base, int n_int) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ RefineShared sm;
+    const int rank = (int)cl.block_rank();
+    const uint32_t axis_id = blockIdx.x / kRefineCtas;
+    const int b = owner_of(axis_base, n_int, axis_id);
+    const Desc &d = desc[b];
+    const int mu = (int)(axis_id - axis_base[b]);
+    const int n_g = d.n_g;
+    if (d.alpha == 0.0 || n_g < 2) return;  // uniform over the cluster
+    const int S = (n_g + kRefineCtas - 1) / kRefineCtas;
+    const int i0 = min(rank * S, n_g), i1 = min(i0 + S, n_g);
+    const int t = threadIdx.x, nt = blockDim.x;
+    double *edges = d.edges + (size_t)mu * (size_t)(n_g + 1);
+    // histograms of the latest iteration (double-buffered by iteration parity)
+    const size_t hb = (size_t)((d.st->t - 1u) & 1u) * (size_t)d.dim * n_g;
+    const double *hs = d.hsum + hb + (size_t)mu * n_g;
+    const uint32_t *hc = d.hcnt + hb + (size_t)mu * n_g;
+
+    // 1. old edges and raw d (with halo)
+    for (int i = i0 + t; i <= i1; i += nt) sm.x[i - i0] = edges[i];
     double part = 0.0;
-    for (int i = t; i <= n_g; i += nt) x[i] = edges[i];
-    for (int i = t; i < n_g; i += nt) {
-        const uint32_t c = hc[i];
-        const double v = c ? __ddiv_rn(hs[i], (double)c) : 0.0;
-        dd[i] = v;
-        part += v;
+    for (int i = i0 - 1 + t; i <= i1; i += nt) {
+        double v = 0.0;
+        if (i >= 0 && i < n_g) {
+            const uint32_t c = hc[i];
+            v = c ? hs[i] / (double)c : 0.0;
+        }
+        sm.d[i - (i0 - 1)] = v;
+        if (i >= i0 && i < i1) part += v;
     }
-    s_red[t] = part;
+    for (int o = 16; o >= 1; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((t & 31) == 0) sm.red[t >> 5] = part;
     __syncthreads();
-    for (int s = nt / 2; s >= 1; s >>= 1) {
-        if (t < s) s_red[t] += s_red[t + s];
-        __syncthreads();
+    if (t == 0) {
+        double p = 0.0;
+        for (int w = 0; w < nt / 32; ++w) p += sm.red[w];
+        sm.part = p;
+        sm.n_own = i1 - i0;
     }
-    const double sum_d = s_red[0];
-    if (!(sum_d > 0.0) || !isfinite(sum_d)) return;  // nothing to refine (reading)
-    // smoothing, normalisation, compression; each thread owns a contiguous segment
-    const int seg = (n_g + nt - 1) / nt;
-    const int i0 = t * seg, i1 = min(i0 + seg, n_g);
-    double cval[16];
+    cl.sync();
+    // 2. the axis total, in rank order
+    double sum_d = 0.0;
+    for (int q = 0; q < kRefineCtas; ++q) sum_d += *cl.map_shared_rank(&sm.part, q);
+    if (!(sum_d > 0.0) || !isfinite(sum_d)) {  // nothing to refine (reading); uniform
+        cl.sync();
+        return;
+    }
+    const double inv_sum = 1.0 / sum_d;
+    // 3. smoothing, normalisation, compression; contiguous quarter-slices per thread
+    const int n_own = i1 - i0;
+    const int per = (n_own + nt - 1) / nt;
+    const int a0 = min(t * per, n_own), a1 = min(a0 + per, n_own);
     double local = 0.0;
-    for (int i = i0; i < i1; ++i) {
+    for (int a = a0; a < a1; ++a) {
+        const int i = i0 + a;
+        const double dm = sm.d[a], d0 = sm.d[a + 1], dp = sm.d[a + 2];
         double s;
-        if (i == 0) s = (7.0 * dd[0] + dd[1]) / 8.0;
-        else if (i == n_g - 1) s = (dd[n_g - 2] + 7.0 * dd[n_g - 1]) / 8.0;
-        else s = (dd[i - 1] + 6.0 * dd[i] + dd[i + 1]) / 8.0;
-        s = s / sum_d;
+        if (i == 0) s = (7.0 * d0 + dp) * 0.125;
+        else if (i == n_g - 1) s = (dm + 7.0 * d0) * 0.125;
+        else s = (dm + 6.0 * d0 + dp) * 0.125;
+        s = s * inv_sum;
         // reading: an unsampled increment keeps the weight of the smallest
         // normal double (the alpha -> 0 limit stays "no refinement")
         if (s <= 0.0) s = 2.2250738585072014e-308;
-        double c;
-        if (s == 1.0) c = 1.0;
-        else c = pow((1.0 - s) / log(1.0 / s), d.alpha);
-        cval[i - i0] = c;
-        local += c;
+        double cv;
+        if (s == 1.0) cv = 1.0;
+        else {
+            const double r = (1.0 - s) / -log(s);
+            cv = d.alpha == 1.0 ? r : (d.alpha == 0.5 ? sqrt(r) : pow(r, d.alpha));
+        }
+        sm.c[a] = cv;
+        local += cv;
+        sm.C[a] = local;  // thread-local inclusive prefix, fixed below
     }
-    __syncthreads();  // every read of the raw d is done
-    for (int i = i0; i < i1; ++i) dd[i] = cval[i - i0];
-    // inclusive scan of the thread totals (Hillis-Steele over 256 values)
-    s_scan[t] = local;
-    __syncthreads();
-    for (int s = 1; s < nt; s <<= 1) {
-        const double o = t >= s ? s_scan[t - s] : 0.0;
-        __syncthreads();
-        s_scan[t] += o;
-        __syncthreads();
-    }
-    double run = s_scan[t] - local;  // exclusive prefix of this segment
-    if (t == 0) C[0] = 0.0;
-    for (int i = i0; i < i1; ++i) {
-        run += dd[i];
-        C[i + 1] = run;
+    // exclusive prefix of the thread totals (warp shuffles, then warps)
+    double inc = local;
+    const int lane = t & 31, w = t >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
     }
     __syncthreads();
-    const double total = C[n_g];
+    if (lane == 31) sm.red[w] = inc;
+    __syncthreads();
+    double wbase = 0.0;
+    for (int q = 0; q < w; ++q) wbase += sm.red[q];
+    const double tbase = wbase + inc - local;
+    for (int a = a0; a < a1; ++a) sm.C[a] += tbase;
+    __syncthreads();
+    if (t == 0) sm.tot = n_own > 0 ? sm.C[n_own - 1] : 0.0;
+    cl.sync();
+    // 4. bases of every rank and the axis total of c
+    double base[kRefineCtas];
+    double total = 0.0;
+    for (int q = 0; q < kRefineCtas; ++q) {
+        base[q] = total;
+        total += *cl.map_shared_rank(&sm.tot, q);
+    }
     const double delta_d = total / (double)n_g;
-    for (int k = 1 + t; k < n_g; k += nt) {
+    // 5. new edges k in [max(i0, 1), min(i1, n_g - 1)]
+    for (int k = max(i0, 1) + t; k < min(i1, n_g); k += nt) {
         const double target = (double)k * delta_d;
-        int lo = 0, hi = n_g;  // C[lo] < target <= C[hi]
+        int q = 0;
+        while (q < kRefineCtas - 1 && base[q + 1] < target) ++q;
+        // rank q holds the crossing: smallest m with base[q] + C_q[m] >= target
+        const RefineShared *rs = cl.map_shared_rank(&sm, q);
+        const int nq = rs->n_own;
+        int lo = -1, hi = nq - 1;  // base + C[hi] >= target (the last one is, up to rounding)
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (C[mid] < target) lo = mid;
+            if (base[q] + rs->C[mid] < target) lo = mid;
             else hi = mid;
         }
-        const int j = hi;
-        const double dj = dd[j - 1];
-        const double xn = dj > 0.0 ? x[j] - ((C[j] - target) / dj) * (x[j] - x[j - 1]) : x[j];
-        edges[k] = xn;
+        // cumulative at the right end of increment j - 1 = q S + hi
+        const double Cj = base[q] + rs->C[hi];
+        const double cj = rs->c[hi];
+        const double xr = rs->x[hi + 1], xl = rs->x[hi];
+        sm.xn[k - i0] = cj > 0.0 ? xr - ((Cj - target) / cj) * (xr - xl) : xr;
     }
-    __syncthreads();
-    // FP32 mirror {x_i, dx_i}
-    float2 *tab = d.tab + (size_t)mu * n_g;
-    for (int i = t; i < n_g; i += nt) {
-        const double e0 = __ldcg(edges + i), e1 = __ldcg(edges + i + 1);
-        tab[i] = make_float2((float)e0, (float)(e1 - e0));
+    if (t == 0) {
+        if (i0 == 0) sm.xn[0] = sm.x[0];
+        if (i1 == n_g && n_own > 0) sm.xn[n_own] = sm.x[n_own];
     }
+    cl.sync();
+    // 6. write back edges and the FP32 table; x'_{i1} comes from rank + 1
+    for (int i = i0 + t; i < i1; i += nt) {
+        const double xi = sm.xn[i - i0];
+        const double xe = (i + 1 < i1 || i1 == n_g) ? sm.xn[i + 1 - i0]
+                                                      : cl.map_shared_rank(&sm, rank + 1)->xn[0];
+        if (i > 0) edges[i] = xi;
+        d.tab[(size_t)mu * n_g + i] = make_float2((float)xi, (float)(xe - xi));
+    }
+    cl.sync();  // keep this CTA's shared memory alive until every remote read is done
 }
 
 // ---------------------------------------------------------------------------
 // Host-side launchers.
 // ---------------------------------------------------------------------------
-cudaError_t launch_zero(const Desc *desc, const uint32_t *tree_base, int n_int,
-                        uint32_t n_blocks, cudaStream_t s) {
-    k_zero<<<n_blocks, 256, 0, s>>>(desc, tree_base, n_int);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_chunks(const Desc *desc, const uint32_t *members, int n_group,
                           uint64_t *chunk_base, uint32_t *head, uint32_t C, cudaStream_t s) {
     k_chunks<<<1, 1024, 0, s>>>(desc, members, n_group, chunk_base, head, C);
@@ -454,7 +592,7 @@ cudaError_t launch_chunks(const Desc *desc, const uint32_t *members, int n_group
 
 cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_int,
                             uint32_t n_blocks, int mode, cudaStream_t s) {
-    k_estimate<<<n_blocks, 512, 0, s>>>(desc, tree_base, n_int, mode);
+    k_estimate<<<n_blocks * kEstCtas, 256, 0, s>>>(desc, tree_base, n_int, mode);
     return cudaGetLastError();
 }
 
@@ -468,16 +606,9 @@ cudaError_t launch_alloc(const Desc *desc, const uint32_t *tree_base, int n_int,
 }
 
 cudaError_t launch_refine(const Desc *desc, const uint32_t *axis_base, int n_int,
-                          uint32_t n_blocks, int max_ng, cudaStream_t s) {
-    const size_t smem = (size_t)(3 * max_ng + 2) * sizeof(double);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((3 * kMaxNg + 2) * sizeof(double)));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    k_refine<<<n_blocks, 256, smem, s>>>(desc, axis_base, n_int);
+                          uint32_t n_axes, int max_ng, cudaStream_t s) {
+    (void)max_ng;
+    k_refine<<<n_axes * kRefineCtas, kRefineThreads, 0, s>>>(desc, axis_base, n_int);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,6 @@
 #include "vp_internal.cuh"
 
 namespace vp {
-cudaError_t launch_zero(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t);
 cudaError_t launch_chunks(const Desc *, const uint32_t *, int, uint64_t *, uint32_t *, uint32_t,
                           cudaStream_t);
 cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
@@ -124,16 +123,19 @@ struct Member {
     uint32_t n_tree;
     int hist_cap;
     int bucket;
+    bool exact;            // dim equals the bucket's dimension
     size_t off_bytes[20];  // offsets of the buffers within the arena
 };
 
 struct Group {
     int bucket, kind, prec;
+    bool exact;
     std::vector<uint32_t> members;
     uint32_t *d_members = nullptr;
     uint64_t *d_chunk_base = nullptr;
-    uint32_t *d_head = nullptr;
-    int threads = 256, R = 1, blocks = 1, hist_shared = 0, hist_words = 0, prm_words = 0;
+    uint32_t *d_head = nullptr;      // d_head[0] queue head, d_head[1] exit counter
+    int threads = 256, r = 8, blocks = 1, hist_shared = 0, hist_words = 0, prm_words = 0;
+    uint32_t task = 0;
     size_t smem = 0;
 };
 
@@ -161,11 +163,23 @@ struct vp_ctx {
 };
 
 static int bucket_of(int dim) {
-    if (dim <= 4) return 0;
-    if (dim <= 8) return 1;
-    if (dim <= 12) return 2;
-    if (dim <= 16) return 3;
-    return 4;
+    for (int b = 0; b < kNumBuckets; ++b)
+        if (dim <= bucket_dim(b)) return b;
+    return kNumBuckets - 1;
+}
+
+// Granlund-Montgomery constants for division by d (32-bit, round-up variant).
+static void div_magic(uint32_t d, uint32_t *magic, int *shift) {
+    if (d <= 1) {
+        *magic = 0;
+        *shift = 0;
+        return;
+    }
+    int l = 0;
+    while ((1ull << l) < d) ++l;  // ceil(log2 d)
+    const unsigned __int128 num = ((unsigned __int128)1 << 32) * (((unsigned __int128)1 << l) - d);
+    *magic = (uint32_t)(num / d + 1);
+    *shift = l;
 }
 
 // floor((N_ev/4)^(1/D)) as the largest n >= 1 with 4 n^D <= N_ev.
@@ -251,6 +265,7 @@ static vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb)
     mb.n_tree = (uint32_t)((nh + kTreeBlock - 1) / kTreeBlock);
     mb.hist_cap = p->max_it > 0 ? p->max_it : 1024;
     mb.bucket = bucket_of(D);
+    mb.exact = (D == bucket_dim(mb.bucket));
     // FP32 integrand constants
     const double L2E = 1.4426950408889634074;
     mb.prm32.clear();
@@ -296,9 +311,9 @@ enum {
 static size_t member_layout(Member &mb, size_t base) {
     const size_t D = mb.p.dim, G = mb.p.n_g, H = mb.n_hc, T = mb.n_tree, C = mb.hist_cap;
     const size_t sz[B_COUNT] = {D * (G + 1) * 8, D * G * 8, mb.prm.size() * 8,
-                                mb.prm32.size() * 4, H * 4, (H + 1) * 8, H * 8, H * 8, H * 8,
-                                D * G * 8, D * G * 4, T * 3 * 8, T * 8, C * 8, C * 8,
-                                sizeof(State)};
+                                mb.prm32.size() * 4, H * 4, (H + 1) * 8, 2 * H * 8, 2 * H * 8,
+                                H * 8, 2 * D * G * 8, 2 * D * G * 4, T * 3 * 8, T * 8, C * 8,
+                                C * 8, sizeof(State)};
     for (int i = 0; i < B_COUNT; ++i) {
         mb.off_bytes[i] = base;
         base = align256(base + sz[i]);
@@ -317,16 +332,20 @@ static void make_tab(const double *e, int n_g, float2 *tab) {
 }
 
 static vp_status plan_groups(Set &s) {
-    // one launch group per (bucket, kind, precision)
+    // one launch group per (bucket, exactness, kind, precision)
     for (uint32_t i = 0; i < s.m.size(); ++i) {
         const Member &mb = s.m[i];
+        const bool exact = mb.exact && mb.p.precision == VP_FP32;  // FP64 kernels are guarded
         Group *g = nullptr;
         for (auto &q : s.groups)
-            if (q.bucket == mb.bucket && q.kind == mb.kind && q.prec == mb.p.precision) g = &q;
+            if (q.bucket == mb.bucket && q.exact == exact && q.kind == mb.kind &&
+                q.prec == mb.p.precision)
+                g = &q;
         if (!g) {
             s.groups.push_back(Group());
             g = &s.groups.back();
             g->bucket = mb.bucket;
+            g->exact = exact;
             g->kind = mb.kind;
             g->prec = mb.p.precision;
         }
@@ -340,31 +359,35 @@ static vp_status plan_groups(Set &s) {
             max_bins = std::max(max_bins, s.m[i].p.dim * s.m[i].p.n_g);
             max_words = std::max(max_words, (int)s.m[i].prm32.size());
         }
+        // big integrals first: tasks of later members fill the tail
+        std::stable_sort(g.members.begin(), g.members.end(), [&](uint32_t a, uint32_t b) {
+            return s.m[a].p.n_ev > s.m[b].p.n_ev;
+        });
         const size_t tbytes = g.prec == VP_FP64 ? 8 : 4;
         const size_t hist_bytes = (size_t)max_bins * (tbytes + 4);
         g.threads = 256;
+        g.r = 8;
         g.hist_words = max_bins;
         g.prm_words = g.prec == VP_FP64 ? 0 : ((max_words + 3) & ~3);
         const size_t prm_bytes = (size_t)g.prm_words * 4;
-        const int occ_probe = g.prec == VP_FP64
-                                  ? sample_occupancy_f64(g.bucket, g.kind, g.threads, 0)
-                                  : sample_occupancy_f32(g.bucket, g.kind, g.threads, 0);
-        const double per_cta = expect / std::max(1, s.n_sm * std::max(1, occ_probe));
-        (void)per_cta;
         g.hist_shared = (hist_bytes + prm_bytes <= 112 * 1024) ? 1 : 0;
         g.smem = prm_bytes + (g.hist_shared ? hist_bytes : 0);
         if (g.smem > 48 * 1024) {
             cudaError_t e = g.prec == VP_FP64
-                                ? sample_smem_config_f64(g.bucket, g.kind, (int)g.smem)
-                                : sample_smem_config_f32(g.bucket, g.kind, (int)g.smem);
+                                ? sample_smem_config_f64(g.bucket, g.exact, g.kind, (int)g.smem)
+                                : sample_smem_config_f32(g.bucket, g.exact, g.kind, (int)g.smem);
             if (e != cudaSuccess) return fail(VP_ECUDA, "smem config: %s", cudaGetErrorString(e));
         }
-        int occ = g.prec == VP_FP64 ? sample_occupancy_f64(g.bucket, g.kind, g.threads, g.smem)
-                                    : sample_occupancy_f32(g.bucket, g.kind, g.threads, g.smem);
+        int occ = g.prec == VP_FP64
+                      ? sample_occupancy_f64(g.bucket, g.exact, g.kind, g.threads, g.smem)
+                      : sample_occupancy_f32(g.bucket, g.exact, g.kind, g.threads, g.smem);
         if (occ < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem);
         g.blocks = s.n_sm * occ;
-        const double per_thread = expect / ((double)g.blocks * g.threads * 4.0);
-        g.R = (int)std::min(64.0, std::max(1.0, std::ceil(per_thread)));
+        // several integrals: tasks of ~1/8 of a CTA's share, whole warp chunks
+        const uint32_t wchunk = 32u * (uint32_t)g.r;
+        const double per = expect / ((double)g.blocks * 8.0);
+        uint32_t task = (uint32_t)std::min(1.0e9, std::max((double)(8 * wchunk), per));
+        g.task = (task + wchunk - 1) / wchunk * wchunk;
     }
     return VP_OK;
 }
@@ -389,6 +412,8 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
     base = align256(base + (n + 1) * 4);
     const size_t axis_off = base;
     base = align256(base + (n + 1) * 4);
+    const size_t inv_off = base;
+    base = align256(base + kInvTab * sizeof(double));
     {
         vp_status pst = plan_groups(s);
         if (pst != VP_OK) return pst;
@@ -409,6 +434,14 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
     s.d_desc = (Desc *)(A + desc_off);
     s.d_tree_base = (uint32_t *)(A + tree_off);
     s.d_axis_base = (uint32_t *)(A + axis_off);
+    const double *d_inv = (const double *)(A + inv_off);
+    {
+        std::vector<double> inv(kInvTab, 0.0);
+        for (int k = 1; k < kInvTab; ++k) inv[k] = 1.0 / (double)k;  // IEEE division on the host
+        CU(cudaMemcpyAsync((void *)d_inv, inv.data(), kInvTab * sizeof(double), cudaMemcpyHostToDevice,
+                           stream));
+        CU(cudaStreamSynchronize(stream));
+    }
     for (size_t g = 0; g < s.groups.size(); ++g) {
         s.groups[g].d_members = (uint32_t *)(A + gmem_off[3 * g]);
         s.groups[g].d_chunk_base = (uint64_t *)(A + gmem_off[3 * g + 1]);
@@ -449,6 +482,8 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
             d.ngD_m = (float)(2.0 * m);
             d.ngD_e = e - 1;
         }
+        div_magic((uint32_t)mb.n_st, &d.nst_magic, &d.nst_shift);
+        d.inv_tab = d_inv;
         d.edges = at<double>(s, mb, B_EDGES);
         d.tab = at<float2>(s, mb, B_TAB);
         d.prm = at<double>(s, mb, B_PRM);
@@ -526,11 +561,11 @@ static void set_destroy(Set &s) {
 
 static vp_status set_iterate(Set &s, cudaStream_t stream) {
     const int n = (int)s.m.size();
-    CU(launch_zero(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream));
     for (size_t gi = 0; gi < s.groups.size(); ++gi) {
         Group &g = s.groups[gi];
-        CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base, g.d_head,
-                         (uint32_t)(g.threads * g.R), stream));
+        if (g.members.size() > 1)  // the task prefix (one integral needs none)
+            CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base,
+                             g.d_head, g.task, stream));
     }
     // inside the step graph's capture the events must be external record nodes
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -544,14 +579,16 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
         a.members = g.d_members;
         a.chunk_base = g.d_chunk_base;
         a.head = g.d_head;
+        a.exit_count = g.d_head + 1;
         a.n_group = (int)g.members.size();
-        a.R = g.R;
+        a.r = g.r;
+        a.task = g.task;
         a.hist_shared = g.hist_shared;
         a.hist_words = g.hist_words;
         a.prm_words = g.prm_words;
         cudaError_t e = g.prec == VP_FP64
-                            ? launch_sample_f64(g.bucket, g.kind, g.blocks, g.threads, g.smem, stream, a)
-                            : launch_sample_f32(g.bucket, g.kind, g.blocks, g.threads, g.smem, stream, a);
+                            ? launch_sample_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a)
+                            : launch_sample_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a);
         if (e != cudaSuccess) return fail(VP_ECUDA, "sampling launch: %s", cudaGetErrorString(e));
     }
     CU(cudaEventRecordWithFlags(s.ev1, stream, ev_flags));
@@ -751,12 +788,23 @@ extern "C" vp_status vp_get_alloc(vp_ctx *c, uint32_t *n_h, uint64_t *offsets) {
     return VP_OK;
 }
 
+// Buffer parity of the latest iteration ((t - 1) & 1); synchronises.
+static vp_status latest_parity(Set &s, size_t *par) {
+    CU(cudaStreamSynchronize(s.last));
+    State st;
+    CU(cudaMemcpy(&st, s.h_desc[0].st, sizeof st, cudaMemcpyDeviceToHost));
+    *par = (size_t)((st.t - 1u) & 1u);
+    return VP_OK;
+}
+
 extern "C" vp_status vp_get_moments(vp_ctx *c, double *s1, double *s2) {
     CHECK_CTX(c);
     const Desc &d = c->set.h_desc[0];
-    CU(cudaStreamSynchronize(c->set.last));
-    if (s1) CU(cudaMemcpy(s1, d.s1, d.n_hc * 8, cudaMemcpyDeviceToHost));
-    if (s2) CU(cudaMemcpy(s2, d.s2, d.n_hc * 8, cudaMemcpyDeviceToHost));
+    size_t par = 0;
+    vp_status st = latest_parity(c->set, &par);
+    if (st != VP_OK) return st;
+    if (s1) CU(cudaMemcpy(s1, d.s1 + par * d.n_hc, d.n_hc * 8, cudaMemcpyDeviceToHost));
+    if (s2) CU(cudaMemcpy(s2, d.s2 + par * d.n_hc, d.n_hc * 8, cudaMemcpyDeviceToHost));
     return VP_OK;
 }
 
@@ -764,11 +812,13 @@ extern "C" vp_status vp_get_hist(vp_ctx *c, double *hsum, double *hcnt) {
     CHECK_CTX(c);
     const Desc &d = c->set.h_desc[0];
     const size_t bins = (size_t)d.dim * d.n_g;
-    CU(cudaStreamSynchronize(c->set.last));
-    if (hsum) CU(cudaMemcpy(hsum, d.hsum, bins * 8, cudaMemcpyDeviceToHost));
+    size_t par = 0;
+    vp_status st = latest_parity(c->set, &par);
+    if (st != VP_OK) return st;
+    if (hsum) CU(cudaMemcpy(hsum, d.hsum + par * bins, bins * 8, cudaMemcpyDeviceToHost));
     if (hcnt) {
         std::vector<uint32_t> tmp(bins);
-        CU(cudaMemcpy(tmp.data(), d.hcnt, bins * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(tmp.data(), d.hcnt + par * bins, bins * 4, cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < bins; ++i) hcnt[i] = (double)tmp[i];
     }
     return VP_OK;
@@ -822,9 +872,12 @@ extern "C" vp_status vp_refine_from_hist(vp_ctx *c, const double *hsum, const do
         if (!std::isfinite(hsum[i]) || hsum[i] < 0.0) return fail(VP_EINVAL, "sums must be finite and >= 0");
         cnt[i] = (uint32_t)hcnt[i];
     }
-    CU(cudaStreamSynchronize(s.last));
-    CU(cudaMemcpyAsync(d.hsum, hsum, bins * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
-    CU(cudaMemcpyAsync(d.hcnt, cnt.data(), bins * 4, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    size_t par = 0;  // the refinement reads the latest iteration's buffer
+    vp_status pst = latest_parity(s, &par);
+    if (pst != VP_OK) return pst;
+    CU(cudaMemcpyAsync(d.hsum + par * bins, hsum, bins * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CU(cudaMemcpyAsync(d.hcnt + par * bins, cnt.data(), bins * 4, cudaMemcpyHostToDevice,
+                       (cudaStream_t)stream));
     CU(launch_refine(s.d_desc, s.d_axis_base, 1, s.n_axis_total, s.max_ng, (cudaStream_t)stream));
     CU(cudaStreamSynchronize((cudaStream_t)stream));
     s.last = (cudaStream_t)stream;
@@ -864,9 +917,10 @@ extern "C" vp_status vp_eval_samples(vp_ctx *c, int64_t n, const uint64_t *h, co
     if (e == cudaSuccess) e = cudaMemcpyAsync(dj, j, n * 4, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
         e = d.prec == VP_FP64
-                ? launch_eval_f64(s.m[0].bucket, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di, djac, df, 0)
-                : launch_eval_f32(s.m[0].bucket, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di, djac, df,
-                                  (int)((s.m[0].prm32.size() + 3) & ~(size_t)3));
+                ? launch_eval_f64(s.m[0].bucket, false, d.kind, stream, s.d_desc, 0, n, dh_, dj, t, dx, di,
+                                  djac, df, 0)
+                : launch_eval_f32(s.m[0].bucket, s.m[0].exact, d.kind, stream, s.d_desc, 0, n, dh_, dj, t,
+                                  dx, di, djac, df, (int)((s.m[0].prm32.size() + 3) & ~(size_t)3));
     if (e == cudaSuccess) e = cudaMemcpyAsync(x, dx, n * D * 8, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, n * D * 4, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(jac, djac, n * 8, cudaMemcpyDeviceToHost, stream);

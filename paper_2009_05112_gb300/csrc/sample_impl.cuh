@@ -29,10 +29,12 @@ namespace vp {
 struct SampleArgs {
     const Desc *desc;          // [n_int] descriptors of the whole set
     const uint32_t *members;   // [n_group] set indices served by this launch
-    const uint64_t *chunk_base;// [n_group + 1]
-    uint32_t *head;            // queue head
+    const uint64_t *chunk_base;// [n_group + 1] prefix of tasks (several integrals)
+    uint32_t *head;            // queue head: warp chunks (one integral) or tasks
+    uint32_t *exit_count;      // CTAs finished; the last one resets head and itself
     int n_group;
-    int R;                     // samples per thread per chunk
+    int r;                     // samples per thread per warp chunk
+    uint32_t task;             // samples per task when the group has several integrals
     int hist_shared;           // histograms privatised in shared memory
     int hist_words;            // dim * n_g bins reserved in shared memory
     int prm_words;             // 4-byte words reserved for integrand constants
@@ -194,6 +196,8 @@ __device__ __forceinline__ float scale2(float x, int n) {
 // Per-integral constants of the sampling loop, read once into registers.
 struct Loop {
     int dim, n_g, K;
+    uint32_t nst_magic;
+    int nst_shift;
     uint32_t n_st, calls, iid, t;
     uint32_t rk0[10], rk1[10];  // Philox round keys
     float c32;                  // N_g / N_st
@@ -212,6 +216,8 @@ __device__ __forceinline__ Loop make_loop(const Desc *dp, uint32_t t) {
     L.n_g = __ldg(&dp->n_g);
     L.K = __ldg(&dp->n_peaks);
     L.n_st = __ldg(&dp->n_st);
+    L.nst_magic = __ldg(&dp->nst_magic);
+    L.nst_shift = __ldg(&dp->nst_shift);
     L.calls = (uint32_t)((L.dim + 3) >> 2);
     L.iid = __ldg(&dp->integral_id);
     L.t = t;
@@ -265,21 +271,23 @@ __device__ __forceinline__ void hcube_offsets(const Loop &L, const uint32_t (&kd
 // ---------------------------------------------------------------------------
 // One sample, FP32 path (a1-a3): x[], idx[], J = Jm 2^Je, f.
 // ---------------------------------------------------------------------------
-template <int DMAX, int KIND>
+template <int DMAX, bool EXACT, int KIND>
 __device__ __forceinline__ void point32(const Loop &L, const float *prm, uint32_t h, uint32_t j,
                                         const float (&kc)[DMAX], float (&x)[DMAX],
                                         int (&idx)[DMAX], float &Jm, int &Je, float &f) {
+    const int dim = EXACT ? DMAX : L.dim;
+    const uint32_t calls = EXACT ? (uint32_t)((DMAX + 3) / 4) : L.calls;
     float J = L.ngD_m;
     int e = L.ngD_e;
 #pragma unroll
     for (int q = 0; q < (DMAX + 3) / 4; ++q) {
-        if (q < (int)L.calls) {
-            U4 c = {j * L.calls + (uint32_t)q, h, L.t, L.iid};
+        if (q < (int)calls) {
+            U4 c = {j * calls + (uint32_t)q, h, L.t, L.iid};
             const U4 r = philox_rk(c, L.rk0, L.rk1);
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
                 const int mu = 4 * q + l;
-                if (mu < DMAX && mu < L.dim) {
+                if (mu < DMAX && mu < dim) {
                     const uint32_t w = lane_of(r, l);
                     // (1 + m 2^-23) from the top 23 bits, no int->float conversion
                     const float one_m = __int_as_float(0x3f800000 | (w >> 9));
@@ -302,8 +310,8 @@ __device__ __forceinline__ void point32(const Loop &L, const float *prm, uint32_
     }
     Jm = J;
     Je = e;
-    if (KIND == VP_POSTERIOR) f = f_post32<DMAX>(prm, L.dim, x);
-    else f = f_peaks32<DMAX>(KIND, prm, L.K, L.dim, x);
+    if (KIND == VP_POSTERIOR) f = f_post32<DMAX>(prm, dim, x);
+    else f = f_peaks32<DMAX>(KIND, prm, L.K, dim, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -343,15 +351,23 @@ __device__ __forceinline__ void point64(const Loop &L, const double *prm, uint32
     else f = f_peaks64<DMAX>(KIND, prm + 1, L.K, L.dim, x);
 }
 
+// h / N_st by multiply and shifts (Granlund & Montgomery, "Division by
+// Invariant Integers using Multiplication", PLDI 1994); exact for all 32-bit h.
+__device__ __forceinline__ uint32_t div_nst(uint32_t h, uint32_t magic, int shift) {
+    if (shift == 0) return h;  // N_st = 1
+    const uint32_t t = __umulhi(magic, h);
+    return (t + ((h - t) >> 1)) >> (shift - 1);
+}
+
 // Mixed-radix digits of h: k_mu = (h / N_st^mu) mod N_st.
 template <int DMAX>
-__device__ __forceinline__ void decode_digits(uint32_t h, uint32_t n_st, int dim,
+__device__ __forceinline__ void decode_digits(uint32_t h, const Loop &L, int dim,
                                               uint32_t (&kd)[DMAX]) {
 #pragma unroll
     for (int mu = 0; mu < DMAX; ++mu) {
         if (mu < dim) {
-            const uint32_t q = h / n_st;
-            kd[mu] = h - q * n_st;
+            const uint32_t q = div_nst(h, L.nst_magic, L.nst_shift);
+            kd[mu] = h - q * L.n_st;
             h = q;
         } else {
             kd[mu] = 0u;
@@ -431,155 +447,287 @@ __device__ __forceinline__ void load_prm32(const Desc *dp, float *sprm, int word
     for (int i = threadIdx.x; i < words; i += blockDim.x) sprm[i] = __ldg(src + i);
 }
 
+// Per-integral device pointers of the sampling loop.
+struct Ptrs {
+    const uint64_t *off;
+    double *S1, *S2, *HS;
+    uint32_t *HC;
+    uint64_t n_hc, n_total;
+};
+
+// Samples [s_begin, s_end) of one integral, consecutive, by one thread:
+// per-hypercube sums in registers, flushed with one FP64 atomic pair per
+// hypercube touched; histograms into shared memory (or global).
+// Hypercube of sample `base` (the warp chunk's first), by a 32-ary search of
+// the offsets: every lane probes one point per round (4 rounds for 2^20
+// hypercubes).  Warp-uniform result.
+__device__ __forceinline__ uint64_t warp_find_hcube(const uint64_t *off, uint64_t n_hc,
+                                                    uint64_t base, int lane) {
+    uint64_t lo = 0, hi = n_hc;  // off[lo] <= base < off[hi]
+    while (hi - lo > 1) {
+        const uint64_t step = (hi - lo + 31) / 32;
+        const uint64_t p = lo + (uint64_t)(lane + 1) * step;
+        const bool le = p < hi && __ldg(off + p) <= base;
+        const int c = __popc(__ballot_sync(0xffffffffu, le));  // probes are increasing
+        const uint64_t nlo = lo + (uint64_t)c * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
+    }
+    return lo;
+}
+
+// Each lane's hypercube h (off[h] <= s < off[h + 1]) for its first sample s,
+// walking windows of 32 consecutive boundaries from the chunk's hypercube.
+// All shuffles run on every lane (no divergent collectives); the loop ends
+// once every active lane has found its hypercube, at the latest when the
+// window passes the last boundary.  Returns h; *lo_off = off[h],
+// *hi_off = off[h + 1].
+__device__ __forceinline__ uint64_t lane_find_hcube(const uint64_t *off, uint64_t n_hc,
+                                                    uint64_t h_base, uint64_t s, bool active,
+                                                    int lane, uint64_t *lo_off,
+                                                    uint64_t *hi_off) {
+    uint64_t win = h_base;  // off[win] <= every active lane's s
+    uint64_t h = h_base;
+    bool done = !active;
+    for (;;) {
+        const uint64_t pi = win + 1 + (uint64_t)lane;  // boundaries off[win + 1 .. win + 32]
+        const uint64_t bnd = pi <= n_hc ? __ldg(off + pi) : ~0ull;
+        int lo = -1, hi = 31;  // smallest m in (lo, hi] with boundary m > s (if any)
+#pragma unroll
+        for (int st = 0; st < 5; ++st) {
+            const int mid = (lo + hi) >> 1;
+            const uint64_t bm = __shfl_sync(0xffffffffu, bnd, mid < 0 ? 0 : mid);
+            if (hi - lo > 1) {
+                if (bm > s) hi = mid;
+                else lo = mid;
+            }
+        }
+        const uint64_t bh = __shfl_sync(0xffffffffu, bnd, hi);
+        const uint64_t bl = __shfl_sync(0xffffffffu, bnd, hi > 0 ? hi - 1 : 0);
+        if (!done && bh > s) {
+            h = win + (uint64_t)hi;
+            *hi_off = bh;
+            *lo_off = hi > 0 ? bl : __ldg(off + win);
+            done = true;
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+        win += 32;
+    }
+    return h;
+}
+
+template <int DMAX, bool EXACT, bool F64, int KIND>
+__device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const void *prm,
+                                            uint64_t s_begin, uint64_t s_end, uint64_t h,
+                                            uint64_t lo_off, uint64_t next,
+                                            typename Real<F64>::T *hs, uint32_t *hc,
+                                            bool hist_shared, int sexp, double unscale) {
+    typedef typename Real<F64>::T T;
+    const int dim = EXACT ? DMAX : L.dim;
+    uint32_t j = (uint32_t)(s_begin - lo_off);
+    uint32_t kd[DMAX];
+    decode_digits<DMAX>((uint32_t)h, L, dim, kd);
+    float kc[DMAX];
+    if (!F64) hcube_offsets<DMAX>(L, kd, kc);
+    const T scale = (T)ldexp(1.0, sexp);
+    const double un2 = unscale * unscale;
+    Acc<F64> acc;
+    acc.reset();
+    for (uint64_t s = s_begin; s < s_end; ++s) {
+        if (s == next) {
+            atomicAdd(P.S1 + h, acc.m1() * unscale);
+            atomicAdd(P.S2 + h, acc.m2() * un2);
+            acc.reset();
+            ++h;
+            next = __ldg(P.off + h + 1);
+            j = 0;
+            next_digits<DMAX>(L.n_st, dim, kd);
+            if (!F64) hcube_offsets<DMAX>(L, kd, kc);
+        }
+        int idx[DMAX];
+        T v;
+        if (F64) {
+            double x[DMAX], J, f;
+            point64<DMAX, KIND>(L, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
+            v = (T)(J * f * (double)scale);
+        } else {
+            float x[DMAX], Jm, f;
+            int Je;
+            point32<DMAX, EXACT, KIND>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je, f);
+            v = (T)scale2(Jm * f, Je + sexp);
+        }
+        const T v2 = v * v;
+        acc.add(v, v2);
+#pragma unroll
+        for (int mu = 0; mu < DMAX; ++mu) {
+            if (mu < dim) {
+                const int b = mu * L.n_g + idx[mu];
+                if (hist_shared) {
+                    if (v2 != (T)0) atomicAdd(hs + b, v2);
+                    atomicAdd(hc + b, 1u);
+                } else {
+                    if (v2 != (T)0) atomicAdd(P.HS + b, (double)v2 * un2);
+                    atomicAdd(P.HC + b, 1u);
+                }
+            }
+        }
+        ++j;
+    }
+    atomicAdd(P.S1 + h, acc.m1() * unscale);
+    atomicAdd(P.S2 + h, acc.m2() * un2);
+}
+
 // ---------------------------------------------------------------------------
-// The fused sampling kernel.
+// The fused sampling kernel (a1-a5).
+//
+// One integral in the launch: every warp of the persistent grid pulls warp
+// chunks of 32 r consecutive samples from one global counter (no block-wide
+// barrier in the loop; the tail is one warp chunk).  Several integrals: a CTA
+// pulls tasks (an integral and a range of `task` samples, big integrals first),
+// and its warps pull warp chunks of the task from a shared counter; the CTA's
+// histograms are flushed when it moves to another integral.  Lane l of a warp
+// chunk owns samples [base + l r, base + (l + 1) r).  The last CTA to finish
+// resets the queue for the next launch.
 // Shared memory: [prm: prm_words x 4 B][hist sum: hist_words x (4|8) B]
 //                [hist count: hist_words x 4 B]
 // ---------------------------------------------------------------------------
-template <int DMAX, bool F64, int KIND>
-__global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
+template <int DMAX, bool EXACT, bool F64, int KIND>
+__global__ void __launch_bounds__(256, 2) k_sample(SampleArgs a) {
     typedef typename Real<F64>::T T;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint32_t s_chunk;
+    __shared__ uint32_t s_task, s_wc;
     float *sprm = (float *)smem;
     T *hs = (T *)(smem + (size_t)a.prm_words * 4);
     uint32_t *hc = (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.hist_words * sizeof(T));
+    const int lane = threadIdx.x & 31;
+    const uint32_t wchunk = 32u * (uint32_t)a.r;
 
-    const uint64_t total = __ldg(a.chunk_base + a.n_group);
-    const uint32_t C = blockDim.x * (uint32_t)a.R;
     int cur = -1;
-    const Desc *dp = nullptr;
     Loop L;
+    Ptrs P;
     const void *prm = nullptr;
     int bins = 0, sexp = 0;
-    T scale = (T)1;
     double unscale = 1.0;
-    const uint64_t *off = nullptr;
-    uint64_t n_hc = 0, n_total = 0;
-    double *S1 = nullptr, *S2 = nullptr, *HS = nullptr;
-    uint32_t *HC = nullptr;
 
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_chunk = atomicAdd(a.head, 1u);
-        __syncthreads();
-        const uint64_t c = s_chunk;
-        if (c >= total) break;
-        const int g = upper_index(a.chunk_base, a.n_group, c);
-        if (g != cur) {
-            if (cur >= 0 && a.hist_shared) {  // leaving integral cur: flush its histograms
-                const double un2 = unscale * unscale;
-                for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-                    const uint32_t n = hc[b];
-                    if (n) {
-                        atomicAdd(HS + b, (double)hs[b] * un2);
-                        atomicAdd(HC + b, n);
-                    }
-                }
-                __syncthreads();
-            }
-            cur = g;
-            dp = a.desc + __ldg(a.members + g);
-            const State *st = (const State *)__ldg((const unsigned long long *)&dp->st);
-            L = make_loop(dp, __ldcg(&st->t));
-            sexp = __ldcg(&st->scale_exp);
-            scale = (T)ldexp(1.0, sexp);
-            unscale = ldexp(1.0, -sexp);
-            bins = L.dim * L.n_g;
-            off = (const uint64_t *)__ldg((const unsigned long long *)&dp->off);
-            n_hc = __ldg(&dp->n_hc);
-            n_total = __ldcg(off + n_hc);
-            S1 = (double *)__ldg((const unsigned long long *)&dp->s1);
-            S2 = (double *)__ldg((const unsigned long long *)&dp->s2);
-            HS = (double *)__ldg((const unsigned long long *)&dp->hsum);
-            HC = (uint32_t *)__ldg((const unsigned long long *)&dp->hcnt);
-            if (F64) {
-                prm = (const void *)__ldg((const unsigned long long *)&dp->prm);
-            } else {
-                load_prm32(dp, sprm, a.prm_words);
-                prm = (const void *)sprm;
-            }
-            if (a.hist_shared) {
-                for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-                    hs[b] = (T)0;
-                    hc[b] = 0u;
-                }
-            }
-            __syncthreads();
-        }
-        const uint64_t c0 = (c - __ldg(a.chunk_base + g)) * (uint64_t)C;
-        const uint64_t c_end = min(c0 + (uint64_t)C, n_total);
-        const uint64_t s_begin = c0 + (uint64_t)threadIdx.x * (uint64_t)a.R;
-        const uint64_t s_end = min(s_begin + (uint64_t)a.R, c_end);
-        if (s_begin >= s_end) continue;
-
-        uint64_t h = find_hcube(off, n_hc, s_begin);
-        uint64_t next = __ldg(off + h + 1);
-        uint32_t j = (uint32_t)(s_begin - __ldg(off + h));
-        uint32_t kd[DMAX];
-        decode_digits<DMAX>((uint32_t)h, L.n_st, L.dim, kd);
-        float kc[DMAX];
-        if (!F64) hcube_offsets<DMAX>(L, kd, kc);
-        Acc<F64> acc;
-        acc.reset();
-        for (uint64_t s = s_begin; s < s_end; ++s) {
-            if (s == next) {
-                atomicAdd(S1 + h, acc.m1() * unscale);
-                atomicAdd(S2 + h, acc.m2() * unscale * unscale);
-                acc.reset();
-                ++h;
-                next = __ldg(off + h + 1);
-                j = 0;
-                next_digits<DMAX>(L.n_st, L.dim, kd);
-                if (!F64) hcube_offsets<DMAX>(L, kd, kc);
-            }
-            int idx[DMAX];
-            T v;
-            if (F64) {
-                double x[DMAX], J, f;
-                point64<DMAX, KIND>(L, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
-                v = (T)(J * f * (double)scale);
-            } else {
-                float x[DMAX], Jm, f;
-                int Je;
-                point32<DMAX, KIND>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je, f);
-                v = (T)scale2(Jm * f, Je + sexp);
-            }
-            const T v2 = v * v;
-            acc.add(v, v2);
-#pragma unroll
-            for (int mu = 0; mu < DMAX; ++mu) {
-                if (mu < L.dim) {
-                    const int b = mu * L.n_g + idx[mu];
-                    if (a.hist_shared) {
-                        if (v2 != (T)0) atomicAdd(hs + b, v2);
-                        atomicAdd(hc + b, 1u);
-                    } else {
-                        if (v2 != (T)0) atomicAdd(HS + b, (double)v2 * unscale * unscale);
-                        atomicAdd(HC + b, 1u);
-                    }
-                }
-            }
-            ++j;
-        }
-        atomicAdd(S1 + h, acc.m1() * unscale);
-        atomicAdd(S2 + h, acc.m2() * unscale * unscale);
-    }
-    if (cur >= 0 && a.hist_shared) {
-        __syncthreads();
+    auto flush_hist = [&]() {
         const double un2 = unscale * unscale;
         for (int b = threadIdx.x; b < bins; b += blockDim.x) {
             const uint32_t n = hc[b];
             if (n) {
-                atomicAdd(HS + b, (double)hs[b] * un2);
-                atomicAdd(HC + b, n);
+                atomicAdd(P.HS + b, (double)hs[b] * un2);
+                atomicAdd(P.HC + b, n);
             }
+        }
+    };
+    auto enter = [&](int g) {  // all threads; caller synchronises afterwards
+        cur = g;
+        const Desc *dp = a.desc + __ldg(a.members + g);
+        const State *st = (const State *)__ldg((const unsigned long long *)&dp->st);
+        const uint32_t t_it = __ldcg(&st->t);
+        L = make_loop(dp, t_it);
+        sexp = __ldcg(&st->scale_exp);
+        unscale = ldexp(1.0, -sexp);
+        bins = L.dim * L.n_g;
+        P.off = (const uint64_t *)__ldg((const unsigned long long *)&dp->off);
+        P.n_hc = __ldg(&dp->n_hc);
+        P.n_total = __ldcg(P.off + P.n_hc);
+        // accumulators of this iteration: buffer (t & 1) of the double-buffered pairs
+        const uint64_t par = t_it & 1u;
+        P.S1 = (double *)__ldg((const unsigned long long *)&dp->s1) + par * P.n_hc;
+        P.S2 = (double *)__ldg((const unsigned long long *)&dp->s2) + par * P.n_hc;
+        P.HS = (double *)__ldg((const unsigned long long *)&dp->hsum) + par * bins;
+        P.HC = (uint32_t *)__ldg((const unsigned long long *)&dp->hcnt) + par * bins;
+        if (F64) {
+            prm = (const void *)__ldg((const unsigned long long *)&dp->prm);
+        } else {
+            load_prm32(dp, sprm, a.prm_words);
+            prm = (const void *)sprm;
+        }
+        if (a.hist_shared) {
+            for (int b = threadIdx.x; b < bins; b += blockDim.x) {
+                hs[b] = (T)0;
+                hc[b] = 0u;
+            }
+        }
+    };
+
+    if (a.n_group == 1) {
+        enter(0);
+        __syncthreads();
+        const uint64_t n_chunks = (P.n_total + wchunk - 1) / wchunk;
+        for (;;) {
+            uint32_t c = 0;
+            if (lane == 0) c = atomicAdd(a.head, 1u);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= n_chunks) break;
+            const uint64_t base = (uint64_t)c * wchunk;
+            const uint64_t s0 = base + (uint64_t)lane * a.r;
+            const uint64_t s1 = min(s0 + (uint64_t)a.r, P.n_total);
+            const uint64_t hb = warp_find_hcube(P.off, P.n_hc, base, lane);
+            uint64_t lo_off = 0, hi_off = 0;
+            const uint64_t h = lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
+            if (s0 < s1)
+                run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs, hc,
+                                                    a.hist_shared != 0, sexp, unscale);
+        }
+        __syncthreads();
+        if (a.hist_shared) flush_hist();
+    } else {
+        const uint64_t total = __ldg(a.chunk_base + a.n_group);
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_task = atomicAdd(a.head, 1u);
+                s_wc = 0u;
+            }
+            __syncthreads();
+            const uint64_t task = s_task;
+            if (task >= total) break;
+            const int g = upper_index(a.chunk_base, a.n_group, task);
+            if (g != cur) {
+                if (cur >= 0 && a.hist_shared) {
+                    flush_hist();
+                    __syncthreads();
+                }
+                enter(g);
+                __syncthreads();
+            }
+            const uint64_t t0 = (task - __ldg(a.chunk_base + g)) * (uint64_t)a.task;
+            const uint64_t t1 = min(t0 + (uint64_t)a.task, P.n_total);
+            const uint32_t n_wc = (uint32_t)((t1 - t0 + wchunk - 1) / wchunk);
+            for (;;) {
+                uint32_t c = 0;
+                if (lane == 0) c = atomicAdd(&s_wc, 1u);
+                c = __shfl_sync(0xffffffffu, c, 0);
+                if (c >= n_wc) break;
+                const uint64_t base = t0 + (uint64_t)c * wchunk;
+                const uint64_t s0 = base + (uint64_t)lane * a.r;
+                const uint64_t s1 = min(s0 + (uint64_t)a.r, t1);
+                const uint64_t hb = warp_find_hcube(P.off, P.n_hc, base, lane);
+                uint64_t lo_off = 0, hi_off = 0;
+                const uint64_t h =
+                    lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
+                if (s0 < s1)
+                    run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
+                                                        hc, a.hist_shared != 0, sexp, unscale);
+            }
+        }
+        if (cur >= 0 && a.hist_shared) flush_hist();
+    }
+    // the last CTA out resets the queue for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.exit_count, 1u) == gridDim.x - 1) {
+            *a.head = 0u;
+            *a.exit_count = 0u;
+            __threadfence();
         }
     }
 }
 
 // Per-sample inspection: the same device code as k_sample, on listed samples.
-template <int DMAX, bool F64, int KIND>
+template <int DMAX, bool EXACT, bool F64, int KIND>
 __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *hs,
                        const uint32_t *js, uint32_t t, double *xo, int32_t *io, double *jo,
                        double *fo, int prm_words) {
@@ -587,13 +735,14 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
     float *sprm = (float *)smem;
     const Desc *dp = desc + member;
     const Loop L = make_loop(dp, t);
+    const int dim = EXACT ? DMAX : L.dim;
     if (!F64) load_prm32(dp, sprm, prm_words);
     __syncthreads();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         uint32_t kd[DMAX];
         int idx[DMAX];
-        decode_digits<DMAX>((uint32_t)hs[k], L.n_st, L.dim, kd);
+        decode_digits<DMAX>((uint32_t)hs[k], L, dim, kd);
         double xd[DMAX], jac, f;
         if (F64) {
             point64<DMAX, KIND>(L, (const double *)__ldg((const unsigned long long *)&dp->prm),
@@ -602,7 +751,7 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
             float kc[DMAX], x[DMAX], Jm, ff;
             int Je;
             hcube_offsets<DMAX>(L, kd, kc);
-            point32<DMAX, KIND>(L, sprm, (uint32_t)hs[k], js[k], kc, x, idx, Jm, Je, ff);
+            point32<DMAX, EXACT, KIND>(L, sprm, (uint32_t)hs[k], js[k], kc, x, idx, Jm, Je, ff);
 #pragma unroll
             for (int mu = 0; mu < DMAX; ++mu) xd[mu] = (double)x[mu];
             jac = ldexp((double)Jm, Je);
@@ -610,9 +759,9 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
         }
 #pragma unroll
         for (int mu = 0; mu < DMAX; ++mu) {
-            if (mu < L.dim) {
-                xo[k * L.dim + mu] = xd[mu];
-                io[k * L.dim + mu] = idx[mu];
+            if (mu < dim) {
+                xo[k * dim + mu] = xd[mu];
+                io[k * dim + mu] = idx[mu];
             }
         }
         jo[k] = jac;
@@ -621,19 +770,24 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
 }
 
 // Launch dispatch (one translation unit per precision instantiates these).
-cudaError_t launch_sample_f32(int bucket, int kind, dim3 grid, dim3 block, size_t smem,
+// bucket b serves D <= kBucketDim[b]; exact: D == kBucketDim[b] (no dimension guards)
+constexpr int kNumBuckets = 6;
+__host__ __device__ constexpr int bucket_dim(int b) {
+    return b == 0 ? 4 : b == 1 ? 8 : b == 2 ? 12 : b == 3 ? 16 : b == 4 ? 20 : 24;
+}
+cudaError_t launch_sample_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, const SampleArgs &a);
-cudaError_t launch_sample_f64(int bucket, int kind, dim3 grid, dim3 block, size_t smem,
+cudaError_t launch_sample_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, const SampleArgs &a);
-cudaError_t launch_eval_f32(int bucket, int kind, cudaStream_t s, const Desc *desc, int member,
-                            int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t,
-                            double *x, int32_t *idx, double *jac, double *f, int prm_words);
-cudaError_t launch_eval_f64(int bucket, int kind, cudaStream_t s, const Desc *desc, int member,
-                            int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t,
-                            double *x, int32_t *idx, double *jac, double *f, int prm_words);
-cudaError_t sample_smem_config_f32(int bucket, int kind, int max_smem);
-cudaError_t sample_smem_config_f64(int bucket, int kind, int max_smem);
-int sample_occupancy_f32(int bucket, int kind, int threads, size_t smem);
-int sample_occupancy_f64(int bucket, int kind, int threads, size_t smem);
+cudaError_t launch_eval_f32(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
+                            int member, int64_t n, const uint64_t *h, const uint32_t *j,
+                            uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
+cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
+                            int member, int64_t n, const uint64_t *h, const uint32_t *j,
+                            uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
+cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, int max_smem);
+cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, int max_smem);
+int sample_occupancy_f32(int bucket, bool exact, int kind, int threads, size_t smem);
+int sample_occupancy_f64(int bucket, bool exact, int kind, int threads, size_t smem);
 
 }  // namespace vp

@@ -19,6 +19,7 @@ constexpr int kMaxNg = 4096;       // N_g limit (refinement keeps a whole axis i
 constexpr int kTreeBlock = 1024;   // hypercubes per block of the fixed-order sum
 constexpr int kMaxPeaks = 64;
 constexpr int kMaxPoints = 256;
+constexpr int kInvTab = 4096;      // table of 1/n for small integers n
 
 // Status bits (State::status).
 constexpr uint32_t kStatusNonFinite = 1u;
@@ -32,6 +33,7 @@ struct State {
     uint32_t status;      // kStatus* bits
     uint32_t pad;
     double sum_d;         // sum_h d_h in the fixed order (set by the estimate kernel)
+    double inv_sum_d;     // 1 / sum_d
     uint64_t n_samples;   // sum_h n_h of the current allocation
     uint64_t n_eval_total;// integrand evaluations over all iterations
     double last_i, last_var;
@@ -55,6 +57,8 @@ struct Desc {
     float inv_ng;              // 1 / N_g (FP32 path)
     float ngD_m;               // N_g^D = ngD_m 2^ngD_e (FP32 path: J = N_g^D prod dx_i)
     int32_t ngD_e;
+    uint32_t nst_magic;        // h / N_st = ((t + ((h - t) >> 1)) >> (nst_shift - 1)),
+    int32_t nst_shift;         //   t = umulhi(nst_magic, h) (Granlund-Montgomery); shift 0: N_st = 1
     // device buffers (all owned by the set)
     double *edges;     // [dim][n_g + 1] FP64 grid
     float2 *tab;       // [dim][n_g] {x_i, dx_i}, FP32 mirror of the grid
@@ -62,21 +66,16 @@ struct Desc {
     const float *prm32; // FP32 constants derived from the blob (FP32 path)
     uint32_t *n_h;     // [n_hc]
     uint64_t *off;     // [n_hc + 1] exclusive offsets; off[n_hc] = samples this iteration
-    double *s1, *s2;   // [n_hc] per-hypercube sums of v, v^2 (unscaled)
+    const double *inv_tab; // [kInvTab] 1/n (IEEE), shared by the set
+    double *s1, *s2;   // [2][n_hc] per-hypercube sums of v, v^2 (unscaled); iteration t
+                       // accumulates into buffer t & 1 while the estimate of t clears the other
     double *dh;        // [n_hc] d_h of the latest estimate
-    double *hsum;      // [dim][n_g] sum v^2 per increment (unscaled)
-    uint32_t *hcnt;    // [dim][n_g] samples per increment
+    double *hsum;      // [2][dim][n_g] sum v^2 per increment (unscaled), same double buffering
+    uint32_t *hcnt;    // [2][dim][n_g] samples per increment
     double *part;      // [n_tree][3] block partial sums (I, var, d)
     uint64_t *bsum;    // [n_tree] block sums of n_h, then block offsets
     double *hist_i, *hist_var;  // [hist_cap] iteration history
     State *st;
-};
-
-// Set-level work queue of the sampling kernel.
-struct Queue {
-    uint64_t *chunk_base;  // [n_int + 1] prefix of chunks per integral
-    uint32_t *head;        // next chunk to hand out
-    uint32_t *done;        // last-block counter of the prefix kernel
 };
 
 // ---------------------------------------------------------------------------
@@ -127,8 +126,5 @@ __device__ __forceinline__ float lg2_approx(float x) {
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-
-// Host-visible launch helpers (defined in the .cu files).
-struct SetDev;  // fwd
 
 }  // namespace vp
