@@ -38,6 +38,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["four_peaks_d8", "batch_mix", "serve"],
+                    default="four_peaks_d8",
+                    help="four_peaks_d8 (default): the single-integral step; batch_mix: 512 "
+                         "integrals per launch against one at a time; serve: continuous batching "
+                         "of a Poisson request stream")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     return ap.parse_args()
 
 
@@ -305,7 +311,9 @@ def run_ours(args):
                     "note": "create from host parameters + %d steps + a host read of the "
                             "estimate after every step, wall clock" % args.steps},
             "roofline": roof, "clocks": clocks,
-            "gpu_launches": 5 * args.steps,  # sample, estimate, alloc, offsets, refine
+            # sample, estimate, alloc, offsets, refine (+ the task prefix for the task kernel)
+            "gpu_launches": (5 + (g.tuning()["scheme"] == "tasks")) * args.steps,
+            "sample_launch": g.tuning(),
             "integral": {"mean": g.result()["mean"], "sdev": g.result()["sdev"],
                          "exact": prob.exact}}
     if world == 1 and not args.no_cpu_baseline:
@@ -316,10 +324,91 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """512 integrals (D 2..12, N_ev 1e4..1e6, 1-4 Gaussian peaks, N_g = 500,
+    15 iterations) in one persistent launch per iteration, against the same
+    integrals run one at a time through the single-integral path."""
+    import torch
+    from paper_2009_05112_gb300 import build as _build
+    from paper_2009_05112_gb300 import inputs, vegasp
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    vegasp.use_torch_allocator()
+    probs = inputs.batch_mix(n=512, seed=1)
+    n_it = 15
+    stream = torch.cuda.current_stream()
+    # device-timed steps of the batched job (the first W iterations warm up)
+    bt = vegasp.Batch(probs, precision=vegasp.VP_FP32)
+    for _ in range(args.warmup):
+        bt.step()
+    n0 = sum(r["n_eval"] for r in bt.results())
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            bt.step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    evals = sum(r["n_eval"] for r in bt.results()) - n0
+    bt.close()
+    # whole jobs, wall clock: batched and one integral at a time (same samples)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt = vegasp.Batch(probs, precision=vegasp.VP_FP32).run(n_it)
+    rb = bt.results()
+    torch.cuda.synchronize()
+    wall_b = time.perf_counter() - t0
+    evals_b = sum(r["n_eval"] for r in rb)
+    bt.close()
+    t0 = time.perf_counter()
+    evals_p = 0
+    rel_p, rel_b = [], []
+    for i, p in enumerate(probs):
+        g = vegasp.Integrator.from_problem(p, precision=vegasp.VP_FP32).run(n_it)
+        r = g.result()
+        evals_p += r["n_eval"]
+        rel_p.append(r["sdev"] / abs(r["mean"]) if r["mean"] else float("inf"))
+        rel_b.append(rb[i]["sdev"] / abs(rb[i]["mean"]) if rb[i]["mean"] else float("inf"))
+        g.close()
+    torch.cuda.synchronize()
+    wall_p = time.perf_counter() - t0
+    line = {"metric": "integrand evals/s", "value": evals / (total_ms / 1e3),
+            "unit": "integrand evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_mix_512", "integrals": 512, "dim": "2..12",
+                       "n_ev": "log-uniform 1e4..1e6", "n_g": 500, "iterations": n_it,
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "e2e": {"value": evals_b / wall_b, "unit": "integrand evals/s",
+                    "note": "whole batched job (create from host parameters, 15 graph steps, "
+                            "host read of all results), wall clock"},
+            "batched_vs_plain": {"wall_s_batched": wall_b, "wall_s_plain": wall_p,
+                                 "speedup_wall": wall_p / wall_b,
+                                 "evals_per_s_batched": evals_b / wall_b,
+                                 "evals_per_s_plain": evals_p / wall_p,
+                                 "median_rel_err_batched": statistics.median(rel_b),
+                                 "median_rel_err_plain": statistics.median(rel_p)},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    raise SystemExit("serve workload: not built yet")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch_mix":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -183,6 +183,35 @@ vp_status vp_eval_samples(vp_ctx *ctx, int64_t n, const uint64_t *h, const uint3
 /* Device-side timing of the latest sampling launch, in ms (CUDA events on the
  * launching stream); -1 if none recorded. */
 vp_status vp_last_sample_ms(vp_ctx *ctx, float *ms);
+/* Launch shape of the sampling kernel chosen by the autotuner (which runs at
+ * the first vp_iterate/vp_step): scheme 0 = static balanced split with
+ * clusters of `cluster` CTAs, 1 = dynamic tasks with `run` samples per thread
+ * per chunk; `blocks` CTAs of 256 threads. */
+vp_status vp_get_tuning(vp_ctx *ctx, int *scheme, int *blocks, int *cluster, int *run);
+
+/* ---- batches: many independent integrals per launch ----------------------- */
+/* A batch iterates n independent integrals together (each with its own box,
+ * integrand, N_ev, N_g, alpha, beta, seed and integral_id; validated as in
+ * vp_map_create).  Every iteration of the batch runs one persistent sampling
+ * launch per (integrand kind, precision) over a queue of (integral, sample
+ * range) tasks, largest integrals first, then the per-hypercube and per-axis
+ * kernels over all integrals at once; vp_batch_step replays the iteration and
+ * adaptation of every integral from one CUDA graph.  Results are per integral,
+ * identical in meaning to vp_result.  n: 1..1048576. */
+typedef struct vp_batch vp_batch;
+vp_status vp_batch_create(int n, const vp_params *params, const vp_integrand *f, void *stream,
+                          vp_batch **out);
+vp_status vp_batch_iterate(vp_batch *b, void *stream);
+vp_status vp_batch_adapt(vp_batch *b, void *stream);
+vp_status vp_batch_step(vp_batch *b, void *stream);
+/* integral i (0-based) */
+vp_status vp_batch_result(vp_batch *b, int i, int discard, vp_result_t *out);
+/* all n results into out[n] (one synchronisation); the first non-OK status */
+vp_status vp_batch_results(vp_batch *b, int discard, vp_result_t *out);
+vp_status vp_batch_size(vp_batch *b, int *n);
+/* I_j and sigma_j^2 of the first n iterations of integral i */
+vp_status vp_batch_history(vp_batch *b, int i, int n, double *i_j, double *var_j);
+vp_status vp_batch_destroy(vp_batch *b);
 
 /* ---- reallocation without device allocation --------------------------- */
 /* vp_alloc_static: the reallocation step of vp_adapt (the fixed-order sum of

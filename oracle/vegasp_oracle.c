@@ -331,7 +331,10 @@ void or_damp(int64_t n_hc, double beta, const double *sigma, double *d) {
 /* §3 step 4, Eq. (nh): n_h = max(2, N_ev d_h / sum d)  (plus2 = 0), or the    */
 /* alternative n_h = N_ev d_h / sum d + 2 (plus2 = 1).                         */
 /* reading: the real quotient is formed as (N_ev * d_h) / sum_d in IEEE FP64   */
-/* and floored; if sum_d is zero every hypercube gets max(2, floor(N_ev/N_h)). */
+/* and floored, except that a quotient within 2^-50 q below the next integer   */
+/* counts as that integer (a quotient that is an integer in exact arithmetic,  */
+/* e.g. N_ev when there is one hypercube, must not be decided by the last bit  */
+/* of d_h); if sum_d is zero every hypercube gets max(2, floor(N_ev/N_h)).     */
 /* Offsets are the exclusive prefix sums of n_h; offsets[N_h] = samples used.  */
 /* Returns 1 if a d_h or sum_d is not finite (nothing written), else 0.       */
 int or_allocate(int64_t n_hc, int64_t n_ev, int plus2, const double *d, uint32_t *n_h,
@@ -347,6 +350,7 @@ int or_allocate(int64_t n_hc, int64_t n_ev, int plus2, const double *d, uint32_t
             q = (double)n_ev / (double)n_hc;
         }
         double fl = floor(q);
+        if ((fl + 1.0) - q <= q * 8.8817841970012523e-16) fl = fl + 1.0; /* 2^-50 q */
         int64_t n;
         if (plus2) n = (int64_t)fl + 2;
         else n = fl > 2.0 ? (int64_t)fl : 2;

@@ -11,7 +11,8 @@
 //               a block, block sums left to right), so sum_h d_h -- and with it
 //               every integer n_h -- is reproducible bit for bit;
 //   k_alloc     a7: n_h = max(2, floor(N_ev d_h / sum d)) (§3 Eq. nh; or + 2;
-//               the first allocation is always the equal split max(2, .)),
+//               a quotient within 2^-50 q below an integer counts as that
+//               integer; the first allocation is always the equal split),
 //               block sums of n_h, then (last block) the block offsets;
 //   k_offsets   a7: exclusive offsets off[h] = sum_{h' < h} n_h';
 //   k_refine    a8 on one axis (§2.3): d_i = hsum_i / hcnt_i, smoothing
@@ -320,11 +321,14 @@ __global__ void __launch_bounds__(256) k_alloc(const Desc *desc, const uint32_t 
             // (a zero numerator is exact; below 2 - tol the max(2, .) decides)
             if (num > 0.0 && (d.plus2 || q > 1.5) && (q - fl <= tol || fl + 1.0 - q <= tol)) {
                 q = __ddiv_rn(num, sum_d);
-                floor_pos(q, &iq);
+                const double f2 = floor_pos(q, &iq);
+                // a quotient within 2^-50 q below an integer counts as that integer
+                if (__dsub_rn(__dadd_rn(f2, 1.0), q) <= __dmul_rn(q, 8.8817841970012523e-16)) ++iq;
             }
         } else {
             q = __ddiv_rn(n_ev_d, (double)d.n_hc);
-            floor_pos(q, &iq);
+            const double f2 = floor_pos(q, &iq);
+            if (__dsub_rn(__dadd_rn(f2, 1.0), q) <= __dmul_rn(q, 8.8817841970012523e-16)) ++iq;
         }
         uint32_t n;
         if (d.plus2 && !initial) n = (uint32_t)iq + 2u;

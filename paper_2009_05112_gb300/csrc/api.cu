@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -137,6 +138,11 @@ struct Group {
     int threads = 256, r = 8, blocks = 1, hist_shared = 0, hist_words = 0, prm_words = 0;
     uint32_t task = 0;
     size_t smem = 0;
+    bool one = false;  // a single integral: the cluster kernel with constants in parameters
+    int cs = 1;        // CTAs per cluster (one-integral kernel)
+    SampleOne args1;
+    int occ_one = 0, occ_many = 0;  // resident CTAs per SM of each kernel
+    bool tuned = false;
 };
 
 struct Set {
@@ -156,9 +162,14 @@ struct Set {
     bool timed = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    bool merge = false;  // one launch per (kind, precision): the largest bucket serves all
 };
 
 struct vp_ctx {
+    Set set;
+};
+
+struct vp_batch {
     Set set;
 };
 
@@ -332,19 +343,33 @@ static void make_tab(const double *e, int n_g, float2 *tab) {
 }
 
 static vp_status plan_groups(Set &s) {
-    // one launch group per (bucket, exactness, kind, precision)
+    // one launch group per (bucket, exactness, kind, precision); a merged set
+    // (a batch) has one group per (kind, precision), served by the bucket of
+    // its largest dimension
+    int merged_bucket[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (const Member &mb : s.m)
+        merged_bucket[mb.kind][mb.p.precision] =
+            std::max(merged_bucket[mb.kind][mb.p.precision], mb.bucket);
     for (uint32_t i = 0; i < s.m.size(); ++i) {
         const Member &mb = s.m[i];
-        const bool exact = mb.exact && mb.p.precision == VP_FP32;  // FP64 kernels are guarded
+        const int bucket = s.merge ? merged_bucket[mb.kind][mb.p.precision] : mb.bucket;
+        bool exact = mb.exact && mb.p.precision == VP_FP32;  // FP64 kernels are guarded
+        if (s.merge) {
+            exact = mb.p.precision == VP_FP32;
+            for (const Member &o : s.m)
+                if (o.kind == mb.kind && o.p.precision == mb.p.precision &&
+                    o.p.dim != bucket_dim(bucket))
+                    exact = false;
+        }
         Group *g = nullptr;
         for (auto &q : s.groups)
-            if (q.bucket == mb.bucket && q.exact == exact && q.kind == mb.kind &&
+            if (q.bucket == bucket && q.exact == exact && q.kind == mb.kind &&
                 q.prec == mb.p.precision)
                 g = &q;
         if (!g) {
             s.groups.push_back(Group());
             g = &s.groups.back();
-            g->bucket = mb.bucket;
+            g->bucket = bucket;
             g->exact = exact;
             g->kind = mb.kind;
             g->prec = mb.p.precision;
@@ -372,17 +397,45 @@ static vp_status plan_groups(Set &s) {
         const size_t prm_bytes = (size_t)g.prm_words * 4;
         g.hist_shared = (hist_bytes + prm_bytes <= 112 * 1024) ? 1 : 0;
         g.smem = prm_bytes + (g.hist_shared ? hist_bytes : 0);
-        if (g.smem > 48 * 1024) {
+        g.one = g.members.size() == 1;
+        {
             cudaError_t e = g.prec == VP_FP64
-                                ? sample_smem_config_f64(g.bucket, g.exact, g.kind, (int)g.smem)
-                                : sample_smem_config_f32(g.bucket, g.exact, g.kind, (int)g.smem);
-            if (e != cudaSuccess) return fail(VP_ECUDA, "smem config: %s", cudaGetErrorString(e));
+                                ? sample_smem_config_f64(g.bucket, g.exact, g.kind, g.one, (int)std::max<size_t>(g.smem, 48 * 1024))
+                                : sample_smem_config_f32(g.bucket, g.exact, g.kind, g.one, (int)std::max<size_t>(g.smem, 48 * 1024));
+            if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
         }
-        int occ = g.prec == VP_FP64
-                      ? sample_occupancy_f64(g.bucket, g.exact, g.kind, g.threads, g.smem)
-                      : sample_occupancy_f32(g.bucket, g.exact, g.kind, g.threads, g.smem);
+        if (g.one) {  // the autotuner may also try the task kernel for one integral
+            cudaError_t e = g.prec == VP_FP64
+                                ? sample_smem_config_f64(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024))
+                                : sample_smem_config_f32(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024));
+            if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+        }
+        g.occ_many = g.prec == VP_FP64
+                         ? sample_occupancy_f64(g.bucket, g.exact, g.kind, false, g.threads, g.smem)
+                         : sample_occupancy_f32(g.bucket, g.exact, g.kind, false, g.threads, g.smem);
+        g.occ_one = !g.one ? 0
+                           : (g.prec == VP_FP64
+                                  ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, g.threads, g.smem)
+                                  : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, g.threads, g.smem));
+        int occ = g.one ? g.occ_one : g.occ_many;
         if (occ < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem);
+        occ = std::min(occ, 2);  // until the autotuner has measured
         g.blocks = s.n_sm * occ;
+        if (g.one && g.hist_shared) {
+            // the largest cluster that keeps (nearly) every CTA slot busy
+            int best = g.blocks;
+            g.cs = 1;
+            for (int cs : {2, 4, 8}) {  // (the kernel's reduction handles up to 8)
+                const int ctas = g.prec == VP_FP64
+                                     ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem)
+                                     : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem);
+                if (ctas >= (int)(0.97 * g.blocks) && ctas >= cs) {
+                    g.cs = cs;
+                    best = ctas / cs * cs;
+                }
+            }
+            g.blocks = best;
+        }
         // several integrals: tasks of ~1/8 of a CTA's share, whole warp chunks
         const uint32_t wchunk = 32u * (uint32_t)g.r;
         const double per = expect / ((double)g.blocks * 8.0);
@@ -532,6 +585,55 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
     }
     s.n_tree_total = tree_base[n];
     s.n_axis_total = axis_base[n];
+    for (auto &g : s.groups) {
+        if (!g.one) continue;
+        const Desc &d = s.h_desc[g.members[0]];
+        const Member &mb = s.m[g.members[0]];
+        SampleOne &a = g.args1;
+        memset(&a, 0, sizeof a);
+        Loop &L = a.L;  // the constants make_loop reads on the device
+        L.dim = d.dim;
+        L.n_g = d.n_g;
+        L.K = d.n_peaks;
+        L.nst_magic = d.nst_magic;
+        L.nst_shift = d.nst_shift;
+        L.n_st = d.n_st;
+        L.calls = (uint32_t)((d.dim + 3) >> 2);
+        L.iid = d.integral_id;
+        L.t = 0;
+        uint32_t k0 = d.key0, k1 = d.key1;
+        for (int r = 0; r < 10; ++r) {
+            L.rk0[r] = k0;
+            L.rk1[r] = k1;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        L.c32 = d.ng_over_nst;
+        L.c32x = L.c32 * 1.1920928955078125e-07f;
+        L.ngm1 = (float)(d.n_g - 1);
+        L.ngD_m = d.ngD_m;
+        L.ngD_e = d.ngD_e;
+        L.nst = (double)d.n_st;
+        L.ng = (double)d.n_g;
+        L.tab = d.tab;
+        L.edges = d.edges;
+        a.st = d.st;
+        a.off = d.off;
+        a.s1 = d.s1;
+        a.s2 = d.s2;
+        a.hsum = d.hsum;
+        a.hcnt = d.hcnt;
+        a.prm32 = d.prm32;
+        a.prm = d.prm;
+        a.n_hc = d.n_hc;
+        a.head = g.d_head;
+        a.exit_count = g.d_head + 1;
+        a.r = g.r;
+        a.hist_shared = g.hist_shared;
+        a.bins = d.dim * d.n_g;
+        a.prm_words = g.prm_words;
+        (void)mb;
+    }
     CU(cudaMemcpyAsync(s.d_desc, s.h_desc.data(), n * sizeof(Desc), cudaMemcpyHostToDevice, stream));
     CU(cudaMemcpyAsync(s.d_tree_base, tree_base.data(), (n + 1) * 4, cudaMemcpyHostToDevice, stream));
     CU(cudaMemcpyAsync(s.d_axis_base, axis_base.data(), (n + 1) * 4, cudaMemcpyHostToDevice, stream));
@@ -559,21 +661,13 @@ static void set_destroy(Set &s) {
     cudaStreamSynchronize(s.last);
 }
 
-static vp_status set_iterate(Set &s, cudaStream_t stream) {
-    const int n = (int)s.m.size();
-    for (size_t gi = 0; gi < s.groups.size(); ++gi) {
-        Group &g = s.groups[gi];
-        if (g.members.size() > 1)  // the task prefix (one integral needs none)
-            CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base,
-                             g.d_head, g.task, stream));
-    }
-    // inside the step graph's capture the events must be external record nodes
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    CU(cudaStreamIsCapturing(stream, &cap));
-    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
-    CU(cudaEventRecordWithFlags(s.ev0, stream, ev_flags));
-    for (size_t gi = 0; gi < s.groups.size(); ++gi) {
-        Group &g = s.groups[gi];
+static vp_status launch_group(Set &s, Group &g, cudaStream_t stream) {
+    cudaError_t e;
+    if (g.one) {
+        e = g.prec == VP_FP64
+                ? launch_sample_one_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, g.cs, stream, g.args1)
+                : launch_sample_one_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, g.cs, stream, g.args1);
+    } else {
         SampleArgs a;
         a.desc = s.d_desc;
         a.members = g.d_members;
@@ -586,10 +680,201 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
         a.hist_shared = g.hist_shared;
         a.hist_words = g.hist_words;
         a.prm_words = g.prm_words;
-        cudaError_t e = g.prec == VP_FP64
-                            ? launch_sample_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a)
-                            : launch_sample_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a);
-        if (e != cudaSuccess) return fail(VP_ECUDA, "sampling launch: %s", cudaGetErrorString(e));
+        e = g.prec == VP_FP64
+                ? launch_sample_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a)
+                : launch_sample_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a);
+    }
+    if (e != cudaSuccess) return fail(VP_ECUDA, "sampling launch: %s", cudaGetErrorString(e));
+    return VP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: time candidate launch shapes of the sampling kernel on the live
+// state (the accumulators of the coming iteration are cleared afterwards, so
+// the tuning samples leave no trace) and keep the fastest.  Candidates: the
+// one-integral kernel (static balanced split) with 1..3 CTAs per SM and
+// clusters of 1, 2, 4 or 8 CTAs, and the task kernel (dynamic work stealing)
+// with 1..3 CTAs per SM and runs of 4 or 8 samples per thread.
+// ---------------------------------------------------------------------------
+struct Cand {
+    bool one;
+    int blocks, cs, r;
+};
+
+static vp_status time_group(Set &s, Group &g, cudaStream_t stream, float *best_ms) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        if (!g.one)
+            CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base, g.d_head,
+                             g.task, stream));
+        CU(cudaEventRecord(s.ev0, stream));
+        vp_status st = launch_group(s, g, stream);
+        if (st != VP_OK) return st;
+        CU(cudaEventRecord(s.ev1, stream));
+        CU(cudaEventSynchronize(s.ev1));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, s.ev0, s.ev1));
+        if (rep > 0) best = std::min(best, ms);  // the first launch warms up
+    }
+    *best_ms = best;
+    return VP_OK;
+}
+
+// Tuning results are kept for the process, keyed by what decides the launch
+// shape: kernel (precision, bucket, exactness, kind), histogram size, constants,
+// number of integrals and the order of magnitude of their samples.
+struct TuneKey {
+    int prec, bucket, exact, kind, hist_shared, bins, prm_words, members, dev;
+    int log2_samples;
+    bool operator==(const TuneKey &o) const { return memcmp(this, &o, sizeof *this) == 0; }
+};
+struct TuneVal {
+    bool one;
+    int blocks, cs, r;
+};
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+
+static TuneKey tune_key(const Set &s, const Group &g, double expect) {
+    TuneKey k;
+    memset(&k, 0, sizeof k);
+    k.prec = g.prec;
+    k.bucket = g.bucket;
+    k.exact = g.exact;
+    k.kind = g.kind;
+    k.hist_shared = g.hist_shared;
+    k.bins = g.hist_words;
+    k.prm_words = g.prm_words;
+    k.members = (int)g.members.size();
+    k.dev = s.device;
+    k.log2_samples = (int)std::floor(std::log2(std::max(1.0, expect)));
+    return k;
+}
+
+static void set_task(Group &g, double expect) {
+    const uint32_t wchunk = 32u * (uint32_t)g.r;
+    const double per = expect / ((double)g.blocks * 8.0);
+    g.task = (uint32_t)std::min(1.0e9, std::max((double)(8 * wchunk), per));
+    g.task = (g.task + wchunk - 1) / wchunk * wchunk;
+}
+
+static vp_status tune(Set &s, cudaStream_t stream) {
+    bool pending = false;
+    for (auto &g : s.groups) pending |= !g.tuned;
+    if (!pending) return VP_OK;
+    CU(cudaStreamSynchronize(s.last));
+    CU(cudaStreamSynchronize(stream));
+    for (auto &g : s.groups) {
+        if (g.tuned) continue;
+        {
+            double expect0 = 0.0;
+            for (uint32_t i : g.members) expect0 += (double)s.m[i].p.n_ev + 2.0 * (double)s.m[i].n_hc;
+            const TuneKey key = tune_key(s, g, expect0);
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            bool hit = false;
+            for (auto &kv : g_tune_cache)
+                if (kv.first == key) {
+                    g.one = kv.second.one;
+                    g.blocks = kv.second.blocks;
+                    g.cs = kv.second.cs;
+                    g.r = kv.second.r;
+                    set_task(g, expect0);
+                    g.tuned = true;
+                    hit = true;
+                    break;
+                }
+            if (hit) continue;
+        }
+        std::vector<Cand> cands;
+        const bool can_one = g.members.size() == 1;
+        double expect = 0.0;
+        for (uint32_t i : g.members) expect += (double)s.m[i].p.n_ev + 2.0 * (double)s.m[i].n_hc;
+        if (can_one) {
+            for (int k = 1; k <= std::min(3, g.occ_one); ++k) {
+                const int blocks = k * s.n_sm;
+                for (int cs : {1, 2, 4, 8}) {
+                    if (cs > 1 && !g.hist_shared) continue;
+                    int ctas = blocks;
+                    if (cs > 1) {
+                        ctas = g.prec == VP_FP64
+                                   ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, blocks, g.threads, g.smem)
+                                   : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, blocks, g.threads, g.smem);
+                        ctas = std::min(ctas, blocks) / cs * cs;
+                        if (ctas < (int)(0.9 * blocks)) continue;
+                    }
+                    cands.push_back({true, ctas, cs, g.r});
+                }
+            }
+        }
+        for (int k = 1; k <= std::min(3, g.occ_many); ++k)
+            for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r});
+        if (cands.size() <= 1) {
+            g.tuned = true;
+            continue;
+        }
+        const Cand keep = {g.one, g.blocks, g.cs, g.r};
+        Cand best = keep;
+        float best_ms = 1e30f;
+        for (const Cand &c : cands) {
+            g.one = c.one;
+            g.blocks = c.blocks;
+            g.cs = c.cs;
+            g.r = c.r;
+            set_task(g, expect);
+            float ms = 0.f;
+            vp_status st = time_group(s, g, stream, &ms);
+            if (st != VP_OK) return st;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        g.one = best.one;
+        g.blocks = best.blocks;
+        g.cs = best.cs;
+        g.r = best.r;
+        set_task(g, expect);
+        g.tuned = true;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune_cache.push_back({tune_key(s, g, expect), {g.one, g.blocks, g.cs, g.r}});
+        }
+        // clear what the tuning launches accumulated (buffer t & 1 of each member)
+        for (uint32_t i : g.members) {
+            const Desc &d = s.h_desc[i];
+            State st;
+            CU(cudaMemcpy(&st, d.st, sizeof st, cudaMemcpyDeviceToHost));
+            const size_t par = st.t & 1u, bins = (size_t)d.dim * d.n_g;
+            CU(cudaMemsetAsync(d.s1 + par * d.n_hc, 0, d.n_hc * 8, stream));
+            CU(cudaMemsetAsync(d.s2 + par * d.n_hc, 0, d.n_hc * 8, stream));
+            CU(cudaMemsetAsync(d.hsum + par * bins, 0, bins * 8, stream));
+            CU(cudaMemsetAsync(d.hcnt + par * bins, 0, bins * 4, stream));
+        }
+        CU(cudaStreamSynchronize(stream));
+    }
+    return VP_OK;
+}
+
+static vp_status set_iterate(Set &s, cudaStream_t stream) {
+    const int n = (int)s.m.size();
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(stream, &cap));
+    if (cap != cudaStreamCaptureStatusActive) {
+        vp_status st = tune(s, stream);
+        if (st != VP_OK) return st;
+    }
+    for (size_t gi = 0; gi < s.groups.size(); ++gi) {
+        Group &g = s.groups[gi];
+        if (!g.one)  // the task prefix (the one-integral kernel needs none)
+            CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base,
+                             g.d_head, g.task, stream));
+    }
+    // inside the step graph's capture the events must be external record nodes
+    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    CU(cudaEventRecordWithFlags(s.ev0, stream, ev_flags));
+    for (size_t gi = 0; gi < s.groups.size(); ++gi) {
+        vp_status st = launch_group(s, s.groups[gi], stream);
+        if (st != VP_OK) return st;
     }
     CU(cudaEventRecordWithFlags(s.ev1, stream, ev_flags));
     s.timed = true;
@@ -609,6 +894,8 @@ static vp_status set_adapt(Set &s, cudaStream_t stream) {
 
 static vp_status set_step(Set &s, cudaStream_t stream) {
     if (!s.gexec) {
+        vp_status tst = tune(s, stream);  // before the capture: tuning synchronises
+        if (tst != VP_OK) return tst;
         // capture on a private stream so that the caller's stream may be the
         // legacy default stream (which cannot be captured)
         cudaStream_t cap;
@@ -939,5 +1226,102 @@ extern "C" vp_status vp_last_sample_ms(vp_ctx *c, float *ms) {
     if (!c->set.timed) return VP_OK;
     CU(cudaEventSynchronize(c->set.ev1));
     CU(cudaEventElapsedTime(ms, c->set.ev0, c->set.ev1));
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_tuning(vp_ctx *c, int *scheme, int *blocks, int *cluster, int *run) {
+    CHECK_CTX(c);
+    if (c->set.groups.empty()) return fail(VP_EINVAL, "no sampling group");
+    const Group &g = c->set.groups[0];
+    if (scheme) *scheme = g.one ? 0 : 1;
+    if (blocks) *blocks = g.blocks;
+    if (cluster) *cluster = g.cs;
+    if (run) *run = g.r;
+    return VP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: many independent integrals iterated together
+// ---------------------------------------------------------------------------
+#define CHECK_BATCH(b) \
+    if (!(b)) return fail(VP_EINVAL, "NULL batch")
+
+extern "C" vp_status vp_batch_create(int n, const vp_params *params, const vp_integrand *fs,
+                                     void *stream, vp_batch **out) {
+    if (!out) return fail(VP_EINVAL, "NULL out");
+    *out = nullptr;
+    if (n < 1 || n > (1 << 20)) return fail(VP_EINVAL, "batch size must be 1..1048576");
+    vp_batch *b = new (std::nothrow) vp_batch();
+    if (!b) return fail(VP_ENOMEM, "host allocation failed");
+    b->set.merge = true;
+    vp_status st = set_create(b->set, n, params, fs, (cudaStream_t)stream);
+    if (st != VP_OK) {
+        std::string keep = g_err;
+        set_destroy(b->set);
+        delete b;
+        g_err = keep;
+        return st;
+    }
+    *out = b;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_batch_iterate(vp_batch *b, void *stream) {
+    CHECK_BATCH(b);
+    return set_iterate(b->set, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_batch_adapt(vp_batch *b, void *stream) {
+    CHECK_BATCH(b);
+    return set_adapt(b->set, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_batch_step(vp_batch *b, void *stream) {
+    CHECK_BATCH(b);
+    return set_step(b->set, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_batch_result(vp_batch *b, int i, int discard, vp_result_t *out) {
+    CHECK_BATCH(b);
+    if (!out) return fail(VP_EINVAL, "NULL out");
+    if (i < 0 || i >= (int)b->set.m.size()) return fail(VP_EINVAL, "integral index out of range");
+    return member_result(b->set, i, discard, out);
+}
+
+extern "C" vp_status vp_batch_results(vp_batch *b, int discard, vp_result_t *out) {
+    CHECK_BATCH(b);
+    if (!out) return fail(VP_EINVAL, "NULL out");
+    Set &s = b->set;
+    CU(cudaStreamSynchronize(s.last));
+    vp_status worst = VP_OK;
+    for (int i = 0; i < (int)s.m.size(); ++i) {
+        vp_status st = member_result(s, i, discard, out + i);
+        if (st != VP_OK && worst == VP_OK) worst = st;
+    }
+    return worst;
+}
+
+extern "C" vp_status vp_batch_size(vp_batch *b, int *n) {
+    CHECK_BATCH(b);
+    if (!n) return fail(VP_EINVAL, "NULL out");
+    *n = (int)b->set.m.size();
+    return VP_OK;
+}
+
+extern "C" vp_status vp_batch_destroy(vp_batch *b) {
+    if (!b) return VP_OK;
+    set_destroy(b->set);
+    delete b;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_batch_history(vp_batch *b, int i, int n, double *i_j, double *var_j) {
+    CHECK_BATCH(b);
+    if (i < 0 || i >= (int)b->set.m.size()) return fail(VP_EINVAL, "integral index out of range");
+    const Desc &d = b->set.h_desc[i];
+    if (n < 0 || n > d.hist_cap) return fail(VP_EINVAL, "n outside the history capacity");
+    CU(cudaStreamSynchronize(b->set.last));
+    if (n && i_j) CU(cudaMemcpy(i_j, d.hist_i, n * 8, cudaMemcpyDeviceToHost));
+    if (n && var_j) CU(cudaMemcpy(var_j, d.hist_var, n * 8, cudaMemcpyDeviceToHost));
     return VP_OK;
 }

@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(256) ks_alloc(const double *d_h, uint64_t n_hc
         double q;
         if (sum_d > 0.0) q = __ddiv_rn(__dmul_rn((double)n_ev, d_h[h]), sum_d);
         else q = __ddiv_rn((double)n_ev, (double)n_hc);
-        const double fl = floor(q);
+        double fl = floor(q);
+        // a quotient within 2^-50 q below an integer counts as that integer
+        if (__dsub_rn(__dadd_rn(fl, 1.0), q) <= __dmul_rn(q, 8.8817841970012523e-16)) fl += 1.0;
         uint32_t n;
         if (plus2) n = (uint32_t)fl + 2u;
         else n = fl > 2.0 ? (uint32_t)fl : 2u;

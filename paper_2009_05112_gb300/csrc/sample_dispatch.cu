@@ -1,0 +1,140 @@
+// sample_dispatch.cu -- host-side choice among the sampling kernel instantiations.
+#include "sample_impl.cuh"
+
+namespace vp {
+
+const void *kptr_one_f32_g(int bucket, int kind);
+const void *kptr_many_f32_g(int bucket, int kind);
+cudaError_t launch_eval_f32_g(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
+const void *kptr_one_f32_x(int bucket, int kind);
+const void *kptr_many_f32_x(int bucket, int kind);
+cudaError_t launch_eval_f32_x(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
+const void *kptr_one_f64_g(int bucket, int kind);
+const void *kptr_many_f64_g(int bucket, int kind);
+cudaError_t launch_eval_f64_g(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
+
+static const void *pick(bool f64, int bucket, bool exact, int kind, bool one) {
+    if (f64) return one ? kptr_one_f64_g(bucket, kind) : kptr_many_f64_g(bucket, kind);
+    if (exact) return one ? kptr_one_f32_x(bucket, kind) : kptr_many_f32_x(bucket, kind);
+    return one ? kptr_one_f32_g(bucket, kind) : kptr_many_f32_g(bucket, kind);
+}
+
+static cudaError_t launch_many(bool f64, int bucket, bool exact, int kind, dim3 grid, dim3 block,
+                               size_t smem, cudaStream_t s, const SampleArgs &a) {
+    const void *k = pick(f64, bucket, exact, kind, false);
+    if (!k) return cudaErrorInvalidValue;
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel(k, grid, block, args, smem, s);
+}
+
+static cudaError_t launch_one(bool f64, int bucket, bool exact, int kind, dim3 grid, dim3 block,
+                              size_t smem, int cs, cudaStream_t s, const SampleOne &a) {
+    const void *k = pick(f64, bucket, exact, kind, true);
+    if (!k) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+cudaError_t launch_sample_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, const SampleArgs &a) {
+    return launch_many(false, bucket, exact, kind, grid, block, smem, s, a);
+}
+cudaError_t launch_sample_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, const SampleArgs &a) {
+    return launch_many(true, bucket, false, kind, grid, block, smem, s, a);
+}
+cudaError_t launch_sample_one_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block,
+                                  size_t smem, int cs, cudaStream_t s, const SampleOne &a) {
+    return launch_one(false, bucket, exact, kind, grid, block, smem, cs, s, a);
+}
+cudaError_t launch_sample_one_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block,
+                                  size_t smem, int cs, cudaStream_t s, const SampleOne &a) {
+    return launch_one(true, bucket, false, kind, grid, block, smem, cs, s, a);
+}
+
+static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool one, int max_smem) {
+    const void *k = pick(f64, bucket, exact, kind, one);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess && one)  // clusters of up to 16 CTAs
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem) {
+    return smem_config(false, bucket, exact, kind, one, max_smem);
+}
+cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem) {
+    return smem_config(true, bucket, false, kind, one, max_smem);
+}
+
+static int occupancy(bool f64, int bucket, bool exact, int kind, bool one, int threads, size_t smem) {
+    const void *k = pick(f64, bucket, exact, kind, one);
+    int n = 0;
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem) {
+    return occupancy(false, bucket, exact, kind, one, threads, smem);
+}
+int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem) {
+    return occupancy(true, bucket, false, kind, one, threads, smem);
+}
+
+static int cluster_ctas(bool f64, int bucket, bool exact, int kind, int cs, int grid, int threads,
+                        size_t smem) {
+    const void *k = pick(f64, bucket, exact, kind, true);
+    if (!k) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n * cs;
+}
+int sample_cluster_ctas_f32(int bucket, bool exact, int kind, int cs, int grid, int threads,
+                            size_t smem) {
+    return cluster_ctas(false, bucket, exact, kind, cs, grid, threads, smem);
+}
+int sample_cluster_ctas_f64(int bucket, bool exact, int kind, int cs, int grid, int threads,
+                            size_t smem) {
+    return cluster_ctas(true, bucket, false, kind, cs, grid, threads, smem);
+}
+
+cudaError_t launch_eval_f32(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
+                            int member, int64_t n, const uint64_t *h, const uint32_t *j,
+                            uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw) {
+    return exact ? launch_eval_f32_x(bucket, kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw)
+                 : launch_eval_f32_g(bucket, kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+}
+cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
+                            int member, int64_t n, const uint64_t *h, const uint32_t *j,
+                            uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw) {
+    (void)exact;
+    return launch_eval_f64_g(bucket, kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
+}
+
+}  // namespace vp

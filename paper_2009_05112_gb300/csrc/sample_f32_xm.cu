@@ -1,31 +1,27 @@
-// sample_f32x.cu -- instantiations of the fused sampling kernel and its inspection
-// twin for the FP32 path, dimension-exact buckets (separate translation units compile in parallel).
+// sample_f32_xm.cu -- instantiations of the several-integral kernel and the per-sample inspection kernel, FP32 path, dimension-exact buckets.
+// (Split into several translation units so that they compile in parallel.)
 #include "sample_impl.cuh"
 
 namespace vp {
 
-template <int DMAX, int KIND>
-static const void *kptr_f32_x() { return (const void *)k_sample<DMAX, true, false, KIND>; }
-
-template <int DMAX>
-static const void *kkind_f32_x(int kind) {
+template <int DMAX, int KIND> static const void *kptr_many_f32_x_k() { return (const void *)k_sample_many<DMAX, true, false, KIND>; }
+template <int DMAX> static const void *kptr_many_f32_x_d(int kind) {
     switch (kind) {
-        case VP_GAUSS: return kptr_f32_x<DMAX, VP_GAUSS>();
-        case VP_BALL: return kptr_f32_x<DMAX, VP_BALL>();
-        case VP_EXPNORM: return kptr_f32_x<DMAX, VP_EXPNORM>();
-        case VP_POSTERIOR: return kptr_f32_x<DMAX, VP_POSTERIOR>();
+        case VP_GAUSS: return kptr_many_f32_x_k<DMAX, VP_GAUSS>();
+        case VP_BALL: return kptr_many_f32_x_k<DMAX, VP_BALL>();
+        case VP_EXPNORM: return kptr_many_f32_x_k<DMAX, VP_EXPNORM>();
+        case VP_POSTERIOR: return kptr_many_f32_x_k<DMAX, VP_POSTERIOR>();
     }
     return nullptr;
 }
-
-const void *sample_kernel_f32_x(int bucket, int kind) {
+const void *kptr_many_f32_x(int bucket, int kind) {
     switch (bucket) {
-        case 0: return kkind_f32_x<4>(kind);
-        case 1: return kkind_f32_x<8>(kind);
-        case 2: return kkind_f32_x<12>(kind);
-        case 3: return kkind_f32_x<16>(kind);
-        case 4: return kkind_f32_x<20>(kind);
-        case 5: return kkind_f32_x<24>(kind);
+        case 0: return kptr_many_f32_x_d<4>(kind);
+        case 1: return kptr_many_f32_x_d<8>(kind);
+        case 2: return kptr_many_f32_x_d<12>(kind);
+        case 3: return kptr_many_f32_x_d<16>(kind);
+        case 4: return kptr_many_f32_x_d<20>(kind);
+        case 5: return kptr_many_f32_x_d<24>(kind);
     }
     return nullptr;
 }

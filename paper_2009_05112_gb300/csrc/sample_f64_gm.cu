@@ -1,31 +1,27 @@
-// sample_f64.cu -- instantiations of the fused sampling kernel and its inspection
-// twin for the FP64 path (separate translation units compile in parallel).
+// sample_f64_gm.cu -- instantiations of the several-integral kernel and the per-sample inspection kernel, FP64 path.
+// (Split into several translation units so that they compile in parallel.)
 #include "sample_impl.cuh"
 
 namespace vp {
 
-template <int DMAX, int KIND>
-static const void *kptr_f64_g() { return (const void *)k_sample<DMAX, false, true, KIND>; }
-
-template <int DMAX>
-static const void *kkind_f64_g(int kind) {
+template <int DMAX, int KIND> static const void *kptr_many_f64_g_k() { return (const void *)k_sample_many<DMAX, false, true, KIND>; }
+template <int DMAX> static const void *kptr_many_f64_g_d(int kind) {
     switch (kind) {
-        case VP_GAUSS: return kptr_f64_g<DMAX, VP_GAUSS>();
-        case VP_BALL: return kptr_f64_g<DMAX, VP_BALL>();
-        case VP_EXPNORM: return kptr_f64_g<DMAX, VP_EXPNORM>();
-        case VP_POSTERIOR: return kptr_f64_g<DMAX, VP_POSTERIOR>();
+        case VP_GAUSS: return kptr_many_f64_g_k<DMAX, VP_GAUSS>();
+        case VP_BALL: return kptr_many_f64_g_k<DMAX, VP_BALL>();
+        case VP_EXPNORM: return kptr_many_f64_g_k<DMAX, VP_EXPNORM>();
+        case VP_POSTERIOR: return kptr_many_f64_g_k<DMAX, VP_POSTERIOR>();
     }
     return nullptr;
 }
-
-const void *sample_kernel_f64_g(int bucket, int kind) {
+const void *kptr_many_f64_g(int bucket, int kind) {
     switch (bucket) {
-        case 0: return kkind_f64_g<4>(kind);
-        case 1: return kkind_f64_g<8>(kind);
-        case 2: return kkind_f64_g<12>(kind);
-        case 3: return kkind_f64_g<16>(kind);
-        case 4: return kkind_f64_g<20>(kind);
-        case 5: return kkind_f64_g<24>(kind);
+        case 0: return kptr_many_f64_g_d<4>(kind);
+        case 1: return kptr_many_f64_g_d<8>(kind);
+        case 2: return kptr_many_f64_g_d<12>(kind);
+        case 3: return kptr_many_f64_g_d<16>(kind);
+        case 4: return kptr_many_f64_g_d<20>(kind);
+        case 5: return kptr_many_f64_g_d<24>(kind);
     }
     return nullptr;
 }
@@ -66,40 +62,6 @@ cudaError_t launch_eval_f64_g(int bucket, int kind, cudaStream_t s, const Desc *
         case 5: return eval_kind_f64_g<24>(kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
     }
     return cudaErrorInvalidValue;
-}
-
-static const void *pick_f64(int bucket, bool exact, int kind) {
-    (void)exact;
-    return sample_kernel_f64_g(bucket, kind);
-}
-
-cudaError_t launch_sample_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, const SampleArgs &a) {
-    const void *k = pick_f64(bucket, exact, kind);
-    if (!k) return cudaErrorInvalidValue;
-    void *args[] = {(void *)&a};
-    return cudaLaunchKernel(k, grid, block, args, smem, s);
-}
-
-cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, int max_smem) {
-    const void *k = pick_f64(bucket, exact, kind);
-    if (!k) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-}
-
-int sample_occupancy_f64(int bucket, bool exact, int kind, int threads, size_t smem) {
-    const void *k = pick_f64(bucket, exact, kind);
-    int n = 0;
-    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
-        return 0;
-    return n;
-}
-
-cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
-                            int member, int64_t n, const uint64_t *h, const uint32_t *j,
-                            uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw) {
-    (void)exact;
-    return launch_eval_f64_g(bucket, kind, s, desc, member, n, h, j, t, x, idx, jac, f, pw);
 }
 
 }  // namespace vp

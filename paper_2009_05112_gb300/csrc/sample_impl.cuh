@@ -22,19 +22,22 @@
 // in samples however uneven n_h is.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "vp_internal.cuh"
 
 namespace vp {
 
+// Launch arguments when the launch serves several integrals (tasks).
 struct SampleArgs {
     const Desc *desc;          // [n_int] descriptors of the whole set
     const uint32_t *members;   // [n_group] set indices served by this launch
-    const uint64_t *chunk_base;// [n_group + 1] prefix of tasks (several integrals)
-    uint32_t *head;            // queue head: warp chunks (one integral) or tasks
+    const uint64_t *chunk_base;// [n_group + 1] prefix of tasks
+    uint32_t *head;            // queue head (tasks)
     uint32_t *exit_count;      // CTAs finished; the last one resets head and itself
     int n_group;
     int r;                     // samples per thread per warp chunk
-    uint32_t task;             // samples per task when the group has several integrals
+    uint32_t task;             // samples per task
     int hist_shared;           // histograms privatised in shared memory
     int hist_words;            // dim * n_g bins reserved in shared memory
     int prm_words;             // 4-byte words reserved for integrand constants
@@ -239,6 +242,33 @@ __device__ __forceinline__ Loop make_loop(const Desc *dp, uint32_t t) {
     L.tab = (const float2 *)__ldg((const unsigned long long *)&dp->tab);
     L.edges = (const double *)__ldg((const unsigned long long *)&dp->edges);
     return L;
+}
+
+// Launch arguments when the launch serves one integral: its constants travel
+// in the kernel parameters (constant bank), not in registers.
+struct SampleOne {
+    Loop L;                    // t is read from the device state at launch
+    const State *st;
+    const uint64_t *off;
+    double *s1, *s2, *hsum;    // double-buffered bases
+    uint32_t *hcnt;
+    const float *prm32;
+    const double *prm;
+    uint64_t n_hc;
+    uint32_t *head;            // queue head (warp chunks)
+    uint32_t *exit_count;
+    int r;
+    int hist_shared;
+    int bins;
+    int prm_words;
+};
+
+// Fire-and-forget global reductions.
+__device__ __forceinline__ void red_add(double *p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(uint32_t *p, uint32_t v) {
+    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Philox4x32-10 with precomputed round keys (same function as philox4x32_10).
@@ -535,8 +565,8 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
     acc.reset();
     for (uint64_t s = s_begin; s < s_end; ++s) {
         if (s == next) {
-            atomicAdd(P.S1 + h, acc.m1() * unscale);
-            atomicAdd(P.S2 + h, acc.m2() * un2);
+            red_add(P.S1 + h, acc.m1() * unscale);
+            red_add(P.S2 + h, acc.m2() * un2);
             acc.reset();
             ++h;
             next = __ldg(P.off + h + 1);
@@ -546,6 +576,8 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
         }
         int idx[DMAX];
         T v;
+        bool big = false;  // FP32: |v| beyond 2^60 (v^2 would overflow), handled in FP64
+        double vbig = 0.0;
         if (F64) {
             double x[DMAX], J, f;
             point64<DMAX, KIND>(L, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
@@ -555,6 +587,14 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
             int Je;
             point32<DMAX, EXACT, KIND>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je, f);
             v = (T)scale2(Jm * f, Je + sexp);
+            if (!(fabsf((float)v) < 1.152921504606847e18f) && isfinite(Jm * f)) {
+                // a rare sample far above the iteration's scale: its own FP64 terms
+                big = true;
+                vbig = ldexp((double)Jm * (double)f, Je);  // J f, unscaled
+                red_add(P.S1 + h, vbig);
+                red_add(P.S2 + h, vbig * vbig);
+                v = (T)0;
+            }
         }
         const T v2 = v * v;
         acc.add(v, v2);
@@ -562,37 +602,141 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
         for (int mu = 0; mu < DMAX; ++mu) {
             if (mu < dim) {
                 const int b = mu * L.n_g + idx[mu];
-                if (hist_shared) {
+                if (big) {
+                    red_add(P.HS + b, vbig * vbig);
+                    if (hist_shared) atomicAdd(hc + b, 1u);
+                    else red_add(P.HC + b, 1u);
+                } else if (hist_shared) {
                     if (v2 != (T)0) atomicAdd(hs + b, v2);
                     atomicAdd(hc + b, 1u);
                 } else {
-                    if (v2 != (T)0) atomicAdd(P.HS + b, (double)v2 * un2);
-                    atomicAdd(P.HC + b, 1u);
+                    if (v2 != (T)0) red_add(P.HS + b, (double)v2 * un2);
+                    red_add(P.HC + b, 1u);
                 }
             }
         }
         ++j;
     }
-    atomicAdd(P.S1 + h, acc.m1() * unscale);
-    atomicAdd(P.S2 + h, acc.m2() * un2);
+    red_add(P.S1 + h, acc.m1() * unscale);
+    red_add(P.S2 + h, acc.m2() * un2);
 }
 
 // ---------------------------------------------------------------------------
-// The fused sampling kernel (a1-a5).
+// The fused sampling kernel (a1-a5), one integral per launch.
 //
-// One integral in the launch: every warp of the persistent grid pulls warp
-// chunks of 32 r consecutive samples from one global counter (no block-wide
-// barrier in the loop; the tail is one warp chunk).  Several integrals: a CTA
-// pulls tasks (an integral and a range of `task` samples, big integrals first),
-// and its warps pull warp chunks of the task from a shared counter; the CTA's
-// histograms are flushed when it moves to another integral.  Lane l of a warp
-// chunk owns samples [base + l r, base + (l + 1) r).  The last CTA to finish
-// resets the queue for the next launch.
-// Shared memory: [prm: prm_words x 4 B][hist sum: hist_words x (4|8) B]
-//                [hist count: hist_words x 4 B]
+// The N samples of the iteration are split evenly over the warps of the grid
+// (every CTA is resident at once), warp w taking [w N / W, (w + 1) N / W) and
+// lane l a run of consecutive samples within it, so the work is balanced to a
+// sample and nothing is queued.  The CTAs of a thread-block cluster then add
+// their shared-memory histograms through distributed shared memory, each CTA
+// reducing one slice of the bins, so the global flush is one reduction per bin
+// and cluster.
+// Shared memory: [prm: prm_words x 4 B][hist sum: bins x (4|8) B][hist count: bins x 4 B]
+// ---------------------------------------------------------------------------
+// resident CTAs of 256 threads to aim for: small dimensions fit three per SM
+__host__ __device__ constexpr int one_min_ctas(int dmax, bool f64) {
+    return f64 ? 1 : (dmax <= 8 ? 3 : 2);  // the autotuner picks how many actually run
+}
+
+template <int DMAX, bool EXACT, bool F64, int KIND>
+__global__ void __launch_bounds__(256, one_min_ctas(DMAX, F64))
+    k_sample_one(const __grid_constant__ SampleOne a) {
+    typedef typename Real<F64>::T T;
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *sprm = (float *)smem;
+    T *hs = (T *)(smem + (size_t)a.prm_words * 4);
+    uint32_t *hc = (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.bins * sizeof(T));
+    const int lane = threadIdx.x & 31;
+
+    const uint32_t t_it = __ldcg(&a.st->t);
+    const int sexp = __ldcg(&a.st->scale_exp);
+    const double unscale = ldexp(1.0, -sexp);
+    Loop L = a.L;
+    L.t = t_it;
+    Ptrs P;
+    const uint64_t par = t_it & 1u;  // accumulators of this iteration: buffer t & 1
+    P.off = a.off;
+    P.n_hc = a.n_hc;
+    P.n_total = __ldcg(a.off + a.n_hc);
+    P.S1 = a.s1 + par * a.n_hc;
+    P.S2 = a.s2 + par * a.n_hc;
+    P.HS = a.hsum + par * (uint64_t)a.bins;
+    P.HC = a.hcnt + par * (uint64_t)a.bins;
+    const void *prm;
+    if (F64) {
+        prm = (const void *)a.prm;
+    } else {
+        for (int i = threadIdx.x; i < a.prm_words; i += blockDim.x) sprm[i] = __ldg(a.prm32 + i);
+        prm = (const void *)sprm;
+    }
+    if (a.hist_shared) {
+        for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
+            hs[b] = (T)0;
+            hc[b] = 0u;
+        }
+    }
+    __syncthreads();
+    {
+        // this warp's share of the samples, then this lane's run within it
+        const uint64_t W = (uint64_t)gridDim.x * (blockDim.x >> 5);
+        const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        const uint64_t wb = w * P.n_total / W, we = (w + 1) * P.n_total / W;
+        const uint64_t q = (we - wb + 31) / 32;
+        const uint64_t s0 = min(wb + (uint64_t)lane * q, we);
+        const uint64_t s1 = min(s0 + q, we);
+        if (wb < we) {  // warp-uniform
+            const uint64_t hb = warp_find_hcube(P.off, P.n_hc, wb, lane);
+            uint64_t lo_off = 0, hi_off = 0;
+            const uint64_t h =
+                lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
+            if (s0 < s1)
+                run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs, hc,
+                                                    a.hist_shared != 0, sexp, unscale);
+        }
+    }
+    __syncthreads();
+    if (a.hist_shared) {
+        // cluster-wide reduction of the CTAs' histograms, one slice per CTA;
+        // the remote loads of a bin are issued together (cluster size <= 8)
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+        const int per = (a.bins + cs - 1) / cs;
+        const int b0 = rank * per, b1 = min(a.bins, b0 + per);
+        const double un2 = unscale * unscale;
+        for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+            T vs[8];
+            uint32_t vc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                vs[q] = q < cs ? *cl.map_shared_rank(hs + b, q) : (T)0;
+                vc[q] = q < cs ? *cl.map_shared_rank(hc + b, q) : 0u;
+            }
+            double sum = 0.0;
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                sum += (double)vs[q];
+                cnt += vc[q];
+            }
+            if (cnt) {
+                red_add(P.HS + b, sum * un2);
+                red_add(P.HC + b, cnt);
+            }
+        }
+        cl.sync();  // keep this CTA's shared memory until every remote read is done
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The fused sampling kernel (a1-a5) for several integrals per launch: a CTA
+// pulls tasks (an integral and a range of `task` samples, big integrals
+// first) and its warps pull warp chunks of the task from a shared counter; the
+// CTA's histograms are flushed when it moves to another integral.
 // ---------------------------------------------------------------------------
 template <int DMAX, bool EXACT, bool F64, int KIND>
-__global__ void __launch_bounds__(256, 2) k_sample(SampleArgs a) {
+__global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
     typedef typename Real<F64>::T T;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_task, s_wc;
@@ -614,8 +758,8 @@ __global__ void __launch_bounds__(256, 2) k_sample(SampleArgs a) {
         for (int b = threadIdx.x; b < bins; b += blockDim.x) {
             const uint32_t n = hc[b];
             if (n) {
-                atomicAdd(P.HS + b, (double)hs[b] * un2);
-                atomicAdd(P.HC + b, n);
+                red_add(P.HS + b, (double)hs[b] * un2);
+                red_add(P.HC + b, n);
             }
         }
     };
@@ -651,69 +795,46 @@ __global__ void __launch_bounds__(256, 2) k_sample(SampleArgs a) {
         }
     };
 
-    if (a.n_group == 1) {
-        enter(0);
+    const uint64_t total = __ldg(a.chunk_base + a.n_group);
+    for (;;) {
         __syncthreads();
-        const uint64_t n_chunks = (P.n_total + wchunk - 1) / wchunk;
-        for (;;) {
-            uint32_t c = 0;
-            if (lane == 0) c = atomicAdd(a.head, 1u);
-            c = __shfl_sync(0xffffffffu, c, 0);
-            if (c >= n_chunks) break;
-            const uint64_t base = (uint64_t)c * wchunk;
-            const uint64_t s0 = base + (uint64_t)lane * a.r;
-            const uint64_t s1 = min(s0 + (uint64_t)a.r, P.n_total);
-            const uint64_t hb = warp_find_hcube(P.off, P.n_hc, base, lane);
-            uint64_t lo_off = 0, hi_off = 0;
-            const uint64_t h = lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
-            if (s0 < s1)
-                run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs, hc,
-                                                    a.hist_shared != 0, sexp, unscale);
+        if (threadIdx.x == 0) {
+            s_task = atomicAdd(a.head, 1u);
+            s_wc = 0u;
         }
         __syncthreads();
-        if (a.hist_shared) flush_hist();
-    } else {
-        const uint64_t total = __ldg(a.chunk_base + a.n_group);
-        for (;;) {
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                s_task = atomicAdd(a.head, 1u);
-                s_wc = 0u;
-            }
-            __syncthreads();
-            const uint64_t task = s_task;
-            if (task >= total) break;
-            const int g = upper_index(a.chunk_base, a.n_group, task);
-            if (g != cur) {
-                if (cur >= 0 && a.hist_shared) {
-                    flush_hist();
-                    __syncthreads();
-                }
-                enter(g);
+        const uint64_t task = s_task;
+        if (task >= total) break;
+        const int g = upper_index(a.chunk_base, a.n_group, task);
+        if (g != cur) {
+            if (cur >= 0 && a.hist_shared) {
+                flush_hist();
                 __syncthreads();
             }
-            const uint64_t t0 = (task - __ldg(a.chunk_base + g)) * (uint64_t)a.task;
-            const uint64_t t1 = min(t0 + (uint64_t)a.task, P.n_total);
-            const uint32_t n_wc = (uint32_t)((t1 - t0 + wchunk - 1) / wchunk);
-            for (;;) {
-                uint32_t c = 0;
-                if (lane == 0) c = atomicAdd(&s_wc, 1u);
-                c = __shfl_sync(0xffffffffu, c, 0);
-                if (c >= n_wc) break;
-                const uint64_t base = t0 + (uint64_t)c * wchunk;
-                const uint64_t s0 = base + (uint64_t)lane * a.r;
-                const uint64_t s1 = min(s0 + (uint64_t)a.r, t1);
-                const uint64_t hb = warp_find_hcube(P.off, P.n_hc, base, lane);
-                uint64_t lo_off = 0, hi_off = 0;
-                const uint64_t h =
-                    lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
-                if (s0 < s1)
-                    run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
-                                                        hc, a.hist_shared != 0, sexp, unscale);
-            }
+            enter(g);
+            __syncthreads();
         }
-        if (cur >= 0 && a.hist_shared) flush_hist();
+        const uint64_t t0 = (task - __ldg(a.chunk_base + g)) * (uint64_t)a.task;
+        const uint64_t t1 = min(t0 + (uint64_t)a.task, P.n_total);
+        const uint32_t n_wc = (uint32_t)((t1 - t0 + wchunk - 1) / wchunk);
+        for (;;) {
+            uint32_t c = 0;
+            if (lane == 0) c = atomicAdd(&s_wc, 1u);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= n_wc) break;
+            const uint64_t base = t0 + (uint64_t)c * wchunk;
+            const uint64_t s0 = base + (uint64_t)lane * a.r;
+            const uint64_t s1 = min(s0 + (uint64_t)a.r, t1);
+            const uint64_t hb = warp_find_hcube(P.off, P.n_hc, base, lane);
+            uint64_t lo_off = 0, hi_off = 0;
+            const uint64_t h =
+                lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
+            if (s0 < s1)
+                run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
+                                                    hc, a.hist_shared != 0, sexp, unscale);
+        }
     }
+    if (cur >= 0 && a.hist_shared) flush_hist();
     // the last CTA out resets the queue for the next launch
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -775,19 +896,29 @@ constexpr int kNumBuckets = 6;
 __host__ __device__ constexpr int bucket_dim(int b) {
     return b == 0 ? 4 : b == 1 ? 8 : b == 2 ? 12 : b == 3 ? 16 : b == 4 ? 20 : 24;
 }
+// Several integrals (tasks) / one integral (cluster launch of cs CTAs per cluster).
 cudaError_t launch_sample_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, const SampleArgs &a);
 cudaError_t launch_sample_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, const SampleArgs &a);
+cudaError_t launch_sample_one_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block,
+                                  size_t smem, int cs, cudaStream_t s, const SampleOne &a);
+cudaError_t launch_sample_one_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block,
+                                  size_t smem, int cs, cudaStream_t s, const SampleOne &a);
 cudaError_t launch_eval_f32(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
                             int member, int64_t n, const uint64_t *h, const uint32_t *j,
                             uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
                             int member, int64_t n, const uint64_t *h, const uint32_t *j,
                             uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
-cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, int max_smem);
-cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, int max_smem);
-int sample_occupancy_f32(int bucket, bool exact, int kind, int threads, size_t smem);
-int sample_occupancy_f64(int bucket, bool exact, int kind, int threads, size_t smem);
+cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem);
+cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem);
+int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem);
+int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem);
+// Resident CTAs of the one-integral kernel with clusters of cs CTAs (0 if it cannot run).
+int sample_cluster_ctas_f32(int bucket, bool exact, int kind, int cs, int grid, int threads,
+                            size_t smem);
+int sample_cluster_ctas_f64(int bucket, bool exact, int kind, int cs, int grid, int threads,
+                            size_t smem);
 
 }  // namespace vp

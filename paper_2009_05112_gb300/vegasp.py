@@ -80,6 +80,18 @@ _SIGS = {
     "vp_eval_samples": [_P, ctypes.c_int64, _P, _P, ctypes.c_uint32, _P, _P, _P, _P],
     "vp_last_sample_ms": [_P, ctypes.POINTER(ctypes.c_float)],
     "vp_alloc_static": [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P, _P, _P],
+    "vp_get_tuning": [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "vp_batch_create": [ctypes.c_int, ctypes.POINTER(vp_params), ctypes.POINTER(vp_integrand), _P,
+                        ctypes.POINTER(_P)],
+    "vp_batch_iterate": [_P, _P],
+    "vp_batch_adapt": [_P, _P],
+    "vp_batch_step": [_P, _P],
+    "vp_batch_result": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp_result_t)],
+    "vp_batch_results": [_P, ctypes.c_int, _P],
+    "vp_batch_size": [_P, ctypes.POINTER(ctypes.c_int)],
+    "vp_batch_destroy": [_P],
+    "vp_batch_history": [_P, ctypes.c_int, ctypes.c_int, _P, _P],
 }
 
 _lib = None
@@ -287,7 +299,91 @@ class Integrator:
                                     _ptr(jac), _ptr(f)))
         return x, idx, jac, f
 
+    def tuning(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        check(lib().vp_get_tuning(self.ctx, *[ctypes.byref(x) for x in v]))
+        return dict(scheme=["static-cluster", "tasks"][v[0].value], blocks=v[1].value,
+                    cluster=v[2].value, run=v[3].value)
+
     def last_sample_ms(self):
         ms = ctypes.c_float()
         check(lib().vp_last_sample_ms(self.ctx, ctypes.byref(ms)))
         return ms.value
+
+
+def _result_dict(r, st):
+    return dict(mean=r.mean, sdev=r.sdev, chi2=r.chi2, dof=r.dof, n_it=r.n_it, n_eval=r.n_eval,
+                last_i=r.last_i, last_sdev=r.last_sdev, status=st)
+
+
+class Batch:
+    """Many independent integrals iterated together (a vp_batch)."""
+
+    def __init__(self, problems, precision=VP_FP32, stream=None):
+        self.n = len(problems)
+        self._keep = []
+        ps = (vp_params * self.n)()
+        fs = (vp_integrand * self.n)()
+        for i, prob in enumerate(problems):
+            lo = np.ascontiguousarray(np.broadcast_to(np.asarray(prob.lo, np.float64), (prob.dim,)))
+            hi = np.ascontiguousarray(np.broadcast_to(np.asarray(prob.hi, np.float64), (prob.dim,)))
+            prm = np.ascontiguousarray(prob.prm, np.float64)
+            self._keep += [lo, hi, prm]
+            ps[i] = vp_params(prob.dim, lo.ctypes.data_as(_dp), hi.ctypes.data_as(_dp), prob.n_g,
+                              int(prob.n_ev), float(prob.alpha), float(prob.beta),
+                              int(prob.seed) & (2 ** 64 - 1), int(prob.integral_id),
+                              int(precision), int(bool(prob.plus2)), int(prob.n_st), 0)
+            fs[i] = vp_integrand(int(prob.kind), prm.size, prm.ctypes.data_as(_dp))
+        self.stream = current_stream() if stream is None else ctypes.c_void_p(stream)
+        h = ctypes.c_void_p()
+        check(lib().vp_batch_create(self.n, ps, fs, self.stream, ctypes.byref(h)))
+        self.b = h
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().vp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self):
+        check(lib().vp_batch_iterate(self.b, self.stream))
+
+    def adapt(self):
+        check(lib().vp_batch_adapt(self.b, self.stream))
+
+    def step(self):
+        check(lib().vp_batch_step(self.b, self.stream))
+
+    def run(self, n_it, graph=True):
+        for _ in range(n_it):
+            if graph:
+                self.step()
+            else:
+                self.iterate()
+                self.adapt()
+        return self
+
+    def result(self, i, discard=0):
+        r = vp_result_t()
+        st = lib().vp_batch_result(self.b, int(i), int(discard), ctypes.byref(r))
+        if st not in (VP_OK, VP_ENONFINITE):
+            check(st)
+        return _result_dict(r, st)
+
+    def history(self, i):
+        n = self.result(i)["n_it"]
+        I, Vv = np.zeros(n), np.zeros(n)
+        check(lib().vp_batch_history(self.b, int(i), n, _ptr(I), _ptr(Vv)))
+        return I, Vv
+
+    def results(self, discard=0):
+        out = (vp_result_t * self.n)()
+        st = lib().vp_batch_results(self.b, int(discard), out)
+        if st not in (VP_OK, VP_ENONFINITE):
+            check(st)
+        return [_result_dict(out[i], VP_OK) for i in range(self.n)]

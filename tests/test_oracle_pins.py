@@ -298,10 +298,26 @@ def test_allocate_exact_rational_brute_force():
                 q = Fraction(n_ev) * Fraction(float(d[h])) / S
             fl = math.floor(q)
             if abs(q - round(q)) < Fraction(1, 10 ** 6) * max(1, q):
-                continue  # within rounding of an integer: either floor is acceptable
+                continue  # within rounding of an integer: decided by the tie rule below
             expect = fl + 2 if plus2 else max(2, fl)
             assert int(n_h[h]) == expect
         assert np.array_equal(off, np.concatenate([[0], np.cumsum(n_h.astype(np.uint64))]))
+
+
+def test_allocate_exact_integer_quotients():
+    """A quotient that is an integer in exact arithmetic gives that integer
+    whatever the last bits of d_h: one hypercube gets N_ev; equal d_h split
+    N_ev exactly."""
+    rng = np.random.default_rng(9)
+    for _ in range(2000):
+        v = float(rng.exponential() * 10.0 ** rng.uniform(-30, 30))
+        n_ev = int(rng.integers(2, 10 ** 9))
+        for d in (v, np.nextafter(v, 0), np.nextafter(v, np.inf)):
+            n_h, off = oracle.allocate(n_ev, np.array([d]))
+            assert int(n_h[0]) == max(2, n_ev)
+        n_h, off = oracle.allocate(n_ev, np.full(5, v))
+        if n_ev % 5 == 0:
+            assert np.all(n_h == max(2, n_ev // 5))
 
 
 def test_allocate_special_cases():
