@@ -397,8 +397,84 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def _serve_once(vegasp, stream_t, probs, rules, max_active, paced):
+    """Feeds the request stream to a server whose worker thread steps while the
+    caller submits: at the stream's arrival times (paced) or all at once.
+    Returns (per-request results, wall seconds first submit -> last done, stats)."""
+    srv = vegasp.Server(max_active=max_active)
+    srv.start()
+    t0 = vegasp.clock()
+    for k, (p, r) in enumerate(zip(probs, rules)):
+        if paced:
+            delay = t0 + stream_t[k] - vegasp.clock()
+            if delay > 0:
+                time.sleep(delay)
+        srv.submit(p, precision=vegasp.VP_FP32, tag=k, **r)
+    srv.wait(len(probs), timeout_s=600)
+    got = []
+    while len(got) < len(probs):
+        got += srv.poll()
+    srv.stop()
+    stats = srv.stats()
+    srv.close()
+    wall = max(r["t_done"] for r in got) - t0
+    return got, wall, stats
+
+
 def run_serve(args):
-    raise SystemExit("serve workload: not built yet")
+    """A Poisson stream of integration requests (mean 200/s; 70% D = 3, 30%
+    D = 21 Bayesian-posterior integrands, 50 points each, rtol 1e-3), served by
+    continuous batching (every admitted request advances one iteration per
+    server step) and, for comparison, one request at a time (max_active = 1)."""
+    import numpy as np
+    import torch
+    from paper_2009_05112_gb300 import build as _build
+    from paper_2009_05112_gb300 import inputs, vegasp
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    rate = 200.0
+    stream_t, probs, rules = inputs.serve_stream(args.requests, rate=rate, seed=0)
+    # warm-up: a few requests through both configurations
+    _serve_once(vegasp, stream_t[:8], probs[:8], rules[:8], 0, False)
+    _serve_once(vegasp, stream_t[:8], probs[:8], rules[:8], 1, False)
+    out = {}
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for name, max_active, paced in [("served", 0, True), ("plain", 1, True),
+                                        ("served_saturated", 0, False),
+                                        ("plain_saturated", 1, False)]:
+            got, wall, st = _serve_once(vegasp, stream_t, probs, rules, max_active, paced)
+            lat = np.array([r["t_done"] - r["t_submit"] for r in got]) * 1e3
+            d21 = np.array([probs[r["tag"]].dim == 21 for r in got])
+            rel = np.array([r["sdev"] / abs(r["mean"]) for r in got])
+            out[name] = {"requests_per_s": len(got) / wall, "wall_s": wall,
+                         "evals_per_s": sum(r["n_eval"] for r in got) / wall,
+                         "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)),
+                         "p50_ms_d3": float(np.percentile(lat[~d21], 50)),
+                         "p50_ms_d21": float(np.percentile(lat[d21], 50)),
+                         "converged_frac": float(np.mean([r["converged"] for r in got])),
+                         "median_rel_err": float(np.median(rel)),
+                         "mean_iterations": float(np.mean([r["n_iter"] for r in got])),
+                         "steps": st["steps"], "busy_s": st["busy_s"],
+                         "peak_state_mib": st["bytes_peak"] / 2 ** 20}
+    sat = out["served_saturated"]
+    line = {"metric": "served requests/s", "value": sat["requests_per_s"],
+            "unit": "requests/s", "n_gpus": 1, "steps": sat["steps"], "warmup": 8,
+            "ms_per_step": 1e3 * sat["busy_s"] / max(1, sat["steps"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serve_posteriors", "requests": args.requests,
+                       "arrivals": "Poisson, mean %g/s" % rate, "mix": "70% D=3, 30% D=21",
+                       "n_ev": "1e4 (D=3), 3e4 (D=21)", "n_g": 1000, "rtol": 1e-3,
+                       "stop": {str(k): v for k, v in inputs.SERVE_RULE.items()},
+                       "l2": "each step touches a few MB of request state (fits L2); "
+                             "latency, not bandwidth, bounds this workload"},
+            "value_note": "value: all requests queued at once (saturation), wall clock from "
+                          "first submit to last result; paced: the Poisson stream in real time",
+            "served": out["served"], "plain": out["plain"],
+            "served_saturated": sat, "plain_saturated": out["plain_saturated"],
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
 
 
 def main():

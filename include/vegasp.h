@@ -65,11 +65,13 @@ typedef enum { VP_FP64 = 0, VP_FP32 = 1 } vp_precision;
  *               (§2.4 Eq. balls; §1 footnote: the 20-D ball)
  *  VP_EXPNORM   [K, {a_k, s_k, c_k[D]} x K]  f = sum_k a_k exp(-s_k |x-c_k|)
  *               (§3.1 Eq. exponentials)
- *  VP_POSTERIOR [n, P, sigma_y, pw, log_ref, y[n], A[n][P]], D = P + 1,
- *               x = (c_0..c_{P-1}, w), r_i = y_i - sum_m A[i][m] c_m,
+ *  VP_POSTERIOR [n, P, G, sigma_y, pw, log_ref, y[n], A[n][P]], D = P + G,
+ *               x = (c_0..c_{P-1}, w_0..w_{G-1}), r_i = y_i - sum_m A[i][m] c_m,
+ *               point i weighted by w = w_{i mod G},
  *               f = exp(sum_i log[(1-w) N(r_i; sigma_y) + w N(r_i; 10 sigma_y)]
  *                       - sum_m c_m^2/(2 pw^2) - log_ref)
- *               (App. B Eqs. posterior, prior with Gaussian priors).
+ *               (App. B Eqs. posterior, prior with Gaussian priors; G = 1 is
+ *               its 3-parameter fit, one weight per point its 21-parameter one).
  * Limits: K <= 64; POSTERIOR n <= 256. */
 enum { VP_GAUSS = 0, VP_BALL = 1, VP_EXPNORM = 2, VP_POSTERIOR = 3 };
 
@@ -212,6 +214,86 @@ vp_status vp_batch_size(vp_batch *b, int *n);
 /* I_j and sigma_j^2 of the first n iterations of integral i */
 vp_status vp_batch_history(vp_batch *b, int i, int n, double *i_j, double *var_j);
 vp_status vp_batch_destroy(vp_batch *b);
+
+/* ---- serving: a stream of integration requests ------------------------------ */
+/* A server iterates requests that arrive over time.  Each request is one
+ * integral with a target relative error; the server runs the adaptive
+ * iterations of §2 and §3 for every admitted request together -- one iteration
+ * of all of them per server step, through the batched kernels above -- and
+ * retires each one when the combination (§2.5) of its iterations j >= discard
+ * has sdev <= rtol |mean| (after at least min_meas of them), or when it has
+ * run p.max_it iterations.  A request's grid, allocation and accumulators stay
+ * on the device from admission to retirement; a request's samples do not
+ * depend on which other requests share its steps (its Philox counters carry
+ * its own seed, integral_id and iteration count).
+ * Admission is by device memory: the server reserves mem_budget bytes at
+ * creation and admits queued requests, first come first served, while their
+ * state fits in what is left (and fewer than max_active are running).
+ * The paper serves one integral at a time; the server, its admission and the
+ * stop rule's form are this library's. */
+typedef struct {
+    int64_t mem_budget; /* device bytes for request state; 0 = 256 MiB */
+    int max_active;     /* requests iterated together, 1..65536; 0 = 4096 */
+} vp_server_config;
+
+typedef struct {
+    vp_params p;        /* as for vp_map_create; p.max_it (> discard) caps the
+                           iterations (0 = 1024) */
+    vp_integrand f;     /* copied at submission */
+    double rtol;        /* target relative error, > 0 */
+    int discard;        /* warm-up iterations left out of the result, >= 0 */
+    int min_meas;       /* least iterations in the result before the test, >= 1 */
+    uint64_t tag;       /* caller's label, returned with the result */
+} vp_request;
+
+typedef struct {
+    uint64_t id;        /* from vp_server_submit */
+    uint64_t tag;
+    vp_status status;   /* VP_OK, or VP_ENONFINITE (non-finite integrand value) */
+    int converged;      /* 1: sdev <= rtol |mean|; 0: stopped at p.max_it */
+    int n_iter;         /* iterations run */
+    vp_result_t r;      /* combination of iterations j >= discard (§2.5) */
+    double t_submit, t_admit, t_done; /* seconds on the steady clock (vp_server_clock) */
+} vp_served;
+
+typedef struct {
+    int64_t submitted, finished, queued, active;
+    int64_t steps;           /* server steps run */
+    int64_t bytes_in_use, bytes_peak, mem_budget;
+    int64_t n_eval;          /* integrand evaluations of all finished requests */
+    double busy_s;           /* wall time spent in steps */
+} vp_server_stats;
+
+typedef struct vp_server vp_server;
+
+/* Creates a server on the current device; its work runs on stream (NULL = a
+ * stream of its own).  VP_ENOMEM if the budget cannot be reserved. */
+vp_status vp_server_create(const vp_server_config *cfg, void *stream, vp_server **out);
+/* Queues a request (thread-safe; copies everything).  VP_EINVAL as for
+ * vp_map_create or for rtol/discard/min_meas/max_it out of range; VP_ENOMEM if
+ * the request's state alone exceeds the budget.  *id (may be NULL) receives
+ * its number, 0, 1, 2, ... in submission order. */
+vp_status vp_server_submit(vp_server *s, const vp_request *req, uint64_t *id);
+/* One server step on the calling thread: retire nothing new, admit what fits,
+ * run one iteration + adaptation of every admitted request, then retire the
+ * finished ones.  *n_active (may be NULL) receives the requests still running.
+ * VP_EINVAL while the server's own worker thread runs. */
+vp_status vp_server_step(vp_server *s, int *n_active);
+/* Starts / stops a worker thread that runs steps while requests are queued or
+ * running and sleeps otherwise.  Stopping waits for the current step. */
+vp_status vp_server_start(vp_server *s);
+vp_status vp_server_stop(vp_server *s);
+/* Moves up to max finished requests, in the order they finished, into out;
+ * *n receives how many.  If the worker failed, its error is returned. */
+vp_status vp_server_poll(vp_server *s, int max, vp_served *out, int *n);
+/* Blocks until `finished` requests have finished in all or timeout_s passes
+ * (VP_ETIMEOUT then). */
+vp_status vp_server_wait(vp_server *s, int64_t finished, double timeout_s);
+vp_status vp_server_get_stats(vp_server *s, vp_server_stats *out);
+/* The server's clock: seconds on the steady clock. */
+double vp_server_clock(void);
+/* Stops the worker and frees everything; unfinished requests are dropped. */
+vp_status vp_server_destroy(vp_server *s);
 
 /* ---- reallocation without device allocation --------------------------- */
 /* vp_alloc_static: the reallocation step of vp_adapt (the fixed-order sum of

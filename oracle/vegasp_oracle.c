@@ -88,8 +88,10 @@ int64_t or_nstrat(int dim, int64_t n_ev) {
 /*  kind 2 exp-norm peaks  §3.1 Eq. (exponentials): [K, {a, s, c[D]} x K]     */
 /*         f = sum_k a_k exp(-s_k |x - c_k|)                                   */
 /*  kind 3 posterior       App. B Eqs. (posterior, prior):                     */
-/*         [n, P, sigma_y, prior_width, log_ref, y[n], A[n][P]], D = P + 1;    */
-/*         x = (c_0..c_{P-1}, w); model_i = sum_m A[i][m] c_m;                 */
+/*         [n, P, G, sigma_y, prior_width, log_ref, y[n], A[n][P]], D = P + G; */
+/*         x = (c_0..c_{P-1}, w_0..w_{G-1}); model_i = sum_m A[i][m] c_m;     */
+/*         point i has the outlier weight w = w_{i mod G} (G = 1: one shared   */
+/*         w, the first example of App. B; one per point: its second);        */
 /*         P_i = (1-w)/(sqrt(2pi) s) e^{-r^2/2s^2} + w/(sqrt(2pi) 10 s) e^{-r^2/200 s^2} */
 /*         f = exp(sum_i log P_i - sum_m c_m^2 / (2 pw^2) - log_ref)           */
 /* ------------------------------------------------------------------------ */
@@ -114,14 +116,14 @@ double or_integrand(int kind, int dim, const double *prm, const double *x) {
         return f;
     }
     if (kind == 3) {
-        int n = (int)prm[0], npar = (int)prm[1];
-        double sy = prm[2], pw = prm[3], log_ref = prm[4];
-        const double *y = prm + 5;
-        const double *A = prm + 5 + n;
+        int n = (int)prm[0], npar = (int)prm[1], ngrp = (int)prm[2];
+        double sy = prm[3], pw = prm[4], log_ref = prm[5];
+        const double *y = prm + 6;
+        const double *A = prm + 6 + n;
         const double two_pi = 6.283185307179586476925286766559;
-        double w = x[npar];
         double logl = 0.0;
         for (int i = 0; i < n; ++i) {
+            double w = x[npar + i % ngrp];
             double model = 0.0;
             for (int m = 0; m < npar; ++m) model += A[i * npar + m] * x[m];
             double r = y[i] - model;

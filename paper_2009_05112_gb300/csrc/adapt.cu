@@ -278,6 +278,30 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
             st->scale_exp = -e;
         }
         st->t = tt + 1;
+        if (d.done_out) {  // a served request: the stop rule
+            if ((int)tt >= d.discard && isfinite(I) && isfinite(V)) {
+                if (V > 0.0) {
+                    st->cw += 1.0 / V;
+                    st->cwi += I / V;
+                } else {
+                    st->n_zero += 1u;
+                    st->zsum += I;
+                }
+            }
+            uint32_t done = 0u;
+            const int meas = (int)tt + 1 - d.discard;
+            if (meas >= d.min_meas && meas >= 1) {
+                if (st->n_zero > 0u) {
+                    done = kDoneStop | kDoneConverged;  // an exact iteration
+                } else if (st->cw > 0.0) {
+                    const double mean = st->cwi / st->cw, sdev = sqrt(1.0 / st->cw);
+                    if (sdev <= d.rtol * fabs(mean)) done = kDoneStop | kDoneConverged;
+                }
+            }
+            if ((int)tt + 1 >= d.stop_it || (st->status & kStatusNonFinite)) done |= kDoneStop;
+            st->done = done;
+            *d.done_out = done;
+        }
     }
 }
 

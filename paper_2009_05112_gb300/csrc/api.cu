@@ -17,25 +17,17 @@
 #include <string>
 #include <vector>
 
-#include "sample_impl.cuh"
-#include "vp_internal.cuh"
-
-namespace vp {
-cudaError_t launch_chunks(const Desc *, const uint32_t *, int, uint64_t *, uint32_t *, uint32_t,
-                          cudaStream_t);
-cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
-cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t, int initial);
-cudaError_t launch_refine(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
-}  // namespace vp
+#include "host.h"
 
 using namespace vp;
 
 // ---------------------------------------------------------------------------
 // errors and allocator
 // ---------------------------------------------------------------------------
-static thread_local std::string g_err = "no error";
+namespace vp {
+thread_local std::string g_err = "no error";
 
-static vp_status fail(vp_status s, const char *fmt, ...) {
+vp_status fail(vp_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -44,14 +36,7 @@ static vp_status fail(vp_status s, const char *fmt, ...) {
     g_err = buf;
     return s;
 }
-
-#define CU(call)                                                                        \
-    do {                                                                                \
-        cudaError_t e_ = (call);                                                        \
-        if (e_ != cudaSuccess)                                                          \
-            return fail(VP_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
-                        __FILE__, __LINE__);                                            \
-    } while (0)
+}  // namespace vp
 
 static vp_alloc_fn g_alloc = nullptr;
 static vp_free_fn g_free = nullptr;
@@ -76,15 +61,7 @@ const char *set_error_message(vp_status, const char *msg) {
 }
 }  // namespace vp
 
-struct DevMem {
-    void *ptr = nullptr;
-    size_t bytes = 0;
-    vp_alloc_fn alloc = nullptr;
-    vp_free_fn free_fn = nullptr;
-    void *user = nullptr;
-};
-
-static vp_status dev_alloc(DevMem &m, size_t bytes, cudaStream_t s) {
+vp_status vp::dev_alloc(DevMem &m, size_t bytes, cudaStream_t s) {
     m.bytes = bytes;
     m.alloc = g_alloc;
     m.free_fn = g_free;
@@ -104,7 +81,7 @@ static vp_status dev_alloc(DevMem &m, size_t bytes, cudaStream_t s) {
     return VP_OK;
 }
 
-static void dev_free(DevMem &m, cudaStream_t s) {
+void vp::dev_free(DevMem &m, cudaStream_t s) {
     if (!m.ptr) return;
     if (m.free_fn) m.free_fn(m.ptr, m.bytes, (void *)s, m.user);
     else cudaFreeAsync(m.ptr, s);
@@ -114,37 +91,6 @@ static void dev_free(DevMem &m, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // the problem set
 // ---------------------------------------------------------------------------
-struct Member {
-    vp_params p;
-    int kind;
-    std::vector<double> lo, hi, prm;
-    std::vector<float> prm32;
-    int64_t n_st;
-    uint64_t n_hc;
-    uint32_t n_tree;
-    int hist_cap;
-    int bucket;
-    bool exact;            // dim equals the bucket's dimension
-    size_t off_bytes[20];  // offsets of the buffers within the arena
-};
-
-struct Group {
-    int bucket, kind, prec;
-    bool exact;
-    std::vector<uint32_t> members;
-    uint32_t *d_members = nullptr;
-    uint64_t *d_chunk_base = nullptr;
-    uint32_t *d_head = nullptr;      // d_head[0] queue head, d_head[1] exit counter
-    int threads = 256, r = 8, blocks = 1, hist_shared = 0, hist_words = 0, prm_words = 0;
-    uint32_t task = 0;
-    size_t smem = 0;
-    bool one = false;  // a single integral: the cluster kernel with constants in parameters
-    int cs = 1;        // CTAs per cluster (one-integral kernel)
-    SampleOne args1;
-    int occ_one = 0, occ_many = 0;  // resident CTAs per SM of each kernel
-    bool tuned = false;
-};
-
 struct Set {
     int device = 0;
     int n_sm = 0;
@@ -173,7 +119,7 @@ struct vp_batch {
     Set set;
 };
 
-static int bucket_of(int dim) {
+int vp::bucket_of(int dim) {
     for (int b = 0; b < kNumBuckets; ++b)
         if (dim <= bucket_dim(b)) return b;
     return kNumBuckets - 1;
@@ -211,7 +157,7 @@ static int64_t nstrat_exact(int dim, int64_t n_ev) {
     return n;
 }
 
-static vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb) {
+vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
     if (!p || !f) return fail(VP_EINVAL, "NULL params or integrand");
     if (p->dim < 1 || p->dim > kMaxDim) return fail(VP_EINVAL, "dim %d outside 1..%d", p->dim, kMaxDim);
     if (p->n_g < 1 || p->n_g > kMaxNg) return fail(VP_EINVAL, "n_g %d outside 1..%d", p->n_g, kMaxNg);
@@ -241,14 +187,15 @@ static vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb)
             break;
         }
         case VP_POSTERIOR: {
-            if (n < 5) return fail(VP_EINVAL, "posterior blob too short");
-            const double nd = q[0], Pd = q[1];
+            if (n < 6) return fail(VP_EINVAL, "posterior blob too short");
+            const double nd = q[0], Pd = q[1], Gd = q[2];
             if (!(nd >= 1 && nd <= kMaxPoints && nd == std::floor(nd)))
                 return fail(VP_EINVAL, "posterior point count must be 1..%d", kMaxPoints);
-            if (!(Pd == D - 1 && Pd >= 1)) return fail(VP_EINVAL, "posterior needs P = dim - 1 >= 1");
+            if (!(Pd >= 1 && Gd >= 1 && Pd == std::floor(Pd) && Gd == std::floor(Gd) && Pd + Gd == D))
+                return fail(VP_EINVAL, "posterior needs P >= 1, G >= 1 and P + G = dim");
             const int np = (int)nd, P = (int)Pd;
-            if (n != 5 + np + np * P) return fail(VP_EINVAL, "posterior blob needs %d doubles", 5 + np + np * P);
-            if (!(q[2] > 0 && q[3] > 0)) return fail(VP_EINVAL, "posterior widths must be > 0");
+            if (n != 6 + np + np * P) return fail(VP_EINVAL, "posterior blob needs %d doubles", 6 + np + np * P);
+            if (!(q[3] > 0 && q[4] > 0)) return fail(VP_EINVAL, "posterior widths must be > 0");
             break;
         }
         default:
@@ -261,6 +208,8 @@ static vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb)
     mb.lo.assign(p->lo, p->lo + D);
     mb.hi.assign(p->hi, p->hi + D);
     mb.prm.assign(q, q + n);
+    mb.p.lo = mb.lo.data();  // the caller's arrays may not outlive the call
+    mb.p.hi = mb.hi.data();
     mb.n_st = p->n_st > 0 ? p->n_st : nstrat_exact(D, p->n_ev);
     // N_h = N_st^D <= 2^31
     uint64_t nh = 1;
@@ -281,19 +230,20 @@ static vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb)
     const double L2E = 1.4426950408889634074;
     mb.prm32.clear();
     if (f->kind == VP_POSTERIOR) {
-        const int np = (int)q[0], P = (int)q[1];
-        const double sy = q[2], pw = q[3], lref = q[4];
+        const int np = (int)q[0], P = (int)q[1], G = (int)q[2];
+        const double sy = q[3], pw = q[4], lref = q[5];
         const double s2pi = std::sqrt(2.0 * M_PI);
         mb.prm32.push_back((float)np);
         mb.prm32.push_back((float)P);
+        mb.prm32.push_back((float)G);
         mb.prm32.push_back((float)(L2E / (2.0 * sy * sy)));
         mb.prm32.push_back((float)(L2E / (200.0 * sy * sy)));
         mb.prm32.push_back((float)std::log2(1.0 / (s2pi * sy)));
         mb.prm32.push_back((float)std::log2(1.0 / (s2pi * 10.0 * sy)));
         mb.prm32.push_back((float)(L2E / (2.0 * pw * pw)));
         mb.prm32.push_back((float)(lref * L2E));
-        for (int i = 0; i < np; ++i) mb.prm32.push_back((float)q[5 + i]);
-        for (int i = 0; i < np * P; ++i) mb.prm32.push_back((float)q[5 + np + i]);
+        for (int i = 0; i < np; ++i) mb.prm32.push_back((float)q[6 + i]);
+        for (int i = 0; i < np * P; ++i) mb.prm32.push_back((float)q[6 + np + i]);
     } else {
         // per peak {a, k, 0, 0, c[D], pad}: a multiple of 4 floats
         const int K = (int)q[0];
@@ -312,14 +262,7 @@ static vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb)
     return VP_OK;
 }
 
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-enum {
-    B_EDGES, B_TAB, B_PRM, B_PRM32, B_NH, B_OFF, B_S1, B_S2, B_DH, B_HSUM, B_HCNT, B_PART,
-    B_BSUM, B_HI, B_HV, B_ST, B_COUNT
-};
-
-static size_t member_layout(Member &mb, size_t base) {
+size_t vp::member_layout(Member &mb, size_t base) {
     const size_t D = mb.p.dim, G = mb.p.n_g, H = mb.n_hc, T = mb.n_tree, C = mb.hist_cap;
     const size_t sz[B_COUNT] = {D * (G + 1) * 8, D * G * 8, mb.prm.size() * 8,
                                 mb.prm32.size() * 4, H * 4, (H + 1) * 8, 2 * H * 8, 2 * H * 8,
@@ -330,11 +273,6 @@ static size_t member_layout(Member &mb, size_t base) {
         base = align256(base + sz[i]);
     }
     return base;
-}
-
-template <typename T>
-static T *at(const Set &s, const Member &mb, int which) {
-    return (T *)((char *)s.arena.ptr + mb.off_bytes[which]);
 }
 
 // FP32 mirror {x_i, dx_i} of one axis.
@@ -376,52 +314,25 @@ static vp_status plan_groups(Set &s) {
         }
         g->members.push_back(i);
     }
+    std::vector<const Member *> mp;
+    for (const Member &mb : s.m) mp.push_back(&mb);
     for (auto &g : s.groups) {
-        double expect = 0.0;
-        int max_bins = 0, max_words = 0;
-        for (uint32_t i : g.members) {
-            expect += (double)s.m[i].p.n_ev + 2.0 * (double)s.m[i].n_hc;
-            max_bins = std::max(max_bins, s.m[i].p.dim * s.m[i].p.n_g);
-            max_words = std::max(max_words, (int)s.m[i].prm32.size());
-        }
-        // big integrals first: tasks of later members fill the tail
-        std::stable_sort(g.members.begin(), g.members.end(), [&](uint32_t a, uint32_t b) {
-            return s.m[a].p.n_ev > s.m[b].p.n_ev;
-        });
-        const size_t tbytes = g.prec == VP_FP64 ? 8 : 4;
-        const size_t hist_bytes = (size_t)max_bins * (tbytes + 4);
-        g.threads = 256;
-        g.r = 8;
-        g.hist_words = max_bins;
-        g.prm_words = g.prec == VP_FP64 ? 0 : ((max_words + 3) & ~3);
-        const size_t prm_bytes = (size_t)g.prm_words * 4;
-        g.hist_shared = (hist_bytes + prm_bytes <= 112 * 1024) ? 1 : 0;
-        g.smem = prm_bytes + (g.hist_shared ? hist_bytes : 0);
+        vp_status st = group_config_many(mp, g, s.n_sm);
+        if (st != VP_OK) return st;
         g.one = g.members.size() == 1;
-        {
-            cudaError_t e = g.prec == VP_FP64
-                                ? sample_smem_config_f64(g.bucket, g.exact, g.kind, g.one, (int)std::max<size_t>(g.smem, 48 * 1024))
-                                : sample_smem_config_f32(g.bucket, g.exact, g.kind, g.one, (int)std::max<size_t>(g.smem, 48 * 1024));
-            if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
-        }
-        if (g.one) {  // the autotuner may also try the task kernel for one integral
-            cudaError_t e = g.prec == VP_FP64
-                                ? sample_smem_config_f64(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024))
-                                : sample_smem_config_f32(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024));
-            if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
-        }
-        g.occ_many = g.prec == VP_FP64
-                         ? sample_occupancy_f64(g.bucket, g.exact, g.kind, false, g.threads, g.smem)
-                         : sample_occupancy_f32(g.bucket, g.exact, g.kind, false, g.threads, g.smem);
-        g.occ_one = !g.one ? 0
-                           : (g.prec == VP_FP64
-                                  ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, g.threads, g.smem)
-                                  : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, g.threads, g.smem));
-        int occ = g.one ? g.occ_one : g.occ_many;
-        if (occ < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem);
-        occ = std::min(occ, 2);  // until the autotuner has measured
-        g.blocks = s.n_sm * occ;
-        if (g.one && g.hist_shared) {
+        if (!g.one) continue;
+        // a single integral: the cluster kernel with its constants in parameters
+        // (the autotuner may still choose the task kernel)
+        cudaError_t e = g.prec == VP_FP64
+                            ? sample_smem_config_f64(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem, 48 * 1024))
+                            : sample_smem_config_f32(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem, 48 * 1024));
+        if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+        g.occ_one = g.prec == VP_FP64
+                        ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, g.threads, g.smem)
+                        : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, g.threads, g.smem);
+        if (g.occ_one < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem);
+        g.blocks = s.n_sm * std::min(g.occ_one, 2);  // until the autotuner has measured
+        if (g.hist_shared) {
             // the largest cluster that keeps (nearly) every CTA slot busy
             int best = g.blocks;
             g.cs = 1;
@@ -436,12 +347,133 @@ static vp_status plan_groups(Set &s) {
             }
             g.blocks = best;
         }
-        // several integrals: tasks of ~1/8 of a CTA's share, whole warp chunks
-        const uint32_t wchunk = 32u * (uint32_t)g.r;
-        const double per = expect / ((double)g.blocks * 8.0);
-        uint32_t task = (uint32_t)std::min(1.0e9, std::max((double)(8 * wchunk), per));
-        g.task = (task + wchunk - 1) / wchunk * wchunk;
+        set_task(g, (double)s.m[g.members[0]].p.n_ev + 2.0 * (double)s.m[g.members[0]].n_hc);
     }
+    return VP_OK;
+}
+
+// Task-kernel launch shape of a group: shared-memory histograms when the
+// largest member's fit (with the FP32 constants) in 112 KB, two CTAs per SM at
+// most, tasks of ~1/8 of a CTA's share in whole warp chunks.
+vp_status vp::group_config_many(const std::vector<const Member *> &m, Group &g, int n_sm) {
+    double expect = 0.0;
+    int max_bins = 0, max_words = 0;
+    for (uint32_t i : g.members) {
+        expect += (double)m[i]->p.n_ev + 2.0 * (double)m[i]->n_hc;
+        max_bins = std::max(max_bins, m[i]->p.dim * m[i]->p.n_g);
+        max_words = std::max(max_words, (int)m[i]->prm32.size());
+    }
+    // big integrals first: tasks of later members fill the tail
+    std::stable_sort(g.members.begin(), g.members.end(), [&](uint32_t a, uint32_t b) {
+        return m[a]->p.n_ev > m[b]->p.n_ev;
+    });
+    const size_t tbytes = g.prec == VP_FP64 ? 8 : 4;
+    const size_t hist_bytes = (size_t)max_bins * (tbytes + 4);
+    g.threads = 256;
+    g.r = 8;
+    g.hist_words = max_bins;
+    g.prm_words = g.prec == VP_FP64 ? 0 : ((max_words + 3) & ~3);
+    const size_t prm_bytes = (size_t)g.prm_words * 4;
+    g.hist_shared = (hist_bytes + prm_bytes <= 112 * 1024) ? 1 : 0;
+    g.smem = prm_bytes + (g.hist_shared ? hist_bytes : 0);
+    g.one = false;
+    g.cs = 1;
+    cudaError_t e = g.prec == VP_FP64
+                        ? sample_smem_config_f64(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024))
+                        : sample_smem_config_f32(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024));
+    if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+    g.occ_many = g.prec == VP_FP64
+                     ? sample_occupancy_f64(g.bucket, g.exact, g.kind, false, g.threads, g.smem)
+                     : sample_occupancy_f32(g.bucket, g.exact, g.kind, false, g.threads, g.smem);
+    if (g.occ_many < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem);
+    g.blocks = n_sm * std::min(g.occ_many, 2);
+    set_task(g, expect);
+    return VP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one member's descriptor and initial device state
+// ---------------------------------------------------------------------------
+void vp::inv_table(std::vector<double> &inv) {
+    inv.assign(kInvTab, 0.0);
+    for (int k = 1; k < kInvTab; ++k) inv[k] = 1.0 / (double)k;  // IEEE division on the host
+}
+
+void vp::fill_desc(const Member &mb, const double *d_inv, Desc &d) {
+    const int D = mb.p.dim, G = mb.p.n_g;
+    memset(&d, 0, sizeof d);
+    d.dim = D;
+    d.n_g = G;
+    d.kind = mb.kind;
+    d.prec = mb.p.precision;
+    d.plus2 = mb.p.plus2 ? 1 : 0;
+    d.n_peaks = (int)mb.prm[0];
+    d.n_par = mb.kind == VP_POSTERIOR ? (int)mb.prm[1] : 0;
+    d.hist_cap = mb.hist_cap;
+    d.n_st = (uint32_t)mb.n_st;
+    d.integral_id = mb.p.integral_id;
+    d.key0 = (uint32_t)mb.p.seed;
+    d.key1 = (uint32_t)(mb.p.seed >> 32);
+    d.n_tree = mb.n_tree;
+    d.n_ev = mb.p.n_ev;
+    d.n_hc = mb.n_hc;
+    d.omega = 1.0 / (double)mb.n_hc;
+    d.alpha = mb.p.alpha;
+    d.beta = mb.p.beta;
+    d.ng_over_nst = (float)((double)G / (double)mb.n_st);
+    d.inv_ng = (float)(1.0 / (double)G);
+    {
+        int e = 0;
+        const double m = std::frexp(std::pow((double)G, (double)D), &e);  // m in [0.5, 1)
+        d.ngD_m = (float)(2.0 * m);
+        d.ngD_e = e - 1;
+    }
+    div_magic((uint32_t)mb.n_st, &d.nst_magic, &d.nst_shift);
+    d.inv_tab = d_inv;
+    d.edges = mbuf<double>(mb, B_EDGES);
+    d.tab = mbuf<float2>(mb, B_TAB);
+    d.prm = mbuf<double>(mb, B_PRM);
+    d.prm32 = mbuf<float>(mb, B_PRM32);
+    d.n_h = mbuf<uint32_t>(mb, B_NH);
+    d.off = mbuf<uint64_t>(mb, B_OFF);
+    d.s1 = mbuf<double>(mb, B_S1);
+    d.s2 = mbuf<double>(mb, B_S2);
+    d.dh = mbuf<double>(mb, B_DH);
+    d.hsum = mbuf<double>(mb, B_HSUM);
+    d.hcnt = mbuf<uint32_t>(mb, B_HCNT);
+    d.part = mbuf<double>(mb, B_PART);
+    d.bsum = mbuf<uint64_t>(mb, B_BSUM);
+    d.hist_i = mbuf<double>(mb, B_HI);
+    d.hist_var = mbuf<double>(mb, B_HV);
+    d.st = mbuf<State>(mb, B_ST);
+}
+
+vp_status vp::upload_member_init(const Member &mb, const Desc &d, cudaStream_t stream) {
+    const int D = mb.p.dim, G = mb.p.n_g;
+    // uniform grid (§2.3: the first iteration uses a uniform grid)
+    std::vector<double> edges((size_t)D * (G + 1));
+    std::vector<float2> tab((size_t)D * G);
+    double vol = 1.0;
+    for (int mu = 0; mu < D; ++mu) {
+        const double a = mb.lo[mu], b = mb.hi[mu];
+        double *e = &edges[(size_t)mu * (G + 1)];
+        for (int k = 0; k <= G; ++k) e[k] = a + (b - a) * (double)k / (double)G;
+        e[0] = a;
+        e[G] = b;
+        make_tab(e, G, &tab[(size_t)mu * G]);
+        vol *= (b - a);
+    }
+    State sti;
+    memset(&sti, 0, sizeof sti);
+    int e = std::ilogb(vol);
+    sti.scale_exp = -(e > 120 ? 120 : (e < -120 ? -120 : e));
+    std::vector<double> ones(mb.n_hc, 1.0);
+    CU(cudaMemcpyAsync(d.edges, edges.data(), edges.size() * 8, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(d.tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync((void *)d.prm, mb.prm.data(), mb.prm.size() * 8, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync((void *)d.prm32, mb.prm32.data(), mb.prm32.size() * 4, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(d.dh, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(d.st, &sti, sizeof sti, cudaMemcpyHostToDevice, stream));
     return VP_OK;
 }
 
@@ -489,8 +521,8 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
     s.d_axis_base = (uint32_t *)(A + axis_off);
     const double *d_inv = (const double *)(A + inv_off);
     {
-        std::vector<double> inv(kInvTab, 0.0);
-        for (int k = 1; k < kInvTab; ++k) inv[k] = 1.0 / (double)k;  // IEEE division on the host
+        std::vector<double> inv;
+        inv_table(inv);
         CU(cudaMemcpyAsync((void *)d_inv, inv.data(), kInvTab * sizeof(double), cudaMemcpyHostToDevice,
                            stream));
         CU(cudaStreamSynchronize(stream));
@@ -503,86 +535,18 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
     // host images of the initial state
     std::vector<uint32_t> tree_base(n + 1, 0), axis_base(n + 1, 0);
     s.h_desc.resize(n);
-    std::vector<char> stage;
     for (int i = 0; i < n; ++i) {
         Member &mb = s.m[i];
-        const int D = mb.p.dim, G = mb.p.n_g;
-        Desc &d = s.h_desc[i];
-        memset(&d, 0, sizeof d);
-        d.dim = D;
-        d.n_g = G;
-        d.kind = mb.kind;
-        d.prec = mb.p.precision;
-        d.plus2 = mb.p.plus2 ? 1 : 0;
-        d.n_peaks = (int)mb.prm[0];
-        d.n_par = mb.kind == VP_POSTERIOR ? (int)mb.prm[1] : 0;
-        d.hist_cap = mb.hist_cap;
-        d.n_st = (uint32_t)mb.n_st;
-        d.integral_id = mb.p.integral_id;
-        d.key0 = (uint32_t)mb.p.seed;
-        d.key1 = (uint32_t)(mb.p.seed >> 32);
-        d.n_tree = mb.n_tree;
-        d.n_ev = mb.p.n_ev;
-        d.n_hc = mb.n_hc;
-        d.omega = 1.0 / (double)mb.n_hc;
-        d.alpha = mb.p.alpha;
-        d.beta = mb.p.beta;
-        d.ng_over_nst = (float)((double)G / (double)mb.n_st);
-        d.inv_ng = (float)(1.0 / (double)G);
-        {
-            int e = 0;
-            const double m = std::frexp(std::pow((double)G, (double)D), &e);  // m in [0.5, 1)
-            d.ngD_m = (float)(2.0 * m);
-            d.ngD_e = e - 1;
-        }
-        div_magic((uint32_t)mb.n_st, &d.nst_magic, &d.nst_shift);
-        d.inv_tab = d_inv;
-        d.edges = at<double>(s, mb, B_EDGES);
-        d.tab = at<float2>(s, mb, B_TAB);
-        d.prm = at<double>(s, mb, B_PRM);
-        d.prm32 = at<float>(s, mb, B_PRM32);
-        d.n_h = at<uint32_t>(s, mb, B_NH);
-        d.off = at<uint64_t>(s, mb, B_OFF);
-        d.s1 = at<double>(s, mb, B_S1);
-        d.s2 = at<double>(s, mb, B_S2);
-        d.dh = at<double>(s, mb, B_DH);
-        d.hsum = at<double>(s, mb, B_HSUM);
-        d.hcnt = at<uint32_t>(s, mb, B_HCNT);
-        d.part = at<double>(s, mb, B_PART);
-        d.bsum = at<uint64_t>(s, mb, B_BSUM);
-        d.hist_i = at<double>(s, mb, B_HI);
-        d.hist_var = at<double>(s, mb, B_HV);
-        d.st = at<State>(s, mb, B_ST);
+        mb.base = A;
+        fill_desc(mb, d_inv, s.h_desc[i]);
+        vp_status ust = upload_member_init(mb, s.h_desc[i], stream);
+        if (ust != VP_OK) return ust;
         tree_base[i + 1] = tree_base[i] + mb.n_tree;
-        axis_base[i + 1] = axis_base[i] + D;
-        s.max_ng = std::max(s.max_ng, G);
-        if (mb.p.alpha > 0.0 && G > 1) s.any_refine = true;
-        // uniform grid (§2.3: the first iteration uses a uniform grid)
-        std::vector<double> edges((size_t)D * (G + 1));
-        std::vector<float2> tab((size_t)D * G);
-        double vol = 1.0;
-        for (int mu = 0; mu < D; ++mu) {
-            const double a = mb.lo[mu], b = mb.hi[mu];
-            double *e = &edges[(size_t)mu * (G + 1)];
-            for (int k = 0; k <= G; ++k) e[k] = a + (b - a) * (double)k / (double)G;
-            e[0] = a;
-            e[G] = b;
-            make_tab(e, G, &tab[(size_t)mu * G]);
-            vol *= (b - a);
-        }
-        State sti;
-        memset(&sti, 0, sizeof sti);
-        int e = std::ilogb(vol);
-        sti.scale_exp = -(e > 120 ? 120 : (e < -120 ? -120 : e));
-        std::vector<double> ones(mb.n_hc, 1.0);
-        CU(cudaMemcpyAsync(d.edges, edges.data(), edges.size() * 8, cudaMemcpyHostToDevice, stream));
-        CU(cudaMemcpyAsync(d.tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, stream));
-        CU(cudaMemcpyAsync((void *)d.prm, mb.prm.data(), mb.prm.size() * 8, cudaMemcpyHostToDevice, stream));
-        CU(cudaMemcpyAsync((void *)d.prm32, mb.prm32.data(), mb.prm32.size() * 4, cudaMemcpyHostToDevice, stream));
-        CU(cudaMemcpyAsync(d.dh, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, stream));
-        CU(cudaMemcpyAsync(d.st, &sti, sizeof sti, cudaMemcpyHostToDevice, stream));
-        CU(cudaStreamSynchronize(stream));  // host vectors go out of scope
+        axis_base[i + 1] = axis_base[i] + mb.p.dim;
+        s.max_ng = std::max(s.max_ng, mb.p.n_g);
+        if (mb.p.alpha > 0.0 && mb.p.n_g > 1) s.any_refine = true;
     }
+    CU(cudaStreamSynchronize(stream));
     s.n_tree_total = tree_base[n];
     s.n_axis_total = axis_base[n];
     for (auto &g : s.groups) {
@@ -661,7 +625,7 @@ static void set_destroy(Set &s) {
     cudaStreamSynchronize(s.last);
 }
 
-static vp_status launch_group(Set &s, Group &g, cudaStream_t stream) {
+vp_status vp::launch_group(const Desc *d_desc, Group &g, cudaStream_t stream) {
     cudaError_t e;
     if (g.one) {
         e = g.prec == VP_FP64
@@ -669,7 +633,7 @@ static vp_status launch_group(Set &s, Group &g, cudaStream_t stream) {
                 : launch_sample_one_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, g.cs, stream, g.args1);
     } else {
         SampleArgs a;
-        a.desc = s.d_desc;
+        a.desc = d_desc;
         a.members = g.d_members;
         a.chunk_base = g.d_chunk_base;
         a.head = g.d_head;
@@ -708,7 +672,7 @@ static vp_status time_group(Set &s, Group &g, cudaStream_t stream, float *best_m
             CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base, g.d_head,
                              g.task, stream));
         CU(cudaEventRecord(s.ev0, stream));
-        vp_status st = launch_group(s, g, stream);
+        vp_status st = launch_group(s.d_desc, g, stream);
         if (st != VP_OK) return st;
         CU(cudaEventRecord(s.ev1, stream));
         CU(cudaEventSynchronize(s.ev1));
@@ -751,7 +715,7 @@ static TuneKey tune_key(const Set &s, const Group &g, double expect) {
     return k;
 }
 
-static void set_task(Group &g, double expect) {
+void vp::set_task(Group &g, double expect) {
     const uint32_t wchunk = 32u * (uint32_t)g.r;
     const double per = expect / ((double)g.blocks * 8.0);
     g.task = (uint32_t)std::min(1.0e9, std::max((double)(8 * wchunk), per));
@@ -873,7 +837,7 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
     const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     CU(cudaEventRecordWithFlags(s.ev0, stream, ev_flags));
     for (size_t gi = 0; gi < s.groups.size(); ++gi) {
-        vp_status st = launch_group(s, s.groups[gi], stream);
+        vp_status st = launch_group(s.d_desc, s.groups[gi], stream);
         if (st != VP_OK) return st;
     }
     CU(cudaEventRecordWithFlags(s.ev1, stream, ev_flags));
@@ -921,7 +885,7 @@ static vp_status set_step(Set &s, cudaStream_t stream) {
 }
 
 // §2.5 combination of iterations j >= discard.
-static void combine(const double *I, const double *V, int n, int discard, vp_result_t *r) {
+void vp::combine(const double *I, const double *V, int n, int discard, vp_result_t *r) {
     int first = discard < 0 ? 0 : discard;
     r->n_it = n > first ? n - first : 0;
     r->dof = r->n_it > 0 ? r->n_it - 1 : 0;

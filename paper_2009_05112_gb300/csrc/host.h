@@ -1,0 +1,115 @@
+// host.h -- host-side internals shared by the translation units of libvegasp
+// (the context/batch API in api.cu and the request server in server.cu).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sample_impl.cuh"
+#include "vp_internal.cuh"
+
+namespace vp {
+
+// kernel launchers (adapt.cu)
+cudaError_t launch_chunks(const Desc *, const uint32_t *, int, uint64_t *, uint32_t *, uint32_t,
+                          cudaStream_t);
+cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
+cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t, int initial);
+cudaError_t launch_refine(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
+
+// the calling thread's last error message (vp_last_error)
+extern thread_local std::string g_err;
+vp_status fail(vp_status s, const char *fmt, ...);
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::vp::fail(VP_ECUDA, "%s failed: %s (%s:%d)", #call,                 \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);              \
+    } while (0)
+
+// Device memory through the allocator set by vp_set_allocator, else
+// cudaMallocAsync on the given stream.
+struct DevMem {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    vp_alloc_fn alloc = nullptr;
+    vp_free_fn free_fn = nullptr;
+    void *user = nullptr;
+};
+vp_status dev_alloc(DevMem &m, size_t bytes, cudaStream_t s);
+void dev_free(DevMem &m, cudaStream_t s);
+
+// One integral: validated parameters, derived sizes and where its buffers sit.
+struct Member {
+    vp_params p;
+    int kind;
+    std::vector<double> lo, hi, prm;
+    std::vector<float> prm32;
+    int64_t n_st;
+    uint64_t n_hc;
+    uint32_t n_tree;
+    int hist_cap;
+    int bucket;
+    bool exact;            // dim equals the bucket's dimension
+    char *base = nullptr;  // device memory the offsets below are relative to
+    size_t off_bytes[20];  // offsets of the buffers from base
+};
+
+// One sampling launch: the integrals of one kernel instantiation.
+struct Group {
+    int bucket, kind, prec;
+    bool exact;
+    std::vector<uint32_t> members;
+    uint32_t *d_members = nullptr;
+    uint64_t *d_chunk_base = nullptr;
+    uint32_t *d_head = nullptr;      // d_head[0] queue head, d_head[1] exit counter
+    int threads = 256, r = 8, blocks = 1, hist_shared = 0, hist_words = 0, prm_words = 0;
+    uint32_t task = 0;
+    size_t smem = 0;
+    bool one = false;  // a single integral: the cluster kernel with constants in parameters
+    int cs = 1;        // CTAs per cluster (one-integral kernel)
+    SampleOne args1;
+    int occ_one = 0, occ_many = 0;  // resident CTAs per SM of each kernel
+    bool tuned = false;
+};
+
+enum {
+    B_EDGES, B_TAB, B_PRM, B_PRM32, B_NH, B_OFF, B_S1, B_S2, B_DH, B_HSUM, B_HCNT, B_PART,
+    B_BSUM, B_HI, B_HV, B_ST, B_COUNT
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T>
+T *mbuf(const Member &mb, int which) {
+    return (T *)(mb.base + mb.off_bytes[which]);
+}
+
+int bucket_of(int dim);
+// Checks one integral's parameters and fills the host side of a Member.
+vp_status validate(const vp_params *p, const vp_integrand *f, Member &mb);
+// Lays out the member's buffers from byte offset `base`; returns the end.
+size_t member_layout(Member &mb, size_t base);
+// The member's descriptor (mb.base must be set).
+void fill_desc(const Member &mb, const double *d_inv, Desc &d);
+// Uniform grid, its FP32 mirror, the integrand blobs, d_h = 1 and the initial
+// state, copied to the member's (zeroed) buffers on `stream`.
+vp_status upload_member_init(const Member &mb, const Desc &d, cudaStream_t stream);
+// Table of 1/n, n < kInvTab (IEEE division on the host), for the descriptors.
+void inv_table(std::vector<double> &inv);
+// Shared memory and residency of a task-kernel group from its members.
+// (g.members index m)
+vp_status group_config_many(const std::vector<const Member *> &m, Group &g, int n_sm);
+// Size of the tasks for `expect` samples over the group's blocks.
+void set_task(Group &g, double expect);
+// One sampling launch of a group.
+vp_status launch_group(const Desc *d_desc, Group &g, cudaStream_t stream);
+// §2.5 combination of iterations j >= discard.
+void combine(const double *I, const double *V, int n, int discard, vp_result_t *r);
+
+}  // namespace vp

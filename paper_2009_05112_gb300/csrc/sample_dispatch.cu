@@ -1,4 +1,7 @@
 // sample_dispatch.cu -- host-side choice among the sampling kernel instantiations.
+#include <mutex>
+#include <vector>
+
 #include "sample_impl.cuh"
 
 namespace vp {
@@ -64,13 +67,34 @@ cudaError_t launch_sample_one_f64(int bucket, bool exact, int kind, dim3 grid, d
     return launch_one(true, bucket, false, kind, grid, block, smem, cs, s, a);
 }
 
+// The limit is a property of the kernel for the whole process, shared by every
+// context, batch and server that launches it: it only ever grows, so that
+// configuring a kernel for small launches cannot break another user's larger ones.
+static std::mutex g_smem_mu;
+struct SmemLimit {
+    const void *kernel;
+    int device, bytes;
+};
+static std::vector<SmemLimit> g_smem_limit;
+
 static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool one, int max_smem) {
     const void *k = pick(f64, bucket, exact, kind, one);
     if (!k) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    int *cur = nullptr;  // the attribute is per device
+    for (auto &l : g_smem_limit)
+        if (l.kernel == k && l.device == dev) cur = &l.bytes;
+    if (cur && *cur >= max_smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess && one)  // clusters of up to 16 CTAs
         e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    return e;
+    if (e != cudaSuccess) return e;
+    if (cur) *cur = max_smem;
+    else g_smem_limit.push_back({k, dev, max_smem});
+    return cudaSuccess;
 }
 cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem) {
     return smem_config(false, bucket, exact, kind, one, max_smem);

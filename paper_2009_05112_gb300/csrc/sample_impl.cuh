@@ -54,7 +54,7 @@ template <> struct Real<false> { typedef float T; };
 //  BALL     per peak {a, r^2, 0, 0, c[D], pad}          f = sum a [|x-c|^2 < r^2]
 //  EXPNORM  per peak {a, s log2(e), 0, 0, c[D], pad}    f = sum a 2^(-k |x-c|)
 //           (peaks padded to a multiple of 4 floats for 16-byte shared loads)
-//  POSTERIOR {n, P, kN, kW, lcN, lcW, kprior, logref2, y[n], A[n][P]} in log2 units
+//  POSTERIOR {n, P, G, kN, kW, lcN, lcW, kprior, logref2, y[n], A[n][P]} in log2 units
 // ---------------------------------------------------------------------------
 template <int DMAX>
 __device__ __forceinline__ double f_peaks64(int kind, const double *p, int K, int dim,
@@ -111,17 +111,18 @@ __device__ __forceinline__ float f_peaks32(int kind, const float *p, int K, int 
 
 template <int DMAX>
 __device__ __forceinline__ double f_post64(const double *p, int dim, const double (&x)[DMAX]) {
-    const int n = (int)p[0], npar = (int)p[1];
-    const double sy = p[2], pw = p[3], log_ref = p[4];
-    const double *y = p + 5;
-    const double *A = p + 5 + n;
+    const int n = (int)p[0], npar = (int)p[1], ngrp = (int)p[2];
+    const double sy = p[3], pw = p[4], log_ref = p[5];
+    const double *y = p + 6;
+    const double *A = p + 6 + n;
     const double s2pi = sqrt(6.283185307179586476925286766559);  // sqrt(2 pi)
-    double w = 0.0;
-#pragma unroll
-    for (int mu = 0; mu < DMAX; ++mu)
-        if (mu == npar) w = x[mu];
     double logl = 0.0;
+    int g = 0;  // i mod G
     for (int i = 0; i < n; ++i) {
+        double w = 0.0;
+#pragma unroll
+        for (int mu = 0; mu < DMAX; ++mu)
+            if (mu == npar + g) w = x[mu];
         double model = 0.0;
 #pragma unroll
         for (int m = 0; m < DMAX; ++m)
@@ -130,6 +131,7 @@ __device__ __forceinline__ double f_post64(const double *p, int dim, const doubl
         const double nar = (1.0 - w) / (s2pi * sy) * exp(-r * r / (2.0 * sy * sy));
         const double wid = w / (s2pi * 10.0 * sy) * exp(-r * r / (200.0 * sy * sy));
         logl += log(nar + wid);
+        if (++g == ngrp) g = 0;
     }
     double lp = 0.0;
 #pragma unroll
@@ -139,29 +141,32 @@ __device__ __forceinline__ double f_post64(const double *p, int dim, const doubl
     return exp(logl + lp - log_ref);
 }
 
+// FP32: the points are visited group by group (points g, g + G, g + 2G, ...
+// share the weight w_g), so that each w_g is read from a fixed register.
 template <int DMAX>
 __device__ __forceinline__ float f_post32(const float *p, int dim, const float (&x)[DMAX]) {
-    const int n = (int)p[0], npar = (int)p[1];
-    const float kN = p[2], kW = p[3], lcN = p[4], lcW = p[5], kpr = p[6], lref = p[7];
-    const float *y = p + 8;
-    const float *A = p + 8 + n;
-    float w = 0.0f;
-#pragma unroll
-    for (int mu = 0; mu < DMAX; ++mu)
-        if (mu == npar) w = x[mu];
-    const float lw1 = lg2_approx(1.0f - w), lw = lg2_approx(w);
+    const int n = (int)p[0], npar = (int)p[1], ngrp = (int)p[2];
+    const float kN = p[3], kW = p[4], lcN = p[5], lcW = p[6], kpr = p[7], lref = p[8];
+    const float *y = p + 9;
+    const float *A = p + 9 + n;
     float acc = 0.0f;
-    for (int i = 0; i < n; ++i) {
-        const float *a = A + i * npar;
-        float model = 0.0f;
 #pragma unroll
-        for (int m = 0; m < DMAX; ++m)
-            if (m < npar) model = fmaf(a[m], x[m], model);
-        const float r = y[i] - model;
-        const float r2 = r * r;
-        const float nar = ex2_approx(fmaf(-kN, r2, lcN + lw1));
-        const float wid = ex2_approx(fmaf(-kW, r2, lcW + lw));
-        acc += lg2_approx(nar + wid);
+    for (int mu = 1; mu < DMAX; ++mu) {
+        if (mu < npar || mu >= npar + ngrp) continue;
+        const float w = x[mu];
+        const float lw1 = lg2_approx(1.0f - w), lw = lg2_approx(w);
+        for (int i = mu - npar; i < n; i += ngrp) {
+            const float *a = A + i * npar;
+            float model = 0.0f;
+#pragma unroll
+            for (int m = 0; m < DMAX; ++m)
+                if (m < npar) model = fmaf(a[m], x[m], model);
+            const float r = y[i] - model;
+            const float r2 = r * r;
+            const float nar = ex2_approx(fmaf(-kN, r2, lcN + lw1));
+            const float wid = ex2_approx(fmaf(-kW, r2, lcW + lw));
+            acc += lg2_approx(nar + wid);
+        }
     }
     float c2 = 0.0f;
 #pragma unroll
@@ -576,7 +581,10 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
         }
         int idx[DMAX];
         T v;
-        bool big = false;  // FP32: |v| beyond 2^60 (v^2 would overflow), handled in FP64
+        // FP32: a sample with |v| outside [2^-60, 2^60) (v^2 would overflow or
+        // underflow FP32, e.g. in the first iteration, before the scale has
+        // adapted to an integral far from the box volume) takes its own FP64 terms
+        bool big = false;
         double vbig = 0.0;
         if (F64) {
             double x[DMAX], J, f;
@@ -586,14 +594,16 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
             float x[DMAX], Jm, f;
             int Je;
             point32<DMAX, EXACT, KIND>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je, f);
-            v = (T)scale2(Jm * f, Je + sexp);
-            if (!(fabsf((float)v) < 1.152921504606847e18f) && isfinite(Jm * f)) {
-                // a rare sample far above the iteration's scale: its own FP64 terms
+            const float jf = Jm * f;  // normal or zero: Jm in [1, 2), f flushed to zero
+            const int ev = ((__float_as_int(jf) >> 23) & 0xff) - 127 + Je + sexp;  // exponent of v
+            if (jf != 0.0f && isfinite(jf) && (ev >= 60 || ev < -60)) {
                 big = true;
                 vbig = ldexp((double)Jm * (double)f, Je);  // J f, unscaled
                 red_add(P.S1 + h, vbig);
                 red_add(P.S2 + h, vbig * vbig);
                 v = (T)0;
+            } else {
+                v = (T)scale2(jf, Je + sexp);
             }
         }
         const T v2 = v * v;

@@ -37,13 +37,22 @@ struct State {
     uint64_t n_samples;   // sum_h n_h of the current allocation
     uint64_t n_eval_total;// integrand evaluations over all iterations
     double last_i, last_var;
+    // served requests: running §2.5 sums over the iterations j >= discard
+    double cw, cwi;       // sum 1/var_j, sum I_j/var_j
+    double zsum;          // sum of I_j over iterations with var_j = 0 (exact)
+    uint32_t n_zero;      // number of those
+    uint32_t done;        // kDone* bits once the stop rule has fired
 };
+
+// Bits of State::done and of the server's per-slot flag.
+constexpr uint32_t kDoneStop = 1u;       // the request is finished
+constexpr uint32_t kDoneConverged = 2u;  // ... because sdev <= rtol |mean|
 
 // Read-only (per iteration) description of one integral.
 struct Desc {
     int32_t dim, n_g, kind, prec;
     int32_t plus2, n_peaks;    // n_peaks: K for peak families, n points for POSTERIOR
-    int32_t n_par;             // POSTERIOR: P (= dim - 1)
+    int32_t n_par;             // POSTERIOR: P (dim = P + G)
     int32_t hist_cap;          // capacity of the iteration history
     uint32_t n_st, integral_id;
     uint32_t key0, key1;       // Philox key (seed lo, hi)
@@ -76,6 +85,12 @@ struct Desc {
     uint64_t *bsum;    // [n_tree] block sums of n_h, then block offsets
     double *hist_i, *hist_var;  // [hist_cap] iteration history
     State *st;
+    // served requests (done_out == nullptr elsewhere): stop when the §2.5
+    // combination of iterations j >= discard has sdev <= rtol |mean| after at
+    // least min_meas of them, or after stop_it iterations in all
+    double rtol;
+    int32_t discard, min_meas, stop_it, pad1;
+    uint32_t *done_out;        // the server's flag for this request's slot
 };
 
 // ---------------------------------------------------------------------------

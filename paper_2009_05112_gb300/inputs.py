@@ -10,9 +10,10 @@ Blob layouts (doubles), shared by every consumer:
 * ``GAUSS``   [K, {a_k, w_k, c_k[D]} x K]   f = sum_k a_k exp(-|x-c_k|^2 / w_k^2)
 * ``BALL``    [K, {a_k, r_k, c_k[D]} x K]   f = sum_k a_k Theta(|x-c_k| < r_k)
 * ``EXPNORM`` [K, {a_k, s_k, c_k[D]} x K]   f = sum_k a_k exp(-s_k |x-c_k|)
-* ``POSTERIOR`` [n, P, sigma_y, prior_width, log_ref, y[n], A[n][P]],
-  D = P + 1: a linear model in P coefficients (A[i][m] = m-th Legendre
-  polynomial at the i-th abscissa) plus the outlier weight w, as in App. B.
+* ``POSTERIOR`` [n, P, G, sigma_y, prior_width, log_ref, y[n], A[n][P]],
+  D = P + G: a linear model in P coefficients (A[i][m] = m-th Legendre
+  polynomial at the i-th abscissa) and G outlier weights, point i using
+  w_{i mod G}, as in App. B (G = 1: one shared w; G = n: one per point).
 """
 import math
 from dataclasses import dataclass, field
@@ -160,16 +161,19 @@ def legendre_design(xs, n_par):
 
 
 def posterior(dim=3, n_pts=50, seed=0, n_ev=10_000, n_it=15, n_g=1000, discard=5,
-              sigma_y=0.1, outlier_frac=0.1, outlier_sigma=1.0, prior_width=1.0):
-    """App. B-shaped posterior: a model with P = dim - 1 Legendre coefficients
-    (P = 2: the straight line p0 + p1 x) and an outlier weight w, n_pts synthetic
-    points with x ~ U[-1,1], y = model + N(0, sigma_y^2), a fraction of them
-    outliers with N(0, outlier_sigma^2) noise; Gaussian priors of width
+              sigma_y=0.1, outlier_frac=0.1, outlier_sigma=1.0, prior_width=1.0, n_par=2):
+    """App. B-shaped posterior: a model with n_par Legendre coefficients
+    (n_par = 2: the straight line p0 + p1 x) and G = dim - n_par outlier
+    weights (G = 1: App. B's shared w, dim 3; G = 19: its 21-parameter
+    variant with a weight per point, here point i using w_{i mod 19}), n_pts
+    synthetic points with x ~ U[-1,1], y = model + N(0, sigma_y^2), a fraction
+    of them outliers with N(0, outlier_sigma^2) noise; Gaussian priors of width
     prior_width on the coefficients, boxes of +-5 prior widths, w in [0, 1].
 
     log_ref is the largest value the log-likelihood can take,
     n_pts * log(1 / (sqrt(2 pi) sigma_y)), so that f stays below one."""
-    n_par = dim - 1
+    n_grp = dim - n_par
+    assert n_grp >= 1 and n_par >= 1
     rng = np.random.default_rng(seed)
     coef = rng.normal(0.0, 0.5 * prior_width, size=n_par)
     xs = rng.uniform(-1.0, 1.0, size=n_pts)
@@ -179,9 +183,9 @@ def posterior(dim=3, n_pts=50, seed=0, n_ev=10_000, n_it=15, n_g=1000, discard=5
     noise[bad] = rng.normal(0.0, outlier_sigma, size=int(bad.sum()))
     ys = A @ coef + noise
     log_ref = n_pts * math.log(1.0 / (math.sqrt(2.0 * math.pi) * sigma_y))
-    prm = np.concatenate([[n_pts, n_par, sigma_y, prior_width, log_ref], ys, A.ravel()])
-    lo = np.concatenate([np.full(n_par, -5.0 * prior_width), [0.0]])
-    hi = np.concatenate([np.full(n_par, 5.0 * prior_width), [1.0]])
+    prm = np.concatenate([[n_pts, n_par, n_grp, sigma_y, prior_width, log_ref], ys, A.ravel()])
+    lo = np.concatenate([np.full(n_par, -5.0 * prior_width), np.zeros(n_grp)])
+    hi = np.concatenate([np.full(n_par, 5.0 * prior_width), np.ones(n_grp)])
     return Problem("posterior_d%d" % dim, dim, POSTERIOR, np.ascontiguousarray(prm), lo, hi,
                    n_g=n_g, n_ev=n_ev, seed=seed, n_it=n_it, discard=discard,
                    meta=dict(coef=coef, xs=xs, ys=ys, outliers=bad))
@@ -204,3 +208,31 @@ def batch_mix(n=512, seed=1, n_g=500, n_it=15):
                              np.ones(dim), n_g=n_g, n_ev=n_ev, seed=seed, n_it=n_it,
                              integral_id=b, exact=gauss_exact(amps, ws, cs)))
     return probs
+
+
+# Stop rule of the request stream, per request dimension: warm-up iterations
+# left out of the result, least measured iterations, iteration cap.
+SERVE_RULE = {3: dict(discard=5, min_meas=3, max_it=40),
+              21: dict(discard=12, min_meas=3, max_it=60)}
+
+
+def serve_stream(n=2000, rate=200.0, seed=0, frac_d21=0.3, rtol=1e-3):
+    """A Poisson stream of integration requests (mean `rate` per second), each
+    with its own synthetic data set: 70% App. B-shaped posteriors with D = 3
+    (a line and one outlier weight) and 30% with D = 21 (a line and 19 outlier
+    weights), 50 points each, N_ev = 1e4 (D = 3) or 3e4 (D = 21) per
+    iteration, N_g = 1000, target relative error rtol.
+
+    Returns (arrival offsets in seconds, problems, stop rules)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    t = np.cumsum(gaps) - gaps[0]
+    probs, rules = [], []
+    for i in range(n):
+        dim = 21 if rng.random() < frac_d21 else 3
+        p = posterior(dim=dim, seed=int(rng.integers(1 << 31)),
+                      n_ev=10_000 if dim == 3 else 30_000)
+        probs.append(Problem("req%05d" % i, dim, POSTERIOR, p.prm, p.lo, p.hi, n_g=1000,
+                             n_ev=p.n_ev, seed=int(rng.integers(1 << 62)), integral_id=i))
+        rules.append(dict(SERVE_RULE[dim], rtol=rtol))
+    return t, probs, rules

@@ -52,6 +52,30 @@ class vp_result_t(ctypes.Structure):
                 ("last_i", ctypes.c_double), ("last_sdev", ctypes.c_double)]
 
 
+class vp_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_int64), ("max_active", ctypes.c_int)]
+
+
+class vp_request(ctypes.Structure):
+    _fields_ = [("p", vp_params), ("f", vp_integrand), ("rtol", ctypes.c_double),
+                ("discard", ctypes.c_int), ("min_meas", ctypes.c_int), ("tag", ctypes.c_uint64)]
+
+
+class vp_served(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("converged", ctypes.c_int), ("n_iter", ctypes.c_int), ("r", vp_result_t),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class vp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("finished", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("active", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("bytes_peak", ctypes.c_int64),
+                ("mem_budget", ctypes.c_int64), ("n_eval", ctypes.c_int64),
+                ("busy_s", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -92,6 +116,15 @@ _SIGS = {
     "vp_batch_size": [_P, ctypes.POINTER(ctypes.c_int)],
     "vp_batch_destroy": [_P],
     "vp_batch_history": [_P, ctypes.c_int, ctypes.c_int, _P, _P],
+    "vp_server_create": [ctypes.POINTER(vp_server_config), _P, ctypes.POINTER(_P)],
+    "vp_server_submit": [_P, ctypes.POINTER(vp_request), ctypes.POINTER(ctypes.c_uint64)],
+    "vp_server_step": [_P, ctypes.POINTER(ctypes.c_int)],
+    "vp_server_start": [_P],
+    "vp_server_stop": [_P],
+    "vp_server_poll": [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int)],
+    "vp_server_wait": [_P, ctypes.c_int64, ctypes.c_double],
+    "vp_server_get_stats": [_P, ctypes.POINTER(vp_server_stats)],
+    "vp_server_destroy": [_P],
 }
 
 _lib = None
@@ -111,6 +144,8 @@ def lib():
             fn.restype = ctypes.c_int
         L.vp_last_error.argtypes = []
         L.vp_last_error.restype = ctypes.c_char_p
+        L.vp_server_clock.argtypes = []
+        L.vp_server_clock.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -387,3 +422,83 @@ class Batch:
         if st not in (VP_OK, VP_ENONFINITE):
             check(st)
         return [_result_dict(out[i], VP_OK) for i in range(self.n)]
+
+
+def _params_of(prob, precision, max_it, keep):
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(prob.lo, np.float64), (prob.dim,)))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(prob.hi, np.float64), (prob.dim,)))
+    prm = np.ascontiguousarray(prob.prm, np.float64)
+    keep += [lo, hi, prm]
+    p = vp_params(prob.dim, lo.ctypes.data_as(_dp), hi.ctypes.data_as(_dp), prob.n_g,
+                  int(prob.n_ev), float(prob.alpha), float(prob.beta),
+                  int(prob.seed) & (2 ** 64 - 1), int(prob.integral_id), int(precision),
+                  int(bool(prob.plus2)), int(prob.n_st), int(max_it))
+    f = vp_integrand(int(prob.kind), prm.size, prm.ctypes.data_as(_dp))
+    return p, f
+
+
+def clock():
+    """The server's clock (seconds, steady)."""
+    return lib().vp_server_clock()
+
+
+class Server:
+    """A stream of integration requests iterated together (a vp_server)."""
+
+    def __init__(self, mem_budget=0, max_active=0, stream=None):
+        cfg = vp_server_config(int(mem_budget), int(max_active))
+        self.stream = ctypes.c_void_p(0) if stream is None else ctypes.c_void_p(stream)
+        h = ctypes.c_void_p()
+        check(lib().vp_server_create(ctypes.byref(cfg), self.stream, ctypes.byref(h)))
+        self.s = h
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().vp_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, prob, rtol, discard=0, min_meas=1, max_it=0, precision=VP_FP32, tag=0):
+        keep = []
+        p, f = _params_of(prob, precision, max_it, keep)
+        q = vp_request(p, f, float(rtol), int(discard), int(min_meas), int(tag) & (2 ** 64 - 1))
+        rid = ctypes.c_uint64()
+        check(lib().vp_server_submit(self.s, ctypes.byref(q), ctypes.byref(rid)))
+        return rid.value
+
+    def step(self):
+        n = ctypes.c_int()
+        check(lib().vp_server_step(self.s, ctypes.byref(n)))
+        return n.value
+
+    def start(self):
+        check(lib().vp_server_start(self.s))
+
+    def stop(self):
+        check(lib().vp_server_stop(self.s))
+
+    def poll(self, max_n=4096):
+        out = (vp_served * max_n)()
+        n = ctypes.c_int()
+        check(lib().vp_server_poll(self.s, max_n, out, ctypes.byref(n)))
+        res = []
+        for k in range(n.value):
+            o = out[k]
+            d = _result_dict(o.r, o.status)
+            d.update(id=o.id, tag=o.tag, converged=bool(o.converged), n_iter=o.n_iter,
+                     t_submit=o.t_submit, t_admit=o.t_admit, t_done=o.t_done)
+            res.append(d)
+        return res
+
+    def wait(self, finished, timeout_s=60.0):
+        check(lib().vp_server_wait(self.s, int(finished), float(timeout_s)))
+
+    def stats(self):
+        o = vp_server_stats()
+        check(lib().vp_server_get_stats(self.s, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in vp_server_stats._fields_}

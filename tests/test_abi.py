@@ -24,7 +24,7 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:vp_status|const char \*|void)\s*\**\s*(vp_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:vp_status|const char \*|void|double)\s*\**\s*(vp_\w+)\s*\(",
                                  text, flags=re.M)))
 
 
@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(lib):
         assert name in exported, name
         assert hasattr(lib, name)
     # the binding wraps every declared entry point
-    assert set(declared_functions()) <= set(vegasp._SIGS) | {"vp_last_error"}
+    assert set(declared_functions()) <= set(vegasp._SIGS) | {"vp_last_error", "vp_server_clock"}
 
 
 def test_build_targets_sm_103a():
@@ -106,6 +106,14 @@ def test_null_context_is_an_error(lib):
     r = vegasp.vp_result_t()
     assert lib.vp_result(None, 0, ctypes.byref(r)) == vegasp.VP_EINVAL
     assert lib.vp_map_destroy(None) == vegasp.VP_OK
+    # the server's calls check their handle before anything else
+    assert lib.vp_server_submit(None, None, None) == vegasp.VP_EINVAL
+    assert lib.vp_server_step(None, None) == vegasp.VP_EINVAL
+    assert lib.vp_server_start(None) == vegasp.VP_EINVAL
+    n = ctypes.c_int()
+    assert lib.vp_server_poll(None, 0, None, ctypes.byref(n)) == vegasp.VP_EINVAL
+    assert lib.vp_server_destroy(None) == vegasp.VP_OK
+    assert lib.vp_server_clock() > 0.0
 
 
 def test_product_never_touches_the_oracle():

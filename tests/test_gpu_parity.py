@@ -306,6 +306,26 @@ def test_four_peaks_d8_fp32_within_3_sigma_of_oracle():
     assert np.all(np.abs(np.sqrt(Vg) / np.sqrt(np.array(o.var)) - 1) < 0.05)
 
 
+@pytest.mark.parametrize("amp", [1e-30, 1e-12, 1e12, 1e30])
+def test_fp32_integrals_far_from_the_box_volume(amp):
+    """The first iteration scales J f by the box volume only; an integral 1e30
+    away from it squares to values beyond FP32 (v^2 under- or overflows).  Those
+    samples take FP64 terms, so the FP32 iterations still track the FP64 oracle
+    on the same samples, sigma_j included."""
+    dim = 4
+    blob = inputs.gauss_blob([amp], [0.15], [np.full(dim, 0.4)])
+    prob = inputs.Problem("tiny", dim, inputs.GAUSS, blob, np.zeros(dim), np.ones(dim), n_g=100,
+                          n_ev=20_000, seed=5)
+    g = gpu_of(prob, 1).run(4)
+    o = oracle_of(prob).run(4)
+    I, Vg = g.history()
+    assert np.all(Vg > 0)
+    np.testing.assert_allclose(I[0], o.I[0], rtol=1e-5)
+    np.testing.assert_allclose(Vg[0], o.var[0], rtol=1e-4)
+    assert np.all(np.abs(I - np.array(o.I)) < 0.25 * np.sqrt(np.array(o.var)))
+    assert np.all(np.abs(np.sqrt(Vg) / np.sqrt(np.array(o.var)) - 1) < 0.05)
+
+
 # ---------------------------------------------------------------------------
 # full size (20-D ball, N_ev = 1e7): sampled outputs the oracle computes one by one
 # ---------------------------------------------------------------------------

@@ -208,7 +208,7 @@ def test_posterior_integrand_closed_form():
     sy, pw, log_ref = 0.3, 1.0, 0.25
     ys = np.array([0.4, -0.2])
     A = np.array([[1.0, 0.5], [1.0, -0.8]])  # asymmetric: a transposed index changes the value
-    prm = np.concatenate([[2, 2, sy, pw, log_ref], ys, A.ravel()])
+    prm = np.concatenate([[2, 2, 1, sy, pw, log_ref], ys, A.ravel()])
     # closed form: int_0^1 dw prod_i [(1-w) N_i + w W_i]
     #   = N1 N2 / 3 + (N1 W2 + W1 N2) / 6 + W1 W2 / 3,  each over R^2 in c.
     def gauss_term(s1, s2):
@@ -227,6 +227,16 @@ def test_posterior_integrand_closed_form():
     X = np.stack([C0, C1, W], -1).reshape(-1, 3)
     val = oracle.integrand_many(3, 3, prm, X) @ np.einsum("i,j,k->ijk", wg, wg, ww).ravel()
     assert val == pytest.approx(exact, rel=2e-5)  # prior mass beyond +-5 widths ~ 1e-6
+    # one weight per point (G = 2, D = 4): the w integrals factor,
+    # int_0^1 [(1-w) N + w W] dw = (N + W)/2 for each point
+    prm2 = np.concatenate([[2, 2, 2, sy, pw, log_ref], ys, A.ravel()])
+    exact2 = 0.25 * (gauss_term(n_, n_) + gauss_term(n_, w_) + gauss_term(w_, n_) +
+                     gauss_term(w_, w_)) * math.exp(-log_ref)
+    C0, C1, W0, W1 = np.meshgrid(xg, xg, wq, wq, indexing="ij")
+    X2 = np.stack([C0, C1, W0, W1], -1).reshape(-1, 4)
+    val2 = oracle.integrand_many(3, 4, prm2, X2) @ np.einsum("i,j,k,l->ijkl", wg, wg, ww,
+                                                              ww).ravel()
+    assert val2 == pytest.approx(exact2, rel=2e-5)
 
 
 # ---------------------------------------------------------------------------
