@@ -44,6 +44,9 @@ def parse():
                          "integrals per launch against one at a time; serve: continuous batching "
                          "of a Poisson request stream")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    ap.add_argument("--launch", default=None,
+                    help="fix the sampling launch shape instead of autotuning it: "
+                         "scheme:blocks:threads:cluster:run with scheme static-cluster or tasks")
     return ap.parse_args()
 
 
@@ -228,6 +231,11 @@ def run_ours(args):
     prob.integral_id = rank
     stream = torch.cuda.current_stream()
     g = vegasp.Integrator.from_problem(prob, precision=vegasp.VP_FP32)
+    launch = None
+    if args.launch:
+        sch, blk, thr, cl, run = args.launch.split(":")
+        launch = (sch, int(blk), int(thr), int(cl), int(run))
+        g.set_tuning(*launch)
     for _ in range(args.warmup):
         g.step()
     n0 = g.result()["n_eval"]
@@ -266,6 +274,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g2 = vegasp.Integrator.from_problem(prob, precision=vegasp.VP_FP32)
+    if launch:
+        g2.set_tuning(*launch)
     for _ in range(args.steps):
         g2.step()
         r2 = g2.result()

@@ -93,8 +93,10 @@ typedef struct {
     uint32_t integral_id; /* Philox counter word 3: distinguishes integrals sharing a seed */
     int precision;      /* VP_FP64: map, integrand and moments in FP64.
                            VP_FP32: map and integrand in FP32, per-hypercube moments
-                           Kahan-compensated FP32, flushed to FP64; estimate,
-                           reallocation and refinement always FP64. */
+                           Kahan-compensated FP32, flushed to FP64; d_h = sigma_h^beta
+                           from the FP64 variance through FP32 log2/exp2 (relative
+                           error ~1e-6); the estimate, the sums over hypercubes,
+                           the reallocation quotient and the refinement stay FP64. */
     int plus2;          /* 0: n_h = max(2, N_ev d_h/sum d); 1: N_ev d_h/sum d + 2 (§3 Eq. nh) */
     int n_st;           /* 0: N_st = floor((N_ev/4)^(1/D)) (§3 Eq. Nst_vegasp),
                            computed exactly; > 0: use this many strata per axis */
@@ -188,8 +190,19 @@ vp_status vp_last_sample_ms(vp_ctx *ctx, float *ms);
 /* Launch shape of the sampling kernel chosen by the autotuner (which runs at
  * the first vp_iterate/vp_step): scheme 0 = static balanced split with
  * clusters of `cluster` CTAs, 1 = dynamic tasks with `run` samples per thread
- * per chunk; `blocks` CTAs of 256 threads. */
-vp_status vp_get_tuning(vp_ctx *ctx, int *scheme, int *blocks, int *cluster, int *run);
+ * per chunk; `blocks` CTAs of `threads` threads. */
+vp_status vp_get_tuning(vp_ctx *ctx, int *scheme, int *blocks, int *threads, int *cluster,
+                        int *run);
+/* Fixes the sampling kernel's launch shape instead of letting the autotuner
+ * choose it (reproducible timing and profiling; no counterpart in the paper,
+ * the shape does not change any result beyond FP summation order).
+ * Arguments as in vp_get_tuning: scheme 0 requires all `blocks` CTAs of
+ * `threads` (256, 512 or 768, within the kernel's limit) resident at once, in
+ * clusters of `cluster` (1, 2, 4, 8; > 1 only with shared-memory histograms);
+ * scheme 1 takes threads = 256 and cluster = 1; run in 1..64.  Synchronises
+ * the context's last stream; a step graph captured before is rebuilt at the
+ * next vp_step.  VP_EINVAL (context unchanged) for shapes that cannot run. */
+vp_status vp_set_tuning(vp_ctx *ctx, int scheme, int blocks, int threads, int cluster, int run);
 
 /* ---- batches: many independent integrals per launch ----------------------- */
 /* A batch iterates n independent integrals together (each with its own box,

@@ -13,7 +13,7 @@
 //   k_alloc     a7: n_h = max(2, floor(N_ev d_h / sum d)) (§3 Eq. nh; or + 2;
 //               a quotient within 2^-50 q below an integer counts as that
 //               integer; the first allocation is always the equal split),
-//               block sums of n_h, then (last block) the block offsets;
+//               sums of n_h over kSubH hypercubes, then (last CTA) their offsets;
 //   k_offsets   a7: exclusive offsets off[h] = sum_{h' < h} n_h';
 //   k_refine    a8 on one axis (§2.3): d_i = hsum_i / hcnt_i, smoothing
 //               (7,1)/(1,6,1)/(1,7) over 8, normalisation by sum d_i,
@@ -84,14 +84,6 @@ __global__ void k_chunks(const Desc *desc, const uint32_t *members, int n_group,
 
 struct D3 { double a, b, c; };
 
-// floor(q) for 0 <= q < 2^52 without FP64 <-> integer conversions (slow on
-// this part): q + 2^52 rounded down holds floor(q) in its low mantissa bits.
-__device__ __forceinline__ double floor_pos(double q, uint64_t *iq) {
-    const double big = __dadd_rd(q, 4503599627370496.0);  // 2^52
-    *iq = (uint64_t)__double_as_longlong(big) & ((1ull << 52) - 1);
-    return big - 4503599627370496.0;
-}
-
 // d_h = sigma_h^beta; beta = 0 and 1 exactly; 1/2 and 3/4 (the paper's
 // default) through square roots, within an ulp or two of pow.
 __device__ __forceinline__ double damp(double sigma, double beta) {
@@ -100,6 +92,31 @@ __device__ __forceinline__ double damp(double sigma, double beta) {
     if (beta == 0.5) return sqrt(sigma);
     if (beta == 0.75) return sqrt(sigma * sqrt(sigma));
     return pow(sigma, beta);
+}
+
+// d_h on the FP32 path: sigma_h^beta = Omega^beta var^(beta/2) (§3 Eq. dh),
+// var^(beta/2) from the exponent and mantissa bits of var with the FP32 log2
+// and exp2 units (relative error ~1e-6; the FP64 path takes damp()).  On this
+// part three FP64 square roots per hypercube would cost more than the
+// sampling of a few of its samples.  var >= 0 and finite.
+__device__ __forceinline__ double damp_var32(double var, const Desc &d) {
+    if ((uint64_t)__double_as_longlong(d.beta) == 0ull) return 1.0;  // beta = 0: d = 1
+    uint64_t b = (uint64_t)__double_as_longlong(var);
+    if (b == 0ull) return 0.0;
+    int E = (int)((b >> 52) & 0x7ffu);
+    if (E == 0x7ff) return var;  // inf or NaN propagates (the iteration is flagged)
+    if (E == 0) {  // subnormal: scale by 2^64 (exact)
+        b = (uint64_t)__double_as_longlong(var * 18446744073709551616.0);
+        E = (int)((b >> 52) & 0x7ffu) - 64;
+    }
+    E -= 1023;
+    const float m = __uint_as_float(0x3f800000u | (uint32_t)((b >> 29) & 0x7fffffu));  // [1, 2)
+    const float Ef = (float)E;                            // exact
+    const float p = d.half_beta_hi * Ef;
+    const float err = fmaf(d.half_beta_hi, Ef, -p);       // p + err = hi E exactly
+    const float fl = floorf(p);                           // exact (|p| < 2^23)
+    const float y = (p - fl) + err + fmaf(d.half_beta_lo, Ef, d.half_beta_hi * lg2_approx(m));
+    return f2d_pow2(ex2_approx(y), (int)fl) * d.omega_beta;
 }
 
 // ---------------------------------------------------------------------------
@@ -139,10 +156,13 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
         d.s1[qh] = 0.0;
         d.s2[qh] = 0.0;
         double var = m2 - m1 * m1;
-        var = var < 0.0 ? 0.0 : var;
+        {  // a rounding-negative variance (or -0) is zero; a NaN stays NaN
+            const long long vb = __double_as_longlong(var);
+            if (vb < 0ll && (vb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) var = 0.0;
+        }
         v.a = om * m1;
         v.b = om * om * var * inv_n1;
-        v.c = damp(om * sqrt(var), d.beta);
+        v.c = d.prec == VP_FP32 ? damp_var32(var, d) : damp(om * sqrt(var), d.beta);
         d.dh[h] = v.c;
     } else if (mode == 1) {
         v.c = damp(d.dh[h], d.beta);
@@ -306,95 +326,154 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// k_alloc: n_h for 1024 hypercubes per block (256 threads x 4), block sum of
-// n_h; the last block of each integral turns the block sums into block
-// offsets and records the total.  Skipped (allocation kept) when sum_d is not
-// finite; the status flag records it.
+// Floor of a double 0 <= q < 2^52 from its bits (no FP64 instructions: they
+// are scarce on this part), with two tests on the distance to the integers:
+// near -- q is within 2^-40 q of an integer (the reciprocal product below is
+// within a few ulp of the IEEE quotient, so only such q need the division);
+// tie  -- q lies within 2^-50 q below an integer, i.e. exactly
+//         (floor(q) + 1) - q <= q 2^-50, the test of the allocation reading.
+// With q = M 2^(e - 52), M in [2^52, 2^53): distances are counted in units
+// of 2^(e - 52) and q itself is M units, so "within c q" is "<= floor(c M)".
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_alloc(const Desc *desc, const uint32_t *tree_base,
-                                               int n_int, int initial) {
-    __shared__ unsigned long long s_sum;
+struct FloorBits {
+    uint64_t iq;
+    bool near, tie;
+};
+
+__device__ __forceinline__ FloorBits floor_bits(double q) {
+    FloorBits r = {0ull, false, false};
+    const uint64_t b = (uint64_t)__double_as_longlong(q);
+    if (b == 0ull) return r;
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    const uint64_t M = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+    if (e >= 52) {  // an integer (not reached: q < 2^32 here)
+        r.iq = M << (e - 52);
+        return r;
+    }
+    uint64_t up;  // distance to the next integer, in units
+    if (e >= 0) {
+        const int sh = 52 - e;
+        r.iq = M >> sh;
+        const uint64_t frac = M & ((1ull << sh) - 1ull);
+        up = (1ull << sh) - frac;
+        r.near = frac <= (M >> 40);
+    } else if (e == -1) {  // q in [1/2, 1): the next integer is 1 = 2^53 units
+        up = (1ull << 53) - M;
+    } else {
+        return r;  // q < 1/2: floor 0, far from both integers
+    }
+    r.near = r.near || up <= (M >> 40);
+    r.tie = up <= (M >> 50);
+    return r;
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((uint64_t)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+// n_h of one hypercube (§3 Eq. nh with the library's reading): max(2,
+// floor(N_ev d_h / sum d)), or floor(.) + 2; the equal split when sum d = 0 or
+// on the first allocation.  The quotient is the IEEE one, (N_ev d_h) then / sum d.
+__device__ __forceinline__ uint32_t alloc_one(const Desc &d, double dh, double n_ev_d,
+                                              double sum_d, double inv_sum, int initial) {
+    uint64_t iq;
+    if (__double_as_longlong(sum_d) > 0ll) {  // sum d > 0 (sum_d is finite here)
+        const double num = __dmul_rn(n_ev_d, dh);
+        FloorBits f = floor_bits(num * inv_sum);
+        iq = f.iq;
+        // (a zero numerator is exact; below 2 - tol the max(2, .) decides)
+        const uint64_t qb = (uint64_t)__double_as_longlong(num * inv_sum);
+        const bool above = qb > 0x3FF8000000000000ull;  // q > 1.5
+        if ((uint64_t)__double_as_longlong(num) != 0ull && (d.plus2 || above) && f.near) {
+            f = floor_bits(__ddiv_rn(num, sum_d));
+            iq = f.iq + (f.tie ? 1ull : 0ull);
+        }
+    } else {
+        const FloorBits f = floor_bits(__ddiv_rn(n_ev_d, (double)d.n_hc));
+        iq = f.iq + (f.tie ? 1ull : 0ull);
+    }
+    if (d.plus2 && !initial) return (uint32_t)iq + 2u;
+    return iq > 2ull ? (uint32_t)iq : 2u;
+}
+
+// Exclusive scan of one value per thread over a CTA of 256 threads; returns
+// the exclusive prefix and (in *total) the CTA's sum.
+__device__ __forceinline__ unsigned long long cta_exclusive_scan(unsigned long long v,
+                                                                 unsigned long long *s_w,
+                                                                 unsigned long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    unsigned long long base = 0ull, all = 0ull;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const unsigned long long x = s_w[w];
+        if (w < warp) base += x;
+        all += x;
+    }
+    __syncthreads();  // s_w may be reused
+    *total = all;
+    return base + inc - v;
+}
+
+// ---------------------------------------------------------------------------
+// k_alloc: n_h, one hypercube per thread, kSub CTAs of kSubH hypercubes per
+// block of kTreeBlock (so the FP64 work spreads over the whole GPU); each CTA
+// stores its sum of n_h and the last CTA of each integral turns those sums
+// into offsets (integers: any order is exact) and records the total.
+// Skipped (allocation kept) when sum_d is not finite; the status flag records it.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSubH) k_alloc(const Desc *desc, const uint32_t *tree_base,
+                                                 int n_int, int initial) {
+    __shared__ unsigned long long s_w[8];
     __shared__ bool s_last;
-    const int b = owner_of(tree_base, n_int, blockIdx.x);
+    __shared__ unsigned long long s_carry;
+    const uint32_t tb = blockIdx.x / kSub;
+    const int b = owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
-    const uint32_t k = blockIdx.x - tree_base[b];
-    const uint64_t h0 = (uint64_t)k * kTreeBlock;
+    const uint32_t sub = (tb - tree_base[b]) * kSub + blockIdx.x % kSub;
+    const uint64_t h = (uint64_t)sub * kSubH + threadIdx.x;
     const double sum_d = d.st->sum_d;
-    const double inv_sum = d.st->inv_sum_d;
-    if (!isfinite(sum_d)) {
-        if (threadIdx.x == 0 && k == 0) d.st->status |= kStatusNonFinite;
+    if (!finite_bits(sum_d)) {
+        if (threadIdx.x == 0 && sub == 0) d.st->status |= kStatusNonFinite;
         return;
     }
-    if (threadIdx.x == 0) s_sum = 0ull;
-    __syncthreads();
-    const double n_ev_d = (double)d.n_ev;
-    unsigned long long mine = 0;
-    for (int i = threadIdx.x; i < kTreeBlock; i += blockDim.x) {
-        const uint64_t h = h0 + i;
-        if (h >= d.n_hc) break;
-        double q;
-        uint64_t iq;
-        if (sum_d > 0.0) {
-            // the IEEE quotient (N_ev d_h)/sum_d decides n_h; a multiply by the
-            // reciprocal is within 4e-16 q of it, so only quotients that close
-            // to an integer need the division itself
-            const double num = __dmul_rn(n_ev_d, d.dh[h]);
-            q = num * inv_sum;
-            const double fl = floor_pos(q, &iq);
-            const double tol = 1e-14 * q;
-            // (a zero numerator is exact; below 2 - tol the max(2, .) decides)
-            if (num > 0.0 && (d.plus2 || q > 1.5) && (q - fl <= tol || fl + 1.0 - q <= tol)) {
-                q = __ddiv_rn(num, sum_d);
-                const double f2 = floor_pos(q, &iq);
-                // a quotient within 2^-50 q below an integer counts as that integer
-                if (__dsub_rn(__dadd_rn(f2, 1.0), q) <= __dmul_rn(q, 8.8817841970012523e-16)) ++iq;
-            }
-        } else {
-            q = __ddiv_rn(n_ev_d, (double)d.n_hc);
-            const double f2 = floor_pos(q, &iq);
-            if (__dsub_rn(__dadd_rn(f2, 1.0), q) <= __dmul_rn(q, 8.8817841970012523e-16)) ++iq;
-        }
-        uint32_t n;
-        if (d.plus2 && !initial) n = (uint32_t)iq + 2u;
-        else n = iq > 2u ? (uint32_t)iq : 2u;
+    uint32_t n = 0;
+    if (h < d.n_hc) {
+        n = alloc_one(d, d.dh[h], (double)d.n_ev, sum_d, d.st->inv_sum_d, initial);
         d.n_h[h] = n;
-        mine += n;
     }
-    for (int s = 16; s >= 1; s >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, s);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&s_sum, mine);
-    __syncthreads();
+    unsigned long long tot;
+    cta_exclusive_scan(n, s_w, &tot);
+    const uint32_t n_sub = d.n_tree * kSub;
     if (threadIdx.x == 0) {
-        d.bsum[k] = s_sum;
+        d.bsum[sub] = tot;
         __threadfence();
         const uint32_t ticket = atomicAdd(&d.st->done_alloc, 1u);
-        s_last = (ticket == d.n_tree - 1);
+        s_last = (ticket == n_sub - 1);
+        s_carry = 0ull;
     }
     __syncthreads();
     if (!s_last) return;
-    // last block: exclusive scan of the block sums (integers: any order is exact)
+    // last CTA: exclusive scan of the sub-block sums in place
     __threadfence();
-    __shared__ unsigned long long s_w[8];
-    __shared__ unsigned long long s_carry;
-    if (threadIdx.x == 0) s_carry = 0ull;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t q0 = 0; q0 < d.n_tree; q0 += blockDim.x) {
+    for (uint32_t q0 = 0; q0 < n_sub; q0 += kSubH) {
         const uint32_t q = q0 + threadIdx.x;
-        const unsigned long long v = q < d.n_tree ? __ldcg(d.bsum + q) : 0ull;
-        unsigned long long inc = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += u;
-        }
+        const unsigned long long v = q < n_sub ? __ldcg(d.bsum + q) : 0ull;
+        unsigned long long all;
+        const unsigned long long ex = cta_exclusive_scan(v, s_w, &all);
+        const unsigned long long base = s_carry;
+        if (q < n_sub) d.bsum[q] = base + ex;
         __syncthreads();
-        if (lane == 31) s_w[warp] = inc;
+        if (threadIdx.x == 0) s_carry = base + all;
         __syncthreads();
-        unsigned long long base = s_carry;
-        for (int w = 0; w < warp; ++w) base += s_w[w];
-        if (q < d.n_tree) d.bsum[q] = base + inc - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry = base + inc;
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned long long run = s_carry;
         d.off[d.n_hc] = run;
@@ -403,41 +482,20 @@ __global__ void __launch_bounds__(256) k_alloc(const Desc *desc, const uint32_t 
     }
 }
 
-// k_offsets: off[h] = bsum[block] + exclusive scan of n_h within the block.
-__global__ void __launch_bounds__(256) k_offsets(const Desc *desc, const uint32_t *tree_base,
-                                                 int n_int) {
-    __shared__ unsigned long long s_warp[8];
-    const int b = owner_of(tree_base, n_int, blockIdx.x);
+// k_offsets: off[h] = offset of the sub-block + exclusive scan of n_h within it.
+__global__ void __launch_bounds__(kSubH) k_offsets(const Desc *desc, const uint32_t *tree_base,
+                                                   int n_int) {
+    __shared__ unsigned long long s_w[8];
+    const uint32_t tb = blockIdx.x / kSub;
+    const int b = owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
-    if (!isfinite(d.st->sum_d)) return;
-    const uint32_t k = blockIdx.x - tree_base[b];
-    const uint64_t h0 = (uint64_t)k * kTreeBlock + (uint64_t)threadIdx.x * 4;
-    const uint64_t n_hc = d.n_hc;
-    // 4 consecutive hypercubes per thread
-    uint32_t n[4];
-    unsigned long long tot = 0;
-    for (int i = 0; i < 4; ++i) {
-        const uint64_t h = h0 + i;
-        n[i] = h < n_hc ? d.n_h[h] : 0u;
-        tot += n[i];
-    }
-    // exclusive scan of tot over the block
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long inc = tot;
-    for (int s = 1; s < 32; s <<= 1) {
-        const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, s);
-        if (lane >= s) inc += o;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    unsigned long long wbase = 0;
-    for (int w = 0; w < warp; ++w) wbase += s_warp[w];
-    unsigned long long run = d.bsum[k] + wbase + inc - tot;
-    for (int i = 0; i < 4; ++i) {
-        const uint64_t h = h0 + i;
-        if (h < n_hc) d.off[h] = run;
-        run += n[i];
-    }
+    if (!finite_bits(d.st->sum_d)) return;
+    const uint32_t sub = (tb - tree_base[b]) * kSub + blockIdx.x % kSub;
+    const uint64_t h = (uint64_t)sub * kSubH + threadIdx.x;
+    const uint32_t n = h < d.n_hc ? d.n_h[h] : 0u;
+    unsigned long long tot;
+    const unsigned long long ex = cta_exclusive_scan(n, s_w, &tot);
+    if (h < d.n_hc) d.off[h] = d.bsum[sub] + ex;
 }
 
 // ---------------------------------------------------------------------------
@@ -487,8 +545,10 @@ __global__ void __cluster_dims__(kRefineCtas, 1, 1) __launch_bounds__(kRefineThr
     const int i0 = min(rank * S, n_g), i1 = min(i0 + S, n_g);
     const int t = threadIdx.x, nt = blockDim.x;
     double *edges = d.edges + (size_t)mu * (size_t)(n_g + 1);
-    // histograms of the latest iteration (double-buffered by iteration parity)
-    const size_t hb = (size_t)((d.st->t - 1u) & 1u) * (size_t)d.dim * n_g;
+    // histograms of the latest sampling pass (double-buffered by iteration
+    // parity; the sampling kernel records which, so that this kernel may run
+    // beside the estimate that advances t)
+    const size_t hb = (size_t)(d.st->hist_par & 1u) * (size_t)d.dim * n_g;
     const double *hs = d.hsum + hb + (size_t)mu * n_g;
     const uint32_t *hc = d.hcnt + hb + (size_t)mu * n_g;
 
@@ -626,10 +686,10 @@ cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_i
 
 cudaError_t launch_alloc(const Desc *desc, const uint32_t *tree_base, int n_int,
                          uint32_t n_blocks, cudaStream_t s, int initial) {
-    k_alloc<<<n_blocks, 256, 0, s>>>(desc, tree_base, n_int, initial);
+    k_alloc<<<n_blocks * kSub, kSubH, 0, s>>>(desc, tree_base, n_int, initial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_offsets<<<n_blocks, 256, 0, s>>>(desc, tree_base, n_int);
+    k_offsets<<<n_blocks * kSub, kSubH, 0, s>>>(desc, tree_base, n_int);
     return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -105,6 +106,10 @@ struct Set {
     bool any_refine = false;
     cudaStream_t last = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // the refinement (a8) runs on a side stream beside the estimate and the
+    // reallocation (a6, a7): it reads only the histograms and the grid
+    cudaStream_t side = nullptr;
+    cudaEvent_t efork = nullptr, ejoin = nullptr;
     bool timed = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -266,7 +271,7 @@ size_t vp::member_layout(Member &mb, size_t base) {
     const size_t D = mb.p.dim, G = mb.p.n_g, H = mb.n_hc, T = mb.n_tree, C = mb.hist_cap;
     const size_t sz[B_COUNT] = {D * (G + 1) * 8, D * G * 8, mb.prm.size() * 8,
                                 mb.prm32.size() * 4, H * 4, (H + 1) * 8, 2 * H * 8, 2 * H * 8,
-                                H * 8, 2 * D * G * 8, 2 * D * G * 4, T * 3 * 8, T * 8, C * 8,
+                                H * 8, 2 * D * G * 8, 2 * D * G * 4, T * 3 * 8, T * kSub * 8, C * 8,
                                 C * 8, sizeof(State)};
     for (int i = 0; i < B_COUNT; ++i) {
         mb.off_bytes[i] = base;
@@ -320,6 +325,13 @@ static vp_status plan_groups(Set &s) {
         vp_status st = group_config_many(mp, g, s.n_sm);
         if (st != VP_OK) return st;
         g.one = g.members.size() == 1;
+        {
+            // the one-integral kernel keeps FP32 peak constants in its
+            // parameters: at most kParamPeaks peaks (else the task kernel)
+            const Member &m0 = s.m[g.members[0]];
+            if (g.prec == VP_FP32 && g.kind != VP_POSTERIOR && (int)m0.prm[0] > kParamPeaks)
+                g.one = false;
+        }
         if (!g.one) continue;
         // a single integral: the cluster kernel with its constants in parameters
         // (the autotuner may still choose the task kernel)
@@ -420,6 +432,9 @@ void vp::fill_desc(const Member &mb, const double *d_inv, Desc &d) {
     d.omega = 1.0 / (double)mb.n_hc;
     d.alpha = mb.p.alpha;
     d.beta = mb.p.beta;
+    d.omega_beta = std::pow(d.omega, mb.p.beta);
+    d.half_beta_hi = (float)(0.5 * mb.p.beta);
+    d.half_beta_lo = (float)(0.5 * mb.p.beta - (double)d.half_beta_hi);
     d.ng_over_nst = (float)((double)G / (double)mb.n_st);
     d.inv_ng = (float)(1.0 / (double)G);
     {
@@ -596,7 +611,18 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         a.hist_shared = g.hist_shared;
         a.bins = d.dim * d.n_g;
         a.prm_words = g.prm_words;
-        (void)mb;
+        a.kp_peaks = 0;
+        if (g.prec == VP_FP32 && g.kind != VP_POSTERIOR) {
+            // {a, k, 0, 0, c[D], pad to 4} per peak -> {a, k, c[D]} at kParamStride
+            const int K = (int)mb.prm[0], st = 4 + ((d.dim + 3) & ~3);
+            for (int k = 0; k < K; ++k) {
+                a.kp[k * kParamStride + 0] = mb.prm32[(size_t)k * st + 0];
+                a.kp[k * kParamStride + 1] = mb.prm32[(size_t)k * st + 1];
+                for (int mu = 0; mu < d.dim; ++mu)
+                    a.kp[k * kParamStride + 2 + mu] = mb.prm32[(size_t)k * st + 4 + mu];
+            }
+            a.kp_peaks = K;
+        }
     }
     CU(cudaMemcpyAsync(s.d_desc, s.h_desc.data(), n * sizeof(Desc), cudaMemcpyHostToDevice, stream));
     CU(cudaMemcpyAsync(s.d_tree_base, tree_base.data(), (n + 1) * 4, cudaMemcpyHostToDevice, stream));
@@ -609,6 +635,9 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
     CU(launch_alloc(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream, 1));
     CU(cudaEventCreate(&s.ev0));
     CU(cudaEventCreate(&s.ev1));
+    CU(cudaEventCreateWithFlags(&s.efork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&s.ejoin, cudaEventDisableTiming));
+    CU(cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking));
     CU(cudaStreamSynchronize(stream));
     s.last = stream;
     return VP_OK;
@@ -620,6 +649,12 @@ static void set_destroy(Set &s) {
     if (s.graph) cudaGraphDestroy(s.graph);
     if (s.ev0) cudaEventDestroy(s.ev0);
     if (s.ev1) cudaEventDestroy(s.ev1);
+    if (s.side) {
+        cudaStreamSynchronize(s.side);
+        cudaStreamDestroy(s.side);
+    }
+    if (s.efork) cudaEventDestroy(s.efork);
+    if (s.ejoin) cudaEventDestroy(s.ejoin);
     cudaStreamSynchronize(s.last);
     dev_free(s.arena, s.last);
     cudaStreamSynchronize(s.last);
@@ -629,8 +664,8 @@ vp_status vp::launch_group(const Desc *d_desc, Group &g, cudaStream_t stream) {
     cudaError_t e;
     if (g.one) {
         e = g.prec == VP_FP64
-                ? launch_sample_one_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, g.cs, stream, g.args1)
-                : launch_sample_one_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, g.cs, stream, g.args1);
+                ? launch_sample_one_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads_one, g.smem, g.cs, stream, g.args1)
+                : launch_sample_one_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads_one, g.smem, g.cs, stream, g.args1);
     } else {
         SampleArgs a;
         a.desc = d_desc;
@@ -662,12 +697,12 @@ vp_status vp::launch_group(const Desc *d_desc, Group &g, cudaStream_t stream) {
 // ---------------------------------------------------------------------------
 struct Cand {
     bool one;
-    int blocks, cs, r;
+    int blocks, cs, r, threads;
 };
 
 static vp_status time_group(Set &s, Group &g, cudaStream_t stream, float *best_ms) {
-    float best = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
+    float t[7];
+    for (int rep = 0; rep < 7; ++rep) {
         if (!g.one)
             CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base, g.d_head,
                              g.task, stream));
@@ -676,11 +711,10 @@ static vp_status time_group(Set &s, Group &g, cudaStream_t stream, float *best_m
         if (st != VP_OK) return st;
         CU(cudaEventRecord(s.ev1, stream));
         CU(cudaEventSynchronize(s.ev1));
-        float ms = 0.f;
-        CU(cudaEventElapsedTime(&ms, s.ev0, s.ev1));
-        if (rep > 0) best = std::min(best, ms);  // the first launch warms up
+        CU(cudaEventElapsedTime(&t[rep], s.ev0, s.ev1));
     }
-    *best_ms = best;
+    std::sort(t + 1, t + 7);  // the first launch warms up; the median of the rest
+    *best_ms = 0.5f * (t[3] + t[4]);
     return VP_OK;
 }
 
@@ -694,7 +728,7 @@ struct TuneKey {
 };
 struct TuneVal {
     bool one;
-    int blocks, cs, r;
+    int blocks, cs, r, threads;
 };
 static std::mutex g_tune_mu;
 static std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
@@ -742,6 +776,8 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                     g.blocks = kv.second.blocks;
                     g.cs = kv.second.cs;
                     g.r = kv.second.r;
+                    g.threads_one = kv.second.threads;
+                    g.args1.r = g.r;
                     set_task(g, expect0);
                     g.tuned = true;
                     hit = true;
@@ -753,30 +789,38 @@ static vp_status tune(Set &s, cudaStream_t stream) {
         const bool can_one = g.members.size() == 1;
         double expect = 0.0;
         for (uint32_t i : g.members) expect += (double)s.m[i].p.n_ev + 2.0 * (double)s.m[i].n_hc;
-        if (can_one) {
-            for (int k = 1; k <= std::min(3, g.occ_one); ++k) {
-                const int blocks = k * s.n_sm;
-                for (int cs : {1, 2, 4, 8}) {
-                    if (cs > 1 && !g.hist_shared) continue;
-                    int ctas = blocks;
-                    if (cs > 1) {
-                        ctas = g.prec == VP_FP64
-                                   ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, blocks, g.threads, g.smem)
-                                   : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, blocks, g.threads, g.smem);
-                        ctas = std::min(ctas, blocks) / cs * cs;
-                        if (ctas < (int)(0.9 * blocks)) continue;
+        if (can_one && g.one) {
+            // CTAs of 256 threads (1..3 per SM), or one larger CTA per SM
+            const int max_threads = one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64);
+            for (int threads : {256, 512, 768}) {
+                if (threads > max_threads) continue;
+                const int occ = g.prec == VP_FP64
+                                    ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem)
+                                    : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem);
+                for (int k = 1; k <= std::min(threads == 256 ? 3 : 1, occ); ++k) {
+                    const int blocks = k * s.n_sm;
+                    for (int cs : {1, 2, 4, 8}) {
+                        if (cs > 1 && !g.hist_shared) continue;
+                        int ctas = blocks;
+                        if (cs > 1) {
+                            ctas = g.prec == VP_FP64
+                                       ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem)
+                                       : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem);
+                            ctas = std::min(ctas, blocks) / cs * cs;
+                            if (ctas < (int)(0.9 * blocks)) continue;
+                        }
+                        cands.push_back({true, ctas, cs, g.r, threads});
                     }
-                    cands.push_back({true, ctas, cs, g.r});
                 }
             }
         }
         for (int k = 1; k <= std::min(3, g.occ_many); ++k)
-            for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r});
+            for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r, 256});
         if (cands.size() <= 1) {
             g.tuned = true;
             continue;
         }
-        const Cand keep = {g.one, g.blocks, g.cs, g.r};
+        const Cand keep = {g.one, g.blocks, g.cs, g.r, g.threads_one};
         Cand best = keep;
         float best_ms = 1e30f;
         for (const Cand &c : cands) {
@@ -784,6 +828,8 @@ static vp_status tune(Set &s, cudaStream_t stream) {
             g.blocks = c.blocks;
             g.cs = c.cs;
             g.r = c.r;
+            g.threads_one = c.threads;
+            g.args1.r = c.r;
             set_task(g, expect);
             float ms = 0.f;
             vp_status st = time_group(s, g, stream, &ms);
@@ -797,11 +843,14 @@ static vp_status tune(Set &s, cudaStream_t stream) {
         g.blocks = best.blocks;
         g.cs = best.cs;
         g.r = best.r;
+        g.threads_one = best.threads;
+        g.args1.r = best.r;
         set_task(g, expect);
         g.tuned = true;
         {
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tune_cache.push_back({tune_key(s, g, expect), {g.one, g.blocks, g.cs, g.r}});
+            g_tune_cache.push_back(
+                {tune_key(s, g, expect), {g.one, g.blocks, g.cs, g.r, g.threads_one}});
         }
         // clear what the tuning launches accumulated (buffer t & 1 of each member)
         for (uint32_t i : g.members) {
@@ -819,7 +868,23 @@ static vp_status tune(Set &s, cudaStream_t stream) {
     return VP_OK;
 }
 
-static vp_status set_iterate(Set &s, cudaStream_t stream) {
+// Forks the refinement onto the side stream after what `stream` holds so far;
+// join_refine makes `stream` wait for it.  (Inside a capture both become graph
+// edges.)
+static vp_status fork_refine(Set &s, cudaStream_t stream) {
+    const int n = (int)s.m.size();
+    CU(cudaEventRecord(s.efork, stream));
+    CU(cudaStreamWaitEvent(s.side, s.efork, 0));
+    CU(launch_refine(s.d_desc, s.d_axis_base, n, s.n_axis_total, s.max_ng, s.side));
+    CU(cudaEventRecord(s.ejoin, s.side));
+    return VP_OK;
+}
+static vp_status join_refine(Set &s, cudaStream_t stream) {
+    CU(cudaStreamWaitEvent(stream, s.ejoin, 0));
+    return VP_OK;
+}
+
+static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = false) {
     const int n = (int)s.m.size();
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing(stream, &cap));
@@ -842,16 +907,26 @@ static vp_status set_iterate(Set &s, cudaStream_t stream) {
     }
     CU(cudaEventRecordWithFlags(s.ev1, stream, ev_flags));
     s.timed = true;
+    if (refine_too && s.any_refine) {  // the step graph: a8 beside a6 and a7
+        vp_status st = fork_refine(s, stream);
+        if (st != VP_OK) return st;
+    }
     CU(launch_estimate(s.d_desc, s.d_tree_base, n, s.n_tree_total, 0, stream));
     s.last = stream;
     return VP_OK;
 }
 
-static vp_status set_adapt(Set &s, cudaStream_t stream) {
+static vp_status set_adapt(Set &s, cudaStream_t stream, bool refine_forked = false) {
     const int n = (int)s.m.size();
+    if (s.any_refine && !refine_forked) {
+        vp_status st = fork_refine(s, stream);
+        if (st != VP_OK) return st;
+    }
     CU(launch_alloc(s.d_desc, s.d_tree_base, n, s.n_tree_total, stream, 0));
-    if (s.any_refine)
-        CU(launch_refine(s.d_desc, s.d_axis_base, n, s.n_axis_total, s.max_ng, stream));
+    if (s.any_refine) {
+        vp_status st = join_refine(s, stream);
+        if (st != VP_OK) return st;
+    }
     s.last = stream;
     return VP_OK;
 }
@@ -866,8 +941,8 @@ static vp_status set_step(Set &s, cudaStream_t stream) {
         CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         CU(cudaStreamSynchronize(stream));
         CU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        vp_status st = set_iterate(s, cap);
-        if (st == VP_OK) st = set_adapt(s, cap);
+        vp_status st = set_iterate(s, cap, true);
+        if (st == VP_OK) st = set_adapt(s, cap, true);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);
@@ -1129,6 +1204,9 @@ extern "C" vp_status vp_refine_from_hist(vp_ctx *c, const double *hsum, const do
     CU(cudaMemcpyAsync(d.hsum + par * bins, hsum, bins * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
     CU(cudaMemcpyAsync(d.hcnt + par * bins, cnt.data(), bins * 4, cudaMemcpyHostToDevice,
                        (cudaStream_t)stream));
+    const uint32_t par32 = (uint32_t)par;
+    CU(cudaMemcpyAsync((char *)d.st + offsetof(State, hist_par), &par32, 4, cudaMemcpyHostToDevice,
+                       (cudaStream_t)stream));
     CU(launch_refine(s.d_desc, s.d_axis_base, 1, s.n_axis_total, s.max_ng, (cudaStream_t)stream));
     CU(cudaStreamSynchronize((cudaStream_t)stream));
     s.last = (cudaStream_t)stream;
@@ -1193,14 +1271,72 @@ extern "C" vp_status vp_last_sample_ms(vp_ctx *c, float *ms) {
     return VP_OK;
 }
 
-extern "C" vp_status vp_get_tuning(vp_ctx *c, int *scheme, int *blocks, int *cluster, int *run) {
+extern "C" vp_status vp_get_tuning(vp_ctx *c, int *scheme, int *blocks, int *threads,
+                                    int *cluster, int *run) {
     CHECK_CTX(c);
     if (c->set.groups.empty()) return fail(VP_EINVAL, "no sampling group");
     const Group &g = c->set.groups[0];
     if (scheme) *scheme = g.one ? 0 : 1;
     if (blocks) *blocks = g.blocks;
+    if (threads) *threads = g.one ? g.threads_one : g.threads;
     if (cluster) *cluster = g.cs;
     if (run) *run = g.r;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int threads, int cluster,
+                                    int run) {
+    CHECK_CTX(c);
+    if (c->set.groups.empty()) return fail(VP_EINVAL, "no sampling group");
+    Group &g = c->set.groups[0];
+    if (scheme != 0 && scheme != 1) return fail(VP_EINVAL, "scheme must be 0 or 1");
+    if (scheme == 1 && threads != 256) return fail(VP_EINVAL, "the task scheme runs 256 threads");
+    if (threads != 256 && threads != 512 && threads != 768)
+        return fail(VP_EINVAL, "threads must be 256, 512 or 768");
+    if (threads > one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64))
+        return fail(VP_EINVAL, "%d threads exceed this kernel's largest CTA", threads);
+    if (scheme == 0 && g.members.size() == 1 && g.prec == VP_FP32 && g.kind != VP_POSTERIOR &&
+        (int)c->set.m[g.members[0]].prm[0] > kParamPeaks)
+        return fail(VP_EINVAL, "more than %d peaks: the task scheme only", kParamPeaks);
+    if (blocks < 1 || blocks > 65535) return fail(VP_EINVAL, "blocks out of range");
+    if (run < 1 || run > 64) return fail(VP_EINVAL, "run must be in 1..64");
+    if (scheme == 1 && cluster != 1) return fail(VP_EINVAL, "the task scheme takes no clusters");
+    if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
+        return fail(VP_EINVAL, "cluster must be 1, 2, 4 or 8");
+    if (cluster > 1 && !g.hist_shared)
+        return fail(VP_EINVAL, "clusters need shared-memory histograms");
+    if (blocks % cluster) return fail(VP_EINVAL, "blocks must be a multiple of the cluster");
+    if (scheme == 0) {
+        // the static split assumes every CTA resident at once
+        const int occ = g.prec == VP_FP64
+                            ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem)
+                            : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem);
+        const int res = cluster > 1
+                            ? (g.prec == VP_FP64
+                                   ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem)
+                                   : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem))
+                            : occ * c->set.n_sm;
+        if (blocks > res)
+            return fail(VP_EINVAL, "%d CTAs in clusters of %d exceed the %d resident ones", blocks,
+                        cluster, res);
+    }
+    CU(cudaStreamSynchronize(c->set.last));
+    if (c->set.gexec) {  // the step graph holds the old shape: capture again
+        cudaGraphExecDestroy(c->set.gexec);
+        cudaGraphDestroy(c->set.graph);
+        c->set.gexec = nullptr;
+        c->set.graph = nullptr;
+    }
+    g.one = scheme == 0;
+    g.blocks = blocks;
+    g.cs = cluster;
+    g.r = run;
+    g.threads_one = threads;
+    g.args1.r = run;
+    double expect = 0.0;
+    for (uint32_t i : g.members) expect += (double)c->set.m[i].p.n_ev + 2.0 * (double)c->set.m[i].n_hc;
+    set_task(g, expect);
+    g.tuned = true;
     return VP_OK;
 }
 

@@ -73,6 +73,7 @@ struct Group {
     size_t smem = 0;
     bool one = false;  // a single integral: the cluster kernel with constants in parameters
     int cs = 1;        // CTAs per cluster (one-integral kernel)
+    int threads_one = 256;  // CTA size of the one-integral kernel
     SampleOne args1;
     int occ_one = 0, occ_many = 0;  // resident CTAs per SM of each kernel
     bool tuned = false;

@@ -109,6 +109,38 @@ __device__ __forceinline__ float f_peaks32(int kind, const float *p, int K, int 
     return f;
 }
 
+// Peak families with their constants in the kernel parameters (one-integral
+// kernel, FP32, K <= kParamPeaks): per peak {a, k, c_0 .. c_{kMaxDim-1}} at a
+// fixed stride, read as constant-bank operands (every index is a compile-time
+// constant once the loops are unrolled), with the same operations in the same
+// order as f_peaks32.
+constexpr int kParamPeaks = 8;
+constexpr int kParamStride = 2 + kMaxDim;
+
+template <int DMAX, int KIND>
+__device__ __forceinline__ float f_peaks32_param(const float *kp, int K, int dim,
+                                                 const float (&x)[DMAX]) {
+    float f = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kParamPeaks; ++k) {
+        if (k < K) {
+            const float *p = kp + k * kParamStride;
+            float r2 = 0.0f;
+#pragma unroll
+            for (int mu = 0; mu < DMAX; ++mu) {
+                if (mu < dim) {
+                    const float dx = x[mu] - p[2 + mu];
+                    r2 = fmaf(dx, dx, r2);
+                }
+            }
+            if (KIND == VP_GAUSS) f = fmaf(p[0], ex2_approx(-p[1] * r2), f);
+            else if (KIND == VP_BALL) f += (r2 < p[1]) ? p[0] : 0.0f;
+            else f = fmaf(p[0], ex2_approx(-p[1] * sqrtf(r2)), f);
+        }
+    }
+    return f;
+}
+
 template <int DMAX>
 __device__ __forceinline__ double f_post64(const double *p, int dim, const double (&x)[DMAX]) {
     const int n = (int)p[0], npar = (int)p[1], ngrp = (int)p[2];
@@ -253,7 +285,7 @@ __device__ __forceinline__ Loop make_loop(const Desc *dp, uint32_t t) {
 // in the kernel parameters (constant bank), not in registers.
 struct SampleOne {
     Loop L;                    // t is read from the device state at launch
-    const State *st;
+    State *st;
     const uint64_t *off;
     double *s1, *s2, *hsum;    // double-buffered bases
     uint32_t *hcnt;
@@ -266,6 +298,8 @@ struct SampleOne {
     int hist_shared;
     int bins;
     int prm_words;
+    int kp_peaks;              // > 0: the peak constants are in kp (FP32 peak families)
+    float kp[kParamPeaks * kParamStride];
 };
 
 // Fire-and-forget global reductions.
@@ -306,7 +340,7 @@ __device__ __forceinline__ void hcube_offsets(const Loop &L, const uint32_t (&kd
 // ---------------------------------------------------------------------------
 // One sample, FP32 path (a1-a3): x[], idx[], J = Jm 2^Je, f.
 // ---------------------------------------------------------------------------
-template <int DMAX, bool EXACT, int KIND>
+template <int DMAX, bool EXACT, int KIND, bool KP = false>
 __device__ __forceinline__ void point32(const Loop &L, const float *prm, uint32_t h, uint32_t j,
                                         const float (&kc)[DMAX], float (&x)[DMAX],
                                         int (&idx)[DMAX], float &Jm, int &Je, float &f) {
@@ -346,6 +380,7 @@ __device__ __forceinline__ void point32(const Loop &L, const float *prm, uint32_
     Jm = J;
     Je = e;
     if (KIND == VP_POSTERIOR) f = f_post32<DMAX>(prm, dim, x);
+    else if (KP) f = f_peaks32_param<DMAX, KIND>(prm, L.K, dim, x);
     else f = f_peaks32<DMAX>(KIND, prm, L.K, dim, x);
 }
 
@@ -455,8 +490,12 @@ template <> struct Acc<true> {
     double s1, s2;
     __device__ __forceinline__ void reset() { s1 = 0.0; s2 = 0.0; }
     __device__ __forceinline__ void add(double v, double v2) { s1 += v; s2 += v2; }
-    __device__ __forceinline__ double m1() const { return s1; }
-    __device__ __forceinline__ double m2() const { return s2; }
+    // adds the sums, unscaled by 2^-sexp, to the hypercube's FP64 accumulators
+    __device__ __forceinline__ void flush(double *p1, double *p2, int sexp) const {
+        const double u = pow2d(-sexp);
+        red_add(p1, s1 * u);
+        red_add(p2, s2 * (u * u));
+    }
 };
 template <> struct Acc<false> {
     float s1, c1, s2, c2;
@@ -471,8 +510,11 @@ template <> struct Acc<false> {
         kahan(s1, c1, v);
         kahan(s2, c2, v2);
     }
-    __device__ __forceinline__ double m1() const { return (double)s1 - (double)c1; }
-    __device__ __forceinline__ double m2() const { return (double)s2 - (double)c2; }
+    // the compensated sums s - c, unscaled by 2^-sexp, exactly converted
+    __device__ __forceinline__ void flush(double *p1, double *p2, int sexp) const {
+        red_add(p1, f2d_pow2(s1, -sexp) - f2d_pow2(c1, -sexp));
+        red_add(p2, f2d_pow2(s2, -2 * sexp) - f2d_pow2(c2, -2 * sexp));
+    }
 };
 
 // Integrand constants for this CTA: FP32 path copies them to shared memory
@@ -551,12 +593,12 @@ __device__ __forceinline__ uint64_t lane_find_hcube(const uint64_t *off, uint64_
     return h;
 }
 
-template <int DMAX, bool EXACT, bool F64, int KIND>
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP = false>
 __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const void *prm,
                                             uint64_t s_begin, uint64_t s_end, uint64_t h,
                                             uint64_t lo_off, uint64_t next,
                                             typename Real<F64>::T *hs, uint32_t *hc,
-                                            bool hist_shared, int sexp, double unscale) {
+                                            bool hist_shared, int sexp) {
     typedef typename Real<F64>::T T;
     const int dim = EXACT ? DMAX : L.dim;
     uint32_t j = (uint32_t)(s_begin - lo_off);
@@ -564,14 +606,11 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
     decode_digits<DMAX>((uint32_t)h, L, dim, kd);
     float kc[DMAX];
     if (!F64) hcube_offsets<DMAX>(L, kd, kc);
-    const T scale = (T)ldexp(1.0, sexp);
-    const double un2 = unscale * unscale;
     Acc<F64> acc;
     acc.reset();
     for (uint64_t s = s_begin; s < s_end; ++s) {
         if (s == next) {
-            red_add(P.S1 + h, acc.m1() * unscale);
-            red_add(P.S2 + h, acc.m2() * un2);
+            acc.flush(P.S1 + h, P.S2 + h, sexp);
             acc.reset();
             ++h;
             next = __ldg(P.off + h + 1);
@@ -589,11 +628,12 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
         if (F64) {
             double x[DMAX], J, f;
             point64<DMAX, KIND>(L, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
-            v = (T)(J * f * (double)scale);
+            v = (T)(J * f * pow2d(sexp));
         } else {
             float x[DMAX], Jm, f;
             int Je;
-            point32<DMAX, EXACT, KIND>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je, f);
+            point32<DMAX, EXACT, KIND, KP>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je,
+                                           f);
             const float jf = Jm * f;  // normal or zero: Jm in [1, 2), f flushed to zero
             const int ev = ((__float_as_int(jf) >> 23) & 0xff) - 127 + Je + sexp;  // exponent of v
             if (jf != 0.0f && isfinite(jf) && (ev >= 60 || ev < -60)) {
@@ -620,15 +660,16 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
                     if (v2 != (T)0) atomicAdd(hs + b, v2);
                     atomicAdd(hc + b, 1u);
                 } else {
-                    if (v2 != (T)0) red_add(P.HS + b, (double)v2 * un2);
+                    if (v2 != (T)0)
+                        red_add(P.HS + b, F64 ? (double)v2 * pow2d(-2 * sexp)
+                                              : f2d_pow2((float)v2, -2 * sexp));
                     red_add(P.HC + b, 1u);
                 }
             }
         }
         ++j;
     }
-    red_add(P.S1 + h, acc.m1() * unscale);
-    red_add(P.S2 + h, acc.m2() * un2);
+    acc.flush(P.S1 + h, P.S2 + h, sexp);
 }
 
 // ---------------------------------------------------------------------------
@@ -643,16 +684,58 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
 // and cluster.
 // Shared memory: [prm: prm_words x 4 B][hist sum: bins x (4|8) B][hist count: bins x 4 B]
 // ---------------------------------------------------------------------------
-// resident CTAs of 256 threads to aim for: small dimensions fit three per SM
-__host__ __device__ constexpr int one_min_ctas(int dmax, bool f64) {
-    return f64 ? 1 : (dmax <= 8 ? 3 : 2);  // the autotuner picks how many actually run
+// Largest CTA of the one-integral kernel: the autotuner also tries one CTA per
+// SM (one shared-memory histogram per SM instead of one per 256 threads).
+// The bound keeps the register budget of the earlier 256 x 3 (D <= 8), 256 x 2
+// (FP32, D > 8) and 256 x 1 (FP64) shapes.
+__host__ __device__ constexpr int one_max_threads(int dmax, bool f64) {
+    return f64 ? 256 : (dmax <= 8 ? 768 : 512);
+}
+
+// Sum of the cluster's CS copies of bins [b0, b1) of the histograms, added to
+// the global FP64 histograms (one reduction per bin and cluster).
+template <int CS, bool F64>
+__device__ __forceinline__ void cluster_flush(cooperative_groups::cluster_group &cl,
+                                              typename Real<F64>::T *hs, uint32_t *hc,
+                                              const Ptrs &P, int b0, int b1, int sexp) {
+    typedef typename Real<F64>::T T;
+    // each cluster starts at its own bin of the slice (in whole warps), so
+    // that the clusters' global reductions do not queue on the same addresses
+    const int n_cl = (int)(gridDim.x / CS), cid = (int)(blockIdx.x / CS);
+    const int len = max(b1 - b0, 0);
+    const int rot = (int)(((uint64_t)cid * (uint64_t)len / n_cl) & ~31ull);
+    for (int q = threadIdx.x; q < len; q += blockDim.x) {
+        const int b = b0 + (q + rot < len ? q + rot : q + rot - len);
+        T vs[CS];
+        uint32_t vc[CS];
+#pragma unroll
+        for (int r = 0; r < CS; ++r) {  // the remote loads of a bin issued together
+            vs[r] = *cl.map_shared_rank(hs + b, r);
+            vc[r] = *cl.map_shared_rank(hc + b, r);
+        }
+        // (the FP32 path adds the CTAs' FP32 sums in FP32, like each CTA's own)
+        T sum = (T)0;
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int r = 0; r < CS; ++r) {
+            sum += vs[r];
+            cnt += vc[r];
+        }
+        if (cnt) {
+            red_add(P.HS + b, F64 ? (double)sum * pow2d(-2 * sexp)
+                                  : f2d_pow2((float)sum, -2 * sexp));
+            red_add(P.HC + b, cnt);
+        }
+    }
 }
 
 template <int DMAX, bool EXACT, bool F64, int KIND>
-__global__ void __launch_bounds__(256, one_min_ctas(DMAX, F64))
+__global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
     k_sample_one(const __grid_constant__ SampleOne a) {
     typedef typename Real<F64>::T T;
     namespace cg = cooperative_groups;
+    // FP32 peak families read their constants from the parameters
+    constexpr bool KP = !F64 && KIND != VP_POSTERIOR;
     extern __shared__ __align__(16) unsigned char smem[];
     float *sprm = (float *)smem;
     T *hs = (T *)(smem + (size_t)a.prm_words * 4);
@@ -661,7 +744,7 @@ __global__ void __launch_bounds__(256, one_min_ctas(DMAX, F64))
 
     const uint32_t t_it = __ldcg(&a.st->t);
     const int sexp = __ldcg(&a.st->scale_exp);
-    const double unscale = ldexp(1.0, -sexp);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->hist_par = t_it & 1u;
     Loop L = a.L;
     L.t = t_it;
     Ptrs P;
@@ -676,6 +759,8 @@ __global__ void __launch_bounds__(256, one_min_ctas(DMAX, F64))
     const void *prm;
     if (F64) {
         prm = (const void *)a.prm;
+    } else if (KP) {
+        prm = (const void *)a.kp;
     } else {
         for (int i = threadIdx.x; i < a.prm_words; i += blockDim.x) sprm[i] = __ldg(a.prm32 + i);
         prm = (const void *)sprm;
@@ -701,39 +786,23 @@ __global__ void __launch_bounds__(256, one_min_ctas(DMAX, F64))
             const uint64_t h =
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)
-                run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs, hc,
-                                                    a.hist_shared != 0, sexp, unscale);
+                run_samples<DMAX, EXACT, F64, KIND, KP>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
+                                                        hc, a.hist_shared != 0, sexp);
         }
     }
     __syncthreads();
     if (a.hist_shared) {
-        // cluster-wide reduction of the CTAs' histograms, one slice per CTA;
-        // the remote loads of a bin are issued together (cluster size <= 8)
+        // cluster-wide reduction of the CTAs' histograms, one slice per CTA
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
         const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
         const int per = (a.bins + cs - 1) / cs;
         const int b0 = rank * per, b1 = min(a.bins, b0 + per);
-        const double un2 = unscale * unscale;
-        for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
-            T vs[8];
-            uint32_t vc[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                vs[q] = q < cs ? *cl.map_shared_rank(hs + b, q) : (T)0;
-                vc[q] = q < cs ? *cl.map_shared_rank(hc + b, q) : 0u;
-            }
-            double sum = 0.0;
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                sum += (double)vs[q];
-                cnt += vc[q];
-            }
-            if (cnt) {
-                red_add(P.HS + b, sum * un2);
-                red_add(P.HC + b, cnt);
-            }
+        switch (cs) {
+            case 1: cluster_flush<1, F64>(cl, hs, hc, P, b0, b1, sexp); break;
+            case 2: cluster_flush<2, F64>(cl, hs, hc, P, b0, b1, sexp); break;
+            case 4: cluster_flush<4, F64>(cl, hs, hc, P, b0, b1, sexp); break;
+            default: cluster_flush<8, F64>(cl, hs, hc, P, b0, b1, sexp); break;
         }
         cl.sync();  // keep this CTA's shared memory until every remote read is done
     }
@@ -761,14 +830,17 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
     Ptrs P;
     const void *prm = nullptr;
     int bins = 0, sexp = 0;
-    double unscale = 1.0;
 
     auto flush_hist = [&]() {
-        const double un2 = unscale * unscale;
-        for (int b = threadIdx.x; b < bins; b += blockDim.x) {
+        // each CTA starts at its own bin (in whole warps), so that the CTAs'
+        // global reductions do not all queue on the same addresses at once
+        const int rot = (int)(((uint64_t)blockIdx.x * (uint64_t)bins / gridDim.x) & ~31ull);
+        for (int q = threadIdx.x; q < bins; q += blockDim.x) {
+            const int b = q + rot < bins ? q + rot : q + rot - bins;
             const uint32_t n = hc[b];
             if (n) {
-                red_add(P.HS + b, (double)hs[b] * un2);
+                red_add(P.HS + b, F64 ? (double)hs[b] * pow2d(-2 * sexp)
+                                      : f2d_pow2((float)hs[b], -2 * sexp));
                 red_add(P.HC + b, n);
             }
         }
@@ -776,11 +848,11 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
     auto enter = [&](int g) {  // all threads; caller synchronises afterwards
         cur = g;
         const Desc *dp = a.desc + __ldg(a.members + g);
-        const State *st = (const State *)__ldg((const unsigned long long *)&dp->st);
+        State *st = (State *)__ldg((const unsigned long long *)&dp->st);
         const uint32_t t_it = __ldcg(&st->t);
+        if (threadIdx.x == 0) st->hist_par = t_it & 1u;  // every CTA of the integral writes the same
         L = make_loop(dp, t_it);
         sexp = __ldcg(&st->scale_exp);
-        unscale = ldexp(1.0, -sexp);
         bins = L.dim * L.n_g;
         P.off = (const uint64_t *)__ldg((const unsigned long long *)&dp->off);
         P.n_hc = __ldg(&dp->n_hc);
@@ -841,7 +913,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)
                 run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
-                                                    hc, a.hist_shared != 0, sexp, unscale);
+                                                    hc, a.hist_shared != 0, sexp);
         }
     }
     if (cur >= 0 && a.hist_shared) flush_hist();

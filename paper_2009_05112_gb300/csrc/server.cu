@@ -103,6 +103,10 @@ struct vp_server {
     int device = 0, n_sm = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the refinement (a8) runs on a side stream beside the estimate and the
+    // reallocation (a6, a7)
+    cudaStream_t side = nullptr;
+    cudaEvent_t efork = nullptr, ejoin = nullptr;
     size_t budget = 0;
     int max_active = 0;
     DevMem pool_mem, tables;
@@ -303,10 +307,15 @@ static vp_status server_step(vp_server *S, int *n_active) {
             rs = launch_group(S->d_desc, S->slots[s], st);
             if (rs != VP_OK) return rs;
         }
+        if (S->any_refine) {
+            CU(cudaEventRecord(S->efork, st));
+            CU(cudaStreamWaitEvent(S->side, S->efork, 0));
+            CU(launch_refine(S->d_desc, S->d_axis, n, S->n_axis_total, S->max_ng, S->side));
+            CU(cudaEventRecord(S->ejoin, S->side));
+        }
         CU(launch_estimate(S->d_desc, S->d_tree, n, S->n_tree_total, 0, st));
         CU(launch_alloc(S->d_desc, S->d_tree, n, S->n_tree_total, st, 0));
-        if (S->any_refine)
-            CU(launch_refine(S->d_desc, S->d_axis, n, S->n_axis_total, S->max_ng, st));
+        if (S->any_refine) CU(cudaStreamWaitEvent(st, S->ejoin, 0));
         CU(cudaMemcpyAsync(S->h_done, S->d_done, n * 4, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         rs = retire(S);
@@ -350,6 +359,12 @@ static void server_free(vp_server *S) {
     dev_free(S->tables, S->stream);
     if (S->stream) cudaStreamSynchronize(S->stream);
     if (S->h_done) cudaFreeHost(S->h_done);
+    if (S->side) {
+        cudaStreamSynchronize(S->side);
+        cudaStreamDestroy(S->side);
+    }
+    if (S->efork) cudaEventDestroy(S->efork);
+    if (S->ejoin) cudaEventDestroy(S->ejoin);
     if (S->own_stream && S->stream) cudaStreamDestroy(S->stream);
 }
 
@@ -373,6 +388,9 @@ static vp_status server_init(vp_server *S, const vp_server_config *cfg, void *st
         CU(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
         S->own_stream = true;
     }
+    CU(cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&S->efork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&S->ejoin, cudaEventDisableTiming));
     // tables: descriptors (running set, newcomers), block prefixes, flags, 1/n,
     // and the group slots' member lists, task prefixes and queue heads
     const size_t A = (size_t)S->max_active;

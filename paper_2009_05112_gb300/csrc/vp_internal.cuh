@@ -17,6 +17,8 @@ namespace vp {
 constexpr int kMaxDim = 24;        // D limit (largest bucket of the sampling kernel)
 constexpr int kMaxNg = 4096;       // N_g limit (refinement keeps a whole axis in shared memory)
 constexpr int kTreeBlock = 1024;   // hypercubes per block of the fixed-order sum
+constexpr int kSub = 4;            // CTAs of the allocation kernels per block of kTreeBlock
+constexpr int kSubH = kTreeBlock / kSub;
 constexpr int kMaxPeaks = 64;
 constexpr int kMaxPoints = 256;
 constexpr int kInvTab = 4096;      // table of 1/n for small integers n
@@ -31,7 +33,7 @@ struct State {
     uint32_t done_est;    // last-block counter of the estimate kernel
     uint32_t done_alloc;  // last-block counter of the allocation kernel
     uint32_t status;      // kStatus* bits
-    uint32_t pad;
+    uint32_t hist_par;    // histogram buffer of the latest sampling pass (read by the refinement)
     double sum_d;         // sum_h d_h in the fixed order (set by the estimate kernel)
     double inv_sum_d;     // 1 / sum_d
     uint64_t n_samples;   // sum_h n_h of the current allocation
@@ -62,6 +64,8 @@ struct Desc {
     uint64_t n_hc;             // N_h = N_st^D
     double omega;              // y-volume of a hypercube, N_st^-D
     double alpha, beta;
+    double omega_beta;         // Omega^beta (FP32 path: d_h = Omega^beta var^(beta/2))
+    float half_beta_hi, half_beta_lo;  // beta/2 = hi + lo (FP32 path)
     float ng_over_nst;         // N_g / N_st (FP32 path)
     float inv_ng;              // 1 / N_g (FP32 path)
     float ngD_m;               // N_g^D = ngD_m 2^ngD_e (FP32 path: J = N_g^D prod dx_i)
@@ -82,7 +86,7 @@ struct Desc {
     double *hsum;      // [2][dim][n_g] sum v^2 per increment (unscaled), same double buffering
     uint32_t *hcnt;    // [2][dim][n_g] samples per increment
     double *part;      // [n_tree][3] block partial sums (I, var, d)
-    uint64_t *bsum;    // [n_tree] block sums of n_h, then block offsets
+    uint64_t *bsum;    // [n_tree kSub] sums of n_h over kSubH hypercubes, then their offsets
     double *hist_i, *hist_var;  // [hist_cap] iteration history
     State *st;
     // served requests (done_out == nullptr elsewhere): stop when the §2.5
@@ -131,6 +135,25 @@ __device__ __forceinline__ float u01_f32(uint32_t r) {
 }
 
 // PTX MUFU forms (documented instructions; ~2^-22 relative error).
+// 2^e as a double, |e| <= 1022, from its bits.
+__device__ __forceinline__ double pow2d(int e) {
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// (double)x 2^e, exact, built from the bits of x: FP64 instructions are scarce
+// on this part (a few per SM per clock), so the FP32 path's values leave the
+// kernel without them.  |e| <= 240, so the result is a normal double.
+__device__ __forceinline__ double f2d_pow2(float x, int e) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t ex = (b >> 23) & 0xffu;
+    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)(b >> 31) << 63);  // +-0
+    if (ex == 0u || ex == 0xffu) return (double)x * pow2d(e);  // subnormal, inf, nan
+    const uint64_t bits = ((uint64_t)(b >> 31) << 63) |
+                          ((uint64_t)(ex + (uint32_t)(1023 - 127 + e)) << 52) |
+                          ((uint64_t)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -105,7 +105,9 @@ _SIGS = {
     "vp_last_sample_ms": [_P, ctypes.POINTER(ctypes.c_float)],
     "vp_alloc_static": [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P, _P, _P],
     "vp_get_tuning": [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                      ctypes.POINTER(ctypes.c_int)],
+    "vp_set_tuning": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "vp_batch_create": [ctypes.c_int, ctypes.POINTER(vp_params), ctypes.POINTER(vp_integrand), _P,
                         ctypes.POINTER(_P)],
     "vp_batch_iterate": [_P, _P],
@@ -335,10 +337,16 @@ class Integrator:
         return x, idx, jac, f
 
     def tuning(self):
-        v = [ctypes.c_int() for _ in range(4)]
+        v = [ctypes.c_int() for _ in range(5)]
         check(lib().vp_get_tuning(self.ctx, *[ctypes.byref(x) for x in v]))
         return dict(scheme=["static-cluster", "tasks"][v[0].value], blocks=v[1].value,
-                    cluster=v[2].value, run=v[3].value)
+                    threads=v[2].value, cluster=v[3].value, run=v[4].value)
+
+    def set_tuning(self, scheme, blocks, threads=256, cluster=1, run=8):
+        """Fixes the sampling launch shape (scheme "static-cluster" or "tasks")."""
+        code = {"static-cluster": 0, "tasks": 1}[scheme] if isinstance(scheme, str) else int(scheme)
+        check(lib().vp_set_tuning(self.ctx, code, int(blocks), int(threads), int(cluster),
+                                  int(run)))
 
     def last_sample_ms(self):
         ms = ctypes.c_float()
