@@ -53,6 +53,8 @@ __global__ void k_chunks(const Desc *desc, const uint32_t *members, int n_group,
                          uint64_t *chunk_base, uint32_t *head, uint32_t C) {
     __shared__ uint64_t s_cnt[1024];
     __shared__ uint64_t s_carry;
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x == 0) {
         s_carry = 0;
         chunk_base[0] = 0;
@@ -65,7 +67,8 @@ __global__ void k_chunks(const Desc *desc, const uint32_t *members, int n_group,
         if (g < n_group) {
             const Desc &d = desc[members[g]];
             const uint64_t n = d.off[d.n_hc];
-            cnt = (n + C - 1) / C;
+            const uint32_t n32 = (uint32_t)n;  // n < 2^32; 32-bit division (no FP64 units)
+            cnt = n32 / C + (n32 % C != 0u ? 1u : 0u);
         }
         s_cnt[threadIdx.x] = cnt;
         __syncthreads();
@@ -179,6 +182,8 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
     cg::cluster_group cl = cg::this_cluster();
     __shared__ EstShared sm;
     __shared__ bool s_last;
+    pdl_wait();
+    pdl_trigger();
     const int rank = (int)cl.block_rank();
     const uint32_t tb = blockIdx.x / kEstCtas;
     const int b = owner_of(tree_base, n_int, tb);
@@ -434,6 +439,8 @@ __global__ void __launch_bounds__(kSubH) k_alloc(const Desc *desc, const uint32_
     __shared__ unsigned long long s_w[8];
     __shared__ bool s_last;
     __shared__ unsigned long long s_carry;
+    pdl_wait();
+    pdl_trigger();
     const uint32_t tb = blockIdx.x / kSub;
     const int b = owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
@@ -486,6 +493,7 @@ __global__ void __launch_bounds__(kSubH) k_alloc(const Desc *desc, const uint32_
 __global__ void __launch_bounds__(kSubH) k_offsets(const Desc *desc, const uint32_t *tree_base,
                                                    int n_int) {
     __shared__ unsigned long long s_w[8];
+    pdl_wait();
     const uint32_t tb = blockIdx.x / kSub;
     const int b = owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
@@ -534,6 +542,7 @@ __global__ void __cluster_dims__(kRefineCtas, 1, 1) __launch_bounds__(kRefineThr
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     __shared__ RefineShared sm;
+    pdl_wait();
     const int rank = (int)cl.block_rank();
     const uint32_t axis_id = blockIdx.x / kRefineCtas;
     const int b = owner_of(axis_base, n_int, axis_id);
@@ -670,34 +679,51 @@ __global__ void __cluster_dims__(kRefineCtas, 1, 1) __launch_bounds__(kRefineThr
 }
 
 // ---------------------------------------------------------------------------
-// Host-side launchers.
+// Host-side launchers: programmatic dependent launches (each kernel waits for
+// its predecessor in pdl_wait), so that a kernel's launch overlaps the end of
+// the one before it.
 // ---------------------------------------------------------------------------
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 cudaError_t launch_chunks(const Desc *desc, const uint32_t *members, int n_group,
                           uint64_t *chunk_base, uint32_t *head, uint32_t C, cudaStream_t s) {
-    k_chunks<<<1, 1024, 0, s>>>(desc, members, n_group, chunk_base, head, C);
-    return cudaGetLastError();
+    return launch_pdl(k_chunks, dim3(1), dim3(1024), s, desc, members, n_group, chunk_base, head,
+                      C);
 }
 
 cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_int,
                             uint32_t n_blocks, int mode, cudaStream_t s) {
-    k_estimate<<<n_blocks * kEstCtas, 256, 0, s>>>(desc, tree_base, n_int, mode);
-    return cudaGetLastError();
+    return launch_pdl(k_estimate, dim3(n_blocks * kEstCtas), dim3(256), s, desc, tree_base, n_int,
+                      mode);
 }
 
 cudaError_t launch_alloc(const Desc *desc, const uint32_t *tree_base, int n_int,
                          uint32_t n_blocks, cudaStream_t s, int initial) {
-    k_alloc<<<n_blocks * kSub, kSubH, 0, s>>>(desc, tree_base, n_int, initial);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_alloc, dim3(n_blocks * kSub), dim3(kSubH), s, desc, tree_base,
+                               n_int, initial);
     if (e != cudaSuccess) return e;
-    k_offsets<<<n_blocks * kSub, kSubH, 0, s>>>(desc, tree_base, n_int);
-    return cudaGetLastError();
+    return launch_pdl(k_offsets, dim3(n_blocks * kSub), dim3(kSubH), s, desc, tree_base, n_int);
 }
 
 cudaError_t launch_refine(const Desc *desc, const uint32_t *axis_base, int n_int,
                           uint32_t n_axes, int max_ng, cudaStream_t s) {
     (void)max_ng;
-    k_refine<<<n_axes * kRefineCtas, kRefineThreads, 0, s>>>(desc, axis_base, n_int);
-    return cudaGetLastError();
+    return launch_pdl(k_refine, dim3(n_axes * kRefineCtas), dim3(kRefineThreads), s, desc,
+                      axis_base, n_int);
 }
 
 }  // namespace vp

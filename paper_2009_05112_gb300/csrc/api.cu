@@ -113,6 +113,7 @@ struct Set {
     bool timed = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    uint64_t iters = 0;  // iterations issued (host count)
     bool merge = false;  // one launch per (kind, precision): the largest bucket serves all
 };
 
@@ -379,8 +380,8 @@ vp_status vp::group_config_many(const std::vector<const Member *> &m, Group &g, 
     std::stable_sort(g.members.begin(), g.members.end(), [&](uint32_t a, uint32_t b) {
         return m[a]->p.n_ev > m[b]->p.n_ev;
     });
-    const size_t tbytes = g.prec == VP_FP64 ? 8 : 4;
-    const size_t hist_bytes = (size_t)max_bins * (tbytes + 4);
+    // per bin: an FP64 sum, or an FP32 sum and an FP32 tiny sum; a count
+    const size_t hist_bytes = (size_t)max_bins * 12;
     g.threads = 256;
     g.r = 8;
     g.hist_words = max_bins;
@@ -729,6 +730,7 @@ struct TuneKey {
 struct TuneVal {
     bool one;
     int blocks, cs, r, threads;
+    bool final;  // measured on an adapted state
 };
 static std::mutex g_tune_mu;
 static std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
@@ -756,14 +758,19 @@ void vp::set_task(Group &g, double expect) {
     g.task = (g.task + wchunk - 1) / wchunk * wchunk;
 }
 
+static bool tune_due(const Set &s, const Group &g) {
+    return !g.tuned || (!g.tuned_final && s.iters >= (uint64_t)kRetuneIt);
+}
+
 static vp_status tune(Set &s, cudaStream_t stream) {
     bool pending = false;
-    for (auto &g : s.groups) pending |= !g.tuned;
+    for (auto &g : s.groups) pending |= tune_due(s, g);
     if (!pending) return VP_OK;
     CU(cudaStreamSynchronize(s.last));
     CU(cudaStreamSynchronize(stream));
     for (auto &g : s.groups) {
-        if (g.tuned) continue;
+        if (!tune_due(s, g)) continue;
+        const bool adapted = s.iters >= (uint64_t)kRetuneIt;
         {
             double expect0 = 0.0;
             for (uint32_t i : g.members) expect0 += (double)s.m[i].p.n_ev + 2.0 * (double)s.m[i].n_hc;
@@ -771,7 +778,7 @@ static vp_status tune(Set &s, cudaStream_t stream) {
             std::lock_guard<std::mutex> lock(g_tune_mu);
             bool hit = false;
             for (auto &kv : g_tune_cache)
-                if (kv.first == key) {
+                if (kv.first == key && (kv.second.final || !adapted)) {
                     g.one = kv.second.one;
                     g.blocks = kv.second.blocks;
                     g.cs = kv.second.cs;
@@ -780,6 +787,7 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                     g.args1.r = g.r;
                     set_task(g, expect0);
                     g.tuned = true;
+                    g.tuned_final = kv.second.final;
                     hit = true;
                     break;
                 }
@@ -818,6 +826,7 @@ static vp_status tune(Set &s, cudaStream_t stream) {
             for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r, 256});
         if (cands.size() <= 1) {
             g.tuned = true;
+            g.tuned_final = true;
             continue;
         }
         const Cand keep = {g.one, g.blocks, g.cs, g.r, g.threads_one};
@@ -847,10 +856,18 @@ static vp_status tune(Set &s, cudaStream_t stream) {
         g.args1.r = best.r;
         set_task(g, expect);
         g.tuned = true;
+        g.tuned_final = adapted;
         {
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tune_cache.push_back(
-                {tune_key(s, g, expect), {g.one, g.blocks, g.cs, g.r, g.threads_one}});
+            const TuneKey key = tune_key(s, g, expect);
+            const TuneVal val = {g.one, g.blocks, g.cs, g.r, g.threads_one, adapted};
+            bool found = false;
+            for (auto &kv : g_tune_cache)
+                if (kv.first == key) {
+                    if (adapted || !kv.second.final) kv.second = val;
+                    found = true;
+                }
+            if (!found) g_tune_cache.push_back({key, val});
         }
         // clear what the tuning launches accumulated (buffer t & 1 of each member)
         for (uint32_t i : g.members) {
@@ -907,6 +924,7 @@ static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = fals
     }
     CU(cudaEventRecordWithFlags(s.ev1, stream, ev_flags));
     s.timed = true;
+    if (cap != cudaStreamCaptureStatusActive) ++s.iters;
     if (refine_too && s.any_refine) {  // the step graph: a8 beside a6 and a7
         vp_status st = fork_refine(s, stream);
         if (st != VP_OK) return st;
@@ -932,6 +950,15 @@ static vp_status set_adapt(Set &s, cudaStream_t stream, bool refine_forked = fal
 }
 
 static vp_status set_step(Set &s, cudaStream_t stream) {
+    bool due = false;
+    for (auto &g : s.groups) due |= tune_due(s, g);
+    if (due && s.gexec) {  // a new launch shape: capture the step again
+        CU(cudaStreamSynchronize(s.last));
+        cudaGraphExecDestroy(s.gexec);
+        cudaGraphDestroy(s.graph);
+        s.gexec = nullptr;
+        s.graph = nullptr;
+    }
     if (!s.gexec) {
         vp_status tst = tune(s, stream);  // before the capture: tuning synchronises
         if (tst != VP_OK) return tst;
@@ -955,6 +982,7 @@ static vp_status set_step(Set &s, cudaStream_t stream) {
         CU(cudaGraphInstantiate(&s.gexec, s.graph, 0));
     }
     CU(cudaGraphLaunch(s.gexec, stream));
+    ++s.iters;
     s.last = stream;
     return VP_OK;
 }
@@ -1332,6 +1360,7 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     g.cs = cluster;
     g.r = run;
     g.threads_one = threads;
+    g.tuned_final = true;
     g.args1.r = run;
     double expect = 0.0;
     for (uint32_t i : g.members) expect += (double)c->set.m[i].p.n_ev + 2.0 * (double)c->set.m[i].n_hc;

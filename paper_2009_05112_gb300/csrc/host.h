@@ -77,7 +77,12 @@ struct Group {
     SampleOne args1;
     int occ_one = 0, occ_many = 0;  // resident CTAs per SM of each kernel
     bool tuned = false;
+    // tuned on an adapted state (or fixed by the caller): the first tuning runs
+    // on the uniform grid of iteration 0, whose costs differ from later ones,
+    // so the shape is measured once more after kRetuneIt iterations
+    bool tuned_final = false;
 };
+constexpr int kRetuneIt = 4;
 
 enum {
     B_EDGES, B_TAB, B_PRM, B_PRM32, B_NH, B_OFF, B_S1, B_S2, B_DH, B_HSUM, B_HCNT, B_PART,

@@ -26,8 +26,18 @@ static cudaError_t launch_many(bool f64, int bucket, bool exact, int kind, dim3 
                                size_t smem, cudaStream_t s, const SampleArgs &a) {
     const void *k = pick(f64, bucket, exact, kind, false);
     if (!k) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];  // programmatic dependent launch (the kernel waits first)
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     void *args[] = {(void *)&a};
-    return cudaLaunchKernel(k, grid, block, args, smem, s);
+    return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 static cudaError_t launch_one(bool f64, int bucket, bool exact, int kind, dim3 grid, dim3 block,
@@ -39,13 +49,15 @@ static cudaError_t launch_one(bool f64, int bucket, bool exact, int kind, dim3 g
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // (the kernel waits first)
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     void *args[] = {(void *)&a};
     return cudaLaunchKernelExC(&cfg, k, args);
 }

@@ -490,6 +490,7 @@ template <> struct Acc<true> {
     double s1, s2;
     __device__ __forceinline__ void reset() { s1 = 0.0; s2 = 0.0; }
     __device__ __forceinline__ void add(double v, double v2) { s1 += v; s2 += v2; }
+    __device__ __forceinline__ void add_tiny(double, double) {}  // (FP32 path only)
     // adds the sums, unscaled by 2^-sexp, to the hypercube's FP64 accumulators
     __device__ __forceinline__ void flush(double *p1, double *p2, int sexp) const {
         const double u = pow2d(-sexp);
@@ -497,9 +498,17 @@ template <> struct Acc<true> {
         red_add(p2, s2 * (u * u));
     }
 };
+// FP32 samples whose v = J f 2^sexp lies far below the iteration's scale
+// (2^-163 <= |v| < 2^-60; most samples of a narrow peak's tails) are summed
+// apart, scaled by 2^kTinyShift, so that v^2 stays a normal FP32 number: t1, t2
+// and the "tiny" shared histogram (plain FP32 sums: such terms only matter
+// where nothing larger falls).
+constexpr int kTinyShift = 100;
+
 template <> struct Acc<false> {
     float s1, c1, s2, c2;
-    __device__ __forceinline__ void reset() { s1 = c1 = s2 = c2 = 0.0f; }
+    float t1, t2;  // sums of v 2^kTinyShift and v^2 2^(2 kTinyShift)
+    __device__ __forceinline__ void reset() { s1 = c1 = s2 = c2 = t1 = t2 = 0.0f; }
     __device__ __forceinline__ static void kahan(float &s, float &c, float v) {
         const float y = __fsub_rn(v, c);
         const float t = __fadd_rn(s, y);
@@ -510,10 +519,16 @@ template <> struct Acc<false> {
         kahan(s1, c1, v);
         kahan(s2, c2, v2);
     }
-    // the compensated sums s - c, unscaled by 2^-sexp, exactly converted
+    __device__ __forceinline__ void add_tiny(float vt, float vt2) {
+        t1 += vt;
+        t2 += vt2;
+    }
+    // the compensated sums s - c plus the tiny sums, each unscaled exactly
     __device__ __forceinline__ void flush(double *p1, double *p2, int sexp) const {
-        red_add(p1, f2d_pow2(s1, -sexp) - f2d_pow2(c1, -sexp));
-        red_add(p2, f2d_pow2(s2, -2 * sexp) - f2d_pow2(c2, -2 * sexp));
+        red_add(p1, (f2d_pow2(s1, -sexp) - f2d_pow2(c1, -sexp)) +
+                        f2d_pow2(t1, -sexp - kTinyShift));
+        red_add(p2, (f2d_pow2(s2, -2 * sexp) - f2d_pow2(c2, -2 * sexp)) +
+                        f2d_pow2(t2, -2 * (sexp + kTinyShift)));
     }
 };
 
@@ -597,7 +612,7 @@ template <int DMAX, bool EXACT, bool F64, int KIND, bool KP = false>
 __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const void *prm,
                                             uint64_t s_begin, uint64_t s_end, uint64_t h,
                                             uint64_t lo_off, uint64_t next,
-                                            typename Real<F64>::T *hs, uint32_t *hc,
+                                            typename Real<F64>::T *hs, float *hs_t, uint32_t *hc,
                                             bool hist_shared, int sexp) {
     typedef typename Real<F64>::T T;
     const int dim = EXACT ? DMAX : L.dim;
@@ -620,11 +635,12 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
         }
         int idx[DMAX];
         T v;
-        // FP32: a sample with |v| outside [2^-60, 2^60) (v^2 would overflow or
-        // underflow FP32, e.g. in the first iteration, before the scale has
-        // adapted to an integral far from the box volume) takes its own FP64 terms
-        bool big = false;
-        double vbig = 0.0;
+        // FP32: v = J f 2^sexp in [2^-60, 2^60) is summed as is, tiny v in
+        // [2^-163, 2^-60) scaled by 2^kTinyShift (see Acc); beyond those (v^2
+        // would leave FP32, e.g. in the first iteration, before the scale has
+        // adapted) a sample takes exact FP64 terms of its own
+        bool big = false, tiny = false;
+        double vbig = 0.0, vbig2 = 0.0;
         if (F64) {
             double x[DMAX], J, f;
             point64<DMAX, KIND>(L, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
@@ -635,34 +651,50 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
             point32<DMAX, EXACT, KIND, KP>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je,
                                            f);
             const float jf = Jm * f;  // normal or zero: Jm in [1, 2), f flushed to zero
-            const int ev = ((__float_as_int(jf) >> 23) & 0xff) - 127 + Je + sexp;  // exponent of v
-            if (jf != 0.0f && isfinite(jf) && (ev >= 60 || ev < -60)) {
+            const int ej = ((__float_as_int(jf) >> 23) & 0xff) - 127;
+            const int ev = ej + Je + sexp;  // exponent of v
+            const bool nz = jf != 0.0f && isfinite(jf);
+            if (nz && (ev >= 60 || ev < -163)) {
                 big = true;
-                vbig = ldexp((double)Jm * (double)f, Je);  // J f, unscaled
+                const float m = __int_as_float((__float_as_int(jf) & 0x807fffff) | 0x3f800000);
+                vbig = f2d_pow2(jf, Je);                    // J f, unscaled
+                vbig2 = f2d_pow2(m * m, 2 * (ej + Je));     // (J f)^2
                 red_add(P.S1 + h, vbig);
-                red_add(P.S2 + h, vbig * vbig);
+                red_add(P.S2 + h, vbig2);
                 v = (T)0;
             } else {
-                v = (T)scale2(jf, Je + sexp);
+                tiny = nz && ev < -60;
+                v = (T)scale2(jf, Je + sexp + (tiny ? kTinyShift : 0));
             }
         }
         const T v2 = v * v;
-        acc.add(v, v2);
+        if (F64) {
+            acc.add(v, v2);
+        } else {
+            acc.add(tiny ? (T)0 : v, tiny ? (T)0 : v2);
+            acc.add_tiny(tiny ? (float)v : 0.0f, tiny ? (float)v2 : 0.0f);
+        }
+        T *hdst = hs;
+        int hexp = -2 * sexp;
+        if (!F64 && tiny) {
+            hdst = (T *)hs_t;
+            hexp -= 2 * kTinyShift;
+        }
 #pragma unroll
         for (int mu = 0; mu < DMAX; ++mu) {
             if (mu < dim) {
                 const int b = mu * L.n_g + idx[mu];
                 if (big) {
-                    red_add(P.HS + b, vbig * vbig);
+                    red_add(P.HS + b, vbig2);
                     if (hist_shared) atomicAdd(hc + b, 1u);
                     else red_add(P.HC + b, 1u);
                 } else if (hist_shared) {
-                    if (v2 != (T)0) atomicAdd(hs + b, v2);
+                    if (v2 != (T)0) atomicAdd(hdst + b, v2);
                     atomicAdd(hc + b, 1u);
                 } else {
                     if (v2 != (T)0)
-                        red_add(P.HS + b, F64 ? (double)v2 * pow2d(-2 * sexp)
-                                              : f2d_pow2((float)v2, -2 * sexp));
+                        red_add(P.HS + b, F64 ? (double)v2 * pow2d(hexp)
+                                              : f2d_pow2((float)v2, hexp));
                     red_add(P.HC + b, 1u);
                 }
             }
@@ -682,7 +714,8 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
 // their shared-memory histograms through distributed shared memory, each CTA
 // reducing one slice of the bins, so the global flush is one reduction per bin
 // and cluster.
-// Shared memory: [prm: prm_words x 4 B][hist sum: bins x (4|8) B][hist count: bins x 4 B]
+// Shared memory: [prm: prm_words x 4 B][hist sums: bins x 8 B (FP64 sum, or FP32 sum and FP32
+// tiny sum)][hist count: bins x 4 B]
 // ---------------------------------------------------------------------------
 // Largest CTA of the one-integral kernel: the autotuner also tries one CTA per
 // SM (one shared-memory histogram per SM instead of one per 256 threads).
@@ -696,34 +729,40 @@ __host__ __device__ constexpr int one_max_threads(int dmax, bool f64) {
 // the global FP64 histograms (one reduction per bin and cluster).
 template <int CS, bool F64>
 __device__ __forceinline__ void cluster_flush(cooperative_groups::cluster_group &cl,
-                                              typename Real<F64>::T *hs, uint32_t *hc,
-                                              const Ptrs &P, int b0, int b1, int sexp) {
+                                              typename Real<F64>::T *hs, float *hs_t,
+                                              uint32_t *hc, const Ptrs &P, int b0, int b1,
+                                              int sexp) {
     typedef typename Real<F64>::T T;
     // each cluster starts at its own bin of the slice (in whole warps), so
     // that the clusters' global reductions do not queue on the same addresses
     const int n_cl = (int)(gridDim.x / CS), cid = (int)(blockIdx.x / CS);
     const int len = max(b1 - b0, 0);
-    const int rot = (int)(((uint64_t)cid * (uint64_t)len / n_cl) & ~31ull);
+    const int rot = (int)(((uint32_t)cid * (uint32_t)len / (uint32_t)n_cl) & ~31u);
     for (int q = threadIdx.x; q < len; q += blockDim.x) {
         const int b = b0 + (q + rot < len ? q + rot : q + rot - len);
         T vs[CS];
+        float vt[CS];
         uint32_t vc[CS];
 #pragma unroll
         for (int r = 0; r < CS; ++r) {  // the remote loads of a bin issued together
             vs[r] = *cl.map_shared_rank(hs + b, r);
+            vt[r] = F64 ? 0.0f : *cl.map_shared_rank(hs_t + b, r);
             vc[r] = *cl.map_shared_rank(hc + b, r);
         }
         // (the FP32 path adds the CTAs' FP32 sums in FP32, like each CTA's own)
         T sum = (T)0;
+        float sum_t = 0.0f;
         uint32_t cnt = 0;
 #pragma unroll
         for (int r = 0; r < CS; ++r) {
             sum += vs[r];
+            sum_t += vt[r];
             cnt += vc[r];
         }
         if (cnt) {
-            red_add(P.HS + b, F64 ? (double)sum * pow2d(-2 * sexp)
-                                  : f2d_pow2((float)sum, -2 * sexp));
+            double d = F64 ? (double)sum * pow2d(-2 * sexp) : f2d_pow2((float)sum, -2 * sexp);
+            if (sum_t != 0.0f) d += f2d_pow2(sum_t, -2 * (sexp + kTinyShift));
+            red_add(P.HS + b, d);
             red_add(P.HC + b, cnt);
         }
     }
@@ -738,9 +777,19 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
     constexpr bool KP = !F64 && KIND != VP_POSTERIOR;
     extern __shared__ __align__(16) unsigned char smem[];
     float *sprm = (float *)smem;
+    // histograms: sums (FP64, or FP32 and the FP32 tiny sums), then counts
     T *hs = (T *)(smem + (size_t)a.prm_words * 4);
-    uint32_t *hc = (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.bins * sizeof(T));
+    float *hs_t = (float *)(smem + (size_t)a.prm_words * 4 + (size_t)a.bins * 4);
+    uint32_t *hc = (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.bins * 8);
     const int lane = threadIdx.x & 31;
+    if (a.hist_shared) {  // (no dependence on earlier kernels: before the wait)
+        for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
+            hs[b] = (T)0;
+            if (!F64) hs_t[b] = 0.0f;
+            hc[b] = 0u;
+        }
+    }
+    pdl_wait();
 
     const uint32_t t_it = __ldcg(&a.st->t);
     const int sexp = __ldcg(&a.st->scale_exp);
@@ -765,18 +814,18 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
         for (int i = threadIdx.x; i < a.prm_words; i += blockDim.x) sprm[i] = __ldg(a.prm32 + i);
         prm = (const void *)sprm;
     }
-    if (a.hist_shared) {
-        for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
-            hs[b] = (T)0;
-            hc[b] = 0u;
-        }
-    }
     __syncthreads();
     {
-        // this warp's share of the samples, then this lane's run within it
-        const uint64_t W = (uint64_t)gridDim.x * (blockDim.x >> 5);
-        const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        const uint64_t wb = w * P.n_total / W, we = (w + 1) * P.n_total / W;
+        // this warp's share of the samples (the first n mod W warps take one
+        // more), then this lane's run within it.  32-bit arithmetic: the
+        // samples of an iteration number below 2^32, and a 64-bit division
+        // by a runtime value would run on the scarce FP64 units.
+        const uint32_t W = gridDim.x * (blockDim.x >> 5);
+        const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        const uint32_t n_tot = (uint32_t)P.n_total;
+        const uint32_t per_w = n_tot / W, extra = n_tot - per_w * W;
+        const uint64_t wb = (uint64_t)w * per_w + min(w, extra);
+        const uint64_t we = wb + per_w + (w < extra ? 1u : 0u);
         const uint64_t q = (we - wb + 31) / 32;
         const uint64_t s0 = min(wb + (uint64_t)lane * q, we);
         const uint64_t s1 = min(s0 + q, we);
@@ -787,7 +836,7 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)
                 run_samples<DMAX, EXACT, F64, KIND, KP>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
-                                                        hc, a.hist_shared != 0, sexp);
+                                                        hs_t, hc, a.hist_shared != 0, sexp);
         }
     }
     __syncthreads();
@@ -799,10 +848,10 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
         const int per = (a.bins + cs - 1) / cs;
         const int b0 = rank * per, b1 = min(a.bins, b0 + per);
         switch (cs) {
-            case 1: cluster_flush<1, F64>(cl, hs, hc, P, b0, b1, sexp); break;
-            case 2: cluster_flush<2, F64>(cl, hs, hc, P, b0, b1, sexp); break;
-            case 4: cluster_flush<4, F64>(cl, hs, hc, P, b0, b1, sexp); break;
-            default: cluster_flush<8, F64>(cl, hs, hc, P, b0, b1, sexp); break;
+            case 1: cluster_flush<1, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp); break;
+            case 2: cluster_flush<2, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp); break;
+            case 4: cluster_flush<4, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp); break;
+            default: cluster_flush<8, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp); break;
         }
         cl.sync();  // keep this CTA's shared memory until every remote read is done
     }
@@ -820,10 +869,13 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_task, s_wc;
     float *sprm = (float *)smem;
+    // histograms: sums (FP64, or FP32 and the FP32 tiny sums), then counts
     T *hs = (T *)(smem + (size_t)a.prm_words * 4);
-    uint32_t *hc = (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.hist_words * sizeof(T));
+    float *hs_t = (float *)(smem + (size_t)a.prm_words * 4 + (size_t)a.hist_words * 4);
+    uint32_t *hc = (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.hist_words * 8);
     const int lane = threadIdx.x & 31;
     const uint32_t wchunk = 32u * (uint32_t)a.r;
+    pdl_wait();
 
     int cur = -1;
     Loop L;
@@ -834,13 +886,14 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
     auto flush_hist = [&]() {
         // each CTA starts at its own bin (in whole warps), so that the CTAs'
         // global reductions do not all queue on the same addresses at once
-        const int rot = (int)(((uint64_t)blockIdx.x * (uint64_t)bins / gridDim.x) & ~31ull);
+        const int rot = (int)(((uint32_t)blockIdx.x * (uint32_t)bins / gridDim.x) & ~31u);
         for (int q = threadIdx.x; q < bins; q += blockDim.x) {
             const int b = q + rot < bins ? q + rot : q + rot - bins;
             const uint32_t n = hc[b];
             if (n) {
-                red_add(P.HS + b, F64 ? (double)hs[b] * pow2d(-2 * sexp)
-                                      : f2d_pow2((float)hs[b], -2 * sexp));
+                double d = F64 ? (double)hs[b] * pow2d(-2 * sexp) : f2d_pow2((float)hs[b], -2 * sexp);
+                if (!F64 && hs_t[b] != 0.0f) d += f2d_pow2(hs_t[b], -2 * (sexp + kTinyShift));
+                red_add(P.HS + b, d);
                 red_add(P.HC + b, n);
             }
         }
@@ -872,6 +925,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
         if (a.hist_shared) {
             for (int b = threadIdx.x; b < bins; b += blockDim.x) {
                 hs[b] = (T)0;
+                if (!F64) hs_t[b] = 0.0f;
                 hc[b] = 0u;
             }
         }
@@ -898,7 +952,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
         }
         const uint64_t t0 = (task - __ldg(a.chunk_base + g)) * (uint64_t)a.task;
         const uint64_t t1 = min(t0 + (uint64_t)a.task, P.n_total);
-        const uint32_t n_wc = (uint32_t)((t1 - t0 + wchunk - 1) / wchunk);
+        const uint32_t n_wc = ((uint32_t)(t1 - t0) + wchunk - 1) / wchunk;  // 32-bit (no FP64 units)
         for (;;) {
             uint32_t c = 0;
             if (lane == 0) c = atomicAdd(&s_wc, 1u);
@@ -913,7 +967,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)
                 run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
-                                                    hc, a.hist_shared != 0, sexp);
+                                                    hs_t, hc, a.hist_shared != 0, sexp);
         }
     }
     if (cur >= 0 && a.hist_shared) flush_hist();

@@ -140,18 +140,39 @@ __device__ __forceinline__ double pow2d(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// (double)x 2^e, exact, built from the bits of x: FP64 instructions are scarce
-// on this part (a few per SM per clock), so the FP32 path's values leave the
-// kernel without them.  |e| <= 240, so the result is a normal double.
+// (double)x 2^e built from the bits of x with integer operations only (FP64
+// instructions are scarce on this part, a few per SM per clock, so the FP32
+// path's values leave the kernels without them): exact whenever the result is
+// a normal double; below that range the result is a signed zero, above it an
+// infinity; infinities and NaNs pass through.
 __device__ __forceinline__ double f2d_pow2(float x, int e) {
     const uint32_t b = __float_as_uint(x);
-    const uint32_t ex = (b >> 23) & 0xffu;
-    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)(b >> 31) << 63);  // +-0
-    if (ex == 0u || ex == 0xffu) return (double)x * pow2d(e);  // subnormal, inf, nan
-    const uint64_t bits = ((uint64_t)(b >> 31) << 63) |
-                          ((uint64_t)(ex + (uint32_t)(1023 - 127 + e)) << 52) |
-                          ((uint64_t)(b & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)bits);
+    const uint64_t sign = (uint64_t)(b >> 31) << 63;
+    int ex = (int)((b >> 23) & 0xffu);
+    uint32_t man = b & 0x7fffffu;
+    if (ex == 0xff)  // inf, nan
+        return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((uint64_t)man << 29)));
+    if (ex == 0) {
+        if (man == 0u) return __longlong_as_double((long long)sign);  // +-0
+        const int sh = __clz((int)man) - 8;  // subnormal: normalise the mantissa
+        man = (man << sh) & 0x7fffffu;
+        ex = 1 - sh;
+    }
+    const int E = ex - 127 + e + 1023;
+    if (E <= 0) return __longlong_as_double((long long)sign);
+    if (E >= 2047) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull));
+    return __longlong_as_double((long long)(sign | ((uint64_t)E << 52) | ((uint64_t)man << 29)));
+}
+
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialisation may be scheduled while its predecessor in
+// the stream is still finishing; pdl_wait() blocks until that predecessor grid
+// has completed and its memory operations are visible (a no-op for a normal
+// launch), so every kernel calls it before reading what earlier kernels wrote.
+// pdl_trigger() lets the successor be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
