@@ -58,6 +58,17 @@ def flops_per_sample(dim, n_peaks):
     return 4 * dim + n_peaks * (3 * dim + 2) + 10
 
 
+def ops_per_sample(dim, n_peaks):
+    """Algorithmic lane operations per sample of the fused kernel (each one
+    issue slot of one lane): Philox4x32-10 6 per round (the high and low words
+    of two 32x32 products, two key XORs) x 10 rounds x ceil(D/4) calls; the map
+    7 per axis (uniform from the bits, y N_g, floor, fraction, table load, x, J);
+    the Gaussian integrand 2D + 3 per peak (difference and multiply-add per
+    axis, scale, exp2, accumulate); the moments 10 (J f, v^2, two compensated
+    adds of 4); the histograms 2 atomic adds per axis."""
+    return 60 * ((dim + 3) // 4) + 7 * dim + n_peaks * (2 * dim + 3) + 10 + 2 * dim
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -123,9 +134,13 @@ def measured_peaks():
         return {}
 
 
-def traffic_from_profile(kernel_src_hash):
-    """DRAM bytes per sampling launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+PROFILED_SAMPLES = 1114112  # samples in the launch the committed summary covers
+
+
+def traffic_from_profile(kernel_src_hash, what="traffic"):
+    """From the committed ncu summary, if it was taken on the current kernel
+    source: DRAM bytes per sampling launch ("traffic"), or the FP32 FMA + ALU
+    pipe utilisation ("fma_alu_issue", fraction of active cycles)."""
     path = os.path.join(ROOT, "profiles", "sample_kernel_four_peaks_d8.txt")
     try:
         text = open(path).read()
@@ -139,8 +154,10 @@ def traffic_from_profile(kernel_src_hash):
     if vals.get("kernel_source_sha1") != kernel_src_hash:
         return None
     try:
+        if what == "fma_alu_issue":
+            return {"fma_alu_issue_frac": float(vals["fma_alu_issue_frac"].split()[0])}
         return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+    except (KeyError, ValueError, IndexError):
         return None
 
 
@@ -169,7 +186,7 @@ def cpu_baseline(seconds=12.0):
         evals += n
         its += 1
         el = time.perf_counter() - t0
-        if el >= seconds or its >= 50:
+        if el >= seconds or its >= 400:
             break
     return {"value": evals / el, "unit": "integrand evals/s", "cores": 1, "kind": "oracle",
             "sample": "%d whole iterations (N_ev=1e6, D=8, 4 peaks, N_g=1000) of the FP64 C "
@@ -296,17 +313,30 @@ def run_ours(args):
     clocks = clk.summary()
     peaks = measured_peaks()
     max_mhz = peaks.get("sm_max_mhz", 2070.0)
+    # issue peak: SMs x 4 schedulers x 32 lanes x clock, one lane operation per
+    # slot (FP32 FMA/ALU and integer alike); the FP32 flop peak counts an FMA as 2
+    issue_peak = n_sm * 128 * max_mhz * 1e6 / 1e12     # Tops/s at the maximum SM clock
     fp32_peak = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     samples_per_step = evals / args.steps
     k1_avg_ms = sum(k1_ms) / len(k1_ms)
+    k1_tops = ops_per_sample(prob.dim, 4) * samples_per_step / (k1_avg_ms / 1e3) / 1e12
     k1_tflops = flops_per_sample(prob.dim, 4) * samples_per_step / (k1_avg_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": k1_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": k1_tflops / fp32_peak, "traffic": traffic_from_profile(kernel_source_hash()),
+    traffic = traffic_from_profile(kernel_source_hash())
+    roof = {"bound": "alu", "achieved": k1_tops, "peak": issue_peak, "unit": "Tops/s",
+            "frac": k1_tops / issue_peak,
+            "traffic": traffic * samples_per_step / PROFILED_SAMPLES if traffic else None,
             "kernel": "k_sample (fused a1-a5)", "kernel_ms": k1_avg_ms,
             "kernel_share_of_step": k1_avg_ms / (total_ms / args.steps),
-            "peak_note": "FP32 = SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % max_mhz}
+            "ops_per_sample": ops_per_sample(prob.dim, 4),
+            "peak_note": "issue slots = SMs x 4 schedulers x 32 lanes x %.0f MHz (max SM "
+                         "clock); algorithmic lane operations counted from the kernel "
+                         "source" % max_mhz,
+            "fp32": {"achieved_tflops": k1_tflops, "peak_tflops": fp32_peak,
+                     "frac": k1_tflops / fp32_peak,
+                     "flops_per_sample": flops_per_sample(prob.dim, 4)},
+            "ncu": traffic_from_profile(kernel_source_hash(), "fma_alu_issue")}
     if clocks.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = k1_tflops / (n_sm * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
+        roof["frac_at_measured_clock"] = k1_tops / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
     line = {"metric": "integrand evals/s", "value": value, "unit": "integrand evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
