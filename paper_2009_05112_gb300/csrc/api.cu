@@ -599,6 +599,7 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         L.edges = d.edges;
         a.st = d.st;
         a.off = d.off;
+        a.n_h = d.n_h;
         a.s1 = d.s1;
         a.s2 = d.s2;
         a.hsum = d.hsum;

@@ -287,6 +287,7 @@ struct SampleOne {
     Loop L;                    // t is read from the device state at launch
     State *st;
     const uint64_t *off;
+    const uint32_t *n_h;
     double *s1, *s2, *hsum;    // double-buffered bases
     uint32_t *hcnt;
     const float *prm32;
@@ -542,6 +543,7 @@ __device__ __forceinline__ void load_prm32(const Desc *dp, float *sprm, int word
 // Per-integral device pointers of the sampling loop.
 struct Ptrs {
     const uint64_t *off;
+    const uint32_t *nh;  // n_h = off[h + 1] - off[h]
     double *S1, *S2, *HS;
     uint32_t *HC;
     uint64_t n_hc, n_total;
@@ -608,12 +610,15 @@ __device__ __forceinline__ uint64_t lane_find_hcube(const uint64_t *off, uint64_
     return h;
 }
 
-template <int DMAX, bool EXACT, bool F64, int KIND, bool KP = false>
-__device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const void *prm,
-                                            uint64_t s_begin, uint64_t s_end, uint64_t h,
-                                            uint64_t lo_off, uint64_t next,
-                                            typename Real<F64>::T *hs, float *hs_t, uint32_t *hc,
-                                            bool hist_shared, int sexp) {
+// (HS: the histograms are privatised in shared memory; a template parameter
+// so that the per-axis updates carry no branch on it)
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, bool HS>
+__device__ __forceinline__ void run_samples_t(const Loop &L, const Ptrs &P, const void *prm,
+                                              uint64_t s_begin, uint64_t s_end, uint64_t h,
+                                              uint64_t lo_off, uint64_t next,
+                                              typename Real<F64>::T *hs, float *hs_t,
+                                              uint32_t *hc, int sexp) {
+    constexpr bool hist_shared = HS;
     typedef typename Real<F64>::T T;
     const int dim = EXACT ? DMAX : L.dim;
     uint32_t j = (uint32_t)(s_begin - lo_off);
@@ -623,16 +628,21 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
     if (!F64) hcube_offsets<DMAX>(L, kd, kc);
     Acc<F64> acc;
     acc.reset();
-    for (uint64_t s = s_begin; s < s_end; ++s) {
-        if (s == next) {
+    // 32-bit counters (an iteration has fewer than 2^32 samples): samples left
+    // in the run, and before the next hypercube (n_h >= 2, so at most one
+    // boundary per sample)
+    uint32_t to_next = (uint32_t)(next - s_begin);
+    for (uint32_t left = (uint32_t)(s_end - s_begin); left > 0; --left) {
+        if (to_next == 0u) {
             acc.flush(P.S1 + h, P.S2 + h, sexp);
             acc.reset();
             ++h;
-            next = __ldg(P.off + h + 1);
+            to_next = __ldg(P.nh + h);
             j = 0;
             next_digits<DMAX>(L.n_st, dim, kd);
             if (!F64) hcube_offsets<DMAX>(L, kd, kc);
         }
+        --to_next;
         int idx[DMAX];
         T v;
         // FP32: v = J f 2^sexp in [2^-60, 2^60) is summed as is, tiny v in
@@ -702,6 +712,20 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
         ++j;
     }
     acc.flush(P.S1 + h, P.S2 + h, sexp);
+}
+
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP = false>
+__device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const void *prm,
+                                            uint64_t s_begin, uint64_t s_end, uint64_t h,
+                                            uint64_t lo_off, uint64_t next,
+                                            typename Real<F64>::T *hs, float *hs_t, uint32_t *hc,
+                                            bool hist_shared, int sexp) {
+    if (hist_shared)
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, true>(L, P, prm, s_begin, s_end, h, lo_off,
+                                                        next, hs, hs_t, hc, sexp);
+    else
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, false>(L, P, prm, s_begin, s_end, h, lo_off,
+                                                         next, hs, hs_t, hc, sexp);
 }
 
 // ---------------------------------------------------------------------------
@@ -799,6 +823,7 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
     Ptrs P;
     const uint64_t par = t_it & 1u;  // accumulators of this iteration: buffer t & 1
     P.off = a.off;
+    P.nh = a.n_h;
     P.n_hc = a.n_hc;
     P.n_total = __ldcg(a.off + a.n_hc);
     P.S1 = a.s1 + par * a.n_hc;
@@ -908,6 +933,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
         sexp = __ldcg(&st->scale_exp);
         bins = L.dim * L.n_g;
         P.off = (const uint64_t *)__ldg((const unsigned long long *)&dp->off);
+        P.nh = (const uint32_t *)__ldg((const unsigned long long *)&dp->n_h);
         P.n_hc = __ldg(&dp->n_hc);
         P.n_total = __ldcg(P.off + P.n_hc);
         // accumulators of this iteration: buffer (t & 1) of the double-buffered pairs
