@@ -184,8 +184,9 @@ vp_status vp_refine_from_hist(vp_ctx *ctx, const double *hsum, const double *hcn
  * own device code: x[n][D], idx[n][D] (increment indices), jac[n], f[n]. */
 vp_status vp_eval_samples(vp_ctx *ctx, int64_t n, const uint64_t *h, const uint32_t *j,
                           uint32_t t, double *x, int32_t *idx, double *jac, double *f);
-/* Device-side timing of the latest sampling launch, in ms (CUDA events on the
- * launching stream); -1 if none recorded. */
+/* Device-side timing of the latest sampling launch made by vp_iterate, in ms
+ * (CUDA events on the launching stream; the step graph of vp_step carries no
+ * events); -1 if none recorded. */
 vp_status vp_last_sample_ms(vp_ctx *ctx, float *ms);
 /* Launch shape of the sampling kernel chosen by the autotuner (which runs at
  * the first vp_iterate/vp_step): scheme 0 = static balanced split with

@@ -269,18 +269,29 @@ void or_hcube_moments(int dim, int n_g, int64_t n_st, uint64_t seed, uint32_t in
 /* reading (summation order): every sum over hypercubes is taken in one fixed */
 /* order -- blocks of 1024 consecutive terms, each summed by pairwise halving */
 /* (term i += term i+s for s = 512, 256, ..., 1; missing terms are zero), and  */
-/* the block sums added left to right starting from zero.  This order makes    */
-/* sum_h d_h, and hence the integer n_h, reproducible bit for bit.            */
+/* the block sums combined by an adjacent pairwise tree: P leaves, P the least */
+/* power of two >= the number of blocks, leaves past the last block zero,      */
+/* level by level (leaf 2i += leaf 2i+1, then 4i += 4i+2, ...).  This order    */
+/* makes sum_h d_h, and hence the integer n_h, reproducible bit for bit.      */
 /* ------------------------------------------------------------------------ */
 double or_tree_sum(const double *v, int64_t n) {
-    double total = 0.0;
+    if (n <= 0) return 0.0;
+    const int64_t nb = (n + 1023) / 1024;
+    int64_t P = 1;
+    while (P < nb) P <<= 1;
+    double *bs = (double *)calloc((size_t)P, sizeof(double));
     double blk[1024];
-    for (int64_t base = 0; base < n; base += 1024) {
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t base = b * 1024;
         for (int i = 0; i < 1024; ++i) blk[i] = (base + i < n) ? v[base + i] : 0.0;
         for (int s = 512; s >= 1; s >>= 1)
             for (int i = 0; i < s; ++i) blk[i] = blk[i] + blk[i + s];
-        total = total + blk[0];
+        bs[b] = blk[0];
     }
+    for (int64_t w = 1; w < P; w <<= 1)
+        for (int64_t i = 0; i < P; i += 2 * w) bs[i] = bs[i] + bs[i + w];
+    const double total = bs[0];
+    free(bs);
     return total;
 }
 

@@ -8,8 +8,9 @@
 //               sigma_h = Omega sqrt(S2_h/n_h - (S1_h/n_h)^2) (§3 step 2) and
 //               d_h = sigma_h^beta (§3 Eq. dh); sums over h in the library's
 //               fixed order (blocks of 1024 hypercubes, pairwise halving inside
-//               a block, block sums left to right), so sum_h d_h -- and with it
-//               every integer n_h -- is reproducible bit for bit;
+//               a block, the block sums by an adjacent pairwise tree), so
+//               sum_h d_h -- and with it every integer n_h -- is reproducible
+//               bit for bit;
 //   k_alloc     a7: n_h = max(2, floor(N_ev d_h / sum d)) (§3 Eq. nh; or + 2;
 //               a quotient within 2^-50 q below an integer counts as that
 //               integer; the first allocation is always the equal split),
@@ -135,6 +136,8 @@ __device__ __forceinline__ double damp_var32(double var, const Desc &d) {
 // ---------------------------------------------------------------------------
 constexpr int kEstCtas = 4;
 
+__device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode);
+
 struct EstShared {
     double own[3][256];
     double recv[3][256];
@@ -257,32 +260,21 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
     }
     __syncthreads();
     if (!s_last) return;
-    // last block of this integral: block sums left to right, staged through
-    // shared memory (loads in parallel; the three sums in three warps)
+    // last block of this integral: the block sums in the fixed tree order
     __threadfence();
-    double acc = 0.0;
-    for (uint32_t q0 = 0; q0 < d.n_tree; q0 += 256) {
-        const uint32_t m = min(256u, d.n_tree - q0);
-        __syncthreads();
-        if ((uint32_t)t < m) {
-            r0[t] = __ldcg(d.part + 3 * (q0 + t) + 0);
-            r1[t] = __ldcg(d.part + 3 * (q0 + t) + 1);
-            r2[t] = __ldcg(d.part + 3 * (q0 + t) + 2);
-        }
-        __syncthreads();
-        if ((t & 31) == 0 && t < 96) {
-            const double *r = t == 0 ? r0 : (t == 32 ? r1 : r2);
-            for (uint32_t i = 0; i < m; ++i) acc = __dadd_rn(acc, r[i]);
-        }
-    }
     __syncthreads();
-    if (t == 32) r1[0] = acc;
-    if (t == 64) r2[0] = acc;
-    __syncthreads();
+    double tot[3];
+    block_tree_sum<3>(d.part, d.n_tree, &sm.red[0][0], tot);
     if (t != 0) return;
-    const double I = acc, V = r1[0], Sd = r2[0];
+    d.st->done_est = 0u;
+    finish_estimate(d, tot[0], tot[1], tot[2], mode);
+}
+
+// The iteration's totals I_j, sigma_j^2 and sum d recorded in the state (one
+// thread): history, the FP32 path's scale, the iteration count and, for a
+// served request, the stop rule.
+__device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode) {
     State *st = d.st;
-    st->done_est = 0u;
     st->sum_d = Sd;
     st->inv_sum_d = Sd > 0.0 ? 1.0 / Sd : 0.0;
     if (mode == 0) {

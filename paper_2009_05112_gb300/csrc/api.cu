@@ -916,15 +916,18 @@ static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = fals
             CU(launch_chunks(s.d_desc, g.d_members, (int)g.members.size(), g.d_chunk_base,
                              g.d_head, g.task, stream));
     }
-    // inside the step graph's capture the events must be external record nodes
-    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
-    CU(cudaEventRecordWithFlags(s.ev0, stream, ev_flags));
+    // the sampling launch is timed by events outside the step graph only: as
+    // record nodes inside it they would add several microseconds to every step
+    const bool timed = cap != cudaStreamCaptureStatusActive;
+    if (timed) CU(cudaEventRecord(s.ev0, stream));
     for (size_t gi = 0; gi < s.groups.size(); ++gi) {
         vp_status st = launch_group(s.d_desc, s.groups[gi], stream);
         if (st != VP_OK) return st;
     }
-    CU(cudaEventRecordWithFlags(s.ev1, stream, ev_flags));
-    s.timed = true;
+    if (timed) {
+        CU(cudaEventRecord(s.ev1, stream));
+        s.timed = true;
+    }
     if (cap != cudaStreamCaptureStatusActive) ++s.iters;
     if (refine_too && s.any_refine) {  // the step graph: a8 beside a6 and a7
         vp_status st = fork_refine(s, stream);

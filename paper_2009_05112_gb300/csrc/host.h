@@ -20,6 +20,7 @@ cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, 
 cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t, int initial);
 cudaError_t launch_refine(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
 
+
 // the calling thread's last error message (vp_last_error)
 extern thread_local std::string g_err;
 vp_status fail(vp_status s, const char *fmt, ...);

@@ -67,11 +67,13 @@ __global__ void __launch_bounds__(512) ks_sum(const double *d_h, uint64_t n_hc,
         s_last = atomicAdd(&sc->done_sum, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
-    double S = 0.0;
-    for (unsigned q = 0; q < gridDim.x; ++q) S = __dadd_rn(S, __ldcg(sc->part + q));
-    sc->sum_d = S;
+    __syncthreads();
+    double S[1];  // the block sums in the library's fixed tree order
+    vp::block_tree_sum<1>(sc->part, gridDim.x, sh, S);
+    if (threadIdx.x != 0) return;
+    sc->sum_d = S[0];
     sc->done_sum = 0u;
 }
 

@@ -26,6 +26,7 @@ constexpr int kInvTab = 4096;      // table of 1/n for small integers n
 // Status bits (State::status).
 constexpr uint32_t kStatusNonFinite = 1u;
 
+
 // Mutable per-integral scalars, device resident.
 struct State {
     uint32_t t;           // iterations done = Philox counter word 2 of the next one
@@ -162,6 +163,65 @@ __device__ __forceinline__ double f2d_pow2(float x, int e) {
     if (E <= 0) return __longlong_as_double((long long)sign);
     if (E >= 2047) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull));
     return __longlong_as_double((long long)(sign | ((uint64_t)E << 52) | ((uint64_t)man << 29)));
+}
+
+// The library's fixed order for combining the block sums (each the sum of a
+// block of kTreeBlock hypercubes): an adjacent pairwise tree over P leaves, P
+// the least power of two >= n, leaves past n zero, level by level (leaf 2i +
+// leaf 2i+1, then 4i + 4i+2, ...); its depth is log2 P, where adding the block
+// sums left to right would chain n dependent FP64 additions (slow on this
+// part).  One CTA (blockDim.x a power of two) evaluates it: thread t takes the
+// aligned run of Q = P / T leaves [t Q, (t + 1) Q) (T = min(P, blockDim.x))
+// and reduces it with a binary counter, which builds exactly the tree
+// restricted to the run; the T run sums are then combined level by level in
+// shared memory.  NS series at once, leaf i of series c at part[NS i + c]
+// (read through L2: written by other CTAs); sh holds NS x blockDim.x doubles.
+// Every thread calls it; the sums are returned in thread 0.
+template <int NS>
+__device__ void block_tree_sum(const double *part, uint32_t n, double *sh, double (&out)[NS]) {
+    uint32_t P = 1;
+    while (P < n) P <<= 1;
+    const uint32_t nt = blockDim.x, t = threadIdx.x;
+    const uint32_t T = P < nt ? P : nt;
+    const uint32_t Q = P / T;
+    double run[NS];
+#pragma unroll
+    for (int c = 0; c < NS; ++c) run[c] = 0.0;
+    if (t < T) {
+        double st[NS][24];  // one partial sum per tree level (Q <= 2^23)
+        uint32_t full = 0u;  // bit l: st[.][l] holds a complete subtree of 2^l leaves
+        for (uint32_t j = 0; j < Q; ++j) {
+            const uint32_t i = t * Q + j;
+            double carry[NS];
+#pragma unroll
+            for (int c = 0; c < NS; ++c) carry[c] = i < n ? __ldcg(part + (size_t)NS * i + c) : 0.0;
+            int l = 0;
+            while (full & (1u << l)) {
+#pragma unroll
+                for (int c = 0; c < NS; ++c) carry[c] = __dadd_rn(st[c][l], carry[c]);
+                full &= ~(1u << l);
+                ++l;
+            }
+#pragma unroll
+            for (int c = 0; c < NS; ++c) st[c][l] = carry[c];
+            full |= 1u << l;
+        }
+        const int top = __ffs((int)full) - 1;  // Q is a power of two: one subtree is left
+#pragma unroll
+        for (int c = 0; c < NS; ++c) run[c] = st[c][top];
+    }
+#pragma unroll
+    for (int c = 0; c < NS; ++c) sh[c * nt + t] = run[c];
+    __syncthreads();
+    for (uint32_t w = 1; w < T; w <<= 1) {
+        if (t < T && (t & (2 * w - 1)) == 0) {
+#pragma unroll
+            for (int c = 0; c < NS; ++c) sh[c * nt + t] = __dadd_rn(sh[c * nt + t], sh[c * nt + t + w]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < NS; ++c) out[c] = sh[c * nt];
 }
 
 // Programmatic dependent launch (sm_90 and later).  A kernel launched with

@@ -245,10 +245,18 @@ def test_posterior_integrand_closed_form():
 def test_tree_sum_order_and_accuracy():
     # pairing within a block is i with i + s for halving s: (1 + 1) + (1e16 - 1e16) = 2
     assert oracle.tree_sum([1.0, 1e16, 1.0, -1e16]) == 2.0
-    # block sums are added left to right from zero: (1 + 1e16) - 1e16 = 0
-    v = np.zeros(3 * 1024)
-    v[0], v[1024], v[2048] = 1.0, 1e16, -1e16
+    # block sums are combined by an adjacent pairwise tree:
+    # (1e16 + 1) + (-1e16 + 1) = 1e16 - 1e16 = 0, where pairing block i with
+    # i + 2 would give (1e16 - 1e16) + (1 + 1) = 2 and left to right
+    # ((1e16 + 1) - 1e16) + 1 = 1
+    v = np.zeros(4 * 1024)
+    v[0], v[1024], v[2048], v[3072] = 1e16, 1.0, -1e16, 1.0
     assert oracle.tree_sum(v) == 0.0
+    # five blocks: the tree has eight leaves, the last three zero:
+    # ((1e16 + 1) + (-1e16 + 0)) + ((1 + 0) + (0 + 0)) = 0 + 1 = 1
+    v = np.zeros(5 * 1024)
+    v[0], v[1024], v[2048], v[4096] = 1e16, 1.0, -1e16, 1.0
+    assert oracle.tree_sum(v) == 1.0
     # integers are exact; random values within the pairwise error bound of fsum
     assert oracle.tree_sum(np.arange(5000, dtype=float)) == 5000 * 4999 / 2
     rng = np.random.default_rng(1)
