@@ -759,6 +759,9 @@ void vp::set_task(Group &g, double expect) {
     g.task = (g.task + wchunk - 1) / wchunk * wchunk;
 }
 
+// Launches of fewer samples than this keep the planned shape untuned.
+constexpr double kTuneMinSamples = 262144.0;
+
 static bool tune_due(const Set &s, const Group &g) {
     return !g.tuned || (!g.tuned_final && s.iters >= (uint64_t)kRetuneIt);
 }
@@ -798,6 +801,11 @@ static vp_status tune(Set &s, cudaStream_t stream) {
         const bool can_one = g.members.size() == 1;
         double expect = 0.0;
         for (uint32_t i : g.members) expect += (double)s.m[i].p.n_ev + 2.0 * (double)s.m[i].n_hc;
+        if (expect < kTuneMinSamples) {  // a small launch: measuring costs more than it saves
+            g.tuned = true;
+            g.tuned_final = true;
+            continue;
+        }
         if (can_one && g.one) {
             // CTAs of 256 threads (1..3 per SM), or one larger CTA per SM
             const int max_threads = one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64);
