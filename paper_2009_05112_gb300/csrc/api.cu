@@ -335,24 +335,40 @@ static vp_status plan_groups(Set &s) {
         }
         if (!g.one) continue;
         // a single integral: the cluster kernel with its constants in parameters
-        // (the autotuner may still choose the task kernel)
+        // (the autotuner may still choose the task kernel).  Its histograms:
+        // the full shared layout (12 B per bin) when it fits one CTA per SM,
+        // else the compact one (8 B; FP32 tiny terms go to global memory)
+        {
+            const size_t prm_bytes = (size_t)g.prm_words * 4;
+            const size_t bins = (size_t)g.hist_words;
+            if (prm_bytes + bins * 12 <= kOneSmemMax) {
+                g.hist_one = kHistShared;
+                g.smem_one = prm_bytes + bins * 12;
+            } else if (g.prec == VP_FP32 && prm_bytes + bins * 8 <= kOneSmemMax) {
+                g.hist_one = kHistCompact;
+                g.smem_one = prm_bytes + bins * 8;
+            } else {
+                g.hist_one = kHistGlobal;
+                g.smem_one = prm_bytes;
+            }
+        }
         cudaError_t e = g.prec == VP_FP64
-                            ? sample_smem_config_f64(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem, 48 * 1024))
-                            : sample_smem_config_f32(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem, 48 * 1024));
+                            ? sample_smem_config_f64(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem_one, 48 * 1024))
+                            : sample_smem_config_f32(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem_one, 48 * 1024));
         if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
         g.occ_one = g.prec == VP_FP64
-                        ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, g.threads, g.smem)
-                        : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, g.threads, g.smem);
-        if (g.occ_one < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem);
+                        ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, g.threads, g.smem_one)
+                        : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, g.threads, g.smem_one);
+        if (g.occ_one < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem_one);
         g.blocks = s.n_sm * std::min(g.occ_one, 2);  // until the autotuner has measured
-        if (g.hist_shared) {
+        if (g.hist_one) {
             // the largest cluster that keeps (nearly) every CTA slot busy
             int best = g.blocks;
             g.cs = 1;
             for (int cs : {2, 4, 8}) {  // (the kernel's reduction handles up to 8)
                 const int ctas = g.prec == VP_FP64
-                                     ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem)
-                                     : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem);
+                                     ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem_one)
+                                     : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem_one);
                 if (ctas >= (int)(0.97 * g.blocks) && ctas >= cs) {
                     g.cs = cs;
                     best = ctas / cs * cs;
@@ -610,7 +626,7 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         a.head = g.d_head;
         a.exit_count = g.d_head + 1;
         a.r = g.r;
-        a.hist_shared = g.hist_shared;
+        a.hist_shared = g.hist_one;
         a.bins = d.dim * d.n_g;
         a.prm_words = g.prm_words;
         a.kp_peaks = 0;
@@ -666,8 +682,8 @@ vp_status vp::launch_group(const Desc *d_desc, Group &g, cudaStream_t stream) {
     cudaError_t e;
     if (g.one) {
         e = g.prec == VP_FP64
-                ? launch_sample_one_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads_one, g.smem, g.cs, stream, g.args1)
-                : launch_sample_one_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads_one, g.smem, g.cs, stream, g.args1);
+                ? launch_sample_one_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads_one, g.smem_one, g.cs, stream, g.args1)
+                : launch_sample_one_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads_one, g.smem_one, g.cs, stream, g.args1);
     } else {
         SampleArgs a;
         a.desc = d_desc;
@@ -743,7 +759,7 @@ static TuneKey tune_key(const Set &s, const Group &g, double expect) {
     k.bucket = g.bucket;
     k.exact = g.exact;
     k.kind = g.kind;
-    k.hist_shared = g.hist_shared;
+    k.hist_shared = g.hist_shared * 4 + g.hist_one;
     k.bins = g.hist_words;
     k.prm_words = g.prm_words;
     k.members = (int)g.members.size();
@@ -812,17 +828,17 @@ static vp_status tune(Set &s, cudaStream_t stream) {
             for (int threads : {256, 512, 768}) {
                 if (threads > max_threads) continue;
                 const int occ = g.prec == VP_FP64
-                                    ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem)
-                                    : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem);
+                                    ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one)
+                                    : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem_one);
                 for (int k = 1; k <= std::min(threads == 256 ? 3 : 1, occ); ++k) {
                     const int blocks = k * s.n_sm;
                     for (int cs : {1, 2, 4, 8}) {
-                        if (cs > 1 && !g.hist_shared) continue;
+                        if (cs > 1 && !g.hist_one) continue;
                         int ctas = blocks;
                         if (cs > 1) {
                             ctas = g.prec == VP_FP64
-                                       ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem)
-                                       : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem);
+                                       ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem_one)
+                                       : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem_one);
                             ctas = std::min(ctas, blocks) / cs * cs;
                             if (ctas < (int)(0.9 * blocks)) continue;
                         }
@@ -1343,18 +1359,18 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     if (scheme == 1 && cluster != 1) return fail(VP_EINVAL, "the task scheme takes no clusters");
     if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
         return fail(VP_EINVAL, "cluster must be 1, 2, 4 or 8");
-    if (cluster > 1 && !g.hist_shared)
+    if (cluster > 1 && !(scheme == 0 ? g.hist_one : g.hist_shared))
         return fail(VP_EINVAL, "clusters need shared-memory histograms");
     if (blocks % cluster) return fail(VP_EINVAL, "blocks must be a multiple of the cluster");
     if (scheme == 0) {
         // the static split assumes every CTA resident at once
         const int occ = g.prec == VP_FP64
-                            ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem)
-                            : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem);
+                            ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one)
+                            : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem_one);
         const int res = cluster > 1
                             ? (g.prec == VP_FP64
-                                   ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem)
-                                   : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem))
+                                   ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem_one)
+                                   : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem_one))
                             : occ * c->set.n_sm;
         if (blocks > res)
             return fail(VP_EINVAL, "%d CTAs in clusters of %d exceed the %d resident ones", blocks,

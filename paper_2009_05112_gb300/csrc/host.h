@@ -75,6 +75,10 @@ struct Group {
     bool one = false;  // a single integral: the cluster kernel with constants in parameters
     int cs = 1;        // CTAs per cluster (one-integral kernel)
     int threads_one = 256;  // CTA size of the one-integral kernel
+    // histograms of the one-integral kernel (one CTA per SM fits more shared
+    // memory than the task kernel's two): kHist* mode and dynamic shared bytes
+    int hist_one = 0;
+    size_t smem_one = 0;
     SampleOne args1;
     int occ_one = 0, occ_many = 0;  // resident CTAs per SM of each kernel
     bool tuned = false;

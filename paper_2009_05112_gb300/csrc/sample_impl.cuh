@@ -28,6 +28,17 @@
 
 namespace vp {
 
+// Histogram layouts of the sampling kernels:
+//   kHistGlobal   FP64 sums and counts with global atomics per sample;
+//   kHistShared   per CTA in shared memory, per bin an FP64 sum (FP64 path) or
+//                 an FP32 sum and an FP32 tiny-term sum (FP32 path), and a
+//                 count: 12 B;
+//   kHistCompact  (one-integral kernel, FP32) an FP32 sum and a count, 8 B;
+//                 tiny terms go to the global FP64 sums.
+constexpr int kHistGlobal = 0, kHistShared = 1, kHistCompact = 2;
+// dynamic shared memory the one-integral kernel may use (one CTA per SM)
+constexpr size_t kOneSmemMax = 220 * 1024;
+
 // Launch arguments when the launch serves several integrals (tasks).
 struct SampleArgs {
     const Desc *desc;          // [n_int] descriptors of the whole set
@@ -296,7 +307,7 @@ struct SampleOne {
     uint32_t *head;            // queue head (warp chunks)
     uint32_t *exit_count;
     int r;
-    int hist_shared;
+    int hist_shared;           // kHist* layout of the histograms
     int bins;
     int prm_words;
     int kp_peaks;              // > 0: the peak constants are in kp (FP32 peak families)
@@ -610,15 +621,16 @@ __device__ __forceinline__ uint64_t lane_find_hcube(const uint64_t *off, uint64_
     return h;
 }
 
-// (HS: the histograms are privatised in shared memory; a template parameter
-// so that the per-axis updates carry no branch on it)
-template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, bool HS>
+// (HM: the histogram layout, kHist*; a template parameter so that the
+// per-axis updates carry no branch on it)
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, int HM>
 __device__ __forceinline__ void run_samples_t(const Loop &L, const Ptrs &P, const void *prm,
                                               uint64_t s_begin, uint64_t s_end, uint64_t h,
                                               uint64_t lo_off, uint64_t next,
                                               typename Real<F64>::T *hs, float *hs_t,
                                               uint32_t *hc, int sexp) {
-    constexpr bool hist_shared = HS;
+    constexpr bool hist_shared = HM != kHistGlobal;
+    constexpr bool compact = HM == kHistCompact;
     typedef typename Real<F64>::T T;
     const int dim = EXACT ? DMAX : L.dim;
     uint32_t j = (uint32_t)(s_begin - lo_off);
@@ -699,7 +711,11 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Ptrs &P, cons
                     if (hist_shared) atomicAdd(hc + b, 1u);
                     else red_add(P.HC + b, 1u);
                 } else if (hist_shared) {
-                    if (v2 != (T)0) atomicAdd(hdst + b, v2);
+                    if (compact && tiny) {  // (FP32 only) the tiny sum to global memory
+                        if (v2 != (T)0) red_add(P.HS + b, f2d_pow2((float)v2, hexp));
+                    } else if (v2 != (T)0) {
+                        atomicAdd(hdst + b, v2);
+                    }
                     atomicAdd(hc + b, 1u);
                 } else {
                     if (v2 != (T)0)
@@ -719,13 +735,16 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const 
                                             uint64_t s_begin, uint64_t s_end, uint64_t h,
                                             uint64_t lo_off, uint64_t next,
                                             typename Real<F64>::T *hs, float *hs_t, uint32_t *hc,
-                                            bool hist_shared, int sexp) {
-    if (hist_shared)
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, true>(L, P, prm, s_begin, s_end, h, lo_off,
-                                                        next, hs, hs_t, hc, sexp);
+                                            int hist_mode, int sexp) {
+    if (hist_mode == kHistShared)
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistShared>(L, P, prm, s_begin, s_end, h,
+                                                               lo_off, next, hs, hs_t, hc, sexp);
+    else if (!F64 && hist_mode == kHistCompact)
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistCompact>(L, P, prm, s_begin, s_end, h,
+                                                                lo_off, next, hs, hs_t, hc, sexp);
     else
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, false>(L, P, prm, s_begin, s_end, h, lo_off,
-                                                         next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistGlobal>(L, P, prm, s_begin, s_end, h,
+                                                               lo_off, next, hs, hs_t, hc, sexp);
 }
 
 // ---------------------------------------------------------------------------
@@ -755,7 +774,7 @@ template <int CS, bool F64>
 __device__ __forceinline__ void cluster_flush(cooperative_groups::cluster_group &cl,
                                               typename Real<F64>::T *hs, float *hs_t,
                                               uint32_t *hc, const Ptrs &P, int b0, int b1,
-                                              int sexp) {
+                                              int sexp, bool tiny_sums) {
     typedef typename Real<F64>::T T;
     // each cluster starts at its own bin of the slice (in whole warps), so
     // that the clusters' global reductions do not queue on the same addresses
@@ -770,7 +789,7 @@ __device__ __forceinline__ void cluster_flush(cooperative_groups::cluster_group 
 #pragma unroll
         for (int r = 0; r < CS; ++r) {  // the remote loads of a bin issued together
             vs[r] = *cl.map_shared_rank(hs + b, r);
-            vt[r] = F64 ? 0.0f : *cl.map_shared_rank(hs_t + b, r);
+            vt[r] = (F64 || !tiny_sums) ? 0.0f : *cl.map_shared_rank(hs_t + b, r);
             vc[r] = *cl.map_shared_rank(hc + b, r);
         }
         // (the FP32 path adds the CTAs' FP32 sums in FP32, like each CTA's own)
@@ -801,15 +820,18 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
     constexpr bool KP = !F64 && KIND != VP_POSTERIOR;
     extern __shared__ __align__(16) unsigned char smem[];
     float *sprm = (float *)smem;
-    // histograms: sums (FP64, or FP32 and the FP32 tiny sums), then counts
+    // histograms: sums (FP64, or FP32 and -- unless compact -- the FP32 tiny
+    // sums), then counts
+    const bool compact = a.hist_shared == kHistCompact;
     T *hs = (T *)(smem + (size_t)a.prm_words * 4);
     float *hs_t = (float *)(smem + (size_t)a.prm_words * 4 + (size_t)a.bins * 4);
-    uint32_t *hc = (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.bins * 8);
+    uint32_t *hc =
+        (uint32_t *)(smem + (size_t)a.prm_words * 4 + (size_t)a.bins * (compact ? 4 : 8));
     const int lane = threadIdx.x & 31;
     if (a.hist_shared) {  // (no dependence on earlier kernels: before the wait)
         for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
             hs[b] = (T)0;
-            if (!F64) hs_t[b] = 0.0f;
+            if (!F64 && !compact) hs_t[b] = 0.0f;
             hc[b] = 0u;
         }
     }
@@ -861,7 +883,7 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)
                 run_samples<DMAX, EXACT, F64, KIND, KP>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
-                                                        hs_t, hc, a.hist_shared != 0, sexp);
+                                                        hs_t, hc, a.hist_shared, sexp);
         }
     }
     __syncthreads();
@@ -873,10 +895,10 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
         const int per = (a.bins + cs - 1) / cs;
         const int b0 = rank * per, b1 = min(a.bins, b0 + per);
         switch (cs) {
-            case 1: cluster_flush<1, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp); break;
-            case 2: cluster_flush<2, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp); break;
-            case 4: cluster_flush<4, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp); break;
-            default: cluster_flush<8, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp); break;
+            case 1: cluster_flush<1, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp, !compact); break;
+            case 2: cluster_flush<2, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp, !compact); break;
+            case 4: cluster_flush<4, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp, !compact); break;
+            default: cluster_flush<8, F64>(cl, hs, hs_t, hc, P, b0, b1, sexp, !compact); break;
         }
         cl.sync();  // keep this CTA's shared memory until every remote read is done
     }
@@ -993,7 +1015,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)
                 run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
-                                                    hs_t, hc, a.hist_shared != 0, sexp);
+                                                    hs_t, hc, a.hist_shared ? kHistShared : kHistGlobal, sexp);
         }
     }
     if (cur >= 0 && a.hist_shared) flush_hist();
