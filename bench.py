@@ -42,11 +42,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["four_peaks_d8", "batch_mix", "serve"],
+    ap.add_argument("--workload", choices=["four_peaks_d8", "ball_d20", "batch_mix", "serve"],
                     default="four_peaks_d8",
-                    help="four_peaks_d8 (default): the single-integral step; batch_mix: 512 "
-                         "integrals per launch against one at a time; serve: continuous batching "
-                         "of a Poisson request stream")
+                    help="four_peaks_d8 (default): the single-integral step; ball_d20: the same "
+                         "step on the 20-D ball (N_ev = 1e7); batch_mix: 512 integrals per launch "
+                         "against one at a time; serve: continuous batching of a Poisson request "
+                         "stream")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     ap.add_argument("--launch", default=None,
                     help="fix the sampling launch shape instead of autotuning it: "
@@ -62,15 +63,23 @@ def flops_per_sample(dim, n_peaks):
     return 4 * dim + n_peaks * (3 * dim + 2) + 10
 
 
-def ops_per_sample(dim, n_peaks):
+def ops_per_sample(dim, n_peaks, ball=False):
     """Algorithmic lane operations per sample of the fused kernel (each one
     issue slot of one lane): Philox4x32-10 6 per round (the high and low words
     of two 32x32 products, two key XORs) x 10 rounds x ceil(D/4) calls; the map
     7 per axis (uniform from the bits, y N_g, floor, fraction, table load, x, J);
     the Gaussian integrand 2D + 3 per peak (difference and multiply-add per
-    axis, scale, exp2, accumulate); the moments 10 (J f, v^2, two compensated
-    adds of 4); the histograms 2 atomic adds per axis."""
-    return 60 * ((dim + 3) // 4) + 7 * dim + n_peaks * (2 * dim + 3) + 10 + 2 * dim
+    axis, scale, exp2, accumulate), the ball 2D + 2 (compare, select); the
+    moments 10 (J f, v^2, two compensated adds of 4); the histograms 2 atomic
+    adds per axis."""
+    f = n_peaks * (2 * dim + (2 if ball else 3))
+    return 60 * ((dim + 3) // 4) + 7 * dim + f + 10 + 2 * dim
+
+
+def ball_flops_per_sample(dim):
+    """Algorithmic FP32 flops of the ball workload: the map 4 per axis, the
+    ball test 2D + 1, the compensated moments 10."""
+    return 4 * dim + 2 * dim + 1 + 10
 
 
 class Clocks:
@@ -173,12 +182,10 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def cpu_baseline(seconds=12.0):
+def cpu_baseline(prob, seconds=12.0):
     """The FP64 CPU oracle, as it stands, on this host: whole iterations of the
-    same workload (N_ev = 1e6) until ~seconds of CPU time; one thread."""
+    same workload until ~seconds of CPU time; one thread."""
     import oracle
-    from paper_2009_05112_gb300 import inputs
-    prob = inputs.four_peaks_d8()
     o = oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
                          alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind,
                          prm=prob.prm)
@@ -193,8 +200,9 @@ def cpu_baseline(seconds=12.0):
         if el >= seconds or its >= 400:
             break
     return {"value": evals / el, "unit": "integrand evals/s", "cores": 1, "kind": "oracle",
-            "sample": "%d whole iterations (N_ev=1e6, D=8, 4 peaks, N_g=1000) of the FP64 C "
-                      "oracle, single thread, %.1f s" % (its, el)}
+            "sample": "%d whole iterations (%s, N_ev=%d, D=%d, N_g=%d) of the FP64 C "
+                      "oracle, single thread, %.1f s" % (its, prob.name, prob.n_ev, prob.dim,
+                                                         prob.n_g, el)}
 
 
 def run_reference(args):
@@ -234,6 +242,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _integral(g, prob, ball):
+    """The combined estimate: all iterations, or for the ball (whose first
+    iterations may see no sample inside it, i.e. exact zeros) the last 10."""
+    if ball:
+        n_it = g.info()[2]  # (N_st, N_h, iterations done)
+        r = g.result(discard=max(0, n_it - 10))
+        return {"mean": r["mean"], "sdev": r["sdev"], "iterations": "last 10"}
+    r = g.result()
+    return {"mean": r["mean"], "sdev": r["sdev"]}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -248,7 +267,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     _build.build()
     vegasp.use_torch_allocator()
-    prob = inputs.four_peaks_d8()
+    ball = args.workload == "ball_d20"
+    prob = inputs.ball_d20() if ball else inputs.four_peaks_d8()
+    n_peaks = 1 if ball else 4
     prob.integral_id = rank
     stream = torch.cuda.current_stream()
     g = vegasp.Integrator.from_problem(prob, precision=vegasp.VP_FP32)
@@ -332,9 +353,11 @@ def run_ours(args):
     fp32_peak = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     samples_per_step = evals / args.steps
     k1_avg_ms = sum(k1_ms) / len(k1_ms)
-    k1_tops = ops_per_sample(prob.dim, 4) * samples_per_step / (k1_avg_ms / 1e3) / 1e12
-    k1_tflops = flops_per_sample(prob.dim, 4) * samples_per_step / (k1_avg_ms / 1e3) / 1e12
-    traffic = traffic_from_profile(kernel_source_hash())
+    ops = ops_per_sample(prob.dim, n_peaks, ball)
+    flops = ball_flops_per_sample(prob.dim) if ball else flops_per_sample(prob.dim, n_peaks)
+    k1_tops = ops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
+    k1_tflops = flops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
+    traffic = None if ball else traffic_from_profile(kernel_source_hash())
     roof = {"bound": "alu", "achieved": k1_tops, "peak": issue_peak, "unit": "Tops/s",
             "frac": k1_tops / issue_peak,
             "traffic": traffic * samples_per_step / PROFILED_SAMPLES if traffic else None,
@@ -342,22 +365,23 @@ def run_ours(args):
             "kernel_ms_note": "CUDA events around the sampling launch, mean of %d eager "
                               "iterations after the timed steps" % KERNEL_TIMING_ITERS,
             "kernel_share_of_step": k1_avg_ms / (total_ms / args.steps),
-            "ops_per_sample": ops_per_sample(prob.dim, 4),
+            "ops_per_sample": ops,
             "peak_note": "issue slots = SMs x 4 schedulers x 32 lanes x %.0f MHz (max SM "
                          "clock); algorithmic lane operations counted from the kernel "
                          "source" % max_mhz,
             "fp32": {"achieved_tflops": k1_tflops, "peak_tflops": fp32_peak,
                      "frac": k1_tflops / fp32_peak,
-                     "flops_per_sample": flops_per_sample(prob.dim, 4)},
-            "ncu": traffic_from_profile(kernel_source_hash(), "fma_alu_issue")}
+                     "flops_per_sample": flops},
+            "ncu": None if ball else traffic_from_profile(kernel_source_hash(), "fma_alu_issue")}
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = k1_tops / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
     line = {"metric": "integrand evals/s", "value": value, "unit": "integrand evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, MIN_WARMUP),
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dim": prob.dim, "n_ev": prob.n_ev,
-                       "n_g": prob.n_g, "alpha": prob.alpha, "beta": prob.beta, "peaks": 4,
+            "config": {"workload": prob.name, "dim": prob.dim, "n_ev": prob.n_ev,
+                       "n_g": prob.n_g, "alpha": prob.alpha, "beta": prob.beta,
+                       "peaks": n_peaks, "integrand": "ball" if ball else "gaussian peaks",
                        "precision": "fp32 map/integrand, Kahan fp32 moments, fp64 estimate",
                        "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": "one integral per GPU" if world > 1 else "single GPU"},
@@ -369,10 +393,9 @@ def run_ours(args):
             # sample, estimate, alloc, offsets, refine (+ the task prefix for the task kernel)
             "gpu_launches": (5 + (g.tuning()["scheme"] == "tasks")) * args.steps,
             "sample_launch": g.tuning(),
-            "integral": {"mean": g.result()["mean"], "sdev": g.result()["sdev"],
-                         "exact": prob.exact}}
+            "integral": dict(_integral(g, prob, ball), exact=prob.exact)}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(prob)
     print(json.dumps(line), flush=True)
     g.close()
     if world > 1:
