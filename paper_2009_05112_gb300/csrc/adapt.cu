@@ -139,8 +139,8 @@ constexpr int kEstCtas = 4;
 __device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode);
 
 struct EstShared {
-    double own[3][256];
-    double recv[3][256];
+    double recv2[3][256];  // level 256: CTA 1's terms, received by CTA 0
+    double recv[3][256];   // level 512: CTA 2's (3's) terms, received by CTA 0 (1)
     double red[3][256];
 };
 
@@ -219,22 +219,23 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
         a.b = __dadd_rn(v.b, sm.recv[1][t]);
         a.c = __dadd_rn(v.c, sm.recv[2][t]);
     }
-    cl.sync();  // CTA 0's recv buffer is free again
-    // s = 256: term t + 256 (CTA 1) joins term t (CTA 0)
+    // s = 256: term t + 256 (CTA 1) joins term t (CTA 0), through a second
+    // buffer (so CTA 0 need not finish reading the first); afterwards only
+    // CTA 0's shared memory is read, so CTAs 1-3 may leave
     if (rank == 1) {
         EstShared *dst = cl.map_shared_rank(&sm, 0);
-        dst->recv[0][t] = a.a;
-        dst->recv[1][t] = a.b;
-        dst->recv[2][t] = a.c;
+        dst->recv2[0][t] = a.a;
+        dst->recv2[1][t] = a.b;
+        dst->recv2[2][t] = a.c;
     }
     cl.sync();
     if (rank != 0) return;
     double *r0 = sm.red[0], *r1 = sm.red[1], *r2 = sm.red[2];
-    r0[t] = __dadd_rn(a.a, sm.recv[0][t]);
-    r1[t] = __dadd_rn(a.b, sm.recv[1][t]);
-    r2[t] = __dadd_rn(a.c, sm.recv[2][t]);
+    r0[t] = __dadd_rn(a.a, sm.recv2[0][t]);
+    r1[t] = __dadd_rn(a.b, sm.recv2[1][t]);
+    r2[t] = __dadd_rn(a.c, sm.recv2[2][t]);
     __syncthreads();
-    for (int s = 128; s >= 32; s >>= 1) {
+    for (int s = 128; s >= 64; s >>= 1) {
         if (t < s) {
             r0[t] = __dadd_rn(r0[t], r0[t + s]);
             r1[t] = __dadd_rn(r1[t], r1[t + s]);
@@ -242,21 +243,24 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
         }
         __syncthreads();
     }
-    if (t < 32) {
-        double x0 = r0[t], x1 = r1[t], x2 = r2[t];
-        for (int s = 16; s >= 1; s >>= 1) {
-            x0 = __dadd_rn(x0, __shfl_down_sync(0xffffffffu, x0, s));
-            x1 = __dadd_rn(x1, __shfl_down_sync(0xffffffffu, x1, s));
-            x2 = __dadd_rn(x2, __shfl_down_sync(0xffffffffu, x2, s));
+    // levels 32 .. 1: one warp per sum, the three in parallel (a chain of
+    // dependent FP64 additions is slow on this part)
+    {
+        const int w = t >> 5, l = t & 31;
+        if (w < 3) {
+            const double *r = w == 0 ? r0 : (w == 1 ? r1 : r2);
+            double x = __dadd_rn(r[l], r[l + 32]);
+            for (int s = 16; s >= 1; s >>= 1) x = __dadd_rn(x, __shfl_down_sync(0xffffffffu, x, s));
+            if (l == 0) {
+                d.part[3 * k + w] = x;
+                __threadfence();
+            }
         }
-        if (t == 0) {
-            d.part[3 * k + 0] = x0;
-            d.part[3 * k + 1] = x1;
-            d.part[3 * k + 2] = x2;
-            __threadfence();
-            const uint32_t ticket = atomicAdd(&d.st->done_est, 1u);
-            s_last = (ticket == d.n_tree - 1);
-        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        const uint32_t ticket = atomicAdd(&d.st->done_est, 1u);
+        s_last = (ticket == d.n_tree - 1);
     }
     __syncthreads();
     if (!s_last) return;

@@ -213,12 +213,21 @@ __device__ void block_tree_sum(const double *part, uint32_t n, double *sh, doubl
 #pragma unroll
     for (int c = 0; c < NS; ++c) sh[c * nt + t] = run[c];
     __syncthreads();
-    for (uint32_t w = 1; w < T; w <<= 1) {
-        if (t < T && (t & (2 * w - 1)) == 0) {
-#pragma unroll
-            for (int c = 0; c < NS; ++c) sh[c * nt + t] = __dadd_rn(sh[c * nt + t], sh[c * nt + t + w]);
+    if (NS > 1 && NS * T <= nt) {  // one thread group per series, the series in parallel
+        const uint32_t c = t / T, u = t - c * T;
+        for (uint32_t w = 1; w < T; w <<= 1) {
+            if (c < (uint32_t)NS && (u & (2 * w - 1)) == 0)
+                sh[c * nt + u] = __dadd_rn(sh[c * nt + u], sh[c * nt + u + w]);
+            __syncthreads();
         }
-        __syncthreads();
+    } else {
+        for (uint32_t w = 1; w < T; w <<= 1) {
+            if (t < T && (t & (2 * w - 1)) == 0) {
+#pragma unroll
+                for (int c = 0; c < NS; ++c) sh[c * nt + t] = __dadd_rn(sh[c * nt + t], sh[c * nt + t + w]);
+            }
+            __syncthreads();
+        }
     }
 #pragma unroll
     for (int c = 0; c < NS; ++c) out[c] = sh[c * nt];
