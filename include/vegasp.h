@@ -153,6 +153,20 @@ vp_status vp_step(vp_ctx *ctx, void *stream);
  * combines iterations j >= discard (§2.5).  VP_ENONFINITE if any iteration saw
  * a non-finite integrand value (out still filled). */
 vp_status vp_result(vp_ctx *ctx, int discard, vp_result_t *out);
+/* §2.5, last paragraph: the unweighted combination for iterations run with a
+ * frozen map (alpha = 0, see vp_set_damping) after the first `discard`:
+ * mean = average of the I_j, sdev = average of the sigma_j / sqrt(N_it) (an
+ * unbiased estimate, free of the weighted average's 1/N_ev bias); chi2 about
+ * that mean (0 if some sigma_j is 0), dof = N_it - 1.  Same errors as
+ * vp_result. */
+vp_status vp_result_unweighted(vp_ctx *ctx, int discard, vp_result_t *out);
+/* Changes the damping exponents for the following iterations: alpha (§2.3;
+ * 0 freezes the grid, "preventing the algorithm from adapting", §2.5) and
+ * beta (§3 Eq. dh; 0 gives the equal split), both finite and >= 0, else
+ * VP_EINVAL with the context unchanged.  Synchronises the context's last
+ * stream; the step graph is captured again when the refinement's presence
+ * changes. */
+vp_status vp_set_damping(vp_ctx *ctx, double alpha, double beta);
 
 vp_status vp_map_destroy(vp_ctx *ctx);
 

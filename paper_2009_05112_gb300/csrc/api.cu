@@ -1049,7 +1049,36 @@ void vp::combine(const double *I, const double *V, int n, int discard, vp_result
     r->chi2 = c;
 }
 
-static vp_status member_result(Set &s, int i, int discard, vp_result_t *out) {
+// §2.5, last paragraph: with the map frozen (alpha = 0) after the first
+// iterations, the unweighted mean of the I_j is unbiased, and the mean of the
+// sigma_j over sqrt(N_it) estimates its error; chi^2 about that mean.
+void vp::combine_unweighted(const double *I, const double *V, int n, int discard,
+                            vp_result_t *r) {
+    int first = discard < 0 ? 0 : discard;
+    r->n_it = n > first ? n - first : 0;
+    r->dof = r->n_it > 0 ? r->n_it - 1 : 0;
+    r->mean = NAN;
+    r->sdev = NAN;
+    r->chi2 = NAN;
+    if (r->n_it == 0) return;
+    double si = 0.0, ss = 0.0;
+    for (int j = first; j < n; ++j) {
+        si += I[j];
+        ss += std::sqrt(V[j] > 0.0 ? V[j] : 0.0);
+    }
+    r->mean = si / r->n_it;
+    r->sdev = ss / r->n_it / std::sqrt((double)r->n_it);
+    double c = 0.0;
+    bool any_zero = false;
+    for (int j = first; j < n; ++j) {
+        if (V[j] > 0.0) c += (I[j] - r->mean) * (I[j] - r->mean) / V[j];
+        else any_zero = true;
+    }
+    r->chi2 = any_zero ? 0.0 : c;
+}
+
+static vp_status member_result(Set &s, int i, int discard, vp_result_t *out,
+                               bool unweighted = false) {
     CU(cudaStreamSynchronize(s.last));
     const Desc &d = s.h_desc[i];
     State st;
@@ -1061,7 +1090,8 @@ static vp_status member_result(Set &s, int i, int discard, vp_result_t *out) {
         CU(cudaMemcpy(V.data(), d.hist_var, n * 8, cudaMemcpyDeviceToHost));
     }
     memset(out, 0, sizeof *out);
-    combine(I.data(), V.data(), n, discard, out);
+    if (unweighted) combine_unweighted(I.data(), V.data(), n, discard, out);
+    else combine(I.data(), V.data(), n, discard, out);
     out->n_eval = (int64_t)st.n_eval_total;
     out->last_i = st.last_i;
     out->last_sdev = std::sqrt(st.last_var);
@@ -1112,6 +1142,44 @@ extern "C" vp_status vp_result(vp_ctx *c, int discard, vp_result_t *out) {
     CHECK_CTX(c);
     if (!out) return fail(VP_EINVAL, "NULL out");
     return member_result(c->set, 0, discard, out);
+}
+
+extern "C" vp_status vp_result_unweighted(vp_ctx *c, int discard, vp_result_t *out) {
+    CHECK_CTX(c);
+    if (!out) return fail(VP_EINVAL, "NULL out");
+    return member_result(c->set, 0, discard, out, true);
+}
+
+// New damping exponents for member i of a set, host and device descriptors.
+static vp_status set_damping(Set &s, int i, double alpha, double beta) {
+    if (!(alpha >= 0.0 && std::isfinite(alpha))) return fail(VP_EINVAL, "alpha must be finite and >= 0");
+    if (!(beta >= 0.0 && std::isfinite(beta))) return fail(VP_EINVAL, "beta must be finite and >= 0");
+    CU(cudaStreamSynchronize(s.last));
+    Member &mb = s.m[i];
+    mb.p.alpha = alpha;
+    mb.p.beta = beta;
+    Desc &d = s.h_desc[i];
+    d.alpha = alpha;
+    d.beta = beta;
+    d.omega_beta = std::pow(d.omega, beta);
+    d.half_beta_hi = (float)(0.5 * beta);
+    d.half_beta_lo = (float)(0.5 * beta - (double)d.half_beta_hi);
+    CU(cudaMemcpy(s.d_desc + i, &d, sizeof d, cudaMemcpyHostToDevice));
+    bool any = false;
+    for (const Member &m : s.m) any |= m.p.alpha > 0.0 && m.p.n_g > 1;
+    if (any != s.any_refine && s.gexec) {  // the step graph's shape changes: capture again
+        cudaGraphExecDestroy(s.gexec);
+        cudaGraphDestroy(s.graph);
+        s.gexec = nullptr;
+        s.graph = nullptr;
+    }
+    s.any_refine = any;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_set_damping(vp_ctx *c, double alpha, double beta) {
+    CHECK_CTX(c);
+    return set_damping(c->set, 0, alpha, beta);
 }
 
 extern "C" vp_status vp_map_destroy(vp_ctx *c) {

@@ -122,5 +122,7 @@ void set_task(Group &g, double expect);
 vp_status launch_group(const Desc *d_desc, Group &g, cudaStream_t stream);
 // §2.5 combination of iterations j >= discard.
 void combine(const double *I, const double *V, int n, int discard, vp_result_t *r);
+// §2.5 unweighted combination (frozen map) of iterations j >= discard.
+void combine_unweighted(const double *I, const double *V, int n, int discard, vp_result_t *r);
 
 }  // namespace vp

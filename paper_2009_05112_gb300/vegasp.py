@@ -104,6 +104,8 @@ _SIGS = {
     "vp_eval_samples": [_P, ctypes.c_int64, _P, _P, ctypes.c_uint32, _P, _P, _P, _P],
     "vp_last_sample_ms": [_P, ctypes.POINTER(ctypes.c_float)],
     "vp_alloc_static": [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P, _P, _P],
+    "vp_result_unweighted": [_P, ctypes.c_int, ctypes.POINTER(vp_result_t)],
+    "vp_set_damping": [_P, ctypes.c_double, ctypes.c_double],
     "vp_get_tuning": [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                       ctypes.POINTER(ctypes.c_int)],
@@ -263,9 +265,14 @@ class Integrator:
                 self.adapt()
         return self
 
-    def result(self, discard=0, allow_nonfinite=False):
+    def set_damping(self, alpha, beta):
+        """alpha, beta for the following iterations (alpha = 0 freezes the map)."""
+        check(lib().vp_set_damping(self.ctx, float(alpha), float(beta)))
+
+    def result(self, discard=0, allow_nonfinite=False, unweighted=False):
         r = vp_result_t()
-        st = lib().vp_result(self.ctx, int(discard), ctypes.byref(r))
+        fn = lib().vp_result_unweighted if unweighted else lib().vp_result
+        st = fn(self.ctx, int(discard), ctypes.byref(r))
         if not (allow_nonfinite and st == VP_ENONFINITE):
             check(st)
         return dict(mean=r.mean, sdev=r.sdev, chi2=r.chi2, dof=r.dof, n_it=r.n_it,

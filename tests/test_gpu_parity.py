@@ -385,6 +385,44 @@ def test_ball_d20_result_matches_volume():
 
 
 # ---------------------------------------------------------------------------
+# §2.5: a frozen map and the unweighted combination
+# ---------------------------------------------------------------------------
+def test_frozen_map_and_unweighted_result_match_oracle():
+    """Five adapting iterations, then vp_set_damping(0, 0) (no refinement, the
+    equal split) for six more, alternating vp_iterate/vp_adapt and the step
+    graph: every I_j and sigma_j^2 within 1e-10 of the oracle's, the grid left
+    exactly as it was, the equal split of n_h, and the unweighted combination
+    of the frozen iterations (§2.5, last paragraph) equal to the oracle's."""
+    prob = inputs.three_peaks_d4(n_ev=5000, n_g=200)
+    g = gpu_of(prob)
+    o = oracle_of(prob)
+    for _ in range(5):
+        g.iterate(); g.adapt(); o.iterate(); o.adapt()
+    g.set_damping(0.0, 0.0)
+    o.alpha, o.beta = 0.0, 0.0
+    e0 = g.edges()
+    for k in range(6):
+        if k % 2:
+            g.step()
+        else:
+            g.iterate(); g.adapt()
+        o.iterate(); o.adapt()
+    I, Vv = g.history()
+    np.testing.assert_allclose(I, o.I, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(Vv, o.var, rtol=1e-9, atol=0)
+    assert np.array_equal(g.edges(), e0)
+    n_h, _ = g.alloc()
+    assert np.array_equal(n_h, o.n_h) and np.unique(n_h).size == 1
+    ru = g.result(discard=5, unweighted=True)
+    ou = oracle.combine_unweighted(o.I, o.var, discard=5)
+    assert ru["n_it"] == ou["n_it"] == 6
+    assert ru["mean"] == pytest.approx(ou["mean"], rel=1e-10)
+    assert ru["sdev"] == pytest.approx(ou["sdev"], rel=1e-9)
+    with pytest.raises(V().VegasError):
+        g.set_damping(-1.0, 0.0)
+
+
+# ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
 def test_single_hypercube_and_single_increment():

@@ -517,3 +517,32 @@ def test_grid_converges_to_equal_d():
         cv.append(float(np.mean(np.std(d, axis=1) / np.mean(d, axis=1))))
         prob.adapt()
     assert cv[-1] < 0.1 * cv[0]
+
+
+def test_frozen_map_unweighted_average():
+    """§2.5, last paragraph: after the grid has adapted, freezing it (alpha =
+    0; here beta = 0 too) makes the iterations independent draws of one
+    estimator, so the unweighted mean of the I_j is unbiased and the mean
+    sigma_j / sqrt(N_it) is its error.  Checked on Eq. easy (closed form) at
+    N_ev = 2000 over 300 frozen iterations: the unweighted mean within 4 of its
+    own sigma of the exact value, the scatter of the I_j equal to the mean
+    sigma_j within 15%, and the weighted mean of the same iterations below the
+    unweighted one on every seed (the weighted average's negative bias from the
+    correlation of I_j with sigma_j that §2.5 describes)."""
+    prob = inputs.two_gaussians_d4(n_ev=2000)
+    for seed in range(3):
+        o = oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
+                             alpha=prob.alpha, beta=prob.beta, seed=seed, kind=prob.kind,
+                             prm=prob.prm)
+        o.run(10)
+        o.alpha, o.beta = 0.0, 0.0
+        edges = o.edges.copy()
+        o.run(300)
+        assert np.array_equal(o.edges, edges)  # alpha = 0: no refinement
+        u = oracle.combine_unweighted(o.I, o.var, discard=10)
+        w = oracle.combine(o.I, o.var, discard=10)
+        assert u["n_it"] == 300
+        assert abs(u["mean"] - prob.exact) < 4 * u["sdev"]
+        s = np.sqrt(np.asarray(o.var[10:]))
+        assert 0.85 < np.std(o.I[10:]) / np.mean(s) < 1.15
+        assert w["mean"] < u["mean"]
