@@ -253,6 +253,25 @@ def _integral(g, prob, ball):
     return {"mean": r["mean"], "sdev": r["sdev"]}
 
 
+def rank_problem(prob, rank):
+    """The integral a rank runs: the same problem with Philox counter word 3 =
+    rank, so that the ranks draw independent samples (no data exchange)."""
+    prob.integral_id = rank
+    return prob
+
+
+def reduce_over_ranks(total_ms, evals, dist, device):
+    """Whole-job figures over the ranks: the slowest rank's time (MAX) and all
+    ranks' integrand evaluations (SUM).  `device` holds the reduction tensors
+    ("cuda" under NCCL, "cpu" under gloo)."""
+    import torch
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(evals)], device=device, dtype=torch.float64)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -270,7 +289,7 @@ def run_ours(args):
     ball = args.workload == "ball_d20"
     prob = inputs.ball_d20() if ball else inputs.four_peaks_d8()
     n_peaks = 1 if ball else 4
-    prob.integral_id = rank
+    prob = rank_problem(prob, rank)
     stream = torch.cuda.current_stream()
     g = vegasp.Integrator.from_problem(prob, precision=vegasp.VP_FP32)
     launch = None
@@ -300,12 +319,7 @@ def run_ours(args):
     t_max = total_ms
     evals_all = evals
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        e = torch.tensor([evals], device="cuda", dtype=torch.float64)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        evals_all = float(e.item())
+        t_max, evals_all = reduce_over_ranks(total_ms, evals, dist, "cuda")
         dist.barrier()
     value = evals_all / (t_max / 1e3)
 
