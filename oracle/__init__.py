@@ -31,6 +31,7 @@ _u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
 _u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
 
 KIND_GAUSS, KIND_BALL, KIND_EXPNORM, KIND_POSTERIOR = 0, 1, 2, 3
 
@@ -45,23 +46,25 @@ def lib():
         L.or_philox4x32_10.restype = None
         L.or_nstrat.argtypes = [ctypes.c_int, ctypes.c_int64]
         L.or_nstrat.restype = ctypes.c_int64
+        L.or_nstrat_mixed.argtypes = [ctypes.c_int, ctypes.c_int64, _i64p]
+        L.or_nstrat_mixed.restype = None
         L.or_integrand.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p]
         L.or_integrand.restype = ctypes.c_double
         L.or_integrand_many.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, ctypes.c_int64, _f64p,
                                         _f64p]
         L.or_integrand_many.restype = None
-        L.or_eval_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+        L.or_eval_sample.argtypes = [ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_uint64,
                                      ctypes.c_uint32, _f64p, ctypes.c_int, _f64p, ctypes.c_uint32,
                                      ctypes.c_uint64, ctypes.c_uint32, _f64p, _i32p,
                                      ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]
         L.or_eval_sample.restype = None
-        L.or_sample_iteration.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+        L.or_sample_iteration.argtypes = [ctypes.c_int, ctypes.c_int, _i64p,
                                           ctypes.c_uint64, ctypes.c_uint32, _f64p, ctypes.c_int,
                                           _f64p, ctypes.c_uint32, _u32p, _f64p, _f64p, _f64p,
                                           _f64p]
         L.or_sample_iteration.restype = ctypes.c_int
-        L.or_hcube_moments.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+        L.or_hcube_moments.argtypes = [ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_uint64,
                                        ctypes.c_uint32, _f64p, ctypes.c_int, _f64p,
                                        ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_double),
@@ -107,6 +110,15 @@ def philox4x32_10(ctr, key):
 def nstrat(dim, n_ev):
     """§3 Eq. (Nst_vegasp) as an exact integer.  Pinned by brute force."""
     return int(lib().or_nstrat(int(dim), int(n_ev)))
+
+
+def nstrat_mixed(dim, n_ev):
+    """§3.2's variation: N_st + 1 strata on the first d axes, N_st on the rest,
+    with the largest d that keeps at least 4 samples per hypercube.  Pinned by
+    the counts the paper quotes for N_ev = 2.5e5 and 5e4 and by brute force."""
+    out = np.zeros(int(dim), np.int64)
+    lib().or_nstrat_mixed(int(dim), int(n_ev), out)
+    return out
 
 
 def integrand(kind, dim, prm, x):
@@ -253,11 +265,13 @@ class VegasPlus:
     increments per axis, n_ev samples per iteration, alpha (§2.3), beta (§3 Eq.
     dh), seed and integral_id (the Philox key and counter word 3), plus2 (the
     alternative of §3 Eq. nh), kind and prm (integrand family and blob), n_st
-    (0: §3 Eq. Nst_vegasp; otherwise the stratification count to use).
+    (0: §3 Eq. Nst_vegasp; otherwise the stratification count to use on every
+    axis), n_st_axis (explicit strata per axis, §3.2) and mixed (§3.2's
+    N_st / N_st + 1 rule in place of Eq. Nst_vegasp).
     """
 
     def __init__(self, dim, lo, hi, n_g, n_ev, alpha, beta, seed, kind, prm,
-                 integral_id=0, plus2=False, n_st=0):
+                 integral_id=0, plus2=False, n_st=0, n_st_axis=None, mixed=False):
         self.dim, self.n_g, self.n_ev = int(dim), int(n_g), int(n_ev)
         self.alpha, self.beta = float(alpha), float(beta)
         self.seed, self.integral_id, self.plus2 = int(seed), int(integral_id), bool(plus2)
@@ -272,8 +286,16 @@ class VegasPlus:
         self.edges[:, -1] = hi
         # §3 Eq. (Nst_vegasp), unless a stratification count is forced (N_st = 1
         # is the simple y-space Monte Carlo of §2.4).
-        self.n_st = int(n_st) if n_st else nstrat(self.dim, self.n_ev)
-        self.n_hc = self.n_st ** self.dim
+        if n_st_axis is not None:
+            self.nst_ax = np.ascontiguousarray(n_st_axis, np.int64).reshape(self.dim)
+        elif n_st:
+            self.nst_ax = np.full(self.dim, int(n_st), np.int64)
+        elif mixed:
+            self.nst_ax = nstrat_mixed(self.dim, self.n_ev)
+        else:
+            self.nst_ax = np.full(self.dim, nstrat(self.dim, self.n_ev), np.int64)
+        self.n_st = int(self.nst_ax.min())
+        self.n_hc = int(np.prod([int(s) for s in self.nst_ax]))
         self.omega = 1.0 / float(self.n_hc)
         # reading: the first allocation is the equal split max(2, floor(N_ev/N_h)).
         self.n_h, self.offsets = allocate(self.n_ev, np.ones(self.n_hc))
@@ -287,7 +309,7 @@ class VegasPlus:
         self.s2 = np.zeros(self.n_hc)
         self.hsum = np.zeros((self.dim, self.n_g))
         self.hcnt = np.zeros((self.dim, self.n_g))
-        rc = lib().or_sample_iteration(self.dim, self.n_g, self.n_st, self.seed,
+        rc = lib().or_sample_iteration(self.dim, self.n_g, self.nst_ax, self.seed,
                                        self.integral_id, self.edges, self.kind, self.prm,
                                        self.t, self.n_h, self.s1, self.s2, self.hsum,
                                        self.hcnt)
@@ -319,7 +341,7 @@ class VegasPlus:
         idx = np.zeros(self.dim, np.int32)
         jac = ctypes.c_double()
         f = ctypes.c_double()
-        lib().or_eval_sample(self.dim, self.n_g, self.n_st, self.seed, self.integral_id,
+        lib().or_eval_sample(self.dim, self.n_g, self.nst_ax, self.seed, self.integral_id,
                              self.edges, self.kind, self.prm, int(t), int(h), int(j), x, idx,
                              ctypes.byref(jac), ctypes.byref(f))
         return x, idx, jac.value, f.value
@@ -328,7 +350,7 @@ class VegasPlus:
         """S1_h, S2_h of hypercube h with n samples at iteration t (same sample
         sequence as sample())."""
         a, b = ctypes.c_double(), ctypes.c_double()
-        lib().or_hcube_moments(self.dim, self.n_g, self.n_st, self.seed, self.integral_id,
+        lib().or_hcube_moments(self.dim, self.n_g, self.nst_ax, self.seed, self.integral_id,
                                self.edges, self.kind, self.prm, int(t), int(h), int(n),
                                ctypes.byref(a), ctypes.byref(b))
         return a.value, b.value

@@ -79,6 +79,30 @@ int64_t or_nstrat(int dim, int64_t n_ev) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* §3.2 (Limitations and a Variation): the mixed stratification -- N_st + 1   */
+/* strata in the first d directions and N_st in the others, N_st from         */
+/* Eq. (Nst_vegasp) and d the largest value that still allows 4 samples per   */
+/* hypercube, i.e. 4 (N_st + 1)^d N_st^(D - d) <= N_ev (exact integers).       */
+/* ------------------------------------------------------------------------ */
+void or_nstrat_mixed(int dim, int64_t n_ev, int64_t *nst_ax) {
+    const int64_t n = or_nstrat(dim, n_ev);
+    const int64_t limit = n_ev / 4;
+    int d = 0;
+    for (int k = 1; k <= dim; ++k) { /* largest k with (n+1)^k n^(dim-k) <= N_ev/4 */
+        int64_t p = 1;
+        int ok = 1;
+        for (int mu = 0; mu < dim && ok; ++mu) {
+            const int64_t s = mu < k ? n + 1 : n;
+            if (p > limit / s) ok = 0;
+            else p *= s;
+        }
+        if (ok && p <= limit) d = k;
+        else break;
+    }
+    for (int mu = 0; mu < dim; ++mu) nst_ax[mu] = mu < d ? n + 1 : n;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Integrands (the paper's example families, written out in FP64).           */
 /* Parameter blob layouts (doubles):                                          */
 /*  kind 0 gaussian peaks  §2.4 Eq. (easy):  [K, {a, w, c[D]} x K]            */
@@ -158,7 +182,7 @@ void or_integrand_many(int kind, int dim, const double *prm, int64_t n, const do
 typedef struct {
     int dim;
     int n_g;
-    int64_t n_st;
+    const int64_t *nst_ax; /* strata per axis (§3; §3.2 allows them to differ) */
     uint64_t seed;
     uint32_t integral_id;
     const double *edges;
@@ -181,10 +205,11 @@ static double or_sample(const or_problem *P, uint32_t t, uint64_t h, uint32_t j,
         for (int lane = 0; lane < 4; ++lane) {
             int mu = (int)(4 * q) + lane;
             if (mu >= dim) break;
-            int64_t k_mu = (int64_t)(rest % (uint64_t)P->n_st);
-            rest /= (uint64_t)P->n_st;
+            const uint64_t s_mu = (uint64_t)P->nst_ax[mu];
+            int64_t k_mu = (int64_t)(rest % s_mu);
+            rest /= s_mu;
             double u = ((double)r[lane] + 0.5) * (1.0 / 4294967296.0);
-            double y = ((double)k_mu + u) / (double)P->n_st; /* point in stratum k_mu of axis mu */
+            double y = ((double)k_mu + u) / (double)s_mu; /* point in stratum k_mu of axis mu */
             double yng = y * (double)n_g;
             int i = (int)floor(yng); /* i(y) = floor(y N_g) */
             if (i > n_g - 1) i = n_g - 1;
@@ -201,10 +226,10 @@ static double or_sample(const or_problem *P, uint32_t t, uint64_t h, uint32_t j,
 }
 
 /* Per-sample inspection: x[dim], idx[dim], jac, f for sample j of hypercube h. */
-void or_eval_sample(int dim, int n_g, int64_t n_st, uint64_t seed, uint32_t integral_id,
+void or_eval_sample(int dim, int n_g, const int64_t *nst_ax, uint64_t seed, uint32_t integral_id,
                     const double *edges, int kind, const double *prm, uint32_t t,
                     uint64_t h, uint32_t j, double *x, int *idx, double *jac, double *f) {
-    or_problem P = {dim, n_g, n_st, seed, integral_id, edges, kind, prm};
+    or_problem P = {dim, n_g, nst_ax, seed, integral_id, edges, kind, prm};
     *jac = or_sample(&P, t, h, j, x, idx, f);
 }
 
@@ -215,13 +240,13 @@ void or_eval_sample(int dim, int n_g, int64_t n_st, uint64_t seed, uint32_t inte
 /*   hsum[mu][i] += (J f)^2,  hcnt[mu][i] += 1                  (§2.4, d_i^mu) */
 /* All outputs are overwritten.                                               */
 /* ------------------------------------------------------------------------ */
-int or_sample_iteration(int dim, int n_g, int64_t n_st, uint64_t seed, uint32_t integral_id,
-                        const double *edges, int kind, const double *prm, uint32_t t,
-                        const uint32_t *n_h, double *s1, double *s2, double *hsum,
+int or_sample_iteration(int dim, int n_g, const int64_t *nst_ax, uint64_t seed,
+                        uint32_t integral_id, const double *edges, int kind, const double *prm,
+                        uint32_t t, const uint32_t *n_h, double *s1, double *s2, double *hsum,
                         double *hcnt) {
-    or_problem P = {dim, n_g, n_st, seed, integral_id, edges, kind, prm};
+    or_problem P = {dim, n_g, nst_ax, seed, integral_id, edges, kind, prm};
     int64_t n_hc = 1;
-    for (int mu = 0; mu < dim; ++mu) n_hc *= n_st;
+    for (int mu = 0; mu < dim; ++mu) n_hc *= nst_ax[mu];
     memset(hsum, 0, sizeof(double) * (size_t)dim * (size_t)n_g);
     memset(hcnt, 0, sizeof(double) * (size_t)dim * (size_t)n_g);
     double x[64];
@@ -248,10 +273,10 @@ int or_sample_iteration(int dim, int n_g, int64_t n_st, uint64_t seed, uint32_t 
 
 /* S1_h, S2_h of one hypercube h with n samples (for spot checks at sizes  */
 /* where a whole iteration is too slow on the CPU).                          */
-void or_hcube_moments(int dim, int n_g, int64_t n_st, uint64_t seed, uint32_t integral_id,
-                      const double *edges, int kind, const double *prm, uint32_t t,
-                      uint64_t h, uint32_t n, double *s1, double *s2) {
-    or_problem P = {dim, n_g, n_st, seed, integral_id, edges, kind, prm};
+void or_hcube_moments(int dim, int n_g, const int64_t *nst_ax, uint64_t seed,
+                      uint32_t integral_id, const double *edges, int kind, const double *prm,
+                      uint32_t t, uint64_t h, uint32_t n, double *s1, double *s2) {
+    or_problem P = {dim, n_g, nst_ax, seed, integral_id, edges, kind, prm};
     double x[64];
     int idx[64];
     double a1 = 0.0, a2 = 0.0;
