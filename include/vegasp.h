@@ -101,6 +101,17 @@ typedef struct {
     int n_st;           /* 0: N_st = floor((N_ev/4)^(1/D)) (§3 Eq. Nst_vegasp),
                            computed exactly; > 0: use this many strata per axis */
     int max_it;         /* capacity of the iteration history (0 = 1024) */
+    /* Strata per axis (§3.2, "Limitations and a Variation").  Hypercube h is
+       the mixed-radix number whose digit on axis mu (axis 0 least significant)
+       is its stratum there.  Contexts of one integral only: vp_batch_create
+       with more than one integral and served requests accept uniform strata
+       only (VP_EINVAL otherwise). */
+    const int32_t *n_st_axis; /* NULL, or [D] strata per axis, each >= 1 (copied);
+                                 overrides n_st and mixed */
+    int mixed;          /* with n_st == 0 and n_st_axis == NULL: 1 = §3.2's mixed
+                           rule, N_st + 1 strata on the first d axes and N_st on
+                           the rest, N_st from Eq. Nst_vegasp and d the largest
+                           with 4 (N_st + 1)^d N_st^(D - d) <= N_ev; 0 = uniform */
 } vp_params;
 
 typedef struct {
@@ -174,7 +185,10 @@ vp_status vp_map_destroy(vp_ctx *ctx);
 const char *vp_last_error(void);
 
 /* ---- inspection and test hooks (host buffers; each synchronises) ------- */
+/* n_st: the smallest strata count over the axes (N_st when uniform) */
 vp_status vp_get_info(vp_ctx *ctx, int64_t *n_st, int64_t *n_hc, int *n_it);
+/* strata[D]: the strata on every axis (§3.2) */
+vp_status vp_get_strata(vp_ctx *ctx, int32_t *strata);
 /* edges[D][N_g + 1] (FP64 master grid) */
 vp_status vp_get_edges(vp_ctx *ctx, double *edges);
 /* replaces the grid (edges[D][N_g+1], strictly increasing, ends = box) */

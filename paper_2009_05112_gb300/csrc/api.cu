@@ -163,6 +163,26 @@ static int64_t nstrat_exact(int dim, int64_t n_ev) {
     return n;
 }
 
+// §3.2's mixed stratification: N_st + 1 strata on the first d axes, N_st on
+// the others, N_st from Eq. (Nst_vegasp) and d the largest value with
+// 4 (N_st + 1)^d N_st^(D - d) <= N_ev (integer arithmetic throughout).
+static void nstrat_mixed_exact(int dim, int64_t n_ev, std::vector<int64_t> &out) {
+    const int64_t n = nstrat_exact(dim, n_ev), cap = n_ev / 4;
+    auto prod_fits = [&](int d) {  // (n + 1)^d n^(dim - d) <= cap
+        int64_t p = 1;
+        for (int mu = 0; mu < dim; ++mu) {
+            const int64_t s = mu < d ? n + 1 : n;
+            if (p > cap / s) return false;
+            p *= s;
+        }
+        return true;
+    };
+    int d = 0;
+    while (d < dim && prod_fits(d + 1)) ++d;
+    out.assign(dim, n);
+    for (int mu = 0; mu < d; ++mu) out[mu] = n + 1;
+}
+
 vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
     if (!p || !f) return fail(VP_EINVAL, "NULL params or integrand");
     if (p->dim < 1 || p->dim > kMaxDim) return fail(VP_EINVAL, "dim %d outside 1..%d", p->dim, kMaxDim);
@@ -176,6 +196,10 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
     if (!(p->beta >= 0.0 && std::isfinite(p->beta))) return fail(VP_EINVAL, "beta must be finite and >= 0");
     if (p->precision != VP_FP64 && p->precision != VP_FP32) return fail(VP_EINVAL, "bad precision");
     if (p->n_st < 0) return fail(VP_EINVAL, "n_st must be >= 0");
+    if (p->mixed != 0 && p->mixed != 1) return fail(VP_EINVAL, "mixed must be 0 or 1");
+    if (p->n_st_axis)
+        for (int i = 0; i < p->dim; ++i)
+            if (p->n_st_axis[i] < 1) return fail(VP_EINVAL, "n_st_axis[%d] must be >= 1", i);
     if (p->max_it < 0 || p->max_it > (1 << 24)) return fail(VP_EINVAL, "max_it outside 0..2^24");
     if (f->n_param < 1 || !f->param) return fail(VP_EINVAL, "empty integrand blob");
     const int D = p->dim;
@@ -216,12 +240,22 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
     mb.prm.assign(q, q + n);
     mb.p.lo = mb.lo.data();  // the caller's arrays may not outlive the call
     mb.p.hi = mb.hi.data();
-    mb.n_st = p->n_st > 0 ? p->n_st : nstrat_exact(D, p->n_ev);
-    // N_h = N_st^D <= 2^31
+    mb.p.n_st_axis = nullptr;  // (kept in nst_ax)
+    if (p->n_st_axis)
+        mb.nst_ax.assign(p->n_st_axis, p->n_st_axis + D);
+    else if (p->n_st > 0)
+        mb.nst_ax.assign(D, p->n_st);
+    else if (p->mixed)
+        nstrat_mixed_exact(D, p->n_ev, mb.nst_ax);
+    else
+        mb.nst_ax.assign(D, nstrat_exact(D, p->n_ev));
+    mb.n_st = *std::min_element(mb.nst_ax.begin(), mb.nst_ax.end());
+    mb.uniform = *std::max_element(mb.nst_ax.begin(), mb.nst_ax.end()) == mb.n_st;
+    // N_h = prod_mu s_mu <= 2^31
     uint64_t nh = 1;
     for (int i = 0; i < D; ++i) {
-        nh *= (uint64_t)mb.n_st;
-        if (nh > (1ull << 31)) return fail(VP_EINVAL, "N_st^D exceeds 2^31 hypercubes");
+        nh *= (uint64_t)mb.nst_ax[i];
+        if (nh > (1ull << 31)) return fail(VP_EINVAL, "the strata make more than 2^31 hypercubes");
     }
     mb.n_hc = nh;
     const uint64_t calls = (uint64_t)((D + 3) / 4);
@@ -333,6 +367,15 @@ static vp_status plan_groups(Set &s) {
             if (g.prec == VP_FP32 && g.kind != VP_POSTERIOR && (int)m0.prm[0] > kParamPeaks)
                 g.one = false;
         }
+        // strata that differ between axes (§3.2): the one-integral kernel only
+        // (the task kernel keeps one strata count in registers)
+        g.uniform = true;
+        for (uint32_t i : g.members) g.uniform = g.uniform && s.m[i].uniform;
+        if (!g.uniform && !g.one)
+            return fail(VP_EINVAL, g.members.size() > 1
+                                       ? "strata that differ between axes: one integral per context"
+                                       : "strata that differ between axes: FP32 peaks at most %d",
+                        kParamPeaks);
         if (!g.one) continue;
         // a single integral: the cluster kernel with its constants in parameters
         // (the autotuner may still choose the task kernel).  Its histograms:
@@ -461,6 +504,15 @@ void vp::fill_desc(const Member &mb, const double *d_inv, Desc &d) {
         d.ngD_e = e - 1;
     }
     div_magic((uint32_t)mb.n_st, &d.nst_magic, &d.nst_shift);
+    d.uniform = mb.uniform ? 1u : 0u;
+    d.n_st = (uint32_t)mb.nst_ax[0];
+    for (int mu = 0; mu < kMaxDim; ++mu) {
+        const uint32_t s = mu < D ? (uint32_t)mb.nst_ax[mu] : 1u;
+        d.strata.n[mu] = s;
+        div_magic(s, &d.strata.magic[mu], &d.strata.shift[mu]);
+        d.strata.c32[mu] = (float)((double)G / (double)s);
+        d.strata.nd[mu] = (double)s;
+    }
     d.inv_tab = d_inv;
     d.edges = mbuf<double>(mb, B_EDGES);
     d.tab = mbuf<float2>(mb, B_TAB);
@@ -605,7 +657,6 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
             k1 += 0xBB67AE85u;
         }
         L.c32 = d.ng_over_nst;
-        L.c32x = L.c32 * 1.1920928955078125e-07f;
         L.ngm1 = (float)(d.n_g - 1);
         L.ngD_m = d.ngD_m;
         L.ngD_e = d.ngD_e;
@@ -613,6 +664,7 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         L.ng = (double)d.n_g;
         L.tab = d.tab;
         L.edges = d.edges;
+        a.S = d.strata;
         a.st = d.st;
         a.off = d.off;
         a.n_h = d.n_h;
@@ -847,8 +899,9 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                 }
             }
         }
-        for (int k = 1; k <= std::min(3, g.occ_many); ++k)
-            for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r, 256});
+        if (g.uniform)
+            for (int k = 1; k <= std::min(3, g.occ_many); ++k)
+                for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r, 256});
         if (cands.size() <= 1) {
             g.tuned = true;
             g.tuned_final = true;
@@ -1200,6 +1253,14 @@ extern "C" vp_status vp_get_info(vp_ctx *c, int64_t *n_st, int64_t *n_hc, int *n
     return VP_OK;
 }
 
+extern "C" vp_status vp_get_strata(vp_ctx *c, int32_t *strata) {
+    CHECK_CTX(c);
+    if (!strata) return fail(VP_EINVAL, "NULL out");
+    const Member &mb = c->set.m[0];
+    for (int mu = 0; mu < mb.p.dim; ++mu) strata[mu] = (int32_t)mb.nst_ax[mu];
+    return VP_OK;
+}
+
 extern "C" vp_status vp_get_edges(vp_ctx *c, double *edges) {
     CHECK_CTX(c);
     if (!edges) return fail(VP_EINVAL, "NULL edges");
@@ -1425,6 +1486,8 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     if (blocks < 1 || blocks > 65535) return fail(VP_EINVAL, "blocks out of range");
     if (run < 1 || run > 64) return fail(VP_EINVAL, "run must be in 1..64");
     if (scheme == 1 && cluster != 1) return fail(VP_EINVAL, "the task scheme takes no clusters");
+    if (scheme == 1 && !g.uniform)
+        return fail(VP_EINVAL, "strata that differ between axes: the one-integral scheme only");
     if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
         return fail(VP_EINVAL, "cluster must be 1, 2, 4 or 8");
     if (cluster > 1 && !(scheme == 0 ? g.hist_one : g.hist_shared))

@@ -51,7 +51,9 @@ struct Member {
     int kind;
     std::vector<double> lo, hi, prm;
     std::vector<float> prm32;
-    int64_t n_st;
+    int64_t n_st;                 // the smallest of nst_ax
+    std::vector<int64_t> nst_ax;  // strata per axis (§3.2)
+    bool uniform;                 // every axis has n_st strata
     uint64_t n_hc;
     uint32_t n_tree;
     int hist_cap;
@@ -73,6 +75,7 @@ struct Group {
     uint32_t task = 0;
     size_t smem = 0;
     bool one = false;  // a single integral: the cluster kernel with constants in parameters
+    bool uniform = true;  // every member has the same strata on every axis (else: one only)
     int cs = 1;        // CTAs per cluster (one-integral kernel)
     int threads_one = 256;  // CTA size of the one-integral kernel
     // histograms of the one-integral kernel (one CTA per SM fits more shared

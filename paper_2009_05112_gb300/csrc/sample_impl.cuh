@@ -252,7 +252,6 @@ struct Loop {
     uint32_t n_st, calls, iid, t;
     uint32_t rk0[10], rk1[10];  // Philox round keys
     float c32;                  // N_g / N_st
-    float c32x;                 // N_g / N_st * 2^-23
     float ngm1;                 // N_g - 1
     float ngD_m;                // N_g^D = ngD_m 2^ngD_e
     int ngD_e;
@@ -281,7 +280,6 @@ __device__ __forceinline__ Loop make_loop(const Desc *dp, uint32_t t) {
         k1 += 0xBB67AE85u;
     }
     L.c32 = __ldg(&dp->ng_over_nst);
-    L.c32x = L.c32 * 1.1920928955078125e-07f;
     L.ngm1 = (float)(L.n_g - 1);
     L.ngD_m = __ldg(&dp->ngD_m);
     L.ngD_e = __ldg(&dp->ngD_e);
@@ -312,6 +310,7 @@ struct SampleOne {
     int prm_words;
     int kp_peaks;              // > 0: the peak constants are in kp (FP32 peak families)
     float kp[kParamPeaks * kParamStride];
+    Strata S;                  // strata per axis (read as constants by the unrolled loops)
 };
 
 // Fire-and-forget global reductions.
@@ -339,21 +338,29 @@ __device__ __forceinline__ U4 philox_rk(U4 c, const uint32_t (&k0)[10], const ui
     return c;
 }
 
-// FP32 per-hypercube offsets kc[mu] = (k_mu - 1 + 2^-24) N_g/N_st so that
-// y N_g = (1 + m 2^-23) N_g/N_st + kc with m = r >> 9, i.e. u = (m + 1/2) 2^-23.
-template <int DMAX>
-__device__ __forceinline__ void hcube_offsets(const Loop &L, const uint32_t (&kd)[DMAX],
-                                              float (&kc)[DMAX]) {
+// The strata constants of axis mu: per axis (AX, from S) or the one count
+// every axis shares (from L).
+template <bool AX>
+__device__ __forceinline__ float c32_of(const Loop &L, const Strata *S, int mu) {
+    return AX ? S->c32[mu] : L.c32;
+}
+
+// FP32 per-hypercube offsets kc[mu] = (k_mu - 1 + 2^-24) N_g/s_mu so that
+// y N_g = (1 + m 2^-23) N_g/s_mu + kc with m = r >> 9, i.e. u = (m + 1/2) 2^-23.
+template <int DMAX, bool AX>
+__device__ __forceinline__ void hcube_offsets(const Loop &L, const Strata *S,
+                                              const uint32_t (&kd)[DMAX], float (&kc)[DMAX]) {
 #pragma unroll
     for (int mu = 0; mu < DMAX; ++mu)
-        kc[mu] = ((float)kd[mu] - 0.99999994039535522461f) * L.c32;
+        kc[mu] = ((float)kd[mu] - 0.99999994039535522461f) * c32_of<AX>(L, S, mu);
 }
 
 // ---------------------------------------------------------------------------
 // One sample, FP32 path (a1-a3): x[], idx[], J = Jm 2^Je, f.
 // ---------------------------------------------------------------------------
-template <int DMAX, bool EXACT, int KIND, bool KP = false>
-__device__ __forceinline__ void point32(const Loop &L, const float *prm, uint32_t h, uint32_t j,
+template <int DMAX, bool EXACT, int KIND, bool KP, bool AX>
+__device__ __forceinline__ void point32(const Loop &L, const Strata *S, const float *prm,
+                                        uint32_t h, uint32_t j,
                                         const float (&kc)[DMAX], float (&x)[DMAX],
                                         int (&idx)[DMAX], float &Jm, int &Je, float &f) {
     const int dim = EXACT ? DMAX : L.dim;
@@ -372,7 +379,7 @@ __device__ __forceinline__ void point32(const Loop &L, const float *prm, uint32_
                     const uint32_t w = lane_of(r, l);
                     // (1 + m 2^-23) from the top 23 bits, no int->float conversion
                     const float one_m = __int_as_float(0x3f800000 | (w >> 9));
-                    const float tt = fmaf(one_m, L.c32, kc[mu]);  // y N_g
+                    const float tt = fmaf(one_m, c32_of<AX>(L, S, mu), kc[mu]);  // y N_g
                     // floor(tt) for 0 <= tt < 2^22 by a round-down add of 1.5 2^23
                     const float big = __fadd_rd(tt, 12582912.0f);
                     int i = __float_as_int(big) - 0x4B400000;
@@ -399,8 +406,9 @@ __device__ __forceinline__ void point32(const Loop &L, const float *prm, uint32_
 // ---------------------------------------------------------------------------
 // One sample, FP64 path (a1-a3), the oracle's IEEE sequence step by step.
 // ---------------------------------------------------------------------------
-template <int DMAX, int KIND>
-__device__ __forceinline__ void point64(const Loop &L, const double *prm, uint32_t h, uint32_t j,
+template <int DMAX, int KIND, bool AX>
+__device__ __forceinline__ void point64(const Loop &L, const Strata *S, const double *prm,
+                                        uint32_t h, uint32_t j,
                                         const uint32_t (&kd)[DMAX], double (&x)[DMAX],
                                         int (&idx)[DMAX], double &J, double &f) {
     J = 1.0;
@@ -414,7 +422,8 @@ __device__ __forceinline__ void point64(const Loop &L, const double *prm, uint32
                 const int mu = 4 * q + l;
                 if (mu < DMAX && mu < L.dim) {
                     const double u = u01_f64(lane_of(r, l));
-                    const double y = __ddiv_rn(__dadd_rn((double)kd[mu], u), L.nst);
+                    const double y =
+                        __ddiv_rn(__dadd_rn((double)kd[mu], u), AX ? S->nd[mu] : L.nst);
                     const double yng = __dmul_rn(y, L.ng);
                     int i = (int)floor(yng);
                     i = i > L.n_g - 1 ? L.n_g - 1 : i;
@@ -441,15 +450,16 @@ __device__ __forceinline__ uint32_t div_nst(uint32_t h, uint32_t magic, int shif
     return (t + ((h - t) >> 1)) >> (shift - 1);
 }
 
-// Mixed-radix digits of h: k_mu = (h / N_st^mu) mod N_st.
-template <int DMAX>
-__device__ __forceinline__ void decode_digits(uint32_t h, const Loop &L, int dim,
+// Mixed-radix digits of h: k_mu = (h / prod_{nu < mu} s_nu) mod s_mu.
+template <int DMAX, bool AX>
+__device__ __forceinline__ void decode_digits(uint32_t h, const Loop &L, const Strata *S, int dim,
                                               uint32_t (&kd)[DMAX]) {
 #pragma unroll
     for (int mu = 0; mu < DMAX; ++mu) {
         if (mu < dim) {
-            const uint32_t q = div_nst(h, L.nst_magic, L.nst_shift);
-            kd[mu] = h - q * L.n_st;
+            const uint32_t q = AX ? div_nst(h, S->magic[mu], S->shift[mu])
+                                  : div_nst(h, L.nst_magic, L.nst_shift);
+            kd[mu] = h - q * (AX ? S->n[mu] : L.n_st);
             h = q;
         } else {
             kd[mu] = 0u;
@@ -458,14 +468,15 @@ __device__ __forceinline__ void decode_digits(uint32_t h, const Loop &L, int dim
 }
 
 // h -> h + 1 on the digits (carry propagation).
-template <int DMAX>
-__device__ __forceinline__ void next_digits(uint32_t n_st, int dim, uint32_t (&kd)[DMAX]) {
+template <int DMAX, bool AX>
+__device__ __forceinline__ void next_digits(const Loop &L, const Strata *S, int dim,
+                                            uint32_t (&kd)[DMAX]) {
     bool carry = true;
 #pragma unroll
     for (int mu = 0; mu < DMAX; ++mu) {
         if (carry && mu < dim) {
             const uint32_t v = kd[mu] + 1u;
-            if (v >= n_st) {
+            if (v >= (AX ? S->n[mu] : L.n_st)) {
                 kd[mu] = 0u;
             } else {
                 kd[mu] = v;
@@ -623,8 +634,9 @@ __device__ __forceinline__ uint64_t lane_find_hcube(const uint64_t *off, uint64_
 
 // (HM: the histogram layout, kHist*; a template parameter so that the
 // per-axis updates carry no branch on it)
-template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, int HM>
-__device__ __forceinline__ void run_samples_t(const Loop &L, const Ptrs &P, const void *prm,
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, int HM, bool AX>
+__device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, const Ptrs &P,
+                                              const void *prm,
                                               uint64_t s_begin, uint64_t s_end, uint64_t h,
                                               uint64_t lo_off, uint64_t next,
                                               typename Real<F64>::T *hs, float *hs_t,
@@ -635,9 +647,9 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Ptrs &P, cons
     const int dim = EXACT ? DMAX : L.dim;
     uint32_t j = (uint32_t)(s_begin - lo_off);
     uint32_t kd[DMAX];
-    decode_digits<DMAX>((uint32_t)h, L, dim, kd);
+    decode_digits<DMAX, AX>((uint32_t)h, L, S, dim, kd);
     float kc[DMAX];
-    if (!F64) hcube_offsets<DMAX>(L, kd, kc);
+    if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
     Acc<F64> acc;
     acc.reset();
     // 32-bit counters (an iteration has fewer than 2^32 samples): samples left
@@ -651,8 +663,8 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Ptrs &P, cons
             ++h;
             to_next = __ldg(P.nh + h);
             j = 0;
-            next_digits<DMAX>(L.n_st, dim, kd);
-            if (!F64) hcube_offsets<DMAX>(L, kd, kc);
+            next_digits<DMAX, AX>(L, S, dim, kd);
+            if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
         }
         --to_next;
         int idx[DMAX];
@@ -665,13 +677,13 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Ptrs &P, cons
         double vbig = 0.0, vbig2 = 0.0;
         if (F64) {
             double x[DMAX], J, f;
-            point64<DMAX, KIND>(L, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
+            point64<DMAX, KIND, AX>(L, S, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
             v = (T)(J * f * pow2d(sexp));
         } else {
             float x[DMAX], Jm, f;
             int Je;
-            point32<DMAX, EXACT, KIND, KP>(L, (const float *)prm, (uint32_t)h, j, kc, x, idx, Jm, Je,
-                                           f);
+            point32<DMAX, EXACT, KIND, KP, AX>(L, S, (const float *)prm, (uint32_t)h, j, kc, x, idx,
+                                               Jm, Je, f);
             const float jf = Jm * f;  // normal or zero: Jm in [1, 2), f flushed to zero
             const int ej = ((__float_as_int(jf) >> 23) & 0xff) - 127;
             const int ev = ej + Je + sexp;  // exponent of v
@@ -730,21 +742,21 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Ptrs &P, cons
     acc.flush(P.S1 + h, P.S2 + h, sexp);
 }
 
-template <int DMAX, bool EXACT, bool F64, int KIND, bool KP = false>
-__device__ __forceinline__ void run_samples(const Loop &L, const Ptrs &P, const void *prm,
-                                            uint64_t s_begin, uint64_t s_end, uint64_t h,
-                                            uint64_t lo_off, uint64_t next,
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, bool AX>
+__device__ __forceinline__ void run_samples(const Loop &L, const Strata *S, const Ptrs &P,
+                                            const void *prm, uint64_t s_begin, uint64_t s_end,
+                                            uint64_t h, uint64_t lo_off, uint64_t next,
                                             typename Real<F64>::T *hs, float *hs_t, uint32_t *hc,
                                             int hist_mode, int sexp) {
     if (hist_mode == kHistShared)
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistShared>(L, P, prm, s_begin, s_end, h,
-                                                               lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistShared, AX>(
+            L, S, P, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
     else if (!F64 && hist_mode == kHistCompact)
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistCompact>(L, P, prm, s_begin, s_end, h,
-                                                                lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistCompact, AX>(
+            L, S, P, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
     else
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistGlobal>(L, P, prm, s_begin, s_end, h,
-                                                               lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistGlobal, AX>(
+            L, S, P, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
 }
 
 // ---------------------------------------------------------------------------
@@ -881,9 +893,10 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
             uint64_t lo_off = 0, hi_off = 0;
             const uint64_t h =
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
-            if (s0 < s1)
-                run_samples<DMAX, EXACT, F64, KIND, KP>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
-                                                        hs_t, hc, a.hist_shared, sexp);
+            if (s0 < s1)  // (the strata per axis: constants of the parameter bank)
+                run_samples<DMAX, EXACT, F64, KIND, KP, true>(L, &a.S, P, prm, s0, s1, h, lo_off,
+                                                              hi_off, hs, hs_t, hc, a.hist_shared,
+                                                              sexp);
         }
     }
     __syncthreads();
@@ -1014,8 +1027,9 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
             const uint64_t h =
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)
-                run_samples<DMAX, EXACT, F64, KIND>(L, P, prm, s0, s1, h, lo_off, hi_off, hs,
-                                                    hs_t, hc, a.hist_shared ? kHistShared : kHistGlobal, sexp);
+                run_samples<DMAX, EXACT, F64, KIND, false, false>(  // (the same strata on every axis)
+                    L, nullptr, P, prm, s0, s1, h, lo_off, hi_off, hs, hs_t, hc,
+                    a.hist_shared ? kHistShared : kHistGlobal, sexp);
         }
     }
     if (cur >= 0 && a.hist_shared) flush_hist();
@@ -1040,6 +1054,7 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
     float *sprm = (float *)smem;
     const Desc *dp = desc + member;
     const Loop L = make_loop(dp, t);
+    const Strata *S = &dp->strata;
     const int dim = EXACT ? DMAX : L.dim;
     if (!F64) load_prm32(dp, sprm, prm_words);
     __syncthreads();
@@ -1047,16 +1062,17 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
          k += (int64_t)gridDim.x * blockDim.x) {
         uint32_t kd[DMAX];
         int idx[DMAX];
-        decode_digits<DMAX>((uint32_t)hs[k], L, dim, kd);
+        decode_digits<DMAX, true>((uint32_t)hs[k], L, S, dim, kd);
         double xd[DMAX], jac, f;
         if (F64) {
-            point64<DMAX, KIND>(L, (const double *)__ldg((const unsigned long long *)&dp->prm),
+            point64<DMAX, KIND, true>(L, S, (const double *)__ldg((const unsigned long long *)&dp->prm),
                                 (uint32_t)hs[k], js[k], kd, xd, idx, jac, f);
         } else {
             float kc[DMAX], x[DMAX], Jm, ff;
             int Je;
-            hcube_offsets<DMAX>(L, kd, kc);
-            point32<DMAX, EXACT, KIND>(L, sprm, (uint32_t)hs[k], js[k], kc, x, idx, Jm, Je, ff);
+            hcube_offsets<DMAX, true>(L, S, kd, kc);
+            point32<DMAX, EXACT, KIND, false, true>(L, S, sprm, (uint32_t)hs[k], js[k], kc, x, idx,
+                                                    Jm, Je, ff);
 #pragma unroll
             for (int mu = 0; mu < DMAX; ++mu) xd[mu] = (double)x[mu];
             jac = ldexp((double)Jm, Je);

@@ -51,19 +51,31 @@ struct State {
 constexpr uint32_t kDoneStop = 1u;       // the request is finished
 constexpr uint32_t kDoneConverged = 2u;  // ... because sdev <= rtol |mean|
 
+// Strata per axis (§3 uses the same N_st on every axis; §3.2 lets them
+// differ) and the constants the sampling loop derives from them.  Hypercube h
+// is the mixed-radix number with digit k_mu in [0, n[mu]) on axis mu, axis 0
+// least significant; entries mu >= D hold 1.
+struct Strata {
+    uint32_t n[kMaxDim];       // strata on axis mu
+    uint32_t magic[kMaxDim];   // h / n[mu] = ((t + ((h - t) >> 1)) >> (shift[mu] - 1)),
+    int32_t shift[kMaxDim];    //   t = umulhi(magic[mu], h); shift 0: n[mu] = 1
+    float c32[kMaxDim];        // N_g / n[mu] (FP32 path)
+    double nd[kMaxDim];        // n[mu] (FP64 path)
+};
+
 // Read-only (per iteration) description of one integral.
 struct Desc {
     int32_t dim, n_g, kind, prec;
     int32_t plus2, n_peaks;    // n_peaks: K for peak families, n points for POSTERIOR
     int32_t n_par;             // POSTERIOR: P (dim = P + G)
     int32_t hist_cap;          // capacity of the iteration history
-    uint32_t n_st, integral_id;
+    uint32_t n_st, integral_id;  // n_st: strata on axis 0 (every axis unless mixed)
     uint32_t key0, key1;       // Philox key (seed lo, hi)
     uint32_t n_tree;           // ceil(n_hc / kTreeBlock)
-    uint32_t pad0;
+    uint32_t uniform;          // 1: the same strata on every axis (the task kernel's case)
     int64_t n_ev;
-    uint64_t n_hc;             // N_h = N_st^D
-    double omega;              // y-volume of a hypercube, N_st^-D
+    uint64_t n_hc;             // N_h = prod_mu strata[mu] (N_st^D when uniform)
+    double omega;              // y-volume of a hypercube, 1 / N_h
     double alpha, beta;
     double omega_beta;         // Omega^beta (FP32 path: d_h = Omega^beta var^(beta/2))
     float half_beta_hi, half_beta_lo;  // beta/2 = hi + lo (FP32 path)
@@ -96,6 +108,7 @@ struct Desc {
     double rtol;
     int32_t discard, min_meas, stop_it, pad1;
     uint32_t *done_out;        // the server's flag for this request's slot
+    Strata strata;
 };
 
 // ---------------------------------------------------------------------------

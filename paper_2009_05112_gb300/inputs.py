@@ -44,6 +44,8 @@ class Problem:
     n_st: int = 0           # 0: Eq. (Nst_vegasp); > 0: forced stratification count
     exact: float = math.nan  # closed form where one exists
     meta: dict = field(default_factory=dict)
+    n_st_axis: tuple = None  # strata per axis (§3.2); overrides n_st
+    mixed: bool = False      # §3.2's mixed N_st / N_st + 1 rule in place of Eq. (Nst_vegasp)
 
 
 def _blob(rows):
@@ -144,6 +146,26 @@ def three_exp_d8(n_ev=1_000_000, n_it=30, discard=10, n_g=1000, seed=0, beta=0.7
     return Problem("three_exp_d8", dim, EXPNORM, expnorm_blob([1.0] * 3, [50.0] * 3, cs),
                    np.zeros(dim), np.ones(dim), n_g=n_g, n_ev=n_ev, seed=seed, n_it=n_it,
                    discard=discard, alpha=alpha, beta=beta)
+
+
+def exp_origin(dim=16, n_ev=250_000, n_it=50, n_g=1000, seed=0, mixed=True):
+    """§3.2 Eq. (mixed): exp(-50 |x|) on [0,1]^D, a sharp peak at a corner of
+    the box, with the paper's alpha = 0.1, beta = 0.75 (set to zero for the
+    second half of the iterations by the caller) and N_ev = 2.5e5."""
+    exact, _ = exp_origin_exact(dim, 50.0)
+    return Problem("exp_origin_d%d" % dim, dim, EXPNORM, expnorm_blob([1.0], [50.0], [np.zeros(dim)]),
+                   np.zeros(dim), np.ones(dim), n_g=n_g, n_ev=n_ev, seed=seed, n_it=n_it,
+                   discard=n_it // 2, alpha=0.1, beta=0.75, mixed=mixed, exact=exact)
+
+
+def exp_origin_exact(dim, slope):
+    """int over [0,1]^D of exp(-slope |x|), as 2^-D of the whole-space value
+    S_{D-1} Gamma(D) / slope^D, and a bound on the relative size of the part
+    outside the box (every such point has |x| > 1): the regularised upper
+    incomplete gamma Q(D, slope)."""
+    full = 2.0 * math.pi ** (dim / 2) / math.gamma(dim / 2) * math.gamma(dim) / slope ** dim
+    q = sum(math.exp(-slope + k * math.log(slope) - math.lgamma(k + 1)) for k in range(dim))
+    return 2.0 ** -dim * full, q
 
 
 def legendre_design(xs, n_par):

@@ -38,7 +38,8 @@ class vp_params(ctypes.Structure):
                 ("n_ev", ctypes.c_int64), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("integral_id", ctypes.c_uint32),
                 ("precision", ctypes.c_int), ("plus2", ctypes.c_int), ("n_st", ctypes.c_int),
-                ("max_it", ctypes.c_int)]
+                ("max_it", ctypes.c_int), ("n_st_axis", ctypes.POINTER(ctypes.c_int32)),
+                ("mixed", ctypes.c_int)]
 
 
 class vp_integrand(ctypes.Structure):
@@ -92,6 +93,7 @@ _SIGS = {
     "vp_map_destroy": [_P],
     "vp_get_info": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                     ctypes.POINTER(ctypes.c_int)],
+    "vp_get_strata": [_P, _P],
     "vp_get_edges": [_P, _P],
     "vp_set_edges": [_P, _P],
     "vp_get_alloc": [_P, _P, _P],
@@ -202,7 +204,7 @@ class Integrator:
 
     def __init__(self, dim, lo, hi, kind, prm, n_g=1000, n_ev=10_000, alpha=0.5, beta=0.75,
                  seed=0, integral_id=0, precision=VP_FP64, plus2=False, n_st=0, max_it=0,
-                 stream=None):
+                 stream=None, n_st_axis=None, mixed=False):
         self.dim, self.n_g = int(dim), int(n_g)
         self._lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.dim,)))
         self._hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (self.dim,)))
@@ -212,6 +214,10 @@ class Integrator:
         p = vp_params(self.dim, self._lo.ctypes.data_as(_dp), self._hi.ctypes.data_as(_dp),
                       self.n_g, int(n_ev), float(alpha), float(beta), int(seed) & (2 ** 64 - 1),
                       int(integral_id), int(precision), int(bool(plus2)), int(n_st), int(max_it))
+        if n_st_axis is not None:
+            self._nst = np.ascontiguousarray(n_st_axis, np.int32).reshape(self.dim)
+            p.n_st_axis = self._nst.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.mixed = int(bool(mixed))
         f = vp_integrand(int(kind), self._prm.size, self._prm.ctypes.data_as(_dp))
         self.stream = current_stream() if stream is None else ctypes.c_void_p(stream)
         h = ctypes.c_void_p()
@@ -225,7 +231,8 @@ class Integrator:
         args = dict(dim=prob.dim, lo=prob.lo, hi=prob.hi, kind=prob.kind, prm=prob.prm,
                     n_g=prob.n_g, n_ev=prob.n_ev, alpha=prob.alpha, beta=prob.beta,
                     seed=prob.seed, integral_id=prob.integral_id, precision=precision,
-                    plus2=prob.plus2, n_st=prob.n_st)
+                    plus2=prob.plus2, n_st=prob.n_st, n_st_axis=prob.n_st_axis,
+                    mixed=prob.mixed)
         args.update(kw)
         return cls(**args)
 
@@ -283,6 +290,12 @@ class Integrator:
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
         check(lib().vp_get_info(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def strata(self):
+        """Strata on every axis (§3.2)."""
+        out = np.zeros(self.dim, np.int32)
+        check(lib().vp_get_strata(self.ctx, _ptr(out)))
+        return out
 
     def edges(self):
         out = np.zeros((self.dim, self.n_g + 1))
@@ -383,6 +396,7 @@ class Batch:
                               int(prob.n_ev), float(prob.alpha), float(prob.beta),
                               int(prob.seed) & (2 ** 64 - 1), int(prob.integral_id),
                               int(precision), int(bool(prob.plus2)), int(prob.n_st), 0)
+            _set_strata(ps[i], prob, self._keep)
             fs[i] = vp_integrand(int(prob.kind), prm.size, prm.ctypes.data_as(_dp))
         self.stream = current_stream() if stream is None else ctypes.c_void_p(stream)
         h = ctypes.c_void_p()
@@ -448,8 +462,18 @@ def _params_of(prob, precision, max_it, keep):
                   int(prob.n_ev), float(prob.alpha), float(prob.beta),
                   int(prob.seed) & (2 ** 64 - 1), int(prob.integral_id), int(precision),
                   int(bool(prob.plus2)), int(prob.n_st), int(max_it))
+    _set_strata(p, prob, keep)
     f = vp_integrand(int(prob.kind), prm.size, prm.ctypes.data_as(_dp))
     return p, f
+
+
+def _set_strata(p, prob, keep):
+    """The per-axis strata fields of vp_params from a Problem (§3.2)."""
+    if getattr(prob, "n_st_axis", None) is not None:
+        a = np.ascontiguousarray(prob.n_st_axis, np.int32).reshape(prob.dim)
+        keep.append(a)
+        p.n_st_axis = a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.mixed = int(bool(getattr(prob, "mixed", False)))
 
 
 def clock():
