@@ -70,6 +70,13 @@ def lib():
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
         L.or_hcube_moments.restype = None
+        L.or_sample_multi.argtypes = [ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_uint64,
+                                      ctypes.c_uint32, _f64p, ctypes.c_int, _f64p,
+                                      ctypes.c_uint32, _u32p, ctypes.c_int, _i32p, _f64p, _f64p]
+        L.or_sample_multi.restype = ctypes.c_int
+        L.or_estimate_multi.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int, _f64p,
+                                        _f64p, _u32p, _f64p, _f64p, _f64p]
+        L.or_estimate_multi.restype = None
         L.or_tree_sum.argtypes = [_f64p, ctypes.c_int64]
         L.or_tree_sum.restype = ctypes.c_double
         L.or_estimate.argtypes = [ctypes.c_int64, ctypes.c_double, _f64p, _f64p, _u32p, _f64p,
@@ -159,6 +166,22 @@ def estimate(omega, s1, s2, n_h):
     return I.value, var.value
 
 
+def estimate_multi(omega, x1, x2, n_h):
+    """§4's several integrals from one set of samples: I[k] and the covariance
+    C[k][l] summed over hypercubes (§2.1 Eq. sigest in several variables, §3
+    Eq. sumI).  x1 is [N_h][M], x2 [N_h][M (M + 1) / 2] (upper triangle by
+    rows).  Pinned by numpy's sample covariance of the per-sample values, by
+    M = 1 against estimate() and by closed-form moments of a Gaussian."""
+    x1 = np.ascontiguousarray(x1, np.float64)
+    n, M = x1.shape
+    work = np.zeros(max(n, 1), np.float64)
+    I = np.zeros(M)
+    C = np.zeros((M, M))
+    lib().or_estimate_multi(n, float(omega), M, x1, np.ascontiguousarray(x2, np.float64),
+                            np.ascontiguousarray(n_h, np.uint32), work, I, C)
+    return I, C
+
+
 def sigma(omega, s1, s2, n_h):
     """§3 step 2: sigma_h(Jf) from the iteration's samples."""
     out = np.zeros(len(n_h), np.float64)
@@ -246,6 +269,39 @@ def combine(I, var, discard=0):
     return dict(mean=mean, sdev=sdev, chi2=chi2, dof=n - 1, n_it=n)
 
 
+def combine_multi(I, C, discard=0, cut=1e-12):
+    """Several integrals over iterations (the §2.5 weighted average in several
+    variables): with W_j the pseudo-inverse of C_j (eigenvalues below cut x
+    the largest dropped),
+        mean = (sum W_j)^+ sum W_j I_j,   cov = (sum W_j)^+,
+        chi2 = sum_j (I_j - mean)^T W_j (I_j - mean),   dof = M (n - 1).
+    reading: the paper gives the one-variable form only; this is its
+    generalised-least-squares extension.  If every W_j vanishes (zero
+    covariances) the plain mean of the I_j is returned with cov 0.  Pinned by
+    M = 1 against combine() and by a 2 x 2 example in exact arithmetic."""
+    I = np.asarray(I, np.float64)[discard:]
+    C = np.asarray(C, np.float64)[discard:]
+    n = I.shape[0]
+    if n == 0:
+        return None
+    M = I.shape[1]
+
+    def pinv(A):
+        w, U = np.linalg.eigh(0.5 * (A + A.T))
+        top = np.max(np.abs(w)) if w.size else 0.0
+        inv = np.array([1.0 / x if top > 0 and x > cut * top else 0.0 for x in w])
+        return (U * inv) @ U.T
+
+    W = [pinv(c) for c in C]
+    Ws = np.sum(W, axis=0)
+    if not np.any(Ws):
+        return dict(mean=I.mean(axis=0), cov=np.zeros((M, M)), chi2=0.0, dof=M * (n - 1), n_it=n)
+    cov = pinv(Ws)
+    mean = cov @ np.sum([w @ i for w, i in zip(W, I)], axis=0)
+    chi2 = float(sum((i - mean) @ w @ (i - mean) for w, i in zip(W, I)))
+    return dict(mean=mean, cov=cov, chi2=chi2, dof=M * (n - 1), n_it=n)
+
+
 def combine_unweighted(I, var, discard=0):
     """§2.5, last paragraph: unweighted mean of the I_j and mean sigma_j over
     sqrt(N_it) (used with a frozen map, alpha = 0)."""
@@ -267,11 +323,14 @@ class VegasPlus:
     alternative of §3 Eq. nh), kind and prm (integrand family and blob), n_st
     (0: §3 Eq. Nst_vegasp; otherwise the stratification count to use on every
     axis), n_st_axis (explicit strata per axis, §3.2) and mixed (§3.2's
-    N_st / N_st + 1 rule in place of Eq. Nst_vegasp).
+    N_st / N_st + 1 rule in place of Eq. Nst_vegasp); out_mono lists extra
+    outputs f x^a x^b as pairs (a, b) (-1: no factor) integrated on the same
+    samples (§4), output 0 being f, which alone drives the adaptation.
     """
 
     def __init__(self, dim, lo, hi, n_g, n_ev, alpha, beta, seed, kind, prm,
-                 integral_id=0, plus2=False, n_st=0, n_st_axis=None, mixed=False):
+                 integral_id=0, plus2=False, n_st=0, n_st_axis=None, mixed=False,
+                 out_mono=None):
         self.dim, self.n_g, self.n_ev = int(dim), int(n_g), int(n_ev)
         self.alpha, self.beta = float(alpha), float(beta)
         self.seed, self.integral_id, self.plus2 = int(seed), int(integral_id), bool(plus2)
@@ -302,6 +361,11 @@ class VegasPlus:
         self.t = 0
         self.I, self.var = [], []
         self.s1 = self.s2 = self.hsum = self.hcnt = None
+        pairs = [(-1, -1)] + [tuple(p) for p in (out_mono or [])]
+        self.mono = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1))
+        self.n_out = len(pairs)
+        self.Im, self.Cm = [], []  # per iteration: I[k], C[k][l] (n_out > 1 only)
+        self.x1 = self.x2 = None
 
     def sample(self):
         """Steps a1-a5 of the current iteration (no state change but the buffers)."""
@@ -315,9 +379,24 @@ class VegasPlus:
                                        self.hcnt)
         assert rc == 0
 
+    def sample_multi(self):
+        """X1_h[k], X2_h[k,l] of the current iteration's samples (§4)."""
+        M = self.n_out
+        self.x1 = np.zeros((self.n_hc, M))
+        self.x2 = np.zeros((self.n_hc, M * (M + 1) // 2))
+        rc = lib().or_sample_multi(self.dim, self.n_g, self.nst_ax, self.seed, self.integral_id,
+                                   self.edges, self.kind, self.prm, self.t, self.n_h, M,
+                                   self.mono, self.x1, self.x2)
+        assert rc == 0
+
     def iterate(self):
         """One iteration's sampling and estimate (steps a1-a6); returns (I_j, var_j)."""
         self.sample()
+        if self.n_out > 1:
+            self.sample_multi()
+            Im, Cm = estimate_multi(self.omega, self.x1, self.x2, self.n_h)
+            self.Im.append(Im)
+            self.Cm.append(Cm)
         I, var = estimate(self.omega, self.s1, self.s2, self.n_h)
         self.I.append(I)
         self.var.append(var)
@@ -364,3 +443,6 @@ class VegasPlus:
 
     def result(self, discard=0):
         return combine(self.I, self.var, discard)
+
+    def result_multi(self, discard=0):
+        return combine_multi(self.Im, self.Cm, discard)

@@ -271,6 +271,78 @@ int or_sample_iteration(int dim, int n_g, const int64_t *nst_ax, uint64_t seed,
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* §4 (several integrals from the same samples): outputs k = 0 .. M-1 with     */
+/* v_k = J f g_k(x), g_k(x) = x^a x^b for the pair (a, b) = mono[2k], mono[2k+1] */
+/* (a or b < 0: that factor is 1; output 0 is f itself, mono = (-1, -1)).      */
+/* Per hypercube, in sample order:                                             */
+/*   X1_h[k] = sum_j v_k,   X2_h[k,l] = sum_j v_k v_l  (k <= l)                */
+/* X2 is stored as the upper triangle row by row: T = M (M + 1) / 2 entries,   */
+/* (k, l) at k M - k (k - 1) / 2 + (l - k).  Overwrites x1 [n_hc][M] and      */
+/* x2 [n_hc][T].                                                              */
+/* ------------------------------------------------------------------------ */
+static int or_tri(int M, int k, int l) { return k * M - k * (k - 1) / 2 + (l - k); }
+double or_tree_sum(const double *v, int64_t n); /* below: the fixed summation order */
+
+int or_sample_multi(int dim, int n_g, const int64_t *nst_ax, uint64_t seed, uint32_t integral_id,
+                    const double *edges, int kind, const double *prm, uint32_t t,
+                    const uint32_t *n_h, int M, const int32_t *mono, double *x1, double *x2) {
+    or_problem P = {dim, n_g, nst_ax, seed, integral_id, edges, kind, prm};
+    int64_t n_hc = 1;
+    for (int mu = 0; mu < dim; ++mu) n_hc *= nst_ax[mu];
+    const int T = M * (M + 1) / 2;
+    double x[64], v[64];
+    int idx[64];
+    if (dim > 64 || M > 64) return -1;
+    for (int64_t h = 0; h < n_hc; ++h) {
+        double *a1 = x1 + (size_t)h * M, *a2 = x2 + (size_t)h * T;
+        for (int k = 0; k < M; ++k) a1[k] = 0.0;
+        for (int q = 0; q < T; ++q) a2[q] = 0.0;
+        for (uint32_t j = 0; j < n_h[h]; ++j) {
+            double f;
+            double jf = or_sample(&P, t, (uint64_t)h, j, x, idx, &f) * f;
+            for (int k = 0; k < M; ++k) {
+                const int a = mono[2 * k], b = mono[2 * k + 1];
+                const double g = (a >= 0 ? x[a] : 1.0) * (b >= 0 ? x[b] : 1.0);
+                v[k] = jf * g;
+            }
+            for (int k = 0; k < M; ++k) {
+                a1[k] += v[k];
+                for (int l = k; l < M; ++l) a2[or_tri(M, k, l)] += v[k] * v[l];
+            }
+        }
+    }
+    return 0;
+}
+
+/* §4 with §2.1 Eq. (sigest) in its several-variable form, per hypercube, and */
+/* §3 Eq. (sumI) over hypercubes:                                            */
+/*   I[k]     = sum_h Omega X1_h[k] / n_h                                    */
+/*   C[k][l]  = sum_h Omega^2 (X2_h[k,l]/n_h - (X1_h[k]/n_h)(X1_h[l]/n_h))   */
+/*                      / (n_h - 1)                                          */
+/* each sum in the fixed order of or_tree_sum; the diagonal terms clamped at   */
+/* zero as the scalar variance is (reading).  out_c is M x M, symmetric.      */
+void or_estimate_multi(int64_t n_hc, double omega, int M, const double *x1, const double *x2,
+                       const uint32_t *n_h, double *work, double *out_i, double *out_c) {
+    const int T = M * (M + 1) / 2;
+    for (int k = 0; k < M; ++k) {
+        for (int64_t h = 0; h < n_hc; ++h)
+            work[h] = omega * (x1[(size_t)h * M + k] / (double)n_h[h]);
+        out_i[k] = or_tree_sum(work, n_hc);
+    }
+    for (int k = 0; k < M; ++k)
+        for (int l = k; l < M; ++l) {
+            for (int64_t h = 0; h < n_hc; ++h) {
+                const double n = (double)n_h[h];
+                const double mk = x1[(size_t)h * M + k] / n, ml = x1[(size_t)h * M + l] / n;
+                double c = x2[(size_t)h * T + or_tri(M, k, l)] / n - mk * ml;
+                if (k == l && c < 0.0) c = 0.0;
+                work[h] = omega * omega * c / (n - 1.0);
+            }
+            out_c[k * M + l] = out_c[l * M + k] = or_tree_sum(work, n_hc);
+        }
+}
+
 /* S1_h, S2_h of one hypercube h with n samples (for spot checks at sizes  */
 /* where a whole iteration is too slow on the CPU).                          */
 void or_hcube_moments(int dim, int n_g, const int64_t *nst_ax, uint64_t seed,
