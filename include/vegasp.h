@@ -112,6 +112,16 @@ typedef struct {
                            rule, N_st + 1 strata on the first d axes and N_st on
                            the rest, N_st from Eq. Nst_vegasp and d the largest
                            with 4 (N_st + 1)^d N_st^(D - d) <= N_ev; 0 = uniform */
+    /* Several integrals from the same samples (§4): besides f itself (output
+       0, which alone drives the adaptation), n_extra outputs f(x) x^a x^b,
+       (a, b) = out_mono[2k], out_mono[2k + 1] for k < n_extra, each in
+       -1..D-1 (-1: that factor is 1): the means and second moments of the
+       paper's Bayesian example.  Every iteration then also records the
+       estimates of all M = n_extra + 1 outputs and their covariance, summed
+       over hypercubes (§2.1 Eq. sigest in several variables).  FP64 only, one
+       integral per context, at most 2^22 hypercubes, n_extra <= 7. */
+    int n_extra;
+    const int32_t *out_mono; /* [2 n_extra] (copied) */
 } vp_params;
 
 typedef struct {
@@ -189,6 +199,21 @@ const char *vp_last_error(void);
 vp_status vp_get_info(vp_ctx *ctx, int64_t *n_st, int64_t *n_hc, int *n_it);
 /* strata[D]: the strata on every axis (§3.2) */
 vp_status vp_get_strata(vp_ctx *ctx, int32_t *strata);
+/* Several integrals (§4), M = n_extra + 1 outputs.  vp_get_history_multi:
+ * i_j[n][M] and cov_j[n][M][M] of the first n iterations.  vp_result_multi:
+ * their combination over iterations j >= discard, the several-variable form
+ * of §2.5's weighted average -- with W_j the pseudo-inverse of cov_j
+ * (eigenvalues below 1e-12 of the largest dropped), mean = (sum W_j)^+
+ * sum W_j I_j, cov = (sum W_j)^+, chi2 = sum_j (I_j - mean)^T W_j (I_j -
+ * mean), dof = M (n_it - 1); if every W_j vanishes, the plain mean with cov 0.
+ * mean[M], cov[M][M]; n_it may be NULL.  VP_EINVAL on a context without extra
+ * outputs; VP_ENONFINITE as vp_result.  vp_get_moments_multi: the latest
+ * iteration's per-hypercube sums x1[N_h][M] = sum J f g_k and x2[N_h][M (M +
+ * 1)/2] = sum J^2 f^2 g_k g_l (k <= l, rows of the upper triangle). */
+vp_status vp_get_history_multi(vp_ctx *ctx, int n, double *i_j, double *cov_j);
+vp_status vp_result_multi(vp_ctx *ctx, int discard, double *mean, double *cov, double *chi2,
+                          int *dof, int *n_it);
+vp_status vp_get_moments_multi(vp_ctx *ctx, double *x1, double *x2);
 /* edges[D][N_g + 1] (FP64 master grid) */
 vp_status vp_get_edges(vp_ctx *ctx, double *edges);
 /* replaces the grid (edges[D][N_g+1], strictly increasing, ends = box) */

@@ -695,6 +695,114 @@ static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaSt
     return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
+// ---------------------------------------------------------------------------
+// Several integrals from the same samples (§4): the iteration's estimates of
+// every output and their covariance, summed over hypercubes (§2.1 Eq. sigest
+// in several variables, §3 Eq. sumI):
+//   I[k]    = sum_h Omega X1_h[k] / n_h
+//   C[k][l] = sum_h Omega^2 (X2_h[k,l]/n_h - (X1_h[k]/n_h)(X1_h[l]/n_h)) / (n_h - 1)
+// (diagonal terms clamped at zero), every sum in the fixed order of the
+// one-integral sums: blocks of kTreeBlock hypercubes by pairwise halving, then
+// an adjacent pairwise tree over the blocks.  One CTA per block; the last CTA
+// to finish combines the blocks and writes the iteration's row of the
+// history.  Launched between the sampling kernel and k_estimate (which
+// advances the iteration counter); it clears the other buffer of X1, X2 for
+// the next iteration.  It does not release its dependents early.
+// ---------------------------------------------------------------------------
+constexpr int kMultiThreads = 256;
+constexpr int kMultiMaxBlocks = (int)(kMultiMaxHc / kTreeBlock);  // 4096
+
+__device__ __forceinline__ double multi_term(const Desc &d, const double *X1, const double *X2,
+                                             int M, int s, uint64_t h) {
+    if (h >= d.n_hc) return 0.0;
+    const double n = (double)d.n_h[h];
+    const double om = d.omega;
+    if (s < M) return __dmul_rn(om, __ddiv_rn(X1[h * M + s], n));
+    int k = 0, q = s - M;  // (k, l) of triangle entry q
+    while (q >= M - k) {
+        q -= M - k;
+        ++k;
+    }
+    const int l = k + q;
+    const uint64_t T = (uint64_t)M * (M + 1) / 2;
+    const double mk = __ddiv_rn(X1[h * M + k], n), ml = __ddiv_rn(X1[h * M + l], n);
+    double c = __dsub_rn(__ddiv_rn(X2[h * T + (s - M)], n), __dmul_rn(mk, ml));
+    if (k == l && c < 0.0) c = 0.0;
+    return __ddiv_rn(__dmul_rn(__dmul_rn(om, om), c), __dsub_rn(n, 1.0));
+}
+
+__global__ void __launch_bounds__(kMultiThreads) k_estimate_multi(const Desc *desc) {
+    __shared__ double sh[kMultiThreads];
+    __shared__ double tree[kMultiMaxBlocks];
+    __shared__ bool s_last;
+    pdl_wait();
+    const Desc &d = *desc;
+    const int M = d.n_out, T = M * (M + 1) / 2, NS = M + T;
+    const uint32_t t_it = __ldcg(&d.st->t);  // the iteration being estimated
+    const uint64_t par = t_it & 1u;
+    const double *X1 = d.x1 + par * d.n_hc * M, *X2 = d.x2 + par * d.n_hc * T;
+    const uint32_t blk = blockIdx.x, t = threadIdx.x;
+    const uint64_t h0 = (uint64_t)blk * kTreeBlock;
+    for (int s = 0; s < NS; ++s) {
+        // halving over the block's 1024 terms: i += i + 512, then i += i + 256
+        // (thread t holds terms t, t + 256, t + 512, t + 768), then in shared
+        // memory down to 32 terms, then by shuffles
+        const double v0 = multi_term(d, X1, X2, M, s, h0 + t);
+        const double v1 = multi_term(d, X1, X2, M, s, h0 + t + 256);
+        const double v2 = multi_term(d, X1, X2, M, s, h0 + t + 512);
+        const double v3 = multi_term(d, X1, X2, M, s, h0 + t + 768);
+        sh[t] = __dadd_rn(__dadd_rn(v0, v2), __dadd_rn(v1, v3));
+        __syncthreads();
+        for (int w = 128; w >= 32; w >>= 1) {
+            if (t < (uint32_t)w) sh[t] = __dadd_rn(sh[t], sh[t + w]);
+            __syncthreads();
+        }
+        if (t < 32) {
+            double a = sh[t];
+            for (int o = 16; o >= 1; o >>= 1) a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
+            if (t == 0) d.mpart[(size_t)blk * NS + s] = a;
+        }
+        __syncthreads();
+    }
+    {  // the other buffer, zero for the next iteration (this block's hypercubes)
+        const uint64_t hb = min((uint64_t)kTreeBlock, d.n_hc - h0);
+        double *Y1 = d.x1 + (par ^ 1u) * d.n_hc * M + h0 * M;
+        double *Y2 = d.x2 + (par ^ 1u) * d.n_hc * T + h0 * T;
+        for (uint64_t i = t; i < hb * M; i += kMultiThreads) Y1[i] = 0.0;
+        for (uint64_t i = t; i < hb * T; i += kMultiThreads) Y2[i] = 0.0;
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = atomicAdd(&d.st->done_multi, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    uint32_t P = 1;
+    while (P < gridDim.x) P <<= 1;
+    for (int s = 0; s < NS; ++s) {
+        for (uint32_t i = t; i < P; i += kMultiThreads)
+            tree[i] = i < gridDim.x ? __ldcg(d.mpart + (size_t)i * NS + s) : 0.0;
+        __syncthreads();
+        for (uint32_t w = 1; w < P; w <<= 1) {
+            for (uint32_t i = t * 2 * w; i < P; i += kMultiThreads * 2 * w)
+                tree[i] = __dadd_rn(tree[i], tree[i + w]);
+            __syncthreads();
+        }
+        if (t == 0 && t_it < (uint32_t)d.hist_cap) {
+            if (s < M) d.hist_im[(size_t)t_it * M + s] = tree[0];
+            else d.hist_cm[(size_t)t_it * T + (s - M)] = tree[0];
+        }
+        __syncthreads();
+    }
+    if (t == 0) d.st->done_multi = 0u;
+}
+
+cudaError_t launch_estimate_multi(const Desc *desc, uint32_t n_blocks, cudaStream_t s) {
+    // (programmatic serialisation: waits for the sampling kernel in pdl_wait;
+    // it never triggers early, so k_estimate after it sees its whole result)
+    return launch_pdl(k_estimate_multi, dim3(n_blocks), dim3(kMultiThreads), s, desc);
+}
+
 cudaError_t launch_chunks(const Desc *desc, const uint32_t *members, int n_group,
                           uint64_t *chunk_base, uint32_t *head, uint32_t C, cudaStream_t s) {
     return launch_pdl(k_chunks, dim3(1), dim3(1024), s, desc, members, n_group, chunk_base, head,

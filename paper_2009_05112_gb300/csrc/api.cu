@@ -200,6 +200,15 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
     if (p->n_st_axis)
         for (int i = 0; i < p->dim; ++i)
             if (p->n_st_axis[i] < 1) return fail(VP_EINVAL, "n_st_axis[%d] must be >= 1", i);
+    if (p->n_extra < 0 || p->n_extra > kMaxOut - 1)
+        return fail(VP_EINVAL, "n_extra outside 0..%d", kMaxOut - 1);
+    if (p->n_extra > 0) {
+        if (!p->out_mono) return fail(VP_EINVAL, "NULL out_mono");
+        if (p->precision != VP_FP64) return fail(VP_EINVAL, "several outputs: FP64 only");
+        for (int i = 0; i < 2 * p->n_extra; ++i)
+            if (p->out_mono[i] < -1 || p->out_mono[i] >= p->dim)
+                return fail(VP_EINVAL, "out_mono[%d] outside -1..dim-1", i);
+    }
     if (p->max_it < 0 || p->max_it > (1 << 24)) return fail(VP_EINVAL, "max_it outside 0..2^24");
     if (f->n_param < 1 || !f->param) return fail(VP_EINVAL, "empty integrand blob");
     const int D = p->dim;
@@ -241,6 +250,10 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
     mb.p.lo = mb.lo.data();  // the caller's arrays may not outlive the call
     mb.p.hi = mb.hi.data();
     mb.p.n_st_axis = nullptr;  // (kept in nst_ax)
+    mb.n_out = 1 + p->n_extra;
+    mb.mono.assign(2, -1);
+    if (p->n_extra > 0) mb.mono.insert(mb.mono.end(), p->out_mono, p->out_mono + 2 * p->n_extra);
+    mb.p.out_mono = nullptr;  // (kept in mono)
     if (p->n_st_axis)
         mb.nst_ax.assign(p->n_st_axis, p->n_st_axis + D);
     else if (p->n_st > 0)
@@ -258,6 +271,9 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
         if (nh > (1ull << 31)) return fail(VP_EINVAL, "the strata make more than 2^31 hypercubes");
     }
     mb.n_hc = nh;
+    if (mb.n_out > 1 && nh > kMultiMaxHc)
+        return fail(VP_EINVAL, "several outputs: at most %llu hypercubes",
+                    (unsigned long long)kMultiMaxHc);
     const uint64_t calls = (uint64_t)((D + 3) / 4);
     const uint64_t max_nh = (uint64_t)p->n_ev + 2 * nh + 2;
     if (max_nh * calls >= (1ull << 32))
@@ -304,10 +320,12 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
 
 size_t vp::member_layout(Member &mb, size_t base) {
     const size_t D = mb.p.dim, G = mb.p.n_g, H = mb.n_hc, T = mb.n_tree, C = mb.hist_cap;
+    const size_t M = mb.n_out > 1 ? mb.n_out : 0, MT = M * (M + 1) / 2;  // (§4 outputs)
     const size_t sz[B_COUNT] = {D * (G + 1) * 8, D * G * 8, mb.prm.size() * 8,
                                 mb.prm32.size() * 4, H * 4, (H + 1) * 8, 2 * H * 8, 2 * H * 8,
                                 H * 8, 2 * D * G * 8, 2 * D * G * 4, T * 3 * 8, T * kSub * 8, C * 8,
-                                C * 8, sizeof(State)};
+                                C * 8, sizeof(State), 2 * H * M * 8, 2 * H * MT * 8,
+                                T * (M + MT) * 8, C * M * 8, C * MT * 8};
     for (int i = 0; i < B_COUNT; ++i) {
         mb.off_bytes[i] = base;
         base = align256(base + sz[i]);
@@ -370,7 +388,13 @@ static vp_status plan_groups(Set &s) {
         // strata that differ between axes (§3.2): the one-integral kernel only
         // (the task kernel keeps one strata count in registers)
         g.uniform = true;
-        for (uint32_t i : g.members) g.uniform = g.uniform && s.m[i].uniform;
+        g.mo = false;
+        for (uint32_t i : g.members) {
+            g.uniform = g.uniform && s.m[i].uniform;
+            g.mo = g.mo || s.m[i].n_out > 1;
+        }
+        if (g.mo && !g.one)  // several outputs (§4): the FP64 one-integral kernel sums them
+            return fail(VP_EINVAL, "several outputs: one integral per context");
         if (!g.uniform && !g.one)
             return fail(VP_EINVAL, g.members.size() > 1
                                        ? "strata that differ between axes: one integral per context"
@@ -396,11 +420,11 @@ static vp_status plan_groups(Set &s) {
             }
         }
         cudaError_t e = g.prec == VP_FP64
-                            ? sample_smem_config_f64(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem_one, 48 * 1024))
+                            ? sample_smem_config_f64(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem_one, 48 * 1024), g.mo)
                             : sample_smem_config_f32(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem_one, 48 * 1024));
         if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
         g.occ_one = g.prec == VP_FP64
-                        ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, g.threads, g.smem_one)
+                        ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, g.threads, g.smem_one, g.mo)
                         : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, g.threads, g.smem_one);
         if (g.occ_one < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem_one);
         g.blocks = s.n_sm * std::min(g.occ_one, 2);  // until the autotuner has measured
@@ -410,7 +434,7 @@ static vp_status plan_groups(Set &s) {
             g.cs = 1;
             for (int cs : {2, 4, 8}) {  // (the kernel's reduction handles up to 8)
                 const int ctas = g.prec == VP_FP64
-                                     ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem_one)
+                                     ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem_one, g.mo)
                                      : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem_one);
                 if (ctas >= (int)(0.97 * g.blocks) && ctas >= cs) {
                     g.cs = cs;
@@ -505,6 +529,15 @@ void vp::fill_desc(const Member &mb, const double *d_inv, Desc &d) {
     }
     div_magic((uint32_t)mb.n_st, &d.nst_magic, &d.nst_shift);
     d.uniform = mb.uniform ? 1u : 0u;
+    d.n_out = mb.n_out;
+    for (int k = 0; k < 2 * kMaxOut; ++k) d.mono[k] = k < (int)mb.mono.size() ? mb.mono[k] : -1;
+    if (mb.n_out > 1) {
+        d.x1 = mbuf<double>(mb, B_X1);
+        d.x2 = mbuf<double>(mb, B_X2);
+        d.mpart = mbuf<double>(mb, B_MPART);
+        d.hist_im = mbuf<double>(mb, B_HIM);
+        d.hist_cm = mbuf<double>(mb, B_HCM);
+    }
     d.n_st = (uint32_t)mb.nst_ax[0];
     for (int mu = 0; mu < kMaxDim; ++mu) {
         const uint32_t s = mu < D ? (uint32_t)mb.nst_ax[mu] : 1u;
@@ -665,6 +698,10 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         L.tab = d.tab;
         L.edges = d.edges;
         a.S = d.strata;
+        a.n_out = d.n_out;
+        for (int k = 0; k < 2 * kMaxOut; ++k) a.mono[k] = d.mono[k];
+        a.x1 = d.x1;
+        a.x2 = d.x2;
         a.st = d.st;
         a.off = d.off;
         a.n_h = d.n_h;
@@ -880,7 +917,7 @@ static vp_status tune(Set &s, cudaStream_t stream) {
             for (int threads : {256, 512, 768}) {
                 if (threads > max_threads) continue;
                 const int occ = g.prec == VP_FP64
-                                    ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one)
+                                    ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one, g.mo)
                                     : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem_one);
                 for (int k = 1; k <= std::min(threads == 256 ? 3 : 1, occ); ++k) {
                     const int blocks = k * s.n_sm;
@@ -889,7 +926,7 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                         int ctas = blocks;
                         if (cs > 1) {
                             ctas = g.prec == VP_FP64
-                                       ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem_one)
+                                       ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem_one, g.mo)
                                        : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem_one);
                             ctas = std::min(ctas, blocks) / cs * cs;
                             if (ctas < (int)(0.9 * blocks)) continue;
@@ -899,7 +936,7 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                 }
             }
         }
-        if (g.uniform)
+        if (g.uniform && !g.mo)
             for (int k = 1; k <= std::min(3, g.occ_many); ++k)
                 for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r, 256});
         if (cands.size() <= 1) {
@@ -957,6 +994,11 @@ static vp_status tune(Set &s, cudaStream_t stream) {
             CU(cudaMemsetAsync(d.s2 + par * d.n_hc, 0, d.n_hc * 8, stream));
             CU(cudaMemsetAsync(d.hsum + par * bins, 0, bins * 8, stream));
             CU(cudaMemsetAsync(d.hcnt + par * bins, 0, bins * 4, stream));
+            if (d.n_out > 1) {
+                const size_t M = (size_t)d.n_out, MT = M * (M + 1) / 2;
+                CU(cudaMemsetAsync(d.x1 + par * d.n_hc * M, 0, d.n_hc * M * 8, stream));
+                CU(cudaMemsetAsync(d.x2 + par * d.n_hc * MT, 0, d.n_hc * MT * 8, stream));
+            }
         }
         CU(cudaStreamSynchronize(stream));
     }
@@ -1006,6 +1048,8 @@ static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = fals
         s.timed = true;
     }
     if (cap != cudaStreamCaptureStatusActive) ++s.iters;
+    if (s.m.size() == 1 && s.m[0].n_out > 1)  // several outputs (§4), before the counter advances
+        CU(launch_estimate_multi(s.d_desc, s.m[0].n_tree, stream));
     if (refine_too && s.any_refine) {  // the step graph: a8 beside a6 and a7
         vp_status st = fork_refine(s, stream);
         if (st != VP_OK) return st;
@@ -1100,6 +1144,122 @@ void vp::combine(const double *I, const double *V, int n, int discard, vp_result
     double c = 0.0;
     for (int j = first; j < n; ++j) c += (I[j] - r->mean) * (I[j] - r->mean) / V[j];
     r->chi2 = c;
+}
+
+// Eigen-decomposition of a symmetric M x M matrix (cyclic Jacobi rotations,
+// Golub & Van Loan, "Matrix Computations", Sec. 8.5): A = U diag(w) U^T.
+static void sym_eigen(int M, std::vector<double> A, std::vector<double> &w,
+                      std::vector<double> &U) {
+    U.assign((size_t)M * M, 0.0);
+    for (int i = 0; i < M; ++i) U[(size_t)i * M + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, all = 0.0;
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                all += A[(size_t)i * M + j] * A[(size_t)i * M + j];
+                if (i != j) off += A[(size_t)i * M + j] * A[(size_t)i * M + j];
+            }
+        if (off <= 1e-32 * all || off == 0.0) break;
+        for (int p = 0; p < M - 1; ++p)
+            for (int q = p + 1; q < M; ++q) {
+                const double apq = A[(size_t)p * M + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * M + p], aqq = A[(size_t)q * M + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double tq = (theta >= 0.0 ? 1.0 : -1.0) /
+                                  (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(tq * tq + 1.0), sn = tq * c;
+                for (int k = 0; k < M; ++k) {  // A <- A J (columns p, q)
+                    const double akp = A[(size_t)k * M + p], akq = A[(size_t)k * M + q];
+                    A[(size_t)k * M + p] = c * akp - sn * akq;
+                    A[(size_t)k * M + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < M; ++k) {  // A <- J^T A (rows p, q)
+                    const double apk = A[(size_t)p * M + k], aqk = A[(size_t)q * M + k];
+                    A[(size_t)p * M + k] = c * apk - sn * aqk;
+                    A[(size_t)q * M + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < M; ++k) {  // U <- U J
+                    const double ukp = U[(size_t)k * M + p], ukq = U[(size_t)k * M + q];
+                    U[(size_t)k * M + p] = c * ukp - sn * ukq;
+                    U[(size_t)k * M + q] = sn * ukp + c * ukq;
+                }
+            }
+    }
+    w.resize(M);
+    for (int i = 0; i < M; ++i) w[i] = A[(size_t)i * M + i];
+}
+
+// Pseudo-inverse of a symmetric matrix: eigenvalues at or below `cut` times
+// the largest magnitude are dropped.  Returns false if all are.
+static bool sym_pinv(int M, const double *A, double cut, std::vector<double> &out) {
+    std::vector<double> S((size_t)M * M), w, U;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j)
+            S[(size_t)i * M + j] = 0.5 * (A[(size_t)i * M + j] + A[(size_t)j * M + i]);
+    sym_eigen(M, S, w, U);
+    double top = 0.0;
+    for (double x : w) top = std::max(top, std::fabs(x));
+    out.assign((size_t)M * M, 0.0);
+    bool any = false;
+    for (int e = 0; e < M; ++e) {
+        if (!(top > 0.0 && w[e] > cut * top)) continue;
+        any = true;
+        const double inv = 1.0 / w[e];
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j)
+                out[(size_t)i * M + j] += U[(size_t)i * M + e] * inv * U[(size_t)j * M + e];
+    }
+    return any;
+}
+
+// §4's several integrals over iterations j >= discard: the several-variable
+// form of §2.5's weighted average (generalised least squares; the paper
+// states the one-variable form only).
+int vp::combine_multi(const double *I, const double *C, int n, int M, int discard, double *mean,
+                      double *cov, double *chi2) {
+    const int first = discard < 0 ? 0 : discard;
+    const int n_it = n > first ? n - first : 0;
+    for (int k = 0; k < M; ++k) mean[k] = NAN;
+    for (int q = 0; q < M * M; ++q) cov[q] = NAN;
+    *chi2 = NAN;
+    if (n_it == 0) return 0;
+    const double cut = 1e-12;
+    std::vector<std::vector<double>> W(n);
+    std::vector<double> Ws((size_t)M * M, 0.0), rhs(M, 0.0);
+    bool any = false;
+    for (int j = first; j < n; ++j) {
+        any |= sym_pinv(M, C + (size_t)j * M * M, cut, W[j]);
+        for (int q = 0; q < M * M; ++q) Ws[q] += W[j][q];
+        for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b) rhs[a] += W[j][(size_t)a * M + b] * I[(size_t)j * M + b];
+    }
+    if (!any) {  // zero covariances: the plain mean
+        for (int k = 0; k < M; ++k) {
+            double s = 0.0;
+            for (int j = first; j < n; ++j) s += I[(size_t)j * M + k];
+            mean[k] = s / n_it;
+        }
+        for (int q = 0; q < M * M; ++q) cov[q] = 0.0;
+        *chi2 = 0.0;
+        return n_it;
+    }
+    std::vector<double> P;
+    sym_pinv(M, Ws.data(), cut, P);
+    for (int q = 0; q < M * M; ++q) cov[q] = P[q];
+    for (int a = 0; a < M; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < M; ++b) s += P[(size_t)a * M + b] * rhs[b];
+        mean[a] = s;
+    }
+    double c2 = 0.0;
+    for (int j = first; j < n; ++j)
+        for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b)
+                c2 += (I[(size_t)j * M + a] - mean[a]) * W[j][(size_t)a * M + b] *
+                      (I[(size_t)j * M + b] - mean[b]);
+    *chi2 = c2;
+    return n_it;
 }
 
 // §2.5, last paragraph: with the map frozen (alpha = 0) after the first
@@ -1258,6 +1418,77 @@ extern "C" vp_status vp_get_strata(vp_ctx *c, int32_t *strata) {
     if (!strata) return fail(VP_EINVAL, "NULL out");
     const Member &mb = c->set.m[0];
     for (int mu = 0; mu < mb.p.dim; ++mu) strata[mu] = (int32_t)mb.nst_ax[mu];
+    return VP_OK;
+}
+
+static vp_status latest_parity(Set &s, size_t *par);
+
+// The several-outputs history of a set's member 0 (§4): i_j[n][M], cov_j[n][M][M].
+static vp_status multi_history(Set &s, int n, std::vector<double> &I, std::vector<double> &C) {
+    const Desc &d = s.h_desc[0];
+    const int M = d.n_out, T = M * (M + 1) / 2;
+    std::vector<double> tri((size_t)n * T);
+    I.assign((size_t)n * M, 0.0);
+    C.assign((size_t)n * M * M, 0.0);
+    if (n) {
+        CU(cudaMemcpy(I.data(), d.hist_im, (size_t)n * M * 8, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(tri.data(), d.hist_cm, (size_t)n * T * 8, cudaMemcpyDeviceToHost));
+    }
+    for (int j = 0; j < n; ++j) {
+        int q = 0;
+        for (int k = 0; k < M; ++k)
+            for (int l = k; l < M; ++l, ++q)
+                C[((size_t)j * M + k) * M + l] = C[((size_t)j * M + l) * M + k] =
+                    tri[(size_t)j * T + q];
+    }
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_history_multi(vp_ctx *c, int n, double *i_j, double *cov_j) {
+    CHECK_CTX(c);
+    const Desc &d = c->set.h_desc[0];
+    if (d.n_out < 2) return fail(VP_EINVAL, "the context has no extra outputs");
+    if (n < 0 || n > d.hist_cap) return fail(VP_EINVAL, "n outside the history capacity");
+    CU(cudaStreamSynchronize(c->set.last));
+    std::vector<double> I, C;
+    vp_status st = multi_history(c->set, n, I, C);
+    if (st != VP_OK) return st;
+    if (i_j) std::copy(I.begin(), I.end(), i_j);
+    if (cov_j) std::copy(C.begin(), C.end(), cov_j);
+    return VP_OK;
+}
+
+extern "C" vp_status vp_result_multi(vp_ctx *c, int discard, double *mean, double *cov,
+                                     double *chi2, int *dof, int *n_it) {
+    CHECK_CTX(c);
+    if (!mean || !cov || !chi2 || !dof) return fail(VP_EINVAL, "NULL out");
+    Set &s = c->set;
+    const Desc &d = s.h_desc[0];
+    if (d.n_out < 2) return fail(VP_EINVAL, "the context has no extra outputs");
+    CU(cudaStreamSynchronize(s.last));
+    State st;
+    CU(cudaMemcpy(&st, d.st, sizeof st, cudaMemcpyDeviceToHost));
+    const int n = (int)std::min<uint32_t>(st.t, (uint32_t)d.hist_cap);
+    std::vector<double> I, C;
+    vp_status rs = multi_history(s, n, I, C);
+    if (rs != VP_OK) return rs;
+    const int used = combine_multi(I.data(), C.data(), n, d.n_out, discard, mean, cov, chi2);
+    *dof = used > 0 ? d.n_out * (used - 1) : 0;
+    if (n_it) *n_it = used;
+    if (st.status & kStatusNonFinite) return fail(VP_ENONFINITE, "integrand produced a non-finite value");
+    return VP_OK;
+}
+
+extern "C" vp_status vp_get_moments_multi(vp_ctx *c, double *x1, double *x2) {
+    CHECK_CTX(c);
+    const Desc &d = c->set.h_desc[0];
+    if (d.n_out < 2) return fail(VP_EINVAL, "the context has no extra outputs");
+    size_t par = 0;
+    vp_status st = latest_parity(c->set, &par);
+    if (st != VP_OK) return st;
+    const size_t M = (size_t)d.n_out, T = M * (M + 1) / 2;
+    if (x1) CU(cudaMemcpy(x1, d.x1 + par * d.n_hc * M, d.n_hc * M * 8, cudaMemcpyDeviceToHost));
+    if (x2) CU(cudaMemcpy(x2, d.x2 + par * d.n_hc * T, d.n_hc * T * 8, cudaMemcpyDeviceToHost));
     return VP_OK;
 }
 
@@ -1488,6 +1719,7 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     if (scheme == 1 && cluster != 1) return fail(VP_EINVAL, "the task scheme takes no clusters");
     if (scheme == 1 && !g.uniform)
         return fail(VP_EINVAL, "strata that differ between axes: the one-integral scheme only");
+    if (scheme == 1 && g.mo) return fail(VP_EINVAL, "several outputs: the one-integral scheme only");
     if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
         return fail(VP_EINVAL, "cluster must be 1, 2, 4 or 8");
     if (cluster > 1 && !(scheme == 0 ? g.hist_one : g.hist_shared))
@@ -1496,11 +1728,11 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     if (scheme == 0) {
         // the static split assumes every CTA resident at once
         const int occ = g.prec == VP_FP64
-                            ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one)
+                            ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one, g.mo)
                             : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem_one);
         const int res = cluster > 1
                             ? (g.prec == VP_FP64
-                                   ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem_one)
+                                   ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem_one, g.mo)
                                    : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem_one))
                             : occ * c->set.n_sm;
         if (blocks > res)

@@ -17,6 +17,7 @@ namespace vp {
 cudaError_t launch_chunks(const Desc *, const uint32_t *, int, uint64_t *, uint32_t *, uint32_t,
                           cudaStream_t);
 cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
+cudaError_t launch_estimate_multi(const Desc *, uint32_t, cudaStream_t);
 cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t, int initial);
 cudaError_t launch_refine(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
 
@@ -54,13 +55,15 @@ struct Member {
     int64_t n_st;                 // the smallest of nst_ax
     std::vector<int64_t> nst_ax;  // strata per axis (§3.2)
     bool uniform;                 // every axis has n_st strata
+    int n_out = 1;                // outputs integrated on the same samples (§4)
+    std::vector<int32_t> mono;    // [2 n_out] factors (a, b) of g_k = x^a x^b; output 0 (-1, -1)
     uint64_t n_hc;
     uint32_t n_tree;
     int hist_cap;
     int bucket;
     bool exact;            // dim equals the bucket's dimension
     char *base = nullptr;  // device memory the offsets below are relative to
-    size_t off_bytes[20];  // offsets of the buffers from base
+    size_t off_bytes[24];  // offsets of the buffers from base
 };
 
 // One sampling launch: the integrals of one kernel instantiation.
@@ -76,6 +79,7 @@ struct Group {
     size_t smem = 0;
     bool one = false;  // a single integral: the cluster kernel with constants in parameters
     bool uniform = true;  // every member has the same strata on every axis (else: one only)
+    bool mo = false;      // several outputs (§4): the FP64 one-integral kernel that sums them
     int cs = 1;        // CTAs per cluster (one-integral kernel)
     int threads_one = 256;  // CTA size of the one-integral kernel
     // histograms of the one-integral kernel (one CTA per SM fits more shared
@@ -94,7 +98,7 @@ constexpr int kRetuneIt = 4;
 
 enum {
     B_EDGES, B_TAB, B_PRM, B_PRM32, B_NH, B_OFF, B_S1, B_S2, B_DH, B_HSUM, B_HCNT, B_PART,
-    B_BSUM, B_HI, B_HV, B_ST, B_COUNT
+    B_BSUM, B_HI, B_HV, B_ST, B_X1, B_X2, B_MPART, B_HIM, B_HCM, B_COUNT
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -127,5 +131,9 @@ vp_status launch_group(const Desc *d_desc, Group &g, cudaStream_t stream);
 void combine(const double *I, const double *V, int n, int discard, vp_result_t *r);
 // §2.5 unweighted combination (frozen map) of iterations j >= discard.
 void combine_unweighted(const double *I, const double *V, int n, int discard, vp_result_t *r);
+// Several integrals (§4) over iterations j >= discard: I[n][M], C[n][M][M];
+// mean[M], cov[M][M], chi2, dof = M (n_it - 1).  Returns the iterations used.
+int combine_multi(const double *I, const double *C, int n, int M, int discard, double *mean,
+                  double *cov, double *chi2);
 
 }  // namespace vp

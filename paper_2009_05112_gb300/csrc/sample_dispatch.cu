@@ -13,10 +13,12 @@ const void *kptr_one_f32_x(int bucket, int kind);
 const void *kptr_many_f32_x(int bucket, int kind);
 cudaError_t launch_eval_f32_x(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 const void *kptr_one_f64_g(int bucket, int kind);
+const void *kptr_one_f64_mo(int bucket, int kind);
 const void *kptr_many_f64_g(int bucket, int kind);
 cudaError_t launch_eval_f64_g(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 
-static const void *pick(bool f64, int bucket, bool exact, int kind, bool one) {
+static const void *pick(bool f64, int bucket, bool exact, int kind, bool one, bool mo = false) {
+    if (f64 && one && mo) return kptr_one_f64_mo(bucket, kind);
     if (f64) return one ? kptr_one_f64_g(bucket, kind) : kptr_many_f64_g(bucket, kind);
     if (exact) return one ? kptr_one_f32_x(bucket, kind) : kptr_many_f32_x(bucket, kind);
     return one ? kptr_one_f32_g(bucket, kind) : kptr_many_f32_g(bucket, kind);
@@ -42,7 +44,7 @@ static cudaError_t launch_many(bool f64, int bucket, bool exact, int kind, dim3 
 
 static cudaError_t launch_one(bool f64, int bucket, bool exact, int kind, dim3 grid, dim3 block,
                               size_t smem, int cs, cudaStream_t s, const SampleOne &a) {
-    const void *k = pick(f64, bucket, exact, kind, true);
+    const void *k = pick(f64, bucket, exact, kind, true, f64 && a.n_out > 1);
     if (!k) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -89,8 +91,9 @@ struct SmemLimit {
 };
 static std::vector<SmemLimit> g_smem_limit;
 
-static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool one, int max_smem) {
-    const void *k = pick(f64, bucket, exact, kind, one);
+static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool one, int max_smem,
+                               bool mo = false) {
+    const void *k = pick(f64, bucket, exact, kind, one, mo);
     if (!k) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -111,12 +114,14 @@ static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool 
 cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem) {
     return smem_config(false, bucket, exact, kind, one, max_smem);
 }
-cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem) {
-    return smem_config(true, bucket, false, kind, one, max_smem);
+cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem,
+                                   bool mo) {
+    return smem_config(true, bucket, false, kind, one, max_smem, mo);
 }
 
-static int occupancy(bool f64, int bucket, bool exact, int kind, bool one, int threads, size_t smem) {
-    const void *k = pick(f64, bucket, exact, kind, one);
+static int occupancy(bool f64, int bucket, bool exact, int kind, bool one, int threads, size_t smem,
+                     bool mo = false) {
+    const void *k = pick(f64, bucket, exact, kind, one, mo);
     int n = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
         return 0;
@@ -125,13 +130,14 @@ static int occupancy(bool f64, int bucket, bool exact, int kind, bool one, int t
 int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem) {
     return occupancy(false, bucket, exact, kind, one, threads, smem);
 }
-int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem) {
-    return occupancy(true, bucket, false, kind, one, threads, smem);
+int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
+                         bool mo) {
+    return occupancy(true, bucket, false, kind, one, threads, smem, mo);
 }
 
 static int cluster_ctas(bool f64, int bucket, bool exact, int kind, int cs, int grid, int threads,
-                        size_t smem) {
-    const void *k = pick(f64, bucket, exact, kind, true);
+                        size_t smem, bool mo = false) {
+    const void *k = pick(f64, bucket, exact, kind, true, mo);
     if (!k) return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -156,8 +162,8 @@ int sample_cluster_ctas_f32(int bucket, bool exact, int kind, int cs, int grid, 
     return cluster_ctas(false, bucket, exact, kind, cs, grid, threads, smem);
 }
 int sample_cluster_ctas_f64(int bucket, bool exact, int kind, int cs, int grid, int threads,
-                            size_t smem) {
-    return cluster_ctas(true, bucket, false, kind, cs, grid, threads, smem);
+                            size_t smem, bool mo) {
+    return cluster_ctas(true, bucket, false, kind, cs, grid, threads, smem, mo);
 }
 
 cudaError_t launch_eval_f32(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,

@@ -311,6 +311,11 @@ struct SampleOne {
     int kp_peaks;              // > 0: the peak constants are in kp (FP32 peak families)
     float kp[kParamPeaks * kParamStride];
     Strata S;                  // strata per axis (read as constants by the unrolled loops)
+    // several integrals from the same samples (§4; FP64 path): M outputs,
+    // g_k = x^a x^b with (a, b) = mono[2k], mono[2k + 1]; output 0 is f
+    int n_out;
+    int32_t mono[2 * kMaxOut];
+    double *x1, *x2;           // double-buffered bases [2][n_hc][M], [2][n_hc][M (M+1)/2]
 };
 
 // Fire-and-forget global reductions.
@@ -555,6 +560,55 @@ template <> struct Acc<false> {
     }
 };
 
+// The outputs of several integrals from the same samples (§4), summed per
+// hypercube in registers (FP64): m1[k] = sum v_k, m2[k,l] = sum v_k v_l with
+// v_k = J f g_k(x), the same IEEE sequence per sample as the oracle's
+// (v_k = (J f)(x^a x^b), products and sums unfused).  MAcc<false> is empty.
+template <bool MO> struct MAcc {
+    __device__ __forceinline__ void reset() {}
+    template <int DMAX>
+    __device__ __forceinline__ void add(const SampleOne &, const double (&)[DMAX], double) {}
+    __device__ __forceinline__ void flush(const SampleOne &, double *, double *) const {}
+};
+template <> struct MAcc<true> {
+    double m1[kMaxOut], m2[kMaxTri];  // m2 by rows of the kMaxOut triangle
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int k = 0; k < kMaxOut; ++k) m1[k] = 0.0;
+#pragma unroll
+        for (int q = 0; q < kMaxTri; ++q) m2[q] = 0.0;
+    }
+    template <int DMAX>
+    __device__ __forceinline__ void add(const SampleOne &a, const double (&x)[DMAX], double jf) {
+        const int M = a.n_out;
+        double v[kMaxOut];
+#pragma unroll
+        for (int k = 0; k < kMaxOut; ++k) {
+            v[k] = 0.0;
+            if (k < M) {
+                const int p = a.mono[2 * k], r = a.mono[2 * k + 1];
+                double xp = 1.0, xr = 1.0;  // x^p, x^r by selects (no indexed registers)
+#pragma unroll
+                for (int mu = 0; mu < DMAX; ++mu) {
+                    xp = mu == p ? x[mu] : xp;
+                    xr = mu == r ? x[mu] : xr;
+                }
+                v[k] = __dmul_rn(jf, __dmul_rn(xp, xr));
+            }
+        }
+        int q = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxOut; ++k) {
+            if (k < M) m1[k] = __dadd_rn(m1[k], v[k]);
+#pragma unroll
+            for (int l = k; l < kMaxOut; ++l, ++q)
+                if (l < M) m2[q] = __dadd_rn(m2[q], __dmul_rn(v[k], v[l]));
+        }
+    }
+    // adds the sums to hypercube h's rows p1 = X1 + h M, p2 = X2 + h M (M+1)/2
+    __device__ __forceinline__ void flush(const SampleOne &a, double *p1, double *p2) const;
+};
+
 // Integrand constants for this CTA: FP32 path copies them to shared memory
 // (read with broadcast loads in the sample loop); FP64 path reads the blob.
 __device__ __forceinline__ void load_prm32(const Desc *dp, float *sprm, int words) {
@@ -632,10 +686,27 @@ __device__ __forceinline__ uint64_t lane_find_hcube(const uint64_t *off, uint64_
     return h;
 }
 
+__device__ __forceinline__ void MAcc<true>::flush(const SampleOne &a, double *p1,
+                                                  double *p2) const {
+    const int M = a.n_out;
+    int q = 0, qm = 0;  // index in the kMaxOut triangle, in the M triangle
+#pragma unroll
+    for (int k = 0; k < kMaxOut; ++k) {
+        if (k < M && m1[k] != 0.0) red_add(p1 + k, m1[k]);
+#pragma unroll
+        for (int l = k; l < kMaxOut; ++l, ++q)
+            if (l < M) {
+                if (m2[q] != 0.0) red_add(p2 + qm, m2[q]);
+                ++qm;
+            }
+    }
+}
+
 // (HM: the histogram layout, kHist*; a template parameter so that the
 // per-axis updates carry no branch on it)
-template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, int HM, bool AX>
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, int HM, bool AX, bool MO>
 __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, const Ptrs &P,
+                                              const SampleOne *A, double *X1, double *X2,
                                               const void *prm,
                                               uint64_t s_begin, uint64_t s_end, uint64_t h,
                                               uint64_t lo_off, uint64_t next,
@@ -652,6 +723,9 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
     if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
     Acc<F64> acc;
     acc.reset();
+    MAcc<MO> macc;  // (several outputs, §4: FP64 path only)
+    macc.reset();
+    const uint64_t MM = MO ? (uint64_t)A->n_out : 0u, MT = MM * (MM + 1) / 2;
     // 32-bit counters (an iteration has fewer than 2^32 samples): samples left
     // in the run, and before the next hypercube (n_h >= 2, so at most one
     // boundary per sample)
@@ -660,6 +734,10 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
         if (to_next == 0u) {
             acc.flush(P.S1 + h, P.S2 + h, sexp);
             acc.reset();
+            if (MO) {
+                macc.flush(*A, X1 + h * MM, X2 + h * MT);
+                macc.reset();
+            }
             ++h;
             to_next = __ldg(P.nh + h);
             j = 0;
@@ -677,8 +755,13 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
         double vbig = 0.0, vbig2 = 0.0;
         if (F64) {
             double x[DMAX], J, f;
+            if (MO) {  // (the outputs' selects read every entry)
+#pragma unroll
+                for (int mu = 0; mu < DMAX; ++mu) x[mu] = 0.0;
+            }
             point64<DMAX, KIND, AX>(L, S, (const double *)prm, (uint32_t)h, j, kd, x, idx, J, f);
             v = (T)(J * f * pow2d(sexp));
+            if (MO) macc.template add<DMAX>(*A, x, __dmul_rn(J, f));
         } else {
             float x[DMAX], Jm, f;
             int Je;
@@ -740,23 +823,26 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
         ++j;
     }
     acc.flush(P.S1 + h, P.S2 + h, sexp);
+    if (MO) macc.flush(*A, X1 + h * MM, X2 + h * MT);
 }
 
-template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, bool AX>
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, bool AX, bool MO = false>
 __device__ __forceinline__ void run_samples(const Loop &L, const Strata *S, const Ptrs &P,
                                             const void *prm, uint64_t s_begin, uint64_t s_end,
                                             uint64_t h, uint64_t lo_off, uint64_t next,
                                             typename Real<F64>::T *hs, float *hs_t, uint32_t *hc,
-                                            int hist_mode, int sexp) {
+                                            int hist_mode, int sexp,
+                                            const SampleOne *A = nullptr, double *X1 = nullptr,
+                                            double *X2 = nullptr) {
     if (hist_mode == kHistShared)
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistShared, AX>(
-            L, S, P, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistShared, AX, MO>(
+            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
     else if (!F64 && hist_mode == kHistCompact)
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistCompact, AX>(
-            L, S, P, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistCompact, AX, MO>(
+            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
     else
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistGlobal, AX>(
-            L, S, P, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistGlobal, AX, MO>(
+            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
 }
 
 // ---------------------------------------------------------------------------
@@ -823,7 +909,7 @@ __device__ __forceinline__ void cluster_flush(cooperative_groups::cluster_group 
     }
 }
 
-template <int DMAX, bool EXACT, bool F64, int KIND>
+template <int DMAX, bool EXACT, bool F64, int KIND, bool MO = false>
 __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
     k_sample_one(const __grid_constant__ SampleOne a) {
     typedef typename Real<F64>::T T;
@@ -850,7 +936,11 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
     pdl_wait();
 
     const uint32_t t_it = __ldcg(&a.st->t);
-    const int sexp = __ldcg(&a.st->scale_exp);
+    // the FP64 path sums J f and (J f)^2 unscaled, the oracle's IEEE sequence
+    // (where (J f)^2 leaves the normal range, as in a sharply peaked
+    // posterior's far tails, scaled squares would round differently, and the
+    // grid's compression weighs those tiny d_i by their logarithm)
+    const int sexp = F64 ? 0 : __ldcg(&a.st->scale_exp);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.st->hist_par = t_it & 1u;
     Loop L = a.L;
     L.t = t_it;
@@ -894,9 +984,10 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
             const uint64_t h =
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)  // (the strata per axis: constants of the parameter bank)
-                run_samples<DMAX, EXACT, F64, KIND, KP, true>(L, &a.S, P, prm, s0, s1, h, lo_off,
-                                                              hi_off, hs, hs_t, hc, a.hist_shared,
-                                                              sexp);
+                run_samples<DMAX, EXACT, F64, KIND, KP, true, MO>(
+                    L, &a.S, P, prm, s0, s1, h, lo_off, hi_off, hs, hs_t, hc, a.hist_shared, sexp,
+                    &a, MO ? a.x1 + par * a.n_hc * (uint64_t)a.n_out : nullptr,
+                    MO ? a.x2 + par * a.n_hc * (uint64_t)(a.n_out * (a.n_out + 1) / 2) : nullptr);
         }
     }
     __syncthreads();
@@ -965,7 +1056,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
         const uint32_t t_it = __ldcg(&st->t);
         if (threadIdx.x == 0) st->hist_par = t_it & 1u;  // every CTA of the integral writes the same
         L = make_loop(dp, t_it);
-        sexp = __ldcg(&st->scale_exp);
+        sexp = F64 ? 0 : __ldcg(&st->scale_exp);  // (FP64: unscaled, as in k_sample_one)
         bins = L.dim * L.n_g;
         P.off = (const uint64_t *)__ldg((const unsigned long long *)&dp->off);
         P.nh = (const uint32_t *)__ldg((const unsigned long long *)&dp->n_h);
@@ -1112,13 +1203,16 @@ cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, co
                             int member, int64_t n, const uint64_t *h, const uint32_t *j,
                             uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem);
-cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem);
+// (mo: the FP64 one-integral kernel with several outputs, §4)
+cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem,
+                                   bool mo = false);
 int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem);
-int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem);
+int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
+                         bool mo = false);
 // Resident CTAs of the one-integral kernel with clusters of cs CTAs (0 if it cannot run).
 int sample_cluster_ctas_f32(int bucket, bool exact, int kind, int cs, int grid, int threads,
                             size_t smem);
 int sample_cluster_ctas_f64(int bucket, bool exact, int kind, int cs, int grid, int threads,
-                            size_t smem);
+                            size_t smem, bool mo = false);
 
 }  // namespace vp

@@ -471,6 +471,7 @@ extern "C" vp_status vp_server_submit(vp_server *S, const vp_request *q, uint64_
     if (st != VP_OK) return st;
     if (!r->mb.uniform)  // served requests share task-kernel launches
         return fail(VP_EINVAL, "served requests take the same strata on every axis");
+    if (r->mb.n_out > 1) return fail(VP_EINVAL, "served requests take no extra outputs");
     if (!(q->rtol > 0.0 && std::isfinite(q->rtol))) return fail(VP_EINVAL, "rtol must be finite and > 0");
     if (q->discard < 0) return fail(VP_EINVAL, "discard must be >= 0");
     if (q->min_meas < 1) return fail(VP_EINVAL, "min_meas must be >= 1");

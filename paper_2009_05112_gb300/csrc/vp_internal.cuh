@@ -22,6 +22,11 @@ constexpr int kSubH = kTreeBlock / kSub;
 constexpr int kMaxPeaks = 64;
 constexpr int kMaxPoints = 256;
 constexpr int kInvTab = 4096;      // table of 1/n for small integers n
+// several integrals from the same samples (§4): at most kMaxOut outputs, the
+// upper triangle of their covariance kMaxTri entries, at most 2^22 hypercubes
+constexpr int kMaxOut = 8;
+constexpr int kMaxTri = kMaxOut * (kMaxOut + 1) / 2;
+constexpr uint64_t kMultiMaxHc = 1ull << 22;
 
 // Status bits (State::status).
 constexpr uint32_t kStatusNonFinite = 1u;
@@ -33,6 +38,7 @@ struct State {
     int32_t scale_exp;    // the sampling kernel accumulates v = J f 2^scale_exp
     uint32_t done_est;    // last-block counter of the estimate kernel
     uint32_t done_alloc;  // last-block counter of the allocation kernel
+    uint32_t done_multi;  // last-block counter of the several-outputs estimate (§4)
     uint32_t status;      // kStatus* bits
     uint32_t hist_par;    // histogram buffer of the latest sampling pass (read by the refinement)
     double sum_d;         // sum_h d_h in the fixed order (set by the estimate kernel)
@@ -109,6 +115,16 @@ struct Desc {
     int32_t discard, min_meas, stop_it, pad1;
     uint32_t *done_out;        // the server's flag for this request's slot
     Strata strata;
+    // several integrals from the same samples (§4), n_out = M >= 2 outputs
+    // (1: the integrand alone).  Output k is J f g_k(x), g_k = x^a x^b for
+    // (a, b) = mono[2k], mono[2k+1] (< 0: that factor is 1); output 0 is f.
+    int32_t n_out;
+    int32_t mono[2 * kMaxOut];
+    double *x1;        // [2][n_hc][M] per-hypercube sums of the outputs (double-buffered)
+    double *x2;        // [2][n_hc][M (M+1)/2] sums of their products, upper triangle by rows
+    double *mpart;     // [n_tree][M + M (M+1)/2] block partial sums
+    double *hist_im;   // [hist_cap][M] I_j of every output
+    double *hist_cm;   // [hist_cap][M (M+1)/2] covariance of the I_j, upper triangle
 };
 
 // ---------------------------------------------------------------------------

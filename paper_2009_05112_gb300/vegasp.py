@@ -39,7 +39,8 @@ class vp_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("integral_id", ctypes.c_uint32),
                 ("precision", ctypes.c_int), ("plus2", ctypes.c_int), ("n_st", ctypes.c_int),
                 ("max_it", ctypes.c_int), ("n_st_axis", ctypes.POINTER(ctypes.c_int32)),
-                ("mixed", ctypes.c_int)]
+                ("mixed", ctypes.c_int), ("n_extra", ctypes.c_int),
+                ("out_mono", ctypes.POINTER(ctypes.c_int32))]
 
 
 class vp_integrand(ctypes.Structure):
@@ -94,6 +95,10 @@ _SIGS = {
     "vp_get_info": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                     ctypes.POINTER(ctypes.c_int)],
     "vp_get_strata": [_P, _P],
+    "vp_get_history_multi": [_P, ctypes.c_int, _P, _P],
+    "vp_result_multi": [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "vp_get_moments_multi": [_P, _P, _P],
     "vp_get_edges": [_P, _P],
     "vp_set_edges": [_P, _P],
     "vp_get_alloc": [_P, _P, _P],
@@ -204,7 +209,7 @@ class Integrator:
 
     def __init__(self, dim, lo, hi, kind, prm, n_g=1000, n_ev=10_000, alpha=0.5, beta=0.75,
                  seed=0, integral_id=0, precision=VP_FP64, plus2=False, n_st=0, max_it=0,
-                 stream=None, n_st_axis=None, mixed=False):
+                 stream=None, n_st_axis=None, mixed=False, out_mono=None):
         self.dim, self.n_g = int(dim), int(n_g)
         self._lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.dim,)))
         self._hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (self.dim,)))
@@ -218,6 +223,12 @@ class Integrator:
             self._nst = np.ascontiguousarray(n_st_axis, np.int32).reshape(self.dim)
             p.n_st_axis = self._nst.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         p.mixed = int(bool(mixed))
+        self.n_out = 1
+        if out_mono:  # extra outputs f x^a x^b (§4)
+            self._mono = np.ascontiguousarray(np.asarray(out_mono, np.int32).reshape(-1))
+            p.n_extra = self._mono.size // 2
+            p.out_mono = self._mono.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            self.n_out = 1 + p.n_extra
         f = vp_integrand(int(kind), self._prm.size, self._prm.ctypes.data_as(_dp))
         self.stream = current_stream() if stream is None else ctypes.c_void_p(stream)
         h = ctypes.c_void_p()
@@ -290,6 +301,31 @@ class Integrator:
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
         check(lib().vp_get_info(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def history_multi(self, n=None):
+        """I_j[n][M] and cov_j[n][M][M] of the outputs (§4)."""
+        n = self.info()[2] if n is None else int(n)
+        I = np.zeros((n, self.n_out))
+        C = np.zeros((n, self.n_out, self.n_out))
+        check(lib().vp_get_history_multi(self.ctx, n, _ptr(I), _ptr(C)))
+        return I, C
+
+    def result_multi(self, discard=0):
+        """The outputs combined over iterations j >= discard (§4, §2.5)."""
+        M = self.n_out
+        mean, cov = np.zeros(M), np.zeros((M, M))
+        chi2, dof, n_it = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+        check(lib().vp_result_multi(self.ctx, int(discard), _ptr(mean), _ptr(cov),
+                                    ctypes.byref(chi2), ctypes.byref(dof), ctypes.byref(n_it)))
+        return dict(mean=mean, cov=cov, chi2=chi2.value, dof=dof.value, n_it=n_it.value)
+
+    def moments_multi(self):
+        """The latest iteration's per-hypercube sums X1[N_h][M], X2[N_h][M(M+1)/2]."""
+        M = self.n_out
+        x1 = np.zeros((self.n_hc, M))
+        x2 = np.zeros((self.n_hc, M * (M + 1) // 2))
+        check(lib().vp_get_moments_multi(self.ctx, _ptr(x1), _ptr(x2)))
+        return x1, x2
 
     def strata(self):
         """Strata on every axis (§3.2)."""
