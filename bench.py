@@ -42,12 +42,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["four_peaks_d8", "ball_d20", "batch_mix", "serve"],
+    ap.add_argument("--workload", choices=["four_peaks_d8", "ball_d20", "exp_origin_d16",
+                                           "bayes_d3", "batch_mix", "serve"],
                     default="four_peaks_d8",
                     help="four_peaks_d8 (default): the single-integral step; ball_d20: the same "
-                         "step on the 20-D ball (N_ev = 1e7); batch_mix: 512 integrals per launch "
-                         "against one at a time; serve: continuous batching of a Poisson request "
-                         "stream")
+                         "step on the 20-D ball (N_ev = 1e7); exp_origin_d16: exp(-50|x|) in 16-D "
+                         "with the mixed stratification (N_ev = 2.5e5, 2^15 hypercubes); "
+                         "bayes_d3: the 3-D posterior with the eight outputs of the Bayesian "
+                         "example (means and second moments, FP64, N_ev = 1e5); batch_mix: 512 "
+                         "integrals per launch against one at a time; serve: continuous batching "
+                         "of a Poisson request stream")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     ap.add_argument("--launch", default=None,
                     help="fix the sampling launch shape instead of autotuning it: "
@@ -63,17 +67,38 @@ def flops_per_sample(dim, n_peaks):
     return 4 * dim + n_peaks * (3 * dim + 2) + 10
 
 
-def ops_per_sample(dim, n_peaks, ball=False):
+def ops_per_sample(dim, n_peaks, ball=False, expnorm=False):
     """Algorithmic lane operations per sample of the fused kernel (each one
     issue slot of one lane): Philox4x32-10 6 per round (the high and low words
     of two 32x32 products, two key XORs) x 10 rounds x ceil(D/4) calls; the map
     7 per axis (uniform from the bits, y N_g, floor, fraction, table load, x, J);
     the Gaussian integrand 2D + 3 per peak (difference and multiply-add per
-    axis, scale, exp2, accumulate), the ball 2D + 2 (compare, select); the
-    moments 10 (J f, v^2, two compensated adds of 4); the histograms 2 atomic
-    adds per axis."""
-    f = n_peaks * (2 * dim + (2 if ball else 3))
+    axis, scale, exp2, accumulate), the exponential 2D + 4 (the square root
+    besides), the ball 2D + 2 (compare, select); the moments 10 (J f, v^2, two
+    compensated adds of 4); the histograms 2 atomic adds per axis."""
+    f = n_peaks * (2 * dim + (2 if ball else (4 if expnorm else 3)))
     return 60 * ((dim + 3) // 4) + 7 * dim + f + 10 + 2 * dim
+
+
+def fp64_ops_per_sample(dim, n_pts, n_par, n_out):
+    """Algorithmic FP64 operations per sample of the FP64 kernel on the
+    posterior with n_out outputs, counted from the source with every add,
+    multiply, division, conversion, floor and library call (exp, log, sqrt)
+    as one operation: the map 14 per axis (uniform from the bits 3, y 2,
+    y N_g 1, floor 1, fraction 2, increment width 1, x 2, J 2); the
+    posterior 27 per point (the model 2 per coefficient, the residual and its
+    square, the narrow and wide Gaussians with their normalisations, their
+    sum, its log and the running sum) plus the prior 5 per coefficient and 3;
+    the moments 5; the histograms 2 per axis; the outputs 3M + 2 M(M+1)/2
+    (g_k, v_k, the sums and the products).  Library calls take many FP64
+    instructions, so the fraction of the FP64 peak is a lower bound."""
+    T = n_out * (n_out + 1) // 2
+    post = n_pts * (2 * n_par + 23) + 5 * n_par + 3
+    outs = (3 * n_out + 2 * T) if n_out > 1 else 0
+    return 14 * dim + post + 5 + 2 * dim + outs
+
+
+BAYES_OUTPUTS = [(0, -1), (1, -1), (2, -1), (0, 0), (0, 1), (1, 1), (2, 2)]
 
 
 def ball_flops_per_sample(dim):
@@ -182,13 +207,14 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def cpu_baseline(prob, seconds=12.0):
+def cpu_baseline(prob, seconds=12.0, out_mono=None):
     """The FP64 CPU oracle, as it stands, on this host: whole iterations of the
     same workload until ~seconds of CPU time; one thread."""
     import oracle
     o = oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
                          alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind,
-                         prm=prob.prm)
+                         prm=prob.prm, n_st_axis=prob.n_st_axis, mixed=prob.mixed,
+                         out_mono=out_mono)
     evals, t0, its = 0, time.perf_counter(), 0
     while True:
         n = int(o.offsets[-1])
@@ -242,13 +268,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _integral(g, prob, ball):
+def _integral(g, prob, ball, late_half=False):
     """The combined estimate: all iterations, or for the ball (whose first
-    iterations may see no sample inside it, i.e. exact zeros) the last 10."""
-    if ball:
+    iterations may see no sample inside it, i.e. exact zeros) the last 10, or
+    (late_half: a peak the first iterations miss, with errors they
+    underestimate, §3.2) the second half of them."""
+    if ball or late_half:
         n_it = g.info()[2]  # (N_st, N_h, iterations done)
-        r = g.result(discard=max(0, n_it - 10))
-        return {"mean": r["mean"], "sdev": r["sdev"], "iterations": "last 10"}
+        keep = n_it // 2 if late_half else 10
+        r = g.result(discard=max(0, n_it - keep))
+        return {"mean": r["mean"], "sdev": r["sdev"], "iterations": "last %d" % keep}
     r = g.result()
     return {"mean": r["mean"], "sdev": r["sdev"]}
 
@@ -287,11 +316,22 @@ def run_ours(args):
     _build.build()
     vegasp.use_torch_allocator()
     ball = args.workload == "ball_d20"
-    prob = inputs.ball_d20() if ball else inputs.four_peaks_d8()
-    n_peaks = 1 if ball else 4
+    expo = args.workload == "exp_origin_d16"
+    bayes = args.workload == "bayes_d3"
+    if ball:
+        prob = inputs.ball_d20()
+    elif expo:
+        prob = inputs.exp_origin(dim=16)
+    elif bayes:
+        prob = inputs.posterior(dim=3, n_ev=100_000, n_g=1000)
+    else:
+        prob = inputs.four_peaks_d8()
+    n_peaks = 4 if args.workload == "four_peaks_d8" else 1
+    out_mono = BAYES_OUTPUTS if bayes else None
+    precision = vegasp.VP_FP64 if bayes else vegasp.VP_FP32
     prob = rank_problem(prob, rank)
     stream = torch.cuda.current_stream()
-    g = vegasp.Integrator.from_problem(prob, precision=vegasp.VP_FP32)
+    g = vegasp.Integrator.from_problem(prob, precision=precision, out_mono=out_mono)
     launch = None
     if args.launch:
         sch, blk, thr, cl, run = args.launch.split(":")
@@ -338,7 +378,7 @@ def run_ours(args):
     # parameters (H2D), steps, and the host read of every step's estimate (D2H)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g2 = vegasp.Integrator.from_problem(prob, precision=vegasp.VP_FP32)
+    g2 = vegasp.Integrator.from_problem(prob, precision=precision, out_mono=out_mono)
     if launch:
         g2.set_tuning(*launch)
     for _ in range(args.steps):
@@ -367,36 +407,62 @@ def run_ours(args):
     fp32_peak = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     samples_per_step = evals / args.steps
     k1_avg_ms = sum(k1_ms) / len(k1_ms)
-    ops = ops_per_sample(prob.dim, n_peaks, ball)
-    flops = ball_flops_per_sample(prob.dim) if ball else flops_per_sample(prob.dim, n_peaks)
-    k1_tops = ops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
-    k1_tflops = flops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
-    traffic = None if ball else traffic_from_profile(kernel_source_hash())
-    roof = {"bound": "alu", "achieved": k1_tops, "peak": issue_peak, "unit": "Tops/s",
-            "frac": k1_tops / issue_peak,
-            "traffic": traffic * samples_per_step / PROFILED_SAMPLES if traffic else None,
-            "kernel": "k_sample (fused a1-a5)", "kernel_ms": k1_avg_ms,
-            "kernel_ms_note": "CUDA events around the sampling launch, mean of %d eager "
-                              "iterations after the timed steps" % KERNEL_TIMING_ITERS,
-            "kernel_share_of_step": k1_avg_ms / (total_ms / args.steps),
-            "ops_per_sample": ops,
-            "peak_note": "issue slots = SMs x 4 schedulers x 32 lanes x %.0f MHz (max SM "
-                         "clock); algorithmic lane operations counted from the kernel "
-                         "source" % max_mhz,
-            "fp32": {"achieved_tflops": k1_tflops, "peak_tflops": fp32_peak,
-                     "frac": k1_tflops / fp32_peak,
-                     "flops_per_sample": flops},
-            "ncu": None if ball else traffic_from_profile(kernel_source_hash(), "fma_alu_issue")}
-    if clocks.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = k1_tops / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    main = args.workload == "four_peaks_d8"
+    timing_note = ("CUDA events around the sampling launch, mean of %d eager iterations after "
+                   "the timed steps" % KERNEL_TIMING_ITERS)
+    if bayes:
+        # FP64 path: bound by the FP64 pipe; peak from the nominal 1.25 TFLOP/s
+        # (an FMA counted as 2 flops), i.e. 0.625e12 FP64 lane instructions/s
+        n_pts, n_par = int(prob.prm[0]), int(prob.prm[1])
+        ops = fp64_ops_per_sample(prob.dim, n_pts, n_par, 1 + len(out_mono))
+        fp64_peak = 1.25 / 2
+        k1_tops = ops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
+        roof = {"bound": "fp64", "achieved": k1_tops, "peak": fp64_peak, "unit": "Tops/s",
+                "frac": k1_tops / fp64_peak, "traffic": None,
+                "kernel": "k_sample (fused a1-a5, FP64, 8 outputs)", "kernel_ms": k1_avg_ms,
+                "kernel_ms_note": timing_note,
+                "kernel_share_of_step": k1_avg_ms / (total_ms / args.steps),
+                "ops_per_sample": ops,
+                "peak_note": "FP64 lane instructions per second from the nominal 1.25 TFLOP/s "
+                             "(fallback figure; FMA = 2 flops); library calls counted as one "
+                             "operation each, so frac is a lower bound"}
+    else:
+        ops = ops_per_sample(prob.dim, n_peaks, ball, expnorm=expo)
+        flops = (ball_flops_per_sample(prob.dim) if ball else
+                 flops_per_sample(prob.dim, n_peaks) + (n_peaks if expo else 0))
+        k1_tops = ops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
+        k1_tflops = flops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
+        traffic = traffic_from_profile(kernel_source_hash()) if main else None
+        roof = {"bound": "alu", "achieved": k1_tops, "peak": issue_peak, "unit": "Tops/s",
+                "frac": k1_tops / issue_peak,
+                "traffic": traffic * samples_per_step / PROFILED_SAMPLES if traffic else None,
+                "kernel": "k_sample (fused a1-a5)", "kernel_ms": k1_avg_ms,
+                "kernel_ms_note": timing_note,
+                "kernel_share_of_step": k1_avg_ms / (total_ms / args.steps),
+                "ops_per_sample": ops,
+                "peak_note": "issue slots = SMs x 4 schedulers x 32 lanes x %.0f MHz (max SM "
+                             "clock); algorithmic lane operations counted from the kernel "
+                             "source" % max_mhz,
+                "fp32": {"achieved_tflops": k1_tflops, "peak_tflops": fp32_peak,
+                         "frac": k1_tflops / fp32_peak,
+                         "flops_per_sample": flops},
+                "ncu": traffic_from_profile(kernel_source_hash(), "fma_alu_issue") if main
+                else None}
+        if clocks.get("sm_mhz"):
+            roof["frac_at_measured_clock"] = k1_tops / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    integrand = ("ball" if ball else "exp(-50|x|), mixed strata %s" % list(g.strata()) if expo
+                 else "App. B posterior (50 points), outputs f, f p1, f p2, f w, f p1^2, "
+                      "f p1 p2, f p2^2, f w^2" if bayes else "gaussian peaks")
+    prec_note = ("fp64 map, integrand, moments and outputs" if bayes else
+                 "fp32 map/integrand, Kahan fp32 moments, fp64 estimate")
     line = {"metric": "integrand evals/s", "value": value, "unit": "integrand evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, MIN_WARMUP),
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": prob.name, "dim": prob.dim, "n_ev": prob.n_ev,
+            "vs_baseline": None, "dtype": "f64" if bayes else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "dim": prob.dim, "n_ev": prob.n_ev,
                        "n_g": prob.n_g, "alpha": prob.alpha, "beta": prob.beta,
-                       "peaks": n_peaks, "integrand": "ball" if ball else "gaussian peaks",
-                       "precision": "fp32 map/integrand, Kahan fp32 moments, fp64 estimate",
+                       "peaks": n_peaks, "integrand": integrand, "n_hc": g.n_hc,
+                       "precision": prec_note,
                        "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": "one integral per GPU" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_evals / e2e_s, "unit": "integrand evals/s",
@@ -404,12 +470,16 @@ def run_ours(args):
                     "note": "create from host parameters + %d steps + a host read of the "
                             "estimate after every step, wall clock" % args.steps},
             "roofline": roof, "clocks": clocks,
-            # sample, estimate, alloc, offsets, refine (+ the task prefix for the task kernel)
-            "gpu_launches": (5 + (g.tuning()["scheme"] == "tasks")) * args.steps,
+            # sample, estimate, alloc, offsets, refine (+ the task prefix for the task
+            # kernel, + the several-outputs estimate)
+            "gpu_launches": (5 + (g.tuning()["scheme"] == "tasks") + bayes) * args.steps,
             "sample_launch": g.tuning(),
-            "integral": dict(_integral(g, prob, ball), exact=prob.exact)}
+            "integral": dict(_integral(g, prob, ball, late_half=expo), exact=prob.exact)}
+    if bayes:
+        r = g.result_multi()
+        line["integral"]["means (p1, p2, w)"] = [float(v) for v in r["mean"][1:4] / r["mean"][0]]
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob)
+        line["cpu_baseline"] = cpu_baseline(prob, out_mono=out_mono)
     print(json.dumps(line), flush=True)
     g.close()
     if world > 1:
