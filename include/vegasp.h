@@ -112,7 +112,7 @@ typedef struct {
                            rule, N_st + 1 strata on the first d axes and N_st on
                            the rest, N_st from Eq. Nst_vegasp and d the largest
                            with 4 (N_st + 1)^d N_st^(D - d) <= N_ev; 0 = uniform */
-    /* Several integrals from the same samples (§4): besides f itself (output
+    /* Several integrals from the same samples (App. B): besides f itself (output
        0, which alone drives the adaptation), n_extra outputs f(x) x^a x^b,
        (a, b) = out_mono[2k], out_mono[2k + 1] for k < n_extra, each in
        -1..D-1 (-1: that factor is 1): the means and second moments of the
@@ -199,7 +199,7 @@ const char *vp_last_error(void);
 vp_status vp_get_info(vp_ctx *ctx, int64_t *n_st, int64_t *n_hc, int *n_it);
 /* strata[D]: the strata on every axis (§3.2) */
 vp_status vp_get_strata(vp_ctx *ctx, int32_t *strata);
-/* Several integrals (§4), M = n_extra + 1 outputs.  vp_get_history_multi:
+/* Several integrals (App. B), M = n_extra + 1 outputs.  vp_get_history_multi:
  * i_j[n][M] and cov_j[n][M][M] of the first n iterations.  vp_result_multi:
  * their combination over iterations j >= discard, the several-variable form
  * of §2.5's weighted average -- with W_j the pseudo-inverse of cov_j

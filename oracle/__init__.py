@@ -167,7 +167,7 @@ def estimate(omega, s1, s2, n_h):
 
 
 def estimate_multi(omega, x1, x2, n_h):
-    """§4's several integrals from one set of samples: I[k] and the covariance
+    """App. B's several integrals from one set of samples: I[k] and the covariance
     C[k][l] summed over hypercubes (§2.1 Eq. sigest in several variables, §3
     Eq. sumI).  x1 is [N_h][M], x2 [N_h][M (M + 1) / 2] (upper triangle by
     rows).  Pinned by numpy's sample covariance of the per-sample values, by
@@ -325,7 +325,7 @@ class VegasPlus:
     axis), n_st_axis (explicit strata per axis, §3.2) and mixed (§3.2's
     N_st / N_st + 1 rule in place of Eq. Nst_vegasp); out_mono lists extra
     outputs f x^a x^b as pairs (a, b) (-1: no factor) integrated on the same
-    samples (§4), output 0 being f, which alone drives the adaptation.
+    samples (App. B), output 0 being f, which alone drives the adaptation.
     """
 
     def __init__(self, dim, lo, hi, n_g, n_ev, alpha, beta, seed, kind, prm,
@@ -380,7 +380,7 @@ class VegasPlus:
         assert rc == 0
 
     def sample_multi(self):
-        """X1_h[k], X2_h[k,l] of the current iteration's samples (§4)."""
+        """X1_h[k], X2_h[k,l] of the current iteration's samples (App. B)."""
         M = self.n_out
         self.x1 = np.zeros((self.n_hc, M))
         self.x2 = np.zeros((self.n_hc, M * (M + 1) // 2))

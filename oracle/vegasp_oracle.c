@@ -272,7 +272,7 @@ int or_sample_iteration(int dim, int n_g, const int64_t *nst_ax, uint64_t seed,
 }
 
 /* ------------------------------------------------------------------------ */
-/* §4 (several integrals from the same samples): outputs k = 0 .. M-1 with     */
+/* App. B (several integrals from the same samples): outputs k = 0 .. M-1  */
 /* v_k = J f g_k(x), g_k(x) = x^a x^b for the pair (a, b) = mono[2k], mono[2k+1] */
 /* (a or b < 0: that factor is 1; output 0 is f itself, mono = (-1, -1)).      */
 /* Per hypercube, in sample order:                                             */
@@ -315,7 +315,7 @@ int or_sample_multi(int dim, int n_g, const int64_t *nst_ax, uint64_t seed, uint
     return 0;
 }
 
-/* §4 with §2.1 Eq. (sigest) in its several-variable form, per hypercube, and */
+/* App. B with §2.1 Eq. (sigest) in its several-variable form, per hypercube, and */
 /* §3 Eq. (sumI) over hypercubes:                                            */
 /*   I[k]     = sum_h Omega X1_h[k] / n_h                                    */
 /*   C[k][l]  = sum_h Omega^2 (X2_h[k,l]/n_h - (X1_h[k]/n_h)(X1_h[l]/n_h))   */

@@ -696,7 +696,7 @@ static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaSt
 }
 
 // ---------------------------------------------------------------------------
-// Several integrals from the same samples (§4): the iteration's estimates of
+// Several integrals from the same samples (App. B): the iteration's estimates of
 // every output and their covariance, summed over hypercubes (§2.1 Eq. sigest
 // in several variables, §3 Eq. sumI):
 //   I[k]    = sum_h Omega X1_h[k] / n_h

@@ -320,7 +320,7 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
 
 size_t vp::member_layout(Member &mb, size_t base) {
     const size_t D = mb.p.dim, G = mb.p.n_g, H = mb.n_hc, T = mb.n_tree, C = mb.hist_cap;
-    const size_t M = mb.n_out > 1 ? mb.n_out : 0, MT = M * (M + 1) / 2;  // (§4 outputs)
+    const size_t M = mb.n_out > 1 ? mb.n_out : 0, MT = M * (M + 1) / 2;  // (App. B outputs)
     const size_t sz[B_COUNT] = {D * (G + 1) * 8, D * G * 8, mb.prm.size() * 8,
                                 mb.prm32.size() * 4, H * 4, (H + 1) * 8, 2 * H * 8, 2 * H * 8,
                                 H * 8, 2 * D * G * 8, 2 * D * G * 4, T * 3 * 8, T * kSub * 8, C * 8,
@@ -393,7 +393,7 @@ static vp_status plan_groups(Set &s) {
             g.uniform = g.uniform && s.m[i].uniform;
             g.mo = g.mo || s.m[i].n_out > 1;
         }
-        if (g.mo && !g.one)  // several outputs (§4): the FP64 one-integral kernel sums them
+        if (g.mo && !g.one)  // several outputs (App. B): the FP64 one-integral kernel sums them
             return fail(VP_EINVAL, "several outputs: one integral per context");
         if (!g.uniform && !g.one)
             return fail(VP_EINVAL, g.members.size() > 1
@@ -1048,7 +1048,7 @@ static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = fals
         s.timed = true;
     }
     if (cap != cudaStreamCaptureStatusActive) ++s.iters;
-    if (s.m.size() == 1 && s.m[0].n_out > 1)  // several outputs (§4), before the counter advances
+    if (s.m.size() == 1 && s.m[0].n_out > 1)  // several outputs (App. B), before the counter advances
         CU(launch_estimate_multi(s.d_desc, s.m[0].n_tree, stream));
     if (refine_too && s.any_refine) {  // the step graph: a8 beside a6 and a7
         vp_status st = fork_refine(s, stream);
@@ -1213,7 +1213,7 @@ static bool sym_pinv(int M, const double *A, double cut, std::vector<double> &ou
     return any;
 }
 
-// §4's several integrals over iterations j >= discard: the several-variable
+// App. B's several integrals over iterations j >= discard: the several-variable
 // form of §2.5's weighted average (generalised least squares; the paper
 // states the one-variable form only).
 int vp::combine_multi(const double *I, const double *C, int n, int M, int discard, double *mean,
@@ -1423,7 +1423,7 @@ extern "C" vp_status vp_get_strata(vp_ctx *c, int32_t *strata) {
 
 static vp_status latest_parity(Set &s, size_t *par);
 
-// The several-outputs history of a set's member 0 (§4): i_j[n][M], cov_j[n][M][M].
+// The several-outputs history of a set's member 0 (App. B): i_j[n][M], cov_j[n][M][M].
 static vp_status multi_history(Set &s, int n, std::vector<double> &I, std::vector<double> &C) {
     const Desc &d = s.h_desc[0];
     const int M = d.n_out, T = M * (M + 1) / 2;

@@ -55,7 +55,7 @@ struct Member {
     int64_t n_st;                 // the smallest of nst_ax
     std::vector<int64_t> nst_ax;  // strata per axis (§3.2)
     bool uniform;                 // every axis has n_st strata
-    int n_out = 1;                // outputs integrated on the same samples (§4)
+    int n_out = 1;                // outputs integrated on the same samples (App. B)
     std::vector<int32_t> mono;    // [2 n_out] factors (a, b) of g_k = x^a x^b; output 0 (-1, -1)
     uint64_t n_hc;
     uint32_t n_tree;
@@ -79,7 +79,7 @@ struct Group {
     size_t smem = 0;
     bool one = false;  // a single integral: the cluster kernel with constants in parameters
     bool uniform = true;  // every member has the same strata on every axis (else: one only)
-    bool mo = false;      // several outputs (§4): the FP64 one-integral kernel that sums them
+    bool mo = false;      // several outputs (App. B): the FP64 one-integral kernel that sums them
     int cs = 1;        // CTAs per cluster (one-integral kernel)
     int threads_one = 256;  // CTA size of the one-integral kernel
     // histograms of the one-integral kernel (one CTA per SM fits more shared
@@ -131,7 +131,7 @@ vp_status launch_group(const Desc *d_desc, Group &g, cudaStream_t stream);
 void combine(const double *I, const double *V, int n, int discard, vp_result_t *r);
 // §2.5 unweighted combination (frozen map) of iterations j >= discard.
 void combine_unweighted(const double *I, const double *V, int n, int discard, vp_result_t *r);
-// Several integrals (§4) over iterations j >= discard: I[n][M], C[n][M][M];
+// Several integrals (App. B) over iterations j >= discard: I[n][M], C[n][M][M];
 // mean[M], cov[M][M], chi2, dof = M (n_it - 1).  Returns the iterations used.
 int combine_multi(const double *I, const double *C, int n, int M, int discard, double *mean,
                   double *cov, double *chi2);

@@ -1,5 +1,5 @@
 // sample_f64_mo.cu -- instantiations of the one-integral kernel, FP64 path,
-// with several outputs summed per hypercube (§4: several integrals from the
+// with several outputs summed per hypercube (App. B: several integrals from the
 // same samples).
 #include "sample_impl.cuh"
 

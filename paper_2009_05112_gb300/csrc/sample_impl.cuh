@@ -311,7 +311,7 @@ struct SampleOne {
     int kp_peaks;              // > 0: the peak constants are in kp (FP32 peak families)
     float kp[kParamPeaks * kParamStride];
     Strata S;                  // strata per axis (read as constants by the unrolled loops)
-    // several integrals from the same samples (§4; FP64 path): M outputs,
+    // several integrals from the same samples (App. B; FP64 path): M outputs,
     // g_k = x^a x^b with (a, b) = mono[2k], mono[2k + 1]; output 0 is f
     int n_out;
     int32_t mono[2 * kMaxOut];
@@ -560,7 +560,7 @@ template <> struct Acc<false> {
     }
 };
 
-// The outputs of several integrals from the same samples (§4), summed per
+// The outputs of several integrals from the same samples (App. B), summed per
 // hypercube in registers (FP64): m1[k] = sum v_k, m2[k,l] = sum v_k v_l with
 // v_k = J f g_k(x), the same IEEE sequence per sample as the oracle's
 // (v_k = (J f)(x^a x^b), products and sums unfused).  MAcc<false> is empty.
@@ -723,7 +723,7 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
     if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
     Acc<F64> acc;
     acc.reset();
-    MAcc<MO> macc;  // (several outputs, §4: FP64 path only)
+    MAcc<MO> macc;  // (several outputs, App. B: FP64 path only)
     macc.reset();
     const uint64_t MM = MO ? (uint64_t)A->n_out : 0u, MT = MM * (MM + 1) / 2;
     // 32-bit counters (an iteration has fewer than 2^32 samples): samples left
@@ -1203,7 +1203,7 @@ cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, co
                             int member, int64_t n, const uint64_t *h, const uint32_t *j,
                             uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem);
-// (mo: the FP64 one-integral kernel with several outputs, §4)
+// (mo: the FP64 one-integral kernel with several outputs, App. B)
 cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem,
                                    bool mo = false);
 int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem);

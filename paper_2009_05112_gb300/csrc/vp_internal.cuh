@@ -22,7 +22,7 @@ constexpr int kSubH = kTreeBlock / kSub;
 constexpr int kMaxPeaks = 64;
 constexpr int kMaxPoints = 256;
 constexpr int kInvTab = 4096;      // table of 1/n for small integers n
-// several integrals from the same samples (§4): at most kMaxOut outputs, the
+// several integrals from the same samples (App. B): at most kMaxOut outputs, the
 // upper triangle of their covariance kMaxTri entries, at most 2^22 hypercubes
 constexpr int kMaxOut = 8;
 constexpr int kMaxTri = kMaxOut * (kMaxOut + 1) / 2;
@@ -38,7 +38,7 @@ struct State {
     int32_t scale_exp;    // the sampling kernel accumulates v = J f 2^scale_exp
     uint32_t done_est;    // last-block counter of the estimate kernel
     uint32_t done_alloc;  // last-block counter of the allocation kernel
-    uint32_t done_multi;  // last-block counter of the several-outputs estimate (§4)
+    uint32_t done_multi;  // last-block counter of the several-outputs estimate (App. B)
     uint32_t status;      // kStatus* bits
     uint32_t hist_par;    // histogram buffer of the latest sampling pass (read by the refinement)
     double sum_d;         // sum_h d_h in the fixed order (set by the estimate kernel)
@@ -115,7 +115,7 @@ struct Desc {
     int32_t discard, min_meas, stop_it, pad1;
     uint32_t *done_out;        // the server's flag for this request's slot
     Strata strata;
-    // several integrals from the same samples (§4), n_out = M >= 2 outputs
+    // several integrals from the same samples (App. B), n_out = M >= 2 outputs
     // (1: the integrand alone).  Output k is J f g_k(x), g_k = x^a x^b for
     // (a, b) = mono[2k], mono[2k+1] (< 0: that factor is 1); output 0 is f.
     int32_t n_out;

@@ -224,7 +224,7 @@ class Integrator:
             p.n_st_axis = self._nst.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         p.mixed = int(bool(mixed))
         self.n_out = 1
-        if out_mono:  # extra outputs f x^a x^b (§4)
+        if out_mono:  # extra outputs f x^a x^b (App. B)
             self._mono = np.ascontiguousarray(np.asarray(out_mono, np.int32).reshape(-1))
             p.n_extra = self._mono.size // 2
             p.out_mono = self._mono.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
@@ -303,7 +303,7 @@ class Integrator:
         return a.value, b.value, c.value
 
     def history_multi(self, n=None):
-        """I_j[n][M] and cov_j[n][M][M] of the outputs (§4)."""
+        """I_j[n][M] and cov_j[n][M][M] of the outputs (App. B)."""
         n = self.info()[2] if n is None else int(n)
         I = np.zeros((n, self.n_out))
         C = np.zeros((n, self.n_out, self.n_out))
@@ -311,7 +311,7 @@ class Integrator:
         return I, C
 
     def result_multi(self, discard=0):
-        """The outputs combined over iterations j >= discard (§4, §2.5)."""
+        """The outputs combined over iterations j >= discard (App. B, §2.5)."""
         M = self.n_out
         mean, cov = np.zeros(M), np.zeros((M, M))
         chi2, dof, n_it = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()

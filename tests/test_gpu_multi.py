@@ -1,4 +1,4 @@
-"""Several integrals from the same samples (§4), CUDA path against the FP64
+"""Several integrals from the same samples (App. B), CUDA path against the FP64
 oracle (through the C-ABI).
 
 Bars: n_h bit-exact; per-hypercube sums X1, X2 within 1e-12; every output's

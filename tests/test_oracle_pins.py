@@ -639,7 +639,7 @@ def test_mixed_stratification_eq_mixed_d16():
 
 
 # ---------------------------------------------------------------------------
-# §4: several integrals from the same samples, with their covariance
+# App. B: several integrals from the same samples, with their covariance
 # ---------------------------------------------------------------------------
 def _gauss2(c, w):
     return inputs.gauss_blob([1.0], [w], [np.asarray(c, float)])
@@ -700,7 +700,7 @@ def test_multi_gaussian_moments_and_ratio_errors():
     of its value from 1-D quadratures (the integrand factorises), the ratios
     <x0> = I_1/I_0 and <x0^2> - <x0>^2 within 4 sigma when their errors are
     propagated with the covariance, and those errors several times smaller
-    than when the correlations are ignored (over 1.5 times here; §4 reports
+    than when the correlations are ignored (over 1.5 times here; App. B reports
     2.5-12 times for its example)."""
     c, w = (0.4, 0.6), 0.3
     a, b = _moments_1d(c[0], w), _moments_1d(c[1], w)
