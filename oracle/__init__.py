@@ -96,6 +96,12 @@ def lib():
                                          _f64p]
         L.or_smooth_compress.restype = ctypes.c_int
         L.or_regrid.argtypes = [ctypes.c_int, _f64p, _f64p, _f64p]
+        L.or_inverse_map.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p, _i32p, _f64p,
+                                     ctypes.POINTER(ctypes.c_double)]
+        L.or_inverse_map.restype = None
+        L.or_precondition_hist.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, ctypes.c_int64,
+                                           _f64p, _f64p, _f64p, _f64p]
+        L.or_precondition_hist.restype = None
         L.or_regrid.restype = None
         _lib = L
     return _lib
@@ -244,6 +250,33 @@ def regrid(edges, d):
     out = np.zeros_like(edges)
     lib().or_regrid(edges.size - 1, edges, np.ascontiguousarray(d, np.float64), out)
     return out
+
+
+def inverse_map(edges, x):
+    """§4.2's y(x), the inverse of the map of Eq. (y): increment indices, y and
+    J(y(x)).  Pinned by round trips through the forward map."""
+    edges = np.ascontiguousarray(edges, np.float64)
+    dim, n_g = edges.shape[0], edges.shape[1] - 1
+    idx = np.zeros(dim, np.int32)
+    y = np.zeros(dim)
+    jac = ctypes.c_double()
+    lib().or_inverse_map(dim, n_g, edges, np.ascontiguousarray(x, np.float64), idx, y,
+                         ctypes.byref(jac))
+    return idx, y, jac.value
+
+
+def precondition_hist(edges, x, f):
+    """§4.2: the data histogram, sums of J^2(y(x)) f^2(x) and counts per
+    increment over the sample data.  Pinned by hand-built one-point cases and
+    a constant integrand."""
+    edges = np.ascontiguousarray(edges, np.float64)
+    dim, n_g = edges.shape[0], edges.shape[1] - 1
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, dim)
+    hs = np.zeros((dim, n_g))
+    hc = np.zeros((dim, n_g))
+    lib().or_precondition_hist(dim, n_g, edges, x.shape[0], x,
+                               np.ascontiguousarray(f, np.float64), hs, hc)
+    return hs, hc
 
 
 def combine(I, var, discard=0):
@@ -413,6 +446,21 @@ class VegasPlus:
         for m in range(self.dim):
             new[m] = refine_axis(self.edges[m], self.hsum[m], self.hcnt[m], self.alpha)
         self.edges = new
+
+    def precondition(self, x, f=None, n_iter=10):
+        """§4.2: trains the map on sample data {x, f(x)} (f evaluated from the
+        integrand when not given), n_iter refinements of every axis (§2.3)
+        from the data histogram, the same data each time."""
+        x = np.ascontiguousarray(x, np.float64).reshape(-1, self.dim)
+        if f is None:
+            f = integrand_many(self.kind, self.dim, self.prm, x)
+        for _ in range(int(n_iter)):
+            hs, hc = precondition_hist(self.edges, x, f)
+            new = np.empty_like(self.edges)
+            for m in range(self.dim):
+                new[m] = refine_axis(self.edges[m], hs[m], hc[m], self.alpha)
+            self.edges = new
+        return self
 
     def eval_sample(self, t, h, j):
         """x, increment indices, J and f of sample j in hypercube h at iteration t."""

@@ -534,6 +534,59 @@ void or_regrid(int n_g, const double *x, const double *d, double *x_new) {
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* §4.2 (preconditioned integrators): the map trained on sample data          */
+/* {x, f(x)} given before integrating.  The inverse map y(x): on axis mu, the */
+/* increment i with x_i <= x < x_{i+1} (the last increment also takes x = b), */
+/* y = (i + (x - x_i) / dx_i) / N_g; J(y(x)) is Eq. (jac) there, the product  */
+/* over axes of N_g dx_i.  The data histogram is that of §2.3/§2.4 with the   */
+/* sum over the data in place of the sum over samples:                        */
+/*   hsum[mu][i] += J^2 f^2 = (J f)^2,  hcnt[mu][i] += 1                       */
+/* (overwrites hsum, hcnt; x [n][dim] inside the box).                        */
+/* ------------------------------------------------------------------------ */
+static int or_increment(int n_g, const double *e, double x) {
+    int lo = 0, hi = n_g; /* e[lo] <= x < e[hi], or x = e[n_g] */
+    if (x >= e[n_g]) return n_g - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (e[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+void or_inverse_map(int dim, int n_g, const double *edges, const double *x, int *idx,
+                    double *y, double *jac) {
+    double J = 1.0;
+    for (int mu = 0; mu < dim; ++mu) {
+        const double *e = edges + (size_t)mu * (size_t)(n_g + 1);
+        const int i = or_increment(n_g, e, x[mu]);
+        const double dx = e[i + 1] - e[i];
+        idx[mu] = i;
+        y[mu] = ((double)i + (x[mu] - e[i]) / dx) / (double)n_g;
+        J *= (double)n_g * dx;
+    }
+    *jac = J;
+}
+
+void or_precondition_hist(int dim, int n_g, const double *edges, int64_t n, const double *x,
+                          const double *f, double *hsum, double *hcnt) {
+    int idx[64];
+    double y[64];
+    memset(hsum, 0, sizeof(double) * (size_t)dim * (size_t)n_g);
+    memset(hcnt, 0, sizeof(double) * (size_t)dim * (size_t)n_g);
+    if (dim > 64) return;
+    for (int64_t p = 0; p < n; ++p) {
+        double jac;
+        or_inverse_map(dim, n_g, edges, x + (size_t)p * dim, idx, y, &jac);
+        const double jf = jac * f[p];
+        for (int mu = 0; mu < dim; ++mu) {
+            hsum[(size_t)mu * n_g + idx[mu]] += jf * jf;
+            hcnt[(size_t)mu * n_g + idx[mu]] += 1.0;
+        }
+    }
+}
+
 /* The whole refinement of one axis.  alpha = 0 means no refinement (§2.3);   */
 /* N_g = 1 or all-zero d_i leave the grid unchanged (reading).  work holds     */
 /* 2 N_g doubles.                                                             */

@@ -148,6 +148,42 @@ def three_exp_d8(n_ev=1_000_000, n_it=30, discard=10, n_g=1000, seed=0, beta=0.7
                    discard=discard, alpha=alpha, beta=beta)
 
 
+def three_sharp_peaks_d8(n_ev=100_000, n_it=8, n_g=1000, seed=0):
+    """§4.2: exp(-1e4 (x - r_i)^2) summed over the three peaks of Eq.
+    (random-diag), in 8-D (Gaussians of width w = 0.01 in this library's
+    form exp(-|x - c|^2 / w^2))."""
+    dim = 8
+    cs = [np.full(dim, c) for c in (0.23, 0.39, 0.74)]
+    amps, ws = [1.0] * 3, [0.01] * 3
+    return Problem("three_sharp_peaks_d8", dim, GAUSS, gauss_blob(amps, ws, cs), np.zeros(dim),
+                   np.ones(dim), n_g=n_g, n_ev=n_ev, seed=seed, n_it=n_it,
+                   exact=gauss_exact(amps, ws, cs))
+
+
+def peak_samples(prob, n=3000, widen=1.0, seed=0):
+    """§4.2's sample data: n points of density proportional to a Gaussian-peak
+    integrand (widen = 1) or to Gaussians `widen` times wider: a peak chosen
+    with probability a_k w_k^D / sum, then x ~ N(c_k, (widen w_k)^2 / 2) per
+    axis, redrawn until inside the box.  Points only: each side evaluates f."""
+    assert prob.kind == GAUSS
+    rng = np.random.default_rng(seed)
+    K = int(prob.prm[0])
+    rows = prob.prm[1:].reshape(K, 2 + prob.dim)
+    a, w, c = rows[:, 0], rows[:, 1], rows[:, 2:]
+    p = a * w ** prob.dim
+    p = p / p.sum()
+    lo, hi = np.asarray(prob.lo, float), np.asarray(prob.hi, float)
+    out = np.empty((n, prob.dim))
+    for k in range(n):
+        i = rng.choice(K, p=p)
+        while True:
+            x = rng.normal(c[i], widen * w[i] / math.sqrt(2.0))
+            if np.all(x >= lo) and np.all(x <= hi):
+                break
+        out[k] = x
+    return out
+
+
 def exp_origin(dim=16, n_ev=250_000, n_it=50, n_g=1000, seed=0, mixed=True):
     """§3.2 Eq. (mixed): exp(-50 |x|) on [0,1]^D, a sharp peak at a corner of
     the box, with the paper's alpha = 0.1, beta = 0.75 (set to zero for the

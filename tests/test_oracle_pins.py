@@ -785,3 +785,77 @@ def test_combine_multi_worked_examples():
     np.testing.assert_allclose(r["mean"], [float(v) for v in mean], rtol=1e-14)
     np.testing.assert_allclose(r["cov"], [[float(v) for v in row] for row in cov], rtol=1e-13)
     assert r["chi2"] == pytest.approx(float(chi2), rel=1e-12) and r["dof"] == 2
+
+
+# ---------------------------------------------------------------------------
+# §4.2: the map trained on sample data {x, f(x)}
+# ---------------------------------------------------------------------------
+def test_inverse_map_round_trips():
+    """y(x(y)) = y, with x(y) from numpy's piecewise-linear interp of the points
+    (i/N_g, x_i) (Eq. y), the increment the one holding x, and J(y(x)) the
+    forward map's Jacobian at the same sample (bit for bit where the increment
+    agrees)."""
+    rng = np.random.default_rng(8)
+    dim, n_g = 3, 13
+    prob = oracle.VegasPlus(dim=dim, lo=[-1.0, 0.0, 2.0], hi=[1.0, 5.0, 2.5], n_g=n_g, n_ev=400,
+                            alpha=0.5, beta=0.75, seed=5, kind=0,
+                            prm=inputs.gauss_blob([1.0], [0.3], [np.zeros(dim)]))
+    for m in range(dim):
+        lo, hi = prob.edges[m][0], prob.edges[m][-1]
+        prob.edges[m][1:-1] = np.sort(rng.uniform(lo, hi, n_g - 1))
+    grid = np.arange(n_g + 1) / n_g
+    for _ in range(200):
+        y = rng.uniform(0, 1, dim)
+        x = np.array([np.interp(y[m], grid, prob.edges[m]) for m in range(dim)])
+        idx, y2, jac = oracle.inverse_map(prob.edges, x)
+        assert np.all(np.abs(y2 - y) < 1e-13)
+        for m in range(dim):
+            assert prob.edges[m][idx[m]] <= x[m] <= prob.edges[m][idx[m] + 1]
+    for h, j in [(0, 0), (3, 1), (prob.n_hc - 1, 2)]:
+        x, idx, jac, f = prob.eval_sample(1, h, j)
+        idx2, _, jac2 = oracle.inverse_map(prob.edges, x)
+        if np.array_equal(idx, idx2):
+            assert jac2 == jac
+    # the ends of the box
+    idx, y2, _ = oracle.inverse_map(prob.edges, [-1.0, 5.0, 2.0])
+    assert list(idx) == [0, n_g - 1, 0] and list(y2) == [0.0, 1.0, 0.0]
+
+
+def test_precondition_hist_hand_values():
+    """One point per increment by hand: hsum = (J f)^2 with J = prod N_g dx, and
+    a constant f on a uniform unit grid gives d_i = f^2 wherever data falls."""
+    e = np.array([[0.0, 0.1, 0.5, 1.0], [2.0, 2.5, 3.0, 4.0]])
+    hs, hc = oracle.precondition_hist(e, [[0.3, 4.0], [0.05, 2.0]], [2.0, 1.0])
+    J1, J2 = (3 * 0.4) * (3 * 1.0), (3 * 0.1) * (3 * 0.5)
+    np.testing.assert_allclose(hs, [[J2 ** 2, (2 * J1) ** 2, 0.0], [J2 ** 2, 0.0, (2 * J1) ** 2]],
+                               rtol=1e-15)
+    assert np.array_equal(hc, [[1, 1, 0], [1, 0, 1]])
+    rng = np.random.default_rng(2)
+    e = np.tile(np.linspace(0.0, 1.0, 9), (2, 1))
+    x = rng.uniform(0, 1, (500, 2))
+    hs, hc = oracle.precondition_hist(e, x, np.full(500, 3.0))
+    occupied = hc > 0
+    np.testing.assert_allclose(hs[occupied] / hc[occupied], 9.0, rtol=1e-12)
+    assert np.all(hc.sum(axis=1) == 500)
+
+
+def test_preconditioned_three_sharp_peaks():
+    """§4.2's example: exp(-1e4 (x - r_i)^2) at the three Eq. (random-diag)
+    points in 8-D, the map trained 10 times on 3000 points drawn from the
+    integrand's density (and from Gaussians twice as wide, which the paper says
+    work about as well), then 8 iterations at alpha = 0 with N_ev = 1e5 (where
+    the paper says good results start): within 5% of the closed form, while
+    18 unpreconditioned iterations of the same size find one of the three
+    equal peaks (about -2/3), as the paper reports."""
+    prob = inputs.three_sharp_peaks_d8(n_ev=100_000, seed=1)
+    args = dict(dim=8, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev, alpha=0.5,
+                beta=0.75, seed=prob.seed, kind=prob.kind, prm=prob.prm)
+    for widen in (1.0, 2.0):
+        xs = inputs.peak_samples(prob, 3000, widen=widen, seed=1)
+        o = oracle.VegasPlus(**args).precondition(xs, n_iter=10)
+        o.alpha = 0.0
+        o.run(8)
+        assert abs(o.result()["mean"] / prob.exact - 1.0) < 0.05, widen
+    o = oracle.VegasPlus(**args).run(18)
+    err = o.result(discard=10)["mean"] / prob.exact - 1.0
+    assert -0.7 < err < -0.6
