@@ -214,6 +214,20 @@ vp_status vp_get_history_multi(vp_ctx *ctx, int n, double *i_j, double *cov_j);
 vp_status vp_result_multi(vp_ctx *ctx, int discard, double *mean, double *cov, double *chi2,
                           int *dof, int *n_it);
 vp_status vp_get_moments_multi(vp_ctx *ctx, double *x1, double *x2);
+
+/* §4.2 (preconditioned integrators): trains the vegas map on sample data
+ * {x, f(x)} given before integrating.  n_iter times: every axis's histogram
+ * over the data of J^2(y(x)) f^2(x) per increment, y(x) the inverse of the
+ * current map (§4.2's d_i^mu, the sum over the data and n_i^mu the data points
+ * in the increment), then the refinement of §2.3 with the context's alpha
+ * (alpha = 0 changes nothing); the same data every time.  x[n][D] (host,
+ * copied; every point inside the box, else VP_EINVAL), f[n] (host, copied;
+ * finite) or NULL: the context's integrand evaluated at x in FP64.  The
+ * allocation, the iteration history and the Philox counters are untouched;
+ * setting alpha to 0 with vp_set_damping afterwards keeps the trained map
+ * (§4.2).  Synchronises `stream`. */
+vp_status vp_precondition(vp_ctx *ctx, int64_t n, const double *x, const double *f, int n_iter,
+                          void *stream);
 /* edges[D][N_g + 1] (FP64 master grid) */
 vp_status vp_get_edges(vp_ctx *ctx, double *edges);
 /* replaces the grid (edges[D][N_g+1], strictly increasing, ends = box) */

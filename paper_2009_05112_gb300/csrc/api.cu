@@ -1629,6 +1629,57 @@ extern "C" vp_status vp_refine_from_hist(vp_ctx *c, const double *hsum, const do
     return VP_OK;
 }
 
+extern "C" vp_status vp_precondition(vp_ctx *c, int64_t n, const double *x, const double *f,
+                                     int n_iter, void *stream) {
+    CHECK_CTX(c);
+    Set &s = c->set;
+    const Member &mb = s.m[0];
+    const Desc &d = s.h_desc[0];
+    const int D = mb.p.dim;
+    if (n < 1 || !x) return fail(VP_EINVAL, "need at least one data point");
+    if (n_iter < 0) return fail(VP_EINVAL, "n_iter must be >= 0");
+    for (int64_t p = 0; p < n; ++p) {
+        for (int mu = 0; mu < D; ++mu) {
+            const double v = x[p * D + mu];
+            if (!(v >= mb.lo[mu] && v <= mb.hi[mu]))
+                return fail(VP_EINVAL, "data point %lld outside the box on axis %d", (long long)p, mu);
+        }
+        if (f && !std::isfinite(f[p])) return fail(VP_EINVAL, "non-finite f at data point %lld", (long long)p);
+    }
+    if (n_iter == 0) return VP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t par = 0;  // the previous iteration's histogram buffer: the next estimate clears it
+    vp_status pst = latest_parity(s, &par);
+    if (pst != VP_OK) return pst;
+    const size_t bins = (size_t)D * d.n_g;
+    DevMem tmp;
+    const size_t xb = align256((size_t)n * D * 8);
+    vp_status ast = dev_alloc(tmp, xb + (f ? (size_t)n * 8 : 0), st);
+    if (ast != VP_OK) return ast;
+    double *dx = (double *)tmp.ptr;
+    double *df = f ? (double *)((char *)tmp.ptr + xb) : nullptr;
+    const uint32_t par32 = (uint32_t)par;
+    cudaError_t e = cudaMemcpyAsync(dx, x, (size_t)n * D * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && f) e = cudaMemcpyAsync(df, f, (size_t)n * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char *)d.st + offsetof(State, hist_par), &par32, 4,
+                            cudaMemcpyHostToDevice, st);
+    for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
+        e = cudaMemsetAsync(d.hsum + par * bins, 0, bins * 8, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.hcnt + par * bins, 0, bins * 4, st);
+        if (e == cudaSuccess)
+            e = launch_precondition(mb.bucket, mb.kind, st, s.d_desc, 0, n, dx, df, par32);
+        if (e == cudaSuccess)
+            e = launch_refine(s.d_desc, s.d_axis_base, 1, s.n_axis_total, s.max_ng, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(tmp, st);
+    cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(VP_ECUDA, "vp_precondition: %s", cudaGetErrorString(e));
+    s.last = st;
+    return VP_OK;
+}
+
 extern "C" vp_status vp_eval_samples(vp_ctx *c, int64_t n, const uint64_t *h, const uint32_t *j,
                                      uint32_t t, double *x, int32_t *idx, double *jac, double *f) {
     CHECK_CTX(c);

@@ -1181,6 +1181,67 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
     }
 }
 
+// §4.2 (preconditioned integrators): the data histogram of the map's training
+// on sample data {x, f(x)}.  Per data point (one thread each): on every axis
+// the increment i holding x (x_i <= x < x_{i+1}, the last one also taking
+// x = b), i.e. the inverse map y(x); J(y(x)) = prod N_g dx_i; f from the data
+// or from the integrand (FP64); then (J f)^2 and a count added to increment i
+// of every axis, in histogram buffer `buf` (the oracle's IEEE sequence).
+template <int DMAX, int KIND>
+__global__ void __launch_bounds__(256) k_precondition(const Desc *desc, int member, int64_t n,
+                                                      const double *xs, const double *fs,
+                                                      uint32_t buf) {
+    const Desc *dp = desc + member;
+    const int dim = __ldg(&dp->dim), n_g = __ldg(&dp->n_g), K = __ldg(&dp->n_peaks);
+    const double *edges = (const double *)__ldg((const unsigned long long *)&dp->edges);
+    const double *prm = (const double *)__ldg((const unsigned long long *)&dp->prm);
+    const size_t bins = (size_t)dim * n_g;
+    double *HS = (double *)__ldg((const unsigned long long *)&dp->hsum) + buf * bins;
+    uint32_t *HC = (uint32_t *)__ldg((const unsigned long long *)&dp->hcnt) + buf * bins;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double x[DMAX];
+        int idx[DMAX];
+        double J = 1.0;
+#pragma unroll
+        for (int mu = 0; mu < DMAX; ++mu) {
+            x[mu] = 0.0;
+            idx[mu] = 0;
+            if (mu < dim) {
+                const double xv = __ldg(xs + p * dim + mu);
+                const double *e = edges + (size_t)mu * (size_t)(n_g + 1);
+                int lo = 0, hi = n_g;  // e[lo] <= x < e[hi]
+                if (xv >= __ldg(e + n_g)) {
+                    lo = n_g - 1;
+                } else {
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (__ldg(e + mid) <= xv) lo = mid;
+                        else hi = mid;
+                    }
+                }
+                const double dx = __dsub_rn(__ldg(e + lo + 1), __ldg(e + lo));
+                J = __dmul_rn(J, __dmul_rn((double)n_g, dx));
+                x[mu] = xv;
+                idx[mu] = lo;
+            }
+        }
+        double f;
+        if (fs) f = __ldg(fs + p);
+        else if (KIND == VP_POSTERIOR) f = f_post64<DMAX>(prm, dim, x);
+        else f = f_peaks64<DMAX>(KIND, prm + 1, K, dim, x);
+        const double jf = __dmul_rn(J, f);
+        const double w = __dmul_rn(jf, jf);
+#pragma unroll
+        for (int mu = 0; mu < DMAX; ++mu) {
+            if (mu < dim) {
+                if (w != 0.0) red_add(HS + (size_t)mu * n_g + idx[mu], w);
+                red_add(HC + (size_t)mu * n_g + idx[mu], 1u);
+            }
+        }
+    }
+}
+
 // Launch dispatch (one translation unit per precision instantiates these).
 // bucket b serves D <= kBucketDim[b]; exact: D == kBucketDim[b] (no dimension guards)
 constexpr int kNumBuckets = 6;
@@ -1203,6 +1264,9 @@ cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, co
                             int member, int64_t n, const uint64_t *h, const uint32_t *j,
                             uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem);
+// §4.2: the data histogram of the map's training (buffer buf; f NULL: the integrand).
+cudaError_t launch_precondition(int bucket, int kind, cudaStream_t s, const Desc *desc, int member,
+                                int64_t n, const double *x, const double *f, uint32_t buf);
 // (mo: the FP64 one-integral kernel with several outputs, App. B)
 cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem,
                                    bool mo = false);

@@ -99,6 +99,7 @@ _SIGS = {
     "vp_result_multi": [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "vp_get_moments_multi": [_P, _P, _P],
+    "vp_precondition": [_P, ctypes.c_int64, _P, _P, ctypes.c_int, _P],
     "vp_get_edges": [_P, _P],
     "vp_set_edges": [_P, _P],
     "vp_get_alloc": [_P, _P, _P],
@@ -326,6 +327,15 @@ class Integrator:
         x2 = np.zeros((self.n_hc, M * (M + 1) // 2))
         check(lib().vp_get_moments_multi(self.ctx, _ptr(x1), _ptr(x2)))
         return x1, x2
+
+    def precondition(self, x, f=None, n_iter=10):
+        """§4.2: trains the map on sample data {x, f(x)} (f None: the
+        integrand), n_iter refinements on the same data."""
+        x = np.ascontiguousarray(x, np.float64).reshape(-1, self.dim)
+        fa = None if f is None else np.ascontiguousarray(f, np.float64).reshape(-1)
+        check(lib().vp_precondition(self.ctx, x.shape[0], _ptr(x), _ptr(fa), int(n_iter),
+                                    self.stream))
+        return self
 
     def strata(self):
         """Strata on every axis (§3.2)."""
