@@ -43,13 +43,15 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["four_peaks_d8", "ball_d20", "exp_origin_d16",
-                                           "bayes_d3", "batch_mix", "serve"],
+                                           "bayes_d3", "precond_d8", "batch_mix", "serve"],
                     default="four_peaks_d8",
                     help="four_peaks_d8 (default): the single-integral step; ball_d20: the same "
                          "step on the 20-D ball (N_ev = 1e7); exp_origin_d16: exp(-50|x|) in 16-D "
                          "with the mixed stratification (N_ev = 2.5e5, 2^15 hypercubes); "
                          "bayes_d3: the 3-D posterior with the eight outputs of the Bayesian "
-                         "example (means and second moments, FP64, N_ev = 1e5); batch_mix: 512 "
+                         "example (means and second moments, FP64, N_ev = 1e5); precond_d8: "
+                         "three sharp 8-D peaks with the map trained on 3000 sample points, "
+                         "then frozen (N_ev = 1e6); batch_mix: 512 "
                          "integrals per launch against one at a time; serve: continuous batching "
                          "of a Poisson request stream")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
@@ -207,14 +209,18 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def cpu_baseline(prob, seconds=12.0, out_mono=None):
+def cpu_baseline(prob, seconds=12.0, out_mono=None, data=None):
     """The FP64 CPU oracle, as it stands, on this host: whole iterations of the
-    same workload until ~seconds of CPU time; one thread."""
+    same workload until ~seconds of CPU time; one thread.  data: sample points
+    the map is first trained on (untimed), the map then frozen."""
     import oracle
     o = oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
                          alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind,
                          prm=prob.prm, n_st_axis=prob.n_st_axis, mixed=prob.mixed,
                          out_mono=out_mono)
+    if data is not None:
+        o.precondition(data, n_iter=10)
+        o.alpha = 0.0
     evals, t0, its = 0, time.perf_counter(), 0
     while True:
         n = int(o.offsets[-1])
@@ -318,20 +324,34 @@ def run_ours(args):
     ball = args.workload == "ball_d20"
     expo = args.workload == "exp_origin_d16"
     bayes = args.workload == "bayes_d3"
+    precond = args.workload == "precond_d8"
     if ball:
         prob = inputs.ball_d20()
     elif expo:
         prob = inputs.exp_origin(dim=16)
     elif bayes:
         prob = inputs.posterior(dim=3, n_ev=100_000, n_g=1000)
+    elif precond:
+        prob = inputs.three_sharp_peaks_d8(n_ev=1_000_000)
     else:
         prob = inputs.four_peaks_d8()
-    n_peaks = 4 if args.workload == "four_peaks_d8" else 1
+    n_peaks = 4 if args.workload == "four_peaks_d8" else (3 if precond else 1)
     out_mono = BAYES_OUTPUTS if bayes else None
     precision = vegasp.VP_FP64 if bayes else vegasp.VP_FP32
     prob = rank_problem(prob, rank)
     stream = torch.cuda.current_stream()
     g = vegasp.Integrator.from_problem(prob, precision=precision, out_mono=out_mono)
+    training = None
+    data = None
+    if precond:  # §4.2: the map trained on 3000 points, then frozen
+        data = inputs.peak_samples(prob, 3000, seed=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.precondition(data, n_iter=10)
+        training = {"points": 3000, "passes": 10,
+                    "ms": 1e3 * (time.perf_counter() - t0),
+                    "note": "vp_precondition wall clock (host copies of the data included)"}
+        g.set_damping(0.0, prob.beta)
     launch = None
     if args.launch:
         sch, blk, thr, cl, run = args.launch.split(":")
@@ -379,6 +399,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g2 = vegasp.Integrator.from_problem(prob, precision=precision, out_mono=out_mono)
+    if precond:
+        g2.precondition(data, n_iter=10)
+        g2.set_damping(0.0, prob.beta)
     if launch:
         g2.set_tuning(*launch)
     for _ in range(args.steps):
@@ -450,7 +473,11 @@ def run_ours(args):
                 else None}
         if clocks.get("sm_mhz"):
             roof["frac_at_measured_clock"] = k1_tops / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    if precond:
+        h2d += data.size * 8
     integrand = ("ball" if ball else "exp(-50|x|), mixed strata %s" % list(g.strata()) if expo
+                 else "three exp(-1e4 (x - r_i)^2) peaks, map trained on 3000 points then frozen"
+                 if precond
                  else "App. B posterior (50 points), outputs f, f p1, f p2, f w, f p1^2, "
                       "f p1 p2, f p2^2, f w^2" if bayes else "gaussian peaks")
     prec_note = ("fp64 map, integrand, moments and outputs" if bayes else
@@ -478,8 +505,10 @@ def run_ours(args):
     if bayes:
         r = g.result_multi()
         line["integral"]["means (p1, p2, w)"] = [float(v) for v in r["mean"][1:4] / r["mean"][0]]
+    if training:
+        line["training"] = training
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob, out_mono=out_mono)
+        line["cpu_baseline"] = cpu_baseline(prob, out_mono=out_mono, data=data)
     print(json.dumps(line), flush=True)
     g.close()
     if world > 1:
