@@ -62,7 +62,7 @@ def lib():
         L.or_sample_iteration.argtypes = [ctypes.c_int, ctypes.c_int, _i64p,
                                           ctypes.c_uint64, ctypes.c_uint32, _f64p, ctypes.c_int,
                                           _f64p, ctypes.c_uint32, _u32p, _f64p, _f64p, _f64p,
-                                          _f64p]
+                                          _f64p, ctypes.c_int]
         L.or_sample_iteration.restype = ctypes.c_int
         L.or_hcube_moments.argtypes = [ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_uint64,
                                        ctypes.c_uint32, _f64p, ctypes.c_int, _f64p,
@@ -90,10 +90,10 @@ def lib():
                                   _u64p]
         L.or_allocate.restype = ctypes.c_int
         L.or_refine_axis.argtypes = [ctypes.c_int, _f64p, _f64p, _f64p, ctypes.c_double, _f64p,
-                                     _f64p]
+                                     _f64p, ctypes.c_int]
         L.or_refine_axis.restype = None
         L.or_smooth_compress.argtypes = [ctypes.c_int, _f64p, _f64p, ctypes.c_double, _f64p,
-                                         _f64p]
+                                         _f64p, ctypes.c_int]
         L.or_smooth_compress.restype = ctypes.c_int
         L.or_regrid.argtypes = [ctypes.c_int, _f64p, _f64p, _f64p]
         L.or_inverse_map.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p, _i32p, _f64p,
@@ -217,16 +217,18 @@ def allocate(n_ev, d, plus2=False):
     return n_h, off
 
 
-def refine_axis(edges, hsum, hcnt, alpha):
-    """§2.3 smoothing, compression and four-step re-gridding of one axis.
-    Pinned by a hand-computed 4-increment example, constant-d invariance and
-    alpha = 0."""
+def refine_axis(edges, hsum, hcnt, alpha, d_weighted=False):
+    """§2.3 smoothing, compression and four-step re-gridding of one axis
+    (d_weighted: the histogram sums are already weighted per sample, d_i =
+    hsum_i).  Pinned by a hand-computed 4-increment example, constant-d
+    invariance and alpha = 0."""
     edges = np.ascontiguousarray(edges, np.float64)
     n_g = edges.size - 1
     out = np.zeros_like(edges)
     work = np.zeros(2 * n_g, np.float64)
     lib().or_refine_axis(n_g, edges, np.ascontiguousarray(hsum, np.float64),
-                         np.ascontiguousarray(hcnt, np.float64), float(alpha), out, work)
+                         np.ascontiguousarray(hcnt, np.float64), float(alpha), out, work,
+                         int(bool(d_weighted)))
     return out
 
 
@@ -239,7 +241,7 @@ def smooth_compress(hsum, hcnt, alpha):
     out = np.zeros(n_g)
     work = np.zeros(n_g)
     rc = lib().or_smooth_compress(n_g, hsum, np.ascontiguousarray(hcnt, np.float64),
-                                  float(alpha), out, work)
+                                  float(alpha), out, work, 0)
     return None if rc else out
 
 
@@ -363,7 +365,7 @@ class VegasPlus:
 
     def __init__(self, dim, lo, hi, n_g, n_ev, alpha, beta, seed, kind, prm,
                  integral_id=0, plus2=False, n_st=0, n_st_axis=None, mixed=False,
-                 out_mono=None):
+                 out_mono=None, d_weighted=False):
         self.dim, self.n_g, self.n_ev = int(dim), int(n_g), int(n_ev)
         self.alpha, self.beta = float(alpha), float(beta)
         self.seed, self.integral_id, self.plus2 = int(seed), int(integral_id), bool(plus2)
@@ -398,6 +400,9 @@ class VegasPlus:
         self.mono = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1))
         self.n_out = len(pairs)
         self.Im, self.Cm = [], []  # per iteration: I[k], C[k][l] (n_out > 1 only)
+        # the grid's d_i: the literal mean over the increment's samples, or
+        # (d_weighted) each sample weighted by 1/n_h of its hypercube
+        self.d_weighted = bool(d_weighted)
         self.x1 = self.x2 = None
 
     def sample(self):
@@ -409,7 +414,7 @@ class VegasPlus:
         rc = lib().or_sample_iteration(self.dim, self.n_g, self.nst_ax, self.seed,
                                        self.integral_id, self.edges, self.kind, self.prm,
                                        self.t, self.n_h, self.s1, self.s2, self.hsum,
-                                       self.hcnt)
+                                       self.hcnt, int(self.d_weighted))
         assert rc == 0
 
     def sample_multi(self):
@@ -444,7 +449,8 @@ class VegasPlus:
         self.n_h, self.offsets = allocate(self.n_ev, d, self.plus2)
         new = np.empty_like(self.edges)
         for m in range(self.dim):
-            new[m] = refine_axis(self.edges[m], self.hsum[m], self.hcnt[m], self.alpha)
+            new[m] = refine_axis(self.edges[m], self.hsum[m], self.hcnt[m], self.alpha,
+                                 self.d_weighted)
         self.edges = new
 
     def precondition(self, x, f=None, n_iter=10):

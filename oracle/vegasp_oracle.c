@@ -238,12 +238,17 @@ void or_eval_sample(int dim, int n_g, const int64_t *nst_ax, uint64_t seed, uint
 /* in order and every sample j < n_h in order, accumulate                     */
 /*   S1_h = sum J f,  S2_h = sum (J f)^2                        (§3 step 2)   */
 /*   hsum[mu][i] += (J f)^2,  hcnt[mu][i] += 1                  (§2.4, d_i^mu) */
+/* or, with d_weighted (reading: each sample weighted by its hypercube's      */
+/* y-volume per sample, Omega_h / n_h, Omega_h being the same for every        */
+/* hypercube and dropped since d is normalised), hsum[mu][i] += (J f)^2 / n_h, */
+/* an estimate of the slab integral of J^2 f^2 whatever the allocation (§3:   */
+/* the optimal map does not depend on the allocation of samples).             */
 /* All outputs are overwritten.                                               */
 /* ------------------------------------------------------------------------ */
 int or_sample_iteration(int dim, int n_g, const int64_t *nst_ax, uint64_t seed,
                         uint32_t integral_id, const double *edges, int kind, const double *prm,
                         uint32_t t, const uint32_t *n_h, double *s1, double *s2, double *hsum,
-                        double *hcnt) {
+                        double *hcnt, int d_weighted) {
     or_problem P = {dim, n_g, nst_ax, seed, integral_id, edges, kind, prm};
     int64_t n_hc = 1;
     for (int mu = 0; mu < dim; ++mu) n_hc *= nst_ax[mu];
@@ -260,8 +265,9 @@ int or_sample_iteration(int dim, int n_g, const int64_t *nst_ax, uint64_t seed,
             double jf = jac * f;
             a1 += jf;
             a2 += jf * jf;
+            const double w = d_weighted ? jf * jf / (double)n_h[h] : jf * jf;
             for (int mu = 0; mu < dim; ++mu) {
-                hsum[(size_t)mu * n_g + idx[mu]] += jf * jf;
+                hsum[(size_t)mu * n_g + idx[mu]] += w;
                 hcnt[(size_t)mu * n_g + idx[mu]] += 1.0;
             }
         }
@@ -479,7 +485,8 @@ int or_allocate(int64_t n_hc, int64_t n_ev, int plus2, const double *d, uint32_t
 /* Step a8: refinement of one axis's grid, §2.3, in the paper's order.        */
 /* ------------------------------------------------------------------------ */
 
-/* d_i = hsum_i / hcnt_i (reading: 0 when the increment got no sample), then   */
+/* d_i = hsum_i / hcnt_i (reading: 0 when the increment got no sample; with   */
+/* d_weighted, hsum_i itself: its samples are already weighted), then         */
 /* the smoothing (7,1)/8, (1,6,1)/8, (1,7)/8 with division by sum_i d_i, then  */
 /* the compression d_i -> ((1 - d_i)/ln(1/d_i))^alpha (reading: 1 at d_i = 1;  */
 /* a smoothed d_i of zero is raised to the smallest normal double first, so    */
@@ -488,11 +495,11 @@ int or_allocate(int64_t n_hc, int64_t n_ev, int plus2, const double *d, uint32_t
 /* when every d_i is zero (or the sum is not finite): nothing to refine.       */
 /* Needs n_g >= 2.                                                             */
 int or_smooth_compress(int n_g, const double *hsum, const double *hcnt, double alpha,
-                       double *out, double *work) {
+                       double *out, double *work, int d_weighted) {
     double *d = work;
     double sum_d = 0.0;
     for (int i = 0; i < n_g; ++i) {
-        d[i] = hcnt[i] > 0.0 ? hsum[i] / hcnt[i] : 0.0;
+        d[i] = hcnt[i] > 0.0 ? (d_weighted ? hsum[i] : hsum[i] / hcnt[i]) : 0.0;
         sum_d += d[i];
     }
     if (!(sum_d > 0.0) || !isfinite(sum_d)) return 1;
@@ -591,10 +598,10 @@ void or_precondition_hist(int dim, int n_g, const double *edges, int64_t n, cons
 /* N_g = 1 or all-zero d_i leave the grid unchanged (reading).  work holds     */
 /* 2 N_g doubles.                                                             */
 void or_refine_axis(int n_g, const double *edges_in, const double *hsum, const double *hcnt,
-                    double alpha, double *edges_out, double *work) {
+                    double alpha, double *edges_out, double *work, int d_weighted) {
     for (int i = 0; i <= n_g; ++i) edges_out[i] = edges_in[i];
     if (alpha == 0.0 || n_g < 2) return;
     double *sm = work + n_g;
-    if (or_smooth_compress(n_g, hsum, hcnt, alpha, sm, work) != 0) return;
+    if (or_smooth_compress(n_g, hsum, hcnt, alpha, sm, work, d_weighted) != 0) return;
     or_regrid(n_g, edges_in, sm, edges_out);
 }
