@@ -122,6 +122,13 @@ typedef struct {
        integral per context, at most 2^22 hypercubes, n_extra <= 7. */
     int n_extra;
     const int32_t *out_mono; /* [2 n_extra] (copied) */
+    int d_weighted;     /* the grid's d_i^mu (§2.3, §2.4): 0 = the mean of (J f)^2 over
+                           the samples in the increment (the paper's form); 1 = the sum
+                           of (J f)^2 / n_h, each sample weighted by its hypercube's
+                           y-volume per sample (Omega_h / n_h, the common Omega dropped
+                           since d is normalised), an estimate of the slab integral of
+                           J^2 f^2 whatever the allocation (§3: the optimal map does not
+                           depend on it) */
 } vp_params;
 
 typedef struct {

@@ -553,7 +553,9 @@ __global__ void __cluster_dims__(kRefineCtas, 1, 1) __launch_bounds__(kRefineThr
     // histograms of the latest sampling pass (double-buffered by iteration
     // parity; the sampling kernel records which, so that this kernel may run
     // beside the estimate that advances t)
-    const size_t hb = (size_t)(d.st->hist_par & 1u) * (size_t)d.dim * n_g;
+    const uint32_t hpar = d.st->hist_par;
+    const bool weighted = (hpar & 2u) != 0u;  // sums already weighted by 1/n_h: d_i = sum
+    const size_t hb = (size_t)(hpar & 1u) * (size_t)d.dim * n_g;
     const double *hs = d.hsum + hb + (size_t)mu * n_g;
     const uint32_t *hc = d.hcnt + hb + (size_t)mu * n_g;
 
@@ -564,7 +566,7 @@ __global__ void __cluster_dims__(kRefineCtas, 1, 1) __launch_bounds__(kRefineThr
         double v = 0.0;
         if (i >= 0 && i < n_g) {
             const uint32_t c = hc[i];
-            v = c ? hs[i] / (double)c : 0.0;
+            v = c ? (weighted ? hs[i] : hs[i] / (double)c) : 0.0;
         }
         sm.d[i - (i0 - 1)] = v;
         if (i >= i0 && i < i1) part += v;

@@ -200,6 +200,7 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
     if (p->n_st_axis)
         for (int i = 0; i < p->dim; ++i)
             if (p->n_st_axis[i] < 1) return fail(VP_EINVAL, "n_st_axis[%d] must be >= 1", i);
+    if (p->d_weighted != 0 && p->d_weighted != 1) return fail(VP_EINVAL, "d_weighted must be 0 or 1");
     if (p->n_extra < 0 || p->n_extra > kMaxOut - 1)
         return fail(VP_EINVAL, "n_extra outside 0..%d", kMaxOut - 1);
     if (p->n_extra > 0) {
@@ -530,6 +531,7 @@ void vp::fill_desc(const Member &mb, const double *d_inv, Desc &d) {
     div_magic((uint32_t)mb.n_st, &d.nst_magic, &d.nst_shift);
     d.uniform = mb.uniform ? 1u : 0u;
     d.n_out = mb.n_out;
+    d.d_weighted = mb.p.d_weighted;
     for (int k = 0; k < 2 * kMaxOut; ++k) d.mono[k] = k < (int)mb.mono.size() ? mb.mono[k] : -1;
     if (mb.n_out > 1) {
         d.x1 = mbuf<double>(mb, B_X1);
@@ -681,6 +683,7 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         L.n_st = d.n_st;
         L.calls = (uint32_t)((d.dim + 3) >> 2);
         L.iid = d.integral_id;
+        L.dw = d.d_weighted;
         L.t = 0;
         uint32_t k0 = d.key0, k1 = d.key1;
         for (int r = 0; r < 10; ++r) {
@@ -1620,7 +1623,8 @@ extern "C" vp_status vp_refine_from_hist(vp_ctx *c, const double *hsum, const do
     CU(cudaMemcpyAsync(d.hsum + par * bins, hsum, bins * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
     CU(cudaMemcpyAsync(d.hcnt + par * bins, cnt.data(), bins * 4, cudaMemcpyHostToDevice,
                        (cudaStream_t)stream));
-    const uint32_t par32 = (uint32_t)par;
+    // (the sums are taken as the context accumulates them: weighted or plain)
+    const uint32_t par32 = (uint32_t)par | (d.d_weighted ? 2u : 0u);
     CU(cudaMemcpyAsync((char *)d.st + offsetof(State, hist_par), &par32, 4, cudaMemcpyHostToDevice,
                        (cudaStream_t)stream));
     CU(launch_refine(s.d_desc, s.d_axis_base, 1, s.n_axis_total, s.max_ng, (cudaStream_t)stream));

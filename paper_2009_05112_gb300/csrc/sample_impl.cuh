@@ -250,6 +250,7 @@ struct Loop {
     uint32_t nst_magic;
     int nst_shift;
     uint32_t n_st, calls, iid, t;
+    int dw;                     // the grid's d_i from samples weighted by 1/n_h
     uint32_t rk0[10], rk1[10];  // Philox round keys
     float c32;                  // N_g / N_st
     float ngm1;                 // N_g - 1
@@ -270,6 +271,7 @@ __device__ __forceinline__ Loop make_loop(const Desc *dp, uint32_t t) {
     L.nst_shift = __ldg(&dp->nst_shift);
     L.calls = (uint32_t)((L.dim + 3) >> 2);
     L.iid = __ldg(&dp->integral_id);
+    L.dw = __ldg(&dp->d_weighted);
     L.t = t;
     uint32_t k0 = __ldg(&dp->key0), k1 = __ldg(&dp->key1);
 #pragma unroll
@@ -730,6 +732,10 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
     // in the run, and before the next hypercube (n_h >= 2, so at most one
     // boundary per sample)
     uint32_t to_next = (uint32_t)(next - s_begin);
+    // the grid's d_i weighted per sample by 1/n_h of its hypercube (L.dw), or
+    // the plain mean (weight 1, an exact multiply)
+    uint32_t nh_cur = L.dw ? __ldg(P.nh + h) : 1u;
+    float hw32 = L.dw ? __frcp_rn((float)nh_cur) : 1.0f;
     for (uint32_t left = (uint32_t)(s_end - s_begin); left > 0; --left) {
         if (to_next == 0u) {
             acc.flush(P.S1 + h, P.S2 + h, sexp);
@@ -740,6 +746,10 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
             }
             ++h;
             to_next = __ldg(P.nh + h);
+            if (L.dw) {
+                nh_cur = to_next;
+                hw32 = __frcp_rn((float)nh_cur);
+            }
             j = 0;
             next_digits<DMAX, AX>(L, S, dim, kd);
             if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
@@ -752,7 +762,7 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
         // would leave FP32, e.g. in the first iteration, before the scale has
         // adapted) a sample takes exact FP64 terms of its own
         bool big = false, tiny = false;
-        double vbig = 0.0, vbig2 = 0.0;
+        double vbig = 0.0, vbig2 = 0.0, hbig = 0.0;
         if (F64) {
             double x[DMAX], J, f;
             if (MO) {  // (the outputs' selects read every entry)
@@ -778,6 +788,7 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
                 vbig2 = f2d_pow2(m * m, 2 * (ej + Je));     // (J f)^2
                 red_add(P.S1 + h, vbig);
                 red_add(P.S2 + h, vbig2);
+                hbig = L.dw ? vbig2 / (double)nh_cur : vbig2;  // (rare: only here)
                 v = (T)0;
             } else {
                 tiny = nz && ev < -60;
@@ -797,25 +808,33 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
             hdst = (T *)hs_t;
             hexp -= 2 * kTinyShift;
         }
+        // the histogram term: (J f)^2, or (J f)^2 / n_h for the weighted d_i
+        // (FP64: the oracle's division; FP32: times the rounded 1/n_h)
+        T hv = v2;
+        if (F64) {
+            if (L.dw) hv = (T)__ddiv_rn((double)v2, (double)nh_cur);
+        } else {
+            hv = v2 * (T)hw32;
+        }
 #pragma unroll
         for (int mu = 0; mu < DMAX; ++mu) {
             if (mu < dim) {
                 const int b = mu * L.n_g + idx[mu];
                 if (big) {
-                    red_add(P.HS + b, vbig2);
+                    red_add(P.HS + b, hbig);
                     if (hist_shared) atomicAdd(hc + b, 1u);
                     else red_add(P.HC + b, 1u);
                 } else if (hist_shared) {
                     if (compact && tiny) {  // (FP32 only) the tiny sum to global memory
-                        if (v2 != (T)0) red_add(P.HS + b, f2d_pow2((float)v2, hexp));
-                    } else if (v2 != (T)0) {
-                        atomicAdd(hdst + b, v2);
+                        if (hv != (T)0) red_add(P.HS + b, f2d_pow2((float)hv, hexp));
+                    } else if (hv != (T)0) {
+                        atomicAdd(hdst + b, hv);
                     }
                     atomicAdd(hc + b, 1u);
                 } else {
-                    if (v2 != (T)0)
-                        red_add(P.HS + b, F64 ? (double)v2 * pow2d(hexp)
-                                              : f2d_pow2((float)v2, hexp));
+                    if (hv != (T)0)
+                        red_add(P.HS + b, F64 ? (double)hv * pow2d(hexp)
+                                              : f2d_pow2((float)hv, hexp));
                     red_add(P.HC + b, 1u);
                 }
             }
@@ -941,7 +960,7 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
     // posterior's far tails, scaled squares would round differently, and the
     // grid's compression weighs those tiny d_i by their logarithm)
     const int sexp = F64 ? 0 : __ldcg(&a.st->scale_exp);
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->hist_par = t_it & 1u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->hist_par = (t_it & 1u) | (a.L.dw ? 2u : 0u);
     Loop L = a.L;
     L.t = t_it;
     Ptrs P;
@@ -1054,7 +1073,8 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
         const Desc *dp = a.desc + __ldg(a.members + g);
         State *st = (State *)__ldg((const unsigned long long *)&dp->st);
         const uint32_t t_it = __ldcg(&st->t);
-        if (threadIdx.x == 0) st->hist_par = t_it & 1u;  // every CTA of the integral writes the same
+        if (threadIdx.x == 0)  // every CTA of the integral writes the same
+            st->hist_par = (t_it & 1u) | (__ldg(&dp->d_weighted) ? 2u : 0u);
         L = make_loop(dp, t_it);
         sexp = F64 ? 0 : __ldcg(&st->scale_exp);  // (FP64: unscaled, as in k_sample_one)
         bins = L.dim * L.n_g;

@@ -40,7 +40,8 @@ struct State {
     uint32_t done_alloc;  // last-block counter of the allocation kernel
     uint32_t done_multi;  // last-block counter of the several-outputs estimate (App. B)
     uint32_t status;      // kStatus* bits
-    uint32_t hist_par;    // histogram buffer of the latest sampling pass (read by the refinement)
+    uint32_t hist_par;    // histogram buffer of the latest sampling pass (bit 0, read by the
+                          // refinement) and its kind (bit 1: sums weighted by 1/n_h, d_i = sum)
     double sum_d;         // sum_h d_h in the fixed order (set by the estimate kernel)
     double inv_sum_d;     // 1 / sum_d
     uint64_t n_samples;   // sum_h n_h of the current allocation
@@ -119,6 +120,7 @@ struct Desc {
     // (1: the integrand alone).  Output k is J f g_k(x), g_k = x^a x^b for
     // (a, b) = mono[2k], mono[2k+1] (< 0: that factor is 1); output 0 is f.
     int32_t n_out;
+    int32_t d_weighted;        // 1: the grid's d_i from samples weighted by 1/n_h (else the mean)
     int32_t mono[2 * kMaxOut];
     double *x1;        // [2][n_hc][M] per-hypercube sums of the outputs (double-buffered)
     double *x2;        // [2][n_hc][M (M+1)/2] sums of their products, upper triangle by rows

@@ -46,6 +46,7 @@ class Problem:
     meta: dict = field(default_factory=dict)
     n_st_axis: tuple = None  # strata per axis (§3.2); overrides n_st
     mixed: bool = False      # §3.2's mixed N_st / N_st + 1 rule in place of Eq. (Nst_vegasp)
+    d_weighted: bool = False # the grid's d_i from samples weighted by 1/n_h
 
 
 def _blob(rows):
