@@ -816,28 +816,35 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
         } else {
             hv = v2 * (T)hw32;
         }
+        // (the branches are taken once per sample, not per axis: the axis
+        // loops below are plain runs of atomics)
+        int bin[DMAX];
 #pragma unroll
-        for (int mu = 0; mu < DMAX; ++mu) {
-            if (mu < dim) {
-                const int b = mu * L.n_g + idx[mu];
-                if (big) {
-                    red_add(P.HS + b, hbig);
-                    if (hist_shared) atomicAdd(hc + b, 1u);
-                    else red_add(P.HC + b, 1u);
-                } else if (hist_shared) {
-                    if (compact && tiny) {  // (FP32 only) the tiny sum to global memory
-                        if (hv != (T)0) red_add(P.HS + b, f2d_pow2((float)hv, hexp));
-                    } else if (hv != (T)0) {
-                        atomicAdd(hdst + b, hv);
-                    }
-                    atomicAdd(hc + b, 1u);
-                } else {
-                    if (hv != (T)0)
-                        red_add(P.HS + b, F64 ? (double)hv * pow2d(hexp)
-                                              : f2d_pow2((float)hv, hexp));
-                    red_add(P.HC + b, 1u);
-                }
+        for (int mu = 0; mu < DMAX; ++mu) bin[mu] = mu * L.n_g + idx[mu];
+        if (big) {
+#pragma unroll
+            for (int mu = 0; mu < DMAX; ++mu)
+                if (mu < dim) red_add(P.HS + bin[mu], hbig);
+        } else if (hv != (T)0) {
+            if (hist_shared && !(compact && tiny)) {
+#pragma unroll
+                for (int mu = 0; mu < DMAX; ++mu)
+                    if (mu < dim) atomicAdd(hdst + bin[mu], hv);
+            } else {  // global sums (and, compact, the FP32 tiny sums)
+                const double hg = F64 ? (double)hv * pow2d(hexp) : f2d_pow2((float)hv, hexp);
+#pragma unroll
+                for (int mu = 0; mu < DMAX; ++mu)
+                    if (mu < dim) red_add(P.HS + bin[mu], hg);
             }
+        }
+        if (hist_shared) {
+#pragma unroll
+            for (int mu = 0; mu < DMAX; ++mu)
+                if (mu < dim) atomicAdd(hc + bin[mu], 1u);
+        } else {
+#pragma unroll
+            for (int mu = 0; mu < DMAX; ++mu)
+                if (mu < dim) red_add(P.HC + bin[mu], 1u);
         }
         ++j;
     }
