@@ -777,7 +777,11 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
             int Je;
             point32<DMAX, EXACT, KIND, KP, AX>(L, S, (const float *)prm, (uint32_t)h, j, kc, x, idx,
                                                Jm, Je, f);
-            const float jf = Jm * f;  // normal or zero: Jm in [1, 2), f flushed to zero
+            float jf = Jm * f;  // Jm in [1, 2); the last multiply-add of f may leave it subnormal
+            if (((__float_as_int(jf) & 0x7f800000) == 0) && jf != 0.0f) {  // renormalise (exact)
+                jf *= 16777216.0f;
+                Je -= 24;
+            }
             const int ej = ((__float_as_int(jf) >> 23) & 0xff) - 127;
             const int ev = ej + Je + sexp;  // exponent of v
             const bool nz = jf != 0.0f && isfinite(jf);
@@ -792,7 +796,12 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
                 v = (T)0;
             } else {
                 tiny = nz && ev < -60;
-                v = (T)scale2(jf, Je + sexp + (tiny ? kTinyShift : 0));
+                // the scaled v has exponent ev (+ kTinyShift if tiny), in
+                // [-63, 60): a normal number, so the power of two goes straight
+                // into the exponent field (exact, as a multiply would be); zero,
+                // inf and NaN pass unchanged
+                const int sh = Je + sexp + (tiny ? kTinyShift : 0);
+                v = (T)(nz ? __int_as_float(__float_as_int(jf) + (sh << 23)) : jf);
             }
         }
         const T v2 = v * v;
