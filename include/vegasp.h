@@ -272,7 +272,7 @@ vp_status vp_get_tuning(vp_ctx *ctx, int *scheme, int *blocks, int *threads, int
  * choose it (reproducible timing and profiling; no counterpart in the paper,
  * the shape does not change any result beyond FP summation order).
  * Arguments as in vp_get_tuning: scheme 0 requires all `blocks` CTAs of
- * `threads` (256, 512 or 768, within the kernel's limit) resident at once, in
+ * `threads` (256, 512, 768 or 1024, within the kernel's limit) resident at once, in
  * clusters of `cluster` (1, 2, 4, 8; > 1 only with shared-memory histograms);
  * scheme 1 takes threads = 256 and cluster = 1; run in 1..64.  Synchronises
  * the context's last stream; a step graph captured before is rebuilt at the

@@ -917,7 +917,7 @@ static vp_status tune(Set &s, cudaStream_t stream) {
         if (can_one && g.one) {
             // CTAs of 256 threads (1..3 per SM), or one larger CTA per SM
             const int max_threads = one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64);
-            for (int threads : {256, 512, 768}) {
+            for (int threads : {256, 512, 768, 1024}) {
                 if (threads > max_threads) continue;
                 const int occ = g.prec == VP_FP64
                                     ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one, g.mo)
@@ -1762,8 +1762,8 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     Group &g = c->set.groups[0];
     if (scheme != 0 && scheme != 1) return fail(VP_EINVAL, "scheme must be 0 or 1");
     if (scheme == 1 && threads != 256) return fail(VP_EINVAL, "the task scheme runs 256 threads");
-    if (threads != 256 && threads != 512 && threads != 768)
-        return fail(VP_EINVAL, "threads must be 256, 512 or 768");
+    if (threads != 256 && threads != 512 && threads != 768 && threads != 1024)
+        return fail(VP_EINVAL, "threads must be 256, 512, 768 or 1024");
     if (threads > one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64))
         return fail(VP_EINVAL, "%d threads exceed this kernel's largest CTA", threads);
     if (scheme == 0 && g.members.size() == 1 && g.prec == VP_FP32 && g.kind != VP_POSTERIOR &&

@@ -895,10 +895,11 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Strata *S, cons
 // ---------------------------------------------------------------------------
 // Largest CTA of the one-integral kernel: the autotuner also tries one CTA per
 // SM (one shared-memory histogram per SM instead of one per 256 threads).
-// The bound keeps the register budget of the earlier 256 x 3 (D <= 8), 256 x 2
-// (FP32, D > 8) and 256 x 1 (FP64) shapes.
+// The bound sets the register budget: 64 for FP32 with D <= 8 (1024 threads,
+// no spills: a third more warps than 768 threads at 80 registers), the 256 x 2
+// shape's for FP32 with D > 8 and the 256 x 1 shape's for FP64.
 __host__ __device__ constexpr int one_max_threads(int dmax, bool f64) {
-    return f64 ? 256 : (dmax <= 8 ? 768 : 512);
+    return f64 ? 256 : (dmax <= 8 ? 1024 : 512);
 }
 
 // Sum of the cluster's CS copies of bins [b0, b1) of the histograms, added to
