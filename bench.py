@@ -237,6 +237,90 @@ def cpu_baseline(prob, seconds=12.0, out_mono=None, data=None):
                                                          prob.n_g, el)}
 
 
+def _oracle_worker(job):
+    """One process of the all-cores baseline: the single-thread oracle on the
+    workload (its own Philox counter word 3) for ~seconds; (evals, seconds)."""
+    name, seed_id, seconds = job
+    import oracle
+    from paper_2009_05112_gb300 import inputs
+    prob = getattr(inputs, name)()
+    o = oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
+                         alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind,
+                         prm=prob.prm, integral_id=seed_id)
+    evals, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        evals += int(o.offsets[-1])
+        o.iterate()
+        o.adapt()
+    return evals, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(name, seconds=12.0):
+    """The oracle as it stands on every host core: one spawned process per
+    core, each running the single-thread oracle on the workload; evals/s
+    summed over the processes (each timed on its own)."""
+    import multiprocessing as mp
+    cores = max(1, min(os.cpu_count() or 1, 128))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(name, k, seconds) for k in range(cores)])
+    value = sum(e / s for e, s in res)
+    return {"value": value, "unit": "integrand evals/s", "cores": cores, "kind": "oracle",
+            "sample": "%d processes, each the single-thread FP64 C oracle on whole iterations "
+                      "of %s for ~%.0f s" % (cores, name, seconds)}
+
+
+def cpu_baseline_batch(probs, n_it, seconds=12.0):
+    """The oracle on the batch's integrals one after another (whole runs of
+    n_it iterations) until ~seconds of CPU time: a bounded sample of the
+    512-integral job; one thread."""
+    import oracle
+    evals, done, t0 = 0, 0, time.perf_counter()
+    for p in probs:
+        o = oracle.VegasPlus(dim=p.dim, lo=p.lo, hi=p.hi, n_g=p.n_g, n_ev=p.n_ev, alpha=p.alpha,
+                             beta=p.beta, seed=p.seed, kind=p.kind, prm=p.prm,
+                             integral_id=p.integral_id)
+        for _ in range(n_it):
+            evals += int(o.offsets[-1])
+            o.iterate()
+            o.adapt()
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": evals / el, "unit": "integrand evals/s", "cores": 1, "kind": "oracle",
+            "sample": "the first %d of the 512 integrals, %d iterations each, FP64 C oracle, "
+                      "single thread, %.1f s" % (done, n_it, el)}
+
+
+def cpu_baseline_serve(probs, rules, seconds=12.0):
+    """The oracle serving the stream's requests one after another, each until
+    its stop rule (the §2.5 combination of iterations >= discard reaching
+    sdev <= rtol |mean| after min_meas of them, or max_it iterations), until
+    ~seconds of CPU time; one thread."""
+    import oracle
+    done, evals, t0 = 0, 0, time.perf_counter()
+    for p, r in zip(probs, rules):
+        o = oracle.VegasPlus(dim=p.dim, lo=p.lo, hi=p.hi, n_g=p.n_g, n_ev=p.n_ev, alpha=p.alpha,
+                             beta=p.beta, seed=p.seed, kind=p.kind, prm=p.prm,
+                             integral_id=p.integral_id)
+        for it in range(r["max_it"]):
+            evals += int(o.offsets[-1])
+            o.iterate()
+            o.adapt()
+            if it + 1 - r["discard"] >= r["min_meas"]:
+                c = oracle.combine(o.I, o.var, r["discard"])
+                if c["sdev"] <= r["rtol"] * abs(c["mean"]):
+                    break
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "requests/s", "cores": 1, "kind": "oracle",
+            "evals_per_s": evals / el,
+            "sample": "the first %d requests of the stream served one at a time by the FP64 C "
+                      "oracle, single thread, %.1f s" % (done, el)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -509,6 +593,8 @@ def run_ours(args):
         line["training"] = training
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, out_mono=out_mono, data=data)
+        if args.workload == "four_peaks_d8":
+            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores("four_peaks_d8")
     print(json.dumps(line), flush=True)
     g.close()
     if world > 1:
@@ -585,6 +671,8 @@ def run_batch(args):
                                  "median_rel_err_batched": statistics.median(rel_b),
                                  "median_rel_err_plain": statistics.median(rel_p)},
             "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batch(probs, n_it)
     print(json.dumps(line), flush=True)
 
 
@@ -665,6 +753,8 @@ def run_serve(args):
             "served": out["served"], "plain": out["plain"],
             "served_saturated": sat, "plain_saturated": out["plain_saturated"],
             "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_serve(probs, rules)
     print(json.dumps(line), flush=True)
 
 
