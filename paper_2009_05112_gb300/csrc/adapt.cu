@@ -136,7 +136,15 @@ __device__ __forceinline__ double damp_var32(double var, const Desc &d) {
 // ---------------------------------------------------------------------------
 constexpr int kEstCtas = 4;
 
-__device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode);
+// The state fields the last step reads, loaded early by every CTA's thread 0
+// (they change only in that step, so the loads overlap the sums instead of
+// queueing behind one another at the end).
+struct EstPre {
+    uint32_t t, status;
+    uint64_t n_samples, n_eval_total;
+};
+__device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode,
+                                const EstPre &pre);
 
 struct EstShared {
     double recv2[3][256];  // level 256: CTA 1's terms, received by CTA 0
@@ -194,6 +202,13 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
     const uint32_t k = tb - tree_base[b];
     const int t = threadIdx.x;
     const uint32_t par = d.st->t & 1u;  // buffer of the iteration being estimated
+    EstPre pre = {0u, 0u, 0ull, 0ull};
+    if (t == 0) {
+        pre.t = d.st->t;
+        pre.status = d.st->status;
+        pre.n_samples = d.st->n_samples;
+        pre.n_eval_total = d.st->n_eval_total;
+    }
     const D3 v = hcube_terms(d, (uint64_t)k * kTreeBlock + 256 * rank + t, mode, par);
     if (mode == 0) {  // clear the other histogram buffer, spread over this integral's CTAs
         const int bins = d.dim * d.n_g;
@@ -271,26 +286,27 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
     block_tree_sum<3>(d.part, d.n_tree, &sm.red[0][0], tot);
     if (t != 0) return;
     d.st->done_est = 0u;
-    finish_estimate(d, tot[0], tot[1], tot[2], mode);
+    finish_estimate(d, tot[0], tot[1], tot[2], mode, pre);
 }
 
 // The iteration's totals I_j, sigma_j^2 and sum d recorded in the state (one
 // thread): history, the FP32 path's scale, the iteration count and, for a
 // served request, the stop rule.
-__device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode) {
+__device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode,
+                                const EstPre &pre) {
     State *st = d.st;
     st->sum_d = Sd;
     st->inv_sum_d = Sd > 0.0 ? 1.0 / Sd : 0.0;
     if (mode == 0) {
-        const uint32_t tt = st->t;
+        const uint32_t tt = pre.t;
         if (tt < (uint32_t)d.hist_cap) {
             d.hist_i[tt] = I;
             d.hist_var[tt] = V;
         }
         st->last_i = I;
         st->last_var = V;
-        st->n_eval_total += st->n_samples;
-        if (!isfinite(I) || !isfinite(V)) st->status |= kStatusNonFinite;
+        st->n_eval_total = pre.n_eval_total + pre.n_samples;
+        if (!isfinite(I) || !isfinite(V)) st->status = pre.status | kStatusNonFinite;
         // keep J f 2^scale_exp near one in the next iteration: the mean of J f
         // over y-space is the integral (an exact power-of-two rescaling).
         if (isfinite(I) && I != 0.0) {

@@ -213,6 +213,28 @@ __device__ void block_tree_sum(const double *part, uint32_t n, double *sh, doubl
     uint32_t P = 1;
     while (P < n) P <<= 1;
     const uint32_t nt = blockDim.x, t = threadIdx.x;
+    if (P <= 64 && (uint32_t)NS * 32u <= nt) {
+        // at most 64 leaves: one warp per series, lane l adds leaves 2l and
+        // 2l + 1 (level 1), then level k adds lane 2^(k-2) further down, the
+        // left node first: the same tree, with no barrier between levels
+        const uint32_t w = t >> 5, l = t & 31u;
+        if (w < (uint32_t)NS) {
+            double x = 0.0;
+            if (P == 1) {
+                x = (n > 0) ? __ldcg(part + w) : 0.0;
+            } else if (2u * l < P) {
+                const double a = 2u * l < n ? __ldcg(part + (size_t)NS * (2u * l) + w) : 0.0;
+                const double b = 2u * l + 1u < n ? __ldcg(part + (size_t)NS * (2u * l + 1u) + w) : 0.0;
+                x = __dadd_rn(a, b);
+            }
+            for (uint32_t o = 1; 4u * o <= P; o <<= 1) x = __dadd_rn(x, __shfl_down_sync(0xffffffffu, x, o));
+            if (l == 0) sh[w] = x;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < NS; ++c) out[c] = sh[c];
+        return;
+    }
     const uint32_t T = P < nt ? P : nt;
     const uint32_t Q = P / T;
     double run[NS];
