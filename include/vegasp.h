@@ -103,9 +103,9 @@ typedef struct {
     int max_it;         /* capacity of the iteration history (0 = 1024) */
     /* Strata per axis (§3.2, "Limitations and a Variation").  Hypercube h is
        the mixed-radix number whose digit on axis mu (axis 0 least significant)
-       is its stratum there.  Contexts of one integral only: vp_batch_create
-       with more than one integral and served requests accept uniform strata
-       only (VP_EINVAL otherwise). */
+       is its stratum there.  Accepted everywhere (contexts, batches, served
+       requests); a single FP32 integral with more than 8 peaks whose D is 4,
+       8, 12, 16, 20 or 24 and whose strata differ is refused (VP_EINVAL). */
     const int32_t *n_st_axis; /* NULL, or [D] strata per axis, each >= 1 (copied);
                                  overrides n_st and mixed */
     int mixed;          /* with n_st == 0 and n_st_axis == NULL: 1 = §3.2's mixed

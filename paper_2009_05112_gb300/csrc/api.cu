@@ -350,12 +350,14 @@ static vp_status plan_groups(Set &s) {
     for (uint32_t i = 0; i < s.m.size(); ++i) {
         const Member &mb = s.m[i];
         const int bucket = s.merge ? merged_bucket[mb.kind][mb.p.precision] : mb.bucket;
-        bool exact = mb.exact && mb.p.precision == VP_FP32;  // FP64 kernels are guarded
+        // FP64 kernels are guarded; so is the task kernel's per-axis form
+        // (several integrals with strata that differ between axes)
+        bool exact = mb.exact && mb.p.precision == VP_FP32 && (mb.uniform || s.m.size() == 1);
         if (s.merge) {
             exact = mb.p.precision == VP_FP32;
             for (const Member &o : s.m)
                 if (o.kind == mb.kind && o.p.precision == mb.p.precision &&
-                    o.p.dim != bucket_dim(bucket))
+                    (o.p.dim != bucket_dim(bucket) || !o.uniform))
                     exact = false;
         }
         Group *g = nullptr;
@@ -386,20 +388,16 @@ static vp_status plan_groups(Set &s) {
             if (g.prec == VP_FP32 && g.kind != VP_POSTERIOR && (int)m0.prm[0] > kParamPeaks)
                 g.one = false;
         }
-        // strata that differ between axes (§3.2): the one-integral kernel only
-        // (the task kernel keeps one strata count in registers)
-        g.uniform = true;
+        // (strata that differ between axes, §3.2: the task kernel's per-axis
+        // instantiation, g.uniform false, set by group_config_many; it has no
+        // exact-dimension form, so such a group is exact only for the
+        // one-integral kernel, and the task scheme is then not offered)
         g.mo = false;
-        for (uint32_t i : g.members) {
-            g.uniform = g.uniform && s.m[i].uniform;
-            g.mo = g.mo || s.m[i].n_out > 1;
-        }
+        for (uint32_t i : g.members) g.mo = g.mo || s.m[i].n_out > 1;
         if (g.mo && !g.one)  // several outputs (App. B): the FP64 one-integral kernel sums them
             return fail(VP_EINVAL, "several outputs: one integral per context");
-        if (!g.uniform && !g.one)
-            return fail(VP_EINVAL, g.members.size() > 1
-                                       ? "strata that differ between axes: one integral per context"
-                                       : "strata that differ between axes: FP32 peaks at most %d",
+        if (!g.uniform && g.exact && !g.one)
+            return fail(VP_EINVAL, "strata that differ between axes: FP32 peaks at most %d",
                         kParamPeaks);
         if (!g.one) continue;
         // a single integral: the cluster kernel with its constants in parameters
@@ -455,6 +453,8 @@ static vp_status plan_groups(Set &s) {
 vp_status vp::group_config_many(const std::vector<const Member *> &m, Group &g, int n_sm) {
     double expect = 0.0;
     int max_bins = 0, max_words = 0;
+    g.uniform = true;  // (else the per-axis instantiation of the task kernel)
+    for (uint32_t i : g.members) g.uniform = g.uniform && m[i]->uniform;
     for (uint32_t i : g.members) {
         expect += (double)m[i]->p.n_ev + 2.0 * (double)m[i]->n_hc;
         max_bins = std::max(max_bins, m[i]->p.dim * m[i]->p.n_g);
@@ -476,12 +476,12 @@ vp_status vp::group_config_many(const std::vector<const Member *> &m, Group &g, 
     g.one = false;
     g.cs = 1;
     cudaError_t e = g.prec == VP_FP64
-                        ? sample_smem_config_f64(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024))
-                        : sample_smem_config_f32(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024));
+                        ? sample_smem_config_f64(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024), false, !g.uniform)
+                        : sample_smem_config_f32(g.bucket, g.exact, g.kind, false, (int)std::max<size_t>(g.smem, 48 * 1024), !g.uniform);
     if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     g.occ_many = g.prec == VP_FP64
-                     ? sample_occupancy_f64(g.bucket, g.exact, g.kind, false, g.threads, g.smem)
-                     : sample_occupancy_f32(g.bucket, g.exact, g.kind, false, g.threads, g.smem);
+                     ? sample_occupancy_f64(g.bucket, g.exact, g.kind, false, g.threads, g.smem, false, !g.uniform)
+                     : sample_occupancy_f32(g.bucket, g.exact, g.kind, false, g.threads, g.smem, !g.uniform);
     if (g.occ_many < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem);
     g.blocks = n_sm * std::min(g.occ_many, 2);
     set_task(g, expect);
@@ -790,8 +790,8 @@ vp_status vp::launch_group(const Desc *d_desc, Group &g, cudaStream_t stream) {
         a.hist_words = g.hist_words;
         a.prm_words = g.prm_words;
         e = g.prec == VP_FP64
-                ? launch_sample_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a)
-                : launch_sample_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a);
+                ? launch_sample_f64(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a, !g.uniform)
+                : launch_sample_f32(g.bucket, g.exact, g.kind, g.blocks, g.threads, g.smem, stream, a, !g.uniform);
     }
     if (e != cudaSuccess) return fail(VP_ECUDA, "sampling launch: %s", cudaGetErrorString(e));
     return VP_OK;
@@ -939,7 +939,7 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                 }
             }
         }
-        if (g.uniform && !g.mo)
+        if ((g.uniform || !g.exact) && !g.mo)
             for (int k = 1; k <= std::min(3, g.occ_many); ++k)
                 for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r, 256});
         if (cands.size() <= 1) {
@@ -1772,8 +1772,9 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     if (blocks < 1 || blocks > 65535) return fail(VP_EINVAL, "blocks out of range");
     if (run < 1 || run > 64) return fail(VP_EINVAL, "run must be in 1..64");
     if (scheme == 1 && cluster != 1) return fail(VP_EINVAL, "the task scheme takes no clusters");
-    if (scheme == 1 && !g.uniform)
-        return fail(VP_EINVAL, "strata that differ between axes: the one-integral scheme only");
+    if (scheme == 1 && !g.uniform && g.exact)
+        return fail(VP_EINVAL, "strata that differ between axes at this exact dimension: the "
+                               "one-integral scheme only");
     if (scheme == 1 && g.mo) return fail(VP_EINVAL, "several outputs: the one-integral scheme only");
     if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
         return fail(VP_EINVAL, "cluster must be 1, 2, 4 or 8");

@@ -14,19 +14,23 @@ const void *kptr_many_f32_x(int bucket, int kind);
 cudaError_t launch_eval_f32_x(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 const void *kptr_one_f64_g(int bucket, int kind);
 const void *kptr_one_f64_mo(int bucket, int kind);
+const void *kptr_many_f32_ax(int bucket, int kind);
+const void *kptr_many_f64_ax(int bucket, int kind);
 const void *kptr_many_f64_g(int bucket, int kind);
 cudaError_t launch_eval_f64_g(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 
-static const void *pick(bool f64, int bucket, bool exact, int kind, bool one, bool mo = false) {
+static const void *pick(bool f64, int bucket, bool exact, int kind, bool one, bool mo = false,
+                        bool ax = false) {
     if (f64 && one && mo) return kptr_one_f64_mo(bucket, kind);
+    if (!one && ax) return f64 ? kptr_many_f64_ax(bucket, kind) : kptr_many_f32_ax(bucket, kind);
     if (f64) return one ? kptr_one_f64_g(bucket, kind) : kptr_many_f64_g(bucket, kind);
     if (exact) return one ? kptr_one_f32_x(bucket, kind) : kptr_many_f32_x(bucket, kind);
     return one ? kptr_one_f32_g(bucket, kind) : kptr_many_f32_g(bucket, kind);
 }
 
 static cudaError_t launch_many(bool f64, int bucket, bool exact, int kind, dim3 grid, dim3 block,
-                               size_t smem, cudaStream_t s, const SampleArgs &a) {
-    const void *k = pick(f64, bucket, exact, kind, false);
+                               size_t smem, cudaStream_t s, const SampleArgs &a, bool ax) {
+    const void *k = pick(f64, bucket, exact, kind, false, false, ax);
     if (!k) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -65,12 +69,12 @@ static cudaError_t launch_one(bool f64, int bucket, bool exact, int kind, dim3 g
 }
 
 cudaError_t launch_sample_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, const SampleArgs &a) {
-    return launch_many(false, bucket, exact, kind, grid, block, smem, s, a);
+                              cudaStream_t s, const SampleArgs &a, bool ax) {
+    return launch_many(false, bucket, exact, kind, grid, block, smem, s, a, ax);
 }
 cudaError_t launch_sample_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, const SampleArgs &a) {
-    return launch_many(true, bucket, false, kind, grid, block, smem, s, a);
+                              cudaStream_t s, const SampleArgs &a, bool ax) {
+    return launch_many(true, bucket, false, kind, grid, block, smem, s, a, ax);
 }
 cudaError_t launch_sample_one_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block,
                                   size_t smem, int cs, cudaStream_t s, const SampleOne &a) {
@@ -92,8 +96,8 @@ struct SmemLimit {
 static std::vector<SmemLimit> g_smem_limit;
 
 static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool one, int max_smem,
-                               bool mo = false) {
-    const void *k = pick(f64, bucket, exact, kind, one, mo);
+                               bool mo = false, bool ax = false) {
+    const void *k = pick(f64, bucket, exact, kind, one, mo, ax);
     if (!k) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -111,28 +115,30 @@ static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool 
     else g_smem_limit.push_back({k, dev, max_smem});
     return cudaSuccess;
 }
-cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem) {
-    return smem_config(false, bucket, exact, kind, one, max_smem);
+cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem,
+                                   bool ax) {
+    return smem_config(false, bucket, exact, kind, one, max_smem, false, ax);
 }
 cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem,
-                                   bool mo) {
-    return smem_config(true, bucket, false, kind, one, max_smem, mo);
+                                   bool mo, bool ax) {
+    return smem_config(true, bucket, false, kind, one, max_smem, mo, ax);
 }
 
 static int occupancy(bool f64, int bucket, bool exact, int kind, bool one, int threads, size_t smem,
-                     bool mo = false) {
-    const void *k = pick(f64, bucket, exact, kind, one, mo);
+                     bool mo = false, bool ax = false) {
+    const void *k = pick(f64, bucket, exact, kind, one, mo, ax);
     int n = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
         return 0;
     return n;
 }
-int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem) {
-    return occupancy(false, bucket, exact, kind, one, threads, smem);
+int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
+                         bool ax) {
+    return occupancy(false, bucket, exact, kind, one, threads, smem, false, ax);
 }
 int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
-                         bool mo) {
-    return occupancy(true, bucket, false, kind, one, threads, smem, mo);
+                         bool mo, bool ax) {
+    return occupancy(true, bucket, false, kind, one, threads, smem, mo, ax);
 }
 
 static int cluster_ctas(bool f64, int bucket, bool exact, int kind, int cs, int grid, int threads,

@@ -1050,7 +1050,10 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
 // first) and its warps pull warp chunks of the task from a shared counter; the
 // CTA's histograms are flushed when it moves to another integral.
 // ---------------------------------------------------------------------------
-template <int DMAX, bool EXACT, bool F64, int KIND>
+// (AX: the strata per axis from each integral's descriptor, for sets with
+// integrals whose strata differ between axes, §3.2; a separate instantiation
+// so that the other sets keep the one count in registers)
+template <int DMAX, bool EXACT, bool F64, int KIND, bool AX = false>
 __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
     typedef typename Real<F64>::T T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1069,6 +1072,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
     Ptrs P;
     const void *prm = nullptr;
     int bins = 0, sexp = 0;
+    const Strata *S = nullptr;
 
     auto flush_hist = [&]() {
         // each CTA starts at its own bin (in whole warps), so that the CTAs'
@@ -1093,6 +1097,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
         if (threadIdx.x == 0)  // every CTA of the integral writes the same
             st->hist_par = (t_it & 1u) | (__ldg(&dp->d_weighted) ? 2u : 0u);
         L = make_loop(dp, t_it);
+        if (AX) S = &dp->strata;
         sexp = F64 ? 0 : __ldcg(&st->scale_exp);  // (FP64: unscaled, as in k_sample_one)
         bins = L.dim * L.n_g;
         P.off = (const uint64_t *)__ldg((const unsigned long long *)&dp->off);
@@ -1155,8 +1160,8 @@ __global__ void __launch_bounds__(256, 2) k_sample_many(SampleArgs a) {
             const uint64_t h =
                 lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
             if (s0 < s1)
-                run_samples<DMAX, EXACT, F64, KIND, false, false>(  // (the same strata on every axis)
-                    L, nullptr, P, prm, s0, s1, h, lo_off, hi_off, hs, hs_t, hc,
+                run_samples<DMAX, EXACT, F64, KIND, false, AX>(
+                    L, S, P, prm, s0, s1, h, lo_off, hi_off, hs, hs_t, hc,
                     a.hist_shared ? kHistShared : kHistGlobal, sexp);
         }
     }
@@ -1286,10 +1291,11 @@ __host__ __device__ constexpr int bucket_dim(int b) {
     return b == 0 ? 4 : b == 1 ? 8 : b == 2 ? 12 : b == 3 ? 16 : b == 4 ? 20 : 24;
 }
 // Several integrals (tasks) / one integral (cluster launch of cs CTAs per cluster).
+// (ax: the task kernel with the strata per axis from the descriptors, §3.2)
 cudaError_t launch_sample_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, const SampleArgs &a);
+                              cudaStream_t s, const SampleArgs &a, bool ax = false);
 cudaError_t launch_sample_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, const SampleArgs &a);
+                              cudaStream_t s, const SampleArgs &a, bool ax = false);
 cudaError_t launch_sample_one_f32(int bucket, bool exact, int kind, dim3 grid, dim3 block,
                                   size_t smem, int cs, cudaStream_t s, const SampleOne &a);
 cudaError_t launch_sample_one_f64(int bucket, bool exact, int kind, dim3 grid, dim3 block,
@@ -1300,16 +1306,18 @@ cudaError_t launch_eval_f32(int bucket, bool exact, int kind, cudaStream_t s, co
 cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
                             int member, int64_t n, const uint64_t *h, const uint32_t *j,
                             uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
-cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem);
+cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem,
+                                   bool ax = false);
 // §4.2: the data histogram of the map's training (buffer buf; f NULL: the integrand).
 cudaError_t launch_precondition(int bucket, int kind, cudaStream_t s, const Desc *desc, int member,
                                 int64_t n, const double *x, const double *f, uint32_t buf);
 // (mo: the FP64 one-integral kernel with several outputs, App. B)
 cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem,
-                                   bool mo = false);
-int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem);
+                                   bool mo = false, bool ax = false);
+int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
+                         bool ax = false);
 int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
-                         bool mo = false);
+                         bool mo = false, bool ax = false);
 // Resident CTAs of the one-integral kernel with clusters of cs CTAs (0 if it cannot run).
 int sample_cluster_ctas_f32(int bucket, bool exact, int kind, int cs, int grid, int threads,
                             size_t smem);

@@ -206,7 +206,8 @@ static vp_status layout(vp_server *S) {
         S->h_axis[i + 1] = S->h_axis[i] + mb.p.dim;
         S->max_ng = std::max(S->max_ng, mb.p.n_g);
         if (mb.p.alpha > 0.0 && mb.p.n_g > 1) S->any_refine = true;
-        const bool exact = mb.exact && mb.p.precision == VP_FP32;  // FP64 kernels are guarded
+        // FP64 kernels are guarded; so is the per-axis form (strata that differ)
+        const bool exact = mb.exact && mb.p.precision == VP_FP32 && mb.uniform;
         S->slots[group_slot(mb.kind, mb.p.precision, mb.bucket, exact)].members.push_back(i);
     }
     S->n_tree_total = S->h_tree[n];
@@ -469,8 +470,6 @@ extern "C" vp_status vp_server_submit(vp_server *S, const vp_request *q, uint64_
     if (!r) return fail(VP_ENOMEM, "host allocation failed");
     vp_status st = validate(&q->p, &q->f, r->mb);
     if (st != VP_OK) return st;
-    if (!r->mb.uniform)  // served requests share task-kernel launches
-        return fail(VP_EINVAL, "served requests take the same strata on every axis");
     if (r->mb.n_out > 1) return fail(VP_EINVAL, "served requests take no extra outputs");
     if (!(q->rtol > 0.0 && std::isfinite(q->rtol))) return fail(VP_EINVAL, "rtol must be finite and > 0");
     if (q->discard < 0) return fail(VP_EINVAL, "discard must be >= 0");

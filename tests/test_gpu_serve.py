@@ -39,7 +39,7 @@ def oracle_of(prob):
     return oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
                             alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind,
                             prm=prob.prm, integral_id=prob.integral_id, plus2=prob.plus2,
-                            n_st=prob.n_st)
+                            n_st=prob.n_st, n_st_axis=prob.n_st_axis, mixed=prob.mixed)
 
 
 def stop_iteration(I, Vv, rtol, discard, min_meas, max_it):
@@ -111,6 +111,34 @@ def test_fp64_served_requests_match_the_oracle_and_its_stop_rule():
         assert r["mean"] == pytest.approx(ro["mean"], rel=1e-10), i
         assert r["sdev"] == pytest.approx(ro["sdev"], rel=1e-9), i
         assert r["status"] == V().VP_OK
+
+
+def test_fp64_served_requests_with_mixed_strata():
+    """Served requests with §3.2's mixed stratification (the D = 21 posteriors
+    at N_ev = 3e4 get 2^12 hypercubes instead of one) and explicit per-axis
+    strata, beside uniform ones: the same iterations and results as the
+    oracle's runs and stop rule."""
+    probs = requests(seed=8)
+    for k, p in enumerate(probs):
+        if p.dim == 21:
+            p.mixed = True
+        elif k == 0:
+            p.n_st_axis = (20, 3, 4)
+    max_it = 25
+    out, _ = serve(probs, V().VP_FP64, max_it=max_it)
+    for i, p in enumerate(probs):
+        r = out[i]
+        o = oracle_of(p)
+        if p.dim == 21:
+            assert o.n_hc == 2 ** 12
+        o.run(max_it)
+        t, conv = stop_iteration(np.array(o.I), np.array(o.var), max_it=max_it, **{
+            k: RULE[k] for k in ("rtol", "discard", "min_meas")})
+        assert r["n_iter"] == t, (i, r["n_iter"], t)
+        assert r["converged"] == conv, i
+        ro = oracle.combine(np.array(o.I[:t]), np.array(o.var[:t]), discard=RULE["discard"])
+        assert r["mean"] == pytest.approx(ro["mean"], rel=1e-10), i
+        assert r["sdev"] == pytest.approx(ro["sdev"], rel=1e-9), i
 
 
 def test_same_alone_and_in_the_mix():

@@ -222,29 +222,55 @@ def test_eq_mixed_fp32_close_to_closed_form(dim):
             assert err < -0.3 and abs(r["mean"] - prob.exact) > 5 * r["sdev"]
 
 
-def test_nonuniform_strata_rejected_where_unsupported():
-    rng = np.random.default_rng(1)
-    mixed = gauss_problem(4, rng, n_st_axis=(3, 2, 2, 2))
-    plain = gauss_problem(4, rng)
-    VE = V().VegasError
-    with pytest.raises(VE):  # several integrals share the task kernel
-        V().Batch([mixed, plain])
-    b = V().Batch([mixed])   # one integral: the one-integral kernel
+def test_batch_with_per_axis_strata_matches_oracle():
+    """Several integrals per launch (the task kernel's per-axis form): explicit
+    strata, the mixed rule at D = 12 and uniform strata side by side, FP64,
+    every integral's I_j and sigma_j^2 within 1e-10 of its own oracle run."""
+    rng = np.random.default_rng(21)
+    probs = [gauss_problem(5, rng, n_g=60, n_ev=4000, n_st_axis=(4, 3, 1, 2, 5)),
+             gauss_problem(5, rng, n_g=60, n_ev=6000),
+             gauss_problem(12, rng, n_g=40, n_ev=50_000, mixed=True)]
+    b = V().Batch(probs, precision=0)
+    os_ = [oracle_of(p) for p in probs]
+    for _ in range(5):
+        b.iterate(); b.adapt()
+        for o in os_:
+            o.iterate(); o.adapt()
+    for i, o in enumerate(os_):
+        I, Vv = b.history(i)
+        np.testing.assert_allclose(I[:5], o.I, rtol=1e-10, atol=0)
+        np.testing.assert_allclose(Vv[:5], o.var, rtol=1e-10, atol=0)
     b.close()
+
+
+def test_task_scheme_with_per_axis_strata():
+    """One integral (D = 5, not a kernel bucket's exact dimension) moved onto
+    the task scheme: the per-axis task kernel, within 1e-10 of the oracle."""
+    rng = np.random.default_rng(22)
+    prob = gauss_problem(5, rng, n_g=60, n_ev=300_000, n_st_axis=(9, 7, 1, 4, 5))
+    g = V().Integrator.from_problem(prob, precision=0)
+    g.set_tuning(1, 152)
+    o = oracle_of(prob)
+    for _ in range(3):
+        g.iterate(); g.adapt()
+        o.iterate(); o.adapt()
+    assert g.tuning()["scheme"] == "tasks"
+    I, Vv = g.history()
+    np.testing.assert_allclose(I[:3], o.I, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(Vv[:3], o.var, rtol=1e-10, atol=0)
+
+
+def test_per_axis_strata_refusals():
+    VE = V().VegasError
+    rng = np.random.default_rng(1)
     with pytest.raises(VE):
         V().Integrator.from_problem(gauss_problem(3, rng, n_st_axis=(2, 0, 2)))
-    g = V().Integrator.from_problem(gauss_problem(3, rng, n_ev=300_000, n_st_axis=(40, 30, 50)))
-    with pytest.raises(VE):  # the task scheme keeps one strata count
-        g.set_tuning(1, 152)
-    g.set_tuning(0, 152, 256, 1)
-    g.run(2)
-    many = inputs.Problem("k9", 3, inputs.GAUSS,
-                          inputs.gauss_blob([1.0] * 9, [0.2] * 9, [np.full(3, 0.5)] * 9),
-                          np.zeros(3), np.ones(3), n_g=20, n_ev=1000, n_st_axis=(2, 3, 2))
-    with pytest.raises(VE):  # FP32 with more peaks than the kernel parameters hold
+    # an FP32 integral with more peaks than the one-integral kernel holds, at an
+    # exact bucket dimension (D = 4): the task kernel's per-axis form has no
+    # exact-dimension instantiation
+    many = inputs.Problem("k9", 4, inputs.GAUSS,
+                          inputs.gauss_blob([1.0] * 9, [0.2] * 9, [np.full(4, 0.5)] * 9),
+                          np.zeros(4), np.ones(4), n_g=20, n_ev=1000, n_st_axis=(2, 3, 2, 2))
+    with pytest.raises(VE):
         V().Integrator.from_problem(many, precision=1)
     V().Integrator.from_problem(many, precision=0).run(1)
-    srv = V().Server()
-    with pytest.raises(VE):
-        srv.submit(mixed, rtol=1e-2)
-    srv.close()
