@@ -48,6 +48,10 @@ def lib():
         L.or_nstrat.restype = ctypes.c_int64
         L.or_nstrat_mixed.argtypes = [ctypes.c_int, ctypes.c_int64, _i64p]
         L.or_nstrat_mixed.restype = None
+        L.or_nstrat_div.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int]
+        L.or_nstrat_div.restype = ctypes.c_int64
+        L.or_nstrat_mixed_div.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _i64p]
+        L.or_nstrat_mixed_div.restype = None
         L.or_integrand.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p]
         L.or_integrand.restype = ctypes.c_double
         L.or_integrand_many.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, ctypes.c_int64, _f64p,
@@ -120,17 +124,18 @@ def philox4x32_10(ctr, key):
     return out
 
 
-def nstrat(dim, n_ev):
-    """§3 Eq. (Nst_vegasp) as an exact integer.  Pinned by brute force."""
-    return int(lib().or_nstrat(int(dim), int(n_ev)))
+def nstrat(dim, n_ev, div=4):
+    """§3 Eq. (Nst_vegasp) as an exact integer (div = 2: classic vegas's Eq.
+    Nst).  Pinned by brute force."""
+    return int(lib().or_nstrat_div(int(dim), int(n_ev), int(div)))
 
 
-def nstrat_mixed(dim, n_ev):
+def nstrat_mixed(dim, n_ev, div=4):
     """§3.2's variation: N_st + 1 strata on the first d axes, N_st on the rest,
     with the largest d that keeps at least 4 samples per hypercube.  Pinned by
     the counts the paper quotes for N_ev = 2.5e5 and 5e4 and by brute force."""
     out = np.zeros(int(dim), np.int64)
-    lib().or_nstrat_mixed(int(dim), int(n_ev), out)
+    lib().or_nstrat_mixed_div(int(dim), int(n_ev), int(div), out)
     return out
 
 
@@ -358,14 +363,17 @@ class VegasPlus:
     alternative of §3 Eq. nh), kind and prm (integrand family and blob), n_st
     (0: §3 Eq. Nst_vegasp; otherwise the stratification count to use on every
     axis), n_st_axis (explicit strata per axis, §3.2) and mixed (§3.2's
-    N_st / N_st + 1 rule in place of Eq. Nst_vegasp); out_mono lists extra
+    N_st / N_st + 1 rule in place of Eq. Nst_vegasp); nst_div 2 takes classic
+    vegas's Eq. Nst, floor((N_ev/2)^(1/D)), in place of the /4 of Eq.
+    Nst_vegasp (with beta = 0 that is classic vegas's stratified sampling, §3);
+    out_mono lists extra
     outputs f x^a x^b as pairs (a, b) (-1: no factor) integrated on the same
     samples (App. B), output 0 being f, which alone drives the adaptation.
     """
 
     def __init__(self, dim, lo, hi, n_g, n_ev, alpha, beta, seed, kind, prm,
                  integral_id=0, plus2=False, n_st=0, n_st_axis=None, mixed=False,
-                 out_mono=None, d_weighted=False):
+                 out_mono=None, d_weighted=False, nst_div=4):
         self.dim, self.n_g, self.n_ev = int(dim), int(n_g), int(n_ev)
         self.alpha, self.beta = float(alpha), float(beta)
         self.seed, self.integral_id, self.plus2 = int(seed), int(integral_id), bool(plus2)
@@ -385,9 +393,9 @@ class VegasPlus:
         elif n_st:
             self.nst_ax = np.full(self.dim, int(n_st), np.int64)
         elif mixed:
-            self.nst_ax = nstrat_mixed(self.dim, self.n_ev)
+            self.nst_ax = nstrat_mixed(self.dim, self.n_ev, nst_div)
         else:
-            self.nst_ax = np.full(self.dim, nstrat(self.dim, self.n_ev), np.int64)
+            self.nst_ax = np.full(self.dim, nstrat(self.dim, self.n_ev, nst_div), np.int64)
         self.n_st = int(self.nst_ax.min())
         self.n_hc = int(np.prod([int(s) for s in self.nst_ax]))
         self.omega = 1.0 / float(self.n_hc)

@@ -56,9 +56,10 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
 }
 
 /* ------------------------------------------------------------------------ */
-/* Stratification count, §3 Eq. (Nst_vegasp): N_st = floor((N_ev/4)^(1/D)).  */
-/* reading: evaluated exactly as the largest integer n >= 1 with 4 n^D <= N_ev */
-/* (the real power is only a starting guess).                                 */
+/* Stratification count, §3 Eq. (Nst_vegasp): N_st = floor((N_ev/4)^(1/D)),  */
+/* or classic vegas's §3 Eq. (Nst): floor((N_ev/2)^(1/D)) -- the divisor div.  */
+/* reading: evaluated exactly as the largest integer n >= 1 with               */
+/* div n^D <= N_ev (the real power is only a starting guess).                 */
 /* ------------------------------------------------------------------------ */
 static int or_pow_le(int64_t n, int d, int64_t limit) { /* 1 if n^d <= limit */
     int64_t p = 1;
@@ -69,14 +70,16 @@ static int or_pow_le(int64_t n, int d, int64_t limit) { /* 1 if n^d <= limit */
     return p <= limit;
 }
 
-int64_t or_nstrat(int dim, int64_t n_ev) {
-    if (dim < 1 || n_ev < 4) return 1;
-    int64_t n = (int64_t)floor(pow((double)n_ev / 4.0, 1.0 / (double)dim));
+int64_t or_nstrat_div(int dim, int64_t n_ev, int div) {
+    if (dim < 1 || n_ev < div) return 1;
+    int64_t n = (int64_t)floor(pow((double)n_ev / (double)div, 1.0 / (double)dim));
     if (n < 1) n = 1;
-    while (n > 1 && !or_pow_le(n, dim, n_ev / 4)) --n;
-    while (or_pow_le(n + 1, dim, n_ev / 4)) ++n;
+    while (n > 1 && !or_pow_le(n, dim, n_ev / div)) --n;
+    while (or_pow_le(n + 1, dim, n_ev / div)) ++n;
     return n;
 }
+
+int64_t or_nstrat(int dim, int64_t n_ev) { return or_nstrat_div(dim, n_ev, 4); }
 
 /* ------------------------------------------------------------------------ */
 /* §3.2 (Limitations and a Variation): the mixed stratification -- N_st + 1   */
@@ -84,9 +87,9 @@ int64_t or_nstrat(int dim, int64_t n_ev) {
 /* Eq. (Nst_vegasp) and d the largest value that still allows 4 samples per   */
 /* hypercube, i.e. 4 (N_st + 1)^d N_st^(D - d) <= N_ev (exact integers).       */
 /* ------------------------------------------------------------------------ */
-void or_nstrat_mixed(int dim, int64_t n_ev, int64_t *nst_ax) {
-    const int64_t n = or_nstrat(dim, n_ev);
-    const int64_t limit = n_ev / 4;
+void or_nstrat_mixed_div(int dim, int64_t n_ev, int div, int64_t *nst_ax) {
+    const int64_t n = or_nstrat_div(dim, n_ev, div);
+    const int64_t limit = n_ev / div;
     int d = 0;
     for (int k = 1; k <= dim; ++k) { /* largest k with (n+1)^k n^(dim-k) <= N_ev/4 */
         int64_t p = 1;
@@ -100,6 +103,10 @@ void or_nstrat_mixed(int dim, int64_t n_ev, int64_t *nst_ax) {
         else break;
     }
     for (int mu = 0; mu < dim; ++mu) nst_ax[mu] = mu < d ? n + 1 : n;
+}
+
+void or_nstrat_mixed(int dim, int64_t n_ev, int64_t *nst_ax) {
+    or_nstrat_mixed_div(dim, n_ev, 4, nst_ax);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -76,6 +76,27 @@ def test_nstrat_brute_force():
     assert oracle.nstrat(21, 8_388_607) == 1 and oracle.nstrat(21, 8_388_608) == 2
 
 
+def test_classic_nstrat_and_equal_split():
+    """§3 Eq. (Nst) of classic vegas: N_st = floor((N_ev/2)^(1/D)), the largest
+    n with 2 n^D <= N_ev (brute force), and with beta = 0 every hypercube gets
+    n_ev = floor(N_ev / N_st^D) >= 2 samples."""
+    for dim in range(1, 16):
+        for n_ev in [1, 2, 3, 4, 7, 8, 63, 64, 65, 1000, 10_000, 2 * 3 ** 9, 2 * 3 ** 9 - 1,
+                     10 ** 6, 2 ** 31 - 1]:
+            n = oracle.nstrat(dim, n_ev, div=2)
+            assert n >= 1
+            assert n == 1 or 2 * n ** dim <= n_ev, (dim, n_ev)
+            assert 2 * (n + 1) ** dim > n_ev, (dim, n_ev)
+            assert n >= oracle.nstrat(dim, n_ev)
+    o = oracle.VegasPlus(dim=3, lo=0.0, hi=1.0, n_g=10, n_ev=10_000, alpha=0.5, beta=0.0,
+                         seed=1, kind=0, prm=inputs.gauss_blob([1.0], [0.3], [np.full(3, 0.5)]),
+                         nst_div=2)
+    assert o.n_st == 17 and o.n_hc == 17 ** 3  # 2 * 17^3 = 9826 <= 1e4 < 2 * 18^3
+    for _ in range(3):
+        o.iterate(); o.adapt()
+        assert np.all(o.n_h == 10_000 // 17 ** 3)
+
+
 def test_nstrat_mixed_paper_counts_and_brute_force():
     """§3.2: N_st + 1 strata on the first d axes and N_st on the rest, d the
     largest that keeps 4 samples per hypercube.  The paper quotes d = 15,
