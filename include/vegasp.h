@@ -129,6 +129,12 @@ typedef struct {
                            since d is normalised), an estimate of the slab integral of
                            J^2 f^2 whatever the allocation (§3: the optimal map does not
                            depend on it) */
+    int nst_div;        /* the divisor of the strata rule when n_st == 0: 0 or 4 =
+                           vegas+'s §3 Eq. Nst_vegasp, floor((N_ev/4)^(1/D)) (and the
+                           mixed rule's 4 samples per hypercube); 2 = classic vegas's
+                           §3 Eq. Nst, floor((N_ev/2)^(1/D)), which with beta = 0 is
+                           classic vegas's stratified sampling (§3: n_ev =
+                           floor(N_ev/N_st^D) >= 2 samples per hypercube) */
 } vp_params;
 
 typedef struct {

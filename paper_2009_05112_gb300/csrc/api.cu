@@ -146,17 +146,19 @@ static void div_magic(uint32_t d, uint32_t *magic, int *shift) {
 }
 
 // floor((N_ev/4)^(1/D)) as the largest n >= 1 with 4 n^D <= N_ev.
-static int64_t nstrat_exact(int dim, int64_t n_ev) {
+// floor((N_ev/div)^(1/D)) as the largest n >= 1 with div n^D <= N_ev: div = 4
+// is §3 Eq. (Nst_vegasp), div = 2 classic vegas's §3 Eq. (Nst).
+static int64_t nstrat_exact(int dim, int64_t n_ev, int div) {
     auto fits = [&](int64_t n) {
-        int64_t lim = n_ev / 4, p = 1;
+        int64_t lim = n_ev / div, p = 1;
         for (int i = 0; i < dim; ++i) {
             if (p > lim / n) return false;
             p *= n;
         }
         return p <= lim;
     };
-    if (n_ev < 4) return 1;
-    int64_t n = (int64_t)std::floor(std::pow((double)n_ev / 4.0, 1.0 / (double)dim));
+    if (n_ev < div) return 1;
+    int64_t n = (int64_t)std::floor(std::pow((double)n_ev / (double)div, 1.0 / (double)dim));
     if (n < 1) n = 1;
     while (n > 1 && !fits(n)) --n;
     while (fits(n + 1)) ++n;
@@ -166,8 +168,8 @@ static int64_t nstrat_exact(int dim, int64_t n_ev) {
 // §3.2's mixed stratification: N_st + 1 strata on the first d axes, N_st on
 // the others, N_st from Eq. (Nst_vegasp) and d the largest value with
 // 4 (N_st + 1)^d N_st^(D - d) <= N_ev (integer arithmetic throughout).
-static void nstrat_mixed_exact(int dim, int64_t n_ev, std::vector<int64_t> &out) {
-    const int64_t n = nstrat_exact(dim, n_ev), cap = n_ev / 4;
+static void nstrat_mixed_exact(int dim, int64_t n_ev, int div, std::vector<int64_t> &out) {
+    const int64_t n = nstrat_exact(dim, n_ev, div), cap = n_ev / div;
     auto prod_fits = [&](int d) {  // (n + 1)^d n^(dim - d) <= cap
         int64_t p = 1;
         for (int mu = 0; mu < dim; ++mu) {
@@ -201,6 +203,8 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
         for (int i = 0; i < p->dim; ++i)
             if (p->n_st_axis[i] < 1) return fail(VP_EINVAL, "n_st_axis[%d] must be >= 1", i);
     if (p->d_weighted != 0 && p->d_weighted != 1) return fail(VP_EINVAL, "d_weighted must be 0 or 1");
+    if (p->nst_div != 0 && p->nst_div != 2 && p->nst_div != 4)
+        return fail(VP_EINVAL, "nst_div must be 0, 2 or 4");
     if (p->n_extra < 0 || p->n_extra > kMaxOut - 1)
         return fail(VP_EINVAL, "n_extra outside 0..%d", kMaxOut - 1);
     if (p->n_extra > 0) {
@@ -260,9 +264,9 @@ vp_status vp::validate(const vp_params *p, const vp_integrand *f, Member &mb) {
     else if (p->n_st > 0)
         mb.nst_ax.assign(D, p->n_st);
     else if (p->mixed)
-        nstrat_mixed_exact(D, p->n_ev, mb.nst_ax);
+        nstrat_mixed_exact(D, p->n_ev, p->nst_div ? p->nst_div : 4, mb.nst_ax);
     else
-        mb.nst_ax.assign(D, nstrat_exact(D, p->n_ev));
+        mb.nst_ax.assign(D, nstrat_exact(D, p->n_ev, p->nst_div ? p->nst_div : 4));
     mb.n_st = *std::min_element(mb.nst_ax.begin(), mb.nst_ax.end());
     mb.uniform = *std::max_element(mb.nst_ax.begin(), mb.nst_ax.end()) == mb.n_st;
     // N_h = prod_mu s_mu <= 2^31

@@ -47,6 +47,7 @@ class Problem:
     n_st_axis: tuple = None  # strata per axis (§3.2); overrides n_st
     mixed: bool = False      # §3.2's mixed N_st / N_st + 1 rule in place of Eq. (Nst_vegasp)
     d_weighted: bool = False # the grid's d_i from samples weighted by 1/n_h
+    nst_div: int = 0         # 2: classic vegas's Eq. (Nst) in place of Eq. (Nst_vegasp)
 
 
 def _blob(rows):

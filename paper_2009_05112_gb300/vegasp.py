@@ -40,7 +40,8 @@ class vp_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("plus2", ctypes.c_int), ("n_st", ctypes.c_int),
                 ("max_it", ctypes.c_int), ("n_st_axis", ctypes.POINTER(ctypes.c_int32)),
                 ("mixed", ctypes.c_int), ("n_extra", ctypes.c_int),
-                ("out_mono", ctypes.POINTER(ctypes.c_int32)), ("d_weighted", ctypes.c_int)]
+                ("out_mono", ctypes.POINTER(ctypes.c_int32)), ("d_weighted", ctypes.c_int),
+                ("nst_div", ctypes.c_int)]
 
 
 class vp_integrand(ctypes.Structure):
@@ -210,7 +211,8 @@ class Integrator:
 
     def __init__(self, dim, lo, hi, kind, prm, n_g=1000, n_ev=10_000, alpha=0.5, beta=0.75,
                  seed=0, integral_id=0, precision=VP_FP64, plus2=False, n_st=0, max_it=0,
-                 stream=None, n_st_axis=None, mixed=False, out_mono=None, d_weighted=False):
+                 stream=None, n_st_axis=None, mixed=False, out_mono=None, d_weighted=False,
+                 nst_div=0):
         self.dim, self.n_g = int(dim), int(n_g)
         self._lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, np.float64), (self.dim,)))
         self._hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, np.float64), (self.dim,)))
@@ -225,6 +227,7 @@ class Integrator:
             p.n_st_axis = self._nst.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         p.mixed = int(bool(mixed))
         p.d_weighted = int(bool(d_weighted))
+        p.nst_div = int(nst_div)
         self.n_out = 1
         if out_mono:  # extra outputs f x^a x^b (App. B)
             self._mono = np.ascontiguousarray(np.asarray(out_mono, np.int32).reshape(-1))
@@ -245,7 +248,7 @@ class Integrator:
                     n_g=prob.n_g, n_ev=prob.n_ev, alpha=prob.alpha, beta=prob.beta,
                     seed=prob.seed, integral_id=prob.integral_id, precision=precision,
                     plus2=prob.plus2, n_st=prob.n_st, n_st_axis=prob.n_st_axis,
-                    mixed=prob.mixed, d_weighted=prob.d_weighted)
+                    mixed=prob.mixed, d_weighted=prob.d_weighted, nst_div=prob.nst_div)
         args.update(kw)
         return cls(**args)
 
@@ -522,6 +525,7 @@ def _set_strata(p, prob, keep):
         p.n_st_axis = a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     p.mixed = int(bool(getattr(prob, "mixed", False)))
     p.d_weighted = int(bool(getattr(prob, "d_weighted", False)))
+    p.nst_div = int(getattr(prob, "nst_div", 0))
 
 
 def clock():

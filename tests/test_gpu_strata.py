@@ -274,3 +274,23 @@ def test_per_axis_strata_refusals():
     with pytest.raises(VE):
         V().Integrator.from_problem(many, precision=1)
     V().Integrator.from_problem(many, precision=0).run(1)
+
+
+def test_classic_vegas_stratification_matches_oracle():
+    """Classic vegas's §3 Eq. (Nst), floor((N_ev/2)^(1/D)), with beta = 0: 17^3
+    hypercubes at D = 3, N_ev = 1e4, each with floor(N_ev/N_st^D) = 2 samples,
+    five FP64 iterations within 1e-10 of the oracle."""
+    rng = np.random.default_rng(30)
+    prob = gauss_problem(3, rng, n_g=50, n_ev=10_000, nst_div=2)
+    prob.beta = 0.0
+    g = V().Integrator.from_problem(prob, precision=0)
+    o = oracle_of(prob, nst_div=2)
+    assert g.n_st == o.n_st == 17 and g.n_hc == 17 ** 3
+    for _ in range(5):
+        g.iterate(); g.adapt()
+        o.iterate(); o.adapt()
+        n_h, _ = g.alloc()
+        assert np.array_equal(n_h, o.n_h) and np.all(n_h == 2)
+    I, Vv = g.history()
+    np.testing.assert_allclose(I[:5], o.I, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(Vv[:5], o.var, rtol=1e-10, atol=0)
