@@ -241,6 +241,21 @@ vp_status vp_get_moments_multi(vp_ctx *ctx, double *x1, double *x2);
  * (§4.2).  Synchronises `stream`. */
 vp_status vp_precondition(vp_ctx *ctx, int64_t n, const double *x, const double *f, int n_iter,
                           void *stream);
+
+/* Checkpoint / resume.  The state of a context between iterations -- the FP64
+ * grid, the allocation n_h and its offsets, the iteration count t (Philox
+ * counter word 2), the scale of the FP32 path, the running totals and the
+ * iteration history (and that of the extra outputs) -- as a byte blob, host
+ * memory.  vp_export_state: *size receives the blob's size; with buf non-NULL
+ * and cap >= *size the blob is written (else VP_EINVAL); synchronises the
+ * context's last stream.  vp_import_state: into a context created with the
+ * same parameters (dimension, N_g, N_ev, strata, seed, integral_id, integrand
+ * kind, precision, outputs, history capacity; else VP_EINVAL, the context
+ * unchanged), which then continues as the exporting one would: the samples
+ * are counter-based, so the following iterations draw the same points and
+ * agree with the uninterrupted run to FP rounding of the reductions. */
+vp_status vp_export_state(vp_ctx *ctx, void *buf, size_t cap, size_t *size);
+vp_status vp_import_state(vp_ctx *ctx, const void *buf, size_t size);
 /* edges[D][N_g + 1] (FP64 master grid) */
 vp_status vp_get_edges(vp_ctx *ctx, double *edges);
 /* replaces the grid (edges[D][N_g+1], strictly increasing, ends = box) */

@@ -1528,6 +1528,145 @@ extern "C" vp_status vp_set_edges(vp_ctx *c, const double *edges) {
     return VP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: a context's state between iterations as a byte blob.
+// Layout: CkptHeader, State, edges [D][N_g + 1] f64, n_h [N_h] u32, offsets
+// [N_h + 1] u64, I_j and sigma_j^2 [hist_cap] f64 each, and with extra outputs
+// their history [hist_cap][M] and [hist_cap][M(M+1)/2] f64.
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];          // "vpstate1"
+    uint32_t state_bytes;   // sizeof(State) of the build that wrote it
+    int32_t dim, n_g, kind, prec, n_out, hist_cap, pad;
+    int64_t n_ev;
+    uint64_t n_hc, seed;
+    uint32_t integral_id;
+    int32_t strata[kMaxDim];
+};
+
+size_t ckpt_bytes(const Desc &d) {
+    const size_t M = d.n_out > 1 ? (size_t)d.n_out : 0, T = M * (M + 1) / 2;
+    return sizeof(CkptHeader) + sizeof(State) + (size_t)d.dim * (d.n_g + 1) * 8 + d.n_hc * 4 +
+           (d.n_hc + 1) * 8 + (size_t)d.hist_cap * 16 + (size_t)d.hist_cap * (M + T) * 8;
+}
+
+CkptHeader ckpt_header(const Member &mb, const Desc &d) {
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "vpstate1", 8);
+    h.state_bytes = (uint32_t)sizeof(State);
+    h.dim = d.dim;
+    h.n_g = d.n_g;
+    h.kind = d.kind;
+    h.prec = d.prec;
+    h.n_out = d.n_out;
+    h.hist_cap = d.hist_cap;
+    h.n_ev = d.n_ev;
+    h.n_hc = d.n_hc;
+    h.seed = mb.p.seed;
+    h.integral_id = d.integral_id;
+    for (int mu = 0; mu < d.dim; ++mu) h.strata[mu] = (int32_t)mb.nst_ax[mu];
+    return h;
+}
+}  // namespace
+
+extern "C" vp_status vp_export_state(vp_ctx *c, void *buf, size_t cap, size_t *size) {
+    CHECK_CTX(c);
+    if (!size) return fail(VP_EINVAL, "NULL size");
+    Set &s = c->set;
+    const Desc &d = s.h_desc[0];
+    const size_t need = ckpt_bytes(d);
+    *size = need;
+    if (!buf) return VP_OK;
+    if (cap < need) return fail(VP_EINVAL, "buffer of %zu bytes, the state needs %zu", cap, need);
+    CU(cudaStreamSynchronize(s.last));
+    char *p = (char *)buf;
+    const CkptHeader h = ckpt_header(s.m[0], d);
+    memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    CU(cudaMemcpy(p, d.st, sizeof(State), cudaMemcpyDeviceToHost));
+    p += sizeof(State);
+    const size_t ne = (size_t)d.dim * (d.n_g + 1) * 8;
+    CU(cudaMemcpy(p, d.edges, ne, cudaMemcpyDeviceToHost));
+    p += ne;
+    CU(cudaMemcpy(p, d.n_h, d.n_hc * 4, cudaMemcpyDeviceToHost));
+    p += d.n_hc * 4;
+    CU(cudaMemcpy(p, d.off, (d.n_hc + 1) * 8, cudaMemcpyDeviceToHost));
+    p += (d.n_hc + 1) * 8;
+    CU(cudaMemcpy(p, d.hist_i, (size_t)d.hist_cap * 8, cudaMemcpyDeviceToHost));
+    p += (size_t)d.hist_cap * 8;
+    CU(cudaMemcpy(p, d.hist_var, (size_t)d.hist_cap * 8, cudaMemcpyDeviceToHost));
+    p += (size_t)d.hist_cap * 8;
+    if (d.n_out > 1) {
+        const size_t M = (size_t)d.n_out, T = M * (M + 1) / 2;
+        CU(cudaMemcpy(p, d.hist_im, (size_t)d.hist_cap * M * 8, cudaMemcpyDeviceToHost));
+        p += (size_t)d.hist_cap * M * 8;
+        CU(cudaMemcpy(p, d.hist_cm, (size_t)d.hist_cap * T * 8, cudaMemcpyDeviceToHost));
+    }
+    return VP_OK;
+}
+
+extern "C" vp_status vp_import_state(vp_ctx *c, const void *buf, size_t size) {
+    CHECK_CTX(c);
+    if (!buf) return fail(VP_EINVAL, "NULL buffer");
+    Set &s = c->set;
+    const Desc &d = s.h_desc[0];
+    const Member &mb = s.m[0];
+    if (size != ckpt_bytes(d)) return fail(VP_EINVAL, "state of %zu bytes, this context's is %zu", size, ckpt_bytes(d));
+    const CkptHeader want = ckpt_header(mb, d);
+    CkptHeader got;
+    memcpy(&got, buf, sizeof got);
+    if (memcmp(&want, &got, sizeof got) != 0)
+        return fail(VP_EINVAL, "the state was written by a context of other parameters");
+    const char *p = (const char *)buf + sizeof(CkptHeader);
+    State st;
+    memcpy(&st, p, sizeof st);
+    p += sizeof(State);
+    const size_t ne = (size_t)d.dim * (d.n_g + 1) * 8;
+    const double *edges = (const double *)p;
+    for (int mu = 0; mu < d.dim; ++mu) {  // the grid as vp_set_edges checks it
+        const double *e = edges + (size_t)mu * (d.n_g + 1);
+        if (e[0] != mb.lo[mu] || e[d.n_g] != mb.hi[mu]) return fail(VP_EINVAL, "grid ends must equal the box");
+        for (int k = 0; k < d.n_g; ++k)
+            if (!(e[k + 1] > e[k])) return fail(VP_EINVAL, "grid must be strictly increasing");
+    }
+    std::vector<float2> tab((size_t)d.dim * d.n_g);
+    for (int mu = 0; mu < d.dim; ++mu)
+        make_tab(edges + (size_t)mu * (d.n_g + 1), d.n_g, &tab[(size_t)mu * d.n_g]);
+    CU(cudaStreamSynchronize(s.last));
+    CU(cudaMemcpy(d.edges, edges, ne, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(d.tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice));
+    p += ne;
+    CU(cudaMemcpy(d.n_h, p, d.n_hc * 4, cudaMemcpyHostToDevice));
+    p += d.n_hc * 4;
+    CU(cudaMemcpy(d.off, p, (d.n_hc + 1) * 8, cudaMemcpyHostToDevice));
+    p += (d.n_hc + 1) * 8;
+    CU(cudaMemcpy(d.hist_i, p, (size_t)d.hist_cap * 8, cudaMemcpyHostToDevice));
+    p += (size_t)d.hist_cap * 8;
+    CU(cudaMemcpy(d.hist_var, p, (size_t)d.hist_cap * 8, cudaMemcpyHostToDevice));
+    p += (size_t)d.hist_cap * 8;
+    const size_t M = d.n_out > 1 ? (size_t)d.n_out : 0, T = M * (M + 1) / 2;
+    if (M) {
+        CU(cudaMemcpy(d.hist_im, p, (size_t)d.hist_cap * M * 8, cudaMemcpyHostToDevice));
+        p += (size_t)d.hist_cap * M * 8;
+        CU(cudaMemcpy(d.hist_cm, p, (size_t)d.hist_cap * T * 8, cudaMemcpyHostToDevice));
+    }
+    // both buffers of the per-iteration sums clear (either parity may come next)
+    const size_t bins = (size_t)d.dim * d.n_g;
+    CU(cudaMemset(d.s1, 0, 2 * d.n_hc * 8));
+    CU(cudaMemset(d.s2, 0, 2 * d.n_hc * 8));
+    CU(cudaMemset(d.hsum, 0, 2 * bins * 8));
+    CU(cudaMemset(d.hcnt, 0, 2 * bins * 4));
+    if (M) {
+        CU(cudaMemset(d.x1, 0, 2 * d.n_hc * M * 8));
+        CU(cudaMemset(d.x2, 0, 2 * d.n_hc * T * 8));
+    }
+    st.done_est = st.done_alloc = st.done_multi = 0u;
+    CU(cudaMemcpy(d.st, &st, sizeof st, cudaMemcpyHostToDevice));
+    return VP_OK;
+}
+
 extern "C" vp_status vp_get_alloc(vp_ctx *c, uint32_t *n_h, uint64_t *offsets) {
     CHECK_CTX(c);
     const Desc &d = c->set.h_desc[0];

@@ -101,6 +101,8 @@ _SIGS = {
                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "vp_get_moments_multi": [_P, _P, _P],
     "vp_precondition": [_P, ctypes.c_int64, _P, _P, ctypes.c_int, _P],
+    "vp_export_state": [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "vp_import_state": [_P, _P, ctypes.c_size_t],
     "vp_get_edges": [_P, _P],
     "vp_set_edges": [_P, _P],
     "vp_get_alloc": [_P, _P, _P],
@@ -339,6 +341,19 @@ class Integrator:
         fa = None if f is None else np.ascontiguousarray(f, np.float64).reshape(-1)
         check(lib().vp_precondition(self.ctx, x.shape[0], _ptr(x), _ptr(fa), int(n_iter),
                                     self.stream))
+        return self
+
+    def export_state(self):
+        """The context's state between iterations (bytes), for vp_import_state."""
+        n = ctypes.c_size_t()
+        check(lib().vp_export_state(self.ctx, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        check(lib().vp_export_state(self.ctx, buf, n.value, ctypes.byref(n)))
+        return buf.raw
+
+    def import_state(self, blob):
+        """Resumes from a state written by export_state (same parameters)."""
+        check(lib().vp_import_state(self.ctx, blob, len(blob)))
         return self
 
     def strata(self):
