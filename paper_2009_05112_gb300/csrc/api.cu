@@ -1029,6 +1029,7 @@ static vp_status join_refine(Set &s, cudaStream_t stream) {
 }
 
 static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = false) {
+    NvtxRange nv("vp.iterate");
     const int n = (int)s.m.size();
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing(stream, &cap));
@@ -1067,6 +1068,7 @@ static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = fals
 }
 
 static vp_status set_adapt(Set &s, cudaStream_t stream, bool refine_forked = false) {
+    NvtxRange nv("vp.adapt");
     const int n = (int)s.m.size();
     if (s.any_refine && !refine_forked) {
         vp_status st = fork_refine(s, stream);
@@ -1082,6 +1084,7 @@ static vp_status set_adapt(Set &s, cudaStream_t stream, bool refine_forked = fal
 }
 
 static vp_status set_step(Set &s, cudaStream_t stream) {
+    NvtxRange nv("vp.step");
     bool due = false;
     for (auto &g : s.groups) due |= tune_due(s, g);
     if (due && s.gexec) {  // a new launch shape: capture the step again
@@ -1779,6 +1782,7 @@ extern "C" vp_status vp_refine_from_hist(vp_ctx *c, const double *hsum, const do
 extern "C" vp_status vp_precondition(vp_ctx *c, int64_t n, const double *x, const double *f,
                                      int n_iter, void *stream) {
     CHECK_CTX(c);
+    NvtxRange nv("vp.precondition");
     Set &s = c->set;
     const Member &mb = s.m[0];
     const Desc &d = s.h_desc[0];

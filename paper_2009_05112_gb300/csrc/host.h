@@ -11,7 +11,18 @@
 #include "sample_impl.cuh"
 #include "vp_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace vp {
+
+// A named NVTX range over a host call (shown by profilers; free otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 // kernel launchers (adapt.cu)
 cudaError_t launch_chunks(const Desc *, const uint32_t *, int, uint64_t *, uint32_t *, uint32_t,

@@ -289,6 +289,7 @@ static vp_status retire(vp_server *S) {
 
 static vp_status server_step(vp_server *S, int *n_active) {
     std::lock_guard<std::mutex> step_lock(S->step_mu);
+    NvtxRange nv("vp.server_step");
     const double t0 = now_s();
     cudaStream_t st = S->stream;
     vp_status rs = admit(S);
