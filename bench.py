@@ -234,7 +234,33 @@ def cpu_baseline(prob, seconds=12.0, out_mono=None, data=None):
     return {"value": evals / el, "unit": "integrand evals/s", "cores": 1, "kind": "oracle",
             "sample": "%d whole iterations (%s, N_ev=%d, D=%d, N_g=%d) of the FP64 C "
                       "oracle, single thread, %.1f s" % (its, prob.name, prob.n_ev, prob.dim,
-                                                         prob.n_g, el)}
+                                                         prob.n_g, el),
+            "host": host_cpu()}
+
+
+def host_cpu():
+    """The host's CPU as the system reports it: lscpu's model name (or
+    /proc/cpuinfo's), the machine type and the logical CPU count."""
+    import platform
+    import subprocess
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"model": model, "machine": platform.machine(), "nproc": os.cpu_count()}
 
 
 def _oracle_worker(job):
@@ -352,7 +378,8 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": "integrand evals/s", "cores": 1,
                              "kind": "oracle",
                              "sample": "%d whole iterations (N_ev=1e6) after %d warm-up, "
-                                       "single thread" % (args.steps, args.warmup)},
+                                       "single thread" % (args.steps, args.warmup),
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": "integrand evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
