@@ -9,7 +9,7 @@ and refinement in FP64.  A step is one vp_step: sampling (a1-a5), estimate
 (a6), reallocation (a7) and grid refinement (a8), replayed from a CUDA graph.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on the host cores instead (the reference arm of this build).
+on the host cores instead (the reference arm).
 
 Multi-GPU (torchrun): one independent integral per rank (distinct Philox
 counter word 3), no collective on the data path; value = all ranks' integrand

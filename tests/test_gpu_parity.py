@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
 
-Bars (stated in the design doc and here):
+Bars:
 * integer work -- n_h, offsets, increment indices -- bit-exact;
 * FP64 path: the map x(y), J(y) bit-exact (same IEEE sequence), f within 1e-14
   (CUDA's exp vs the host's), per-hypercube moments and histograms within
@@ -386,6 +386,45 @@ def test_ball_d20_full_size_sampled(precision):
         elif not (abs(s1[h] - a) <= 1e-5 * abs(a) + 1e-30):
             bad += 1  # a sample within FP32 rounding of the sphere
     assert bad <= 3
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_four_peaks_d8_full_size_sampled(precision):
+    """The 8-D four-peak workload at full size (N_ev = 1e6, 65,536 hypercubes)
+    in the launch shape the library tunes for it, on a shared seeded grid:
+    properties at any size (counts, the histograms' totals, I_j from the
+    moments), then 400 hypercubes' moments recomputed one by one by the oracle
+    -- the 200 that carry the most of the integral and 200 drawn at random.
+    FP64 within 1e-12; FP32 within 1e-4 relative (the exponent's rounding,
+    A 2^-24 for f = e^-A) plus 1e-10 of the largest hypercube's sum."""
+    prob = inputs.four_peaks_d8()
+    rng = np.random.default_rng(8)
+    g = gpu_of(prob, precision)
+    o = oracle_of(prob)
+    assert g.n_hc == 4 ** 8 and o.n_st == 4
+    e = random_grid(rng, prob.lo, prob.hi, prob.n_g)
+    g.set_edges(e)
+    o.edges = np.ascontiguousarray(e)
+    g.iterate()
+    n_h, off = g.alloc()
+    assert np.all(n_h == 15) and int(off[-1]) == 15 * 4 ** 8
+    s1, s2 = g.moments()
+    hs, hc = g.hist()
+    assert np.all(hc.sum(axis=1) == off[-1])
+    np.testing.assert_allclose(hs.sum(axis=1), s2.sum(), rtol=1e-6 if precision else 1e-12)
+    I, _ = g.history()
+    np.testing.assert_allclose(I[0], (s1 / n_h).sum() / 4 ** 8, rtol=1e-9)
+    top = np.argsort(s1)[::-1][:200]
+    picks = np.concatenate([top, rng.integers(0, 4 ** 8, 200)])
+    big = float(s1.max())
+    for h in picks:
+        a, b = o.hcube_moments(0, int(h), int(n_h[h]))
+        if precision == 0:
+            assert s1[h] == pytest.approx(a, rel=1e-12, abs=1e-300)
+            assert s2[h] == pytest.approx(b, rel=1e-12, abs=1e-300)
+        else:
+            assert abs(s1[h] - a) <= 1e-4 * abs(a) + 1e-10 * big, (h, s1[h], a)
+            assert abs(s2[h] - b) <= 2e-4 * abs(b) + 1e-10 * big * big, (h, s2[h], b)
 
 
 def test_ball_d20_result_matches_volume():
