@@ -118,8 +118,10 @@ typedef struct {
        -1..D-1 (-1: that factor is 1): the means and second moments of the
        paper's Bayesian example.  Every iteration then also records the
        estimates of all M = n_extra + 1 outputs and their covariance, summed
-       over hypercubes (§2.1 Eq. sigest in several variables).  FP64 only, one
-       integral per context, at most 2^22 hypercubes, n_extra <= 7. */
+       over hypercubes (§2.1 Eq. sigest in several variables).  FP64 only, at
+       most 2^22 hypercubes, n_extra <= 7; contexts and batches (in a batch
+       such an integral is sampled by a launch of its own), not served
+       requests. */
     int n_extra;
     const int32_t *out_mono; /* [2 n_extra] (copied) */
     int d_weighted;     /* the grid's d_i^mu (§2.3, §2.4): 0 = the mean of (J f)^2 over
@@ -322,6 +324,12 @@ vp_status vp_batch_results(vp_batch *b, int discard, vp_result_t *out);
 vp_status vp_batch_size(vp_batch *b, int *n);
 /* I_j and sigma_j^2 of the first n iterations of integral i */
 vp_status vp_batch_history(vp_batch *b, int i, int n, double *i_j, double *var_j);
+/* Integral i's several outputs (App. B), as vp_result_multi and
+ * vp_get_history_multi; VP_EINVAL for an integral without extra outputs or
+ * an index out of range. */
+vp_status vp_batch_result_multi(vp_batch *b, int i, int discard, double *mean, double *cov,
+                                double *chi2, int *dof, int *n_it);
+vp_status vp_batch_history_multi(vp_batch *b, int i, int n, double *i_j, double *cov_j);
 vp_status vp_batch_destroy(vp_batch *b);
 
 /* ---- serving: a stream of integration requests ------------------------------ */

@@ -353,7 +353,10 @@ static vp_status plan_groups(Set &s) {
             std::max(merged_bucket[mb.kind][mb.p.precision], mb.bucket);
     for (uint32_t i = 0; i < s.m.size(); ++i) {
         const Member &mb = s.m[i];
-        const int bucket = s.merge ? merged_bucket[mb.kind][mb.p.precision] : mb.bucket;
+        // several outputs (App. B): a group of its own, served by the FP64
+        // one-integral kernel that sums them
+        const bool solo = mb.n_out > 1;
+        const int bucket = s.merge && !solo ? merged_bucket[mb.kind][mb.p.precision] : mb.bucket;
         // FP64 kernels are guarded; so is the task kernel's per-axis form
         // (several integrals with strata that differ between axes)
         bool exact = mb.exact && mb.p.precision == VP_FP32 && (mb.uniform || s.m.size() == 1);
@@ -366,7 +369,7 @@ static vp_status plan_groups(Set &s) {
         }
         Group *g = nullptr;
         for (auto &q : s.groups)
-            if (q.bucket == bucket && q.exact == exact && q.kind == mb.kind &&
+            if (!solo && !q.solo && q.bucket == bucket && q.exact == exact && q.kind == mb.kind &&
                 q.prec == mb.p.precision)
                 g = &q;
         if (!g) {
@@ -376,6 +379,7 @@ static vp_status plan_groups(Set &s) {
             g->exact = exact;
             g->kind = mb.kind;
             g->prec = mb.p.precision;
+            g->solo = solo;
         }
         g->members.push_back(i);
     }
@@ -398,8 +402,8 @@ static vp_status plan_groups(Set &s) {
         // one-integral kernel, and the task scheme is then not offered)
         g.mo = false;
         for (uint32_t i : g.members) g.mo = g.mo || s.m[i].n_out > 1;
-        if (g.mo && !g.one)  // several outputs (App. B): the FP64 one-integral kernel sums them
-            return fail(VP_EINVAL, "several outputs: one integral per context");
+        if (g.mo && !g.one)  // (not reached: such a member has a group of its own)
+            return fail(VP_EINVAL, "several outputs: one integral per launch group");
         if (!g.uniform && g.exact && !g.one)
             return fail(VP_EINVAL, "strata that differ between axes: FP32 peaks at most %d",
                         kParamPeaks);
@@ -1056,8 +1060,9 @@ static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = fals
         s.timed = true;
     }
     if (cap != cudaStreamCaptureStatusActive) ++s.iters;
-    if (s.m.size() == 1 && s.m[0].n_out > 1)  // several outputs (App. B), before the counter advances
-        CU(launch_estimate_multi(s.d_desc, s.m[0].n_tree, stream));
+    for (int i = 0; i < n; ++i)
+        if (s.m[i].n_out > 1)  // several outputs (App. B), before the counter advances
+            CU(launch_estimate_multi(s.d_desc + i, s.m[i].n_tree, stream));
     if (refine_too && s.any_refine) {  // the step graph: a8 beside a6 and a7
         vp_status st = fork_refine(s, stream);
         if (st != VP_OK) return st;
@@ -1434,8 +1439,9 @@ extern "C" vp_status vp_get_strata(vp_ctx *c, int32_t *strata) {
 static vp_status latest_parity(Set &s, size_t *par);
 
 // The several-outputs history of a set's member 0 (App. B): i_j[n][M], cov_j[n][M][M].
-static vp_status multi_history(Set &s, int n, std::vector<double> &I, std::vector<double> &C) {
-    const Desc &d = s.h_desc[0];
+static vp_status multi_history(Set &s, int i, int n, std::vector<double> &I,
+                               std::vector<double> &C) {
+    const Desc &d = s.h_desc[i];
     const int M = d.n_out, T = M * (M + 1) / 2;
     std::vector<double> tri((size_t)n * T);
     I.assign((size_t)n * M, 0.0);
@@ -1461,32 +1467,36 @@ extern "C" vp_status vp_get_history_multi(vp_ctx *c, int n, double *i_j, double 
     if (n < 0 || n > d.hist_cap) return fail(VP_EINVAL, "n outside the history capacity");
     CU(cudaStreamSynchronize(c->set.last));
     std::vector<double> I, C;
-    vp_status st = multi_history(c->set, n, I, C);
+    vp_status st = multi_history(c->set, 0, n, I, C);
     if (st != VP_OK) return st;
     if (i_j) std::copy(I.begin(), I.end(), i_j);
     if (cov_j) std::copy(C.begin(), C.end(), cov_j);
     return VP_OK;
 }
 
-extern "C" vp_status vp_result_multi(vp_ctx *c, int discard, double *mean, double *cov,
+static vp_status member_result_multi(Set &s, int i, int discard, double *mean, double *cov,
                                      double *chi2, int *dof, int *n_it) {
-    CHECK_CTX(c);
     if (!mean || !cov || !chi2 || !dof) return fail(VP_EINVAL, "NULL out");
-    Set &s = c->set;
-    const Desc &d = s.h_desc[0];
-    if (d.n_out < 2) return fail(VP_EINVAL, "the context has no extra outputs");
+    const Desc &d = s.h_desc[i];
+    if (d.n_out < 2) return fail(VP_EINVAL, "the integral has no extra outputs");
     CU(cudaStreamSynchronize(s.last));
     State st;
     CU(cudaMemcpy(&st, d.st, sizeof st, cudaMemcpyDeviceToHost));
     const int n = (int)std::min<uint32_t>(st.t, (uint32_t)d.hist_cap);
     std::vector<double> I, C;
-    vp_status rs = multi_history(s, n, I, C);
+    vp_status rs = multi_history(s, i, n, I, C);
     if (rs != VP_OK) return rs;
     const int used = combine_multi(I.data(), C.data(), n, d.n_out, discard, mean, cov, chi2);
     *dof = used > 0 ? d.n_out * (used - 1) : 0;
     if (n_it) *n_it = used;
     if (st.status & kStatusNonFinite) return fail(VP_ENONFINITE, "integrand produced a non-finite value");
     return VP_OK;
+}
+
+extern "C" vp_status vp_result_multi(vp_ctx *c, int discard, double *mean, double *cov,
+                                     double *chi2, int *dof, int *n_it) {
+    CHECK_CTX(c);
+    return member_result_multi(c->set, 0, discard, mean, cov, chi2, dof, n_it);
 }
 
 extern "C" vp_status vp_get_moments_multi(vp_ctx *c, double *x1, double *x2) {
@@ -2035,6 +2045,29 @@ extern "C" vp_status vp_batch_destroy(vp_batch *b) {
     if (!b) return VP_OK;
     set_destroy(b->set);
     delete b;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_batch_result_multi(vp_batch *b, int i, int discard, double *mean,
+                                           double *cov, double *chi2, int *dof, int *n_it) {
+    CHECK_BATCH(b);
+    if (i < 0 || i >= (int)b->set.m.size()) return fail(VP_EINVAL, "integral index out of range");
+    return member_result_multi(b->set, i, discard, mean, cov, chi2, dof, n_it);
+}
+
+extern "C" vp_status vp_batch_history_multi(vp_batch *b, int i, int n, double *i_j,
+                                            double *cov_j) {
+    CHECK_BATCH(b);
+    if (i < 0 || i >= (int)b->set.m.size()) return fail(VP_EINVAL, "integral index out of range");
+    const Desc &d = b->set.h_desc[i];
+    if (d.n_out < 2) return fail(VP_EINVAL, "the integral has no extra outputs");
+    if (n < 0 || n > d.hist_cap) return fail(VP_EINVAL, "n outside the history capacity");
+    CU(cudaStreamSynchronize(b->set.last));
+    std::vector<double> I, C;
+    vp_status st = multi_history(b->set, i, n, I, C);
+    if (st != VP_OK) return st;
+    if (i_j) std::copy(I.begin(), I.end(), i_j);
+    if (cov_j) std::copy(C.begin(), C.end(), cov_j);
     return VP_OK;
 }
 

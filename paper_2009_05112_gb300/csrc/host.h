@@ -91,6 +91,7 @@ struct Group {
     bool one = false;  // a single integral: the cluster kernel with constants in parameters
     bool uniform = true;  // every member has the same strata on every axis (else: one only)
     bool mo = false;      // several outputs (App. B): the FP64 one-integral kernel that sums them
+    bool solo = false;    // a group of one member by construction (several outputs)
     int cs = 1;        // CTAs per cluster (one-integral kernel)
     int threads_one = 256;  // CTA size of the one-integral kernel
     // histograms of the one-integral kernel (one CTA per SM fits more shared

@@ -131,6 +131,10 @@ _SIGS = {
     "vp_batch_size": [_P, ctypes.POINTER(ctypes.c_int)],
     "vp_batch_destroy": [_P],
     "vp_batch_history": [_P, ctypes.c_int, ctypes.c_int, _P, _P],
+    "vp_batch_result_multi": [_P, ctypes.c_int, ctypes.c_int, _P, _P,
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_int)],
+    "vp_batch_history_multi": [_P, ctypes.c_int, ctypes.c_int, _P, _P],
     "vp_server_create": [ctypes.POINTER(vp_server_config), _P, ctypes.POINTER(_P)],
     "vp_server_submit": [_P, ctypes.POINTER(vp_request), ctypes.POINTER(ctypes.c_uint64)],
     "vp_server_step": [_P, ctypes.POINTER(ctypes.c_int)],
@@ -447,9 +451,12 @@ def _result_dict(r, st):
 class Batch:
     """Many independent integrals iterated together (a vp_batch)."""
 
-    def __init__(self, problems, precision=VP_FP32, stream=None):
+    def __init__(self, problems, precision=VP_FP32, stream=None, out_mono=None):
+        """out_mono: None, or per problem None or the (a, b) pairs of its extra
+        outputs f x^a x^b (App. B; FP64)."""
         self.n = len(problems)
         self._keep = []
+        self.n_out = [1] * self.n
         ps = (vp_params * self.n)()
         fs = (vp_integrand * self.n)()
         for i, prob in enumerate(problems):
@@ -462,6 +469,12 @@ class Batch:
                               int(prob.seed) & (2 ** 64 - 1), int(prob.integral_id),
                               int(precision), int(bool(prob.plus2)), int(prob.n_st), 0)
             _set_strata(ps[i], prob, self._keep)
+            if out_mono is not None and out_mono[i]:
+                mono = np.ascontiguousarray(np.asarray(out_mono[i], np.int32).reshape(-1))
+                self._keep.append(mono)
+                ps[i].n_extra = mono.size // 2
+                ps[i].out_mono = mono.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+                self.n_out[i] = 1 + mono.size // 2
             fs[i] = vp_integrand(int(prob.kind), prm.size, prm.ctypes.data_as(_dp))
         self.stream = current_stream() if stream is None else ctypes.c_void_p(stream)
         h = ctypes.c_void_p()
@@ -509,6 +522,24 @@ class Batch:
         I, Vv = np.zeros(n), np.zeros(n)
         check(lib().vp_batch_history(self.b, int(i), n, _ptr(I), _ptr(Vv)))
         return I, Vv
+
+    def history_multi(self, i, n=None):
+        """Integral i's I_j[n][M] and cov_j[n][M][M] (App. B)."""
+        n = self.result(i)["n_it"] if n is None else int(n)
+        M = self.n_out[i] if 0 <= i < self.n else 1
+        I, C = np.zeros((n, M)), np.zeros((n, M, M))
+        check(lib().vp_batch_history_multi(self.b, int(i), n, _ptr(I), _ptr(C)))
+        return I, C
+
+    def result_multi(self, i, discard=0):
+        """Integral i's outputs combined over iterations j >= discard (App. B, §2.5)."""
+        M = self.n_out[i] if 0 <= i < self.n else 1  # (the library refuses a bad index)
+        mean, cov = np.zeros(M), np.zeros((M, M))
+        chi2, dof, n_it = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+        check(lib().vp_batch_result_multi(self.b, int(i), int(discard), _ptr(mean), _ptr(cov),
+                                          ctypes.byref(chi2), ctypes.byref(dof),
+                                          ctypes.byref(n_it)))
+        return dict(mean=mean, cov=cov, chi2=chi2.value, dof=dof.value, n_it=n_it.value)
 
     def results(self, discard=0):
         out = (vp_result_t * self.n)()

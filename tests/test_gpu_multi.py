@@ -125,6 +125,58 @@ def test_eight_dimensional_full_allocation():
     check_iteration(g, o, 2)
 
 
+def test_batch_with_several_outputs_matches_oracle():
+    """A batch (FP64) of two posteriors with extra outputs -- the paper's
+    Bayesian moments and a shorter list -- beside a plain Gaussian and a
+    posterior without outputs: each integral with outputs is sampled by a
+    launch of its own, the rest by the task kernel, and the per-hypercube and
+    per-axis kernels run over all four.  Every integral against its own
+    oracle run (I_j, sigma_j^2 within 1e-10; outputs and covariances as for a
+    context) and the combined outputs within 1e-8."""
+    post_a = inputs.posterior(dim=3, n_ev=10_000, n_g=200, seed=2)
+    post_b = inputs.posterior(dim=3, n_ev=6000, n_g=150, seed=3)
+    post_b.integral_id = 7
+    post_c = inputs.posterior(dim=3, n_ev=8000, n_g=100, seed=4)
+    post_c.integral_id = 9
+    gauss = inputs.Problem("g3", 3, inputs.GAUSS,
+                           inputs.gauss_blob([1.0, 0.5], [0.2, 0.3],
+                                             [np.full(3, 0.4), np.full(3, 0.7)]),
+                           np.zeros(3), np.ones(3), n_g=120, n_ev=20_000, seed=5,
+                           integral_id=11)
+    probs = [post_a, gauss, post_b, post_c]
+    monos = [BAYES3, None, [(0, -1), (2, 2)], None]
+    b = V().Batch(probs, precision=0, out_mono=monos)
+    oracles = []
+    for prob, mono in zip(probs, monos):
+        oracles.append(oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g,
+                                        n_ev=prob.n_ev, alpha=prob.alpha, beta=prob.beta,
+                                        seed=prob.seed, kind=prob.kind, prm=prob.prm,
+                                        integral_id=prob.integral_id, out_mono=mono))
+    n_it = 6
+    b.run(n_it)
+    for o in oracles:
+        o.run(n_it)
+    for i, (o, mono) in enumerate(zip(oracles, monos)):
+        I, Vv = b.history(i)
+        np.testing.assert_allclose(I, o.I, rtol=1e-10, atol=0)
+        np.testing.assert_allclose(Vv, o.var, rtol=1e-10, atol=0)
+        if mono is None:
+            with pytest.raises(V().VegasError):
+                b.result_multi(i)
+            continue
+        Ig, Cg = b.history_multi(i)
+        Io, Co = np.asarray(o.Im), np.asarray(o.Cm)
+        np.testing.assert_allclose(Ig, Io, rtol=1e-10, atol=0)
+        for j in range(n_it):
+            s = np.sqrt(np.outer(np.diag(Co[j]), np.diag(Co[j])))
+            assert np.all(np.abs(Cg[j] - Co[j]) <= 1e-9 * s + 1e-300), (i, j)
+        r, ro = b.result_multi(i, discard=2), o.result_multi(discard=2)
+        np.testing.assert_allclose(r["mean"], ro["mean"], rtol=1e-8)
+        assert r["n_it"] == n_it - 2 and r["dof"] == len(Io[0]) * (n_it - 3)
+    with pytest.raises(V().VegasError):
+        b.result_multi(len(probs))
+
+
 def test_several_outputs_rejected_where_unsupported():
     VE = V().VegasError
     dim = 3
