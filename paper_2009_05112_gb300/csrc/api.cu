@@ -349,8 +349,9 @@ static vp_status plan_groups(Set &s) {
     // its largest dimension
     int merged_bucket[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (const Member &mb : s.m)
-        merged_bucket[mb.kind][mb.p.precision] =
-            std::max(merged_bucket[mb.kind][mb.p.precision], mb.bucket);
+        if (mb.n_out <= 1)  // (an integral with several outputs has a group of its own)
+            merged_bucket[mb.kind][mb.p.precision] =
+                std::max(merged_bucket[mb.kind][mb.p.precision], mb.bucket);
     for (uint32_t i = 0; i < s.m.size(); ++i) {
         const Member &mb = s.m[i];
         // several outputs (App. B): a group of its own, served by the FP64
@@ -363,7 +364,7 @@ static vp_status plan_groups(Set &s) {
         if (s.merge) {
             exact = mb.p.precision == VP_FP32;
             for (const Member &o : s.m)
-                if (o.kind == mb.kind && o.p.precision == mb.p.precision &&
+                if (o.kind == mb.kind && o.p.precision == mb.p.precision && o.n_out <= 1 &&
                     (o.p.dim != bucket_dim(bucket) || !o.uniform))
                     exact = false;
         }
