@@ -184,6 +184,17 @@ vp_status vp_adapt(vp_ctx *ctx, void *stream);
 
 /* vp_iterate + vp_adapt replayed from a CUDA graph captured on first use. */
 vp_status vp_step(vp_ctx *ctx, void *stream);
+/* A step (as vp_step) that also reads the estimates back without waiting for
+ * them: enqueues the step on `stream`, then an asynchronous copy of its I_j
+ * and sigma_j^2 into pinned host memory the context owns, then waits for the
+ * copy made by the previous vp_step_read call (its step finished while this
+ * one was being enqueued) and returns those values in *i_j, *var_j with
+ * *have = 1; *have = 0 on the first call (or the first after
+ * vp_step_read_flush).  vp_step_read_flush waits for the last call's copy
+ * and returns it the same way (*have = 0 if none is pending).  The
+ * estimates are those vp_get_history records (§2.5's I_j, sigma_j^2). */
+vp_status vp_step_read(vp_ctx *ctx, void *stream, int *have, double *i_j, double *var_j);
+vp_status vp_step_read_flush(vp_ctx *ctx, int *have, double *i_j, double *var_j);
 
 /* Synchronises the context's stream, reads the iteration history and
  * combines iterations j >= discard (§2.5).  VP_ENONFINITE if any iteration saw

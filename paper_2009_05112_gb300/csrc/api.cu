@@ -119,6 +119,17 @@ struct Set {
 
 struct vp_ctx {
     Set set;
+    // vp_step_read: two pinned slots {I_j, sigma_j^2}, filled on a side stream
+    // from the iteration history (written once per iteration, so the copy may
+    // trail the next step); step_ev marks a step's end, ev its copy's.
+    // `pending`: slot ^ 1 holds a copy not yet returned.  t_off: the device's
+    // iteration count minus set.iters (nonzero after an import).
+    double *pin = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr}, step_ev[2] = {nullptr, nullptr};
+    int slot = 0;
+    bool pending = false;
+    int64_t t_off = 0;
 };
 
 struct vp_batch {
@@ -1367,6 +1378,61 @@ extern "C" vp_status vp_step(vp_ctx *c, void *stream) {
     return set_step(c->set, (cudaStream_t)stream);
 }
 
+extern "C" vp_status vp_step_read(vp_ctx *c, void *stream, int *have, double *i_j,
+                                  double *var_j) {
+    CHECK_CTX(c);
+    if (!have || !i_j || !var_j) return fail(VP_EINVAL, "NULL out");
+    *have = 0;
+    if (!c->pin) {
+        CU(cudaHostAlloc((void **)&c->pin, 4 * sizeof(double), cudaHostAllocDefault));
+        CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : c->ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (cudaEvent_t &e : c->step_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const Desc &d = c->set.h_desc[0];
+    const int64_t t = (int64_t)c->set.iters + c->t_off;  // the index of this step's iteration
+    vp_status st = set_step(c->set, (cudaStream_t)stream);
+    if (st != VP_OK) return st;
+    const int k = c->slot;
+    if (t >= 0 && t < d.hist_cap) {  // from the history, beside the next step
+        CU(cudaEventRecord(c->step_ev[k], (cudaStream_t)stream));
+        CU(cudaStreamWaitEvent(c->side, c->step_ev[k], 0));
+        CU(cudaMemcpyAsync(c->pin + 2 * k, d.hist_i + t, sizeof(double), cudaMemcpyDeviceToHost,
+                           c->side));
+        CU(cudaMemcpyAsync(c->pin + 2 * k + 1, d.hist_var + t, sizeof(double),
+                           cudaMemcpyDeviceToHost, c->side));
+        CU(cudaEventRecord(c->ev[k], c->side));
+    } else {  // the history is full: the state's copy, before the next step may change it
+        const State *dst = d.st;  // last_i, last_var: adjacent doubles
+        CU(cudaMemcpyAsync(c->pin + 2 * k, &dst->last_i, 2 * sizeof(double),
+                           cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+        CU(cudaEventRecord(c->ev[k], (cudaStream_t)stream));
+    }
+    if (c->pending) {  // the previous call's step, finished while this one was enqueued
+        CU(cudaEventSynchronize(c->ev[k ^ 1]));
+        *i_j = c->pin[2 * (k ^ 1)];
+        *var_j = c->pin[2 * (k ^ 1) + 1];
+        *have = 1;
+    }
+    c->pending = true;
+    c->slot = k ^ 1;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_step_read_flush(vp_ctx *c, int *have, double *i_j, double *var_j) {
+    CHECK_CTX(c);
+    if (!have || !i_j || !var_j) return fail(VP_EINVAL, "NULL out");
+    *have = 0;
+    if (!c->pending) return VP_OK;
+    const int k = c->slot ^ 1;
+    CU(cudaEventSynchronize(c->ev[k]));
+    *i_j = c->pin[2 * k];
+    *var_j = c->pin[2 * k + 1];
+    *have = 1;
+    c->pending = false;
+    return VP_OK;
+}
+
 extern "C" vp_status vp_result(vp_ctx *c, int discard, vp_result_t *out) {
     CHECK_CTX(c);
     if (!out) return fail(VP_EINVAL, "NULL out");
@@ -1413,6 +1479,16 @@ extern "C" vp_status vp_set_damping(vp_ctx *c, double alpha, double beta) {
 
 extern "C" vp_status vp_map_destroy(vp_ctx *c) {
     if (!c) return VP_OK;
+    if (c->pin) {
+        cudaStreamSynchronize(c->set.last);
+        cudaStreamSynchronize(c->side);
+        cudaFreeHost(c->pin);
+        cudaStreamDestroy(c->side);
+    }
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->step_ev)
+        if (e) cudaEventDestroy(e);
     set_destroy(c->set);
     delete c;
     return VP_OK;
@@ -1678,6 +1754,7 @@ extern "C" vp_status vp_import_state(vp_ctx *c, const void *buf, size_t size) {
     }
     st.done_est = st.done_alloc = st.done_multi = 0u;
     CU(cudaMemcpy(d.st, &st, sizeof st, cudaMemcpyHostToDevice));
+    c->t_off = (int64_t)st.t - (int64_t)s.iters;
     return VP_OK;
 }
 

@@ -131,6 +131,10 @@ _SIGS = {
     "vp_batch_size": [_P, ctypes.POINTER(ctypes.c_int)],
     "vp_batch_destroy": [_P],
     "vp_batch_history": [_P, ctypes.c_int, ctypes.c_int, _P, _P],
+    "vp_step_read": [_P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                     ctypes.POINTER(ctypes.c_double)],
+    "vp_step_read_flush": [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double)],
     "vp_batch_result_multi": [_P, ctypes.c_int, ctypes.c_int, _P, _P,
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int)],
@@ -293,6 +297,21 @@ class Integrator:
                 self.iterate()
                 self.adapt()
         return self
+
+    def step_read(self):
+        """One step; returns the previous step_read call's (I_j, sigma_j^2), or
+        None on the first call (vp_step_read)."""
+        have, i, v = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        check(lib().vp_step_read(self.ctx, self.stream, ctypes.byref(have), ctypes.byref(i),
+                                 ctypes.byref(v)))
+        return (i.value, v.value) if have.value else None
+
+    def step_read_flush(self):
+        """The last step_read call's (I_j, sigma_j^2), or None."""
+        have, i, v = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        check(lib().vp_step_read_flush(self.ctx, ctypes.byref(have), ctypes.byref(i),
+                                       ctypes.byref(v)))
+        return (i.value, v.value) if have.value else None
 
     def set_damping(self, alpha, beta):
         """alpha, beta for the following iterations (alpha = 0 freezes the map)."""

@@ -103,3 +103,55 @@ def test_import_refuses_other_parameters():
     with pytest.raises(VE):
         V().Integrator.from_problem(prob, precision=0).import_state(blob[:-8])
     assert np.array_equal(b.edges(), e0) and np.array_equal(b.history()[0][:1], h0)
+
+
+def test_step_read_returns_every_estimate_one_call_later():
+    """vp_step_read: the first call returns nothing, every later call the
+    previous step's (I_j, sigma_j^2) exactly as the history records them, the
+    flush the last one; interleaved eager iterations keep their own order."""
+    prob = inputs.three_peaks_d4(n_ev=20_000, n_g=300)
+    g = V().Integrator.from_problem(prob, precision=0)
+    assert g.step_read_flush() is None
+    got = [g.step_read()]
+    assert got[0] is None
+    for _ in range(5):
+        got.append(g.step_read())
+    last = g.step_read_flush()
+    assert g.step_read_flush() is None
+    I, Vv = g.history()
+    assert len(I) == 6
+    for k in range(5):
+        assert got[k + 1] == (I[k], Vv[k])
+    assert last == (I[5], Vv[5])
+    g.iterate(); g.adapt()
+    assert g.step_read() is None  # nothing pending after the flush
+    assert g.step_read_flush() == tuple(x[-1] for x in g.history())
+    fp32 = V().Integrator.from_problem(prob, precision=1)
+    vals = [fp32.step_read() for _ in range(4)] + [fp32.step_read_flush()]
+    I32, V32 = fp32.history()
+    assert vals[1:] == list(zip(I32, V32))
+
+
+def test_step_read_after_import_and_past_the_history():
+    """vp_step_read after vp_import_state reads the imported run's next
+    iterations; past the history's capacity it reads the state's copy."""
+    prob = inputs.three_peaks_d4(n_ev=20_000, n_g=300)
+    a = V().Integrator.from_problem(prob, precision=0).run(5)
+    c = V().Integrator.from_problem(prob, precision=0)
+    c.run(1)
+    c.import_state(a.export_state())
+    vals = [c.step_read(), c.step_read(), c.step_read_flush()]
+    I, Vv = c.history()
+    assert len(I) == 7 and vals[0] is None
+    assert vals[1:] == [(I[5], Vv[5]), (I[6], Vv[6])]
+    kw = dict(dim=prob.dim, lo=prob.lo, hi=prob.hi, kind=prob.kind, prm=prob.prm, n_g=prob.n_g,
+              n_ev=prob.n_ev, seed=prob.seed, precision=0, max_it=2)
+    g = V().Integrator(**kw)
+    vals = [g.step_read() for _ in range(4)] + [g.step_read_flush()]
+    I, Vv = np.zeros(2), np.zeros(2)  # (the history holds the first two)
+    V().check(V().lib().vp_get_history(g.ctx, 2, V()._ptr(I), V()._ptr(Vv)))
+    assert vals[1:3] == [(I[0], Vv[0]), (I[1], Vv[1])]
+    r = g.result()
+    assert vals[4][0] == r["last_i"]
+    assert vals[4][1] == pytest.approx(r["last_sdev"] ** 2, rel=1e-12)
+    assert all(v is not None and np.isfinite(v[0]) for v in vals[1:])
