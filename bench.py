@@ -55,6 +55,9 @@ def parse():
                          "integrals per launch against one at a time; serve: continuous batching "
                          "of a Poisson request stream")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    ap.add_argument("--n-ev", type=float, default=None,
+                    help="four_peaks_d8: samples per iteration other than the workload's 1e6 "
+                         "(a sweep of the step's size; N_st follows Eq. Nst_vegasp)")
     ap.add_argument("--launch", default=None,
                     help="fix the sampling launch shape instead of autotuning it: "
                          "scheme:blocks:threads:cluster:run with scheme static-cluster or tasks")
@@ -445,7 +448,7 @@ def run_ours(args):
     elif precond:
         prob = inputs.three_sharp_peaks_d8(n_ev=1_000_000)
     else:
-        prob = inputs.four_peaks_d8()
+        prob = inputs.four_peaks_d8(**({"n_ev": int(args.n_ev)} if args.n_ev else {}))
     n_peaks = 4 if args.workload == "four_peaks_d8" else (3 if precond else 1)
     out_mono = BAYES_OUTPUTS if bayes else None
     precision = vegasp.VP_FP64 if bayes else vegasp.VP_FP32

@@ -187,7 +187,7 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
     return v;
 }
 
-__global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256)
+__global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256, 4)
     k_estimate(const Desc *desc, const uint32_t *tree_base, int n_int, int mode) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -446,8 +446,10 @@ __device__ __forceinline__ unsigned long long cta_exclusive_scan(unsigned long l
 // into offsets (integers: any order is exact) and records the total.
 // Skipped (allocation kept) when sum_d is not finite; the status flag records it.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSubH) k_alloc(const Desc *desc, const uint32_t *tree_base,
-                                                 int n_int, int initial) {
+// (eight CTAs per SM: the batched loads of the last CTA's scan must not cost
+// the other CTAs their occupancy)
+__global__ void __launch_bounds__(kSubH, 8) k_alloc(const Desc *desc, const uint32_t *tree_base,
+                                                    int n_int, int initial) {
     __shared__ unsigned long long s_w[8];
     __shared__ bool s_last;
     __shared__ unsigned long long s_carry;
@@ -480,17 +482,30 @@ __global__ void __launch_bounds__(kSubH) k_alloc(const Desc *desc, const uint32_
     }
     __syncthreads();
     if (!s_last) return;
-    // last CTA: exclusive scan of the sub-block sums in place
+    // last CTA: exclusive scan of the sub-block sums in place, kScanV
+    // consecutive sums per thread per pass (their loads issued together)
     __threadfence();
-    for (uint32_t q0 = 0; q0 < n_sub; q0 += kSubH) {
-        const uint32_t q = q0 + threadIdx.x;
-        const unsigned long long v = q < n_sub ? __ldcg(d.bsum + q) : 0ull;
+    constexpr uint32_t kScanV = 4;
+    for (uint32_t q0 = 0; q0 < n_sub; q0 += kSubH * kScanV) {
+        const uint32_t q = q0 + threadIdx.x * kScanV;
+        unsigned long long v[kScanV];
+#pragma unroll
+        for (uint32_t k = 0; k < kScanV; ++k) v[k] = q + k < n_sub ? __ldcg(d.bsum + q + k) : 0ull;
+        unsigned long long own = 0ull;
+#pragma unroll
+        for (uint32_t k = 0; k < kScanV; ++k) {  // exclusive within the thread's run
+            const unsigned long long x = v[k];
+            v[k] = own;
+            own += x;
+        }
         unsigned long long all;
-        const unsigned long long ex = cta_exclusive_scan(v, s_w, &all);
-        const unsigned long long base = s_carry;
-        if (q < n_sub) d.bsum[q] = base + ex;
+        const unsigned long long ex = cta_exclusive_scan(own, s_w, &all);
+        const unsigned long long base = s_carry + ex;
+#pragma unroll
+        for (uint32_t k = 0; k < kScanV; ++k)
+            if (q + k < n_sub) d.bsum[q + k] = base + v[k];
         __syncthreads();
-        if (threadIdx.x == 0) s_carry = base + all;
+        if (threadIdx.x == 0) s_carry += all;
         __syncthreads();
     }
     if (threadIdx.x == 0) {

@@ -243,21 +243,35 @@ __device__ void block_tree_sum(const double *part, uint32_t n, double *sh, doubl
     if (t < T) {
         double st[NS][24];  // one partial sum per tree level (Q <= 2^23)
         uint32_t full = 0u;  // bit l: st[.][l] holds a complete subtree of 2^l leaves
-        for (uint32_t j = 0; j < Q; ++j) {
-            const uint32_t i = t * Q + j;
-            double carry[NS];
+        // leaves in groups of up to 4 whose loads are issued together, then
+        // folded into the stack one by one (the same order of additions)
+        constexpr uint32_t G = 4;
+        for (uint32_t j0 = 0; j0 < Q; j0 += G) {
+            double buf[G][NS];
 #pragma unroll
-            for (int c = 0; c < NS; ++c) carry[c] = i < n ? __ldcg(part + (size_t)NS * i + c) : 0.0;
-            int l = 0;
-            while (full & (1u << l)) {
+            for (uint32_t g = 0; g < G; ++g) {
+                const uint32_t i = t * Q + j0 + g;
 #pragma unroll
-                for (int c = 0; c < NS; ++c) carry[c] = __dadd_rn(st[c][l], carry[c]);
-                full &= ~(1u << l);
-                ++l;
+                for (int c = 0; c < NS; ++c)
+                    buf[g][c] = (j0 + g < Q && i < n) ? __ldcg(part + (size_t)NS * i + c) : 0.0;
             }
 #pragma unroll
-            for (int c = 0; c < NS; ++c) st[c][l] = carry[c];
-            full |= 1u << l;
+            for (uint32_t g = 0; g < G; ++g) {
+                if (j0 + g >= Q) break;
+                double carry[NS];
+#pragma unroll
+                for (int c = 0; c < NS; ++c) carry[c] = buf[g][c];
+                int l = 0;
+                while (full & (1u << l)) {
+#pragma unroll
+                    for (int c = 0; c < NS; ++c) carry[c] = __dadd_rn(st[c][l], carry[c]);
+                    full &= ~(1u << l);
+                    ++l;
+                }
+#pragma unroll
+                for (int c = 0; c < NS; ++c) st[c][l] = carry[c];
+                full |= 1u << l;
+            }
         }
         const int top = __ffs((int)full) - 1;  // Q is a power of two: one subtree is left
 #pragma unroll

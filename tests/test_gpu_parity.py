@@ -154,7 +154,8 @@ def test_samples_fp32_within_tolerance(kind, dim):
 # ---------------------------------------------------------------------------
 # a7: integer allocation, bit-exact
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("dim,n_st", [(1, 1), (2, 4), (4, 7), (1, 1025), (8, 4), (20, 2)])
+@pytest.mark.parametrize("dim,n_st", [(1, 1), (2, 4), (4, 7), (1, 1025), (8, 4), (20, 2),
+                                      (8, 8)])
 @pytest.mark.parametrize("plus2", [False, True])
 def test_alloc_from_dh_bit_exact(dim, n_st, plus2):
     rng = np.random.default_rng(dim * 1000 + n_st + plus2)
