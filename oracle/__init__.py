@@ -148,7 +148,9 @@ def integrand(kind, dim, prm, x):
 
 
 def integrand_many(kind, dim, prm, X):
-    """The integrand at the rows of X (n x dim)."""
+    """The integrand at the rows of X (n x dim).  Pinned by the closed forms of
+    each family integrated by tensor Gauss-Legendre quadrature or a fine grid
+    (erf products, disc areas, e^{-s|x|}, a Gaussian posterior)."""
     X = np.ascontiguousarray(X, np.float64).reshape(-1, int(dim))
     out = np.zeros(X.shape[0])
     lib().or_integrand_many(int(kind), int(dim), np.ascontiguousarray(prm, np.float64),
@@ -194,7 +196,8 @@ def estimate_multi(omega, x1, x2, n_h):
 
 
 def sigma(omega, s1, s2, n_h):
-    """§3 step 2: sigma_h(Jf) from the iteration's samples."""
+    """§3 step 2: sigma_h(Jf) from the iteration's samples.  Pinned by numpy's
+    population spread of the per-sample values, scaled by Omega_h."""
     out = np.zeros(len(n_h), np.float64)
     lib().or_sigma(len(n_h), float(omega), np.ascontiguousarray(s1, np.float64),
                    np.ascontiguousarray(s2, np.float64), np.ascontiguousarray(n_h, np.uint32),
@@ -203,7 +206,8 @@ def sigma(omega, s1, s2, n_h):
 
 
 def damp(beta, sig):
-    """§3 Eq. (dh): d_h = sigma_h^beta."""
+    """§3 Eq. (dh): d_h = sigma_h^beta.  Pinned by beta = 0 (every d_h = 1,
+    the equal split) and beta = 1 (d_h = sigma_h exactly)."""
     sig = np.ascontiguousarray(sig, np.float64)
     out = np.zeros_like(sig)
     lib().or_damp(sig.size, float(beta), sig, out)
@@ -344,7 +348,10 @@ def combine_multi(I, C, discard=0, cut=1e-12):
 
 def combine_unweighted(I, var, discard=0):
     """§2.5, last paragraph: unweighted mean of the I_j and mean sigma_j over
-    sqrt(N_it) (used with a frozen map, alpha = 0)."""
+    sqrt(N_it) (used with a frozen map, alpha = 0).  Pinned on Eq. (easy) with
+    a frozen map over 300 iterations: within 4 sigma of the closed form, the
+    scatter of the I_j equal to the mean sigma_j within 15%, and the weighted
+    mean of the same iterations below it (the bias §2.5 describes)."""
     I = np.asarray(I, np.float64)[discard:]
     s = np.sqrt(np.asarray(var, np.float64)[discard:])
     n = I.size
