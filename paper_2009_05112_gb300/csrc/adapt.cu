@@ -175,7 +175,7 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
             if (vb < 0ll && (vb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) var = 0.0;
         }
         v.a = om * m1;
-        v.b = om * om * var * inv_n1;
+        v.b = d.omega2 * var * inv_n1;  // (Omega Omega) var / (n_h - 1), left to right
         v.c = d.prec == VP_FP32 ? damp_var32(var, d) : damp(om * sqrt(var), d.beta);
         d.dh[h] = v.c;
     } else if (mode == 1) {
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kSubH, 8) k_alloc(const Desc *desc, const uint
     }
     uint32_t n = 0;
     if (h < d.n_hc) {
-        n = alloc_one(d, d.dh[h], (double)d.n_ev, sum_d, d.st->inv_sum_d, initial);
+        n = alloc_one(d, d.dh[h], d.n_ev_d, sum_d, d.st->inv_sum_d, initial);
         d.n_h[h] = n;
     }
     unsigned long long tot;

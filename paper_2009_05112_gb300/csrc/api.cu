@@ -535,6 +535,8 @@ void vp::fill_desc(const Member &mb, const double *d_inv, Desc &d) {
     d.n_ev = mb.p.n_ev;
     d.n_hc = mb.n_hc;
     d.omega = 1.0 / (double)mb.n_hc;
+    d.omega2 = d.omega * d.omega;
+    d.n_ev_d = (double)mb.p.n_ev;
     d.alpha = mb.p.alpha;
     d.beta = mb.p.beta;
     d.omega_beta = std::pow(d.omega, mb.p.beta);

@@ -83,6 +83,8 @@ struct Desc {
     int64_t n_ev;
     uint64_t n_hc;             // N_h = prod_mu strata[mu] (N_st^D when uniform)
     double omega;              // y-volume of a hypercube, 1 / N_h
+    double omega2;             // omega * omega (IEEE product, as the kernels would form it)
+    double n_ev_d;             // (double) n_ev (exact below 2^53)
     double alpha, beta;
     double omega_beta;         // Omega^beta (FP32 path: d_h = Omega^beta var^(beta/2))
     float half_beta_hi, half_beta_lo;  // beta/2 = hi + lo (FP32 path)
