@@ -1,15 +1,19 @@
 #!/usr/bin/env python3
 """Throughput of the vegas+ hot path (one adaptive iteration = one step) on GB300.
 
-Workload: the 8-D integral of four Gaussian peaks on the diagonal (centres
-0.2, 0.4, 0.6, 0.8, width 0.1, amplitudes U[0.5, 2] from seed 0), N_ev = 1e6
-samples per iteration, N_g = 1000, beta = 0.75, alpha = 0.5; map and integrand
-in FP32, per-hypercube moments Kahan-compensated FP32, estimate, reallocation
-and refinement in FP64.  A step is one vp_step: sampling (a1-a5), estimate
-(a6), reallocation (a7) and grid refinement (a8), replayed from a CUDA graph.
+Default workload (the largest single-GPU configuration): the 20-D indicator of
+the ball of radius 0.5 centred in [0,1]^20 (§1 footnote), N_ev = 1e7 samples
+per iteration, N_g = 1000, beta = 0.75, alpha = 0.5, 2^20 hypercubes; map and
+integrand in FP32, per-hypercube moments Kahan-compensated FP32, estimate,
+reallocation and refinement in FP64.  A step is one vp_step: sampling
+(a1-a5), estimate (a6), reallocation (a7) and grid refinement (a8), replayed
+from a CUDA graph.  The same JSON line carries, as extra keys, the 8-D
+four-peak step (N_ev = 1e6), the 512-integral batch against one integral at a
+time, and the served request stream with its p50/p99 latency.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on the host cores instead (the reference arm).
+on the host cores instead (the reference arm), on whole iterations of the same
+workload.
 
 Multi-GPU (torchrun): one independent integral per rank (distinct Philox
 counter word 3), no collective on the data path; value = all ranks' integrand
@@ -27,7 +31,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "four_peaks_d8"
+WORKLOAD = "ball_d20"
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB of L2, written between timed steps
 KERNEL_TIMING_ITERS = 10     # eager iterations timing the sampling kernel
 # the library measures the sampling launch shape again once the grid has
@@ -44,9 +48,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["four_peaks_d8", "ball_d20", "exp_origin_d16",
                                            "bayes_d3", "precond_d8", "batch_mix", "serve"],
-                    default="four_peaks_d8",
-                    help="four_peaks_d8 (default): the single-integral step; ball_d20: the same "
-                         "step on the 20-D ball (N_ev = 1e7); exp_origin_d16: exp(-50|x|) in 16-D "
+                    default="ball_d20",
+                    help="ball_d20 (default): the single-integral step on the 20-D ball "
+                         "(N_ev = 1e7), with the four-peak, batched and served figures as extra "
+                         "keys; four_peaks_d8: the step on the 8-D four peaks (N_ev = 1e6); "
+                         "exp_origin_d16: exp(-50|x|) in 16-D "
                          "with the mixed stratification (N_ev = 2.5e5, 2^15 hypercubes); "
                          "bayes_d3: the 3-D posterior with the eight outputs of the Bayesian "
                          "example (means and second moments, FP64, N_ev = 1e5); precond_d8: "
@@ -54,7 +60,13 @@ def parse():
                          "then frozen (N_ev = 1e6); batch_mix: 512 "
                          "integrals per launch against one at a time; serve: continuous batching "
                          "of a Poisson request stream")
-    ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    ap.add_argument("--requests", type=int, default=2000,
+                    help="serve: requests of the stream served at their arrival times")
+    ap.add_argument("--saturated-requests", type=int, default=20000,
+                    help="serve: requests queued at once for the saturated rate (the whole "
+                         "20k-request stream)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="ball_d20: leave out the four-peak, batched and served keys")
     ap.add_argument("--n-ev", type=float, default=None,
                     help="four_peaks_d8: samples per iteration other than the workload's 1e6 "
                          "(a sweep of the step's size; N_st follows Eq. Nst_vegasp)")
@@ -177,16 +189,24 @@ def measured_peaks():
         return {}
 
 
-PROFILED_SAMPLES = 1114112  # samples in the launch the committed summary covers
+# ncu summaries of the sampling kernel, one per workload, under profiles/
+PROFILE_FILES = {"ball_d20": "sample_kernel_ball_d20.txt",
+                 "four_peaks_d8": "sample_kernel_four_peaks_d8.txt"}
+# per-pipe figures the summaries carry, as percentages of the peak sustained
+# over ELAPSED cycles (ncu's .pct_of_peak_sustained_elapsed)
+PIPE_KEYS = ["sm__pipe_fma_cycles_active", "sm__pipe_alu_cycles_active",
+             "sm__inst_executed_pipe_xu", "smsp__issue_active"]
 
 
-def traffic_from_profile(kernel_src_hash, what="traffic"):
-    """From the committed ncu summary, if it was taken on the current kernel
-    source: DRAM bytes per sampling launch ("traffic"), or the FP32 FMA + ALU
-    pipe utilisation ("fma_alu_issue", fraction of active cycles)."""
-    path = os.path.join(ROOT, "profiles", "sample_kernel_four_peaks_d8.txt")
+def profile_figures(workload, kernel_src_hash):
+    """The committed ncu summary of the workload's sampling kernel, if it was
+    taken on the current kernel source: {"traffic_per_sample": DRAM bytes per
+    sample of the profiled launch, "pipes_pct_elapsed": {...}}; else None."""
+    name = PROFILE_FILES.get(workload)
+    if not name:
+        return None
     try:
-        text = open(path).read()
+        text = open(os.path.join(ROOT, "profiles", name)).read()
     except OSError:
         return None
     vals = {}
@@ -197,10 +217,12 @@ def traffic_from_profile(kernel_src_hash, what="traffic"):
     if vals.get("kernel_source_sha1") != kernel_src_hash:
         return None
     try:
-        if what == "fma_alu_issue":
-            return {"fma_alu_issue_frac": float(vals["fma_alu_issue_frac"].split()[0])}
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError, IndexError):
+        out = {"traffic_per_sample": float(vals["dram_bytes_per_launch"].split()[0]) /
+               float(vals["profiled_samples"].split()[0])}
+        out["pipes_pct_elapsed"] = {k: float(vals[k + "_pct_elapsed"].split()[0])
+                                    for k in PIPE_KEYS if k + "_pct_elapsed" in vals}
+        return out
+    except (KeyError, ValueError, IndexError, ZeroDivisionError):
         return None
 
 
@@ -351,12 +373,16 @@ def cpu_baseline_serve(probs, rules, seconds=12.0):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 C oracle, as it stands, on this host, on
+    whole iterations of the same workload as our arm (W untimed, then K
+    timed); rank 0 alone."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     from paper_2009_05112_gb300 import inputs
-    prob = inputs.four_peaks_d8()
+    name = args.workload if args.workload in ("ball_d20", "four_peaks_d8") else WORKLOAD
+    prob = getattr(inputs, name)()
     o = oracle.VegasPlus(dim=prob.dim, lo=prob.lo, hi=prob.hi, n_g=prob.n_g, n_ev=prob.n_ev,
                          alpha=prob.alpha, beta=prob.beta, seed=prob.seed, kind=prob.kind,
                          prm=prob.prm)
@@ -376,12 +402,13 @@ def run_reference(args):
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "dim": 8, "n_ev": prob.n_ev, "n_g": prob.n_g,
+            "config": {"workload": name, "dim": prob.dim, "n_ev": prob.n_ev, "n_g": prob.n_g,
                        "alpha": prob.alpha, "beta": prob.beta},
             "cpu_baseline": {"value": v, "unit": "integrand evals/s", "cores": 1,
                              "kind": "oracle",
-                             "sample": "%d whole iterations (N_ev=1e6) after %d warm-up, "
-                                       "single thread" % (args.steps, args.warmup),
+                             "sample": "%d whole iterations of %s (N_ev=%d) after %d warm-up, "
+                                       "single thread" % (args.steps, name, prob.n_ev,
+                                                          args.warmup),
                              "host": host_cpu()},
             "e2e": {"value": v, "unit": "integrand evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -421,6 +448,119 @@ def reduce_over_ranks(total_ms, evals, dist, device):
     return float(t.item()), float(e.item())
 
 
+def _problem(workload, inputs, vegasp, n_ev=None):
+    """(problem, peaks, extra outputs, precision) of a single-integral workload."""
+    if workload == "ball_d20":
+        return inputs.ball_d20(), 1, None, vegasp.VP_FP32
+    if workload == "exp_origin_d16":
+        return inputs.exp_origin(dim=16), 1, None, vegasp.VP_FP32
+    if workload == "bayes_d3":
+        return (inputs.posterior(dim=3, n_ev=100_000, n_g=1000), 1, BAYES_OUTPUTS,
+                vegasp.VP_FP64)
+    if workload == "precond_d8":
+        return inputs.three_sharp_peaks_d8(n_ev=1_000_000), 3, None, vegasp.VP_FP32
+    prob = inputs.four_peaks_d8(**({"n_ev": int(n_ev)} if n_ev else {}))
+    return prob, 4, None, vegasp.VP_FP32
+
+
+def _timed_steps(g, steps, stream, flush, clk_index, world=1, dist=None):
+    """K steps, L2 flushed before each, CUDA events around each graph launch
+    on the launching stream; (total ms, evaluations, clocks summary)."""
+    import torch
+    n0 = g.result()["n_eval"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(clk_index) as clk:
+        for k in range(steps):
+            flush.fill_(k & 0xff)           # evict L2 between timed steps
+            ev[k][0].record(stream)
+            g.step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    return total_ms, g.result()["n_eval"] - n0, clk.summary()
+
+
+def _sampling_ms(g, flush):
+    """The sampling kernel's own duration: CUDA events around its launch on
+    its stream, in eager iterations of the same integral right after the timed
+    steps (the step graph carries no events: as graph nodes they would add
+    microseconds to every step); L2 flushed before each, as in the timed
+    steps.  Mean over KERNEL_TIMING_ITERS."""
+    ms = []
+    for k in range(KERNEL_TIMING_ITERS):
+        flush.fill_(k & 0xff)
+        g.iterate()
+        g.adapt()
+        ms.append(g.last_sample_ms())
+    return sum(ms) / len(ms)
+
+
+def _sample_roofline(workload, prob, n_peaks, samples_per_step, k1_ms, step_ms, n_sm,
+                     clocks, max_mhz):
+    """The sampling kernel against the FP32 roofline: algorithmic FP32 flops
+    per sample (counted from the source, an FMA as 2) x samples per launch /
+    its CUDA-event duration, over SMs x 128 lanes x 2 flops x the maximum SM
+    clock; the issue-slot view (algorithmic lane operations over SMs x 128 x
+    clock) and the ncu pipe figures of the committed summary beside it."""
+    ball = workload == "ball_d20"
+    expo = workload == "exp_origin_d16"
+    flops = (ball_flops_per_sample(prob.dim) if ball else
+             flops_per_sample(prob.dim, n_peaks) + (n_peaks if expo else 0))
+    ops = ops_per_sample(prob.dim, n_peaks, ball, expnorm=expo)
+    fp32_peak = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12   # TFLOP/s at the maximum SM clock
+    issue_peak = n_sm * 128 * max_mhz * 1e6 / 1e12      # lane operations/s, Tops/s
+    tflops = flops * samples_per_step / (k1_ms / 1e3) / 1e12
+    tops = ops * samples_per_step / (k1_ms / 1e3) / 1e12
+    prof = profile_figures(workload, kernel_source_hash())
+    roof = {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": tflops / fp32_peak,
+            "traffic": (prof["traffic_per_sample"] * samples_per_step) if prof else None,
+            "kernel": "k_sample (fused a1-a5)", "kernel_ms": k1_ms,
+            "kernel_ms_note": "CUDA events around the sampling launch on its stream, mean of "
+                              "%d eager iterations after the timed steps" % KERNEL_TIMING_ITERS,
+            "kernel_share_of_step": k1_ms / step_ms,
+            "flops_per_sample": flops,
+            "peak_note": "FP32 peak = %d SMs x 128 lanes x 2 flops x %.0f MHz (maximum SM clock; "
+                         "MEASURED_PEAKS.json records no FP32 figure); algorithmic FP32 flops "
+                         "counted from the kernel source, an FMA as 2" % (n_sm, max_mhz),
+            "issue_view": {"achieved_tops": tops, "peak_tops": issue_peak,
+                           "frac": tops / issue_peak, "ops_per_sample": ops,
+                           "note": "algorithmic lane operations (Philox, map, integrand, "
+                                   "moments, histogram atomics) over issue slots"},
+            "ncu_pct_of_peak_elapsed": prof["pipes_pct_elapsed"] if prof else None}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = tflops / (n_sm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    return roof
+
+
+def _single_summary(workload, args, inputs, vegasp, flush, n_sm, max_mhz):
+    """A secondary single-integral line: device-timed steps and the sampling
+    kernel's FP32 fraction, as the main line measures them."""
+    import torch
+    prob, n_peaks, out_mono, precision = _problem(workload, inputs, vegasp)
+    g = vegasp.Integrator.from_problem(prob, precision=precision, out_mono=out_mono)
+    for _ in range(max(args.warmup, MIN_WARMUP)):
+        g.step()
+    total_ms, evals, clocks = _timed_steps(g, args.steps, torch.cuda.current_stream(), flush,
+                                           int(os.environ.get("LOCAL_RANK", "0")))
+    k1 = _sampling_ms(g, flush)
+    roof = _sample_roofline(workload, prob, n_peaks, evals / args.steps, k1,
+                            total_ms / args.steps, n_sm, clocks, max_mhz)
+    out = {"value": evals / (total_ms / 1e3), "unit": "integrand evals/s",
+           "ms_per_step": total_ms / args.steps, "steps": args.steps,
+           "n_ev": prob.n_ev, "dim": prob.dim, "n_hc": g.n_hc,
+           "kernel_ms": k1, "fp32_frac": roof["frac"], "issue_frac": roof["issue_view"]["frac"],
+           "traffic": roof["traffic"], "ncu_pct_of_peak_elapsed": roof["ncu_pct_of_peak_elapsed"],
+           "clocks": clocks, "sample_launch": g.tuning(),
+           "integral": dict(_integral(g, prob, False), exact=prob.exact)}
+    g.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -439,19 +579,7 @@ def run_ours(args):
     expo = args.workload == "exp_origin_d16"
     bayes = args.workload == "bayes_d3"
     precond = args.workload == "precond_d8"
-    if ball:
-        prob = inputs.ball_d20()
-    elif expo:
-        prob = inputs.exp_origin(dim=16)
-    elif bayes:
-        prob = inputs.posterior(dim=3, n_ev=100_000, n_g=1000)
-    elif precond:
-        prob = inputs.three_sharp_peaks_d8(n_ev=1_000_000)
-    else:
-        prob = inputs.four_peaks_d8(**({"n_ev": int(args.n_ev)} if args.n_ev else {}))
-    n_peaks = 4 if args.workload == "four_peaks_d8" else (3 if precond else 1)
-    out_mono = BAYES_OUTPUTS if bayes else None
-    precision = vegasp.VP_FP64 if bayes else vegasp.VP_FP32
+    prob, n_peaks, out_mono, precision = _problem(args.workload, inputs, vegasp, args.n_ev)
     prob = rank_problem(prob, rank)
     stream = torch.cuda.current_stream()
     g = vegasp.Integrator.from_problem(prob, precision=precision, out_mono=out_mono)
@@ -473,23 +601,8 @@ def run_ours(args):
         g.set_tuning(*launch)
     for _ in range(max(args.warmup, MIN_WARMUP)):
         g.step()
-    n0 = g.result()["n_eval"]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(k & 0xff)           # evict L2 between timed steps
-            ev[k][0].record(stream)
-            g.step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    evals = g.result()["n_eval"] - n0
+    total_ms, evals, clocks = _timed_steps(g, args.steps, stream, flush, local, world, dist)
     t_max = total_ms
     evals_all = evals
     if world > 1:
@@ -497,16 +610,7 @@ def run_ours(args):
         dist.barrier()
     value = evals_all / (t_max / 1e3)
 
-    # the sampling kernel's own duration: CUDA events around its launch on its
-    # stream, in eager iterations of the same integral right after the timed
-    # steps (the step graph carries no events: as graph nodes they would add
-    # microseconds to every step); L2 flushed before each, as in the timed steps
-    k1_ms = []
-    for k in range(KERNEL_TIMING_ITERS):
-        flush.fill_(k & 0xff)
-        g.iterate()
-        g.adapt()
-        k1_ms.append(g.last_sample_ms())
+    k1_avg_ms = _sampling_ms(g, flush)
 
     # end to end through the public API with host buffers: create from host
     # parameters (H2D), steps each reading its estimate (I_j, sigma_j^2) back
@@ -542,18 +646,12 @@ def run_ours(args):
         return
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    clocks = clk.summary()
     peaks = measured_peaks()
     max_mhz = peaks.get("sm_max_mhz", 2070.0)
-    # issue peak: SMs x 4 schedulers x 32 lanes x clock, one lane operation per
-    # slot (FP32 FMA/ALU and integer alike); the FP32 flop peak counts an FMA as 2
-    issue_peak = n_sm * 128 * max_mhz * 1e6 / 1e12     # Tops/s at the maximum SM clock
-    fp32_peak = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     samples_per_step = evals / args.steps
-    k1_avg_ms = sum(k1_ms) / len(k1_ms)
-    main = args.workload == "four_peaks_d8"
-    timing_note = ("CUDA events around the sampling launch, mean of %d eager iterations after "
-                   "the timed steps" % KERNEL_TIMING_ITERS)
+    step_ms = total_ms / args.steps
+    timing_note = ("CUDA events around the sampling launch on its stream, mean of %d eager "
+                   "iterations after the timed steps" % KERNEL_TIMING_ITERS)
     if bayes:
         # FP64 path: bound by the FP64 pipe; peak from the nominal 1.25 TFLOP/s
         # (an FMA counted as 2 flops), i.e. 0.625e12 FP64 lane instructions/s
@@ -565,35 +663,14 @@ def run_ours(args):
                 "frac": k1_tops / fp64_peak, "traffic": None,
                 "kernel": "k_sample (fused a1-a5, FP64, 8 outputs)", "kernel_ms": k1_avg_ms,
                 "kernel_ms_note": timing_note,
-                "kernel_share_of_step": k1_avg_ms / (total_ms / args.steps),
+                "kernel_share_of_step": k1_avg_ms / step_ms,
                 "ops_per_sample": ops,
                 "peak_note": "FP64 lane instructions per second from the nominal 1.25 TFLOP/s "
                              "(fallback figure; FMA = 2 flops); library calls counted as one "
                              "operation each, so frac is a lower bound"}
     else:
-        ops = ops_per_sample(prob.dim, n_peaks, ball, expnorm=expo)
-        flops = (ball_flops_per_sample(prob.dim) if ball else
-                 flops_per_sample(prob.dim, n_peaks) + (n_peaks if expo else 0))
-        k1_tops = ops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
-        k1_tflops = flops * samples_per_step / (k1_avg_ms / 1e3) / 1e12
-        traffic = traffic_from_profile(kernel_source_hash()) if main else None
-        roof = {"bound": "alu", "achieved": k1_tops, "peak": issue_peak, "unit": "Tops/s",
-                "frac": k1_tops / issue_peak,
-                "traffic": traffic * samples_per_step / PROFILED_SAMPLES if traffic else None,
-                "kernel": "k_sample (fused a1-a5)", "kernel_ms": k1_avg_ms,
-                "kernel_ms_note": timing_note,
-                "kernel_share_of_step": k1_avg_ms / (total_ms / args.steps),
-                "ops_per_sample": ops,
-                "peak_note": "issue slots = SMs x 4 schedulers x 32 lanes x %.0f MHz (max SM "
-                             "clock); algorithmic lane operations counted from the kernel "
-                             "source" % max_mhz,
-                "fp32": {"achieved_tflops": k1_tflops, "peak_tflops": fp32_peak,
-                         "frac": k1_tflops / fp32_peak,
-                         "flops_per_sample": flops},
-                "ncu": traffic_from_profile(kernel_source_hash(), "fma_alu_issue") if main
-                else None}
-        if clocks.get("sm_mhz"):
-            roof["frac_at_measured_clock"] = k1_tops / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+        roof = _sample_roofline(args.workload, prob, n_peaks, samples_per_step, k1_avg_ms,
+                                step_ms, n_sm, clocks, max_mhz)
     if precond:
         h2d += data.size * 8
     integrand = ("ball" if ball else "exp(-50|x|), mixed strata %s" % list(g.strata()) if expo
@@ -605,7 +682,7 @@ def run_ours(args):
                  "fp32 map/integrand, Kahan fp32 moments, fp64 estimate")
     line = {"metric": "integrand evals/s", "value": value, "unit": "integrand evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, MIN_WARMUP),
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if bayes else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "dim": prob.dim, "n_ev": prob.n_ev,
                        "n_g": prob.n_g, "alpha": prob.alpha, "beta": prob.beta,
@@ -629,26 +706,31 @@ def run_ours(args):
         line["integral"]["means (p1, p2, w)"] = [float(v) for v in r["mean"][1:4] / r["mean"][0]]
     if training:
         line["training"] = training
+    g.close()
+    if ball and world == 1 and not args.no_extras:
+        # the other terms of the metric, measured in the same run
+        line["four_peaks_d8"] = _single_summary("four_peaks_d8", args, inputs, vegasp, flush,
+                                                n_sm, max_mhz)
+        del flush
+        torch.cuda.empty_cache()
+        line["batched_vs_plain"] = batch_summary(args, inputs, vegasp)
+        line["served"] = serve_summary(args, inputs, vegasp)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, out_mono=out_mono, data=data)
-        if args.workload == "four_peaks_d8":
-            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores("four_peaks_d8")
+        if args.workload in ("four_peaks_d8", "ball_d20"):
+            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args.workload)
     print(json.dumps(line), flush=True)
-    g.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_batch(args):
+def batch_summary(args, inputs, vegasp):
     """512 integrals (D 2..12, N_ev 1e4..1e6, 1-4 Gaussian peaks, N_g = 500,
-    15 iterations) in one persistent launch per iteration, against the same
-    integrals run one at a time through the single-integral path."""
+    15 iterations) in one persistent launch per iteration: device-timed steps
+    of the batch, then the whole batched job against the same integrals run
+    one at a time through the single-integral path (wall clock, same samples,
+    so equal relative error)."""
     import torch
-    from paper_2009_05112_gb300 import build as _build
-    from paper_2009_05112_gb300 import inputs, vegasp
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    _build.build()
-    vegasp.use_torch_allocator()
     probs = inputs.batch_mix(n=512, seed=1)
     n_it = 15
     stream = torch.cuda.current_stream()
@@ -671,6 +753,7 @@ def run_batch(args):
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     evals = sum(r["n_eval"] for r in bt.results()) - n0
     bt.close()
+    del flush
     # whole jobs, wall clock: batched and one integral at a time (same samples)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -692,25 +775,45 @@ def run_batch(args):
         g.close()
     torch.cuda.synchronize()
     wall_p = time.perf_counter() - t0
-    line = {"metric": "integrand evals/s", "value": evals / (total_ms / 1e3),
-            "unit": "integrand evals/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, MIN_WARMUP),
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    return {"workload": "batch_mix_512", "integrals": 512, "iterations": n_it,
+            "device_evals_per_s": evals / (total_ms / 1e3),
+            "device_ms_per_step": total_ms / args.steps, "steps": args.steps,
+            "wall_s_batched": wall_b, "wall_s_plain": wall_p,
+            "speedup_wall": wall_p / wall_b,
+            "evals_per_s_batched": evals_b / wall_b,
+            "evals_per_s_plain": evals_p / wall_p,
+            "median_rel_err_batched": statistics.median(rel_b),
+            "median_rel_err_plain": statistics.median(rel_p),
+            "note": "device: graph steps of all 512 integrals, L2 flushed between; wall: whole "
+                    "jobs (create from host parameters, 15 iterations, host read of every "
+                    "result), batched vs one integral at a time through the single-integral "
+                    "path, same samples",
+            "clocks": clk.summary()}
+
+
+def run_batch(args):
+    """The batched workload on its own line."""
+    import torch
+    from paper_2009_05112_gb300 import build as _build
+    from paper_2009_05112_gb300 import inputs, vegasp
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    vegasp.use_torch_allocator()
+    b = batch_summary(args, inputs, vegasp)
+    line = {"metric": "integrand evals/s", "value": b["device_evals_per_s"],
+            "unit": "integrand evals/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, MIN_WARMUP),
+            "ms_per_step": b["device_ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch_mix_512", "integrals": 512, "dim": "2..12",
-                       "n_ev": "log-uniform 1e4..1e6", "n_g": 500, "iterations": n_it,
+                       "n_ev": "log-uniform 1e4..1e6", "n_g": 500, "iterations": 15,
                        "l2": "flushed between timed steps (512 MiB write)"},
-            "e2e": {"value": evals_b / wall_b, "unit": "integrand evals/s",
+            "e2e": {"value": b["evals_per_s_batched"], "unit": "integrand evals/s",
                     "note": "whole batched job (create from host parameters, 15 graph steps, "
                             "host read of all results), wall clock"},
-            "batched_vs_plain": {"wall_s_batched": wall_b, "wall_s_plain": wall_p,
-                                 "speedup_wall": wall_p / wall_b,
-                                 "evals_per_s_batched": evals_b / wall_b,
-                                 "evals_per_s_plain": evals_p / wall_p,
-                                 "median_rel_err_batched": statistics.median(rel_b),
-                                 "median_rel_err_plain": statistics.median(rel_p)},
-            "clocks": clk.summary()}
+            "batched_vs_plain": b, "clocks": b["clocks"]}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_batch(probs, n_it)
+        line["cpu_baseline"] = cpu_baseline_batch(inputs.batch_mix(n=512, seed=1), 15)
     print(json.dumps(line), flush=True)
 
 
@@ -738,60 +841,82 @@ def _serve_once(vegasp, stream_t, probs, rules, max_active, paced):
     return got, wall, stats
 
 
-def run_serve(args):
-    """A Poisson stream of integration requests (mean 200/s; 70% D = 3, 30%
-    D = 21 Bayesian-posterior integrands, 50 points each, rtol 1e-3), served by
-    continuous batching (every admitted request advances one iteration per
-    server step) and, for comparison, one request at a time (max_active = 1)."""
+def _serve_figures(got, wall, st, probs):
     import numpy as np
-    import torch
-    from paper_2009_05112_gb300 import build as _build
-    from paper_2009_05112_gb300 import inputs, vegasp
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    _build.build()
+    lat = np.array([r["t_done"] - r["t_submit"] for r in got]) * 1e3
+    d21 = np.array([probs[r["tag"]].dim == 21 for r in got])
+    rel = np.array([r["sdev"] / abs(r["mean"]) for r in got])
+    return {"requests": len(got), "requests_per_s": len(got) / wall, "wall_s": wall,
+            "evals_per_s": sum(r["n_eval"] for r in got) / wall,
+            "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_d3": float(np.percentile(lat[~d21], 50)),
+            "p50_ms_d21": float(np.percentile(lat[d21], 50)),
+            "converged_frac": float(np.mean([r["converged"] for r in got])),
+            "median_rel_err": float(np.median(rel)),
+            "mean_iterations": float(np.mean([r["n_iter"] for r in got])),
+            "steps": st["steps"], "busy_s": st["busy_s"],
+            "peak_state_mib": st["bytes_peak"] / 2 ** 20}
+
+
+def serve_summary(args, inputs, vegasp):
+    """A Poisson stream of integration requests (mean 200/s; 70% D = 3, 30%
+    D = 21 Bayesian-posterior integrands, 50 points each, rtol 1e-3): the
+    first args.requests served at their arrival times by continuous batching
+    (every admitted request advances one iteration per server step) and one
+    request at a time (max_active = 1), with p50/p99 latency; the saturated
+    rates with requests queued at once (the whole stream of
+    args.saturated_requests batched; the first args.requests one at a time)."""
     rate = 200.0
-    stream_t, probs, rules = inputs.serve_stream(args.requests, rate=rate, seed=0)
+    n_all = max(args.requests, args.saturated_requests)
+    stream_t, probs, rules = inputs.serve_stream(n_all, rate=rate, seed=0)
+    n = args.requests
     # warm-up: a few requests through both configurations
     _serve_once(vegasp, stream_t[:8], probs[:8], rules[:8], 0, False)
     _serve_once(vegasp, stream_t[:8], probs[:8], rules[:8], 1, False)
     out = {}
     with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        for name, max_active, paced in [("served", 0, True), ("plain", 1, True),
-                                        ("served_saturated", 0, False),
-                                        ("plain_saturated", 1, False)]:
-            got, wall, st = _serve_once(vegasp, stream_t, probs, rules, max_active, paced)
-            lat = np.array([r["t_done"] - r["t_submit"] for r in got]) * 1e3
-            d21 = np.array([probs[r["tag"]].dim == 21 for r in got])
-            rel = np.array([r["sdev"] / abs(r["mean"]) for r in got])
-            out[name] = {"requests_per_s": len(got) / wall, "wall_s": wall,
-                         "evals_per_s": sum(r["n_eval"] for r in got) / wall,
-                         "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99)),
-                         "p50_ms_d3": float(np.percentile(lat[~d21], 50)),
-                         "p50_ms_d21": float(np.percentile(lat[d21], 50)),
-                         "converged_frac": float(np.mean([r["converged"] for r in got])),
-                         "median_rel_err": float(np.median(rel)),
-                         "mean_iterations": float(np.mean([r["n_iter"] for r in got])),
-                         "steps": st["steps"], "busy_s": st["busy_s"],
-                         "peak_state_mib": st["bytes_peak"] / 2 ** 20}
+        for name, max_active, paced, m in [("served", 0, True, n), ("plain", 1, True, n),
+                                           ("served_saturated", 0, False,
+                                            args.saturated_requests),
+                                           ("plain_saturated", 1, False, n)]:
+            got, wall, st = _serve_once(vegasp, stream_t[:m], probs[:m], rules[:m], max_active,
+                                        paced)
+            out[name] = _serve_figures(got, wall, st, probs)
+    out["config"] = {"arrivals": "Poisson, mean %g/s" % rate, "mix": "70% D=3, 30% D=21",
+                     "n_ev": "1e4 (D=3), 3e4 (D=21)", "n_g": 1000, "rtol": 1e-3,
+                     "stop": {str(k): v for k, v in inputs.SERVE_RULE.items()},
+                     "paced_requests": n, "saturated_requests": args.saturated_requests,
+                     "note": "paced: the first %d requests of the stream submitted at their "
+                             "arrival times (latency = submit to result); saturated: requests "
+                             "queued at once, wall clock from first submit to last result" % n}
+    out["p50_ms"] = out["served"]["p50_ms"]
+    out["p99_ms"] = out["served"]["p99_ms"]
+    out["latency_speedup_p99"] = out["plain"]["p99_ms"] / out["served"]["p99_ms"]
+    out["clocks"] = clk.summary()
+    return out
+
+
+def run_serve(args):
+    """The served workload on its own line (value: the saturated rate)."""
+    import torch
+    from paper_2009_05112_gb300 import build as _build
+    from paper_2009_05112_gb300 import inputs, vegasp
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    out = serve_summary(args, inputs, vegasp)
     sat = out["served_saturated"]
     line = {"metric": "served requests/s", "value": sat["requests_per_s"],
             "unit": "requests/s", "n_gpus": 1, "steps": sat["steps"], "warmup": 8,
             "ms_per_step": 1e3 * sat["busy_s"] / max(1, sat["steps"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "serve_posteriors", "requests": args.requests,
-                       "arrivals": "Poisson, mean %g/s" % rate, "mix": "70% D=3, 30% D=21",
-                       "n_ev": "1e4 (D=3), 3e4 (D=21)", "n_g": 1000, "rtol": 1e-3,
-                       "stop": {str(k): v for k, v in inputs.SERVE_RULE.items()},
-                       "l2": "each step touches a few MB of request state (fits L2); "
-                             "latency, not bandwidth, bounds this workload"},
-            "value_note": "value: all requests queued at once (saturation), wall clock from "
-                          "first submit to last result; paced: the Poisson stream in real time",
-            "served": out["served"], "plain": out["plain"],
-            "served_saturated": sat, "plain_saturated": out["plain_saturated"],
-            "clocks": clk.summary()}
+            "config": dict(out["config"], workload="serve_posteriors",
+                           l2="each step touches a few MB of request state (fits L2); "
+                              "latency, not bandwidth, bounds this workload"),
+            "served": out, "clocks": out["clocks"]}
     if not args.no_cpu_baseline:
+        _, probs, rules = inputs.serve_stream(args.requests, rate=200.0, seed=0)
         line["cpu_baseline"] = cpu_baseline_serve(probs, rules)
     print(json.dumps(line), flush=True)
 

@@ -281,6 +281,14 @@ vp_status vp_get_moments(vp_ctx *ctx, double *s1, double *s2);
 vp_status vp_get_hist(vp_ctx *ctx, double *hsum, double *hcnt);
 /* I_j and sigma_j^2 of the first n iterations */
 vp_status vp_get_history(vp_ctx *ctx, int n, double *i_j, double *var_j);
+/* d_h[N_h] = sigma_h^beta (§3 Eq. dh) as the latest estimate (vp_iterate) or
+ * vp_alloc_from_sigma / vp_alloc_from_dh left it, and *sum_d = their sum in
+ * the library's fixed order (either pointer may be NULL).  On the FP64 path
+ * and from a given sigma_h, beta = 1/2 and 3/4 are correctly rounded square
+ * roots (sqrt(sigma), sqrt(sigma sqrt(sigma))), other beta pow; the FP32
+ * path's estimate forms d_h from the variance with the FP32 log2 / exp2
+ * units (relative error below 1e-6). */
+vp_status vp_get_dh(vp_ctx *ctx, double *d_h, double *sum_d);
 /* Reallocation (a7) from given d_h[N_h] (skips sigma_h and the damping) or
  * from given sigma_h[N_h] (applies d_h = sigma_h^beta); sets n_h and offsets. */
 vp_status vp_alloc_from_dh(vp_ctx *ctx, const double *d_h, void *stream);
@@ -436,7 +444,8 @@ vp_status vp_server_destroy(vp_server *s);
  *   n_h      [n_hc] DEVICE uint32 (written)
  *   offsets  [n_hc + 1] DEVICE uint64 (written; offsets[n_hc] = sum of n_h)
  *   n_hc     1 .. 4,194,304 (VP_EINVAL beyond: the scratch holds 4096 blocks of
- *            1024 hypercubes); n_ev >= 2
+ *            1024 hypercubes); n_ev 2 .. 4,294,967,293 (every n_h, at most
+ *            n_ev + 2, is a 32-bit integer)
  * Work is enqueued on stream; nothing is allocated and nothing is freed.  Its
  * scratch is one static device array of about 64 KB, which every GPU that loads
  * the library holds until the process exits.  The first call on a device looks

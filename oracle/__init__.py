@@ -206,8 +206,11 @@ def sigma(omega, s1, s2, n_h):
 
 
 def damp(beta, sig):
-    """§3 Eq. (dh): d_h = sigma_h^beta.  Pinned by beta = 0 (every d_h = 1,
-    the equal split) and beta = 1 (d_h = sigma_h exactly)."""
+    """§3 Eq. (dh): d_h = sigma_h^beta (beta = 1/2 and 3/4 through correctly
+    rounded square roots, other beta through pow).  Pinned by beta = 0 (every
+    d_h = 1, the equal split), beta = 1 (d_h = sigma_h exactly), exact powers
+    (16^(3/4) = 8, 81^(1/4) = 3, 4^(3/2) = 8, ...) and 50-digit decimal powers
+    at beta = 1/2, 3/4 and general beta (within an ulp)."""
     sig = np.ascontiguousarray(sig, np.float64)
     out = np.zeros_like(sig)
     lib().or_damp(sig.size, float(beta), sig, out)

@@ -443,11 +443,20 @@ void or_sigma(int64_t n_hc, double omega, const double *s1, const double *s2,
 
 /* §3 step 3, Eq. (dh): d_h = sigma_h^beta (beta = 0 gives d_h = 1, beta = 1   */
 /* gives d_h = sigma_h, both exactly).                                         */
+/* reading: the powers 1/2 and 3/4 (the paper's default beta) are taken as     */
+/* correctly rounded IEEE square roots, sigma^(1/2) = sqrt(sigma) and          */
+/* sigma^(3/4) = sqrt(sigma * sqrt(sigma)) (two roots, one product, each       */
+/* rounded once), so that the result is one fixed IEEE sequence on every       */
+/* machine; any other beta goes through pow.                                   */
 void or_damp(int64_t n_hc, double beta, const double *sigma, double *d) {
     for (int64_t h = 0; h < n_hc; ++h) {
         if (beta == 0.0) d[h] = 1.0;
         else if (beta == 1.0) d[h] = sigma[h];
-        else d[h] = pow(sigma[h], beta);
+        else if (beta == 0.5) d[h] = sqrt(sigma[h]);
+        else if (beta == 0.75) {
+            double r = sqrt(sigma[h]);
+            d[h] = sqrt(sigma[h] * r);
+        } else d[h] = pow(sigma[h], beta);
     }
 }
 

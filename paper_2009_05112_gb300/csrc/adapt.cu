@@ -88,13 +88,16 @@ __global__ void k_chunks(const Desc *desc, const uint32_t *members, int n_group,
 
 struct D3 { double a, b, c; };
 
-// d_h = sigma_h^beta; beta = 0 and 1 exactly; 1/2 and 3/4 (the paper's
-// default) through square roots, within an ulp or two of pow.
+// d_h = sigma_h^beta (§3 Eq. dh); beta = 0 and 1 exactly; 1/2 and 3/4 (the
+// paper's default) as correctly rounded square roots, sqrt(sigma) and
+// sqrt(sigma * sqrt(sigma)) -- each operation rounded once, the library's
+// reading of these two powers, so that d_h (and every n_h) is reproducible
+// bit for bit from sigma_h; other beta through pow.
 __device__ __forceinline__ double damp(double sigma, double beta) {
     if (beta == 0.0) return 1.0;
     if (beta == 1.0) return sigma;
-    if (beta == 0.5) return sqrt(sigma);
-    if (beta == 0.75) return sqrt(sigma * sqrt(sigma));
+    if (beta == 0.5) return __dsqrt_rn(sigma);
+    if (beta == 0.75) return __dsqrt_rn(__dmul_rn(sigma, __dsqrt_rn(sigma)));
     return pow(sigma, beta);
 }
 

@@ -1805,6 +1805,15 @@ extern "C" vp_status vp_get_hist(vp_ctx *c, double *hsum, double *hcnt) {
     return VP_OK;
 }
 
+extern "C" vp_status vp_get_dh(vp_ctx *c, double *d_h, double *sum_d) {
+    CHECK_CTX(c);
+    const Desc &d = c->set.h_desc[0];
+    CU(cudaStreamSynchronize(c->set.last));
+    if (d_h) CU(cudaMemcpy(d_h, d.dh, d.n_hc * 8, cudaMemcpyDeviceToHost));
+    if (sum_d) CU(cudaMemcpy(sum_d, &d.st->sum_d, 8, cudaMemcpyDeviceToHost));
+    return VP_OK;
+}
+
 extern "C" vp_status vp_get_history(vp_ctx *c, int n, double *i_j, double *var_j) {
     CHECK_CTX(c);
     const Desc &d = c->set.h_desc[0];

@@ -192,7 +192,12 @@ extern "C" vp_status vp_alloc_static(const double *d_h, int64_t n_hc, int64_t n_
                    VP_EINVAL, "vp_alloc_static: n_hc must be 1..4194304 (the static scratch holds "
                               "4096 blocks of 1024 hypercubes)"),
                VP_EINVAL;
-    if (n_ev < 2) return vp::set_error_message(VP_EINVAL, "vp_alloc_static: n_ev must be >= 2"), VP_EINVAL;
+    // every n_h is at most floor(N_ev) (+ 2 with plus2) and is stored as a
+    // 32-bit integer: larger N_ev would not fit (the contexts bound N_ev more
+    // tightly still, through the Philox counter)
+    if (n_ev < 2 || n_ev > (int64_t)0xFFFFFFFFll - 2)
+        return vp::set_error_message(VP_EINVAL, "vp_alloc_static: n_ev must be 2 .. 4294967293"),
+               VP_EINVAL;
     StaticScratch *sc = nullptr;
     vp_status st = scratch_for_current_device(&sc);
     if (st != VP_OK) return st;

@@ -109,6 +109,7 @@ _SIGS = {
     "vp_get_moments": [_P, _P, _P],
     "vp_get_hist": [_P, _P, _P],
     "vp_get_history": [_P, ctypes.c_int, _P, _P],
+    "vp_get_dh": [_P, _P, ctypes.POINTER(ctypes.c_double)],
     "vp_alloc_from_dh": [_P, _P, _P],
     "vp_alloc_from_sigma": [_P, _P, _P],
     "vp_refine_from_hist": [_P, _P, _P, _P],
@@ -417,6 +418,13 @@ class Integrator:
         I, V = np.zeros(n), np.zeros(n)
         check(lib().vp_get_history(self.ctx, n, _ptr(I), _ptr(V)))
         return I, V
+
+    def dh(self):
+        """(d_h[N_h], sum d) as the latest estimate or reallocation left them."""
+        d = np.zeros(self.n_hc)
+        sd = ctypes.c_double(0.0)
+        check(lib().vp_get_dh(self.ctx, _ptr(d), ctypes.byref(sd)))
+        return d, sd.value
 
     def alloc_from_dh(self, d_h):
         d = np.ascontiguousarray(d_h, np.float64)

@@ -434,6 +434,39 @@ def test_allocate_special_cases():
         oracle.allocate(100, np.array([1.0, np.nan]))
 
 
+def test_damp_exact_powers():
+    """§3 Eq. (dh), d_h = sigma_h^beta, on every branch of the oracle (beta =
+    1/2 and 3/4 by square roots, anything else by pow) at arguments whose power
+    is an exact double: a squared sigma, an inverted exponent or a swapped
+    argument fails here."""
+    cases = [(0.5, 4.0, 2.0), (0.5, 2.25, 1.5), (0.5, 2.0 ** -60, 2.0 ** -30),
+             (0.75, 16.0, 8.0), (0.75, 81.0, 27.0), (0.75, 0.0625, 0.125),
+             (0.75, 2.0 ** -40, 2.0 ** -30), (0.75, 2.0 ** 80, 2.0 ** 60), (0.75, 0.0, 0.0),
+             (0.25, 81.0, 3.0), (0.25, 16.0, 2.0), (1.5, 4.0, 8.0), (2.0, 3.0, 9.0),
+             (1.25, 16.0, 32.0), (0.125, 256.0, 2.0)]
+    for beta, s, expect in cases:
+        assert oracle.damp(beta, np.array([s]))[0] == expect, (beta, s)
+
+
+@pytest.mark.parametrize("beta", [0.5, 0.75, 0.3, 0.6, 1.7])
+def test_damp_against_decimal_powers(beta):
+    """sigma^beta within an ulp or two of the 50-digit decimal power: the
+    square-root forms (beta = 1/2, 3/4) round three times at most (2 ulp
+    bound), pow within 1 ulp."""
+    import decimal
+    ctx = decimal.Context(prec=50)
+    rng = np.random.default_rng(int(beta * 1000))
+    sig = rng.exponential(size=400) * 10.0 ** rng.uniform(-120, 120, size=400)
+    d = oracle.damp(beta, sig)
+    bound = 2.0 if beta in (0.5, 0.75) else 1.0
+    worst = 0.0
+    for s, v in zip(sig, d):
+        exact = ctx.power(decimal.Decimal(float(s)), decimal.Decimal(beta))
+        err = abs(decimal.Decimal(float(v)) - exact) / decimal.Decimal(math.ulp(float(exact)))
+        worst = max(worst, float(err))
+    assert worst <= bound, worst
+
+
 def test_sigma_matches_sample_spread():
     """§3 step 2: sigma_h^2 = Omega^2 (mean (Jf)^2 - mean(Jf)^2) per hypercube."""
     s1 = np.array([3.0, 0.0, 10.0])
