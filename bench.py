@@ -845,7 +845,7 @@ def _serve_figures(got, wall, st, probs):
     import numpy as np
     lat = np.array([r["t_done"] - r["t_submit"] for r in got]) * 1e3
     d21 = np.array([probs[r["tag"]].dim == 21 for r in got])
-    rel = np.array([r["sdev"] / abs(r["mean"]) for r in got])
+    rel = np.array([r["sdev"] / abs(r["mean"]) if r["mean"] else float("inf") for r in got])
     return {"requests": len(got), "requests_per_s": len(got) / wall, "wall_s": wall,
             "evals_per_s": sum(r["n_eval"] for r in got) / wall,
             "p50_ms": float(np.percentile(lat, 50)),
@@ -853,6 +853,7 @@ def _serve_figures(got, wall, st, probs):
             "p50_ms_d3": float(np.percentile(lat[~d21], 50)),
             "p50_ms_d21": float(np.percentile(lat[d21], 50)),
             "converged_frac": float(np.mean([r["converged"] for r in got])),
+            "zero_estimates": int(sum(1 for r in got if not r["mean"])),
             "median_rel_err": float(np.median(rel)),
             "mean_iterations": float(np.mean([r["n_iter"] for r in got])),
             "steps": st["steps"], "busy_s": st["busy_s"],

@@ -196,6 +196,33 @@ vp_status vp_step(vp_ctx *ctx, void *stream);
 vp_status vp_step_read(vp_ctx *ctx, void *stream, int *have, double *i_j, double *var_j);
 vp_status vp_step_read_flush(vp_ctx *ctx, int *have, double *i_j, double *var_j);
 
+/* ---- one integral over several devices ---------------------------------- */
+/* vegas+ shards by samples (§1: the method parallelises easily; §3 Eq. sumI
+ * and the d_i of §2.3/§2.4 are sums over all samples).  Every rank creates a
+ * context with the same parameters; per iteration each rank
+ *   vp_iterate_part(ctx, rank, n_ranks, stream)   steps a1-a5 over samples
+ *        [T rank / n_ranks, T (rank + 1) / n_ranks) of the T samples the
+ *        current allocation draws (contiguous in the offsets, equal in
+ *        samples), adding to the iteration's partial sums;
+ *   vp_partials_export(ctx, buf, stream)   packs those sums into buf, a DEVICE
+ *        vector of vp_partials_size doubles: [S1_h, S2_h (N_h each) | hsum,
+ *        hcnt (D N_g each, counts as doubles)];
+ *   (the caller sums buf over the ranks, e.g. an NCCL all-reduce in place)
+ *   vp_partials_import(ctx, buf, stream)   replaces the sums by the total;
+ *   vp_estimate(ctx, stream)   step a6 (and sigma_h, d_h) from them, recorded
+ *        as the iteration (what vp_iterate does after its sampling);
+ *   vp_adapt(ctx, stream)      as usual.
+ * Identical sums give identical estimates, allocations and grids on every
+ * rank.  FP32 peak families with more than 8 peaks, and contexts with extra
+ * outputs, are refused (VP_EINVAL).  vp_iterate_part may be called for
+ * several parts on one context (they add up).  Buffers are the caller's;
+ * nothing is allocated. */
+vp_status vp_iterate_part(vp_ctx *ctx, int part, int n_parts, void *stream);
+vp_status vp_partials_size(vp_ctx *ctx, int64_t *n);
+vp_status vp_partials_export(vp_ctx *ctx, double *buf, void *stream);
+vp_status vp_partials_import(vp_ctx *ctx, const double *buf, void *stream);
+vp_status vp_estimate(vp_ctx *ctx, void *stream);
+
 /* Synchronises the context's stream, reads the iteration history and
  * combines iterations j >= discard (§2.5).  VP_ENONFINITE if any iteration saw
  * a non-finite integrand value (out still filled). */

@@ -27,6 +27,7 @@
 //
 // The per-hypercube kernels are memory-bound streams over N_h elements; the
 // refinement is one CTA per (integral, axis) and latency-bound at N_g <= 4096.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cstdio>
 
@@ -831,6 +832,44 @@ __global__ void __launch_bounds__(kMultiThreads) k_estimate_multi(const Desc *de
         __syncthreads();
     }
     if (t == 0) d.st->done_multi = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// k_partials: one integral sampled in parts (several devices, each a range of
+// the iteration's samples) -- the partial sums of the current iteration
+// (buffer t & 1): S1_h, S2_h [N_h] (§3 step 2), hsum, hcnt [D][N_g] (§2.3
+// d_i), packed into (dir 0) or unpacked from (dir 1) one flat FP64 vector
+// [S1 | S2 | hsum | hcnt], the counts as doubles (exact: below 2^32).  The sum
+// of every part's vector is the vector of the whole iteration, so the
+// exchange is one FP64 sum over the devices.
+// ---------------------------------------------------------------------------
+__global__ void k_partials(const Desc *desc, double *buf, int dir) {
+    pdl_wait();
+    pdl_trigger();
+    const Desc &d = desc[0];
+    const uint64_t par = __ldcg(&d.st->t) & 1u;
+    const uint64_t nh = d.n_hc, bins = (uint64_t)d.dim * (uint64_t)d.n_g;
+    double *s1 = d.s1 + par * nh, *s2 = d.s2 + par * nh, *hs = d.hsum + par * bins;
+    uint32_t *hc = d.hcnt + par * bins;
+    const uint64_t total = 2 * nh + 2 * bins;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        double *p = nullptr;
+        uint32_t *pc = nullptr;
+        if (i < nh) p = s1 + i;
+        else if (i < 2 * nh) p = s2 + (i - nh);
+        else if (i < 2 * nh + bins) p = hs + (i - 2 * nh);
+        else pc = hc + (i - 2 * nh - bins);
+        if (dir == 0) buf[i] = p ? *p : (double)*pc;
+        else if (p) *p = buf[i];
+        else *pc = (uint32_t)buf[i];
+    }
+}
+
+cudaError_t launch_partials(const Desc *desc, double *buf, uint64_t n, int dir, cudaStream_t s) {
+    const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 152ull * 8);
+    return launch_pdl(k_partials, dim3((unsigned)std::max<uint64_t>(blocks, 1)), dim3(256), s,
+                      desc, buf, dir);
 }
 
 cudaError_t launch_estimate_multi(const Desc *desc, uint32_t n_blocks, cudaStream_t s) {

@@ -463,6 +463,9 @@ static vp_status plan_groups(Set &s) {
             g.blocks = best;
         }
         set_task(g, (double)s.m[g.members[0]].p.n_ev + 2.0 * (double)s.m[g.members[0]].n_hc);
+        g.blocks_plan = g.blocks;
+        g.cs_plan = g.cs;
+        g.threads_plan = g.threads;
     }
     return VP_OK;
 }
@@ -1378,6 +1381,95 @@ extern "C" vp_status vp_adapt(vp_ctx *c, void *stream) {
 extern "C" vp_status vp_step(vp_ctx *c, void *stream) {
     CHECK_CTX(c);
     return set_step(c->set, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// One integral over several devices (ranks): each samples a part of the
+// iteration's samples, the parts' partial sums are added across ranks, and
+// every rank then runs the same estimate and adaptation on the same sums.
+// ---------------------------------------------------------------------------
+static vp_status shard_check(vp_ctx *c) {
+    CHECK_CTX(c);
+    const Set &s = c->set;
+    if (s.groups.size() != 1 || s.groups[0].blocks_plan == 0)
+        return fail(VP_EINVAL, "sampling in parts needs the one-integral kernel (FP32 peak "
+                               "families: at most %d peaks)", kParamPeaks);
+    if (s.m[0].n_out > 1) return fail(VP_EINVAL, "sampling in parts: one output only");
+    return VP_OK;
+}
+
+extern "C" vp_status vp_iterate_part(vp_ctx *c, int part, int n_parts, void *stream) {
+    vp_status st = shard_check(c);
+    if (st != VP_OK) return st;
+    if (n_parts < 1 || n_parts > 65536 || part < 0 || part >= n_parts)
+        return fail(VP_EINVAL, "part must be in 0..n_parts-1, n_parts in 1..65536");
+    NvtxRange nv("vp.iterate_part");
+    Set &s = c->set;
+    cudaStream_t strm = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(strm, &cap));
+    if (cap != cudaStreamCaptureStatusActive) {
+        st = tune(s, strm);
+        if (st != VP_OK) return st;
+    }
+    // the one-integral kernel in its tuned shape, or its planned one if the
+    // tuner chose the task kernel (which has no sample ranges)
+    Group g = s.groups[0];
+    if (!g.one) {
+        g.one = true;
+        g.blocks = g.blocks_plan;
+        g.cs = g.cs_plan;
+        g.threads_one = g.threads_plan;
+    }
+    g.args1.part = part;
+    g.args1.n_parts = n_parts;
+    st = launch_group(s.d_desc, g, strm);
+    if (st != VP_OK) return st;
+    s.last = strm;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_partials_size(vp_ctx *c, int64_t *n) {
+    CHECK_CTX(c);
+    if (!n) return fail(VP_EINVAL, "NULL out");
+    const Desc &d = c->set.h_desc[0];
+    *n = (int64_t)(2 * d.n_hc + 2 * (uint64_t)d.dim * (uint64_t)d.n_g);
+    return VP_OK;
+}
+
+static vp_status partials_move(vp_ctx *c, double *buf, int dir, cudaStream_t stream) {
+    vp_status st = shard_check(c);
+    if (st != VP_OK) return st;
+    if (!buf) return fail(VP_EINVAL, "NULL buffer");
+    cudaPointerAttributes pa;
+    CU(cudaPointerGetAttributes(&pa, buf));
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+        return fail(VP_EINVAL, "the partial sums buffer must be device memory");
+    int64_t n = 0;
+    vp_partials_size(c, &n);
+    CU(launch_partials(c->set.d_desc, buf, (uint64_t)n, dir, stream));
+    c->set.last = stream;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_partials_export(vp_ctx *c, double *buf, void *stream) {
+    return partials_move(c, buf, 0, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_partials_import(vp_ctx *c, const double *buf, void *stream) {
+    return partials_move(c, (double *)buf, 1, (cudaStream_t)stream);
+}
+
+extern "C" vp_status vp_estimate(vp_ctx *c, void *stream) {
+    vp_status st = shard_check(c);
+    if (st != VP_OK) return st;
+    Set &s = c->set;
+    CU(launch_estimate(s.d_desc, s.d_tree_base, 1, s.n_tree_total, 0, (cudaStream_t)stream));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
+    if (cap != cudaStreamCaptureStatusActive) ++s.iters;
+    s.last = (cudaStream_t)stream;
+    return VP_OK;
 }
 
 extern "C" vp_status vp_step_read(vp_ctx *c, void *stream, int *have, double *i_j,

@@ -31,6 +31,7 @@ cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, 
 cudaError_t launch_estimate_multi(const Desc *, uint32_t, cudaStream_t);
 cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t, int initial);
 cudaError_t launch_refine(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
+cudaError_t launch_partials(const Desc *, double *, uint64_t, int dir, cudaStream_t);
 
 
 // the calling thread's last error message (vp_last_error)
@@ -94,6 +95,9 @@ struct Group {
     bool solo = false;    // a group of one member by construction (several outputs)
     int cs = 1;        // CTAs per cluster (one-integral kernel)
     int threads_one = 256;  // CTA size of the one-integral kernel
+    // the one-integral kernel's shape as planned (before the autotuner), for
+    // launches that need that kernel whatever the tuner chose (sharded sampling)
+    int blocks_plan = 0, cs_plan = 1, threads_plan = 256;
     // histograms of the one-integral kernel (one CTA per SM fits more shared
     // memory than the task kernel's two): kHist* mode and dynamic shared bytes
     int hist_one = 0;

@@ -318,6 +318,10 @@ struct SampleOne {
     int n_out;
     int32_t mono[2 * kMaxOut];
     double *x1, *x2;           // double-buffered bases [2][n_hc][M], [2][n_hc][M (M+1)/2]
+    // one integral over several devices: this launch samples part `part` of
+    // n_parts equal, contiguous ranges of the iteration's samples (n_parts <= 1:
+    // all of them)
+    int part, n_parts;
 };
 
 // Fire-and-forget global reductions.
@@ -1007,9 +1011,14 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
         // by a runtime value would run on the scarce FP64 units.
         const uint32_t W = gridDim.x * (blockDim.x >> 5);
         const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        const uint32_t n_tot = (uint32_t)P.n_total;
+        uint32_t n_tot = (uint32_t)P.n_total, lo = 0u;
+        if (a.n_parts > 1) {  // samples [T p / P, T (p + 1) / P) of the T in the iteration
+            const uint64_t T = P.n_total;
+            lo = (uint32_t)(T * (uint64_t)a.part / (uint64_t)a.n_parts);
+            n_tot = (uint32_t)(T * (uint64_t)(a.part + 1) / (uint64_t)a.n_parts) - lo;
+        }
         const uint32_t per_w = n_tot / W, extra = n_tot - per_w * W;
-        const uint64_t wb = (uint64_t)w * per_w + min(w, extra);
+        const uint64_t wb = (uint64_t)lo + (uint64_t)w * per_w + min(w, extra);
         const uint64_t we = wb + per_w + (w < extra ? 1u : 0u);
         const uint64_t q = (we - wb + 31) / 32;
         const uint64_t s0 = min(wb + (uint64_t)lane * q, we);

@@ -110,6 +110,11 @@ _SIGS = {
     "vp_get_hist": [_P, _P, _P],
     "vp_get_history": [_P, ctypes.c_int, _P, _P],
     "vp_get_dh": [_P, _P, ctypes.POINTER(ctypes.c_double)],
+    "vp_iterate_part": [_P, ctypes.c_int, ctypes.c_int, _P],
+    "vp_partials_size": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "vp_partials_export": [_P, _P, _P],
+    "vp_partials_import": [_P, _P, _P],
+    "vp_estimate": [_P, _P],
     "vp_alloc_from_dh": [_P, _P, _P],
     "vp_alloc_from_sigma": [_P, _P, _P],
     "vp_refine_from_hist": [_P, _P, _P, _P],
@@ -418,6 +423,27 @@ class Integrator:
         I, V = np.zeros(n), np.zeros(n)
         check(lib().vp_get_history(self.ctx, n, _ptr(I), _ptr(V)))
         return I, V
+
+    # one integral over several devices: sampling in parts, the partial sums
+    # exchanged by the caller, then the estimate (see vegasp.h)
+    def iterate_part(self, part, n_parts):
+        check(lib().vp_iterate_part(self.ctx, int(part), int(n_parts), self.stream))
+
+    def partials_size(self):
+        n = ctypes.c_int64(0)
+        check(lib().vp_partials_size(self.ctx, ctypes.byref(n)))
+        return n.value
+
+    def export_partials(self, dev_ptr):
+        """Packs the iteration's partial sums into the device buffer at
+        dev_ptr (partials_size() doubles)."""
+        check(lib().vp_partials_export(self.ctx, ctypes.c_void_p(int(dev_ptr)), self.stream))
+
+    def import_partials(self, dev_ptr):
+        check(lib().vp_partials_import(self.ctx, ctypes.c_void_p(int(dev_ptr)), self.stream))
+
+    def estimate(self):
+        check(lib().vp_estimate(self.ctx, self.stream))
 
     def dh(self):
         """(d_h[N_h], sum d) as the latest estimate or reallocation left them."""

@@ -216,3 +216,59 @@ def test_worker_thread_serves_a_stream():
     for r in got:
         assert t0 <= r["t_submit"] <= r["t_admit"] <= r["t_done"]
         assert r["status"] == V().VP_OK and np.isfinite(r["mean"])
+
+
+def test_staggered_admission_same_as_alone():
+    """Continuous batching with requests arriving while others run: three
+    requests start, the server steps a few times, then six more arrive; one
+    is admitted at once beside the running three, and a slot limit and a
+    memory budget keep the others queued until earlier ones retire.  Every request -- early, admitted mid-run, or held
+    back -- ends with the iterations and the result it has when served
+    alone (within 1e-9) and that the oracle's run and stop rule give (1e-10)."""
+    probs = requests(seed=14) + requests(seed=15)[:2]
+    early, late = probs[:3], probs[3:]
+    max_it = 25
+    # four slots, and a budget for about four requests' state (the largest is
+    # a D = 21 one): one late request starts at once, the others wait
+    _, st1 = serve([p for p in probs if p.dim == 21][:1], V().VP_FP64)
+    srv = V().Server(mem_budget=4 * st1["bytes_peak"] + st1["bytes_peak"] // 2, max_active=4)
+    for i, p in enumerate(early):
+        srv.submit(p, max_it=max_it, precision=V().VP_FP64, tag=i, **RULE)
+    out, admitted_mid_run = {}, []
+    for _ in range(3):
+        srv.step()
+        for r in srv.poll():
+            out[r["tag"]] = r
+    assert srv.stats()["active"] > 0  # the early requests are mid-run
+    for k, p in enumerate(late):
+        srv.submit(p, max_it=max_it, precision=V().VP_FP64, tag=3 + k, **RULE)
+    queued_at_arrival = srv.stats()["queued"]
+    for _ in range(10 * max_it * len(probs)):
+        n = srv.step()
+        for r in srv.poll():
+            out[r["tag"]] = r
+        if n == 0 and srv.stats()["queued"] == 0:
+            break
+    srv.close()
+    assert len(out) == len(probs)
+    assert queued_at_arrival > 0  # some late requests waited for a slot
+    first_done = min(out[i]["t_done"] for i in range(3))
+    # a late request ran beside the early ones, and others were admitted only
+    # after an early one retired
+    assert any(out[3 + k]["t_admit"] < first_done for k in range(len(late)))
+    assert any(out[3 + k]["t_admit"] >= first_done for k in range(len(late)))
+    assert all(out[3 + k]["t_submit"] > max(out[i]["t_admit"] for i in range(3))
+               for k in range(len(late)))
+    for i, p in enumerate(probs):
+        alone, _ = serve([p], V().VP_FP64, max_it=max_it)
+        a, m = alone[0], out[i]
+        assert a["n_iter"] == m["n_iter"], i
+        assert m["mean"] == pytest.approx(a["mean"], rel=1e-9, abs=1e-300), i
+        assert m["sdev"] == pytest.approx(a["sdev"], rel=1e-9, abs=1e-300), i
+        o = oracle_of(p)
+        o.run(max_it)
+        t, conv = stop_iteration(np.array(o.I), np.array(o.var), max_it=max_it, **{
+            k: RULE[k] for k in ("rtol", "discard", "min_meas")})
+        assert m["n_iter"] == t and m["converged"] == conv, (i, m["n_iter"], t)
+        ro = oracle.combine(np.array(o.I[:t]), np.array(o.var[:t]), discard=RULE["discard"])
+        assert m["mean"] == pytest.approx(ro["mean"], rel=1e-10), i
