@@ -332,15 +332,19 @@ vp_status vp_eval_samples(vp_ctx *ctx, int64_t n, const uint64_t *h, const uint3
  * events); -1 if none recorded. */
 vp_status vp_last_sample_ms(vp_ctx *ctx, float *ms);
 /* Launch shape of the sampling kernel chosen by the autotuner (which runs at
- * the first vp_iterate/vp_step): scheme 0 = static balanced split with
- * clusters of `cluster` CTAs, 1 = dynamic tasks with `run` samples per thread
- * per chunk; `blocks` CTAs of `threads` threads. */
+ * the first vp_iterate/vp_step): scheme 0 = the one-integral kernel, its
+ * samples split evenly over its warps, with clusters of `cluster` CTAs;
+ * 1 = dynamic tasks with `run` samples per thread per chunk; 2 = the
+ * one-integral kernel with half of its samples split evenly over its warps
+ * and the other half pulled by the warps as they finish, in chunks of 32 x
+ * `run` samples (sample costs differ with the allocation and the integrand);
+ * `blocks` CTAs of `threads` threads. */
 vp_status vp_get_tuning(vp_ctx *ctx, int *scheme, int *blocks, int *threads, int *cluster,
                         int *run);
 /* Fixes the sampling kernel's launch shape instead of letting the autotuner
  * choose it (reproducible timing and profiling; no counterpart in the paper,
  * the shape does not change any result beyond FP summation order).
- * Arguments as in vp_get_tuning: scheme 0 requires all `blocks` CTAs of
+ * Arguments as in vp_get_tuning: schemes 0 and 2 require all `blocks` CTAs of
  * `threads` (256, 512, 768 or 1024, within the kernel's limit) resident at once, in
  * clusters of `cluster` (1, 2, 4, 8; > 1 only with shared-memory histograms);
  * scheme 1 takes threads = 256 and cluster = 1; run in 1..64.  Synchronises

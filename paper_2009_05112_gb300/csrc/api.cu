@@ -420,6 +420,13 @@ static vp_status plan_groups(Set &s) {
             return fail(VP_EINVAL, "strata that differ between axes: FP32 peaks at most %d",
                         kParamPeaks);
         if (!g.one) continue;
+        {
+            // a single FP32 peak at a dimension-exact bucket: the kernel's
+            // single-peak form (see point32_p1)
+            const Member &m0 = s.m[g.members[0]];
+            g.p1 = g.prec == VP_FP32 && g.exact && g.kind != VP_POSTERIOR && !g.mo &&
+                   (int)m0.prm[0] == 1;
+        }
         // a single integral: the cluster kernel with its constants in parameters
         // (the autotuner may still choose the task kernel).  Its histograms:
         // the full shared layout (12 B per bin) when it fits one CTA per SM,
@@ -440,11 +447,11 @@ static vp_status plan_groups(Set &s) {
         }
         cudaError_t e = g.prec == VP_FP64
                             ? sample_smem_config_f64(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem_one, 48 * 1024), g.mo)
-                            : sample_smem_config_f32(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem_one, 48 * 1024));
+                            : sample_smem_config_f32(g.bucket, g.exact, g.kind, true, (int)std::max<size_t>(g.smem_one, 48 * 1024), false, g.p1);
         if (e != cudaSuccess) return fail(VP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
         g.occ_one = g.prec == VP_FP64
                         ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, g.threads, g.smem_one, g.mo)
-                        : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, g.threads, g.smem_one);
+                        : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, g.threads, g.smem_one, false, g.p1);
         if (g.occ_one < 1) return fail(VP_ECUDA, "sampling kernel cannot be resident (smem %zu)", g.smem_one);
         g.blocks = s.n_sm * std::min(g.occ_one, 2);  // until the autotuner has measured
         if (g.hist_one) {
@@ -454,7 +461,7 @@ static vp_status plan_groups(Set &s) {
             for (int cs : {2, 4, 8}) {  // (the kernel's reduction handles up to 8)
                 const int ctas = g.prec == VP_FP64
                                      ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem_one, g.mo)
-                                     : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem_one);
+                                     : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, g.blocks, g.threads, g.smem_one, g.p1);
                 if (ctas >= (int)(0.97 * g.blocks) && ctas >= cs) {
                     g.cs = cs;
                     best = ctas / cs * cs;
@@ -653,8 +660,8 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         base = align256(base + s.groups[g].members.size() * 4);
         gmem_off[3 * g + 1] = base;
         base = align256(base + (s.groups[g].members.size() + 1) * 8);
-        gmem_off[3 * g + 2] = base;
-        base = align256(base + 16);
+        gmem_off[3 * g + 2] = base;  // task queue head and exit counter, then the tail queues
+        base = align256(base + 256 + (size_t)kTailQueues * kQueueStride * 4);
     }
     vp_status st = dev_alloc(s.arena, base, stream);
     if (st != VP_OK) return st;
@@ -740,9 +747,10 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
         a.prm32 = d.prm32;
         a.prm = d.prm;
         a.n_hc = d.n_hc;
-        a.head = g.d_head;
+        a.head = g.d_head + kQueueStride;
         a.exit_count = g.d_head + 1;
         a.r = g.r;
+        a.static16 = g.static16;
         a.hist_shared = g.hist_one;
         a.bins = d.dim * d.n_g;
         a.prm_words = g.prm_words;
@@ -832,7 +840,7 @@ vp_status vp::launch_group(const Desc *d_desc, Group &g, cudaStream_t stream) {
 // ---------------------------------------------------------------------------
 struct Cand {
     bool one;
-    int blocks, cs, r, threads;
+    int blocks, cs, r, threads, static16;
 };
 
 static vp_status time_group(Set &s, Group &g, cudaStream_t stream, float *best_ms) {
@@ -863,7 +871,7 @@ struct TuneKey {
 };
 struct TuneVal {
     bool one;
-    int blocks, cs, r, threads;
+    int blocks, cs, r, threads, static16;
     bool final;  // measured on an adapted state
 };
 static std::mutex g_tune_mu;
@@ -921,7 +929,9 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                     g.cs = kv.second.cs;
                     g.r = kv.second.r;
                     g.threads_one = kv.second.threads;
+                    g.static16 = kv.second.static16;
                     g.args1.r = g.r;
+                    g.args1.static16 = g.static16;
                     set_task(g, expect0);
                     g.tuned = true;
                     g.tuned_final = kv.second.final;
@@ -941,12 +951,12 @@ static vp_status tune(Set &s, cudaStream_t stream) {
         }
         if (can_one && g.one) {
             // CTAs of 256 threads (1..3 per SM), or one larger CTA per SM
-            const int max_threads = one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64);
+            const int max_threads = one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64, g.p1);
             for (int threads : {256, 512, 768, 1024}) {
                 if (threads > max_threads) continue;
                 const int occ = g.prec == VP_FP64
                                     ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one, g.mo)
-                                    : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem_one);
+                                    : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem_one, false, g.p1);
                 for (int k = 1; k <= std::min(threads == 256 ? 3 : 1, occ); ++k) {
                     const int blocks = k * s.n_sm;
                     for (int cs : {1, 2, 4, 8}) {
@@ -955,24 +965,27 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                         if (cs > 1) {
                             ctas = g.prec == VP_FP64
                                        ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem_one, g.mo)
-                                       : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem_one);
+                                       : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cs, blocks, threads, g.smem_one, g.p1);
                             ctas = std::min(ctas, blocks) / cs * cs;
                             if (ctas < (int)(0.9 * blocks)) continue;
                         }
-                        cands.push_back({true, ctas, cs, g.r, threads});
+                        cands.push_back({true, ctas, cs, g.r, threads, kStaticShare});
+                        // a static head and a dynamic tail in chunks of 32 x 8
+                        // samples (SMs run this kernel at different speeds)
+                        cands.push_back({true, ctas, cs, 8, threads, kTailShare});
                     }
                 }
             }
         }
         if ((g.uniform || !g.exact) && !g.mo)
             for (int k = 1; k <= std::min(3, g.occ_many); ++k)
-                for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r, 256});
+                for (int r : {4, 8}) cands.push_back({false, k * s.n_sm, 1, r, 256, 16});
         if (cands.size() <= 1) {
             g.tuned = true;
             g.tuned_final = true;
             continue;
         }
-        const Cand keep = {g.one, g.blocks, g.cs, g.r, g.threads_one};
+        const Cand keep = {g.one, g.blocks, g.cs, g.r, g.threads_one, g.static16};
         Cand best = keep;
         float best_ms = 1e30f;
         for (const Cand &c : cands) {
@@ -981,7 +994,9 @@ static vp_status tune(Set &s, cudaStream_t stream) {
             g.cs = c.cs;
             g.r = c.r;
             g.threads_one = c.threads;
+            g.static16 = c.static16;
             g.args1.r = c.r;
+            g.args1.static16 = c.static16;
             set_task(g, expect);
             float ms = 0.f;
             vp_status st = time_group(s, g, stream, &ms);
@@ -996,14 +1011,16 @@ static vp_status tune(Set &s, cudaStream_t stream) {
         g.cs = best.cs;
         g.r = best.r;
         g.threads_one = best.threads;
+        g.static16 = best.static16;
         g.args1.r = best.r;
+        g.args1.static16 = best.static16;
         set_task(g, expect);
         g.tuned = true;
         g.tuned_final = adapted;
         {
             std::lock_guard<std::mutex> lock(g_tune_mu);
             const TuneKey key = tune_key(s, g, expect);
-            const TuneVal val = {g.one, g.blocks, g.cs, g.r, g.threads_one, adapted};
+            const TuneVal val = {g.one, g.blocks, g.cs, g.r, g.threads_one, g.static16, adapted};
             bool found = false;
             for (auto &kv : g_tune_cache)
                 if (kv.first == key) {
@@ -2085,7 +2102,7 @@ extern "C" vp_status vp_get_tuning(vp_ctx *c, int *scheme, int *blocks, int *thr
     CHECK_CTX(c);
     if (c->set.groups.empty()) return fail(VP_EINVAL, "no sampling group");
     const Group &g = c->set.groups[0];
-    if (scheme) *scheme = g.one ? 0 : 1;
+    if (scheme) *scheme = g.one ? (g.static16 >= 16 ? 0 : 2) : 1;
     if (blocks) *blocks = g.blocks;
     if (threads) *threads = g.one ? g.threads_one : g.threads;
     if (cluster) *cluster = g.cs;
@@ -2098,11 +2115,13 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     CHECK_CTX(c);
     if (c->set.groups.empty()) return fail(VP_EINVAL, "no sampling group");
     Group &g = c->set.groups[0];
-    if (scheme != 0 && scheme != 1) return fail(VP_EINVAL, "scheme must be 0 or 1");
+    if (scheme < 0 || scheme > 2) return fail(VP_EINVAL, "scheme must be 0, 1 or 2");
+    const int static16 = scheme == 2 ? kTailShare : kStaticShare;
+    if (scheme == 2) scheme = 0;  // the one-integral kernel with a dynamic tail
     if (scheme == 1 && threads != 256) return fail(VP_EINVAL, "the task scheme runs 256 threads");
     if (threads != 256 && threads != 512 && threads != 768 && threads != 1024)
         return fail(VP_EINVAL, "threads must be 256, 512, 768 or 1024");
-    if (threads > one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64))
+    if (threads > one_max_threads(bucket_dim(g.bucket), g.prec == VP_FP64, g.p1))
         return fail(VP_EINVAL, "%d threads exceed this kernel's largest CTA", threads);
     if (scheme == 0 && g.members.size() == 1 && g.prec == VP_FP32 && g.kind != VP_POSTERIOR &&
         (int)c->set.m[g.members[0]].prm[0] > kParamPeaks)
@@ -2123,11 +2142,11 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
         // the static split assumes every CTA resident at once
         const int occ = g.prec == VP_FP64
                             ? sample_occupancy_f64(g.bucket, g.exact, g.kind, true, threads, g.smem_one, g.mo)
-                            : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem_one);
+                            : sample_occupancy_f32(g.bucket, g.exact, g.kind, true, threads, g.smem_one, false, g.p1);
         const int res = cluster > 1
                             ? (g.prec == VP_FP64
                                    ? sample_cluster_ctas_f64(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem_one, g.mo)
-                                   : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem_one))
+                                   : sample_cluster_ctas_f32(g.bucket, g.exact, g.kind, cluster, blocks, threads, g.smem_one, g.p1))
                             : occ * c->set.n_sm;
         if (blocks > res)
             return fail(VP_EINVAL, "%d CTAs in clusters of %d exceed the %d resident ones", blocks,
@@ -2145,8 +2164,10 @@ extern "C" vp_status vp_set_tuning(vp_ctx *c, int scheme, int blocks, int thread
     g.cs = cluster;
     g.r = run;
     g.threads_one = threads;
+    g.static16 = static16;
     g.tuned_final = true;
     g.args1.r = run;
+    g.args1.static16 = static16;
     double expect = 0.0;
     for (uint32_t i : g.members) expect += (double)c->set.m[i].p.n_ev + 2.0 * (double)c->set.m[i].n_hc;
     set_task(g, expect);

@@ -79,6 +79,10 @@ struct Member {
 };
 
 // One sampling launch: the integrals of one kernel instantiation.
+// the one-integral kernel's share of samples split statically, in 16ths: all
+// of them by default; half with a dynamic tail (launch scheme 2)
+constexpr int kStaticShare = 16, kTailShare = 8;
+
 struct Group {
     int bucket, kind, prec;
     bool exact;
@@ -93,8 +97,12 @@ struct Group {
     bool uniform = true;  // every member has the same strata on every axis (else: one only)
     bool mo = false;      // several outputs (App. B): the FP64 one-integral kernel that sums them
     bool solo = false;    // a group of one member by construction (several outputs)
+    bool p1 = false;      // the one-integral kernel's single-peak FP32 form
     int cs = 1;        // CTAs per cluster (one-integral kernel)
     int threads_one = 256;  // CTA size of the one-integral kernel
+    // the one-integral kernel's static share of the samples in 16ths (16: all;
+    // the rest pulled by warps in chunks of 32 r samples)
+    int static16 = kStaticShare;
     // the one-integral kernel's shape as planned (before the autotuner), for
     // launches that need that kernel whatever the tuner chose (sharded sampling)
     int blocks_plan = 0, cs_plan = 1, threads_plan = 256;

@@ -10,6 +10,7 @@ const void *kptr_one_f32_g(int bucket, int kind);
 const void *kptr_many_f32_g(int bucket, int kind);
 cudaError_t launch_eval_f32_g(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 const void *kptr_one_f32_x(int bucket, int kind);
+const void *kptr_one_f32_p1(int bucket, int kind);
 const void *kptr_many_f32_x(int bucket, int kind);
 cudaError_t launch_eval_f32_x(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 const void *kptr_one_f64_g(int bucket, int kind);
@@ -19,9 +20,11 @@ const void *kptr_many_f64_ax(int bucket, int kind);
 const void *kptr_many_f64_g(int bucket, int kind);
 cudaError_t launch_eval_f64_g(int bucket, int kind, cudaStream_t s, const Desc *desc, int member, int64_t n, const uint64_t *h, const uint32_t *j, uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
 
+// (p1: the one-integral FP32 kernel's single-peak form, dimension-exact buckets)
 static const void *pick(bool f64, int bucket, bool exact, int kind, bool one, bool mo = false,
-                        bool ax = false) {
+                        bool ax = false, bool p1 = false) {
     if (f64 && one && mo) return kptr_one_f64_mo(bucket, kind);
+    if (!f64 && one && exact && p1 && kind != VP_POSTERIOR) return kptr_one_f32_p1(bucket, kind);
     if (!one && ax) return f64 ? kptr_many_f64_ax(bucket, kind) : kptr_many_f32_ax(bucket, kind);
     if (f64) return one ? kptr_one_f64_g(bucket, kind) : kptr_many_f64_g(bucket, kind);
     if (exact) return one ? kptr_one_f32_x(bucket, kind) : kptr_many_f32_x(bucket, kind);
@@ -48,7 +51,8 @@ static cudaError_t launch_many(bool f64, int bucket, bool exact, int kind, dim3 
 
 static cudaError_t launch_one(bool f64, int bucket, bool exact, int kind, dim3 grid, dim3 block,
                               size_t smem, int cs, cudaStream_t s, const SampleOne &a) {
-    const void *k = pick(f64, bucket, exact, kind, true, f64 && a.n_out > 1);
+    const void *k = pick(f64, bucket, exact, kind, true, f64 && a.n_out > 1, false,
+                         !f64 && a.kp_peaks == 1);
     if (!k) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -96,8 +100,8 @@ struct SmemLimit {
 static std::vector<SmemLimit> g_smem_limit;
 
 static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool one, int max_smem,
-                               bool mo = false, bool ax = false) {
-    const void *k = pick(f64, bucket, exact, kind, one, mo, ax);
+                               bool mo = false, bool ax = false, bool p1 = false) {
+    const void *k = pick(f64, bucket, exact, kind, one, mo, ax, p1);
     if (!k) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -116,8 +120,8 @@ static cudaError_t smem_config(bool f64, int bucket, bool exact, int kind, bool 
     return cudaSuccess;
 }
 cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem,
-                                   bool ax) {
-    return smem_config(false, bucket, exact, kind, one, max_smem, false, ax);
+                                   bool ax, bool p1) {
+    return smem_config(false, bucket, exact, kind, one, max_smem, false, ax, p1);
 }
 cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem,
                                    bool mo, bool ax) {
@@ -125,16 +129,16 @@ cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, i
 }
 
 static int occupancy(bool f64, int bucket, bool exact, int kind, bool one, int threads, size_t smem,
-                     bool mo = false, bool ax = false) {
-    const void *k = pick(f64, bucket, exact, kind, one, mo, ax);
+                     bool mo = false, bool ax = false, bool p1 = false) {
+    const void *k = pick(f64, bucket, exact, kind, one, mo, ax, p1);
     int n = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
         return 0;
     return n;
 }
 int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
-                         bool ax) {
-    return occupancy(false, bucket, exact, kind, one, threads, smem, false, ax);
+                         bool ax, bool p1) {
+    return occupancy(false, bucket, exact, kind, one, threads, smem, false, ax, p1);
 }
 int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
                          bool mo, bool ax) {
@@ -142,8 +146,8 @@ int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads
 }
 
 static int cluster_ctas(bool f64, int bucket, bool exact, int kind, int cs, int grid, int threads,
-                        size_t smem, bool mo = false) {
-    const void *k = pick(f64, bucket, exact, kind, true, mo);
+                        size_t smem, bool mo = false, bool p1 = false) {
+    const void *k = pick(f64, bucket, exact, kind, true, mo, false, p1);
     if (!k) return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -164,8 +168,8 @@ static int cluster_ctas(bool f64, int bucket, bool exact, int kind, int cs, int 
     return n * cs;
 }
 int sample_cluster_ctas_f32(int bucket, bool exact, int kind, int cs, int grid, int threads,
-                            size_t smem) {
-    return cluster_ctas(false, bucket, exact, kind, cs, grid, threads, smem);
+                            size_t smem, bool p1) {
+    return cluster_ctas(false, bucket, exact, kind, cs, grid, threads, smem, false, p1);
 }
 int sample_cluster_ctas_f64(int bucket, bool exact, int kind, int cs, int grid, int threads,
                             size_t smem, bool mo) {

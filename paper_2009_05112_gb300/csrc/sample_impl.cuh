@@ -292,6 +292,13 @@ __device__ __forceinline__ Loop make_loop(const Desc *dp, uint32_t t) {
     return L;
 }
 
+// The dynamic tail of the one-integral kernel is split into kTailQueues
+// equal queues, each with its own counter on its own 256-byte line: warps
+// start at queue (warp mod kTailQueues) and move on when it runs dry, so that
+// no single counter takes every warp's atomic (atomics on one address are
+// served one at a time).
+constexpr uint32_t kTailQueues = 32, kQueueStride = 64;
+
 // Launch arguments when the launch serves one integral: its constants travel
 // in the kernel parameters (constant bank), not in registers.
 struct SampleOne {
@@ -304,9 +311,12 @@ struct SampleOne {
     const float *prm32;
     const double *prm;
     uint64_t n_hc;
-    uint32_t *head;            // queue head (warp chunks)
-    uint32_t *exit_count;
-    int r;
+    uint32_t *head;            // the dynamic tail's kTailQueues counters, kQueueStride apart
+    uint32_t *exit_count;      // CTAs finished; the last one resets the counters and itself
+    int r;                     // samples per lane in a chunk of the dynamic tail
+    // the share of the samples split statically over the warps, in 16ths
+    // (16: all of them); the rest is pulled by warps in chunks of 32 r samples
+    int static16;
     int hist_shared;           // kHist* layout of the histograms
     int bins;
     int prm_words;
@@ -412,6 +422,63 @@ __device__ __forceinline__ void point32(const Loop &L, const Strata *S, const fl
     if (KIND == VP_POSTERIOR) f = f_post32<DMAX>(prm, dim, x);
     else if (KP) f = f_peaks32_param<DMAX, KIND>(prm, L.K, dim, x);
     else f = f_peaks32<DMAX>(KIND, prm, L.K, dim, x);
+}
+
+// ---------------------------------------------------------------------------
+// One sample, FP32 path, an integrand of one peak with its constants in the
+// kernel parameters (a1-a3, and the counts of a5): the same operations as
+// point32 followed by f_peaks32_param, reordered so that no per-axis array of
+// x is kept -- the peak's squared distance is accumulated axis by axis as each
+// x_mu is formed (the same sum in the same order), the sample's count goes to
+// its increment on every axis as soon as the increment is known, and the
+// increment indices are kept two to a register for the histogram sums.
+// Fewer live registers, so more warps per SM.
+// ---------------------------------------------------------------------------
+template <int DMAX, int KIND, int HM>
+__device__ __forceinline__ void point32_p1(const Loop &L, const Strata *S, const float *kp,
+                                           uint32_t h, uint32_t j, const float (&kc)[DMAX],
+                                           uint32_t (&ip)[DMAX / 2], float &Jm, int &Je,
+                                           float &f, uint32_t *hc, uint32_t *HC) {
+    constexpr uint32_t calls = (uint32_t)((DMAX + 3) / 4);
+    float J = L.ngD_m;
+    int e = L.ngD_e;
+    float r2 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < (DMAX + 3) / 4; ++q) {
+        U4 c = {j * calls + (uint32_t)q, h, L.t, L.iid};
+        const U4 r = philox_rk(c, L.rk0, L.rk1);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int mu = 4 * q + l;
+            if (mu < DMAX) {
+                const uint32_t w = lane_of(r, l);
+                const float one_m = __int_as_float(0x3f800000 | (w >> 9));
+                const float tt = fmaf(one_m, S->c32[mu], kc[mu]);  // y N_g
+                const float big = __fadd_rd(tt, 12582912.0f);
+                int i = __float_as_int(big) - 0x4B400000;
+                float fl = big - 12582912.0f;
+                i = min(i, L.n_g - 1);
+                fl = fminf(fl, L.ngm1);
+                const float delta = tt - fl;
+                const uint32_t bin = (uint32_t)mu * (uint32_t)L.n_g + (uint32_t)i;
+                const float2 ed = __ldg(L.tab + bin);  // {x_i, dx_i}
+                const float x = fmaf(ed.y, delta, ed.x);
+                J *= ed.y;
+                const float dx = x - kp[2 + mu];
+                r2 = fmaf(dx, dx, r2);
+                if (HM != kHistGlobal) atomicAdd(hc + bin, 1u);
+                else red_add(HC + bin, 1u);
+                if (mu & 1) ip[mu >> 1] |= (uint32_t)i << 16;
+                else ip[mu >> 1] = (uint32_t)i;
+            }
+        }
+        renorm(J, e);
+    }
+    Jm = J;
+    Je = e;
+    if (KIND == VP_GAUSS) f = fmaf(kp[0], ex2_approx(-kp[1] * r2), 0.0f);
+    else if (KIND == VP_BALL) f = 0.0f + ((r2 < kp[1]) ? kp[0] : 0.0f);
+    else f = fmaf(kp[0], ex2_approx(-kp[1] * sqrtf(r2)), 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -525,11 +592,27 @@ template <> struct Acc<true> {
     __device__ __forceinline__ void reset() { s1 = 0.0; s2 = 0.0; }
     __device__ __forceinline__ void add(double v, double v2) { s1 += v; s2 += v2; }
     __device__ __forceinline__ void add_tiny(double, double) {}  // (FP32 path only)
-    // adds the sums, unscaled by 2^-sexp, to the hypercube's FP64 accumulators
-    __device__ __forceinline__ void flush(double *p1, double *p2, int sexp) const {
+    // the sums, unscaled by 2^-sexp
+    __device__ __forceinline__ void values(int sexp, double &d1, double &d2) const {
         const double u = pow2d(-sexp);
-        red_add(p1, s1 * u);
-        red_add(p2, s2 * (u * u));
+        d1 = s1 * u;
+        d2 = s2 * (u * u);
+    }
+    // adds them to the hypercube's FP64 accumulators
+    template <bool SPLIT = true>
+    __device__ __forceinline__ void flush(double *p1, double *p2, int sexp) const {
+        double d1, d2;
+        values(sexp, d1, d2);
+        red_add(p1, d1);
+        red_add(p2, d2);
+    }
+    __device__ __forceinline__ void shfl_down(Acc &o, int s) const {
+        o.s1 = __shfl_down_sync(0xffffffffu, s1, s);
+        o.s2 = __shfl_down_sync(0xffffffffu, s2, s);
+    }
+    __device__ __forceinline__ void combine(const Acc &o) {
+        s1 += o.s1;
+        s2 += o.s2;
     }
 };
 // FP32 samples whose v = J f 2^sexp lies far below the iteration's scale
@@ -557,13 +640,62 @@ template <> struct Acc<false> {
         t1 += vt;
         t2 += vt2;
     }
-    // the compensated sums s - c plus the tiny sums, each unscaled exactly
+    // adds the compensated sums s - c and the tiny sums, unscaled exactly, to
+    // the hypercube's FP64 accumulators.  SPLIT: each nonzero term reduced on
+    // its own (FP64 arithmetic is scarce on this part: the conversions are
+    // integer operations and the memory system adds the terms); else the terms
+    // added in FP64 first and two reductions issued.  (Measured: the split
+    // form is faster for the 20-D kernels, slower for the 64-register ones up
+    // to D = 8.)
+    template <bool SPLIT = true>
     __device__ __forceinline__ void flush(double *p1, double *p2, int sexp) const {
-        red_add(p1, (f2d_pow2(s1, -sexp) - f2d_pow2(c1, -sexp)) +
-                        f2d_pow2(t1, -sexp - kTinyShift));
-        red_add(p2, (f2d_pow2(s2, -2 * sexp) - f2d_pow2(c2, -2 * sexp)) +
-                        f2d_pow2(t2, -2 * (sexp + kTinyShift)));
+        if (!SPLIT) {
+            red_add(p1, (f2d_pow2(s1, -sexp) - f2d_pow2(c1, -sexp)) +
+                            f2d_pow2(t1, -sexp - kTinyShift));
+            red_add(p2, (f2d_pow2(s2, -2 * sexp) - f2d_pow2(c2, -2 * sexp)) +
+                            f2d_pow2(t2, -2 * (sexp + kTinyShift)));
+            return;
+        }
+        if (s1 != 0.0f) red_add(p1, f2d_pow2(s1, -sexp));
+        if (c1 != 0.0f) red_add(p1, f2d_pow2(-c1, -sexp));
+        if (t1 != 0.0f) red_add(p1, f2d_pow2(t1, -sexp - kTinyShift));
+        if (s2 != 0.0f) red_add(p2, f2d_pow2(s2, -2 * sexp));
+        if (c2 != 0.0f) red_add(p2, f2d_pow2(-c2, -2 * sexp));
+        if (t2 != 0.0f) red_add(p2, f2d_pow2(t2, -2 * (sexp + kTinyShift)));
     }
+    __device__ __forceinline__ void shfl_down(Acc &o, int s) const {
+        o.s1 = __shfl_down_sync(0xffffffffu, s1, s);
+        o.c1 = __shfl_down_sync(0xffffffffu, c1, s);
+        o.s2 = __shfl_down_sync(0xffffffffu, s2, s);
+        o.c2 = __shfl_down_sync(0xffffffffu, c2, s);
+        o.t1 = __shfl_down_sync(0xffffffffu, t1, s);
+        o.t2 = __shfl_down_sync(0xffffffffu, t2, s);
+    }
+    // (s, c) + (os, oc), both meaning s - c: the sum s + os split exactly into
+    // t + e (Knuth's two-sum), the compensations carried as c + oc - e
+    __device__ __forceinline__ static void add_pair(float &s, float &c, float os, float oc) {
+        const float t = __fadd_rn(s, os);
+        const float bb = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(os, bb));
+        c = __fsub_rn(__fadd_rn(c, oc), e);
+        s = t;
+    }
+    __device__ __forceinline__ void combine(const Acc &o) {
+        add_pair(s1, c1, o.s1, o.c1);
+        add_pair(s2, c2, o.s2, o.c2);
+        t1 += o.t1;
+        t2 += o.t2;
+    }
+};
+
+// A lane's last partial sums of a run, handed back instead of flushed, so that
+// the lanes of a warp whose runs end in the same hypercube add them first
+// (warp_flush): a hypercube holding many samples -- up to most of an
+// iteration's -- otherwise receives reductions from every lane, all on the
+// same addresses.
+template <bool F64> struct RunTail {
+    uint64_t h;  // ~0: none
+    Acc<F64> acc;
 };
 
 // The outputs of several integrals from the same samples (App. B), summed per
@@ -710,23 +842,34 @@ __device__ __forceinline__ void MAcc<true>::flush(const SampleOne &a, double *p1
 
 // (HM: the histogram layout, kHist*; a template parameter so that the
 // per-axis updates carry no branch on it)
-template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, int HM, bool AX, bool MO>
+// (P1: an FP32 integrand of one peak through point32_p1 -- counts added as
+// each axis is formed, no digit array kept: the digits of the next hypercube
+// are decoded from its index)
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, int HM, bool AX, bool MO,
+          bool P1 = false>
 __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, const Ptrs &P,
                                               const SampleOne *A, double *X1, double *X2,
                                               const void *prm,
                                               uint64_t s_begin, uint64_t s_end, uint64_t h,
                                               uint64_t lo_off, uint64_t next,
                                               typename Real<F64>::T *hs, float *hs_t,
-                                              uint32_t *hc, int sexp) {
+                                              uint32_t *hc, int sexp, RunTail<F64> *tail) {
     constexpr bool hist_shared = HM != kHistGlobal;
     constexpr bool compact = HM == kHistCompact;
+    static_assert(!P1 || (!F64 && KP && EXACT && !MO && KIND != VP_POSTERIOR), "P1 path");
     typedef typename Real<F64>::T T;
     const int dim = EXACT ? DMAX : L.dim;
     uint32_t j = (uint32_t)(s_begin - lo_off);
-    uint32_t kd[DMAX];
-    decode_digits<DMAX, AX>((uint32_t)h, L, S, dim, kd);
+    uint32_t kd[P1 ? 1 : DMAX];
     float kc[DMAX];
-    if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
+    if constexpr (P1) {
+        uint32_t kd1[DMAX];
+        decode_digits<DMAX, AX>((uint32_t)h, L, S, dim, kd1);
+        hcube_offsets<DMAX, AX>(L, S, kd1, kc);
+    } else {
+        decode_digits<DMAX, AX>((uint32_t)h, L, S, dim, kd);
+        if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
+    }
     Acc<F64> acc;
     acc.reset();
     MAcc<MO> macc;  // (several outputs, App. B: FP64 path only)
@@ -740,26 +883,47 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
     // the plain mean (weight 1, an exact multiply)
     uint32_t nh_cur = L.dw ? __ldg(P.nh + h) : 1u;
     float hw32 = L.dw ? __frcp_rn((float)nh_cur) : 1.0f;
-    for (uint32_t left = (uint32_t)(s_end - s_begin); left > 0; --left) {
+    // above D = 8 (fewer warps per SM to hide latency): n_h of the next
+    // hypercube loaded one hypercube ahead, its latency hidden behind the
+    // current hypercube's samples
+    constexpr bool kPrefetch = DMAX > 8;
+    const uint32_t left0 = (uint32_t)(s_end - s_begin);
+    uint32_t nh_next =
+        (kPrefetch && to_next < left0 && h + 1 < P.n_hc) ? __ldg(P.nh + h + 1) : 0u;
+    for (uint32_t left = left0; left > 0; --left) {
         if (to_next == 0u) {
-            acc.flush(P.S1 + h, P.S2 + h, sexp);
+            acc.template flush<(DMAX > 8)>(P.S1 + h, P.S2 + h, sexp);
             acc.reset();
             if (MO) {
                 macc.flush(*A, X1 + h * MM, X2 + h * MT);
                 macc.reset();
             }
             ++h;
-            to_next = __ldg(P.nh + h);
+            if (kPrefetch) {
+                to_next = nh_next;
+                // (n_h >= 2: the run reaches the next boundary only if more
+                // than n_h samples are left)
+                nh_next = (to_next < left && h + 1 < P.n_hc) ? __ldg(P.nh + h + 1) : 0u;
+            } else {
+                to_next = __ldg(P.nh + h);
+            }
             if (L.dw) {
                 nh_cur = to_next;
                 hw32 = __frcp_rn((float)nh_cur);
             }
             j = 0;
-            next_digits<DMAX, AX>(L, S, dim, kd);
-            if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
+            if constexpr (P1) {
+                uint32_t kd1[DMAX];
+                decode_digits<DMAX, AX>((uint32_t)h, L, S, dim, kd1);
+                hcube_offsets<DMAX, AX>(L, S, kd1, kc);
+            } else {
+                next_digits<DMAX, AX>(L, S, dim, kd);
+                if (!F64) hcube_offsets<DMAX, AX>(L, S, kd, kc);
+            }
         }
         --to_next;
-        int idx[DMAX];
+        int idx[P1 ? 1 : DMAX];
+        uint32_t ip[P1 ? DMAX / 2 : 1];  // (P1: increment indices, two to a register)
         T v;
         // FP32: v = J f 2^sexp in [2^-60, 2^60) is summed as is, tiny v in
         // [2^-163, 2^-60) scaled by 2^kTinyShift (see Acc); beyond those (v^2
@@ -767,7 +931,7 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
         // adapted) a sample takes exact FP64 terms of its own
         bool big = false, tiny = false;
         double vbig = 0.0, vbig2 = 0.0, hbig = 0.0;
-        if (F64) {
+        if constexpr (F64) {
             double x[DMAX], J, f;
             if (MO) {  // (the outputs' selects read every entry)
 #pragma unroll
@@ -777,10 +941,16 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
             v = (T)(J * f * pow2d(sexp));
             if (MO) macc.template add<DMAX>(*A, x, __dmul_rn(J, f));
         } else {
-            float x[DMAX], Jm, f;
+            float Jm, f;
             int Je;
-            point32<DMAX, EXACT, KIND, KP, AX>(L, S, (const float *)prm, (uint32_t)h, j, kc, x, idx,
-                                               Jm, Je, f);
+            if constexpr (P1) {
+                point32_p1<DMAX, KIND, HM>(L, S, (const float *)prm, (uint32_t)h, j, kc, ip, Jm,
+                                           Je, f, hc, P.HC);
+            } else {
+                float x[DMAX];
+                point32<DMAX, EXACT, KIND, KP, AX>(L, S, (const float *)prm, (uint32_t)h, j, kc, x,
+                                                   idx, Jm, Je, f);
+            }
             float jf = Jm * f;  // Jm in [1, 2); the last multiply-add of f may leave it subnormal
             if (((__float_as_int(jf) & 0x7f800000) == 0) && jf != 0.0f) {  // renormalise (exact)
                 jf *= 16777216.0f;
@@ -833,7 +1003,10 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
         // loops below are plain runs of atomics)
         int bin[DMAX];
 #pragma unroll
-        for (int mu = 0; mu < DMAX; ++mu) bin[mu] = mu * L.n_g + idx[mu];
+        for (int mu = 0; mu < DMAX; ++mu) {
+            if constexpr (P1) bin[mu] = mu * L.n_g + (int)((ip[mu >> 1] >> (16 * (mu & 1))) & 0xffffu);
+            else bin[mu] = mu * L.n_g + idx[mu];
+        }
         if (big) {
 #pragma unroll
             for (int mu = 0; mu < DMAX; ++mu)
@@ -850,7 +1023,9 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
                     if (mu < dim) red_add(P.HS + bin[mu], hg);
             }
         }
-        if (hist_shared) {
+        if (P1) {
+            // (the counts were added as the axes were formed)
+        } else if (hist_shared) {
 #pragma unroll
             for (int mu = 0; mu < DMAX; ++mu)
                 if (mu < dim) atomicAdd(hc + bin[mu], 1u);
@@ -861,27 +1036,54 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
         }
         ++j;
     }
-    acc.flush(P.S1 + h, P.S2 + h, sexp);
+    if (tail && !MO) {  // (the caller adds it with the warp's others)
+        tail->h = h;
+        tail->acc = acc;
+    } else {
+        acc.template flush<(DMAX > 8)>(P.S1 + h, P.S2 + h, sexp);
+    }
     if (MO) macc.flush(*A, X1 + h * MM, X2 + h * MT);
 }
 
-template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, bool AX, bool MO = false>
+// The warp's run tails, added per hypercube before they reach global memory:
+// lanes hold consecutive samples, so lanes with the same hypercube are
+// contiguous; a segmented tree of shuffles leaves each segment's sum in its
+// lowest lane, which issues the two reductions.  Every lane of the warp calls
+// it (tail.h = ~0 for a lane without samples).
+template <bool F64>
+__device__ __forceinline__ void warp_flush(const Ptrs &P, RunTail<F64> t, int lane, int sexp) {
+    const uint64_t ph = __shfl_up_sync(0xffffffffu, t.h, 1);
+    const bool head = lane == 0 || ph != t.h;  // the lowest lane of its hypercube
+    if (!__all_sync(0xffffffffu, head)) {  // (else every lane its own: nothing to add)
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const uint64_t oh = __shfl_down_sync(0xffffffffu, t.h, s);
+            Acc<F64> o;
+            t.acc.shfl_down(o, s);
+            if (lane + s < 32 && oh == t.h) t.acc.combine(o);
+        }
+    }
+    if (t.h != ~0ull && head) t.acc.flush(P.S1 + t.h, P.S2 + t.h, sexp);
+}
+
+template <int DMAX, bool EXACT, bool F64, int KIND, bool KP, bool AX, bool MO = false,
+          bool P1 = false>
 __device__ __forceinline__ void run_samples(const Loop &L, const Strata *S, const Ptrs &P,
                                             const void *prm, uint64_t s_begin, uint64_t s_end,
                                             uint64_t h, uint64_t lo_off, uint64_t next,
                                             typename Real<F64>::T *hs, float *hs_t, uint32_t *hc,
                                             int hist_mode, int sexp,
                                             const SampleOne *A = nullptr, double *X1 = nullptr,
-                                            double *X2 = nullptr) {
+                                            double *X2 = nullptr, RunTail<F64> *tail = nullptr) {
     if (hist_mode == kHistShared)
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistShared, AX, MO>(
-            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistShared, AX, MO, P1>(
+            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp, tail);
     else if (!F64 && hist_mode == kHistCompact)
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistCompact, AX, MO>(
-            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistCompact, AX, MO, P1>(
+            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp, tail);
     else
-        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistGlobal, AX, MO>(
-            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp);
+        run_samples_t<DMAX, EXACT, F64, KIND, KP, kHistGlobal, AX, MO, P1>(
+            L, S, P, A, X1, X2, prm, s_begin, s_end, h, lo_off, next, hs, hs_t, hc, sexp, tail);
 }
 
 // ---------------------------------------------------------------------------
@@ -902,8 +1104,10 @@ __device__ __forceinline__ void run_samples(const Loop &L, const Strata *S, cons
 // The bound sets the register budget: 64 for FP32 with D <= 8 (1024 threads,
 // no spills: a third more warps than 768 threads at 80 registers), the 256 x 2
 // shape's for FP32 with D > 8 and the 256 x 1 shape's for FP64.
-__host__ __device__ constexpr int one_max_threads(int dmax, bool f64) {
-    return f64 ? 256 : (dmax <= 8 ? 1024 : 512);
+// The single-peak FP32 form (P1), which keeps fewer registers, takes 768
+// threads above D = 8.
+__host__ __device__ constexpr int one_max_threads(int dmax, bool f64, bool p1 = false) {
+    return f64 ? 256 : (dmax <= 8 ? 1024 : (p1 ? 768 : 512));
 }
 
 // Sum of the cluster's CS copies of bins [b0, b1) of the histograms, added to
@@ -949,14 +1153,15 @@ __device__ __forceinline__ void cluster_flush(cooperative_groups::cluster_group 
     }
 }
 
-template <int DMAX, bool EXACT, bool F64, int KIND, bool MO = false>
-__global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
+template <int DMAX, bool EXACT, bool F64, int KIND, bool MO = false, bool P1 = false>
+__global__ void __launch_bounds__(one_max_threads(DMAX, F64, P1), 1)
     k_sample_one(const __grid_constant__ SampleOne a) {
     typedef typename Real<F64>::T T;
     namespace cg = cooperative_groups;
     // FP32 peak families read their constants from the parameters
     constexpr bool KP = !F64 && KIND != VP_POSTERIOR;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint8_t s_tried[32];  // per warp: tail queues found empty
     float *sprm = (float *)smem;
     // histograms: sums (FP64, or FP32 and -- unless compact -- the FP32 tiny
     // sums), then counts
@@ -1017,25 +1222,89 @@ __global__ void __launch_bounds__(one_max_threads(DMAX, F64), 1)
             lo = (uint32_t)(T * (uint64_t)a.part / (uint64_t)a.n_parts);
             n_tot = (uint32_t)(T * (uint64_t)(a.part + 1) / (uint64_t)a.n_parts) - lo;
         }
-        const uint32_t per_w = n_tot / W, extra = n_tot - per_w * W;
-        const uint64_t wb = (uint64_t)lo + (uint64_t)w * per_w + min(w, extra);
-        const uint64_t we = wb + per_w + (w < extra ? 1u : 0u);
-        const uint64_t q = (we - wb + 31) / 32;
-        const uint64_t s0 = min(wb + (uint64_t)lane * q, we);
-        const uint64_t s1 = min(s0 + q, we);
-        if (wb < we) {  // warp-uniform
-            const uint64_t hb = warp_find_hcube(P.off, P.n_hc, wb, lane);
+        // the static head: the first n_st samples of the range, split evenly
+        // over the warps (the costs of samples differ -- hypercube changes,
+        // nonzero integrand values -- so a dynamic tail evens out the end)
+        const uint32_t n_st =
+            a.static16 >= 16 ? n_tot : (uint32_t)(((uint64_t)n_tot * (uint32_t)a.static16) >> 4);
+        double *X1 = MO ? a.x1 + par * a.n_hc * (uint64_t)a.n_out : nullptr;
+        double *X2 = MO ? a.x2 + par * a.n_hc * (uint64_t)(a.n_out * (a.n_out + 1) / 2) : nullptr;
+        // (sample indices are 32-bit: an iteration has fewer than 2^32 samples)
+        const uint32_t per_w = n_st / W, extra = n_st - per_w * W;
+        const uint32_t wb = lo + w * per_w + min(w, extra);
+        const uint32_t we = wb + per_w + (w < extra ? 1u : 0u);
+        // the dynamic tail: chunks of 32 r samples, each warp pulling the next
+        // one from the queue as it finishes
+        const uint32_t C = 32u * (uint32_t)a.r;
+        const uint32_t n_ch = (n_tot - n_st + C - 1) / C;
+        // work items of this warp: its static range, then the chunks it pulls;
+        // lane l takes `per` consecutive samples of an item (one call site of
+        // the sample loop, so that it is inlined once)
+        uint32_t base = wb, end = we, per = (we - wb + 31) / 32;
+        // (lane 0: queues found empty so far, kept in shared memory rather
+        // than in a register of the sample loop)
+        if (lane == 0) s_tried[threadIdx.x >> 5] = 0u;
+        for (bool first = true;; first = false) {
+            if (!first) {
+                uint32_t c = n_ch;
+                if (lane == 0) {
+                    uint32_t tried = s_tried[threadIdx.x >> 5];
+                    while (n_st < n_tot && tried < kTailQueues) {
+                        const uint32_t qu = (w + tried) % kTailQueues;
+                        const uint32_t q0 = (uint32_t)((uint64_t)n_ch * qu / kTailQueues);
+                        const uint32_t q1 = (uint32_t)((uint64_t)n_ch * (qu + 1) / kTailQueues);
+                        const uint32_t k = atomicAdd(a.head + kQueueStride * qu, 1u);
+                        if (k < q1 - q0) {
+                            c = q0 + k;
+                            break;
+                        }
+                        ++tried;  // this queue is done: the next one
+                    }
+                    s_tried[threadIdx.x >> 5] = (uint8_t)min(tried, kTailQueues);
+                }
+                c = __shfl_sync(0xffffffffu, c, 0);
+                if (c >= n_ch) break;
+                base = lo + n_st + c * C;
+                end = min(base + C, lo + n_tot);
+                per = (uint32_t)a.r;
+            }
+            if (base >= end) continue;  // (warp-uniform: an empty static range)
+            const uint32_t c0 = min(base + (uint32_t)lane * per, end);
+            const uint32_t c1 = min(c0 + per, end);
+            const uint64_t hb = warp_find_hcube(P.off, P.n_hc, base, lane);
             uint64_t lo_off = 0, hi_off = 0;
             const uint64_t h =
-                lane_find_hcube(P.off, P.n_hc, hb, s0, s0 < s1, lane, &lo_off, &hi_off);
-            if (s0 < s1)  // (the strata per axis: constants of the parameter bank)
-                run_samples<DMAX, EXACT, F64, KIND, KP, true, MO>(
-                    L, &a.S, P, prm, s0, s1, h, lo_off, hi_off, hs, hs_t, hc, a.hist_shared, sexp,
-                    &a, MO ? a.x1 + par * a.n_hc * (uint64_t)a.n_out : nullptr,
-                    MO ? a.x2 + par * a.n_hc * (uint64_t)(a.n_out * (a.n_out + 1) / 2) : nullptr);
+                lane_find_hcube(P.off, P.n_hc, hb, c0, c0 < c1, lane, &lo_off, &hi_off);
+            RunTail<F64> tail;
+            if (c0 < c1) {  // (the strata per axis: constants of the parameter bank)
+                run_samples<DMAX, EXACT, F64, KIND, KP, true, MO, P1>(
+                    L, &a.S, P, prm, c0, c1, h, lo_off, hi_off, hs, hs_t, hc, a.hist_shared,
+                    sexp, &a, X1, X2, MO ? nullptr : &tail);
+            } else {  // (set here, not before the loop: no registers held across it)
+                tail.h = ~0ull;
+                tail.acc.reset();
+            }
+            // (measured: the 64-register kernels up to D = 8 run the eight-D
+            // four-peak workload slower with the warp's combine, the larger
+            // ones gain from it where one hypercube holds many samples)
+            if (!MO) {
+                if (DMAX > 8) warp_flush<F64>(P, tail, lane, sexp);
+                else if (tail.h != ~0ull)
+                    tail.acc.template flush<false>(P.S1 + tail.h, P.S2 + tail.h, sexp);
+            }
         }
     }
     __syncthreads();
+    if (a.static16 < 16 && threadIdx.x == 0) {
+        // the last CTA out resets the queue for the next launch (every other
+        // CTA has left its tail loop, so none reads the head again)
+        __threadfence();
+        if (atomicAdd(a.exit_count, 1u) == gridDim.x - 1) {
+            for (uint32_t q = 0; q < kTailQueues; ++q) a.head[kQueueStride * q] = 0u;
+            *a.exit_count = 0u;
+            __threadfence();
+        }
+    }
     if (a.hist_shared) {
         // cluster-wide reduction of the CTAs' histograms, one slice per CTA
         cg::cluster_group cl = cg::this_cluster();
@@ -1315,8 +1584,10 @@ cudaError_t launch_eval_f32(int bucket, bool exact, int kind, cudaStream_t s, co
 cudaError_t launch_eval_f64(int bucket, bool exact, int kind, cudaStream_t s, const Desc *desc,
                             int member, int64_t n, const uint64_t *h, const uint32_t *j,
                             uint32_t t, double *x, int32_t *idx, double *jac, double *f, int pw);
+// (p1: the one-integral kernel's single-peak form, chosen at launch when the
+// FP32 integrand has one peak and the bucket is dimension-exact)
 cudaError_t sample_smem_config_f32(int bucket, bool exact, int kind, bool one, int max_smem,
-                                   bool ax = false);
+                                   bool ax = false, bool p1 = false);
 // §4.2: the data histogram of the map's training (buffer buf; f NULL: the integrand).
 cudaError_t launch_precondition(int bucket, int kind, cudaStream_t s, const Desc *desc, int member,
                                 int64_t n, const double *x, const double *f, uint32_t buf);
@@ -1324,12 +1595,12 @@ cudaError_t launch_precondition(int bucket, int kind, cudaStream_t s, const Desc
 cudaError_t sample_smem_config_f64(int bucket, bool exact, int kind, bool one, int max_smem,
                                    bool mo = false, bool ax = false);
 int sample_occupancy_f32(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
-                         bool ax = false);
+                         bool ax = false, bool p1 = false);
 int sample_occupancy_f64(int bucket, bool exact, int kind, bool one, int threads, size_t smem,
                          bool mo = false, bool ax = false);
 // Resident CTAs of the one-integral kernel with clusters of cs CTAs (0 if it cannot run).
 int sample_cluster_ctas_f32(int bucket, bool exact, int kind, int cs, int grid, int threads,
-                            size_t smem);
+                            size_t smem, bool p1 = false);
 int sample_cluster_ctas_f64(int bucket, bool exact, int kind, int cs, int grid, int threads,
                             size_t smem, bool mo = false);
 

@@ -481,12 +481,15 @@ class Integrator:
     def tuning(self):
         v = [ctypes.c_int() for _ in range(5)]
         check(lib().vp_get_tuning(self.ctx, *[ctypes.byref(x) for x in v]))
-        return dict(scheme=["static-cluster", "tasks"][v[0].value], blocks=v[1].value,
+        return dict(scheme=["static-cluster", "tasks", "static-dynamic"][v[0].value],
+                    blocks=v[1].value,
                     threads=v[2].value, cluster=v[3].value, run=v[4].value)
 
     def set_tuning(self, scheme, blocks, threads=256, cluster=1, run=8):
-        """Fixes the sampling launch shape (scheme "static-cluster" or "tasks")."""
-        code = {"static-cluster": 0, "tasks": 1}[scheme] if isinstance(scheme, str) else int(scheme)
+        """Fixes the sampling launch shape (scheme "static-cluster", "tasks" or
+        "static-dynamic")."""
+        code = ({"static-cluster": 0, "tasks": 1, "static-dynamic": 2}[scheme]
+                if isinstance(scheme, str) else int(scheme))
         check(lib().vp_set_tuning(self.ctx, code, int(blocks), int(threads), int(cluster),
                                   int(run)))
 
