@@ -969,10 +969,11 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                             ctas = std::min(ctas, blocks) / cs * cs;
                             if (ctas < (int)(0.9 * blocks)) continue;
                         }
+                        // (the dynamic tail, scheme 2, is not among the candidates:
+                        // measured, it wins only while one hypercube holds most of
+                        // an iteration's samples, and loses on the settled
+                        // allocations the tuner sees; vp_set_tuning selects it)
                         cands.push_back({true, ctas, cs, g.r, threads, kStaticShare});
-                        // a static head and a dynamic tail in chunks of 32 x 8
-                        // samples (SMs run this kernel at different speeds)
-                        cands.push_back({true, ctas, cs, 8, threads, kTailShare});
                     }
                 }
             }
