@@ -149,6 +149,8 @@ struct EstPre {
 };
 __device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode,
                                 const EstPre &pre);
+__device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, int mode, const EstPre &pre,
+                                    double *red, bool *s_last);
 
 struct EstShared {
     double recv2[3][256];  // level 256: CTA 1's terms, received by CTA 0
@@ -253,6 +255,19 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256, 4)
     r0[t] = __dadd_rn(a.a, sm.recv2[0][t]);
     r1[t] = __dadd_rn(a.b, sm.recv2[1][t]);
     r2[t] = __dadd_rn(a.c, sm.recv2[2][t]);
+    estimate_block_tail(d, k, mode, pre, &sm.red[0][0], &s_last);
+}
+
+// The rest of a block's fixed-order tree, one CTA of 256 threads: red[c][t]
+// (red = 3 x 256 doubles in shared memory) holds the sum of terms t, t + 256,
+// t + 512, t + 768 of series c (the first two halving levels); then the
+// levels 128 .. 1, the block sum to part[3 k + c], and in the last block of
+// the integral the block sums in the fixed tree order and the iteration's
+// bookkeeping.
+__device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, int mode, const EstPre &pre,
+                                    double *red, bool *s_last) {
+    const int t = threadIdx.x;
+    double *r0 = red, *r1 = red + 256, *r2 = red + 512;
     __syncthreads();
     for (int s = 128; s >= 64; s >>= 1) {
         if (t < s) {
@@ -279,18 +294,61 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256, 4)
     __syncthreads();
     if (t == 0) {
         const uint32_t ticket = atomicAdd(&d.st->done_est, 1u);
-        s_last = (ticket == d.n_tree - 1);
+        *s_last = (ticket == d.n_tree - 1);
     }
     __syncthreads();
-    if (!s_last) return;
+    if (!*s_last) return;
     // last block of this integral: the block sums in the fixed tree order
     __threadfence();
     __syncthreads();
     double tot[3];
-    block_tree_sum<3>(d.part, d.n_tree, &sm.red[0][0], tot);
+    block_tree_sum<3>(d.part, d.n_tree, red, tot);
     if (t != 0) return;
     d.st->done_est = 0u;
     finish_estimate(d, tot[0], tot[1], tot[2], mode, pre);
+}
+
+// k_estimate for many blocks (large N_h): one CTA of 256 threads per block of
+// 1024 hypercubes, each thread four of them (t, t + 256, t + 512, t + 768),
+// so that more loads are in flight per thread; the first two halving levels
+// are the thread's own (t + 512 joins t, t + 768 joins t + 256, then t + 256
+// joins t), the same tree as the cluster form's.
+__global__ void __launch_bounds__(256, 4)
+    k_estimate_wide(const Desc *desc, const uint32_t *tree_base, int n_int, int mode) {
+    __shared__ double red[3 * 256];
+    __shared__ bool s_last;
+    pdl_wait();
+    pdl_trigger();
+    const uint32_t tb = blockIdx.x;
+    const int b = owner_of(tree_base, n_int, tb);
+    const Desc &d = desc[b];
+    const uint32_t k = tb - tree_base[b];
+    const int t = threadIdx.x;
+    const uint32_t par = d.st->t & 1u;
+    EstPre pre = {0u, 0u, 0ull, 0ull};
+    if (t == 0) {
+        pre.t = d.st->t;
+        pre.status = d.st->status;
+        pre.n_samples = d.st->n_samples;
+        pre.n_eval_total = d.st->n_eval_total;
+    }
+    const uint64_t h0 = (uint64_t)k * kTreeBlock + t;
+    const D3 v0 = hcube_terms(d, h0, mode, par), v1 = hcube_terms(d, h0 + 256, mode, par);
+    const D3 v2 = hcube_terms(d, h0 + 512, mode, par), v3 = hcube_terms(d, h0 + 768, mode, par);
+    if (mode == 0) {  // clear the other histogram buffer, spread over this integral's CTAs
+        const int bins = d.dim * d.n_g;
+        double *hs = d.hsum + (size_t)(par ^ 1u) * bins;
+        uint32_t *hc = d.hcnt + (size_t)(par ^ 1u) * bins;
+        const int stride = (int)d.n_tree * 256;
+        for (int i = (int)k * 256 + t; i < bins; i += stride) {
+            hs[i] = 0.0;
+            hc[i] = 0u;
+        }
+    }
+    red[t] = __dadd_rn(__dadd_rn(v0.a, v2.a), __dadd_rn(v1.a, v3.a));
+    red[256 + t] = __dadd_rn(__dadd_rn(v0.b, v2.b), __dadd_rn(v1.b, v3.b));
+    red[512 + t] = __dadd_rn(__dadd_rn(v0.c, v2.c), __dadd_rn(v1.c, v3.c));
+    estimate_block_tail(d, k, mode, pre, red, &s_last);
 }
 
 // The iteration's totals I_j, sigma_j^2 and sum d recorded in the state (one
@@ -452,6 +510,9 @@ __device__ __forceinline__ unsigned long long cta_exclusive_scan(unsigned long l
 // ---------------------------------------------------------------------------
 // (eight CTAs per SM: the batched loads of the last CTA's scan must not cost
 // the other CTAs their occupancy)
+__device__ __forceinline__ void alloc_scan_tail(const Desc &d, unsigned long long *s_w,
+                                unsigned long long *s_carry);
+
 __global__ void __launch_bounds__(kSubH, 8) k_alloc(const Desc *desc, const uint32_t *tree_base,
                                                     int n_int, int initial) {
     __shared__ unsigned long long s_w[8];
@@ -486,6 +547,15 @@ __global__ void __launch_bounds__(kSubH, 8) k_alloc(const Desc *desc, const uint
     }
     __syncthreads();
     if (!s_last) return;
+    alloc_scan_tail(d, s_w, &s_carry);
+}
+
+// The last CTA of an integral's allocation: the exclusive scan of its
+// sub-block sums in place (bsum[q] becomes the offset of sub-block q),
+// off[N_h] and the iteration's sample count.
+__device__ __forceinline__ void alloc_scan_tail(const Desc &d, unsigned long long *s_w,
+                                unsigned long long *s_carry) {
+    const uint32_t n_sub = d.n_tree * kSub;
     // last CTA: exclusive scan of the sub-block sums in place, kScanV
     // consecutive sums per thread per pass (their loads issued together)
     __threadfence();
@@ -504,16 +574,16 @@ __global__ void __launch_bounds__(kSubH, 8) k_alloc(const Desc *desc, const uint
         }
         unsigned long long all;
         const unsigned long long ex = cta_exclusive_scan(own, s_w, &all);
-        const unsigned long long base = s_carry + ex;
+        const unsigned long long base = *s_carry + ex;
 #pragma unroll
         for (uint32_t k = 0; k < kScanV; ++k)
             if (q + k < n_sub) d.bsum[q + k] = base + v[k];
         __syncthreads();
-        if (threadIdx.x == 0) s_carry += all;
+        if (threadIdx.x == 0) *s_carry += all;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const unsigned long long run = s_carry;
+        const unsigned long long run = *s_carry;
         d.off[d.n_hc] = run;
         d.st->n_samples = run;
         d.st->done_alloc = 0u;
@@ -535,6 +605,87 @@ __global__ void __launch_bounds__(kSubH) k_offsets(const Desc *desc, const uint3
     unsigned long long tot;
     const unsigned long long ex = cta_exclusive_scan(n, s_w, &tot);
     if (h < d.n_hc) d.off[h] = d.bsum[sub] + ex;
+}
+
+// k_alloc and k_offsets for many blocks (large N_h): one CTA of kSubH threads
+// per block of kTreeBlock hypercubes, each thread the hypercubes t + kSubH q of
+// its kSub sub-blocks q (the same sub-blocks, sums and scans as one CTA per
+// sub-block).
+__global__ void __launch_bounds__(kSubH, 4) k_alloc_wide(const Desc *desc,
+                                                         const uint32_t *tree_base, int n_int,
+                                                         int initial) {
+    __shared__ unsigned long long s_w[8];
+    __shared__ bool s_last;
+    __shared__ unsigned long long s_carry;
+    pdl_wait();
+    pdl_trigger();
+    const uint32_t tb = blockIdx.x;
+    const int b = owner_of(tree_base, n_int, tb);
+    const Desc &d = desc[b];
+    const uint32_t k = tb - tree_base[b];
+    const double sum_d = d.st->sum_d;
+    if (!finite_bits(sum_d)) {
+        if (threadIdx.x == 0 && k == 0) d.st->status |= kStatusNonFinite;
+        return;
+    }
+    const double inv_sum = d.st->inv_sum_d;
+    uint32_t n[kSub];
+    double dh[kSub];
+#pragma unroll
+    for (int q = 0; q < kSub; ++q) {  // (the loads first, together)
+        const uint64_t h = (uint64_t)k * kTreeBlock + (uint64_t)q * kSubH + threadIdx.x;
+        dh[q] = h < d.n_hc ? d.dh[h] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kSub; ++q) {
+        const uint64_t h = (uint64_t)k * kTreeBlock + (uint64_t)q * kSubH + threadIdx.x;
+        n[q] = 0u;
+        if (h < d.n_hc) {
+            n[q] = alloc_one(d, dh[q], d.n_ev_d, sum_d, inv_sum, initial);
+            d.n_h[h] = n[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSub; ++q) {
+        unsigned long long tot;
+        cta_exclusive_scan(n[q], s_w, &tot);
+        if (threadIdx.x == 0) d.bsum[(uint64_t)k * kSub + q] = tot;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t ticket = atomicAdd(&d.st->done_alloc, 1u);
+        s_last = (ticket == d.n_tree - 1);
+        s_carry = 0ull;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    alloc_scan_tail(d, s_w, &s_carry);
+}
+
+__global__ void __launch_bounds__(kSubH, 4) k_offsets_wide(const Desc *desc,
+                                                           const uint32_t *tree_base, int n_int) {
+    __shared__ unsigned long long s_w[8];
+    pdl_wait();
+    const uint32_t tb = blockIdx.x;
+    const int b = owner_of(tree_base, n_int, tb);
+    const Desc &d = desc[b];
+    if (!finite_bits(d.st->sum_d)) return;
+    const uint32_t k = tb - tree_base[b];
+    uint32_t n[kSub];
+    unsigned long long base[kSub];
+#pragma unroll
+    for (int q = 0; q < kSub; ++q) {
+        const uint64_t h = (uint64_t)k * kTreeBlock + (uint64_t)q * kSubH + threadIdx.x;
+        n[q] = h < d.n_hc ? d.n_h[h] : 0u;
+        base[q] = d.bsum[(uint64_t)k * kSub + q];
+    }
+#pragma unroll
+    for (int q = 0; q < kSub; ++q) {
+        const uint64_t h = (uint64_t)k * kTreeBlock + (uint64_t)q * kSubH + threadIdx.x;
+        unsigned long long tot;
+        const unsigned long long ex = cta_exclusive_scan(n[q], s_w, &tot);
+        if (h < d.n_hc) d.off[h] = base[q] + ex;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -884,14 +1035,29 @@ cudaError_t launch_chunks(const Desc *desc, const uint32_t *members, int n_group
                       C);
 }
 
+// Blocks of kTreeBlock hypercubes from which the per-hypercube kernels take
+// one CTA per block, four hypercubes per thread, instead of several CTAs per
+// block: with fewer blocks the one-CTA form leaves SMs (and their FP64 units)
+// idle, with more it keeps more loads in flight per thread.
+constexpr uint32_t kWideBlocks = 512;
+
 cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_int,
                             uint32_t n_blocks, int mode, cudaStream_t s) {
+    if (n_blocks >= kWideBlocks)
+        return launch_pdl(k_estimate_wide, dim3(n_blocks), dim3(256), s, desc, tree_base, n_int,
+                          mode);
     return launch_pdl(k_estimate, dim3(n_blocks * kEstCtas), dim3(256), s, desc, tree_base, n_int,
                       mode);
 }
 
 cudaError_t launch_alloc(const Desc *desc, const uint32_t *tree_base, int n_int,
                          uint32_t n_blocks, cudaStream_t s, int initial) {
+    if (n_blocks >= kWideBlocks) {
+        cudaError_t e = launch_pdl(k_alloc_wide, dim3(n_blocks), dim3(kSubH), s, desc, tree_base,
+                                   n_int, initial);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(k_offsets_wide, dim3(n_blocks), dim3(kSubH), s, desc, tree_base, n_int);
+    }
     cudaError_t e = launch_pdl(k_alloc, dim3(n_blocks * kSub), dim3(kSubH), s, desc, tree_base,
                                n_int, initial);
     if (e != cudaSuccess) return e;

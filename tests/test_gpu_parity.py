@@ -185,13 +185,16 @@ def _alloc_problem(beta, dim=8, n_st=4, n_ev=10 ** 6):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("beta", [0.0, 0.5, 0.75, 1.0])
-def test_alloc_from_sigma_bit_exact(beta, precision):
+@pytest.mark.parametrize("dim,n_st", [(8, 4), (20, 2)])
+def test_alloc_from_sigma_bit_exact(beta, precision, dim, n_st):
     """§3 Eqs. (dh), (nh) from the same sigma_h: d_h = sigma_h^beta, their sum
     in the fixed order, n_h and the offsets all bit-exact with the oracle on
     both paths (beta = 1/2 and 3/4 as correctly rounded square roots, the
-    reading both sides take), over sigma_h spanning 40 decades with zeros."""
-    rng = np.random.default_rng(11 + int(beta * 100))
-    prob = _alloc_problem(beta)
+    reading both sides take), over sigma_h spanning 40 decades with zeros;
+    65,536 hypercubes (several CTAs per block of 1024) and 2^20 (one CTA per
+    block, four hypercubes per thread)."""
+    rng = np.random.default_rng(11 + int(beta * 100) + dim)
+    prob = _alloc_problem(beta, dim=dim, n_st=n_st, n_ev=10 ** 7 if dim == 20 else 10 ** 6)
     g = gpu_of(prob, precision=precision)
     n_hc = g.n_hc
     for trial in range(3):
