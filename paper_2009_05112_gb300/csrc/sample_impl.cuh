@@ -186,8 +186,11 @@ __device__ __forceinline__ double f_post64(const double *p, int dim, const doubl
 
 // FP32: the points are visited group by group (points g, g + G, g + 2G, ...
 // share the weight w_g), so that each w_g is read from a fixed register.
+// Returns log2 f: a posterior's values span hundreds of binary orders below
+// its maximum (a sharp 21-parameter one integrates to ~1e-28), far beyond the
+// FP32 range, so f is formed by the caller as a mantissa and an exponent.
 template <int DMAX>
-__device__ __forceinline__ float f_post32(const float *p, int dim, const float (&x)[DMAX]) {
+__device__ __forceinline__ float f_post32_log2(const float *p, int dim, const float (&x)[DMAX]) {
     const int n = (int)p[0], npar = (int)p[1], ngrp = (int)p[2];
     const float kN = p[3], kW = p[4], lcN = p[5], lcW = p[6], kpr = p[7], lref = p[8];
     const float *y = p + 9;
@@ -216,7 +219,7 @@ __device__ __forceinline__ float f_post32(const float *p, int dim, const float (
     for (int m = 0; m < DMAX; ++m)
         if (m < npar) c2 = fmaf(x[m], x[m], c2);
     (void)dim;
-    return ex2_approx(fmaf(-kpr, c2, acc - lref));
+    return fmaf(-kpr, c2, acc - lref);
 }
 
 // ---------------------------------------------------------------------------
@@ -383,7 +386,8 @@ template <int DMAX, bool EXACT, int KIND, bool KP, bool AX>
 __device__ __forceinline__ void point32(const Loop &L, const Strata *S, const float *prm,
                                         uint32_t h, uint32_t j,
                                         const float (&kc)[DMAX], float (&x)[DMAX],
-                                        int (&idx)[DMAX], float &Jm, int &Je, float &f) {
+                                        int (&idx)[DMAX], float &Jm, int &Je, float &f,
+                                        int &fe) {
     const int dim = EXACT ? DMAX : L.dim;
     const uint32_t calls = EXACT ? (uint32_t)((DMAX + 3) / 4) : L.calls;
     float J = L.ngD_m;
@@ -419,9 +423,23 @@ __device__ __forceinline__ void point32(const Loop &L, const Strata *S, const fl
     }
     Jm = J;
     Je = e;
-    if (KIND == VP_POSTERIOR) f = f_post32<DMAX>(prm, dim, x);
-    else if (KP) f = f_peaks32_param<DMAX, KIND>(prm, L.K, dim, x);
-    else f = f_peaks32<DMAX>(KIND, prm, L.K, dim, x);
+    fe = 0;  // the integrand is f 2^fe
+    if (KIND == VP_POSTERIOR) {
+        // f = 2^lf as a mantissa in [1, 2) and an integer exponent (f = 0
+        // when log2 f is -inf or below any exponent that can matter)
+        const float lf = f_post32_log2<DMAX>(prm, dim, x);
+        if (lf > -1.0e9f) {
+            const float fl = floorf(lf);
+            f = ex2_approx(lf - fl);
+            fe = (int)fl;
+        } else {
+            f = 0.0f;
+        }
+    } else if (KP) {
+        f = f_peaks32_param<DMAX, KIND>(prm, L.K, dim, x);
+    } else {
+        f = f_peaks32<DMAX>(KIND, prm, L.K, dim, x);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -948,8 +966,10 @@ __device__ __forceinline__ void run_samples_t(const Loop &L, const Strata *S, co
                                            Je, f, hc, P.HC);
             } else {
                 float x[DMAX];
+                int fe;
                 point32<DMAX, EXACT, KIND, KP, AX>(L, S, (const float *)prm, (uint32_t)h, j, kc, x,
-                                                   idx, Jm, Je, f);
+                                                   idx, Jm, Je, f, fe);
+                Je += fe;  // J f = (Jm f) 2^(Je + fe)
             }
             float jf = Jm * f;  // Jm in [1, 2); the last multiply-add of f may leave it subnormal
             if (((__float_as_int(jf) & 0x7f800000) == 0) && jf != 0.0f) {  // renormalise (exact)
@@ -1482,12 +1502,13 @@ __global__ void k_eval(const Desc *desc, int member, int64_t n, const uint64_t *
             float kc[DMAX], x[DMAX], Jm, ff;
             int Je;
             hcube_offsets<DMAX, true>(L, S, kd, kc);
+            int fe;
             point32<DMAX, EXACT, KIND, false, true>(L, S, sprm, (uint32_t)hs[k], js[k], kc, x, idx,
-                                                    Jm, Je, ff);
+                                                    Jm, Je, ff, fe);
 #pragma unroll
             for (int mu = 0; mu < DMAX; ++mu) xd[mu] = (double)x[mu];
             jac = ldexp((double)Jm, Je);
-            f = (double)ff;
+            f = ldexp((double)ff, fe);
         }
 #pragma unroll
         for (int mu = 0; mu < DMAX; ++mu) {
