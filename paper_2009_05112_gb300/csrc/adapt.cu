@@ -102,11 +102,13 @@ __device__ __forceinline__ double damp(double sigma, double beta) {
     return pow(sigma, beta);
 }
 
-// d_h on the FP32 path: sigma_h^beta = Omega^beta var^(beta/2) (§3 Eq. dh),
-// var^(beta/2) from the exponent and mantissa bits of var with the FP32 log2
-// and exp2 units (relative error ~1e-6; the FP64 path takes damp()).  On this
-// part three FP64 square roots per hypercube would cost more than the
-// sampling of a few of its samples.  var >= 0 and finite.
+// d_h on the FP32 path: sigma_h^beta = 2^(beta/2 log2 var + beta log2 Omega)
+// (§3 Eq. dh), log2 var from the exponent and mantissa bits of var with the
+// FP32 log2 unit, the power's integer part put into the exponent field and its
+// fraction through the FP32 exp2 unit (relative error ~1e-6; the FP64 path
+// takes damp()).  On this part three FP64 square roots per hypercube would
+// cost more than the sampling of a few of its samples, and the result is
+// formed without an FP64 instruction.  var >= 0 and finite.
 __device__ __forceinline__ double damp_var32(double var, const Desc &d) {
     if ((uint64_t)__double_as_longlong(d.beta) == 0ull) return 1.0;  // beta = 0: d = 1
     uint64_t b = (uint64_t)__double_as_longlong(var);
@@ -123,8 +125,9 @@ __device__ __forceinline__ double damp_var32(double var, const Desc &d) {
     const float p = d.half_beta_hi * Ef;
     const float err = fmaf(d.half_beta_hi, Ef, -p);       // p + err = hi E exactly
     const float fl = floorf(p);                           // exact (|p| < 2^23)
-    const float y = (p - fl) + err + fmaf(d.half_beta_lo, Ef, d.half_beta_hi * lg2_approx(m));
-    return f2d_pow2(ex2_approx(y), (int)fl) * d.omega_beta;
+    const float y =
+        (p - fl) + err + fmaf(d.half_beta_lo, Ef, d.half_beta_hi * lg2_approx(m)) + d.lob_f;
+    return f2d_pow2(ex2_approx(y), (int)fl + d.lob_i);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,21 +171,36 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
         const double inv_n = nh < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh) : 1.0 / (double)nh;
         const double inv_n1 =
             nh - 1 < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh - 1) : 1.0 / (double)(nh - 1);
-        const double om = d.omega;
         const uint64_t ph = (uint64_t)par * d.n_hc + h;
-        const double m1 = d.s1[ph] * inv_n, m2 = d.s2[ph] * inv_n;
+        const double s1 = d.s1[ph], s2 = d.s2[ph];
         // the other buffer collects the next iteration's sums
         const uint64_t qh = (uint64_t)(par ^ 1u) * d.n_hc + h;
         d.s1[qh] = 0.0;
         d.s2[qh] = 0.0;
-        double var = m2 - m1 * m1;
+        const double m1 = s1 * inv_n;
+        double var;
+        if (d.prec == VP_FP32) {
+            // four FP64 operations (FP64 is scarce on this part): the variance as
+            // (S2 - S1 m1) / n_h, one fused multiply-add and one product, and
+            // Omega, Omega^2 applied to the two totals (finish_estimate)
+            var = fma(-s1, m1, s2) * inv_n;
+        } else {
+            var = fma(-m1, m1, __dmul_rn(s2, inv_n));  // m2 - m1^2
+        }
         {  // a rounding-negative variance (or -0) is zero; a NaN stays NaN
             const long long vb = __double_as_longlong(var);
             if (vb < 0ll && (vb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) var = 0.0;
         }
-        v.a = om * m1;
-        v.b = d.omega2 * var * inv_n1;  // (Omega Omega) var / (n_h - 1), left to right
-        v.c = d.prec == VP_FP32 ? damp_var32(var, d) : damp(om * sqrt(var), d.beta);
+        if (d.prec == VP_FP32) {
+            v.a = m1;
+            v.b = var * inv_n1;
+            v.c = damp_var32(var, d);
+        } else {
+            const double om = d.omega;
+            v.a = om * m1;
+            v.b = d.omega2 * var * inv_n1;  // (Omega Omega) var / (n_h - 1), left to right
+            v.c = damp(om * sqrt(var), d.beta);
+        }
         d.dh[h] = v.c;
     } else if (mode == 1) {
         v.c = damp(d.dh[h], d.beta);
@@ -357,6 +375,10 @@ __global__ void __launch_bounds__(256, 4)
 __device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode,
                                 const EstPre &pre) {
     State *st = d.st;
+    if (d.prec == VP_FP32) {  // (the FP32 path's terms leave Omega and Omega^2 to the totals)
+        I *= d.omega;
+        V *= d.omega2;
+    }
     st->sum_d = Sd;
     st->inv_sum_d = Sd > 0.0 ? 1.0 / Sd : 0.0;
     if (mode == 0) {
@@ -475,30 +497,44 @@ __device__ __forceinline__ uint32_t alloc_one(const Desc &d, double dh, double n
     return iq > 2ull ? (uint32_t)iq : 2u;
 }
 
-// Exclusive scan of one value per thread over a CTA of 256 threads; returns
+// Exclusive scan of one value per thread over a CTA of 256 threads, in 32-bit
+// arithmetic (sums of n_h: an iteration's samples number below 2^32); returns
 // the exclusive prefix and (in *total) the CTA's sum.
-__device__ __forceinline__ unsigned long long cta_exclusive_scan(unsigned long long v,
-                                                                 unsigned long long *s_w,
-                                                                 unsigned long long *total) {
+__device__ __forceinline__ uint32_t cta_exclusive_scan32(uint32_t v, uint32_t *s_w,
+                                                         uint32_t *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long inc = v;
+    uint32_t inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += u;
     }
     if (lane == 31) s_w[warp] = inc;
     __syncthreads();
-    unsigned long long base = 0ull, all = 0ull;
+    uint32_t base = 0u, all = 0u;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
-        const unsigned long long x = s_w[w];
+        const uint32_t x = s_w[w];
         if (w < warp) base += x;
         all += x;
     }
     __syncthreads();  // s_w may be reused
     *total = all;
     return base + inc - v;
+}
+
+// Sum of one 32-bit value per thread over a CTA of 256 threads (every thread
+// gets it).
+__device__ __forceinline__ uint32_t cta_sum32(uint32_t v, uint32_t *s_w) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t all = 0u;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) all += s_w[w];
+    __syncthreads();
+    return all;
 }
 
 // ---------------------------------------------------------------------------
@@ -510,14 +546,15 @@ __device__ __forceinline__ unsigned long long cta_exclusive_scan(unsigned long l
 // ---------------------------------------------------------------------------
 // (eight CTAs per SM: the batched loads of the last CTA's scan must not cost
 // the other CTAs their occupancy)
-__device__ __forceinline__ void alloc_scan_tail(const Desc &d, unsigned long long *s_w,
-                                unsigned long long *s_carry);
+template <uint32_t kScanV>
+__device__ __forceinline__ void alloc_scan_tail(const Desc &d, uint32_t n_sub, uint32_t *s_w,
+                                                uint32_t *s_carry);
 
 __global__ void __launch_bounds__(kSubH, 8) k_alloc(const Desc *desc, const uint32_t *tree_base,
                                                     int n_int, int initial) {
-    __shared__ unsigned long long s_w[8];
+    __shared__ uint32_t s_w[8];
     __shared__ bool s_last;
-    __shared__ unsigned long long s_carry;
+    __shared__ uint32_t s_carry;
     pdl_wait();
     pdl_trigger();
     const uint32_t tb = blockIdx.x / kSub;
@@ -535,49 +572,48 @@ __global__ void __launch_bounds__(kSubH, 8) k_alloc(const Desc *desc, const uint
         n = alloc_one(d, d.dh[h], d.n_ev_d, sum_d, d.st->inv_sum_d, initial);
         d.n_h[h] = n;
     }
-    unsigned long long tot;
-    cta_exclusive_scan(n, s_w, &tot);
+    const uint32_t tot = cta_sum32(n, s_w);
     const uint32_t n_sub = d.n_tree * kSub;
     if (threadIdx.x == 0) {
         d.bsum[sub] = tot;
         __threadfence();
         const uint32_t ticket = atomicAdd(&d.st->done_alloc, 1u);
         s_last = (ticket == n_sub - 1);
-        s_carry = 0ull;
+        s_carry = 0u;
     }
     __syncthreads();
     if (!s_last) return;
-    alloc_scan_tail(d, s_w, &s_carry);
+    alloc_scan_tail<4>(d, n_sub, s_w, &s_carry);
 }
 
-// The last CTA of an integral's allocation: the exclusive scan of its
-// sub-block sums in place (bsum[q] becomes the offset of sub-block q),
-// off[N_h] and the iteration's sample count.
-__device__ __forceinline__ void alloc_scan_tail(const Desc &d, unsigned long long *s_w,
-                                unsigned long long *s_carry) {
-    const uint32_t n_sub = d.n_tree * kSub;
-    // last CTA: exclusive scan of the sub-block sums in place, kScanV
-    // consecutive sums per thread per pass (their loads issued together)
+// The last CTA of an integral's allocation: the exclusive scan of its n_sub
+// partial sums of n_h in place (bsum[q] becomes the offset of part q),
+// off[N_h] and the iteration's sample count.  kScanV consecutive sums per
+// thread per pass, their loads issued together; 32-bit sums (an iteration's
+// samples number below 2^32).
+template <uint32_t kScanV>
+__device__ __forceinline__ void alloc_scan_tail(const Desc &d, uint32_t n_sub, uint32_t *s_w,
+                                                uint32_t *s_carry) {
     __threadfence();
-    constexpr uint32_t kScanV = 4;
     for (uint32_t q0 = 0; q0 < n_sub; q0 += kSubH * kScanV) {
         const uint32_t q = q0 + threadIdx.x * kScanV;
-        unsigned long long v[kScanV];
+        uint32_t v[kScanV];
 #pragma unroll
-        for (uint32_t k = 0; k < kScanV; ++k) v[k] = q + k < n_sub ? __ldcg(d.bsum + q + k) : 0ull;
-        unsigned long long own = 0ull;
+        for (uint32_t k = 0; k < kScanV; ++k)
+            v[k] = q + k < n_sub ? (uint32_t)__ldcg(d.bsum + q + k) : 0u;
+        uint32_t own = 0u;
 #pragma unroll
         for (uint32_t k = 0; k < kScanV; ++k) {  // exclusive within the thread's run
-            const unsigned long long x = v[k];
+            const uint32_t x = v[k];
             v[k] = own;
             own += x;
         }
-        unsigned long long all;
-        const unsigned long long ex = cta_exclusive_scan(own, s_w, &all);
-        const unsigned long long base = *s_carry + ex;
+        uint32_t all;
+        const uint32_t ex = cta_exclusive_scan32(own, s_w, &all);
+        const uint32_t base = *s_carry + ex;
 #pragma unroll
         for (uint32_t k = 0; k < kScanV; ++k)
-            if (q + k < n_sub) d.bsum[q + k] = base + v[k];
+            if (q + k < n_sub) d.bsum[q + k] = (unsigned long long)(base + v[k]);
         __syncthreads();
         if (threadIdx.x == 0) *s_carry += all;
         __syncthreads();
@@ -593,7 +629,7 @@ __device__ __forceinline__ void alloc_scan_tail(const Desc &d, unsigned long lon
 // k_offsets: off[h] = offset of the sub-block + exclusive scan of n_h within it.
 __global__ void __launch_bounds__(kSubH) k_offsets(const Desc *desc, const uint32_t *tree_base,
                                                    int n_int) {
-    __shared__ unsigned long long s_w[8];
+    __shared__ uint32_t s_w[8];
     pdl_wait();
     const uint32_t tb = blockIdx.x / kSub;
     const int b = owner_of(tree_base, n_int, tb);
@@ -602,21 +638,32 @@ __global__ void __launch_bounds__(kSubH) k_offsets(const Desc *desc, const uint3
     const uint32_t sub = (tb - tree_base[b]) * kSub + blockIdx.x % kSub;
     const uint64_t h = (uint64_t)sub * kSubH + threadIdx.x;
     const uint32_t n = h < d.n_hc ? d.n_h[h] : 0u;
-    unsigned long long tot;
-    const unsigned long long ex = cta_exclusive_scan(n, s_w, &tot);
+    uint32_t tot;
+    const uint32_t ex = cta_exclusive_scan32(n, s_w, &tot);
     if (h < d.n_hc) d.off[h] = d.bsum[sub] + ex;
 }
 
 // k_alloc and k_offsets for many blocks (large N_h): one CTA of kSubH threads
-// per block of kTreeBlock hypercubes, each thread the hypercubes t + kSubH q of
-// its kSub sub-blocks q (the same sub-blocks, sums and scans as one CTA per
-// sub-block).
+// per block of kTreeBlock hypercubes, thread t holding hypercubes 4t .. 4t + 3
+// of the block (vector loads and stores), one sum of n_h per block; the last
+// CTA scans the n_tree block sums (16 per thread per pass).
+__device__ __forceinline__ void load4_dh(const Desc &d, uint64_t h0, bool full, double (&dh)[4]) {
+    if (full) {
+        const double2 a = __ldcs((const double2 *)(d.dh + h0));
+        const double2 b = __ldcs((const double2 *)(d.dh + h0 + 2));
+        dh[0] = a.x; dh[1] = a.y; dh[2] = b.x; dh[3] = b.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dh[q] = h0 + q < d.n_hc ? d.dh[h0 + q] : 0.0;
+    }
+}
+
 __global__ void __launch_bounds__(kSubH, 4) k_alloc_wide(const Desc *desc,
                                                          const uint32_t *tree_base, int n_int,
                                                          int initial) {
-    __shared__ unsigned long long s_w[8];
+    __shared__ uint32_t s_w[8];
     __shared__ bool s_last;
-    __shared__ unsigned long long s_carry;
+    __shared__ uint32_t s_carry;
     pdl_wait();
     pdl_trigger();
     const uint32_t tb = blockIdx.x;
@@ -629,62 +676,73 @@ __global__ void __launch_bounds__(kSubH, 4) k_alloc_wide(const Desc *desc,
         return;
     }
     const double inv_sum = d.st->inv_sum_d;
-    uint32_t n[kSub];
-    double dh[kSub];
+    const uint64_t h0 = (uint64_t)k * kTreeBlock + 4u * threadIdx.x;
+    const bool full = h0 + 4 <= d.n_hc;
+    double dh[4];
+    load4_dh(d, h0, full, dh);
+    uint32_t n[4], own = 0u;
 #pragma unroll
-    for (int q = 0; q < kSub; ++q) {  // (the loads first, together)
-        const uint64_t h = (uint64_t)k * kTreeBlock + (uint64_t)q * kSubH + threadIdx.x;
-        dh[q] = h < d.n_hc ? d.dh[h] : 0.0;
+    for (int q = 0; q < 4; ++q) {
+        n[q] = h0 + q < d.n_hc ? alloc_one(d, dh[q], d.n_ev_d, sum_d, inv_sum, initial) : 0u;
+        own += n[q];
     }
+    if (full) {
+        *(uint4 *)(d.n_h + h0) = make_uint4(n[0], n[1], n[2], n[3]);
+    } else {
 #pragma unroll
-    for (int q = 0; q < kSub; ++q) {
-        const uint64_t h = (uint64_t)k * kTreeBlock + (uint64_t)q * kSubH + threadIdx.x;
-        n[q] = 0u;
-        if (h < d.n_hc) {
-            n[q] = alloc_one(d, dh[q], d.n_ev_d, sum_d, inv_sum, initial);
-            d.n_h[h] = n[q];
-        }
+        for (int q = 0; q < 4; ++q)
+            if (h0 + q < d.n_hc) d.n_h[h0 + q] = n[q];
     }
-#pragma unroll
-    for (int q = 0; q < kSub; ++q) {
-        unsigned long long tot;
-        cta_exclusive_scan(n[q], s_w, &tot);
-        if (threadIdx.x == 0) d.bsum[(uint64_t)k * kSub + q] = tot;
-    }
+    const uint32_t tot = cta_sum32(own, s_w);
     if (threadIdx.x == 0) {
+        d.bsum[k] = tot;
         __threadfence();
         const uint32_t ticket = atomicAdd(&d.st->done_alloc, 1u);
         s_last = (ticket == d.n_tree - 1);
-        s_carry = 0ull;
+        s_carry = 0u;
     }
     __syncthreads();
     if (!s_last) return;
-    alloc_scan_tail(d, s_w, &s_carry);
+    alloc_scan_tail<16>(d, d.n_tree, s_w, &s_carry);
 }
 
 __global__ void __launch_bounds__(kSubH, 4) k_offsets_wide(const Desc *desc,
                                                            const uint32_t *tree_base, int n_int) {
-    __shared__ unsigned long long s_w[8];
+    __shared__ uint32_t s_w[8];
     pdl_wait();
     const uint32_t tb = blockIdx.x;
     const int b = owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
     if (!finite_bits(d.st->sum_d)) return;
     const uint32_t k = tb - tree_base[b];
-    uint32_t n[kSub];
-    unsigned long long base[kSub];
+    const uint64_t h0 = (uint64_t)k * kTreeBlock + 4u * threadIdx.x;
+    const bool full = h0 + 4 <= d.n_hc;
+    uint32_t n[4];
+    if (full) {
+        const uint4 v = __ldcs((const uint4 *)(d.n_h + h0));
+        n[0] = v.x; n[1] = v.y; n[2] = v.z; n[3] = v.w;
+    } else {
 #pragma unroll
-    for (int q = 0; q < kSub; ++q) {
-        const uint64_t h = (uint64_t)k * kTreeBlock + (uint64_t)q * kSubH + threadIdx.x;
-        n[q] = h < d.n_hc ? d.n_h[h] : 0u;
-        base[q] = d.bsum[(uint64_t)k * kSub + q];
+        for (int q = 0; q < 4; ++q) n[q] = h0 + q < d.n_hc ? d.n_h[h0 + q] : 0u;
     }
+    const unsigned long long blk = d.bsum[k];
+    uint32_t e[4], own = 0u;
 #pragma unroll
-    for (int q = 0; q < kSub; ++q) {
-        const uint64_t h = (uint64_t)k * kTreeBlock + (uint64_t)q * kSubH + threadIdx.x;
-        unsigned long long tot;
-        const unsigned long long ex = cta_exclusive_scan(n[q], s_w, &tot);
-        if (h < d.n_hc) d.off[h] = base[q] + ex;
+    for (int q = 0; q < 4; ++q) {
+        e[q] = own;
+        own += n[q];
+    }
+    uint32_t tot;
+    const uint32_t ex = cta_exclusive_scan32(own, s_w, &tot);
+    const unsigned long long base = blk + ex;
+    if (full) {
+        ulonglong2 *o = (ulonglong2 *)(d.off + h0);
+        o[0] = make_ulonglong2(base + e[0], base + e[1]);
+        o[1] = make_ulonglong2(base + e[2], base + e[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (h0 + q < d.n_hc) d.off[h0 + q] = base + e[q];
     }
 }
 

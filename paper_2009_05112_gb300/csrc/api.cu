@@ -521,6 +521,22 @@ vp_status vp::group_config_many(const std::vector<const Member *> &m, Group &g, 
 // ---------------------------------------------------------------------------
 // one member's descriptor and initial device state
 // ---------------------------------------------------------------------------
+// The FP32 path's constants of d_h = sigma_h^beta (§3 Eq. dh) with
+// sigma_h = Omega sqrt(var): beta/2 as a sum of two floats, and
+// beta log2(Omega) = -beta log2(N_h) as an integer plus a fraction in [0, 1).
+void vp::damp_consts(Desc &d, double beta) {
+    d.half_beta_hi = (float)(0.5 * beta);
+    d.half_beta_lo = (float)(0.5 * beta - (double)d.half_beta_hi);
+    const double c = -beta * std::log2((double)d.n_hc);
+    const double ci = std::floor(c);
+    d.lob_i = (int32_t)ci;
+    d.lob_f = (float)(c - ci);
+    if (d.lob_f >= 1.0f) {  // (the fraction rounded up to 1)
+        d.lob_i += 1;
+        d.lob_f = 0.0f;
+    }
+}
+
 void vp::inv_table(std::vector<double> &inv) {
     inv.assign(kInvTab, 0.0);
     for (int k = 1; k < kInvTab; ++k) inv[k] = 1.0 / (double)k;  // IEEE division on the host
@@ -549,9 +565,7 @@ void vp::fill_desc(const Member &mb, const double *d_inv, Desc &d) {
     d.n_ev_d = (double)mb.p.n_ev;
     d.alpha = mb.p.alpha;
     d.beta = mb.p.beta;
-    d.omega_beta = std::pow(d.omega, mb.p.beta);
-    d.half_beta_hi = (float)(0.5 * mb.p.beta);
-    d.half_beta_lo = (float)(0.5 * mb.p.beta - (double)d.half_beta_hi);
+    damp_consts(d, mb.p.beta);
     d.ng_over_nst = (float)((double)G / (double)mb.n_st);
     d.inv_ng = (float)(1.0 / (double)G);
     {
@@ -1568,9 +1582,7 @@ static vp_status set_damping(Set &s, int i, double alpha, double beta) {
     Desc &d = s.h_desc[i];
     d.alpha = alpha;
     d.beta = beta;
-    d.omega_beta = std::pow(d.omega, beta);
-    d.half_beta_hi = (float)(0.5 * beta);
-    d.half_beta_lo = (float)(0.5 * beta - (double)d.half_beta_hi);
+    damp_consts(d, beta);
     CU(cudaMemcpy(s.d_desc + i, &d, sizeof d, cudaMemcpyHostToDevice));
     bool any = false;
     for (const Member &m : s.m) any |= m.p.alpha > 0.0 && m.p.n_g > 1;

@@ -144,6 +144,8 @@ void fill_desc(const Member &mb, const double *d_inv, Desc &d);
 vp_status upload_member_init(const Member &mb, const Desc &d, cudaStream_t stream);
 // Table of 1/n, n < kInvTab (IEEE division on the host), for the descriptors.
 void inv_table(std::vector<double> &inv);
+// The FP32 path's constants of the damping power beta in a descriptor (n_hc set).
+void damp_consts(Desc &d, double beta);
 // Shared memory and residency of a task-kernel group from its members.
 // (g.members index m)
 vp_status group_config_many(const std::vector<const Member *> &m, Group &g, int n_sm);

@@ -86,7 +86,8 @@ struct Desc {
     double omega2;             // omega * omega (IEEE product, as the kernels would form it)
     double n_ev_d;             // (double) n_ev (exact below 2^53)
     double alpha, beta;
-    double omega_beta;         // Omega^beta (FP32 path: d_h = Omega^beta var^(beta/2))
+    int32_t lob_i;             // beta log2(Omega) = lob_i + lob_f, lob_f in [0, 1)
+    float lob_f;               //   (FP32 path: d_h = 2^(beta/2 log2 var + beta log2 Omega))
     float half_beta_hi, half_beta_lo;  // beta/2 = hi + lo (FP32 path)
     float ng_over_nst;         // N_g / N_st (FP32 path)
     float inv_ng;              // 1 / N_g (FP32 path)
