@@ -499,8 +499,41 @@ def _sampling_ms(g, flush):
     return sum(ms) / len(ms)
 
 
+_ATOMIC_RATES = {}
+
+
+def _atomic_view(g, vegasp, dim, samples_per_step, k1_ms, n_sample=65536):
+    """The sampling kernel against the shared-memory atomic bound of its
+    histograms (§2.3 d_i): D 32-bit count adds per sample and D FP32 sum adds
+    per sample whose J f is nonzero, at the rates the library's probe measures
+    on this device; the share of nonzero samples from n_sample samples of the
+    current allocation evaluated by the kernel's own code (vp_eval_samples)."""
+    import numpy as np
+    if not _ATOMIC_RATES:
+        _ATOMIC_RATES["u32"] = vegasp.shared_atomic_rate(False)
+        _ATOMIC_RATES["f32"] = vegasp.shared_atomic_rate(True)
+    n_h, off = g.alloc()
+    total = int(off[-1])
+    rng = np.random.default_rng(12345)
+    s = rng.integers(0, total, size=n_sample).astype(np.uint64)
+    h = (np.searchsorted(off, s, side="right") - 1).astype(np.uint64)
+    j = (s - off[h.astype(np.int64)]).astype(np.uint32)
+    f = g.eval_samples(h, j, g.result()["n_it"])[3]
+    nz = float(np.count_nonzero(f) / n_sample)
+    counts, sums = dim * samples_per_step, dim * nz * samples_per_step
+    bound_ms = (counts / _ATOMIC_RATES["u32"] + sums / _ATOMIC_RATES["f32"]) * 1e3
+    return {"bound": "shared-memory atomics", "count_adds_per_launch": counts,
+            "sum_adds_per_launch": sums, "nonzero_share": nz,
+            "peak_u32_adds_per_s": _ATOMIC_RATES["u32"], "peak_f32_adds_per_s": _ATOMIC_RATES["f32"],
+            "bound_ms": bound_ms, "frac": bound_ms / k1_ms,
+            "note": "time the histogram adds alone would take at the rates measured live by "
+                    "vp_shared_atomic_rate (random increments, 20 axes x 1000, one 768-thread "
+                    "CTA per SM) over the kernel's CUDA-event time; the nonzero share sampled "
+                    "from %d samples of the current allocation" % n_sample}
+
+
 def _sample_roofline(workload, prob, n_peaks, samples_per_step, k1_ms, step_ms, n_sm,
-                     clocks, max_mhz):
+                     clocks, max_mhz, atomics=None):
     """The sampling kernel against the FP32 roofline: algorithmic FP32 flops
     per sample (counted from the source, an FMA as 2) x samples per launch /
     its CUDA-event duration, over SMs x 128 lanes x 2 flops x the maximum SM
@@ -532,6 +565,8 @@ def _sample_roofline(workload, prob, n_peaks, samples_per_step, k1_ms, step_ms, 
                            "note": "algorithmic lane operations (Philox, map, integrand, "
                                    "moments, histogram atomics) over issue slots"},
             "ncu_pct_of_peak_elapsed": prof["pipes_pct_elapsed"] if prof else None}
+    if atomics is not None:
+        roof["atomics_view"] = atomics
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = tflops / (n_sm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
     return roof
@@ -549,11 +584,13 @@ def _single_summary(workload, args, inputs, vegasp, flush, n_sm, max_mhz):
                                            int(os.environ.get("LOCAL_RANK", "0")))
     k1 = _sampling_ms(g, flush)
     roof = _sample_roofline(workload, prob, n_peaks, evals / args.steps, k1,
-                            total_ms / args.steps, n_sm, clocks, max_mhz)
+                            total_ms / args.steps, n_sm, clocks, max_mhz,
+                            _atomic_view(g, vegasp, prob.dim, evals / args.steps, k1))
     out = {"value": evals / (total_ms / 1e3), "unit": "integrand evals/s",
            "ms_per_step": total_ms / args.steps, "steps": args.steps,
            "n_ev": prob.n_ev, "dim": prob.dim, "n_hc": g.n_hc,
            "kernel_ms": k1, "fp32_frac": roof["frac"], "issue_frac": roof["issue_view"]["frac"],
+           "atomics_frac": roof["atomics_view"]["frac"],
            "traffic": roof["traffic"], "ncu_pct_of_peak_elapsed": roof["ncu_pct_of_peak_elapsed"],
            "clocks": clocks, "sample_launch": g.tuning(),
            "integral": dict(_integral(g, prob, False), exact=prob.exact)}
@@ -670,7 +707,8 @@ def run_ours(args):
                              "operation each, so frac is a lower bound"}
     else:
         roof = _sample_roofline(args.workload, prob, n_peaks, samples_per_step, k1_avg_ms,
-                                step_ms, n_sm, clocks, max_mhz)
+                                step_ms, n_sm, clocks, max_mhz,
+                                _atomic_view(g, vegasp, prob.dim, samples_per_step, k1_avg_ms))
     if precond:
         h2d += data.size * 8
     integrand = ("ball" if ball else "exp(-50|x|), mixed strata %s" % list(g.strata()) if expo

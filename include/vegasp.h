@@ -490,6 +490,19 @@ vp_status vp_server_destroy(vp_server *s);
 vp_status vp_alloc_static(const double *d_h, int64_t n_hc, int64_t n_ev, int plus2,
                           uint32_t *n_h, uint64_t *offsets, void *stream);
 
+/* Measures the device's throughput of shared-memory atomic adds in the access
+ * pattern of the sampling kernel's histograms (§2.3 d_i: one count per axis per
+ * sample, and one FP32 sum per axis per sample where J f is nonzero): every
+ * thread of one 768-thread CTA per SM adds to one random increment on each of
+ * 20 axes of 1000 increments, 256 times.  f32 = 0: 32-bit integer adds (the
+ * counts); f32 = 1: FP32 adds (the sums).  *per_s = adds per second, the best
+ * of three timed launches after one warm-up (CUDA events on the legacy default
+ * stream, which the call synchronises).  A measurement aid, not a step of the
+ * method: the bench reports the sampling kernel against this bound.  Uses the
+ * current device; allocates 4 bytes of device memory for the duration of the
+ * call.  VP_EINVAL: NULL out; VP_ECUDA: a launch failed. */
+vp_status vp_shared_atomic_rate(int f32, double *per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -177,30 +177,18 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
         const uint64_t qh = (uint64_t)(par ^ 1u) * d.n_hc + h;
         d.s1[qh] = 0.0;
         d.s2[qh] = 0.0;
+        // four FP64 operations (FP64 is scarce on this part): the variance as
+        // (S2 - S1 m1) / n_h, one fused multiply-add and one product, and
+        // Omega, Omega^2 applied to the two totals (finish_estimate)
         const double m1 = s1 * inv_n;
-        double var;
-        if (d.prec == VP_FP32) {
-            // four FP64 operations (FP64 is scarce on this part): the variance as
-            // (S2 - S1 m1) / n_h, one fused multiply-add and one product, and
-            // Omega, Omega^2 applied to the two totals (finish_estimate)
-            var = fma(-s1, m1, s2) * inv_n;
-        } else {
-            var = fma(-m1, m1, __dmul_rn(s2, inv_n));  // m2 - m1^2
-        }
+        double var = fma(-s1, m1, s2) * inv_n;
         {  // a rounding-negative variance (or -0) is zero; a NaN stays NaN
             const long long vb = __double_as_longlong(var);
             if (vb < 0ll && (vb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) var = 0.0;
         }
-        if (d.prec == VP_FP32) {
-            v.a = m1;
-            v.b = var * inv_n1;
-            v.c = damp_var32(var, d);
-        } else {
-            const double om = d.omega;
-            v.a = om * m1;
-            v.b = d.omega2 * var * inv_n1;  // (Omega Omega) var / (n_h - 1), left to right
-            v.c = damp(om * sqrt(var), d.beta);
-        }
+        v.a = m1;
+        v.b = var * inv_n1;
+        v.c = d.prec == VP_FP32 ? damp_var32(var, d) : damp(d.omega * sqrt(var), d.beta);
         d.dh[h] = v.c;
     } else if (mode == 1) {
         v.c = damp(d.dh[h], d.beta);
@@ -375,12 +363,17 @@ __global__ void __launch_bounds__(256, 4)
 __device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode,
                                 const EstPre &pre) {
     State *st = d.st;
-    if (d.prec == VP_FP32) {  // (the FP32 path's terms leave Omega and Omega^2 to the totals)
-        I *= d.omega;
-        V *= d.omega2;
-    }
+    I *= d.omega;  // (the per-hypercube terms leave Omega and Omega^2 to the totals)
+    V *= d.omega2;
     st->sum_d = Sd;
     st->inv_sum_d = Sd > 0.0 ? 1.0 / Sd : 0.0;
+    {
+        const double c = d.n_ev_d * st->inv_sum_d;
+        const bool normal = Sd >= 2.2250738585072014e-308 && c >= 2.2250738585072014e-308 &&
+                            c <= 1.7976931348623157e308;
+        st->alloc_c = normal ? c : 0.0;
+        st->alloc_dmin = 4.4501477170144028e-308 / d.n_ev_d;  // 2^-1021 / N_ev
+    }
     if (mode == 0) {
         const uint32_t tt = pre.t;
         if (tt < (uint32_t)d.hist_cap) {
@@ -474,27 +467,52 @@ __device__ __forceinline__ bool finite_bits(double x) {
 
 // n_h of one hypercube (§3 Eq. nh with the library's reading): max(2,
 // floor(N_ev d_h / sum d)), or floor(.) + 2; the equal split when sum d = 0 or
-// on the first allocation.  The quotient is the IEEE one, (N_ev d_h) then / sum d.
-__device__ __forceinline__ uint32_t alloc_one(const Desc &d, double dh, double n_ev_d,
-                                              double sum_d, double inv_sum, int initial) {
+// on the first allocation.  The quotient is the IEEE one, (N_ev d_h) then
+// / sum d.  One FP64 product decides almost every hypercube: q ~ d_h c with
+// c = N_ev / sum d (within a few ulp of the IEEE quotient), and only a q within
+// 2^-40 q of an integer takes the exact quotient; where N_ev d_h would not be
+// a normal number, or c is unavailable (st.alloc_c = 0), the exact quotient
+// is taken directly.
+struct AllocK {
+    double n_ev_d, sum_d, c, dmin;
+};
+
+__device__ __forceinline__ uint32_t alloc_one(const Desc &d, double dh, const AllocK &K,
+                                              int initial) {
     uint64_t iq;
-    if (__double_as_longlong(sum_d) > 0ll) {  // sum d > 0 (sum_d is finite here)
-        const double num = __dmul_rn(n_ev_d, dh);
-        FloorBits f = floor_bits(num * inv_sum);
-        iq = f.iq;
-        // (a zero numerator is exact; below 2 - tol the max(2, .) decides)
-        const uint64_t qb = (uint64_t)__double_as_longlong(num * inv_sum);
-        const bool above = qb > 0x3FF8000000000000ull;  // q > 1.5
-        if ((uint64_t)__double_as_longlong(num) != 0ull && (d.plus2 || above) && f.near) {
-            f = floor_bits(__ddiv_rn(num, sum_d));
+    if (__double_as_longlong(K.sum_d) > 0ll) {  // sum d > 0 (sum_d is finite here)
+        if ((uint64_t)__double_as_longlong(dh) == 0ull) {
+            iq = 0ull;  // (a zero numerator is exact)
+        } else if ((uint64_t)__double_as_longlong(dh) >= (uint64_t)__double_as_longlong(K.dmin) &&
+                   (uint64_t)__double_as_longlong(K.c) != 0ull) {  // (integer compares: d_h, c >= 0)
+            const double q = dh * K.c;
+            FloorBits f = floor_bits(q);
+            iq = f.iq;
+            // (below 2 - tol the max(2, .) decides)
+            const bool above = (uint64_t)__double_as_longlong(q) > 0x3FF8000000000000ull;  // q > 1.5
+            if ((d.plus2 || above) && f.near) {
+                f = floor_bits(__ddiv_rn(__dmul_rn(K.n_ev_d, dh), K.sum_d));
+                iq = f.iq + (f.tie ? 1ull : 0ull);
+            }
+        } else {
+            const FloorBits f = floor_bits(__ddiv_rn(__dmul_rn(K.n_ev_d, dh), K.sum_d));
             iq = f.iq + (f.tie ? 1ull : 0ull);
         }
     } else {
-        const FloorBits f = floor_bits(__ddiv_rn(n_ev_d, (double)d.n_hc));
+        const FloorBits f = floor_bits(__ddiv_rn(K.n_ev_d, (double)d.n_hc));
         iq = f.iq + (f.tie ? 1ull : 0ull);
     }
     if (d.plus2 && !initial) return (uint32_t)iq + 2u;
     return iq > 2ull ? (uint32_t)iq : 2u;
+}
+
+__device__ __forceinline__ AllocK alloc_consts(const Desc &d) {
+    AllocK K;
+    K.n_ev_d = d.n_ev_d;
+    K.sum_d = d.st->sum_d;
+    K.c = d.st->alloc_c;
+    K.dmin = d.st->alloc_dmin;
+    return K;
 }
 
 // Exclusive scan of one value per thread over a CTA of 256 threads, in 32-bit
@@ -562,14 +580,14 @@ __global__ void __launch_bounds__(kSubH, 8) k_alloc(const Desc *desc, const uint
     const Desc &d = desc[b];
     const uint32_t sub = (tb - tree_base[b]) * kSub + blockIdx.x % kSub;
     const uint64_t h = (uint64_t)sub * kSubH + threadIdx.x;
-    const double sum_d = d.st->sum_d;
-    if (!finite_bits(sum_d)) {
+    const AllocK K = alloc_consts(d);
+    if (!finite_bits(K.sum_d)) {
         if (threadIdx.x == 0 && sub == 0) d.st->status |= kStatusNonFinite;
         return;
     }
     uint32_t n = 0;
     if (h < d.n_hc) {
-        n = alloc_one(d, d.dh[h], d.n_ev_d, sum_d, d.st->inv_sum_d, initial);
+        n = alloc_one(d, d.dh[h], K, initial);
         d.n_h[h] = n;
     }
     const uint32_t tot = cta_sum32(n, s_w);
@@ -660,45 +678,49 @@ __device__ __forceinline__ void load4_dh(const Desc &d, uint64_t h0, bool full, 
 
 __global__ void __launch_bounds__(kSubH, 4) k_alloc_wide(const Desc *desc,
                                                          const uint32_t *tree_base, int n_int,
-                                                         int initial) {
+                                                         int initial, int group) {
     __shared__ uint32_t s_w[8];
     __shared__ bool s_last;
     __shared__ uint32_t s_carry;
     pdl_wait();
     pdl_trigger();
+    // blocks k0 .. k0 + group - 1 of one integral (group > 1 only for one integral)
     const uint32_t tb = blockIdx.x;
-    const int b = owner_of(tree_base, n_int, tb);
+    const int b = group > 1 ? 0 : owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
-    const uint32_t k = tb - tree_base[b];
-    const double sum_d = d.st->sum_d;
-    if (!finite_bits(sum_d)) {
-        if (threadIdx.x == 0 && k == 0) d.st->status |= kStatusNonFinite;
+    const uint32_t k0 = group > 1 ? tb * (uint32_t)group : tb - tree_base[b];
+    const uint32_t k1 = min(k0 + (uint32_t)group, d.n_tree);
+    const AllocK K = alloc_consts(d);
+    if (!finite_bits(K.sum_d)) {
+        if (threadIdx.x == 0 && k0 == 0) d.st->status |= kStatusNonFinite;
         return;
     }
-    const double inv_sum = d.st->inv_sum_d;
-    const uint64_t h0 = (uint64_t)k * kTreeBlock + 4u * threadIdx.x;
-    const bool full = h0 + 4 <= d.n_hc;
-    double dh[4];
-    load4_dh(d, h0, full, dh);
-    uint32_t n[4], own = 0u;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint64_t h0 = (uint64_t)k * kTreeBlock + 4u * threadIdx.x;
+        const bool full = h0 + 4 <= d.n_hc;
+        double dh[4];
+        load4_dh(d, h0, full, dh);
+        uint32_t n[4], own = 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        n[q] = h0 + q < d.n_hc ? alloc_one(d, dh[q], d.n_ev_d, sum_d, inv_sum, initial) : 0u;
-        own += n[q];
-    }
-    if (full) {
-        *(uint4 *)(d.n_h + h0) = make_uint4(n[0], n[1], n[2], n[3]);
-    } else {
+        for (int q = 0; q < 4; ++q) {
+            n[q] = h0 + q < d.n_hc ? alloc_one(d, dh[q], K, initial) : 0u;
+            own += n[q];
+        }
+        if (full) {
+            *(uint4 *)(d.n_h + h0) = make_uint4(n[0], n[1], n[2], n[3]);
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (h0 + q < d.n_hc) d.n_h[h0 + q] = n[q];
+            for (int q = 0; q < 4; ++q)
+                if (h0 + q < d.n_hc) d.n_h[h0 + q] = n[q];
+        }
+        const uint32_t tot = cta_sum32(own, s_w);
+        if (threadIdx.x == 0) d.bsum[k] = tot;
     }
-    const uint32_t tot = cta_sum32(own, s_w);
     if (threadIdx.x == 0) {
-        d.bsum[k] = tot;
         __threadfence();
         const uint32_t ticket = atomicAdd(&d.st->done_alloc, 1u);
-        s_last = (ticket == d.n_tree - 1);
+        const uint32_t n_cta = (d.n_tree + (uint32_t)group - 1u) / (uint32_t)group;
+        s_last = (ticket == n_cta - 1);
         s_carry = 0u;
     }
     __syncthreads();
@@ -707,42 +729,46 @@ __global__ void __launch_bounds__(kSubH, 4) k_alloc_wide(const Desc *desc,
 }
 
 __global__ void __launch_bounds__(kSubH, 4) k_offsets_wide(const Desc *desc,
-                                                           const uint32_t *tree_base, int n_int) {
+                                                           const uint32_t *tree_base, int n_int,
+                                                           int group) {
     __shared__ uint32_t s_w[8];
     pdl_wait();
     const uint32_t tb = blockIdx.x;
-    const int b = owner_of(tree_base, n_int, tb);
+    const int b = group > 1 ? 0 : owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
     if (!finite_bits(d.st->sum_d)) return;
-    const uint32_t k = tb - tree_base[b];
-    const uint64_t h0 = (uint64_t)k * kTreeBlock + 4u * threadIdx.x;
-    const bool full = h0 + 4 <= d.n_hc;
-    uint32_t n[4];
-    if (full) {
-        const uint4 v = __ldcs((const uint4 *)(d.n_h + h0));
-        n[0] = v.x; n[1] = v.y; n[2] = v.z; n[3] = v.w;
-    } else {
+    const uint32_t k0 = group > 1 ? tb * (uint32_t)group : tb - tree_base[b];
+    const uint32_t k1 = min(k0 + (uint32_t)group, d.n_tree);
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint64_t h0 = (uint64_t)k * kTreeBlock + 4u * threadIdx.x;
+        const bool full = h0 + 4 <= d.n_hc;
+        uint32_t n[4];
+        if (full) {
+            const uint4 v = __ldcs((const uint4 *)(d.n_h + h0));
+            n[0] = v.x; n[1] = v.y; n[2] = v.z; n[3] = v.w;
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) n[q] = h0 + q < d.n_hc ? d.n_h[h0 + q] : 0u;
-    }
-    const unsigned long long blk = d.bsum[k];
-    uint32_t e[4], own = 0u;
+            for (int q = 0; q < 4; ++q) n[q] = h0 + q < d.n_hc ? d.n_h[h0 + q] : 0u;
+        }
+        const unsigned long long blk = d.bsum[k];
+        uint32_t e[4], own = 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        e[q] = own;
-        own += n[q];
-    }
-    uint32_t tot;
-    const uint32_t ex = cta_exclusive_scan32(own, s_w, &tot);
-    const unsigned long long base = blk + ex;
-    if (full) {
-        ulonglong2 *o = (ulonglong2 *)(d.off + h0);
-        o[0] = make_ulonglong2(base + e[0], base + e[1]);
-        o[1] = make_ulonglong2(base + e[2], base + e[3]);
-    } else {
+        for (int q = 0; q < 4; ++q) {
+            e[q] = own;
+            own += n[q];
+        }
+        uint32_t tot;
+        const uint32_t ex = cta_exclusive_scan32(own, s_w, &tot);
+        const unsigned long long base = blk + ex;
+        if (full) {
+            ulonglong2 *o = (ulonglong2 *)(d.off + h0);
+            o[0] = make_ulonglong2(base + e[0], base + e[1]);
+            o[1] = make_ulonglong2(base + e[2], base + e[3]);
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (h0 + q < d.n_hc) d.off[h0 + q] = base + e[q];
+            for (int q = 0; q < 4; ++q)
+                if (h0 + q < d.n_hc) d.off[h0 + q] = base + e[q];
+        }
     }
 }
 
@@ -1097,7 +1123,7 @@ cudaError_t launch_chunks(const Desc *desc, const uint32_t *members, int n_group
 // one CTA per block, four hypercubes per thread, instead of several CTAs per
 // block: with fewer blocks the one-CTA form leaves SMs (and their FP64 units)
 // idle, with more it keeps more loads in flight per thread.
-constexpr uint32_t kWideBlocks = 512;
+constexpr uint32_t kWideBlocks = 512, kGroupBlocks = 4096;
 
 cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_int,
                             uint32_t n_blocks, int mode, cudaStream_t s) {
@@ -1111,10 +1137,15 @@ cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_i
 cudaError_t launch_alloc(const Desc *desc, const uint32_t *tree_base, int n_int,
                          uint32_t n_blocks, cudaStream_t s, int initial) {
     if (n_blocks >= kWideBlocks) {
-        cudaError_t e = launch_pdl(k_alloc_wide, dim3(n_blocks), dim3(kSubH), s, desc, tree_base,
-                                   n_int, initial);
+        // one integral of many blocks: four blocks per CTA (the per-CTA sum,
+        // fence and ticket amortised over 4096 hypercubes)
+        const int group = (n_int == 1 && n_blocks >= kGroupBlocks) ? 4 : 1;
+        const uint32_t n_cta = (n_blocks + (uint32_t)group - 1u) / (uint32_t)group;
+        cudaError_t e = launch_pdl(k_alloc_wide, dim3(n_cta), dim3(kSubH), s, desc, tree_base,
+                                   n_int, initial, group);
         if (e != cudaSuccess) return e;
-        return launch_pdl(k_offsets_wide, dim3(n_blocks), dim3(kSubH), s, desc, tree_base, n_int);
+        return launch_pdl(k_offsets_wide, dim3(n_cta), dim3(kSubH), s, desc, tree_base, n_int,
+                          group);
     }
     cudaError_t e = launch_pdl(k_alloc, dim3(n_blocks * kSub), dim3(kSubH), s, desc, tree_base,
                                n_int, initial);

@@ -52,6 +52,10 @@ struct State {
     double zsum;          // sum of I_j over iterations with var_j = 0 (exact)
     uint32_t n_zero;      // number of those
     uint32_t done;        // kDone* bits once the stop rule has fired
+    // the allocation's fast quotient q ~ d_h alloc_c (alloc_c = N_ev / sum d;
+    // 0 where 1 / sum d or the product leaves the normal range), taken for
+    // d_h >= alloc_dmin (then N_ev d_h is a normal number)
+    double alloc_c, alloc_dmin;
 };
 
 // Bits of State::done and of the server's per-slot flag.

@@ -120,6 +120,7 @@ _SIGS = {
     "vp_refine_from_hist": [_P, _P, _P, _P],
     "vp_eval_samples": [_P, ctypes.c_int64, _P, _P, ctypes.c_uint32, _P, _P, _P, _P],
     "vp_last_sample_ms": [_P, ctypes.POINTER(ctypes.c_float)],
+    "vp_shared_atomic_rate": [ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
     "vp_alloc_static": [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P, _P, _P],
     "vp_result_unweighted": [_P, ctypes.c_int, ctypes.POINTER(vp_result_t)],
     "vp_set_damping": [_P, ctypes.c_double, ctypes.c_double],
@@ -220,6 +221,15 @@ def use_torch_allocator():
     a, f = ALLOC_FN(_alloc), FREE_FN(_free)
     _keep[:] = [a, f]
     check(lib().vp_set_allocator(a, f, None))
+
+
+def shared_atomic_rate(f32=False):
+    """Shared-memory atomic adds per second on the current device in the
+    sampling kernel's histogram pattern (vp_shared_atomic_rate): 32-bit integer
+    adds (the counts) or, with f32, FP32 adds (the sums)."""
+    r = ctypes.c_double()
+    check(lib().vp_shared_atomic_rate(1 if f32 else 0, ctypes.byref(r)))
+    return r.value
 
 
 class Integrator:

@@ -155,9 +155,15 @@ def test_samples_fp32_within_tolerance(kind, dim):
 # a7: integer allocation, bit-exact
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("dim,n_st", [(1, 1), (2, 4), (4, 7), (1, 1025), (8, 4), (20, 2),
-                                      (8, 8)])
+                                      (8, 8), (14, 3)])
 @pytest.mark.parametrize("plus2", [False, True])
 def test_alloc_from_dh_bit_exact(dim, n_st, plus2):
+    """§3 Eq. (nh) from the same d_h: n_h and offsets bit-exact with the
+    oracle, over d_h spanning 40 decades with zeros, all zeros, subnormal d_h
+    (their sum subnormal: the exact quotient throughout) and a mix of normal
+    and subnormal d_h (N_ev d_h below the normal range: the exact quotient for
+    those); sizes from one hypercube to 3^14 (4,671 blocks of 1024, the last
+    ragged: four blocks per CTA)."""
     rng = np.random.default_rng(dim * 1000 + n_st + plus2)
     prob = inputs.Problem("alloc", dim, inputs.GAUSS,
                           inputs.gauss_blob([1.0], [0.2], [np.full(dim, 0.5)]), np.zeros(dim),
@@ -165,11 +171,16 @@ def test_alloc_from_dh_bit_exact(dim, n_st, plus2):
                           n_st=n_st, plus2=plus2)
     g = gpu_of(prob)
     n_hc = n_st ** dim
-    for trial in range(3):
+    for trial in range(5):
         d = rng.exponential(size=n_hc) * 10.0 ** rng.uniform(-20, 20, size=n_hc)
         d[rng.uniform(size=n_hc) < 0.25] = 0.0
         if trial == 2:
             d[:] = 0.0
+        elif trial == 3:
+            d = rng.exponential(size=n_hc) * 1e-316
+        elif trial == 4:
+            d = np.where(rng.uniform(size=n_hc) < 0.5, rng.exponential(size=n_hc) * 1e-3,
+                         rng.exponential(size=n_hc) * 1e-318)
         g.alloc_from_dh(d)
         n_h, off = g.alloc()
         n_ref, off_ref = oracle.allocate(prob.n_ev, d, plus2=plus2)
@@ -684,3 +695,13 @@ def test_fp32_posterior_below_the_fp32_range():
     assert np.all(np.abs(np.sqrt(Vg[2:]) / np.sqrt(Vo[2:]) - 1) < 0.5)
     r, ro = g.result(discard=3), o.result(discard=3)
     assert abs(r["mean"] - ro["mean"]) <= 2 * np.hypot(r["sdev"], ro["sdev"])
+
+
+@pytest.mark.gpu
+def test_shared_atomic_rate_probe():
+    """The measurement aid behind the bench's atomic bound returns a rate for
+    both kinds of add, 32-bit integer above FP32 or near it."""
+    from paper_2009_05112_gb300 import vegasp
+    u32, f32 = vegasp.shared_atomic_rate(False), vegasp.shared_atomic_rate(True)
+    assert u32 > 1e10 and f32 > 1e10
+    assert f32 <= 1.5 * u32
