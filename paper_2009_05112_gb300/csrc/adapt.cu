@@ -154,6 +154,9 @@ __device__ void finish_estimate(const Desc &d, double I, double V, double Sd, in
                                 const EstPre &pre);
 __device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, int mode, const EstPre &pre,
                                     double *red, bool *s_last);
+__device__ __forceinline__ void block_levels(const Desc &d, uint32_t k, double *red);
+__device__ __forceinline__ void estimate_last_cta(const Desc &d, uint32_t n_cta, int mode,
+                                                  const EstPre &pre, double *red, bool *s_last);
 
 struct EstShared {
     double recv2[3][256];  // level 256: CTA 1's terms, received by CTA 0
@@ -267,11 +270,10 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256, 4)
 // The rest of a block's fixed-order tree, one CTA of 256 threads: red[c][t]
 // (red = 3 x 256 doubles in shared memory) holds the sum of terms t, t + 256,
 // t + 512, t + 768 of series c (the first two halving levels); then the
-// levels 128 .. 1, the block sum to part[3 k + c], and in the last block of
-// the integral the block sums in the fixed tree order and the iteration's
-// bookkeeping.
-__device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, int mode, const EstPre &pre,
-                                    double *red, bool *s_last) {
+// levels 128 .. 1 and the block sum to part[3 k + c] (block_levels); then,
+// once per CTA, the ticket and in the last CTA of the integral the block sums
+// in the fixed tree order and the iteration's bookkeeping (estimate_last_cta).
+__device__ __forceinline__ void block_levels(const Desc &d, uint32_t k, double *red) {
     const int t = threadIdx.x;
     double *r0 = red, *r1 = red + 256, *r2 = red + 512;
     __syncthreads();
@@ -285,26 +287,27 @@ __device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, i
     }
     // levels 32 .. 1: one warp per sum, the three in parallel (a chain of
     // dependent FP64 additions is slow on this part)
-    {
-        const int w = t >> 5, l = t & 31;
-        if (w < 3) {
-            const double *r = w == 0 ? r0 : (w == 1 ? r1 : r2);
-            double x = __dadd_rn(r[l], r[l + 32]);
-            for (int s = 16; s >= 1; s >>= 1) x = __dadd_rn(x, __shfl_down_sync(0xffffffffu, x, s));
-            if (l == 0) {
-                d.part[3 * k + w] = x;
-                __threadfence();
-            }
-        }
+    const int w = t >> 5, l = t & 31;
+    if (w < 3) {
+        const double *r = w == 0 ? r0 : (w == 1 ? r1 : r2);
+        double x = __dadd_rn(r[l], r[l + 32]);
+        for (int s = 16; s >= 1; s >>= 1) x = __dadd_rn(x, __shfl_down_sync(0xffffffffu, x, s));
+        if (l == 0) d.part[3 * k + w] = x;
     }
+}
+
+__device__ __forceinline__ void estimate_last_cta(const Desc &d, uint32_t n_cta, int mode,
+                                                  const EstPre &pre, double *red, bool *s_last) {
+    const int t = threadIdx.x;
+    if (t < 96 && (t & 31) == 0) __threadfence();  // (the writers of part[]: lane 0 of warps 0-2)
     __syncthreads();
     if (t == 0) {
         const uint32_t ticket = atomicAdd(&d.st->done_est, 1u);
-        *s_last = (ticket == d.n_tree - 1);
+        *s_last = (ticket == n_cta - 1);
     }
     __syncthreads();
     if (!*s_last) return;
-    // last block of this integral: the block sums in the fixed tree order
+    // last CTA of this integral: the block sums in the fixed tree order
     __threadfence();
     __syncthreads();
     double tot[3];
@@ -314,21 +317,29 @@ __device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, i
     finish_estimate(d, tot[0], tot[1], tot[2], mode, pre);
 }
 
+__device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, int mode, const EstPre &pre,
+                                    double *red, bool *s_last) {
+    block_levels(d, k, red);
+    estimate_last_cta(d, d.n_tree, mode, pre, red, s_last);
+}
+
 // k_estimate for many blocks (large N_h): one CTA of 256 threads per block of
 // 1024 hypercubes, each thread four of them (t, t + 256, t + 512, t + 768),
 // so that more loads are in flight per thread; the first two halving levels
 // are the thread's own (t + 512 joins t, t + 768 joins t + 256, then t + 256
 // joins t), the same tree as the cluster form's.
 __global__ void __launch_bounds__(256, 4)
-    k_estimate_wide(const Desc *desc, const uint32_t *tree_base, int n_int, int mode) {
+    k_estimate_wide(const Desc *desc, const uint32_t *tree_base, int n_int, int mode, int group) {
     __shared__ double red[3 * 256];
     __shared__ bool s_last;
     pdl_wait();
     pdl_trigger();
+    // blocks k0 .. k0 + group - 1 of one integral (group > 1 only for one integral)
     const uint32_t tb = blockIdx.x;
-    const int b = owner_of(tree_base, n_int, tb);
+    const int b = group > 1 ? 0 : owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
-    const uint32_t k = tb - tree_base[b];
+    const uint32_t k0 = group > 1 ? tb * (uint32_t)group : tb - tree_base[b];
+    const uint32_t k1 = min(k0 + (uint32_t)group, d.n_tree);
     const int t = threadIdx.x;
     const uint32_t par = d.st->t & 1u;
     EstPre pre = {0u, 0u, 0ull, 0ull};
@@ -338,23 +349,29 @@ __global__ void __launch_bounds__(256, 4)
         pre.n_samples = d.st->n_samples;
         pre.n_eval_total = d.st->n_eval_total;
     }
-    const uint64_t h0 = (uint64_t)k * kTreeBlock + t;
-    const D3 v0 = hcube_terms(d, h0, mode, par), v1 = hcube_terms(d, h0 + 256, mode, par);
-    const D3 v2 = hcube_terms(d, h0 + 512, mode, par), v3 = hcube_terms(d, h0 + 768, mode, par);
     if (mode == 0) {  // clear the other histogram buffer, spread over this integral's CTAs
         const int bins = d.dim * d.n_g;
         double *hs = d.hsum + (size_t)(par ^ 1u) * bins;
         uint32_t *hc = d.hcnt + (size_t)(par ^ 1u) * bins;
-        const int stride = (int)d.n_tree * 256;
-        for (int i = (int)k * 256 + t; i < bins; i += stride) {
+        const uint32_t n_cta = (d.n_tree + (uint32_t)group - 1u) / (uint32_t)group;
+        const int stride = (int)n_cta * 256;
+        for (int i = (int)(k0 / (uint32_t)group) * 256 + t; i < bins; i += stride) {
             hs[i] = 0.0;
             hc[i] = 0u;
         }
     }
-    red[t] = __dadd_rn(__dadd_rn(v0.a, v2.a), __dadd_rn(v1.a, v3.a));
-    red[256 + t] = __dadd_rn(__dadd_rn(v0.b, v2.b), __dadd_rn(v1.b, v3.b));
-    red[512 + t] = __dadd_rn(__dadd_rn(v0.c, v2.c), __dadd_rn(v1.c, v3.c));
-    estimate_block_tail(d, k, mode, pre, red, &s_last);
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint64_t h0 = (uint64_t)k * kTreeBlock + t;
+        const D3 v0 = hcube_terms(d, h0, mode, par), v1 = hcube_terms(d, h0 + 256, mode, par);
+        const D3 v2 = hcube_terms(d, h0 + 512, mode, par), v3 = hcube_terms(d, h0 + 768, mode, par);
+        __syncthreads();  // (the previous block's last reads of red are done)
+        red[t] = __dadd_rn(__dadd_rn(v0.a, v2.a), __dadd_rn(v1.a, v3.a));
+        red[256 + t] = __dadd_rn(__dadd_rn(v0.b, v2.b), __dadd_rn(v1.b, v3.b));
+        red[512 + t] = __dadd_rn(__dadd_rn(v0.c, v2.c), __dadd_rn(v1.c, v3.c));
+        block_levels(d, k, red);
+    }
+    estimate_last_cta(d, (d.n_tree + (uint32_t)group - 1u) / (uint32_t)group, mode, pre, red,
+                      &s_last);
 }
 
 // The iteration's totals I_j, sigma_j^2 and sum d recorded in the state (one
@@ -1127,9 +1144,14 @@ constexpr uint32_t kWideBlocks = 512, kGroupBlocks = 4096;
 
 cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_int,
                             uint32_t n_blocks, int mode, cudaStream_t s) {
-    if (n_blocks >= kWideBlocks)
-        return launch_pdl(k_estimate_wide, dim3(n_blocks), dim3(256), s, desc, tree_base, n_int,
-                          mode);
+    if (n_blocks >= kWideBlocks) {
+        // one integral of many blocks: four blocks per CTA (the per-CTA fence
+        // and ticket amortised over 4096 hypercubes)
+        const int group = (n_int == 1 && n_blocks >= kGroupBlocks) ? 4 : 1;
+        const uint32_t n_cta = (n_blocks + (uint32_t)group - 1u) / (uint32_t)group;
+        return launch_pdl(k_estimate_wide, dim3(n_cta), dim3(256), s, desc, tree_base, n_int,
+                          mode, group);
+    }
     return launch_pdl(k_estimate, dim3(n_blocks * kEstCtas), dim3(256), s, desc, tree_base, n_int,
                       mode);
 }

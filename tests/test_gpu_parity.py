@@ -258,14 +258,16 @@ def _dh_from_iteration(prec, beta, n_ev):
     n_used, _ = g.alloc()
     s1, s2 = g.moments()
     d_gpu, sd_gpu = g.dh()
+    I_h, V_h = g.history()
     g.adapt()
     n_next, off_next = g.alloc()
     g.close()
-    return prob, s1, s2, n_used, d_gpu, sd_gpu, n_next, off_next
+    return prob, s1, s2, n_used, d_gpu, sd_gpu, n_next, off_next, I_h[-1], V_h[-1]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_dh_from_moments_within_bound(prec):
+@pytest.mark.parametrize("n_ev", [200_000, 25_000_000])
+def test_dh_from_moments_within_bound(prec, n_ev):
     """§3 step 2 and Eq. (dh) inside a real iteration: the library's d_h from
     its own moments against the oracle's sigma_h^beta from the same moments.
     FP64 path: within 4e-15 relative where the variance is not a cancellation
@@ -273,10 +275,19 @@ def test_dh_from_moments_within_bound(prec):
     the FP32 log2/exp2 units): within 1e-6 relative.  sum d is bit-exact with
     the oracle's fixed-order sum of the library's d_h; the next allocation is
     bit-exact from the library's d_h, and differs from the oracle's own (from
-    its own d_h) in a bounded fraction of the hypercubes, by one sample."""
-    prob, s1, s2, n_used, d_gpu, sd_gpu, n_next, off_next = _dh_from_iteration(prec, 0.75,
-                                                                                200_000)
+    its own d_h) in a bounded fraction of the hypercubes, by one sample.  The
+    iteration's I_j and sigma_j^2 (§3 Eq. sumI) from the same moments agree
+    with the oracle's to FP64 rounding.  Sizes: 3^8 hypercubes, and 7^8
+    (5,630 blocks of 1024, the last ragged: four blocks per CTA)."""
+    (prob, s1, s2, n_used, d_gpu, sd_gpu, n_next, off_next, I_gpu,
+     V_gpu) = _dh_from_iteration(prec, 0.75, n_ev)
     omega = 1.0 / s1.size
+    I_ref, V_ref = oracle.estimate(omega, s1, s2, n_used)
+    assert abs(I_gpu - I_ref) <= 1e-12 * abs(I_ref)
+    # (each var_h a difference: a few ulp of its m2 per hypercube)
+    v_tol = 1e-12 * V_ref + 8.0 * np.finfo(float).eps * np.sum(
+        omega * omega * (s2 / n_used) / (n_used - 1.0))
+    assert abs(V_gpu - V_ref) <= v_tol
     d_ref = oracle.damp(0.75, oracle.sigma(omega, s1, s2, n_used))
     m1, m2 = s1 / n_used, s2 / n_used
     var = np.maximum(m2 - m1 * m1, 0.0)
