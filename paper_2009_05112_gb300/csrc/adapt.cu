@@ -115,9 +115,10 @@ __device__ __forceinline__ double damp_var32(double var, const Desc &d) {
     if (b == 0ull) return 0.0;
     int E = (int)((b >> 52) & 0x7ffu);
     if (E == 0x7ff) return var;  // inf or NaN propagates (the iteration is flagged)
-    if (E == 0) {  // subnormal: scale by 2^64 (exact)
-        b = (uint64_t)__double_as_longlong(var * 18446744073709551616.0);
-        E = (int)((b >> 52) & 0x7ffu) - 64;
+    if (E == 0) {  // subnormal: normalise the mantissa (integer operations)
+        const int sh = __clzll((long long)(b & ((1ull << 52) - 1ull))) - 11;
+        b = (b << sh) & ((1ull << 52) - 1ull);
+        E = 1 - sh;
     }
     E -= 1023;
     const float m = __uint_as_float(0x3f800000u | (uint32_t)((b >> 29) & 0x7fffffu));  // [1, 2)
@@ -164,6 +165,13 @@ struct EstShared {
     double red[3][256];
 };
 
+// 1/n for n beyond the table (rare: a call, so that none of its FP64 work is
+// hoisted into the common path)
+__device__ __noinline__ double recip_u32(uint32_t n) { return 1.0 / u32_to_f64(n); }
+
+// (PREC: -1 the descriptor's precision at run time, else VP_FP64 / VP_FP32
+// for a set whose integrals all take that path: one path compiled)
+template <int PREC = -1>
 __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, uint32_t par) {
     D3 v = {0.0, 0.0, 0.0};
     if (h >= d.n_hc) return v;
@@ -171,9 +179,9 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
         // FP64 is scarce on this part: reciprocals of the (small, integer)
         // n_h come from a table; one square root for sigma_h
         const uint32_t nh = d.n_h[h];
-        const double inv_n = nh < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh) : 1.0 / (double)nh;
+        const double inv_n = nh < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh) : recip_u32(nh);
         const double inv_n1 =
-            nh - 1 < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh - 1) : 1.0 / (double)(nh - 1);
+            nh - 1 < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh - 1) : recip_u32(nh - 1);
         const uint64_t ph = (uint64_t)par * d.n_hc + h;
         const double s1 = d.s1[ph], s2 = d.s2[ph];
         // the other buffer collects the next iteration's sums
@@ -184,14 +192,15 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
         // (S2 - S1 m1) / n_h, one fused multiply-add and one product, and
         // Omega, Omega^2 applied to the two totals (finish_estimate)
         const double m1 = s1 * inv_n;
-        double var = fma(-s1, m1, s2) * inv_n;
+        double var = __fma_rn(-s1, m1, s2) * inv_n;
         {  // a rounding-negative variance (or -0) is zero; a NaN stays NaN
             const long long vb = __double_as_longlong(var);
             if (vb < 0ll && (vb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) var = 0.0;
         }
         v.a = m1;
         v.b = var * inv_n1;
-        v.c = d.prec == VP_FP32 ? damp_var32(var, d) : damp(d.omega * sqrt(var), d.beta);
+        const bool fp32 = PREC < 0 ? d.prec == VP_FP32 : PREC == VP_FP32;
+        v.c = fp32 ? damp_var32(var, d) : damp(d.omega * sqrt(var), d.beta);
         d.dh[h] = v.c;
     } else if (mode == 1) {
         v.c = damp(d.dh[h], d.beta);
@@ -328,6 +337,7 @@ __device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, i
 // so that more loads are in flight per thread; the first two halving levels
 // are the thread's own (t + 512 joins t, t + 768 joins t + 256, then t + 256
 // joins t), the same tree as the cluster form's.
+template <int PREC>
 __global__ void __launch_bounds__(256, 4)
     k_estimate_wide(const Desc *desc, const uint32_t *tree_base, int n_int, int mode, int group) {
     __shared__ double red[3 * 256];
@@ -362,8 +372,10 @@ __global__ void __launch_bounds__(256, 4)
     }
     for (uint32_t k = k0; k < k1; ++k) {
         const uint64_t h0 = (uint64_t)k * kTreeBlock + t;
-        const D3 v0 = hcube_terms(d, h0, mode, par), v1 = hcube_terms(d, h0 + 256, mode, par);
-        const D3 v2 = hcube_terms(d, h0 + 512, mode, par), v3 = hcube_terms(d, h0 + 768, mode, par);
+        const D3 v0 = hcube_terms<PREC>(d, h0, mode, par);
+        const D3 v1 = hcube_terms<PREC>(d, h0 + 256, mode, par);
+        const D3 v2 = hcube_terms<PREC>(d, h0 + 512, mode, par);
+        const D3 v3 = hcube_terms<PREC>(d, h0 + 768, mode, par);
         __syncthreads();  // (the previous block's last reads of red are done)
         red[t] = __dadd_rn(__dadd_rn(v0.a, v2.a), __dadd_rn(v1.a, v3.a));
         red[256 + t] = __dadd_rn(__dadd_rn(v0.b, v2.b), __dadd_rn(v1.b, v3.b));
@@ -1143,13 +1155,19 @@ cudaError_t launch_chunks(const Desc *desc, const uint32_t *members, int n_group
 constexpr uint32_t kWideBlocks = 512, kGroupBlocks = 4096;
 
 cudaError_t launch_estimate(const Desc *desc, const uint32_t *tree_base, int n_int,
-                            uint32_t n_blocks, int mode, cudaStream_t s) {
+                            uint32_t n_blocks, int mode, cudaStream_t s, int prec) {
     if (n_blocks >= kWideBlocks) {
         // one integral of many blocks: four blocks per CTA (the per-CTA fence
         // and ticket amortised over 4096 hypercubes)
         const int group = (n_int == 1 && n_blocks >= kGroupBlocks) ? 4 : 1;
         const uint32_t n_cta = (n_blocks + (uint32_t)group - 1u) / (uint32_t)group;
-        return launch_pdl(k_estimate_wide, dim3(n_cta), dim3(256), s, desc, tree_base, n_int,
+        if (prec == VP_FP32)
+            return launch_pdl(k_estimate_wide<VP_FP32>, dim3(n_cta), dim3(256), s, desc,
+                              tree_base, n_int, mode, group);
+        if (prec == VP_FP64)
+            return launch_pdl(k_estimate_wide<VP_FP64>, dim3(n_cta), dim3(256), s, desc,
+                              tree_base, n_int, mode, group);
+        return launch_pdl(k_estimate_wide<-1>, dim3(n_cta), dim3(256), s, desc, tree_base, n_int,
                           mode, group);
     }
     return launch_pdl(k_estimate, dim3(n_blocks * kEstCtas), dim3(256), s, desc, tree_base, n_int,

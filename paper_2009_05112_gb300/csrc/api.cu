@@ -354,6 +354,14 @@ static void make_tab(const double *e, int n_g, float2 *tab) {
     for (int i = 0; i < n_g; ++i) tab[i] = make_float2((float)e[i], (float)(e[i + 1] - e[i]));
 }
 
+// The precision every integral of a set takes (VP_FP32 or VP_FP64), or -1.
+static int set_prec(const Set &s) {
+    int p = s.h_desc.empty() ? -1 : s.h_desc[0].prec;
+    for (const Desc &d : s.h_desc)
+        if (d.prec != p) return -1;
+    return p;
+}
+
 static vp_status plan_groups(Set &s) {
     // one launch group per (bucket, exactness, kind, precision); a merged set
     // (a batch) has one group per (kind, precision), served by the bucket of
@@ -1116,7 +1124,7 @@ static vp_status set_iterate(Set &s, cudaStream_t stream, bool refine_too = fals
         vp_status st = fork_refine(s, stream);
         if (st != VP_OK) return st;
     }
-    CU(launch_estimate(s.d_desc, s.d_tree_base, n, s.n_tree_total, 0, stream));
+    CU(launch_estimate(s.d_desc, s.d_tree_base, n, s.n_tree_total, 0, stream, set_prec(s)));
     s.last = stream;
     return VP_OK;
 }
@@ -1496,7 +1504,8 @@ extern "C" vp_status vp_estimate(vp_ctx *c, void *stream) {
     vp_status st = shard_check(c);
     if (st != VP_OK) return st;
     Set &s = c->set;
-    CU(launch_estimate(s.d_desc, s.d_tree_base, 1, s.n_tree_total, 0, (cudaStream_t)stream));
+    CU(launch_estimate(s.d_desc, s.d_tree_base, 1, s.n_tree_total, 0, (cudaStream_t)stream,
+                       set_prec(s)));
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
     if (cap != cudaStreamCaptureStatusActive) ++s.iters;
@@ -1955,7 +1964,7 @@ static vp_status alloc_from(vp_ctx *c, const double *v, int mode, cudaStream_t s
         if (!(v[h] >= 0.0) || !std::isfinite(v[h])) return fail(VP_EINVAL, "entries must be finite and >= 0");
     CU(cudaStreamSynchronize(s.last));
     CU(cudaMemcpyAsync(d.dh, v, d.n_hc * 8, cudaMemcpyHostToDevice, stream));
-    CU(launch_estimate(s.d_desc, s.d_tree_base, 1, s.n_tree_total, mode, stream));
+    CU(launch_estimate(s.d_desc, s.d_tree_base, 1, s.n_tree_total, mode, stream, set_prec(s)));
     CU(launch_alloc(s.d_desc, s.d_tree_base, 1, s.n_tree_total, stream, 0));
     CU(cudaStreamSynchronize(stream));
     s.last = stream;

@@ -27,7 +27,9 @@ struct NvtxRange {
 // kernel launchers (adapt.cu)
 cudaError_t launch_chunks(const Desc *, const uint32_t *, int, uint64_t *, uint32_t *, uint32_t,
                           cudaStream_t);
-cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);
+// (prec: VP_FP32 or VP_FP64 when every integral of the launch takes that path, else -1)
+cudaError_t launch_estimate(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t,
+                            int prec = -1);
 cudaError_t launch_estimate_multi(const Desc *, uint32_t, cudaStream_t);
 cudaError_t launch_alloc(const Desc *, const uint32_t *, int, uint32_t, cudaStream_t, int initial);
 cudaError_t launch_refine(const Desc *, const uint32_t *, int, uint32_t, int, cudaStream_t);

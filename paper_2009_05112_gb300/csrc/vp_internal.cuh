@@ -179,6 +179,16 @@ __device__ __forceinline__ double pow2d(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+// (double)n of a 32-bit unsigned integer from its bits with integer
+// operations only (exact; a conversion instruction would run on the FP64
+// pipe, a few operations per SM per clock on this part).
+__device__ __forceinline__ double u32_to_f64(uint32_t n) {
+    if (n == 0u) return 0.0;
+    const int e = 31 - __clz((int)n);
+    const uint64_t man = ((uint64_t)n << (52 - e)) & ((1ull << 52) - 1ull);
+    return __longlong_as_double((long long)(((uint64_t)(e + 1023) << 52) | man));
+}
+
 // (double)x 2^e built from the bits of x with integer operations only (FP64
 // instructions are scarce on this part, a few per SM per clock, so the FP32
 // path's values leave the kernels without them): exact whenever the result is
