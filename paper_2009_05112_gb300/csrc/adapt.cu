@@ -131,6 +131,38 @@ __device__ __forceinline__ double damp_var32(double var, const Desc &d) {
     return f2d_pow2(ex2_approx(y), (int)fl + d.lob_i);
 }
 
+// The same from t = n_h var and log2 n_h = L.x + L.y (a float pair from the
+// table): d_h = 2^(beta/2 (log2 t - log2 n_h) + beta log2 Omega), so that var
+// itself is never formed (one FP64 product less per hypercube).  The
+// integer parts of beta/2 log2 t and beta/2 log2 n_h go into the exponent
+// field, their fractions (whose difference is exact) through the exp2 unit.
+// t >= 0 and finite.
+__device__ __forceinline__ double damp_tn32(double t, float2 L, const Desc &d) {
+    if ((uint64_t)__double_as_longlong(d.beta) == 0ull) return 1.0;  // beta = 0: d = 1
+    uint64_t b = (uint64_t)__double_as_longlong(t);
+    if (b == 0ull) return 0.0;
+    int E = (int)((b >> 52) & 0x7ffu);
+    if (E == 0x7ff) return t;  // inf or NaN propagates (the iteration is flagged)
+    if (E == 0) {  // subnormal: normalise the mantissa (integer operations)
+        const int sh = __clzll((long long)(b & ((1ull << 52) - 1ull))) - 11;
+        b = (b << sh) & ((1ull << 52) - 1ull);
+        E = 1 - sh;
+    }
+    E -= 1023;
+    const float m = __uint_as_float(0x3f800000u | (uint32_t)((b >> 29) & 0x7fffffu));  // [1, 2)
+    const float Ef = (float)E;                            // exact
+    const float p = d.half_beta_hi * Ef;
+    const float err = fmaf(d.half_beta_hi, Ef, -p);       // p + err = hi E exactly
+    const float fl = floorf(p);
+    const float q = d.half_beta_hi * L.x;
+    const float qe = fmaf(d.half_beta_hi, L.x, -q);       // q + qe = hi L.x exactly
+    const float fq = floorf(q);
+    const float frac = (p - fl) - (q - fq);               // exact: both fractions on a 2^-21 grid
+    const float small = fmaf(d.half_beta_lo, Ef, -fmaf(d.half_beta_hi, L.y, d.half_beta_lo * L.x));
+    const float y = (frac + (err - qe)) + fmaf(d.half_beta_hi, lg2_approx(m), small) + d.lob_f;
+    return f2d_pow2(ex2_approx(y), (int)fl - (int)fq + d.lob_i);
+}
+
 // ---------------------------------------------------------------------------
 // k_estimate.  mode 0: from the moments (a6 + sigma_h + d_h), records the
 // iteration; mode 1: dh[] holds sigma_h, turn it into d_h and sum; mode 2:
@@ -176,31 +208,50 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
     D3 v = {0.0, 0.0, 0.0};
     if (h >= d.n_hc) return v;
     if (mode == 0) {
-        // FP64 is scarce on this part: reciprocals of the (small, integer)
-        // n_h come from a table; one square root for sigma_h
+        // (reciprocals of the small integer n_h come from the set's table, one
+        // 32-byte entry per n: 1/n, 1/(n (n-1)), log2 n)
         const uint32_t nh = d.n_h[h];
-        const double inv_n = nh < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh) : recip_u32(nh);
-        const double inv_n1 =
-            nh - 1 < (uint32_t)kInvTab ? __ldg(d.inv_tab + nh - 1) : recip_u32(nh - 1);
+        const bool in_tab = nh < (uint32_t)kInvTab;
+        double2 e01 = make_double2(0.0, 0.0);
+        float2 e2 = make_float2(0.0f, 0.0f);
+        if (in_tab) {
+            const double2 *e = (const double2 *)(d.inv_tab + 4 * (size_t)nh);
+            e01 = __ldg(e);
+            const double2 w = __ldg(e + 1);
+            e2 = make_float2(__uint_as_float((uint32_t)__double_as_longlong(w.x)),
+                             __uint_as_float((uint32_t)((uint64_t)__double_as_longlong(w.x) >> 32)));
+        }
+        const double inv_n = in_tab ? e01.x : recip_u32(nh);
         const uint64_t ph = (uint64_t)par * d.n_hc + h;
         const double s1 = d.s1[ph], s2 = d.s2[ph];
         // the other buffer collects the next iteration's sums
         const uint64_t qh = (uint64_t)(par ^ 1u) * d.n_hc + h;
         d.s1[qh] = 0.0;
         d.s2[qh] = 0.0;
-        // four FP64 operations (FP64 is scarce on this part): the variance as
-        // (S2 - S1 m1) / n_h, one fused multiply-add and one product, and
-        // Omega, Omega^2 applied to the two totals (finish_estimate)
+        // FP64 is scarce on this part: m1 = S1 / n_h, t = S2 - S1 m1 (one fused
+        // multiply-add; t = n_h var) and, on the FP32 path, var / (n_h - 1) as
+        // t / (n_h (n_h - 1)) from the table and d_h from t and log2 n_h: three
+        // FP64 operations (four beyond the table and on the FP64 path, which
+        // forms var = t / n_h); Omega and Omega^2 multiply the two totals
+        // (finish_estimate)
+        const bool fp32 = PREC < 0 ? d.prec == VP_FP32 : PREC == VP_FP32;
         const double m1 = s1 * inv_n;
-        double var = __fma_rn(-s1, m1, s2) * inv_n;
+        double t = __fma_rn(-s1, m1, s2);
         {  // a rounding-negative variance (or -0) is zero; a NaN stays NaN
-            const long long vb = __double_as_longlong(var);
-            if (vb < 0ll && (vb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) var = 0.0;
+            const long long tb = __double_as_longlong(t);
+            if (tb < 0ll && (tb & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) t = 0.0;
         }
         v.a = m1;
-        v.b = var * inv_n1;
-        const bool fp32 = PREC < 0 ? d.prec == VP_FP32 : PREC == VP_FP32;
-        v.c = fp32 ? damp_var32(var, d) : damp(d.omega * sqrt(var), d.beta);
+        if (fp32 && in_tab) {
+            v.b = t * e01.y;
+            v.c = damp_tn32(t, e2, d);
+        } else {
+            const double inv_n1 =
+                nh - 1 < (uint32_t)kInvTab ? __ldg(d.inv_tab + 4 * (size_t)(nh - 1)) : recip_u32(nh - 1);
+            const double var = t * inv_n;
+            v.b = var * inv_n1;
+            v.c = fp32 ? damp_var32(var, d) : damp(d.omega * sqrt(var), d.beta);
+        }
         d.dh[h] = v.c;
     } else if (mode == 1) {
         v.c = damp(d.dh[h], d.beta);

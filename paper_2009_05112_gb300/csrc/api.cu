@@ -546,8 +546,16 @@ void vp::damp_consts(Desc &d, double beta) {
 }
 
 void vp::inv_table(std::vector<double> &inv) {
-    inv.assign(kInvTab, 0.0);
-    for (int k = 1; k < kInvTab; ++k) inv[k] = 1.0 / (double)k;  // IEEE division on the host
+    inv.assign(kInvTabWords, 0.0);
+    for (int k = 1; k < kInvTab; ++k) {
+        double *e = inv.data() + 4 * k;
+        e[0] = 1.0 / (double)k;  // IEEE division on the host
+        if (k >= 2) e[1] = 1.0 / ((double)k * (double)(k - 1));  // (exact product)
+        const double L = std::log2((double)k);
+        float *l2 = (float *)(e + 2);
+        l2[0] = (float)L;
+        l2[1] = (float)(L - (double)l2[0]);
+    }
 }
 
 void vp::fill_desc(const Member &mb, const double *d_inv, Desc &d) {
@@ -671,7 +679,7 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
     const size_t axis_off = base;
     base = align256(base + (n + 1) * 4);
     const size_t inv_off = base;
-    base = align256(base + kInvTab * sizeof(double));
+    base = align256(base + kInvTabWords * sizeof(double));
     {
         vp_status pst = plan_groups(s);
         if (pst != VP_OK) return pst;
@@ -696,8 +704,8 @@ static vp_status set_create(Set &s, int n, const vp_params *ps, const vp_integra
     {
         std::vector<double> inv;
         inv_table(inv);
-        CU(cudaMemcpyAsync((void *)d_inv, inv.data(), kInvTab * sizeof(double), cudaMemcpyHostToDevice,
-                           stream));
+        CU(cudaMemcpyAsync((void *)d_inv, inv.data(), kInvTabWords * sizeof(double),
+                           cudaMemcpyHostToDevice, stream));
         CU(cudaStreamSynchronize(stream));
     }
     for (size_t g = 0; g < s.groups.size(); ++g) {

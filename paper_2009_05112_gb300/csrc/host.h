@@ -144,7 +144,8 @@ void fill_desc(const Member &mb, const double *d_inv, Desc &d);
 // Uniform grid, its FP32 mirror, the integrand blobs, d_h = 1 and the initial
 // state, copied to the member's (zeroed) buffers on `stream`.
 vp_status upload_member_init(const Member &mb, const Desc &d, cudaStream_t stream);
-// Table of 1/n, n < kInvTab (IEEE division on the host), for the descriptors.
+// Table for n < kInvTab (host arithmetic), for the descriptors, 32 bytes per
+// n: 1/n and 1/(n (n-1)) (IEEE divisions), log2 n as a float pair hi + lo.
 void inv_table(std::vector<double> &inv);
 // The FP32 path's constants of the damping power beta in a descriptor (n_hc set).
 void damp_consts(Desc &d, double beta);

@@ -404,7 +404,7 @@ static vp_status server_init(vp_server *S, const vp_server_config *cfg, void *st
     };
     const size_t o_desc = take(A * sizeof(Desc)), o_new = take(A * sizeof(Desc));
     const size_t o_tree = take((A + 1) * 4), o_axis = take((A + 1) * 4), o_ntree = take((A + 1) * 4);
-    const size_t o_done = take(A * 4), o_inv = take(kInvTab * sizeof(double));
+    const size_t o_done = take(A * 4), o_inv = take(kInvTabWords * sizeof(double));
     size_t o_slot[kGroupSlots][3];
     for (int s = 0; s < kGroupSlots; ++s) {
         o_slot[s][0] = take(A * 4);

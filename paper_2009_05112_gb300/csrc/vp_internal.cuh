@@ -21,7 +21,8 @@ constexpr int kSub = 4;            // CTAs of the allocation kernels per block o
 constexpr int kSubH = kTreeBlock / kSub;
 constexpr int kMaxPeaks = 64;
 constexpr int kMaxPoints = 256;
-constexpr int kInvTab = 4096;      // table of 1/n for small integers n
+constexpr int kInvTab = 4096;      // table of 1/n, 1/(n(n-1)) and log2 n for small integers n
+constexpr int kInvTabWords = 4 * kInvTab;  // 32 bytes per n: 1/n, 1/(n(n-1)), log2 n (2 floats), pad
 // several integrals from the same samples (App. B): at most kMaxOut outputs, the
 // upper triangle of their covariance kMaxTri entries, at most 2^22 hypercubes
 constexpr int kMaxOut = 8;
@@ -106,7 +107,8 @@ struct Desc {
     const float *prm32; // FP32 constants derived from the blob (FP32 path)
     uint32_t *n_h;     // [n_hc]
     uint64_t *off;     // [n_hc + 1] exclusive offsets; off[n_hc] = samples this iteration
-    const double *inv_tab; // [kInvTab] 1/n (IEEE), shared by the set
+    const double *inv_tab; // [kInvTab][4]: 1/n, 1/(n (n-1)) (IEEE), log2 n as a float pair
+                           // hi + lo, padding (one 32-byte sector per n); shared by the set
     double *s1, *s2;   // [2][n_hc] per-hypercube sums of v, v^2 (unscaled); iteration t
                        // accumulates into buffer t & 1 while the estimate of t clears the other
     double *dh;        // [n_hc] d_h of the latest estimate
