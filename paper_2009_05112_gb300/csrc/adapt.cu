@@ -167,12 +167,14 @@ __device__ __forceinline__ double damp_tn32(double t, float2 L, const Desc &d) {
 // k_estimate.  mode 0: from the moments (a6 + sigma_h + d_h), records the
 // iteration; mode 1: dh[] holds sigma_h, turn it into d_h and sum; mode 2:
 // dh[] holds d_h, sum only.
-// A cluster of 4 CTAs (256 threads each) serves one block of 1024 hypercubes,
-// so the per-hypercube FP64 work (square roots, the damping power) spreads
-// over four SMs.  CTA q holds terms 256q .. 256q + 255; the fixed-order tree
-// runs its first two halving steps across the cluster through distributed
-// shared memory (s = 512: CTAs 2, 3 -> 0, 1; s = 256: CTA 1 -> 0) and the
-// rest in CTA 0.
+// Four CTAs (256 threads each) serve one block of 1024 hypercubes, so the
+// per-hypercube FP64 work spreads over four SMs.  CTA q holds the terms
+// 4t + q: the fixed-order tree's halving levels 512 .. 4 join terms of one
+// residue class mod 4, so each CTA runs them on its own terms as levels
+// 128 .. 1 and stores its class's sum; the last CTA of the integral takes the
+// last two levels (classes 0 + 2 and 1 + 3, then their sum) for every block
+// before the tree over the blocks -- the same additions in the same order,
+// with no exchange between the CTAs of a block.
 // ---------------------------------------------------------------------------
 constexpr int kEstCtas = 4;
 
@@ -185,17 +187,10 @@ struct EstPre {
 };
 __device__ void finish_estimate(const Desc &d, double I, double V, double Sd, int mode,
                                 const EstPre &pre);
-__device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, int mode, const EstPre &pre,
-                                    double *red, bool *s_last);
-__device__ __forceinline__ void block_levels(const Desc &d, uint32_t k, double *red);
+__device__ __forceinline__ void block_levels(const Desc &d, uint64_t dst, double *red);
 __device__ __forceinline__ void estimate_last_cta(const Desc &d, uint32_t n_cta, int mode,
-                                                  const EstPre &pre, double *red, bool *s_last);
-
-struct EstShared {
-    double recv2[3][256];  // level 256: CTA 1's terms, received by CTA 0
-    double recv[3][256];   // level 512: CTA 2's (3's) terms, received by CTA 0 (1)
-    double red[3][256];
-};
+                                                  const EstPre &pre, double *red, bool *s_last,
+                                                  bool residues = false);
 
 // 1/n for n beyond the table (rare: a call, so that none of its FP64 work is
 // hoisted into the common path)
@@ -262,15 +257,13 @@ __device__ __forceinline__ D3 hcube_terms(const Desc &d, uint64_t h, int mode, u
     return v;
 }
 
-__global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 4)
     k_estimate(const Desc *desc, const uint32_t *tree_base, int n_int, int mode) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    __shared__ EstShared sm;
+    __shared__ double red[3 * 256];
     __shared__ bool s_last;
     pdl_wait();
     pdl_trigger();
-    const int rank = (int)cl.block_rank();
+    const int q = (int)(blockIdx.x % kEstCtas);  // residue class of this CTA
     const uint32_t tb = blockIdx.x / kEstCtas;
     const int b = owner_of(tree_base, n_int, tb);
     const Desc &d = desc[b];
@@ -284,56 +277,36 @@ __global__ void __cluster_dims__(kEstCtas, 1, 1) __launch_bounds__(256, 4)
         pre.n_samples = d.st->n_samples;
         pre.n_eval_total = d.st->n_eval_total;
     }
-    const D3 v = hcube_terms(d, (uint64_t)k * kTreeBlock + 256 * rank + t, mode, par);
+    const D3 v = hcube_terms(d, (uint64_t)k * kTreeBlock + 4 * t + q, mode, par);
     if (mode == 0) {  // clear the other histogram buffer, spread over this integral's CTAs
         const int bins = d.dim * d.n_g;
         double *hs = d.hsum + (size_t)(par ^ 1u) * bins;
         uint32_t *hc = d.hcnt + (size_t)(par ^ 1u) * bins;
         const int stride = (int)d.n_tree * kEstCtas * 256;
-        for (int i = (int)(k * kEstCtas + rank) * 256 + t; i < bins; i += stride) {
+        for (int i = (int)(k * kEstCtas + q) * 256 + t; i < bins; i += stride) {
             hs[i] = 0.0;
             hc[i] = 0u;
         }
     }
-    // s = 512: term t + 512 (CTA 2) joins term t (CTA 0); t + 768 (CTA 3) joins t + 256 (CTA 1)
-    if (rank >= 2) {
-        EstShared *dst = cl.map_shared_rank(&sm, rank - 2);
-        dst->recv[0][t] = v.a;
-        dst->recv[1][t] = v.b;
-        dst->recv[2][t] = v.c;
-    }
-    cl.sync();
-    D3 a = v;
-    if (rank < 2) {
-        a.a = __dadd_rn(v.a, sm.recv[0][t]);
-        a.b = __dadd_rn(v.b, sm.recv[1][t]);
-        a.c = __dadd_rn(v.c, sm.recv[2][t]);
-    }
-    // s = 256: term t + 256 (CTA 1) joins term t (CTA 0), through a second
-    // buffer (so CTA 0 need not finish reading the first); afterwards only
-    // CTA 0's shared memory is read, so CTAs 1-3 may leave
-    if (rank == 1) {
-        EstShared *dst = cl.map_shared_rank(&sm, 0);
-        dst->recv2[0][t] = a.a;
-        dst->recv2[1][t] = a.b;
-        dst->recv2[2][t] = a.c;
-    }
-    cl.sync();
-    if (rank != 0) return;
-    double *r0 = sm.red[0], *r1 = sm.red[1], *r2 = sm.red[2];
-    r0[t] = __dadd_rn(a.a, sm.recv2[0][t]);
-    r1[t] = __dadd_rn(a.b, sm.recv2[1][t]);
-    r2[t] = __dadd_rn(a.c, sm.recv2[2][t]);
-    estimate_block_tail(d, k, mode, pre, &sm.red[0][0], &s_last);
+    red[t] = v.a;
+    red[256 + t] = v.b;
+    red[512 + t] = v.c;
+    // the halving levels 512 .. 4 of the block join terms of one residue class
+    // mod 4 (term i and term i + s, s a multiple of 4): on this CTA's terms
+    // 4t + q they are the levels 128 .. 1 over t; the last two levels (2, 1)
+    // join the four classes' sums, in the last CTA
+    block_levels(d, 3 * (uint64_t)d.n_tree + 12 * (uint64_t)k + 3 * (uint64_t)q, red);
+    estimate_last_cta(d, d.n_tree * kEstCtas, mode, pre, red, &s_last, true);
 }
 
-// The rest of a block's fixed-order tree, one CTA of 256 threads: red[c][t]
-// (red = 3 x 256 doubles in shared memory) holds the sum of terms t, t + 256,
-// t + 512, t + 768 of series c (the first two halving levels); then the
-// levels 128 .. 1 and the block sum to part[3 k + c] (block_levels); then,
-// once per CTA, the ticket and in the last CTA of the integral the block sums
-// in the fixed tree order and the iteration's bookkeeping (estimate_last_cta).
-__device__ __forceinline__ void block_levels(const Desc &d, uint32_t k, double *red) {
+// A pairwise halving over 256 values, one CTA of 256 threads: red[c][t]
+// (red = 3 x 256 doubles in shared memory) holds value t of series c -- in
+// the wide form the sum of terms t, t + 256, t + 512, t + 768 of a block (its
+// first two halving levels), in the four-CTA form the term 4t + q; the
+// levels 128 .. 1 leave the sum in part[dst + c] (block_levels).  Then, once
+// per CTA, the ticket and in the last CTA of the integral the block sums in
+// the fixed tree order and the iteration's bookkeeping (estimate_last_cta).
+__device__ __forceinline__ void block_levels(const Desc &d, uint64_t dst, double *red) {
     const int t = threadIdx.x;
     double *r0 = red, *r1 = red + 256, *r2 = red + 512;
     __syncthreads();
@@ -352,12 +325,13 @@ __device__ __forceinline__ void block_levels(const Desc &d, uint32_t k, double *
         const double *r = w == 0 ? r0 : (w == 1 ? r1 : r2);
         double x = __dadd_rn(r[l], r[l + 32]);
         for (int s = 16; s >= 1; s >>= 1) x = __dadd_rn(x, __shfl_down_sync(0xffffffffu, x, s));
-        if (l == 0) d.part[3 * k + w] = x;
+        if (l == 0) d.part[dst + w] = x;
     }
 }
 
 __device__ __forceinline__ void estimate_last_cta(const Desc &d, uint32_t n_cta, int mode,
-                                                  const EstPre &pre, double *red, bool *s_last) {
+                                                  const EstPre &pre, double *red, bool *s_last,
+                                                  bool residues) {
     const int t = threadIdx.x;
     if (t < 96 && (t & 31) == 0) __threadfence();  // (the writers of part[]: lane 0 of warps 0-2)
     __syncthreads();
@@ -370,17 +344,24 @@ __device__ __forceinline__ void estimate_last_cta(const Desc &d, uint32_t n_cta,
     // last CTA of this integral: the block sums in the fixed tree order
     __threadfence();
     __syncthreads();
+    if (residues) {
+        // the block sums from their residue classes: the last two halving
+        // levels (term 0 += term 2, 1 += 3; then 0 += 1)
+        const double *r4 = d.part + 3 * (size_t)d.n_tree;
+        for (uint32_t i = t; i < 3 * d.n_tree; i += blockDim.x) {
+            const uint32_t k = i / 3, c = i - 3 * k;
+            const double *q = r4 + 12 * (size_t)k + c;
+            d.part[i] = __dadd_rn(__dadd_rn(__ldcg(q), __ldcg(q + 6)),
+                                  __dadd_rn(__ldcg(q + 3), __ldcg(q + 9)));
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
     double tot[3];
     block_tree_sum<3>(d.part, d.n_tree, red, tot);
     if (t != 0) return;
     d.st->done_est = 0u;
     finish_estimate(d, tot[0], tot[1], tot[2], mode, pre);
-}
-
-__device__ __forceinline__ void estimate_block_tail(const Desc &d, uint32_t k, int mode, const EstPre &pre,
-                                    double *red, bool *s_last) {
-    block_levels(d, k, red);
-    estimate_last_cta(d, d.n_tree, mode, pre, red, s_last);
 }
 
 // k_estimate for many blocks (large N_h): one CTA of 256 threads per block of
@@ -431,7 +412,7 @@ __global__ void __launch_bounds__(256, 4)
         red[t] = __dadd_rn(__dadd_rn(v0.a, v2.a), __dadd_rn(v1.a, v3.a));
         red[256 + t] = __dadd_rn(__dadd_rn(v0.b, v2.b), __dadd_rn(v1.b, v3.b));
         red[512 + t] = __dadd_rn(__dadd_rn(v0.c, v2.c), __dadd_rn(v1.c, v3.c));
-        block_levels(d, k, red);
+        block_levels(d, 3 * (uint64_t)k, red);
     }
     estimate_last_cta(d, (d.n_tree + (uint32_t)group - 1u) / (uint32_t)group, mode, pre, red,
                       &s_last);

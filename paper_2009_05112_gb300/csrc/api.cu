@@ -339,7 +339,7 @@ size_t vp::member_layout(Member &mb, size_t base) {
     const size_t M = mb.n_out > 1 ? mb.n_out : 0, MT = M * (M + 1) / 2;  // (App. B outputs)
     const size_t sz[B_COUNT] = {D * (G + 1) * 8, D * G * 8, mb.prm.size() * 8,
                                 mb.prm32.size() * 4, H * 4, (H + 1) * 8, 2 * H * 8, 2 * H * 8,
-                                H * 8, 2 * D * G * 8, 2 * D * G * 4, T * 3 * 8, T * kSub * 8, C * 8,
+                                H * 8, 2 * D * G * 8, 2 * D * G * 4, T * 15 * 8, T * kSub * 8, C * 8,
                                 C * 8, sizeof(State), 2 * H * M * 8, 2 * H * MT * 8,
                                 T * (M + MT) * 8, C * M * 8, C * MT * 8};
     for (int i = 0; i < B_COUNT; ++i) {

@@ -114,7 +114,8 @@ struct Desc {
     double *dh;        // [n_hc] d_h of the latest estimate
     double *hsum;      // [2][dim][n_g] sum v^2 per increment (unscaled), same double buffering
     uint32_t *hcnt;    // [2][dim][n_g] samples per increment
-    double *part;      // [n_tree][3] block partial sums (I, var, d)
+    double *part;      // [n_tree][3] block partial sums (I, var, d), then [n_tree][4][3]
+                       // the four residue classes' sums of each block (k_estimate)
     uint64_t *bsum;    // [n_tree kSub] sums of n_h over kSubH hypercubes, then their offsets
     double *hist_i, *hist_var;  // [hist_cap] iteration history
     State *st;
