@@ -490,13 +490,46 @@ def _sampling_ms(g, flush):
     steps (the step graph carries no events: as graph nodes they would add
     microseconds to every step); L2 flushed before each, as in the timed
     steps.  Mean over KERNEL_TIMING_ITERS."""
-    ms = []
+    import torch
+    ms, whole = [], []
+    s = torch.cuda.current_stream()
     for k in range(KERNEL_TIMING_ITERS):
         flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
         g.iterate()
         g.adapt()
+        e1.record(s)
         ms.append(g.last_sample_ms())
+        e1.synchronize()
+        whole.append(e0.elapsed_time(e1))
+    # the same iterations' estimate -> allocation -> offsets (and k_refine beside
+    # them): the eager iteration less its sampling launch
+    _LAST_CHAIN_MS[0] = sum(w - m for w, m in zip(whole, ms)) / len(ms)
     return sum(ms) / len(ms)
+
+
+_LAST_CHAIN_MS = [0.0]
+
+
+def _chain_view(n_hc, dim, n_g, hbm_gbs):
+    """The estimate -> allocation -> offsets chain (steps a6-a7) against HBM:
+    algorithmic bytes per iteration -- per hypercube S1, S2, n_h read, d_h
+    written and the other buffer's S1, S2 cleared (44 B), d_h read and n_h
+    written (12 B), n_h read and the offset written (12 B); the other
+    histogram buffer cleared (12 B per increment) -- over the chain's time:
+    CUDA events around each eager iteration (iterate + adapt) less its
+    sampling launch, in the iterations that time the sampling kernel (k_refine
+    runs beside the chain on its side stream)."""
+    nbytes = 68.0 * n_hc + 12.0 * dim * n_g
+    ms = _LAST_CHAIN_MS[0]
+    out = {"bytes_per_iteration": nbytes, "ms": ms, "peak_gbs": hbm_gbs,
+           "note": "estimate, allocation and offsets, eager iterations less the sampling "
+                   "launch; peak = MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if ms > 0:
+        out["achieved_gbs"] = nbytes / (ms * 1e-3) / 1e9
+        out["frac"] = out["achieved_gbs"] / hbm_gbs
+    return out
 
 
 _ATOMIC_RATES = {}
@@ -591,6 +624,8 @@ def _single_summary(workload, args, inputs, vegasp, flush, n_sm, max_mhz):
            "n_ev": prob.n_ev, "dim": prob.dim, "n_hc": g.n_hc,
            "kernel_ms": k1, "fp32_frac": roof["frac"], "issue_frac": roof["issue_view"]["frac"],
            "atomics_frac": roof["atomics_view"]["frac"],
+           "chain": _chain_view(g.n_hc, prob.dim, prob.n_g,
+                                measured_peaks().get("hbm_gbs", 6800.0)),
            "traffic": roof["traffic"], "ncu_pct_of_peak_elapsed": roof["ncu_pct_of_peak_elapsed"],
            "clocks": clocks, "sample_launch": g.tuning(),
            "integral": dict(_integral(g, prob, False), exact=prob.exact)}
@@ -734,6 +769,7 @@ def run_ours(args):
                             "copied to host memory (vp_step_read, read one call later) + the "
                             "final result, wall clock" % args.steps},
             "roofline": roof, "clocks": clocks,
+            "chain": _chain_view(g.n_hc, prob.dim, prob.n_g, peaks.get("hbm_gbs", 6800.0)),
             # sample, estimate, alloc, offsets, refine (+ the task prefix for the task
             # kernel, + the several-outputs estimate)
             "gpu_launches": (5 + (g.tuning()["scheme"] == "tasks") + bayes) * args.steps,
