@@ -525,7 +525,9 @@ def _chain_view(n_hc, dim, n_g, hbm_gbs):
     ms = _LAST_CHAIN_MS[0]
     out = {"bytes_per_iteration": nbytes, "ms": ms, "peak_gbs": hbm_gbs,
            "note": "estimate, allocation and offsets, eager iterations less the sampling "
-                   "launch; peak = MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                   "launch: an upper bound on the chain in the step graph (eager launches "
+                   "add host gaps and run k_refine after the estimate, not beside it), so "
+                   "frac is a lower bound; peak = MEASURED_PEAKS.json hbm_gbs (of measured)"}
     if ms > 0:
         out["achieved_gbs"] = nbytes / (ms * 1e-3) / 1e9
         out["frac"] = out["achieved_gbs"] / hbm_gbs
