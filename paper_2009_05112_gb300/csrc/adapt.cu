@@ -433,7 +433,10 @@ __device__ void finish_estimate(const Desc &d, double I, double V, double Sd, in
         const bool normal = Sd >= 2.2250738585072014e-308 && c >= 2.2250738585072014e-308 &&
                             c <= 1.7976931348623157e308;
         st->alloc_c = normal ? c : 0.0;
-        st->alloc_dmin = 4.4501477170144028e-308 / d.n_ev_d;  // 2^-1021 / N_ev
+        // d_h >= 2^-1021 keeps N_ev d_h normal for every N_ev >= 1 (a constant:
+        // no FP64 division in this serial step; the rare d_h below it take the
+        // exact quotient)
+        st->alloc_dmin = 4.4501477170144028e-308;
     }
     if (mode == 0) {
         const uint32_t tt = pre.t;
