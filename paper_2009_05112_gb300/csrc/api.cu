@@ -932,6 +932,8 @@ void vp::set_task(Group &g, double expect) {
 
 // Launches of fewer samples than this keep the planned shape untuned.
 constexpr double kTuneMinSamples = 262144.0;
+// Launches of at least this many samples also try the dynamic tail.
+constexpr double kTailMinSamples = 16777216.0;
 
 static bool tune_due(const Set &s, const Group &g) {
     return !g.tuned || (!g.tuned_final && s.iters >= (uint64_t)kRetuneIt);
@@ -999,10 +1001,8 @@ static vp_status tune(Set &s, cudaStream_t stream) {
                             ctas = std::min(ctas, blocks) / cs * cs;
                             if (ctas < (int)(0.9 * blocks)) continue;
                         }
-                        // (the dynamic tail, scheme 2, is not among the candidates:
-                        // measured, it wins only while one hypercube holds most of
-                        // an iteration's samples, and loses on the settled
-                        // allocations the tuner sees; vp_set_tuning selects it)
+                        // (the dynamic tail, scheme 2, is timed below for large
+                        // launches only, on the best static shape)
                         cands.push_back({true, ctas, cs, g.r, threads, kStaticShare});
                     }
                 }
@@ -1035,6 +1035,30 @@ static vp_status tune(Set &s, cudaStream_t stream) {
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
+            }
+        }
+        if (best.one && expect >= kTailMinSamples) {
+            // the best static shape with a dynamic tail (scheme 2): measured, the
+            // SMs' differing speeds leave an even split waiting on the slowest
+            // at large launches (the eight-D four peaks at N_ev = 1e8: 3.54 ->
+            // 2.96 ms), while at small ones the queue costs more than it evens
+            Cand twin = best;
+            twin.static16 = kTailShare;
+            g.one = twin.one;
+            g.blocks = twin.blocks;
+            g.cs = twin.cs;
+            g.r = twin.r;
+            g.threads_one = twin.threads;
+            g.static16 = twin.static16;
+            g.args1.r = twin.r;
+            g.args1.static16 = twin.static16;
+            set_task(g, expect);
+            float ms = 0.f;
+            vp_status st = time_group(s, g, stream, &ms);
+            if (st != VP_OK) return st;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = twin;
             }
         }
         g.one = best.one;

@@ -388,6 +388,36 @@ def test_three_peaks_d4_fp64_iterations_match_oracle(graph):
     assert abs(r["mean"] - prob.exact) < 3 * r["sdev"]
 
 
+def test_static_head_dynamic_tail_matches_oracle():
+    """The sampling launch with a static head and a dynamic tail (launch
+    scheme 2: half of the samples split evenly over the warps, the rest pulled
+    in chunks from 32 queues, which the autotuner picks for large launches):
+    the 4-D three-peak workload's ten FP64 iterations against the oracle, as
+    with the static split -- I_j and sigma_j^2 within 1e-10, every n_h
+    identical, edges within 1e-10 (every sample drawn once, whichever warp
+    takes it)."""
+    prob = inputs.three_peaks_d4()
+    g = gpu_of(prob)
+    g.set_tuning("static-dynamic", 152, 256, 1, 8)
+    assert g.tuning()["scheme"] == "static-dynamic"
+    o = oracle_of(prob)
+    for it in range(prob.n_it):
+        g.iterate()
+        o.iterate()
+        if it == 0:
+            hs, hc = g.hist()
+            assert np.array_equal(hc, o.hcnt)
+        g.adapt()
+        o.adapt()
+        n_h, off = g.alloc()
+        assert np.array_equal(n_h, o.n_h), it
+        assert np.max(np.abs(g.edges() - o.edges)) <= 1e-10, it
+    assert g.tuning()["scheme"] == "static-dynamic"
+    I, Vv = g.history()
+    np.testing.assert_allclose(I, o.I, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(Vv, o.var, rtol=1e-10, atol=0)
+
+
 @pytest.mark.parametrize("kind,dim", [(1, 4), (2, 8), (3, 3)])
 def test_other_integrands_fp64_iterations_match_oracle(kind, dim):
     rng = np.random.default_rng(kind * 31 + dim)
