@@ -190,19 +190,22 @@ def measured_peaks():
 
 
 # ncu summaries of the sampling kernel, one per workload, under profiles/
-PROFILE_FILES = {"ball_d20": "sample_kernel_ball_d20.txt",
-                 "four_peaks_d8": "sample_kernel_four_peaks_d8.txt"}
+PROFILE_FILES = {("ball_d20", 10 ** 7): "sample_kernel_ball_d20.txt",
+                 ("four_peaks_d8", 10 ** 6): "sample_kernel_four_peaks_d8.txt",
+                 ("four_peaks_d8", 10 ** 8): "sample_kernel_four_peaks_d8_n1e8.txt"}
 # per-pipe figures the summaries carry, as percentages of the peak sustained
 # over ELAPSED cycles (ncu's .pct_of_peak_sustained_elapsed)
 PIPE_KEYS = ["sm__pipe_fma_cycles_active", "sm__pipe_alu_cycles_active",
              "sm__inst_executed_pipe_xu", "smsp__issue_active"]
 
 
-def profile_figures(workload, kernel_src_hash):
-    """The committed ncu summary of the workload's sampling kernel, if it was
-    taken on the current kernel source: {"traffic_per_sample": DRAM bytes per
-    sample of the profiled launch, "pipes_pct_elapsed": {...}}; else None."""
-    name = PROFILE_FILES.get(workload)
+def profile_figures(workload, kernel_src_hash, n_ev):
+    """The committed ncu summary of the workload's sampling kernel at this N_ev
+    (the traffic per sample grows with the hypercubes' moments, so it is kept
+    per size), if it was taken on the current kernel source:
+    {"traffic_per_sample": DRAM bytes per sample of the profiled launch,
+    "pipes_pct_elapsed": {...}}; else None."""
+    name = PROFILE_FILES.get((workload, int(n_ev)))
     if not name:
         return None
     try:
@@ -583,7 +586,7 @@ def _sample_roofline(workload, prob, n_peaks, samples_per_step, k1_ms, step_ms, 
     issue_peak = n_sm * 128 * max_mhz * 1e6 / 1e12      # lane operations/s, Tops/s
     tflops = flops * samples_per_step / (k1_ms / 1e3) / 1e12
     tops = ops * samples_per_step / (k1_ms / 1e3) / 1e12
-    prof = profile_figures(workload, kernel_source_hash())
+    prof = profile_figures(workload, kernel_source_hash(), prob.n_ev)
     roof = {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": tflops / fp32_peak,
             "traffic": (prof["traffic_per_sample"] * samples_per_step) if prof else None,

@@ -32,13 +32,14 @@ def test_chain_bytes():
 def test_committed_profiles_parse():
     """Each committed sampling-kernel summary names the source it was taken on
     and carries the DRAM bytes and the pipe percentages the bench line reads."""
-    for workload, name in bench.PROFILE_FILES.items():
+    for (workload, n_ev), name in bench.PROFILE_FILES.items():
         text = open(os.path.join(bench.ROOT, "profiles", name)).read()
         keys = dict(line.split(":", 1) for line in text.splitlines()[:8] if ":" in line)
         assert len(keys["kernel_source_sha1"].strip()) == 40
         assert int(keys["profiled_samples"]) > 0 and int(keys["dram_bytes_per_launch"]) > 0
         for k in bench.PIPE_KEYS:
             assert 0.0 < float(keys[k + "_pct_elapsed"].split()[0]) < 100.0
-        fig = bench.profile_figures(workload, keys["kernel_source_sha1"].strip())
+        fig = bench.profile_figures(workload, keys["kernel_source_sha1"].strip(), n_ev)
         assert fig is not None and fig["traffic_per_sample"] > 0
-        assert bench.profile_figures(workload, "0" * 40) is None
+        assert bench.profile_figures(workload, "0" * 40, n_ev) is None
+        assert bench.profile_figures(workload, keys["kernel_source_sha1"].strip(), 12345) is None
