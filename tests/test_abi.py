@@ -126,3 +126,24 @@ def test_product_never_touches_the_oracle():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "vegasp_oracle" not in text and "liboracle" not in text, fn
+
+
+@pytest.mark.parametrize("case", ["null", "hc0", "hc_big", "ev1", "ev_big"])
+def test_alloc_static_rejects_on_host(lib, case):
+    """vp_alloc_static checks its arguments before it touches a device: NULL
+    buffers, n_hc outside 1 .. 4,194,304 and n_ev outside 2 .. 2^32 - 3 are
+    VP_EINVAL (the buffers below are never dereferenced)."""
+    from paper_2009_05112_gb300 import vegasp
+    fake = ctypes.c_void_p(256)
+    n_hc, n_ev, dh = 1024, 10_000, fake
+    if case == "null": dh = None
+    if case == "hc0": n_hc = 0
+    if case == "hc_big": n_hc = 4_194_305
+    if case == "ev1": n_ev = 1
+    if case == "ev_big": n_ev = 2 ** 32 - 2
+    assert lib.vp_alloc_static(dh, n_hc, n_ev, 0, fake, fake, None) == vegasp.VP_EINVAL
+
+
+def test_atomic_rate_probe_rejects_null(lib):
+    from paper_2009_05112_gb300 import vegasp
+    assert lib.vp_shared_atomic_rate(0, None) == vegasp.VP_EINVAL
